@@ -1,0 +1,405 @@
+"""Pins of the FP64 oracle against what optics and mathematics fix (no GPU).
+
+Each test checks the oracle against something other than itself: a closed form, an
+independent textbook formula, an invariant, brute force, or an independent library
+implementation.  Chosen so that a dropped term, a wrong sign, a swapped index or operand
+in the oracle fails at least one of them.
+"""
+import math
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+from paper_1912_05494_gb300 import scenes as S
+
+
+# ----------------------------------------------------------------------------- helpers
+def fresnel_real_form(theta, n, k):
+    """Reflectance of air -> (n + i k) written in real arithmetic (Born & Wolf form with the
+    auxiliary quantities a, b); an independent route to the complex-amplitude formula."""
+    s, c = math.sin(theta), math.cos(theta)
+    A = n * n - k * k - s * s
+    B = math.sqrt(A * A + 4 * n * n * k * k)
+    a = math.sqrt(0.5 * (B + A))
+    b2 = 0.5 * (B - A)
+    Rs = (a * a + b2 - 2 * a * c + c * c) / (a * a + b2 + 2 * a * c + c * c)
+    if c == 0.0:
+        return 1.0, 1.0, 1.0
+    st = s * math.tan(theta)
+    Rp = Rs * (a * a + b2 - 2 * a * st + st * st) / (a * a + b2 + 2 * a * st + st * st)
+    return 0.5 * (Rs + Rp), Rs, Rp
+
+
+def slab_by_bounce_sum(R, tau, n_terms=400):
+    """Slab reflectance/transmittance by explicitly summing the bounce series term by term."""
+    Rsum, Tsum = R, 0.0
+    amp = (1 - R) * tau  # entered and crossed once
+    for m in range(n_terms):
+        Tsum += amp * (1 - R)          # leaves through the far face
+        amp *= R * tau                 # reflected back across
+        Rsum += amp * (1 - R)          # leaves through the near face
+        amp *= R * tau
+    return Rsum, Tsum
+
+
+def custom_scene(tris, mats, sky=1.0, sky_mode=0, sun=None, sun_dir=(0, 0, 1), half=0.0, lam=550.0, eps=1e-5):
+    """Build a SceneData from a list of (v0, v1, v2, material) and material dicts."""
+    v = np.array([p for t in tris for p in t[:3]], np.float32)
+    idx = np.arange(v.shape[0], dtype=np.uint32).reshape(-1, 3)
+    m = np.array([t[3] for t in tris], np.uint16)
+    nm = len(mats)
+    return S.SceneData(
+        vertices=v, indices=idx, tri_material=m,
+        mat_kind=np.array([q["kind"] for q in mats], np.int32),
+        mat_thickness=np.array([q.get("d", 0.0) for q in mats], np.float32),
+        table_nm=np.array([lam], np.float32),
+        mat_n=np.array([[q.get("n", 1.0)] for q in mats], np.float32),
+        mat_k=np.array([[q.get("k", 0.0)] for q in mats], np.float32),
+        mat_albedo=np.array([[q.get("albedo", 0.0)] for q in mats], np.float32),
+        sky=np.array([sky], np.float32), sky_mode=sky_mode,
+        sun_dir=np.asarray(sun_dir, np.float32), sun_half_angle=half,
+        sun=None if sun is None else np.array([sun], np.float32), ray_eps=eps,
+    )
+
+
+def quad(a, b, c, d, mat):
+    return [(a, b, c, mat), (a, c, d, mat)]
+
+
+def box_tris(lo, hi, mat):
+    x0, y0, z0 = lo
+    x1, y1, z1 = hi
+    p = [(x0, y0, z0), (x1, y0, z0), (x1, y1, z0), (x0, y1, z0),
+         (x0, y0, z1), (x1, y0, z1), (x1, y1, z1), (x0, y1, z1)]
+    out = []
+    for a, b, c, d in ((0, 3, 2, 1), (4, 5, 6, 7), (0, 1, 5, 4), (2, 3, 7, 6), (1, 2, 6, 5), (0, 4, 7, 3)):
+        out += quad(p[a], p[b], p[c], p[d], mat)
+    return out
+
+
+# ----------------------------------------------------------------------------- Fresnel
+@pytest.mark.parametrize("n,k", [(1.5338842975, 0.0), (1.52, 5e-7), (1.55, 1e-3), (0.2, 3.5), (2.4, 0.6)])
+def test_fresnel_normal_incidence_closed_form(orc, n, k):
+    R, Rs, Rp = orc.fresnel(1.0, 1.0, n, k)
+    expect = ((n - 1) ** 2 + k * k) / ((n + 1) ** 2 + k * k)
+    assert abs(R - expect) < 1e-14
+    assert abs(Rs - Rp) < 1e-15  # s and p coincide at normal incidence
+
+
+def test_fresnel_550nm_value(orc):
+    n = 1.52 + 0.0042 / 0.55**2  # 1.533884...
+    R, _, _ = orc.fresnel(1.0, 1.0, n, 0.0)
+    assert abs(n - 1.533884) < 1e-6 and abs(R - 0.0443936) < 1e-7
+
+
+@pytest.mark.parametrize("n,k", [(1.52, 0.0), (1.52, 1e-5), (1.58, 0.02), (0.27, 2.9), (3.9, 0.02)])
+def test_fresnel_oblique_matches_real_arithmetic_form(orc, n, k):
+    thetas = np.linspace(0.0, math.radians(89.5), 40)
+    R, Rs, Rp = orc.fresnel(np.cos(thetas), 1.0, n, k)
+    for i, th in enumerate(thetas):
+        r, rs, rp = fresnel_real_form(th, n, k)
+        assert abs(Rs[i] - rs) < 1e-12, (th, Rs[i], rs)
+        assert abs(Rp[i] - rp) < 1e-12, (th, Rp[i], rp)
+        assert abs(R[i] - r) < 1e-12
+
+
+def test_fresnel_brewster_and_grazing(orc):
+    n = 1.5
+    tb = math.atan(n)
+    _, _, Rp = orc.fresnel(math.cos(tb), 1.0, n, 0.0)
+    assert Rp < 1e-28
+    R, _, _ = orc.fresnel(0.0, 1.0, n, 0.0)
+    assert abs(R - 1.0) < 1e-12
+
+
+def test_fresnel_total_internal_reflection_and_reciprocity(orc):
+    n = 1.5
+    crit = math.asin(1.0 / n)
+    for th in np.linspace(crit + 1e-4, math.radians(89.9), 25):
+        R, _, _ = orc.fresnel(math.cos(th), n, 1.0, 0.0)
+        assert abs(R - 1.0) < 1e-12
+    for th_i in np.linspace(0.0, math.radians(85.0), 25):  # air -> glass vs glass -> air (Stokes)
+        th_t = math.asin(math.sin(th_i) / n)
+        Ra, _, _ = orc.fresnel(math.cos(th_i), 1.0, n, 0.0)
+        Rg, _, _ = orc.fresnel(math.cos(th_t), n, 1.0, 0.0)
+        assert abs(Ra - Rg) < 1e-12
+
+
+# ----------------------------------------------------------------------------- absorption / slab
+def test_beer_lambert_closed_form(orc):
+    tau = orc.beer_lambert(5e-7, 3e-3, 550.0)
+    assert abs(tau - 0.966309) < 5e-7
+    assert abs(tau - math.exp(-4 * math.pi * 5e-7 * 3e-3 / 550e-9)) < 1e-15
+    assert orc.beer_lambert(1e-5, 0.0, 500.0) == 1.0
+    a, b = orc.beer_lambert(2e-6, 1e-3, 480.0), orc.beer_lambert(2e-6, 2.5e-3, 480.0)
+    assert abs(a * b - orc.beer_lambert(2e-6, 3.5e-3, 480.0)) < 1e-15
+
+
+@pytest.mark.parametrize("theta_deg", [0.0, 20.0, 45.0, 70.0, 85.0, 89.0])
+@pytest.mark.parametrize("k", [0.0, 5e-7, 1e-5, 3e-4])
+def test_slab_closed_form_vs_bounce_sum(orc, theta_deg, k):
+    n, d, lam = 1.53, 3.2e-3, 610.0
+    th = math.radians(theta_deg)
+    R, _, _ = fresnel_real_form(th, n, k)
+    cos_t = math.sqrt(1 - (math.sin(th) / n) ** 2)
+    tau = math.exp(-4 * math.pi * k * d / cos_t / (lam * 1e-9))
+    Re, Te = slab_by_bounce_sum(R, tau, 4000)
+    Rs, Ts = orc.slab(math.cos(th), n, k, d, lam)
+    assert abs(Rs - Re) < 1e-10 and abs(Ts - Te) < 1e-10
+    if k == 0.0:
+        assert abs(Rs + Ts - 1.0) < 1e-12
+
+
+def test_slab_table_values(orc):
+    """R_slab + T_slab at normal incidence, k = 5e-7, d = 3 mm (derived from the closed forms)."""
+    for lam, want in ((380, 0.951720), (550, 0.966361), (730, 0.974539)):
+        n = 1.52 + 0.0042 / (lam / 1000.0) ** 2
+        Rs, Ts = orc.slab(1.0, n, 5e-7, 3e-3, lam)
+        assert abs(Rs + Ts - want) < 1e-6
+
+
+# ----------------------------------------------------------------------------- tracer vs series
+def _ortho_cam(theta_deg, w=4, h=4):
+    th = math.radians(theta_deg)
+    pos = (0.0, -math.cos(th), math.sin(th))
+    return S.CameraData(pos=pos, look_at=(0.0, 0.0, 0.0), up=(0.0, 0.0, 1.0), vfov_deg=1.0,
+                        width=w, height=h, ortho=1, ortho_height=0.02)
+
+
+@pytest.mark.parametrize("theta_deg", [0.0, 30.0, 60.0])
+def test_explicit_tracer_matches_slab_series(orc, theta_deg):
+    """A solid glass slab traced ray by ray (refraction, internal reflections, Beer-Lambert
+    along the refracted path) converges to the slab closed form; at depth 6 it equals the
+    truncated bounce sum R + (1-R)^2 tau sum_{m<5} (R tau)^m at normal incidence."""
+    n, k, d, lam = 1.533, 2e-5, 3e-3, 550.0
+    sc = custom_scene(box_tris((-0.5, 0.0, -0.5), (0.5, d, 0.5), 0), [{"kind": S.MAT_SOLID, "n": n, "k": k}])
+    osc = orc.OracleScene(sc)
+    cam = _ortho_cam(theta_deg)
+    spec = S.RenderSpec(lambda_nm=np.array([lam], np.float32), spp=1, seed=0, max_depth=60, mode=0)
+    film, _, _ = osc.render(cam, spec)
+    th = math.radians(theta_deg)
+    R, _, _ = fresnel_real_form(th, n, k)
+    cos_t = math.sqrt(1 - (math.sin(th) / n) ** 2)
+    tau = math.exp(-4 * math.pi * k * d / cos_t / (lam * 1e-9))
+    Re, Te = slab_by_bounce_sum(R, tau)
+    n32 = float(np.float32(n))  # the scene stores n in float32
+    assert np.allclose(film, Re + Te, rtol=2e-7, atol=0), (film.ravel()[:3], Re + Te, n32)
+    if theta_deg == 0.0:
+        spec6 = S.RenderSpec(lambda_nm=np.array([lam], np.float32), spp=1, seed=0, max_depth=6, mode=0)
+        f6, _, _ = osc.render(cam, spec6)
+        trunc = R + (1 - R) ** 2 * tau * sum((R * tau) ** m for m in range(5))
+        assert np.allclose(f6, trunc, rtol=2e-7, atol=0)
+
+
+def test_furnace_lossless_glass_is_white(orc):
+    """k = 0 glass under a uniform sky of radiance 1: every pixel is 1 up to the (tiny)
+    depth-truncation remainder -- Fresnel R + T = 1, no energy made or lost."""
+    sc = custom_scene(box_tris((-0.5, 0.0, -0.5), (0.5, 0.003, 0.5), 0), [{"kind": S.MAT_SOLID, "n": 1.52, "k": 0.0}])
+    osc = orc.OracleScene(sc)
+    cam = S.CameraData(pos=(0.0, -1.0, 0.0), look_at=(0, 0, 0), up=(0, 0, 1), vfov_deg=60.0, width=24, height=24)
+    spec = S.RenderSpec(lambda_nm=np.array([550.0], np.float32), spp=1, seed=0, max_depth=40, mode=0)
+    film, _, _ = osc.render(cam, spec)
+    assert np.all(np.abs(film - 1.0) < 1e-9)
+
+
+def test_camera_field_of_view_and_symmetry(orc):
+    """Config-1 slab: with vfov 60 deg at 1 m, columns 0-3 and 60-63 miss the +-0.5 m slab
+    (sky = 1 exactly) and columns 4-59 see glass; the image is mirror-symmetric."""
+    sc, cam, spec = S.slab_scene(0)
+    film, _, _ = orc.OracleScene(sc).render(cam, spec)
+    img = film.reshape(64, 64, 16)
+    assert np.all(img[:, :4] == 1.0) and np.all(img[:, 60:] == 1.0)
+    assert np.all(img[:4, :] == 1.0) and np.all(img[60:, :] == 1.0)
+    assert np.all(img[4:60, 4:60] < 0.999)
+    assert np.allclose(img, img[:, ::-1], rtol=0, atol=1e-6)  # side-face triangulation is not mirror-symmetric
+    assert np.allclose(img, img[::-1, :], rtol=0, atol=1e-6)
+
+
+def test_mc_estimator_is_unbiased_against_splitting(orc):
+    """Monte Carlo branching (reflect with P = R) averages to the deterministic split tree."""
+    n, k, d = 1.55, 1e-5, 3e-3
+    sc = custom_scene(box_tris((-0.5, 0.0, -0.5), (0.5, d, 0.5), 0), [{"kind": S.MAT_SOLID, "n": n, "k": k}])
+    osc = orc.OracleScene(sc)
+    cam = _ortho_cam(40.0, w=2, h=2)
+    lam = np.array([550.0], np.float32)
+    det, _, _ = osc.render(cam, S.RenderSpec(lambda_nm=lam, spp=1, seed=0, max_depth=8, mode=0))
+    mc, paths, _ = osc.render(cam, S.RenderSpec(lambda_nm=lam, spp=40000, seed=7, max_depth=8, mode=1),
+                              want_paths=True)
+    se = paths.std() / math.sqrt(paths.size)
+    assert abs(mc.mean() - det.mean()) < 4 * se + 1e-9, (mc.mean(), det.mean(), se)
+
+
+# ----------------------------------------------------------------------------- NEE / sun (Eq. 3)
+def _floor_scene(orc, extra=(), extra_mats=(), sky=1.0, sun=1000.0):
+    elev = math.radians(35.0)
+    sdir = (0.0, -math.cos(elev), math.sin(elev))
+    tris = quad((-100, -100, 0), (100, -100, 0), (100, 100, 0), (-100, 100, 0), 0) + list(extra)
+    mats = [{"kind": S.MAT_DIFFUSE, "albedo": 0.5}] + list(extra_mats)
+    sc = custom_scene(tris, mats, sky=sky, sky_mode=1, sun=sun, sun_dir=sdir, half=math.radians(0.2665))
+    return orc.OracleScene(sc), sdir
+
+
+def _floor_cam():
+    return S.CameraData(pos=(0, 0, 1.0), look_at=(0, 0, 0), up=(0, 1, 0), vfov_deg=1.0, width=16, height=16,
+                        ortho=1, ortho_height=0.5)
+
+
+def test_nee_open_sky_closed_form(orc):
+    """Lambertian floor, albedo rho, under a sky L_sky (upper hemisphere) and a sun disc of
+    half-angle a at elevation e: pixel = rho L_sky + rho L_sun sin(e) sin^2(a)."""
+    osc, _ = _floor_scene(orc)
+    spec = S.RenderSpec(lambda_nm=np.array([550.0], np.float32), spp=64, seed=3, max_depth=1, mode=1)
+    film, _, _ = osc.render(_floor_cam(), spec)
+    a = math.radians(0.2665)
+    want = 0.5 * 1.0 + 0.5 * 1000.0 * math.sin(math.radians(35.0)) * math.sin(a) ** 2
+    assert abs(film.mean() / want - 1.0) < 5e-4, (film.mean(), want)
+
+
+def test_nee_through_thin_slab_and_blocked(orc):
+    """The same floor, sky off, with a vertical wall between the floor and the sun: a thin
+    glass slab multiplies the sun term by its transmittance; a diffuse wall blocks it."""
+    elev = math.radians(35.0)
+    a = math.radians(0.2665)
+    n, k, d, lam = 1.52, 2e-6, 4e-3, 550.0
+    wall = quad((-100, -5, 0), (-100, -5, 100), (100, -5, 100), (100, -5, 0), 1)
+    osc, _ = _floor_scene(orc, extra=wall, extra_mats=[{"kind": S.MAT_SLAB, "n": n, "k": k, "d": d}], sky=0.0)
+    spec = S.RenderSpec(lambda_nm=np.array([lam], np.float32), spp=64, seed=4, max_depth=1, mode=1)
+    film, _, _ = osc.render(_floor_cam(), spec)
+    th = math.acos(math.cos(elev))  # angle between the sun direction and the wall normal (+-y)
+    R, _, _ = fresnel_real_form(th, float(np.float32(n)), float(np.float32(k)))
+    cos_t = math.sqrt(1 - (math.sin(th) / float(np.float32(n))) ** 2)
+    tau = math.exp(-4 * math.pi * float(np.float32(k)) * float(np.float32(d)) / cos_t / (lam * 1e-9))
+    _, T = slab_by_bounce_sum(R, tau)
+    want = 0.5 * 1000.0 * math.sin(elev) * math.sin(a) ** 2 * T
+    assert abs(film.mean() / want - 1.0) < 1e-3, (film.mean(), want)
+    osc2, _ = _floor_scene(orc, extra=wall, extra_mats=[{"kind": S.MAT_DIFFUSE, "albedo": 0.3}], sky=0.0)
+    film2, _, _ = osc2.render(_floor_cam(), spec)
+    assert np.all(film2 == 0.0)
+
+
+# ----------------------------------------------------------------------------- geometry
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_bvh_closest_hit_equals_brute_force(orc, seed):
+    sc = S.tiny_scene(seed, n_triangles=64)
+    osc = orc.OracleScene(sc)
+    o, d = S.random_rays(seed + 10, 3000)
+    tb, pb = osc.closest(o, d, brute=True)
+    tv, pv = osc.closest(o, d, brute=False)
+    assert np.array_equal(pb, pv)
+    assert np.array_equal(tb, tv)
+    assert (pb >= 0).mean() > 0.3  # the test actually exercises hits
+
+
+def test_intersection_distance_against_planes(orc):
+    """Rays toward an axis-aligned quad at y = 2: t = (2 - o_y) / d_y; edges and the shared
+    diagonal are watertight for rays through exactly representable points."""
+    tris = quad((-1, 2, -1), (1, 2, -1), (1, 2, 1), (-1, 2, 1), 0)
+    sc = custom_scene(tris, [{"kind": S.MAT_DIFFUSE, "albedo": 0.5}])
+    osc = orc.OracleScene(sc)
+    rng = np.random.default_rng(0)
+    o = np.column_stack([rng.uniform(-3, 3, 500), rng.uniform(-3, 1.5, 500), rng.uniform(-3, 3, 500)])
+    target = np.column_stack([rng.uniform(-0.99, 0.99, 500), np.full(500, 2.0), rng.uniform(-0.99, 0.99, 500)])
+    diag = np.linspace(-1, 1, 33)[:, None] * np.array([[1.0, 0.0, 1.0]]) + np.array([[0.0, 2.0, 0.0]])
+    target = np.vstack([target, diag])
+    o = np.vstack([o, np.tile([[0.0, 0.0, 0.0]], (diag.shape[0], 1))])
+    d = target - o
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    t, prim = osc.closest(o, d)
+    assert np.all(prim >= 0)
+    assert np.allclose(t, (2.0 - o[:, 1]) / d[:, 1], rtol=1e-12, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------- sampling / spectra
+def test_cosine_and_cone_sampling_moments(orc):
+    g = (np.arange(200) + 0.5) / 200
+    u = np.array(np.meshgrid(g, g)).reshape(2, -1).T
+    rng = np.random.default_rng(0)
+    nrm = rng.normal(size=(1, 3))
+    nrm /= np.linalg.norm(nrm)
+    dirs = orc.cosine_dir(np.repeat(nrm, u.shape[0], 0), u)
+    assert np.allclose(np.linalg.norm(dirs, axis=1), 1.0, atol=1e-12)
+    c = dirs @ nrm[0]
+    assert c.min() >= 0 and abs(c.mean() - 2.0 / 3.0) < 1e-4  # E[cos] = 2/3 under cos-weighting
+    assert abs((c**2).mean() - 0.5) < 1e-4                     # E[cos^2] = 1/2
+    a = math.radians(0.2665)
+    h = 2 * math.sin(a / 2) ** 2
+    cd = orc.cone_dir(np.repeat(nrm, u.shape[0], 0), h, u) @ nrm[0]
+    assert cd.min() >= math.cos(a) - 1e-15
+    assert abs((1 - cd).mean() / (h / 2) - 1.0) < 1e-3      # uniform in solid angle
+
+
+def test_cmf_fit_properties(orc):
+    lam = np.arange(360.0, 831.0, 1.0)
+    x = orc.cmf(lam)
+    ints = x.sum(axis=0)  # equal-energy white: the three integrals are almost equal
+    assert np.all(np.abs(ints / ints.mean() - 1) < 2e-3)
+    assert abs(lam[np.argmax(x[:, 1])] - 557) <= 5 and abs(x[:, 1].max() - 1.0) < 0.02
+    xyz = orc.xyz(np.ones(81), S.SPECTRAL_GRID_81)  # equal-energy spectrum -> Y = 1, x = y ~ 1/3
+    assert abs(xyz[0, 1] - 1.0) < 1e-12
+    ch = xyz[0] / xyz[0].sum()
+    assert abs(ch[0] - 1 / 3) < 3e-3 and abs(ch[1] - 1 / 3) < 3e-3
+
+
+def test_planck_wien_and_stefan_boltzmann():
+    lam = np.linspace(100.0, 3000.0, 290001)
+    b = S.planck(lam, 6500.0)
+    assert abs(lam[np.argmax(b)] * 1e-9 * 6500.0 - 2.897772e-3) < 2e-7
+    lam2 = np.linspace(50.0, 200000.0, 4000001)
+    total = np.trapezoid(S.planck(lam2, 6500.0), lam2 * 1e-9)
+    assert abs(total * math.pi / (5.670374419e-8 * 6500.0**4) - 1) < 2e-3
+
+
+def test_cauchy_values():
+    n = S.cauchy_n(np.array([550.0]), 1.52, 0.0042)
+    assert abs(n[0] - 1.533884297) < 1e-9
+
+
+# ----------------------------------------------------------------------------- Philox
+_TRITON_PROBE = r"""
+import os, sys, json
+os.environ["TRITON_INTERPRET"] = "1"
+import numpy as np, torch, triton, triton.language as tl
+@triton.jit
+def k(c_ptr, k_ptr, out_ptr, N: tl.constexpr):
+    i = tl.arange(0, N)
+    c0 = tl.load(c_ptr + i * 4 + 0); c1 = tl.load(c_ptr + i * 4 + 1)
+    c2 = tl.load(c_ptr + i * 4 + 2); c3 = tl.load(c_ptr + i * 4 + 3)
+    k0 = tl.load(k_ptr + i * 2 + 0); k1 = tl.load(k_ptr + i * 2 + 1)
+    a, b, c, d = tl.random.philox_impl(c0, c1, c2, c3, k0, k1, 10)
+    tl.store(out_ptr + i * 4 + 0, a); tl.store(out_ptr + i * 4 + 1, b)
+    tl.store(out_ptr + i * 4 + 2, c); tl.store(out_ptr + i * 4 + 3, d)
+data = np.load(sys.argv[1])
+c = torch.from_numpy(data["ctr"].astype(np.int64)).to(torch.uint32)
+kk = torch.from_numpy(data["key"].astype(np.int64)).to(torch.uint32)
+out = torch.zeros_like(c)
+k[(1,)](c, kk, out, N=c.shape[0] // 4)
+np.save(sys.argv[2], out.to(torch.int64).numpy().astype(np.uint32))
+"""
+
+
+def test_philox_matches_independent_library_implementation(orc, tmp_path):
+    """Philox4x32-10 against Triton's implementation, run on the CPU by its interpreter."""
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(5)
+    n = 64
+    ctr = rng.integers(0, 2**32, (n, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    ctr[1] = 0xFFFFFFFF
+    keys = rng.integers(0, 2**32, (n, 2), dtype=np.uint64).astype(np.uint32)
+    keys[0] = 0
+    inp = tmp_path / "in.npz"
+    np.savez(inp, ctr=ctr.ravel(), key=keys.ravel())
+    outp = tmp_path / "out.npy"
+    script = tmp_path / "probe.py"
+    script.write_text(_TRITON_PROBE)
+    env = dict(os.environ, TRITON_INTERPRET="1", CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, str(script), str(inp), str(outp)], env=env, capture_output=True,
+                       text=True, timeout=600)
+    if r.returncode != 0:
+        pytest.skip("triton interpreter unavailable: " + r.stderr[-300:])
+    ref = np.load(outp).reshape(n, 4)
+    mine = np.vstack([orc.philox(ctr[i], keys[i]) for i in range(n)])
+    assert np.array_equal(mine, ref)
