@@ -1,0 +1,209 @@
+/*
+ * sdd.h -- C ABI of the GB300 spectral domain-decomposed glass ray tracer (libsdd.so).
+ *
+ * The library renders naturally lit scenes whose glass is described by optical constants
+ * n~(lambda) = n(lambda) + i k(lambda) (arXiv:1912.05494, Sec. 2, Eq. 1) and by per-tile
+ * distribution maps of (n, k, thickness) (Sec. 6), sampled on any wavelength set
+ * (Sec. 4: 81 samples, 380-780 nm).  The scene geometry is split once into subdomains
+ * (Sec. 5); rays are binned into per-subdomain queues, traversed against each
+ * subdomain's BVH, handed to the neighbouring subdomain's queue with their properties
+ * unchanged when they cross an interface (Sec. 5), shaded per wavelength with complex
+ * Fresnel reflection/transmission and Beer-Lambert absorption, and accumulated into a
+ * spectral / CIE XYZ film.
+ *
+ * Conventions
+ *   - Lengths in metres, wavelengths in nanometres, angles in radians unless a field name
+ *     says otherwise; +z is "up" for the sky.
+ *   - Scene inputs are HOST pointers; sdd_scene_create copies everything it needs.
+ *   - Render outputs are caller-owned DEVICE buffers unless the entry point says host.
+ *   - No C++ exception crosses this boundary.  Every call returns an sdd_status; on a
+ *     non-zero status sdd_last_error() gives a message (thread-local, valid until the
+ *     next call from that thread).
+ *   - Calls run on the CUDA stream given (a cudaStream_t passed as void*, NULL = the
+ *     legacy default stream) and return after the work they queued has finished, so that
+ *     device-side errors (queue overflow, stack overflow, watchdog) are reported by the
+ *     call that caused them.
+ *   - A scene handle must not be used by two threads at once.
+ */
+#ifndef SDD_H
+#define SDD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sdd_scene sdd_scene; /* opaque, owned by the library */
+
+typedef enum {
+  SDD_OK = 0,
+  SDD_ERR_ARG = -1,            /* invalid argument (message says which) */
+  SDD_ERR_OOM = -2,            /* device or host allocation failed */
+  SDD_ERR_CUDA = -3,           /* a CUDA runtime call failed */
+  SDD_ERR_QUEUE_OVERFLOW = -4, /* a ray queue would have exceeded its capacity */
+  SDD_ERR_TIMEOUT = -5,        /* a device-side loop hit its iteration cap */
+  SDD_ERR_STATE = -6,          /* call not valid in the handle's current state */
+  SDD_ERR_STACK = -7           /* BVH traversal stack would have overflowed */
+} sdd_status;
+
+/* Material kinds.  Sec. 6: the windows' glass is refractive only (no scattering); walls
+ * and lead came are not described by the paper and are modelled as Lambertian. */
+typedef enum {
+  SDD_MAT_DIELECTRIC_SOLID = 0, /* closed glass body: Fresnel at each interface, Beer-Lambert inside;
+                                   triangles must wind counter-clockwise seen from outside */
+  SDD_MAT_THIN_SLAB = 1,        /* zero-thickness tile of glass of thickness thickness_m: closed-form
+                                   series over internal reflections; two-sided */
+  SDD_MAT_HETERO_TILE = 2,      /* heterogeneous tile (thickness field, air bubbles) */
+  SDD_MAT_DIFFUSE = 3,          /* Lambertian, spectral albedo; two-sided */
+  SDD_MAT_OPAQUE = 4            /* absorbs everything */
+} sdd_mat_kind;
+
+typedef struct {
+  int kind;               /* sdd_mat_kind */
+  int n_lambda;           /* length of the tables below (>= 1) */
+  const float* lambda_nm; /* ascending table grid; tables are interpolated linearly and
+                             clamped at the ends */
+  const float* n;         /* real index n(lambda) (Eq. 1); glass kinds only, may be NULL otherwise */
+  const float* k;         /* absorption index k(lambda) >= 0 (Eq. 1); glass kinds only */
+  float thickness_m;      /* THIN_SLAB / HETERO_TILE thickness */
+  const float* albedo;    /* DIFFUSE albedo(lambda) in [0,1]; may be NULL otherwise */
+  int tile_param_id;      /* HETERO_TILE: index into the tile set */
+} sdd_material;
+
+/* Natural lighting: a uniform sky and a sun disc, both spectral (Eq. 3 reads the sun as one
+ * directional source; escaping rays see the sky). */
+typedef struct {
+  int n_lambda;
+  const float* lambda_nm;     /* ascending table grid of the two spectra */
+  const float* sky_radiance;  /* [n_lambda] */
+  int sky_mode;               /* 0: every direction, 1: only directions with z > 0 */
+  float sun_dir[3];           /* toward the sun (normalised by the library) */
+  float sun_half_angle_rad;   /* <= 0 or sun_radiance == NULL: no sun */
+  const float* sun_radiance;  /* [n_lambda] radiance inside the disc, or NULL */
+} sdd_illuminant;
+
+typedef struct {
+  int n_vertices;
+  const float* vertices;                 /* [n_vertices][3] */
+  int n_triangles;
+  const uint32_t* indices;               /* [n_triangles][3] */
+  const uint16_t* material_of_triangle;  /* [n_triangles] */
+  int n_materials;
+  const sdd_material* materials;         /* [n_materials] */
+  sdd_illuminant illum;
+  int n_subdomains;   /* 1..64 slabs of equal length along split_axis (Sec. 5) */
+  int split_axis;     /* 0, 1, 2, or -1 = longest axis of the scene box */
+  float ray_epsilon_m;/* spawned rays start this far off the surface along its normal;
+                         0 = 2e-6 x the largest absolute scene coordinate (at least 1e-5) */
+} sdd_scene_desc;
+
+typedef struct {
+  float pos[3], look_at[3], up[3];
+  float vfov_deg;       /* pinhole vertical field of view */
+  int width, height;    /* pixels; row 0 is the top row */
+  int orthographic;     /* 1: parallel rays along the view direction */
+  float ortho_height_m; /* orthographic image height */
+} sdd_camera;
+
+/* Render modes. */
+#define SDD_MODE_DETERMINISTIC 0 /* Sec. 3.1: split into reflected + transmitted children at
+                                    every glass hit, no randomness, spp must be 1 */
+#define SDD_MODE_MONTE_CARLO 1   /* Sec. 3.2: one Philox-driven path per (pixel, sample, lambda) */
+
+typedef struct {
+  int n_lambda;            /* number of render wavelengths (each one an independent path, Sec. 4) */
+  const float* lambda_nm;  /* host [n_lambda] */
+  int spp;                 /* samples per pixel */
+  uint64_t seed;           /* Philox key */
+  int max_depth;           /* surface interactions per path; deterministic mode: <= 10 */
+  int mode;                /* SDD_MODE_* */
+  int rr_start_depth;      /* Russian roulette from this interaction on (Monte Carlo) */
+  int use_surrogate;       /* reserved: must be 0 for now */
+  int batched;             /* 0: host-driven wavefront; 1: persistent drain kernels */
+  int n_pixels;            /* 0: whole image; else render only these pixel indices */
+  const int32_t* pixels;   /* host [n_pixels] row-major pixel indices (y * width + x) */
+  int wave_paths;          /* paths per wave; 0 = automatic */
+  float* path_radiance_out;/* optional device [pixels][spp][n_lambda] radiance of every path */
+  uint32_t* path_hash_out; /* optional device [pixels][spp][n_lambda] event hash of every path
+                              (Monte Carlo; FNV-1a over hit primitives and branch events) */
+} sdd_render_opts;
+
+/* Build the scene: validates, partitions the geometry into n_subdomains slabs (Sec. 5:
+ * split once, reused for every render), builds one SAH BVH per subdomain and uploads it.
+ * Returns SDD_ERR_ARG on bad input (message names the field). */
+sdd_status sdd_scene_create(const sdd_scene_desc* desc, sdd_scene** out);
+
+/* Frees the scene and all device memory it holds.  NULL is allowed. */
+void sdd_scene_destroy(sdd_scene* scene);
+
+/* Render one frame.  spectral_out: device float [n_px][n_lambda] (n_px = width * height or
+ * opts->n_pixels), the per-pixel mean radiance of each wavelength; xyz_out: device float
+ * [n_px][3] CIE XYZ (multi-lobe fit of the 1931 observer, normalised so that Y equals the
+ * radiance of a flat spectrum) or NULL.  The film sums samples in FP64 in sample order,
+ * so results do not depend on the wave size or the subdomain count beyond FP32 rounding
+ * of branch decisions. */
+sdd_status sdd_render(sdd_scene* scene, const sdd_camera* cam, const sdd_render_opts* opts,
+                      float* spectral_out, float* xyz_out, void* cuda_stream);
+
+/* Same as sdd_render, but spectral_out / xyz_out are HOST buffers: the library renders into
+ * its own device buffers and copies the result back (the end-to-end form of the call). */
+sdd_status sdd_render_to_host(sdd_scene* scene, const sdd_camera* cam, const sdd_render_opts* opts,
+                              float* spectral_out_host, float* xyz_out_host, void* cuda_stream);
+
+/* Per-kernel timing and counters of the most recent render. */
+typedef struct {
+  double ms_raygen, ms_traverse, ms_shade, ms_shadow, ms_film, ms_total;
+  int64_t launches_raygen, launches_traverse, launches_shade, launches_shadow, launches_film,
+      launches_total;
+  int64_t rays_closest;    /* closest-hit traversals, counting each subdomain visit */
+  int64_t rays_shadow;     /* shadow traversals, counting each subdomain visit */
+  int64_t node_visits;     /* BVH nodes fetched by closest-hit traversal (level >= 2) */
+  int64_t tri_tests;       /* triangles tested by closest-hit traversal (level >= 2) */
+  int64_t shadow_node_visits, shadow_tri_tests;
+  int64_t crossings;       /* interface hand-offs between subdomain queues */
+  int64_t paths;           /* spectral paths traced */
+  int64_t waves;
+  int64_t bytes_ray_state; /* ray/queue/hit bytes read+written by the traversal kernels */
+} sdd_stats;
+
+/* level 0: nothing; 1: CUDA-event timing of every launch; 2: also count BVH nodes and
+ * triangles (slower; for computing algorithmic bytes). */
+sdd_status sdd_set_profiling(sdd_scene* scene, int level);
+sdd_status sdd_get_stats(const sdd_scene* scene, sdd_stats* out);
+
+/* Scene facts: triangle references per subdomain after the split, BVH nodes, bytes. */
+typedef struct {
+  int n_triangles, n_subdomains, split_axis, bvh_max_depth;
+  int64_t n_tri_refs, n_nodes, device_bytes;
+  float planes[65]; /* subdomain boundaries along split_axis (first/last are -inf/+inf) */
+} sdd_scene_info;
+sdd_status sdd_scene_get_info(const sdd_scene* scene, sdd_scene_info* out);
+
+/* Batched closest-hit query (used by tests and by tools): n rays with device origins
+ * [n][3] and directions [n][3] (float), t in (0, inf).  Writes device t_out[n] (inf on a
+ * miss) and prim_out[n] (-1 on a miss), going through the subdomain queues exactly as
+ * rendering does. */
+sdd_status sdd_trace_closest(sdd_scene* scene, int n, const float* org_dev, const float* dir_dev,
+                             float* t_out_dev, int32_t* prim_out_dev, void* cuda_stream);
+
+/* Spectral material module on its own (for tests): for n queries with device arrays
+ * cos_i, n, k, thickness_m, lambda_nm writes the single-interface reflectance R (air ->
+ * n + ik), and the thin-slab reflectance / transmittance.  FP32, with the FP64 branch near
+ * grazing incidence exactly as the renderer uses them. */
+sdd_status sdd_eval_optics(int n, const float* cos_i, const float* n_re, const float* k,
+                           const float* thickness_m, const float* lambda_nm, float* R_out,
+                           float* R_slab_out, float* T_slab_out, void* cuda_stream);
+
+/* Philox4x32-10 as the renderer draws it: out[i] = philox(ctr[i], key) for device uint32
+ * arrays ctr [n][4] and out [n][4]. */
+sdd_status sdd_philox(int n, const uint32_t* ctr_dev, uint64_t key, uint32_t* out_dev, void* cuda_stream);
+
+const char* sdd_last_error(void);
+const char* sdd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SDD_H */

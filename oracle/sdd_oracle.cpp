@@ -173,8 +173,11 @@ V3 cone_dir(V3 s, double h, double u0, double u1) {
 }
 
 // ---------------------------------------------------------------- geometry
-// Moller-Trumbore ray/triangle test, edges inclusive.
+// Moller-Trumbore ray/triangle test.  Edges are inclusive and widened by a barycentric
+// tolerance far above double rounding (1e-12), so that a ray through an edge shared by two
+// triangles always hits the surface (the plain test can reject it in both).
 bool ray_triangle(V3 o, V3 d, V3 a, V3 b, V3 c, double* t_out) {
+  const double tol = 1e-12;
   V3 e1 = b - a, e2 = c - a;
   V3 p = cross(d, e2);
   double det = dot(e1, p);
@@ -182,10 +185,10 @@ bool ray_triangle(V3 o, V3 d, V3 a, V3 b, V3 c, double* t_out) {
   double inv = 1.0 / det;
   V3 s = o - a;
   double u = dot(s, p) * inv;
-  if (u < 0.0 || u > 1.0) return false;
+  if (u < -tol || u > 1.0 + tol) return false;
   V3 q = cross(s, e1);
   double v = dot(d, q) * inv;
-  if (v < 0.0 || u + v > 1.0) return false;
+  if (v < -tol || u + v > 1.0 + tol) return false;
   *t_out = dot(e2, q) * inv;
   return true;
 }
@@ -486,6 +489,7 @@ double trace_mc(const RenderCtx& cx, uint32_t px, uint32_t sample, int lam, uint
     double cos_i = std::fabs(cos_n);
     Draw u = draw(px, sample, (uint32_t)v, STREAM_PATH, 0, lam, cx.seed);
     V3 nd;
+    int nee_event = -1;  // shadow outcome, hashed after the roulette decision of this vertex
     if (m.kind == MAT_SOLID) {
       bool inside = cos_n > 0.0;
       if (inside) thr *= beer_lambert(m.k[lam], h.t + seg0, lambda);
@@ -525,7 +529,7 @@ double trace_mc(const RenderCtx& cx, uint32_t px, uint32_t sample, int lam, uint
           double T = shadow_T(s, offset(s, p, ng, wl), wl, lam, lambda);
           double omega = 2.0 * PI * s.sun_h;
           L += thr * m.albedo[lam] / PI * cl * s.sun[lam] * omega * T;
-          ph.byte(T > 0.0 ? EV_SHADOW_OPEN : EV_SHADOW_BLOCKED);
+          nee_event = T > 0.0 ? EV_SHADOW_OPEN : EV_SHADOW_BLOCKED;
         }
       }
       thr *= m.albedo[lam];
@@ -535,11 +539,18 @@ double trace_mc(const RenderCtx& cx, uint32_t px, uint32_t sample, int lam, uint
       ph.byte(EV_ABSORB);
       break;
     }
+    bool killed = false;
     if (v >= cx.rr_start) {
       double q = std::min(0.95, thr);
-      if (u.u[3] >= q) { ph.byte(EV_RR_KILL); break; }
-      thr /= q;
+      if (u.u[3] >= q) {
+        killed = true;
+        ph.byte(EV_RR_KILL);
+      } else {
+        thr /= q;
+      }
     }
+    if (nee_event >= 0) ph.byte((uint32_t)nee_event);
+    if (killed) break;
     o = offset(s, p, ng, nd);
     seg0 = seg0_of(s, ng, nd);
     d = nd;

@@ -1,0 +1,827 @@
+// api.cu -- C ABI of libsdd (include/sdd.h): scene creation, the host-driven wavefront
+// render loop, and the small query entry points.
+//
+// Render loop of one wave (a block of spectral paths, Sec. 4: every wavelength is an
+// independent path):
+//   raygen -> [ closest-hit passes over the subdomain queues until no ray is handed on
+//               (Sec. 5) -> shade (children + shadow rays binned by subdomain) ->
+//               shadow passes ]  repeated while rays remain -> film accumulation.
+// The host reads the queue counters after each launch to size the next grid.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstddef>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/sdd.h"
+#include "render_kernels.cuh"
+#include "scene_build.h"
+#include "sdd_internal.h"
+
+using namespace sdd;
+
+namespace {
+
+thread_local std::string g_err;
+
+sdd_status fail(sdd_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      return fail(e_ == cudaErrorMemoryAllocation ? SDD_ERR_OOM : SDD_ERR_CUDA,         \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+    }                                                                                   \
+  } while (0)
+
+template <typename T>
+struct DevArr {
+  T* p = nullptr;
+  size_t n = 0;
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  cudaError_t ensure(size_t want) {
+    if (want <= n && p) return cudaSuccess;
+    release();
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(want, 1) * sizeof(T));
+    if (e == cudaSuccess) n = want;
+    else p = nullptr;
+    return e;
+  }
+};
+
+struct HostMaterial {
+  int kind;
+  std::vector<float> lam, n, k, albedo;
+  float thick;
+  int tile_id;
+};
+
+double interp_table(const std::vector<float>& grid, const std::vector<float>& val, double lam) {
+  if (val.empty()) return 0.0;
+  size_t n = grid.size();
+  if (n == 1 || lam <= grid[0]) return val[0];
+  if (lam >= grid[n - 1]) return val[n - 1];
+  size_t i = 0;
+  while (grid[i + 1] < lam) ++i;
+  double f = (lam - grid[i]) / ((double)grid[i + 1] - grid[i]);
+  return (1.0 - f) * val[i] + f * val[i + 1];
+}
+
+enum TimedKind { TK_RAYGEN = 0, TK_TRAVERSE, TK_SHADE, TK_SHADOW, TK_FILM, TK_COUNT };
+
+}  // namespace
+
+struct sdd_scene {
+  // host copies
+  int n_tris = 0;
+  std::vector<HostMaterial> mats;
+  std::vector<float> il_lam, il_sky, il_sun;
+  int sky_mode = 0;
+  float sun_dir[3] = {0, 0, 1};
+  float sun_half = 0.f;
+  float eps = 1e-5f;
+  // device scene
+  DevArr<Node> nodes;
+  DevArr<TriRec> tris;
+  DevArr<float4> prim;
+  DevScene dev{};
+  int n_sub = 1, axis = 0, bvh_max_depth = 0;
+  int64_t n_refs = 0, n_nodes = 0;
+  // per-render spectral tables (cached for the last wavelength set)
+  std::vector<float> cached_lambda;
+  DevArr<float> t_lambda, t_thick, t_n, t_k, t_alb, t_sky, t_sun;
+  DevArr<int> t_kind;
+  DevArr<double> cmf_w;
+  // workspace
+  DevArr<float4> rb_o[2], rb_d[2], sb_o, sb_d;
+  DevArr<uint2> rb_info[2], sb_info;
+  DevArr<float2> hits;
+  DevArr<uint32_t> q[2], sq[2];
+  DevArr<float> path_L;
+  DevArr<uint32_t> path_hash;
+  DevArr<double> film;
+  DevArr<int32_t> pixel_list;
+  DevArr<float> out_spec, out_xyz;
+  Control* d_ctl = nullptr;
+  Control* h_ctl = nullptr;
+  int top_nodes = 0;
+  // profiling
+  int profiling = 0;
+  sdd_stats stats{};
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, int>> ev_used;  // (kind, index of the start event)
+  size_t ev_next = 0;
+
+  ~sdd_scene() {
+    DevArr<Node>* a[] = {&nodes};
+    for (auto* x : a) x->release();
+    tris.release();
+    prim.release();
+    t_lambda.release(); t_thick.release(); t_n.release(); t_k.release(); t_alb.release();
+    t_sky.release(); t_sun.release(); t_kind.release(); cmf_w.release();
+    for (int i = 0; i < 2; ++i) {
+      rb_o[i].release(); rb_d[i].release(); rb_info[i].release(); q[i].release(); sq[i].release();
+    }
+    sb_o.release(); sb_d.release(); sb_info.release(); hits.release(); path_L.release();
+    path_hash.release(); film.release(); pixel_list.release(); out_spec.release(); out_xyz.release();
+    if (d_ctl) cudaFree(d_ctl);
+    if (h_ctl) cudaFreeHost(h_ctl);
+    for (auto e : ev_pool) cudaEventDestroy(e);
+  }
+
+  // ---- timing helpers: a pair of events around every launch when profiling >= 1
+  int ev_begin(int kind, cudaStream_t st) {
+    if (profiling < 1) return -1;
+    if (ev_next + 2 > ev_pool.size()) {
+      for (int i = 0; i < 64; ++i) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        ev_pool.push_back(e);
+      }
+    }
+    int idx = (int)ev_next;
+    ev_next += 2;
+    cudaEventRecord(ev_pool[idx], st);
+    ev_used.push_back({kind, idx});
+    return idx;
+  }
+  void ev_end(int idx, cudaStream_t st) {
+    if (idx >= 0) cudaEventRecord(ev_pool[idx + 1], st);
+  }
+  // Called after a stream sync: fold every recorded pair into the stats.
+  void ev_collect() {
+    for (auto& u : ev_used) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev_pool[u.second], ev_pool[u.second + 1]);
+      double* dst[TK_COUNT] = {&stats.ms_raygen, &stats.ms_traverse, &stats.ms_shade, &stats.ms_shadow,
+                               &stats.ms_film};
+      *dst[u.first] += ms;
+    }
+    ev_used.clear();
+    ev_next = 0;
+  }
+};
+
+namespace {
+
+void count_launch(sdd_scene* s, int kind) {
+  int64_t* dst[TK_COUNT] = {&s->stats.launches_raygen, &s->stats.launches_traverse, &s->stats.launches_shade,
+                            &s->stats.launches_shadow, &s->stats.launches_film};
+  ++*dst[kind];
+  ++s->stats.launches_total;
+}
+
+sdd_status validate_table(const char* what, int n, const float* lam, const float* v, bool required) {
+  if (!v) {
+    if (required) return fail(SDD_ERR_ARG, std::string(what) + " table is NULL");
+    return SDD_OK;
+  }
+  if (n < 1 || !lam) return fail(SDD_ERR_ARG, std::string(what) + ": n_lambda < 1 or lambda_nm NULL");
+  for (int i = 1; i < n; ++i)
+    if (!(lam[i] > lam[i - 1])) return fail(SDD_ERR_ARG, std::string(what) + ": lambda_nm not ascending");
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return fail(SDD_ERR_ARG, std::string(what) + ": non-finite value");
+  return SDD_OK;
+}
+
+sdd_status read_ctl(sdd_scene* s, cudaStream_t st) {
+  CK(cudaMemcpyAsync(s->h_ctl, s->d_ctl, sizeof(Control), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return SDD_OK;
+}
+
+sdd_status device_error(uint32_t e) {
+  if (e & ERR_STACK_OVERFLOW) return fail(SDD_ERR_STACK, "BVH traversal stack overflow");
+  if (e & (ERR_QUEUE_OVERFLOW | ERR_SHADOW_OVERFLOW))
+    return fail(SDD_ERR_QUEUE_OVERFLOW, "ray queue capacity exceeded (lower wave_paths or max_depth)");
+  if (e & ERR_TIMEOUT) return fail(SDD_ERR_TIMEOUT, "device loop hit its iteration cap");
+  return SDD_OK;
+}
+
+Sched make_sched(int n_sub, const int* counts, int cap, int block, int* total_blocks, long long* total) {
+  Sched sc;
+  sc.n_sub = n_sub;
+  int b = 0;
+  long long t = 0;
+  for (int s = 0; s < n_sub; ++s) {
+    sc.blk_start[s] = b;
+    sc.count[s] = std::min(std::max(counts[s], 0), cap);  // overflow is reported, never read past cap
+    b += (counts[s] + block - 1) / block;
+    t += counts[s];
+  }
+  sc.blk_start[n_sub] = b;
+  *total_blocks = b;
+  *total = t;
+  return sc;
+}
+
+constexpr int kTravBlock = 128;
+
+// Closest-hit passes: the queues in q[a] (counts in ctl->q_count[a]) are traversed and
+// rays crossing an interface move to q[1-a], until every ray has a hit record.
+sdd_status run_closest_passes(sdd_scene* s, const RenderParams& p, RayBuf rb, int qcap, cudaStream_t st) {
+  int a = 0;
+  for (int pass = 0; pass <= 2 * kMaxSubdomains + 2; ++pass) {
+    sdd_status r = read_ctl(s, st);
+    if (r) return r;
+    if (s->h_ctl->error) return device_error(s->h_ctl->error);
+    int nb;
+    long long total;
+    Sched sch = make_sched(s->n_sub, s->h_ctl->q_count[a], qcap, kTravBlock, &nb, &total);
+    if (total == 0) return SDD_OK;
+    CK(cudaMemsetAsync(s->d_ctl->q_count[1 - a], 0, sizeof(int) * kMaxSubdomains, st));
+    QueuePair qp{s->q[a].p, s->q[1 - a].p, s->d_ctl->q_count[1 - a], qcap};
+    int ev = s->ev_begin(TK_TRAVERSE, st);
+    launch_traverse(p, sch, nb, kTravBlock, s->top_nodes, qp, rb, s->hits.p, s->d_ctl, st);
+    s->ev_end(ev, st);
+    CK(cudaGetLastError());
+    count_launch(s, TK_TRAVERSE);
+    a = 1 - a;
+  }
+  return fail(SDD_ERR_TIMEOUT, "closest-hit passes did not drain the subdomain queues");
+}
+
+sdd_status run_shadow_passes(sdd_scene* s, const RenderParams& p, const WaveDesc& w, int qcap, cudaStream_t st) {
+  int a = 0;
+  ShadowBuf sb{s->sb_o.p, s->sb_d.p, s->sb_info.p, qcap};
+  for (int pass = 0; pass <= 2 * kMaxSubdomains + 2; ++pass) {
+    sdd_status r = read_ctl(s, st);
+    if (r) return r;
+    if (s->h_ctl->error) return device_error(s->h_ctl->error);
+    int nb;
+    long long total;
+    Sched sch = make_sched(s->n_sub, s->h_ctl->sq_count[a], qcap, kTravBlock, &nb, &total);
+    if (total == 0) return SDD_OK;
+    CK(cudaMemsetAsync(s->d_ctl->sq_count[1 - a], 0, sizeof(int) * kMaxSubdomains, st));
+    QueuePair qp{s->sq[a].p, s->sq[1 - a].p, s->d_ctl->sq_count[1 - a], qcap};
+    int ev = s->ev_begin(TK_SHADOW, st);
+    launch_shadow(p, w, sch, nb, kTravBlock, qp, sb, s->path_L.p, s->d_ctl, st);
+    s->ev_end(ev, st);
+    CK(cudaGetLastError());
+    count_launch(s, TK_SHADOW);
+    a = 1 - a;
+  }
+  return fail(SDD_ERR_TIMEOUT, "shadow passes did not drain the subdomain queues");
+}
+
+// Resample every material / illuminant table to the render wavelengths and upload.
+sdd_status prepare_spectral(sdd_scene* s, int L, const float* lam, cudaStream_t st) {
+  std::vector<float> want(lam, lam + L);
+  if (want == s->cached_lambda && s->t_lambda.p) return SDD_OK;
+  size_t M = s->mats.size();
+  std::vector<int> kind(M);
+  std::vector<float> thick(M), tn(M * L), tk(M * L), ta(M * L), sky(L), sun(L);
+  for (size_t m = 0; m < M; ++m) {
+    const HostMaterial& hm = s->mats[m];
+    kind[m] = hm.kind;
+    thick[m] = hm.thick;
+    for (int l = 0; l < L; ++l) {
+      tn[m * L + l] = (float)interp_table(hm.lam, hm.n, lam[l]);
+      tk[m * L + l] = (float)interp_table(hm.lam, hm.k, lam[l]);
+      ta[m * L + l] = (float)interp_table(hm.lam, hm.albedo, lam[l]);
+    }
+  }
+  for (int l = 0; l < L; ++l) {
+    sky[l] = (float)interp_table(s->il_lam, s->il_sky, lam[l]);
+    sun[l] = s->il_sun.empty() ? 0.f : (float)interp_table(s->il_lam, s->il_sun, lam[l]);
+  }
+  CK(s->t_lambda.ensure(L));
+  CK(s->t_kind.ensure(M));
+  CK(s->t_thick.ensure(M));
+  CK(s->t_n.ensure(M * L));
+  CK(s->t_k.ensure(M * L));
+  CK(s->t_alb.ensure(M * L));
+  CK(s->t_sky.ensure(L));
+  CK(s->t_sun.ensure(L));
+  CK(s->cmf_w.ensure(3 * (size_t)L));
+  CK(cudaMemcpyAsync(s->t_lambda.p, lam, sizeof(float) * L, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(s->t_kind.p, kind.data(), sizeof(int) * M, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(s->t_thick.p, thick.data(), sizeof(float) * M, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(s->t_n.p, tn.data(), sizeof(float) * M * L, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(s->t_k.p, tk.data(), sizeof(float) * M * L, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(s->t_alb.p, ta.data(), sizeof(float) * M * L, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(s->t_sky.p, sky.data(), sizeof(float) * L, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(s->t_sun.p, sun.data(), sizeof(float) * L, cudaMemcpyHostToDevice, st));
+  launch_cmf_table(L, s->t_lambda.p, s->cmf_w.p, st);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));  // host vectors above go out of scope
+  s->cached_lambda = want;
+  return SDD_OK;
+}
+
+DevCamera make_camera(const sdd_camera* c) {
+  double pos[3] = {c->pos[0], c->pos[1], c->pos[2]};
+  double f[3] = {c->look_at[0] - pos[0], c->look_at[1] - pos[1], c->look_at[2] - pos[2]};
+  double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+  for (double& x : f) x /= fl;
+  double up[3] = {c->up[0], c->up[1], c->up[2]};
+  double r[3] = {f[1] * up[2] - f[2] * up[1], f[2] * up[0] - f[0] * up[2], f[0] * up[1] - f[1] * up[0]};
+  double rl = std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+  for (double& x : r) x /= rl;
+  double u[3] = {r[1] * f[2] - r[2] * f[1], r[2] * f[0] - r[0] * f[2], r[0] * f[1] - r[1] * f[0]};
+  DevCamera dc;
+  dc.pos = make_float3((float)pos[0], (float)pos[1], (float)pos[2]);
+  dc.fwd = make_float3((float)f[0], (float)f[1], (float)f[2]);
+  dc.right = make_float3((float)r[0], (float)r[1], (float)r[2]);
+  dc.up = make_float3((float)u[0], (float)u[1], (float)u[2]);
+  dc.tan_half = (float)std::tan(0.5 * c->vfov_deg * M_PI / 180.0);
+  dc.aspect = (float)c->width / (float)c->height;
+  dc.ortho_half = 0.5f * c->ortho_height_m;
+  dc.width = c->width;
+  dc.height = c->height;
+  dc.ortho = c->orthographic;
+  return dc;
+}
+
+sdd_status ensure_ctl(sdd_scene* s) {
+  if (!s->d_ctl) {
+    CK(cudaMalloc(&s->d_ctl, sizeof(Control)));
+    CK(cudaMallocHost(&s->h_ctl, sizeof(Control)));
+  }
+  return SDD_OK;
+}
+
+// Workspace for `cap` rays per generation and `paths` paths per wave.
+sdd_status ensure_workspace(sdd_scene* s, size_t cap, size_t paths, int n_slots, bool hash) {
+  for (int i = 0; i < 2; ++i) {
+    CK(s->rb_o[i].ensure(cap));
+    CK(s->rb_d[i].ensure(cap));
+    CK(s->rb_info[i].ensure(cap));
+    CK(s->q[i].ensure(cap * (size_t)s->n_sub));
+    CK(s->sq[i].ensure(cap * (size_t)s->n_sub));
+  }
+  CK(s->sb_o.ensure(cap));
+  CK(s->sb_d.ensure(cap));
+  CK(s->sb_info.ensure(cap));
+  CK(s->hits.ensure(cap));
+  CK(s->path_L.ensure(paths * (size_t)n_slots));
+  if (hash) CK(s->path_hash.ensure(paths));
+  return ensure_ctl(s);
+}
+
+sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opts* o, float* spectral_out,
+                       float* xyz_out, cudaStream_t st) {
+  if (!s || !cam || !o) return fail(SDD_ERR_ARG, "NULL scene, camera or options");
+  if (cam->width <= 0 || cam->height <= 0) return fail(SDD_ERR_ARG, "camera width/height must be positive");
+  if ((long long)cam->width * cam->height > (1LL << 30)) return fail(SDD_ERR_ARG, "image too large");
+  if (!cam->orthographic && !(cam->vfov_deg > 0.f && cam->vfov_deg < 180.f))
+    return fail(SDD_ERR_ARG, "vfov_deg must be in (0, 180)");
+  if (cam->orthographic && !(cam->ortho_height_m > 0.f)) return fail(SDD_ERR_ARG, "ortho_height_m must be > 0");
+  if (o->n_lambda < 1 || !o->lambda_nm) return fail(SDD_ERR_ARG, "n_lambda < 1 or lambda_nm NULL");
+  if (o->n_lambda > 4096) return fail(SDD_ERR_ARG, "n_lambda > 4096");
+  for (int i = 0; i < o->n_lambda; ++i)
+    if (!(o->lambda_nm[i] > 0.f)) return fail(SDD_ERR_ARG, "lambda_nm must be positive");
+  if (o->spp < 1) return fail(SDD_ERR_ARG, "spp must be >= 1");
+  if (o->mode != SDD_MODE_DETERMINISTIC && o->mode != SDD_MODE_MONTE_CARLO) return fail(SDD_ERR_ARG, "unknown mode");
+  if (o->mode == SDD_MODE_DETERMINISTIC && o->spp != 1) return fail(SDD_ERR_ARG, "deterministic mode needs spp == 1");
+  if (o->max_depth < 0 || o->max_depth > 255) return fail(SDD_ERR_ARG, "max_depth must be in [0, 255]");
+  if (o->mode == SDD_MODE_DETERMINISTIC && o->max_depth > 10)
+    return fail(SDD_ERR_ARG, "deterministic mode supports max_depth <= 10");
+  if (o->use_surrogate) return fail(SDD_ERR_ARG, "use_surrogate is not available in this build");
+  if (o->n_pixels < 0) return fail(SDD_ERR_ARG, "n_pixels < 0");
+  if (o->n_pixels > 0 && !o->pixels) return fail(SDD_ERR_ARG, "pixels is NULL");
+  const long long img = (long long)cam->width * cam->height;
+  for (int i = 0; i < o->n_pixels; ++i)
+    if (o->pixels[i] < 0 || o->pixels[i] >= img) return fail(SDD_ERR_ARG, "pixel index out of range");
+  const int L = o->n_lambda;
+  const long long n_px = o->n_pixels > 0 ? o->n_pixels : img;
+  const long long n_cells = n_px * L;
+  if (n_cells > 0x7FFFFFFFLL) return fail(SDD_ERR_ARG, "pixels x wavelengths exceeds 2^31");
+
+  sdd_status r = prepare_spectral(s, L, o->lambda_nm, st);
+  if (r) return r;
+  r = ensure_ctl(s);
+  if (r) return r;
+
+  // waves
+  const bool det = o->mode == SDD_MODE_DETERMINISTIC;
+  long long wmax = o->wave_paths > 0 ? o->wave_paths : (1LL << 26);
+  wmax = std::min<long long>(wmax, 1LL << 28);
+  std::vector<WaveDesc> waves;
+  if (n_cells <= wmax) {
+    uint32_t ns_per = (uint32_t)std::max<long long>(1, wmax / n_cells);
+    for (uint32_t s0 = 0; s0 < (uint32_t)o->spp; s0 += ns_per) {
+      WaveDesc w;
+      w.s0 = s0;
+      w.ns = std::min<uint32_t>(ns_per, (uint32_t)o->spp - s0);
+      w.c0 = 0;
+      w.nc = (uint32_t)n_cells;
+      w.n_paths = w.ns * w.nc;
+      waves.push_back(w);
+    }
+  } else {
+    for (uint32_t s0 = 0; s0 < (uint32_t)o->spp; ++s0)
+      for (long long c0 = 0; c0 < n_cells; c0 += wmax) {
+        WaveDesc w;
+        w.s0 = s0;
+        w.ns = 1;
+        w.c0 = (uint32_t)c0;
+        w.nc = (uint32_t)std::min<long long>(wmax, n_cells - c0);
+        w.n_paths = w.nc;
+        waves.push_back(w);
+      }
+  }
+  size_t wave_paths = 0;
+  for (auto& w : waves) wave_paths = std::max<size_t>(wave_paths, w.n_paths);
+  const int n_slots = det ? (1 << (o->max_depth + 1)) : 1;
+  const size_t cap = det ? wave_paths * 4 : wave_paths;
+  const bool want_hash = o->path_hash_out != nullptr;
+  r = ensure_workspace(s, cap, wave_paths, n_slots, want_hash);
+  if (r) return r;
+  CK(s->film.ensure((size_t)n_cells));
+  CK(cudaMemsetAsync(s->film.p, 0, sizeof(double) * n_cells, st));
+  if (o->n_pixels > 0) {
+    CK(s->pixel_list.ensure(o->n_pixels));
+    CK(cudaMemcpyAsync(s->pixel_list.p, o->pixels, sizeof(int32_t) * o->n_pixels, cudaMemcpyHostToDevice, st));
+  }
+
+  RenderParams p{};
+  p.sc = s->dev;
+  p.sp.n_lambda = L;
+  p.sp.lambda_nm = s->t_lambda.p;
+  p.sp.mat_kind = s->t_kind.p;
+  p.sp.mat_thick = s->t_thick.p;
+  p.sp.mat_n = s->t_n.p;
+  p.sp.mat_k = s->t_k.p;
+  p.sp.mat_albedo = s->t_alb.p;
+  p.sp.sky = s->t_sky.p;
+  p.sp.sun = s->t_sun.p;
+  p.sp.sky_mode = s->sky_mode;
+  {
+    double sd[3] = {s->sun_dir[0], s->sun_dir[1], s->sun_dir[2]};
+    double l = std::sqrt(sd[0] * sd[0] + sd[1] * sd[1] + sd[2] * sd[2]);
+    p.sp.sun_dir = make_float3((float)(sd[0] / l), (float)(sd[1] / l), (float)(sd[2] / l));
+    bool has_sun = !s->il_sun.empty() && s->sun_half > 0.f;
+    double h = has_sun ? 2.0 * std::sin(0.5 * s->sun_half) * std::sin(0.5 * s->sun_half) : 0.0;
+    p.sp.sun_h = (float)h;
+    p.sp.sun_omega = (float)(2.0 * M_PI * h);
+  }
+  p.cam = make_camera(cam);
+  p.pixel_list = o->n_pixels > 0 ? s->pixel_list.p : nullptr;
+  p.n_px = (int)n_px;
+  p.spp = o->spp;
+  p.seed = o->seed;
+  p.max_depth = o->max_depth;
+  p.mode = o->mode;
+  p.rr_start = o->rr_start_depth;
+  p.n_slots = n_slots;
+  p.stats = s->profiling;
+  p.path_hash = want_hash ? s->path_hash.p : nullptr;
+
+  s->stats = sdd_stats{};
+  CK(cudaMemsetAsync(s->d_ctl, 0, sizeof(Control), st));
+  const int qcap = (int)cap;
+  for (const WaveDesc& w : waves) {
+    CK(cudaMemsetAsync(s->d_ctl, 0, offsetof(Control, node_visits), st));
+    CK(cudaMemsetAsync(s->path_L.p, 0, sizeof(float) * (size_t)w.n_paths * n_slots, st));
+    int cur = 0;
+    RayBuf rb0{s->rb_o[0].p, s->rb_d[0].p, s->rb_info[0].p, qcap};
+    int ev = s->ev_begin(TK_RAYGEN, st);
+    launch_raygen(p, w, rb0, s->q[0].p, s->d_ctl->q_count[0], qcap, s->d_ctl, st);
+    s->ev_end(ev, st);
+    CK(cudaGetLastError());
+    count_launch(s, TK_RAYGEN);
+    int n_rays = (int)w.n_paths;
+    for (int gen = 0; n_rays > 0; ++gen) {
+      if (gen > o->max_depth + 1) return fail(SDD_ERR_TIMEOUT, "generation count exceeded max_depth + 1");
+      RayBuf rc{s->rb_o[cur].p, s->rb_d[cur].p, s->rb_info[cur].p, qcap};
+      RayBuf rn{s->rb_o[1 - cur].p, s->rb_d[1 - cur].p, s->rb_info[1 - cur].p, qcap};
+      r = run_closest_passes(s, p, rc, qcap, st);
+      if (r) return r;
+      // the closest passes left every count at zero; shade refills q[0] and sq[0]
+      CK(cudaMemsetAsync(s->d_ctl, 0, offsetof(Control, error), st));
+      ShadowBuf sb{s->sb_o.p, s->sb_d.p, s->sb_info.p, qcap};
+      ev = s->ev_begin(TK_SHADE, st);
+      launch_shade(p, w, n_rays, rc, s->hits.p, rn, s->q[0].p, s->d_ctl->q_count[0], qcap, sb, s->sq[0].p,
+                   s->d_ctl->sq_count[0], s->path_L.p, s->d_ctl, st);
+      s->ev_end(ev, st);
+      CK(cudaGetLastError());
+      count_launch(s, TK_SHADE);
+      r = run_shadow_passes(s, p, w, qcap, st);
+      if (r) return r;
+      n_rays = s->h_ctl->next_rays;
+      if (n_rays > qcap) return fail(SDD_ERR_QUEUE_OVERFLOW, "ray queue capacity exceeded");
+      cur = 1 - cur;
+    }
+    float* prad = o->path_radiance_out;
+    ev = s->ev_begin(TK_FILM, st);
+    launch_film_accum(p, w, s->path_L.p, s->film.p, prad, o->path_hash_out, st);
+    s->ev_end(ev, st);
+    CK(cudaGetLastError());
+    count_launch(s, TK_FILM);
+    s->stats.waves++;
+    s->stats.paths += w.n_paths;
+  }
+  int ev = s->ev_begin(TK_FILM, st);
+  launch_film_finalize(p, s->film.p, s->cmf_w.p, spectral_out, xyz_out, st);
+  s->ev_end(ev, st);
+  CK(cudaGetLastError());
+  count_launch(s, TK_FILM);
+  r = read_ctl(s, st);
+  if (r) return r;
+  if (s->h_ctl->error) return device_error(s->h_ctl->error);
+  s->stats.node_visits = (int64_t)s->h_ctl->node_visits;
+  s->stats.tri_tests = (int64_t)s->h_ctl->tri_tests;
+  s->stats.shadow_node_visits = (int64_t)s->h_ctl->shadow_node_visits;
+  s->stats.shadow_tri_tests = (int64_t)s->h_ctl->shadow_tri_tests;
+  s->stats.rays_closest = (int64_t)s->h_ctl->rays_closest;
+  s->stats.rays_shadow = (int64_t)s->h_ctl->rays_shadow;
+  s->stats.crossings = (int64_t)s->h_ctl->crossings;
+  // traversal ray-state traffic: per closest visit read queue index 4 B + origin/direction
+  // 32 B, write hit 8 B or hand-off 4 B; per shadow visit read 4 + 32 + 8 B.
+  s->stats.bytes_ray_state = s->stats.rays_closest * 44 + s->stats.rays_shadow * 44;
+  s->ev_collect();
+  s->stats.ms_total = s->stats.ms_raygen + s->stats.ms_traverse + s->stats.ms_shade + s->stats.ms_shadow +
+                      s->stats.ms_film;
+  return SDD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sdd_last_error(void) { return g_err.c_str(); }
+const char* sdd_version(void) { return "sdd 0.1 (sm_103a)"; }
+
+sdd_status sdd_scene_create(const sdd_scene_desc* d, sdd_scene** out) {
+  g_err.clear();
+  if (!d || !out) return fail(SDD_ERR_ARG, "NULL desc or out");
+  *out = nullptr;
+  if (d->n_vertices < 3 || !d->vertices) return fail(SDD_ERR_ARG, "need >= 3 vertices");
+  if (d->n_triangles < 1 || !d->indices || !d->material_of_triangle) return fail(SDD_ERR_ARG, "need >= 1 triangle");
+  if (d->n_triangles > (1 << 28)) return fail(SDD_ERR_ARG, "too many triangles");
+  if (d->n_materials < 1 || !d->materials) return fail(SDD_ERR_ARG, "need >= 1 material");
+  if (d->n_subdomains < 1 || d->n_subdomains > kMaxSubdomains) return fail(SDD_ERR_ARG, "n_subdomains must be 1..64");
+  if (d->split_axis < -1 || d->split_axis > 2) return fail(SDD_ERR_ARG, "split_axis must be -1, 0, 1 or 2");
+  for (long long i = 0; i < 3LL * d->n_vertices; ++i)
+    if (!std::isfinite(d->vertices[i])) return fail(SDD_ERR_ARG, "non-finite vertex coordinate");
+  for (long long i = 0; i < 3LL * d->n_triangles; ++i)
+    if (d->indices[i] >= (uint32_t)d->n_vertices) return fail(SDD_ERR_ARG, "triangle index out of range");
+  for (int t = 0; t < d->n_triangles; ++t)
+    if (d->material_of_triangle[t] >= d->n_materials) return fail(SDD_ERR_ARG, "material index out of range");
+  sdd_scene* s = new (std::nothrow) sdd_scene;
+  if (!s) return fail(SDD_ERR_OOM, "host allocation failed");
+  for (int m = 0; m < d->n_materials; ++m) {
+    const sdd_material& sm = d->materials[m];
+    if (sm.kind < 0 || sm.kind > 4) {
+      delete s;
+      return fail(SDD_ERR_ARG, "material " + std::to_string(m) + ": unknown kind");
+    }
+    if (sm.kind == SDD_MAT_HETERO_TILE) {
+      delete s;
+      return fail(SDD_ERR_ARG, "material " + std::to_string(m) + ": HETERO_TILE is not available in this build");
+    }
+    bool glass = sm.kind == SDD_MAT_DIELECTRIC_SOLID || sm.kind == SDD_MAT_THIN_SLAB;
+    sdd_status v = validate_table("material n", sm.n_lambda, sm.lambda_nm, sm.n, glass);
+    if (!v) v = validate_table("material k", sm.n_lambda, sm.lambda_nm, sm.k, glass);
+    if (!v) v = validate_table("material albedo", sm.n_lambda, sm.lambda_nm, sm.albedo, sm.kind == SDD_MAT_DIFFUSE);
+    if (v) {
+      delete s;
+      return fail(v, "material " + std::to_string(m) + ": " + g_err);
+    }
+    HostMaterial hm;
+    hm.kind = sm.kind;
+    hm.lam.assign(sm.lambda_nm, sm.lambda_nm + sm.n_lambda);
+    if (sm.n) hm.n.assign(sm.n, sm.n + sm.n_lambda);
+    if (sm.k) hm.k.assign(sm.k, sm.k + sm.n_lambda);
+    if (sm.albedo) hm.albedo.assign(sm.albedo, sm.albedo + sm.n_lambda);
+    if (glass) {
+      for (float x : hm.n)
+        if (!(x >= 1.0f)) {
+          delete s;
+          return fail(SDD_ERR_ARG, "material " + std::to_string(m) + ": glass index n must be >= 1");
+        }
+      for (float x : hm.k)
+        if (!(x >= 0.f)) {
+          delete s;
+          return fail(SDD_ERR_ARG, "material " + std::to_string(m) + ": k must be >= 0");
+        }
+    }
+    if (sm.kind == SDD_MAT_THIN_SLAB && !(sm.thickness_m > 0.f)) {
+      delete s;
+      return fail(SDD_ERR_ARG, "material " + std::to_string(m) + ": thin slab needs thickness_m > 0");
+    }
+    hm.thick = sm.thickness_m;
+    hm.tile_id = sm.tile_param_id;
+    s->mats.push_back(hm);
+  }
+  const sdd_illuminant& il = d->illum;
+  sdd_status v = validate_table("sky_radiance", il.n_lambda, il.lambda_nm, il.sky_radiance, true);
+  if (!v && il.sun_radiance) v = validate_table("sun_radiance", il.n_lambda, il.lambda_nm, il.sun_radiance, true);
+  if (v) {
+    delete s;
+    return v;
+  }
+  s->il_lam.assign(il.lambda_nm, il.lambda_nm + il.n_lambda);
+  s->il_sky.assign(il.sky_radiance, il.sky_radiance + il.n_lambda);
+  if (il.sun_radiance && il.sun_half_angle_rad > 0.f) s->il_sun.assign(il.sun_radiance, il.sun_radiance + il.n_lambda);
+  s->sky_mode = il.sky_mode;
+  double sl = std::sqrt((double)il.sun_dir[0] * il.sun_dir[0] + (double)il.sun_dir[1] * il.sun_dir[1] +
+                        (double)il.sun_dir[2] * il.sun_dir[2]);
+  if (!s->il_sun.empty() && !(sl > 0.0)) {
+    delete s;
+    return fail(SDD_ERR_ARG, "sun_dir must be non-zero");
+  }
+  for (int i = 0; i < 3; ++i) s->sun_dir[i] = il.sun_dir[i];
+  s->sun_half = il.sun_half_angle_rad;
+
+  // scene box, split axis, planes, epsilon
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300}, amax = 0.0;
+  for (int i = 0; i < d->n_vertices; ++i)
+    for (int a = 0; a < 3; ++a) {
+      double x = d->vertices[3 * i + a];
+      lo[a] = std::min(lo[a], x);
+      hi[a] = std::max(hi[a], x);
+      amax = std::max(amax, std::fabs(x));
+    }
+  int axis = d->split_axis;
+  if (axis < 0) axis = (hi[0] - lo[0] >= hi[1] - lo[1] && hi[0] - lo[0] >= hi[2] - lo[2]) ? 0
+                       : (hi[1] - lo[1] >= hi[2] - lo[2] ? 1 : 2);
+  s->eps = d->ray_epsilon_m > 0.f ? d->ray_epsilon_m : (float)std::max(1e-5, 2e-6 * amax);
+  BuildInput in;
+  in.verts = d->vertices;
+  in.idx = d->indices;
+  in.n_tris = d->n_triangles;
+  in.n_sub = d->n_subdomains;
+  in.axis = axis;
+  in.slop = (float)std::max<double>(s->eps, 1e-6 * amax);
+  for (int i = 0; i <= in.n_sub; ++i) {
+    if (i == 0) in.planes[i] = -INFINITY;
+    else if (i == in.n_sub) in.planes[i] = INFINITY;
+    else in.planes[i] = (float)(lo[axis] + (hi[axis] - lo[axis]) * i / in.n_sub);
+  }
+  HostBVH bvh;
+  try {
+    build_scene_bvh(in, bvh);
+  } catch (const std::bad_alloc&) {
+    delete s;
+    return fail(SDD_ERR_OOM, "host allocation failed during BVH build");
+  }
+  // per-primitive normal + material
+  std::vector<float4> prim(d->n_triangles);
+  for (int t = 0; t < d->n_triangles; ++t) {
+    const float* a = d->vertices + 3 * d->indices[3 * t];
+    const float* b = d->vertices + 3 * d->indices[3 * t + 1];
+    const float* c = d->vertices + 3 * d->indices[3 * t + 2];
+    double e1[3] = {(double)b[0] - a[0], (double)b[1] - a[1], (double)b[2] - a[2]};
+    double e2[3] = {(double)c[0] - a[0], (double)c[1] - a[1], (double)c[2] - a[2]};
+    double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    double l = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    if (!(l > 0.0)) l = 1.0;  // degenerate triangle: never hit by the watertight test
+    float mf;
+    int mi = d->material_of_triangle[t];
+    std::memcpy(&mf, &mi, 4);
+    prim[t] = make_float4((float)(n[0] / l), (float)(n[1] / l), (float)(n[2] / l), mf);
+  }
+  s->n_tris = d->n_triangles;
+  s->n_sub = d->n_subdomains;
+  s->axis = axis;
+  s->bvh_max_depth = bvh.max_depth;
+  s->n_refs = bvh.n_refs;
+  s->n_nodes = (int64_t)bvh.nodes.size();
+  cudaError_t e;
+  if ((e = s->nodes.ensure(bvh.nodes.size())) != cudaSuccess ||
+      (e = s->tris.ensure(std::max<size_t>(1, bvh.tris.size()))) != cudaSuccess ||
+      (e = s->prim.ensure(prim.size())) != cudaSuccess) {
+    delete s;
+    return fail(e == cudaErrorMemoryAllocation ? SDD_ERR_OOM : SDD_ERR_CUDA, cudaGetErrorString(e));
+  }
+  if ((e = cudaMemcpy(s->nodes.p, bvh.nodes.data(), sizeof(Node) * bvh.nodes.size(), cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (e = cudaMemcpy(s->tris.p, bvh.tris.data(), sizeof(TriRec) * bvh.tris.size(), cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (e = cudaMemcpy(s->prim.p, prim.data(), sizeof(float4) * prim.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    delete s;
+    return fail(SDD_ERR_CUDA, cudaGetErrorString(e));
+  }
+  DevScene& ds = s->dev;
+  ds.nodes = s->nodes.p;
+  ds.tris = s->tris.p;
+  ds.prim_nrm_mat = s->prim.p;
+  ds.n_prims = d->n_triangles;
+  ds.n_sub = in.n_sub;
+  ds.axis = axis;
+  for (int i = 0; i <= in.n_sub; ++i) ds.planes[i] = in.planes[i];
+  for (int i = in.n_sub + 1; i <= kMaxSubdomains; ++i) ds.planes[i] = INFINITY;
+  for (int i = 0; i < in.n_sub; ++i) {
+    ds.root[i] = bvh.root[i];
+    ds.n_nodes_sub[i] = bvh.n_nodes[i];
+  }
+  ds.eps = s->eps;
+  *out = s;
+  return SDD_OK;
+}
+
+void sdd_scene_destroy(sdd_scene* s) { delete s; }
+
+sdd_status sdd_scene_get_info(const sdd_scene* s, sdd_scene_info* out) {
+  if (!s || !out) return fail(SDD_ERR_ARG, "NULL argument");
+  std::memset(out, 0, sizeof(*out));
+  out->n_triangles = s->n_tris;
+  out->n_subdomains = s->n_sub;
+  out->split_axis = s->axis;
+  out->bvh_max_depth = s->bvh_max_depth;
+  out->n_tri_refs = s->n_refs;
+  out->n_nodes = s->n_nodes;
+  out->device_bytes = (int64_t)(s->nodes.n * sizeof(Node) + s->tris.n * sizeof(TriRec) + s->prim.n * sizeof(float4));
+  for (int i = 0; i <= s->n_sub; ++i) out->planes[i] = s->dev.planes[i];
+  return SDD_OK;
+}
+
+sdd_status sdd_render(sdd_scene* scene, const sdd_camera* cam, const sdd_render_opts* opts, float* spectral_out,
+                      float* xyz_out, void* stream) {
+  g_err.clear();
+  if (!spectral_out && !xyz_out) return fail(SDD_ERR_ARG, "spectral_out and xyz_out are both NULL");
+  return render_impl(scene, cam, opts, spectral_out, xyz_out, (cudaStream_t)stream);
+}
+
+sdd_status sdd_render_to_host(sdd_scene* s, const sdd_camera* cam, const sdd_render_opts* o, float* spec_host,
+                              float* xyz_host, void* stream) {
+  g_err.clear();
+  if (!s || !cam || !o) return fail(SDD_ERR_ARG, "NULL scene, camera or options");
+  if (!spec_host && !xyz_host) return fail(SDD_ERR_ARG, "spectral_out and xyz_out are both NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  long long n_px = o->n_pixels > 0 ? o->n_pixels : (long long)cam->width * cam->height;
+  size_t ns = (size_t)n_px * std::max(o->n_lambda, 1), nx = (size_t)n_px * 3;
+  CK(s->out_spec.ensure(ns));
+  CK(s->out_xyz.ensure(nx));
+  sdd_status r = render_impl(s, cam, o, spec_host ? s->out_spec.p : nullptr, xyz_host ? s->out_xyz.p : nullptr, st);
+  if (r) return r;
+  if (spec_host) CK(cudaMemcpyAsync(spec_host, s->out_spec.p, ns * sizeof(float), cudaMemcpyDeviceToHost, st));
+  if (xyz_host) CK(cudaMemcpyAsync(xyz_host, s->out_xyz.p, nx * sizeof(float), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return SDD_OK;
+}
+
+sdd_status sdd_set_profiling(sdd_scene* s, int level) {
+  if (!s || level < 0 || level > 2) return fail(SDD_ERR_ARG, "bad scene or profiling level");
+  s->profiling = level;
+  return SDD_OK;
+}
+
+sdd_status sdd_get_stats(const sdd_scene* s, sdd_stats* out) {
+  if (!s || !out) return fail(SDD_ERR_ARG, "NULL argument");
+  *out = s->stats;
+  return SDD_OK;
+}
+
+sdd_status sdd_trace_closest(sdd_scene* s, int n, const float* org, const float* dir, float* t_out, int32_t* prim_out,
+                             void* stream) {
+  g_err.clear();
+  if (!s || n < 0 || (n > 0 && (!org || !dir || !t_out || !prim_out))) return fail(SDD_ERR_ARG, "bad arguments");
+  if (n == 0) return SDD_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  sdd_status r = ensure_workspace(s, (size_t)n, (size_t)n, 1, false);
+  if (r) return r;
+  CK(cudaMemsetAsync(s->d_ctl, 0, sizeof(Control), st));
+  RayBuf rb{s->rb_o[0].p, s->rb_d[0].p, s->rb_info[0].p, n};
+  launch_rays_from_arrays(n, org, dir, s->dev, rb, s->q[0].p, s->d_ctl->q_count[0], n, st);
+  CK(cudaGetLastError());
+  RenderParams p{};
+  p.sc = s->dev;
+  p.stats = 0;
+  r = run_closest_passes(s, p, rb, n, st);
+  if (r) return r;
+  launch_hits_to_arrays(n, s->hits.p, t_out, prim_out, st);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  return SDD_OK;
+}
+
+sdd_status sdd_eval_optics(int n, const float* cos_i, const float* n_re, const float* k, const float* d,
+                           const float* lam, float* R, float* Rs, float* Ts, void* stream) {
+  g_err.clear();
+  if (n < 0 || (n > 0 && (!cos_i || !n_re || !k || !d || !lam || !R || !Rs || !Ts))) return fail(SDD_ERR_ARG, "bad arguments");
+  if (n == 0) return SDD_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  launch_eval_optics(n, cos_i, n_re, k, d, lam, R, Rs, Ts, st);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  return SDD_OK;
+}
+
+sdd_status sdd_philox(int n, const uint32_t* ctr, uint64_t key, uint32_t* out, void* stream) {
+  g_err.clear();
+  if (n < 0 || (n > 0 && (!ctr || !out))) return fail(SDD_ERR_ARG, "bad arguments");
+  if (n == 0) return SDD_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  launch_philox(n, ctr, key, out, st);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  return SDD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,292 @@
+// scene_build.cpp -- host-side scene preparation for libsdd: the subdomain split and one
+// binned-SAH BVH per subdomain.
+//
+// Sec. 5 of arXiv:1912.05494: the global geometry is split into sub-domains once and the
+// split is reused for every run; each sub-domain keeps its own acceleration structure.
+// Here the sub-domains are S slabs of equal length along one axis (the nave's length),
+// the outer two extending to infinity.  A triangle is referenced by every slab its
+// bounding box overlaps (widened by `slop`), with its box clipped to the slab so that
+// the BVH of a slab bounds only the part of the geometry that lies in it.  A hit inside a
+// slab's ray interval therefore always lies inside that slab's BVH.
+//
+// The BVH is binary, built top-down with 16-bin SAH, stored in breadth-first order
+// (so that the top levels form one contiguous block), 64-byte nodes holding both
+// children's boxes, and 48-byte triangle records (three float4 vertices).
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <limits>
+#include <vector>
+
+#include "sdd_internal.h"
+#include "scene_build.h"
+
+namespace sdd {
+namespace {
+
+struct Box3 {
+  float lo[3] = {INFINITY, INFINITY, INFINITY};
+  float hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  void grow(const Box3& b) {
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], b.lo[a]);
+      hi[a] = std::max(hi[a], b.hi[a]);
+    }
+  }
+  void grow_pt(const float* p) {
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], p[a]);
+      hi[a] = std::max(hi[a], p[a]);
+    }
+  }
+  bool empty() const { return !(lo[0] <= hi[0] && lo[1] <= hi[1] && lo[2] <= hi[2]); }
+  float area() const {
+    if (empty()) return 0.f;
+    float dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
+    return 2.f * (dx * dy + dy * dz + dz * dx);
+  }
+  float cen(int a) const { return 0.5f * (lo[a] + hi[a]); }
+};
+
+struct Ref {
+  Box3 box;
+  int prim;
+};
+
+struct TmpNode {
+  Box3 box;
+  int left = -1, right = -1;  // children (tmp indices) for inner nodes
+  int first = 0, count = 0;   // refs for leaves
+};
+
+constexpr int kBins = 16;
+constexpr int kLeafMax = 4;
+constexpr int kDepthLimit = kStackSize - 4;
+
+struct Builder {
+  std::vector<Ref>& refs;
+  std::vector<TmpNode> nodes;
+  int max_depth = 0;
+  explicit Builder(std::vector<Ref>& r) : refs(r) {}
+
+  int make_leaf(int first, int count, const Box3& box) {
+    TmpNode n;
+    n.box = box;
+    n.first = first;
+    n.count = count;
+    nodes.push_back(n);
+    return (int)nodes.size() - 1;
+  }
+
+  int build(int first, int count, int depth) {
+    max_depth = std::max(max_depth, depth);
+    Box3 box, cb;
+    for (int i = first; i < first + count; ++i) {
+      box.grow(refs[i].box);
+      float c[3] = {refs[i].box.cen(0), refs[i].box.cen(1), refs[i].box.cen(2)};
+      cb.grow_pt(c);
+    }
+    if (count <= kLeafMax || depth >= kDepthLimit) return make_leaf(first, count, box);
+
+    int best_axis = -1, best_split = -1;
+    float best_cost = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+      float ext = cb.hi[a] - cb.lo[a];
+      if (!(ext > 0.f)) continue;
+      Box3 bb[kBins];
+      int bc[kBins] = {0};
+      float scale = kBins / ext;
+      for (int i = first; i < first + count; ++i) {
+        int b = std::min(kBins - 1, (int)((refs[i].box.cen(a) - cb.lo[a]) * scale));
+        bb[b].grow(refs[i].box);
+        bc[b]++;
+      }
+      float right_area[kBins];
+      int right_count[kBins];
+      Box3 acc;
+      int cnt = 0;
+      for (int b = kBins - 1; b > 0; --b) {
+        acc.grow(bb[b]);
+        cnt += bc[b];
+        right_area[b] = acc.area();
+        right_count[b] = cnt;
+      }
+      Box3 lacc;
+      int lcnt = 0;
+      for (int b = 0; b < kBins - 1; ++b) {
+        lacc.grow(bb[b]);
+        lcnt += bc[b];
+        if (lcnt == 0 || right_count[b + 1] == 0) continue;
+        float cost = lacc.area() * lcnt + right_area[b + 1] * right_count[b + 1];
+        if (cost < best_cost) {
+          best_cost = cost;
+          best_axis = a;
+          best_split = b;
+        }
+      }
+    }
+    int mid;
+    if (best_axis < 0) {
+      // all centroids coincide: split by count
+      mid = first + count / 2;
+    } else {
+      float leaf_cost = box.area() * count;
+      if (count <= 2 * kLeafMax && best_cost >= leaf_cost) return make_leaf(first, count, box);
+      float scale = kBins / (cb.hi[best_axis] - cb.lo[best_axis]);
+      auto it = std::partition(refs.begin() + first, refs.begin() + first + count, [&](const Ref& r) {
+        int b = std::min(kBins - 1, (int)((r.box.cen(best_axis) - cb.lo[best_axis]) * scale));
+        return b <= best_split;
+      });
+      mid = (int)(it - refs.begin());
+      if (mid == first || mid == first + count) mid = first + count / 2;
+    }
+    int me = (int)nodes.size();
+    nodes.push_back(TmpNode{});
+    nodes[me].box = box;
+    int l = build(first, mid - first, depth + 1);
+    int r = build(mid, first + count - mid, depth + 1);
+    nodes[me].left = l;
+    nodes[me].right = r;
+    return me;
+  }
+};
+
+void set_child(Node& n, int which, const Box3& b, int link, int count) {
+  float* ab = which == 0 ? &n.a.x : &n.b.x;
+  ab[0] = b.lo[0];
+  ab[1] = b.hi[0];
+  ab[2] = b.lo[1];
+  ab[3] = b.hi[1];
+  if (which == 0) {
+    n.c.x = b.lo[2];
+    n.c.y = b.hi[2];
+    n.d.x = link;
+    n.d.z = count;
+  } else {
+    n.c.z = b.lo[2];
+    n.c.w = b.hi[2];
+    n.d.y = link;
+    n.d.w = count;
+  }
+}
+
+// Flatten one tmp tree into BFS-ordered Nodes appended to `out`, triangle records to `tris`.
+int flatten(const Builder& bld, int tmp_root, const std::vector<Ref>& refs, const float* verts,
+            const uint32_t* idx, std::vector<Node>& out, std::vector<TriRec>& tris) {
+  const int base = (int)out.size();
+  const Box3 none;  // inverted box: never hit
+  std::vector<int> order;  // tmp inner node per output node
+  std::vector<int> synthetic;
+  if (bld.nodes[tmp_root].left < 0) {
+    // whole subdomain is one leaf: synthesise a root with one child
+    order.push_back(-1);
+  } else {
+    order.push_back(tmp_root);
+  }
+  std::vector<int> out_index(bld.nodes.size(), -1);
+  if (order[0] >= 0) out_index[order[0]] = base;
+  // BFS over inner nodes
+  for (size_t q = 0; q < order.size(); ++q) {
+    int t = order[q];
+    if (t < 0) continue;
+    for (int c : {bld.nodes[t].left, bld.nodes[t].right}) {
+      if (bld.nodes[c].left >= 0) {
+        out_index[c] = base + (int)order.size();
+        order.push_back(c);
+      }
+    }
+  }
+  out.resize(base + order.size());
+  auto emit_leaf = [&](const TmpNode& lf) -> int {
+    int first = (int)tris.size();
+    for (int i = lf.first; i < lf.first + lf.count; ++i) {
+      int p = refs[i].prim;
+      TriRec r;
+      const float* a = verts + 3 * idx[3 * p + 0];
+      const float* b = verts + 3 * idx[3 * p + 1];
+      const float* c = verts + 3 * idx[3 * p + 2];
+      float pid;
+      uint32_t up = (uint32_t)p;
+      std::memcpy(&pid, &up, 4);
+      r.v0 = make_float4(a[0], a[1], a[2], pid);
+      r.v1 = make_float4(b[0], b[1], b[2], 0.f);
+      r.v2 = make_float4(c[0], c[1], c[2], 0.f);
+      tris.push_back(r);
+    }
+    return first;
+  };
+  for (size_t q = 0; q < order.size(); ++q) {
+    Node n;
+    std::memset(&n, 0, sizeof(n));
+    int t = order[q];
+    if (t < 0) {
+      const TmpNode& lf = bld.nodes[tmp_root];
+      if (lf.count > 0) {
+        set_child(n, 0, lf.box, emit_leaf(lf), lf.count);
+      } else {
+        set_child(n, 0, none, -1, 0);
+      }
+      set_child(n, 1, none, -1, 0);
+    } else {
+      int ch[2] = {bld.nodes[t].left, bld.nodes[t].right};
+      for (int w = 0; w < 2; ++w) {
+        const TmpNode& c = bld.nodes[ch[w]];
+        if (c.left >= 0) {
+          set_child(n, w, c.box, out_index[ch[w]], 0);
+        } else if (c.count > 0) {
+          set_child(n, w, c.box, emit_leaf(c), c.count);
+        } else {
+          set_child(n, w, none, -1, 0);
+        }
+      }
+    }
+    out[base + q] = n;
+  }
+  return base;
+}
+
+}  // namespace
+
+void build_scene_bvh(const BuildInput& in, HostBVH& out) {
+  out.nodes.clear();
+  out.tris.clear();
+  out.root.assign(in.n_sub, 0);
+  out.n_nodes.assign(in.n_sub, 0);
+  out.max_depth = 0;
+  out.n_refs = 0;
+  // triangle boxes
+  std::vector<Box3> tbox(in.n_tris);
+  for (int t = 0; t < in.n_tris; ++t)
+    for (int c = 0; c < 3; ++c) tbox[t].grow_pt(in.verts + 3 * in.idx[3 * t + c]);
+  for (int s = 0; s < in.n_sub; ++s) {
+    float lo = in.planes[s] - in.slop, hi = in.planes[s + 1] + in.slop;
+    std::vector<Ref> refs;
+    for (int t = 0; t < in.n_tris; ++t) {
+      const Box3& b = tbox[t];
+      if (b.hi[in.axis] < lo || b.lo[in.axis] > hi) continue;
+      Ref r;
+      r.box = b;
+      r.box.lo[in.axis] = std::max(b.lo[in.axis], lo);
+      r.box.hi[in.axis] = std::min(b.hi[in.axis], hi);
+      r.prim = t;
+      refs.push_back(r);
+    }
+    out.n_refs += (int64_t)refs.size();
+    Builder bld(refs);
+    int root;
+    if (refs.empty()) {
+      TmpNode n;  // empty leaf
+      bld.nodes.push_back(n);
+      root = 0;
+    } else {
+      root = bld.build(0, (int)refs.size(), 0);
+    }
+    out.max_depth = std::max(out.max_depth, bld.max_depth);
+    int before = (int)out.nodes.size();
+    out.root[s] = flatten(bld, root, refs, in.verts, in.idx, out.nodes, out.tris);
+    out.n_nodes[s] = (int)out.nodes.size() - before;
+  }
+}
+
+}  // namespace sdd

@@ -1,0 +1,132 @@
+// sdd_internal.h -- device-side data layout shared by the host driver and the kernels of
+// libsdd.  Nothing here is part of the public C ABI (include/sdd.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+namespace sdd {
+
+constexpr int kMaxSubdomains = 64;
+constexpr int kStackSize = 64;            // BVH traversal stack entries per ray
+constexpr uint32_t kMissPrim = 0xFFFFFFFFu;
+
+enum MatKind : int { MAT_SOLID = 0, MAT_SLAB = 1, MAT_TILE = 2, MAT_DIFFUSE = 3, MAT_OPAQUE = 4 };
+
+// Error bits raised by kernels into Control::error.
+enum ErrBits : uint32_t {
+  ERR_QUEUE_OVERFLOW = 1u,
+  ERR_STACK_OVERFLOW = 2u,
+  ERR_TIMEOUT = 4u,
+  ERR_SHADOW_OVERFLOW = 8u,
+};
+
+// BVH node, 64 bytes: the bounds of both children and their links.
+//   a = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
+//   b = (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
+//   c = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
+//   d = (link0, link1, count0, count1) as int bits:
+//       count > 0  -> leaf: triangle records [link, link + count)
+//       count == 0 -> inner node index `link` (absolute), or no child when link < 0
+struct alignas(16) Node {
+  float4 a, b, c;
+  int4 d;
+};
+
+// Triangle record, 48 bytes: the three vertices; v0.w holds the global primitive id bits.
+struct alignas(16) TriRec {
+  float4 v0, v1, v2;
+};
+
+// Everything the kernels read about the scene (device pointers).
+struct DevScene {
+  const Node* nodes;
+  const TriRec* tris;
+  const float4* prim_nrm_mat;   // per global primitive: unit normal xyz, material id in w bits
+  int n_prims;
+  int n_sub;
+  int axis;
+  float planes[kMaxSubdomains + 1];  // slab boundaries (planes[0] = -inf, planes[n_sub] = +inf)
+  int root[kMaxSubdomains];          // root node of each subdomain's BVH
+  int n_nodes_sub[kMaxSubdomains];   // nodes of each subdomain's BVH (BFS order from root)
+  float eps;                         // spawn offset along the normal
+};
+
+// Per-render spectral tables (device pointers) and illuminant.
+struct DevSpectral {
+  int n_lambda;
+  const float* lambda_nm;    // [L]
+  const int* mat_kind;       // [M]
+  const float* mat_thick;    // [M]
+  const float* mat_n;        // [M][L]
+  const float* mat_k;        // [M][L]
+  const float* mat_albedo;   // [M][L]
+  const float* sky;          // [L]
+  const float* sun;          // [L]
+  int sky_mode;
+  float3 sun_dir;
+  float sun_h;               // 1 - cos(half angle); 0 = no sun
+  float sun_omega;           // solid angle of the disc
+};
+
+struct DevCamera {
+  float3 pos, fwd, right, up;
+  float tan_half, aspect, ortho_half;
+  int width, height, ortho;
+};
+
+// Ray state, structure of arrays with capacity `cap`.
+struct RayBuf {
+  float4* o;      // origin xyz, w = seg0 (distance back to the previous surface plane)
+  float4* d;      // direction xyz, w = throughput
+  uint2* info;    // x = wave-local path id, y = depth(8) | flags(8) << 8 | code(16) << 16
+  int cap;
+};
+
+struct ShadowBuf {
+  float4* o;      // origin xyz, w unused
+  float4* d;      // direction xyz, w = contribution carried so far
+  uint2* info;    // x = wave-local path id, y = contribution slot (deterministic mode)
+  int cap;
+};
+
+// Device control block: queue counters and error word, read back by the host.
+struct Control {
+  int q_count[2][kMaxSubdomains];       // closest-hit queues (current / crossing)
+  int sq_count[2][kMaxSubdomains];      // shadow queues
+  int next_rays;                        // rays written into the next generation buffer
+  int next_shadow;                      // shadow rays written this generation
+  uint32_t error;
+  int pad;
+  unsigned long long node_visits, tri_tests, shadow_node_visits, shadow_tri_tests;
+  unsigned long long rays_closest, rays_shadow, crossings;
+};
+
+enum RayFlags : uint32_t { FLAG_SUN_COUNTED = 1u };
+
+struct WaveDesc {
+  uint32_t s0, ns;        // samples [s0, s0 + ns)
+  uint32_t c0, nc;        // cells [c0, c0 + nc) with cell = pixel_index * L + lambda
+  uint32_t n_paths;       // ns * nc
+};
+
+struct RenderParams {
+  DevScene sc;
+  DevSpectral sp;
+  DevCamera cam;
+  const int32_t* pixel_list;   // device, or nullptr for all pixels
+  int n_px;
+  int spp;
+  uint64_t seed;
+  int max_depth;
+  int mode;                    // 0 deterministic, 1 Monte Carlo
+  int rr_start;
+  int n_slots;                 // contribution slots per path (deterministic: 2^(max_depth+1))
+  int stats;                   // profiling level
+  uint32_t* path_hash;         // wave-local hash per path or nullptr
+};
+
+}  // namespace sdd

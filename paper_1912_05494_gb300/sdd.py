@@ -1,0 +1,310 @@
+"""ctypes binding of libsdd (include/sdd.h).  Argument marshalling only: every step of the
+render runs in the library's CUDA kernels.  Loading fails loudly when the library has not
+been built; there is no CPU fallback.
+
+Functions keep the C names.  Device buffers are passed as torch CUDA tensors (their data
+pointers), host inputs as numpy arrays, streams as torch streams (or None for the current
+stream).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsdd.so")
+_lib = None
+
+SDD_MODE_DETERMINISTIC = 0
+SDD_MODE_MONTE_CARLO = 1
+STATUS_NAMES = {0: "SDD_OK", -1: "SDD_ERR_ARG", -2: "SDD_ERR_OOM", -3: "SDD_ERR_CUDA",
+                -4: "SDD_ERR_QUEUE_OVERFLOW", -5: "SDD_ERR_TIMEOUT", -6: "SDD_ERR_STATE", -7: "SDD_ERR_STACK"}
+
+
+class SddError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class sdd_material(C.Structure):
+    _fields_ = [("kind", C.c_int), ("n_lambda", C.c_int), ("lambda_nm", C.c_void_p),
+                ("n", C.c_void_p), ("k", C.c_void_p), ("thickness_m", C.c_float),
+                ("albedo", C.c_void_p), ("tile_param_id", C.c_int)]
+
+
+class sdd_illuminant(C.Structure):
+    _fields_ = [("n_lambda", C.c_int), ("lambda_nm", C.c_void_p), ("sky_radiance", C.c_void_p),
+                ("sky_mode", C.c_int), ("sun_dir", C.c_float * 3), ("sun_half_angle_rad", C.c_float),
+                ("sun_radiance", C.c_void_p)]
+
+
+class sdd_scene_desc(C.Structure):
+    _fields_ = [("n_vertices", C.c_int), ("vertices", C.c_void_p), ("n_triangles", C.c_int),
+                ("indices", C.c_void_p), ("material_of_triangle", C.c_void_p),
+                ("n_materials", C.c_int), ("materials", C.c_void_p), ("illum", sdd_illuminant),
+                ("n_subdomains", C.c_int), ("split_axis", C.c_int), ("ray_epsilon_m", C.c_float)]
+
+
+class sdd_camera(C.Structure):
+    _fields_ = [("pos", C.c_float * 3), ("look_at", C.c_float * 3), ("up", C.c_float * 3),
+                ("vfov_deg", C.c_float), ("width", C.c_int), ("height", C.c_int),
+                ("orthographic", C.c_int), ("ortho_height_m", C.c_float)]
+
+
+class sdd_render_opts(C.Structure):
+    _fields_ = [("n_lambda", C.c_int), ("lambda_nm", C.c_void_p), ("spp", C.c_int),
+                ("seed", C.c_uint64), ("max_depth", C.c_int), ("mode", C.c_int),
+                ("rr_start_depth", C.c_int), ("use_surrogate", C.c_int), ("batched", C.c_int),
+                ("n_pixels", C.c_int), ("pixels", C.c_void_p), ("wave_paths", C.c_int),
+                ("path_radiance_out", C.c_void_p), ("path_hash_out", C.c_void_p)]
+
+
+class sdd_stats(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("ms_raygen", "ms_traverse", "ms_shade", "ms_shadow", "ms_film",
+                                           "ms_total")] + \
+               [(n, C.c_int64) for n in ("launches_raygen", "launches_traverse", "launches_shade",
+                                          "launches_shadow", "launches_film", "launches_total", "rays_closest",
+                                          "rays_shadow", "node_visits", "tri_tests", "shadow_node_visits",
+                                          "shadow_tri_tests", "crossings", "paths", "waves", "bytes_ray_state")]
+
+    def as_dict(self):
+        return {f[0]: getattr(self, f[0]) for f in self._fields_}
+
+
+class sdd_scene_info(C.Structure):
+    _fields_ = [("n_triangles", C.c_int), ("n_subdomains", C.c_int), ("split_axis", C.c_int),
+                ("bvh_max_depth", C.c_int), ("n_tri_refs", C.c_int64), ("n_nodes", C.c_int64),
+                ("device_bytes", C.c_int64), ("planes", C.c_float * 65)]
+
+
+def lib():
+    """Load libsdd.so; raises if it has not been built (no fallback path exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                              "(the renderer has no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        vp, i32 = C.c_void_p, C.c_int
+        L.sdd_scene_create.argtypes = [C.POINTER(sdd_scene_desc), C.POINTER(vp)]
+        L.sdd_scene_destroy.argtypes = [vp]
+        L.sdd_scene_destroy.restype = None
+        L.sdd_render.argtypes = [vp, C.POINTER(sdd_camera), C.POINTER(sdd_render_opts), vp, vp, vp]
+        L.sdd_render_to_host.argtypes = [vp, C.POINTER(sdd_camera), C.POINTER(sdd_render_opts), vp, vp, vp]
+        L.sdd_set_profiling.argtypes = [vp, i32]
+        L.sdd_get_stats.argtypes = [vp, C.POINTER(sdd_stats)]
+        L.sdd_scene_get_info.argtypes = [vp, C.POINTER(sdd_scene_info)]
+        L.sdd_trace_closest.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+        L.sdd_eval_optics.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.sdd_philox.argtypes = [i32, vp, C.c_uint64, vp, vp]
+        L.sdd_last_error.restype = C.c_char_p
+        L.sdd_version.restype = C.c_char_p
+        for name in ("sdd_scene_create", "sdd_render", "sdd_render_to_host", "sdd_set_profiling", "sdd_get_stats",
+                     "sdd_scene_get_info", "sdd_trace_closest", "sdd_eval_optics", "sdd_philox"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(st: int):
+    if st != 0:
+        raise SddError(st, lib().sdd_last_error().decode(errors="replace"))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return C.c_void_p(t.ctypes.data)
+    return C.c_void_p(t.data_ptr())
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+# ----------------------------------------------------------------------------- scene
+def sdd_scene_create(sd, n_subdomains=None, split_axis=None, ray_epsilon_m=None):
+    """Create a device scene from a ``scenes.SceneData``; returns the opaque handle."""
+    keep = []
+
+    def P(a, dt):
+        a = _c(a, dt)
+        keep.append(a)
+        return C.c_void_p(a.ctypes.data)
+
+    M = int(sd.mat_kind.shape[0])
+    mats = (sdd_material * M)()
+    lam = P(sd.table_nm, np.float32)
+    nt = int(sd.table_nm.shape[0])
+    mat_n = _c(sd.mat_n, np.float32)
+    mat_k = _c(sd.mat_k, np.float32)
+    alb = _c(sd.mat_albedo, np.float32)
+    keep += [mat_n, mat_k, alb]
+    for m in range(M):
+        mats[m].kind = int(sd.mat_kind[m])
+        mats[m].n_lambda = nt
+        mats[m].lambda_nm = lam
+        mats[m].n = C.c_void_p(mat_n.ctypes.data + 4 * nt * m)
+        mats[m].k = C.c_void_p(mat_k.ctypes.data + 4 * nt * m)
+        mats[m].albedo = C.c_void_p(alb.ctypes.data + 4 * nt * m)
+        mats[m].thickness_m = float(sd.mat_thickness[m])
+        mats[m].tile_param_id = 0
+    d = sdd_scene_desc()
+    d.n_vertices = int(sd.vertices.shape[0])
+    d.vertices = P(sd.vertices, np.float32)
+    d.n_triangles = int(sd.indices.shape[0])
+    d.indices = P(sd.indices, np.uint32)
+    d.material_of_triangle = P(sd.tri_material, np.uint16)
+    d.n_materials = M
+    d.materials = C.cast(mats, C.c_void_p)
+    il = d.illum
+    il.n_lambda = nt
+    il.lambda_nm = lam
+    il.sky_radiance = P(sd.sky, np.float32)
+    il.sky_mode = int(sd.sky_mode)
+    for i in range(3):
+        il.sun_dir[i] = float(sd.sun_dir[i])
+    il.sun_half_angle_rad = float(sd.sun_half_angle)
+    il.sun_radiance = P(sd.sun, np.float32) if sd.sun is not None else None
+    d.n_subdomains = int(sd.n_subdomains if n_subdomains is None else n_subdomains)
+    d.split_axis = int(sd.split_axis if split_axis is None else split_axis)
+    d.ray_epsilon_m = float(sd.ray_eps if ray_epsilon_m is None else ray_epsilon_m)
+    h = C.c_void_p()
+    _check(lib().sdd_scene_create(C.byref(d), C.byref(h)))
+    return h
+
+
+def sdd_scene_destroy(h):
+    lib().sdd_scene_destroy(h)
+
+
+def sdd_scene_get_info(h) -> dict:
+    info = sdd_scene_info()
+    _check(lib().sdd_scene_get_info(h, C.byref(info)))
+    out = {f[0]: getattr(info, f[0]) for f in info._fields_ if f[0] != "planes"}
+    out["planes"] = [info.planes[i] for i in range(info.n_subdomains + 1)]
+    return out
+
+
+def make_camera(cam) -> sdd_camera:
+    c = sdd_camera()
+    for i in range(3):
+        c.pos[i], c.look_at[i], c.up[i] = cam.pos[i], cam.look_at[i], cam.up[i]
+    c.vfov_deg = cam.vfov_deg
+    c.width, c.height = cam.width, cam.height
+    c.orthographic = cam.ortho
+    c.ortho_height_m = cam.ortho_height
+    return c
+
+
+def make_opts(spec, pixels=None, wave_paths=0, batched=0, path_radiance_out=None, path_hash_out=None,
+              use_surrogate=0):
+    keep = []
+    o = sdd_render_opts()
+    lam = _c(spec.lambda_nm, np.float32)
+    keep.append(lam)
+    o.n_lambda = lam.size
+    o.lambda_nm = C.c_void_p(lam.ctypes.data)
+    o.spp = spec.spp
+    o.seed = spec.seed
+    o.max_depth = spec.max_depth
+    o.mode = spec.mode
+    o.rr_start_depth = min(spec.rr_start_depth, 2**31 - 1)
+    o.use_surrogate = use_surrogate
+    o.batched = batched
+    if pixels is not None:
+        px = _c(pixels, np.int32)
+        keep.append(px)
+        o.n_pixels = px.size
+        o.pixels = C.c_void_p(px.ctypes.data)
+    o.wave_paths = wave_paths
+    o.path_radiance_out = _ptr(path_radiance_out)
+    o.path_hash_out = _ptr(path_hash_out)
+    o._keep = keep
+    return o
+
+
+def sdd_render(h, cam, spec, spectral_out, xyz_out=None, stream=None, **kw):
+    """Render into device tensors spectral_out [n_px, L] and xyz_out [n_px, 3] (float32)."""
+    c = make_camera(cam)
+    o = make_opts(spec, **kw)
+    _check(lib().sdd_render(h, C.byref(c), C.byref(o), _ptr(spectral_out), _ptr(xyz_out), _stream(stream)))
+
+
+def sdd_render_to_host(h, cam, spec, spectral_out, xyz_out=None, stream=None, **kw):
+    """Render into HOST buffers (numpy arrays or pinned CPU tensors); the library copies back."""
+    c = make_camera(cam)
+    o = make_opts(spec, **kw)
+    _check(lib().sdd_render_to_host(h, C.byref(c), C.byref(o), _ptr(spectral_out), _ptr(xyz_out), _stream(stream)))
+
+
+def sdd_set_profiling(h, level: int):
+    _check(lib().sdd_set_profiling(h, int(level)))
+
+
+def sdd_get_stats(h) -> dict:
+    s = sdd_stats()
+    _check(lib().sdd_get_stats(h, C.byref(s)))
+    return s.as_dict()
+
+
+def sdd_trace_closest(h, org, dirs, t_out, prim_out, stream=None):
+    """Closest hit of n rays: device float [n,3] origins/directions -> t [n], prim [n] (int32)."""
+    n = int(org.shape[0])
+    _check(lib().sdd_trace_closest(h, n, _ptr(org), _ptr(dirs), _ptr(t_out), _ptr(prim_out), _stream(stream)))
+
+
+def sdd_eval_optics(cos_i, n_re, k, d, lam, R, Rs, Ts, stream=None):
+    n = int(cos_i.numel())
+    _check(lib().sdd_eval_optics(n, _ptr(cos_i), _ptr(n_re), _ptr(k), _ptr(d), _ptr(lam), _ptr(R), _ptr(Rs),
+                                 _ptr(Ts), _stream(stream)))
+
+
+def sdd_philox(ctr, key: int, out, stream=None):
+    n = int(ctr.shape[0])
+    _check(lib().sdd_philox(n, _ptr(ctr), C.c_uint64(key), _ptr(out), _stream(stream)))
+
+
+def sdd_last_error() -> str:
+    return lib().sdd_last_error().decode(errors="replace")
+
+
+def sdd_version() -> str:
+    return lib().sdd_version().decode()
+
+
+class SceneHandle:
+    """RAII wrapper around an sdd_scene handle."""
+
+    def __init__(self, sd, **kw):
+        self.h = sdd_scene_create(sd, **kw)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            sdd_scene_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,62 @@
+"""The C-ABI library loads on a machine without a GPU and exports every symbol that
+include/sdd.h declares; argument validation that needs no device is exercised here too."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1912_05494_gb300 import sdd
+    return sdd
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "sdd.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sdd_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "sdd_render" in names and "sdd_scene_create" in names
+    L = lib.lib()
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_null_arguments_are_rejected_without_a_device(lib):
+    L = lib.lib()
+    out = C.c_void_p()
+    assert L.sdd_scene_create(None, C.byref(out)) == -1
+    assert b"NULL" in L.sdd_last_error()
+    assert L.sdd_render(None, None, None, None, None, None) == -1
+    assert L.sdd_trace_closest(None, 1, None, None, None, None, None) == -1
+    assert L.sdd_philox(-1, None, 0, None, None) == -1
+
+
+def test_bad_scene_descriptions_are_rejected(lib):
+    from paper_1912_05494_gb300 import scenes as S
+    sc, _, _ = S.slab_scene(0)
+    bad = S.SceneData(**{**sc.__dict__})
+    bad.indices = sc.indices.copy()
+    bad.indices[0, 0] = 10**6
+    with pytest.raises(lib.SddError, match="index out of range"):
+        lib.sdd_scene_create(bad)
+    bad2 = S.SceneData(**{**sc.__dict__})
+    bad2.mat_n = np.full_like(sc.mat_n, 0.5)
+    with pytest.raises(lib.SddError, match="n must be >= 1"):
+        lib.sdd_scene_create(bad2)
+    with pytest.raises(lib.SddError, match="n_subdomains"):
+        lib.sdd_scene_create(sc, n_subdomains=65)
+    bad3 = S.SceneData(**{**sc.__dict__})
+    bad3.table_nm = sc.table_nm[::-1].copy()
+    with pytest.raises(lib.SddError, match="ascending"):
+        lib.sdd_scene_create(bad3)

@@ -1,0 +1,227 @@
+"""GPU (through the C ABI) versus the FP64 oracle on identical seeded inputs.
+
+Tolerances:
+  * deterministic configs: per-pixel relative error <= 1e-4;
+  * Monte Carlo configs on the same Philox streams: mean relative image error <= 1e-3 and
+    branch flips (paths whose event hash differs) <= 0.1 % of paths;
+  * single-interface optics: the FP32 evaluation of R, R_slab, T_slab to 2e-6 absolute
+    (a few float ulps of quantities of order 1);
+  * Philox: bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1912_05494_gb300 import scenes as S  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def sdd():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1912_05494_gb300 import sdd as m
+    assert torch.cuda.is_available()
+    return m
+
+
+def mean_rel_image_error(a, b):
+    """Mean over pixels and wavelengths of |a - b| / (|b| + eps), eps = 1e-3 mean|b|."""
+    eps = 1e-3 * np.abs(b).mean()
+    return float(np.mean(np.abs(a - b) / (np.abs(b) + eps)))
+
+
+def render_gpu(sdd, h, cam, spec, pixels=None, paths=False, **kw):
+    n_px = cam.width * cam.height if pixels is None else len(pixels)
+    out = torch.empty((n_px, spec.n_lambda), device="cuda", dtype=torch.float32)
+    xyz = torch.empty((n_px, 3), device="cuda", dtype=torch.float32)
+    pr = ph = None
+    if paths:
+        pr = torch.empty((n_px, spec.spp, spec.n_lambda), device="cuda", dtype=torch.float32)
+        ph = torch.empty((n_px, spec.spp, spec.n_lambda), device="cuda", dtype=torch.int32)
+    sdd.sdd_render(h.h, cam, spec, out, xyz, pixels=pixels, path_radiance_out=pr, path_hash_out=ph, **kw)
+    torch.cuda.synchronize()
+    res = [out.cpu().numpy().astype(np.float64), xyz.cpu().numpy().astype(np.float64)]
+    if paths:
+        res += [pr.cpu().numpy().astype(np.float64), ph.cpu().numpy().view(np.uint32)]
+    return res
+
+
+# ----------------------------------------------------------------------------- building blocks
+def test_philox_bit_exact(sdd, orc):
+    rng = np.random.default_rng(1)
+    ctr = rng.integers(0, 2**32, (4096, 4), dtype=np.uint64).astype(np.uint32)
+    key = 0x0123456789ABCDEF
+    d_ctr = torch.from_numpy(ctr.view(np.int32)).cuda()
+    d_out = torch.empty_like(d_ctr)
+    sdd.sdd_philox(d_ctr, key, d_out)
+    gpu = d_out.cpu().numpy().view(np.uint32)
+    ref = np.vstack([orc.philox(ctr[i], [key & 0xFFFFFFFF, key >> 32]) for i in range(ctr.shape[0])])
+    assert np.array_equal(gpu, ref)
+
+
+def test_optics_module_matches_oracle(sdd, orc):
+    rng = np.random.default_rng(2)
+    n = 20000
+    cos_i = np.concatenate([rng.uniform(0, 1, n - 6), [1.0, 0.0, 1e-4, 0.05, 0.0625, 0.07]]).astype(np.float32)
+    nre = rng.uniform(1.45, 1.65, n).astype(np.float32)
+    k = np.exp(rng.uniform(np.log(1e-8), np.log(1e-4), n)).astype(np.float32)
+    d = rng.uniform(2e-3, 5e-3, n).astype(np.float32)
+    lam = rng.uniform(380, 780, n).astype(np.float32)
+    t = [torch.from_numpy(x).cuda() for x in (cos_i, nre, k, d, lam)]
+    R, Rs, Ts = (torch.empty(n, device="cuda") for _ in range(3))
+    sdd.sdd_eval_optics(*t, R, Rs, Ts)
+    R_ref, _, _ = orc.fresnel(cos_i.astype(np.float64), 1.0, nre.astype(np.float64), k.astype(np.float64))
+    Rs_ref, Ts_ref = orc.slab(cos_i, nre, k, d, lam)
+    assert np.max(np.abs(R.cpu().numpy() - R_ref)) < 2e-6
+    assert np.max(np.abs(Rs.cpu().numpy() - Rs_ref)) < 2e-6
+    assert np.max(np.abs(Ts.cpu().numpy() - Ts_ref)) < 2e-6
+    assert np.all(Rs.cpu().numpy() + Ts.cpu().numpy() <= 1.0 + 1e-6)
+
+
+@pytest.mark.parametrize("n_sub", [1, 2, 5])
+def test_closest_hit_matches_oracle_brute_force(sdd, orc, n_sub):
+    sc = S.tiny_scene(3, n_triangles=64)
+    o, d = S.random_rays(4, 20000)
+    h = sdd.SceneHandle(sc, n_subdomains=n_sub, split_axis=0)
+    do, dd = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+    t = torch.empty(o.shape[0], device="cuda")
+    prim = torch.empty(o.shape[0], device="cuda", dtype=torch.int32)
+    sdd.sdd_trace_closest(h.h, do, dd, t, prim)
+    t_ref, p_ref = orc.OracleScene(sc).closest(o.astype(np.float64), d.astype(np.float64), brute=True)
+    p = prim.cpu().numpy()
+    tg = t.cpu().numpy()
+    same = p == p_ref
+    assert same.mean() > 0.999, f"primitive mismatches: {(~same).sum()}"
+    hit = same & (p_ref >= 0)
+    assert np.allclose(tg[hit], t_ref[hit], rtol=2e-5, atol=1e-6)
+    assert hit.mean() > 0.3
+
+
+# ----------------------------------------------------------------------------- config 1: slab
+@pytest.mark.parametrize("size", [64, 16, 24])
+def test_slab_deterministic_matches_oracle(sdd, orc, size):
+    """64x64 pinhole, 16 wavelengths, reflect+transmit splitting to depth 6: per-pixel
+    relative error <= 1e-4 against the FP64 oracle.  At 16x16 and 24x24 pixel centres fall
+    exactly on the shared diagonals of the slab's faces (watertightness)."""
+    sc, cam, spec = S.slab_scene(0)
+    cam.width = cam.height = size
+    h = sdd.SceneHandle(sc)
+    gpu, gxyz = render_gpu(sdd, h, cam, spec)
+    ref, _, _ = orc.OracleScene(sc).render(cam, spec)
+    rel = np.abs(gpu - ref) / np.abs(ref)
+    assert rel.max() <= 1e-4, rel.max()
+    ref_xyz = orc.xyz(ref, spec.lambda_nm)
+    assert np.max(np.abs(gxyz - ref_xyz) / np.abs(ref_xyz)) <= 1e-4
+
+
+@pytest.mark.parametrize("n_sub,axis", [(2, 0), (7, 0), (3, 2)])
+def test_slab_is_subdomain_invariant(sdd, orc, n_sub, axis):
+    sc, cam, spec = S.slab_scene(1)
+    h1 = sdd.SceneHandle(sc, n_subdomains=1)
+    hn = sdd.SceneHandle(sc, n_subdomains=n_sub, split_axis=axis)
+    a, _ = render_gpu(sdd, h1, cam, spec)
+    b, _ = render_gpu(sdd, hn, cam, spec)
+    assert np.max(np.abs(a - b) / np.abs(a)) <= 1e-6
+
+
+def test_slab_oblique_orthographic(sdd, orc):
+    """Orthographic view at 50 degrees through a strongly absorbing slab (k = 2e-5)."""
+    sc, _, spec = S.slab_scene(2)
+    sc.mat_k[:] = 2e-5
+    th = math.radians(50.0)
+    cam = S.CameraData(pos=(0.1, -math.cos(th), math.sin(th)), look_at=(0.1, 0, 0), up=(0, 0, 1), vfov_deg=1.0,
+                       width=8, height=8, ortho=1, ortho_height=0.05)
+    h = sdd.SceneHandle(sc)
+    gpu, _ = render_gpu(sdd, h, cam, spec)
+    ref, _, _ = orc.OracleScene(sc).render(cam, spec)
+    assert np.max(np.abs(gpu - ref) / np.abs(ref)) <= 1e-4
+
+
+def test_render_to_host_equals_device_render(sdd):
+    sc, cam, spec = S.slab_scene(0)
+    h = sdd.SceneHandle(sc)
+    gpu, gxyz = render_gpu(sdd, h, cam, spec)
+    host = np.zeros((cam.width * cam.height, spec.n_lambda), np.float32)
+    hx = np.zeros((cam.width * cam.height, 3), np.float32)
+    sdd.sdd_render_to_host(h.h, cam, spec, host, hx)
+    assert np.array_equal(host.astype(np.float64), gpu)
+    assert np.array_equal(hx.astype(np.float64), gxyz)
+
+
+# ----------------------------------------------------------------------------- config 2: nave (MC)
+@pytest.fixture(scope="module")
+def nave():
+    return S.nave_scene(seed=1)
+
+
+def mc_compare(sdd, orc, sc, cam, spec, pixels, n_sub=None, **kw):
+    h = sdd.SceneHandle(sc, n_subdomains=n_sub)
+    gpu, _, gp, gh = render_gpu(sdd, h, cam, spec, pixels=pixels, paths=True, **kw)
+    ref, rp, rh = orc.OracleScene(sc).render(cam, spec, pixels=pixels, want_paths=True)
+    flips = float(np.mean(gh != rh))
+    err = mean_rel_image_error(gpu, ref)
+    same = gh == rh
+    path_rel = np.abs(gp[same] - rp[same]) / (np.abs(rp[same]) + 1e-6 * np.abs(rp).mean() + 1e-30)
+    return flips, err, path_rel, gpu, ref
+
+
+def test_nave_mc_small_frame_matches_oracle(sdd, orc, nave):
+    """The nave at 64x48, 4 spp, 81 wavelengths, depth 12, Russian roulette, 8 subdomains:
+    every path is compared on the same Philox streams."""
+    sc, cam, spec = nave
+    cam = S.CameraData(**{**cam.__dict__, "width": 64, "height": 48})
+    spec = S.RenderSpec(**{**spec.__dict__, "spp": 4})
+    flips, err, path_rel, gpu, ref = mc_compare(sdd, orc, sc, cam, spec, None)
+    assert flips <= 1e-3, flips
+    assert err <= 1e-3, err
+    assert np.quantile(path_rel, 0.999) < 1e-3
+
+
+def test_nave_full_size_sampled_pixels(sdd, orc, nave):
+    """The full 1024x768, 16 spp, 81-wavelength configuration on a seeded subset of pixels
+    (paths are keyed per pixel, so a subset is exactly the same computation)."""
+    sc, cam, spec = nave
+    pixels = np.sort(np.random.default_rng(11).choice(cam.width * cam.height, 300, replace=False)).astype(np.int32)
+    flips, err, path_rel, gpu, ref = mc_compare(sdd, orc, sc, cam, spec, pixels)
+    assert flips <= 1e-3, flips
+    assert err <= 1e-3, err
+
+
+@pytest.mark.parametrize("n_sub", [1, 3, 64])
+def test_nave_subdomain_count_does_not_change_paths(sdd, nave, n_sub):
+    """Sec. 5: hand-off keeps every ray property, so the image must not depend on S."""
+    sc, cam, spec = nave
+    cam = S.CameraData(**{**cam.__dict__, "width": 48, "height": 32})
+    spec = S.RenderSpec(**{**spec.__dict__, "spp": 2})
+    h8 = sdd.SceneHandle(sc, n_subdomains=8)
+    hn = sdd.SceneHandle(sc, n_subdomains=n_sub)
+    a, _, pa, ha = render_gpu(sdd, h8, cam, spec, paths=True)
+    b, _, pb, hb = render_gpu(sdd, hn, cam, spec, paths=True)
+    assert np.mean(ha != hb) <= 1e-3
+    same = ha == hb
+    assert np.allclose(pa[same], pb[same], rtol=1e-6, atol=0)
+
+
+def test_wave_size_does_not_change_the_image(sdd, nave):
+    sc, cam, spec = nave
+    cam = S.CameraData(**{**cam.__dict__, "width": 40, "height": 30})
+    spec = S.RenderSpec(**{**spec.__dict__, "spp": 3})
+    h = sdd.SceneHandle(sc)
+    a, ax = render_gpu(sdd, h, cam, spec)
+    b, bx = render_gpu(sdd, h, cam, spec, wave_paths=5000)
+    assert np.array_equal(a, b) and np.array_equal(ax, bx)
+
+
+def test_bad_render_arguments(sdd):
+    sc, cam, spec = S.slab_scene(0)
+    h = sdd.SceneHandle(sc)
+    out = torch.empty((cam.width * cam.height, spec.n_lambda), device="cuda")
+    bad = S.RenderSpec(**{**spec.__dict__, "spp": 2})  # deterministic mode needs spp == 1
+    with pytest.raises(sdd.SddError, match="spp"):
+        sdd.sdd_render(h.h, cam, bad, out)
+    with pytest.raises(sdd.SddError, match="pixel index"):
+        sdd.sdd_render(h.h, cam, spec, out, pixels=np.array([cam.width * cam.height], np.int32))

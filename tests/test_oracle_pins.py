@@ -205,6 +205,20 @@ def test_furnace_lossless_glass_is_white(orc):
     assert np.all(np.abs(film - 1.0) < 1e-9)
 
 
+@pytest.mark.parametrize("size", [16, 24])
+def test_rays_through_shared_edges_do_not_leak(orc, size):
+    """At 16x16 and 24x24 the pixel centres of the slab image fall exactly on the quad
+    diagonals of the front and back faces; a ray through a shared edge must hit the surface,
+    so the image stays mirror-symmetric (a leak shows up as an outlier of ~1e-3 or more)."""
+    sc, cam, spec = S.slab_scene(0)
+    cam.width = cam.height = size
+    film, _, _ = orc.OracleScene(sc).render(cam, spec)
+    img = film.reshape(size, size, 16)
+    assert np.allclose(img, img[:, ::-1], rtol=0, atol=1e-6)
+    assert np.allclose(img, img[::-1, :], rtol=0, atol=1e-6)
+    assert np.allclose(img, np.transpose(img, (1, 0, 2)), rtol=0, atol=1e-6)
+
+
 def test_camera_field_of_view_and_symmetry(orc):
     """Config-1 slab: with vfov 60 deg at 1 m, columns 0-3 and 60-63 miss the +-0.5 m slab
     (sky = 1 exactly) and columns 4-59 see glass; the image is mirror-symmetric."""
