@@ -39,7 +39,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Mspectral-samples/s at <=1% rel. image error vs FP64 oracle; surrogate vs plain"
 UNIT = "Mspectral-samples/s"
-WORKLOAD = "nave-200k 1024x768 16spp 81lambda depth12 RR S=8 (plain Monte Carlo)"
+WORKLOAD = "nave-200k {w}x{h} {spp}spp 81lambda depth12 RR S={s} (plain Monte Carlo)"
 TRAVERSE_SOURCES = ["paper_1912_05494_gb300/csrc/render_kernels.cu", "paper_1912_05494_gb300/csrc/device_math.cuh",
                     "paper_1912_05494_gb300/csrc/sdd_internal.h"]
 NCU_SUMMARY = os.path.join(ROOT, "profiles", "traverse_nave_ncu.md")
@@ -61,7 +61,7 @@ def source_hash(paths) -> str:
 
 
 def read_traffic():
-    """DRAM bytes per traversal launch from the committed ncu summary, or None when the
+    """DRAM bytes per traversed ray from the committed ncu summary, or None when the
     kernel source changed since the counters were taken."""
     if not os.path.exists(NCU_SUMMARY):
         return None
@@ -73,7 +73,7 @@ def read_traffic():
     if vals.get("kernel_source_hash") != source_hash(TRAVERSE_SOURCES):
         return None
     try:
-        return float(vals["traffic_bytes_per_launch"])
+        return float(vals["traffic_bytes_per_ray"])
     except (KeyError, ValueError):
         return None
 
@@ -161,18 +161,18 @@ def oracle_sample(scene, cam, spec, seconds_target=15.0, seed=5):
     threads = O.hardware_threads()
     rng = np.random.default_rng(seed)
     n_pix = cam.width * cam.height
-    probe = np.sort(rng.choice(n_pix, 16, replace=False)).astype(np.int32)
+    probe = np.sort(rng.choice(n_pix, 256, replace=False)).astype(np.int32)
     t0 = time.perf_counter()
     osc.render(cam, spec, pixels=probe, n_threads=threads)
     dt = max(time.perf_counter() - t0, 1e-3)
-    n = int(max(16, min(n_pix, 16 * seconds_target / dt)))
+    n = int(max(16, min(n_pix, 256 * seconds_target / dt)))
     pixels = np.sort(rng.choice(n_pix, n, replace=False)).astype(np.int32)
     t0 = time.perf_counter()
     osc.render(cam, spec, pixels=pixels, n_threads=threads)
     dt = time.perf_counter() - t0
     paths = n * spec.spp * spec.n_lambda
     return {"value": paths / dt / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{n} seeded pixels of the 1024x768 frame x {spec.spp} spp x {spec.n_lambda} lambda "
+            "sample": f"{n} seeded pixels of the {cam.width}x{cam.height} frame x {spec.spp} spp x {spec.n_lambda} lambda "
                       f"({paths} paths, {dt:.1f} s)"}
 
 
@@ -194,12 +194,36 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": frame_paths / (v * 1e6) * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "note": "each step renders a bounded seeded pixel sample; ms_per_step is "
+            "config": {"workload": WORKLOAD.format(w=cam.width, h=cam.height, spp=spec.spp, s=scene.n_subdomains),
+                       "note": "each step renders a bounded seeded pixel sample; ms_per_step is "
                                                      "the full-frame time at that rate"},
             "cpu_baseline": {**last, "value": v},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def run_e2e(args, sdd, h, cam, spec, flush, n_px, frame_paths, world, dist, kw):
+    """The same frames through sdd_render_to_host: host inputs in, images back to pinned memory."""
+    import torch
+    host_spec = torch.empty((n_px, spec.n_lambda), dtype=torch.float32, pin_memory=True)
+    host_xyz = torch.empty((n_px, 3), dtype=torch.float32, pin_memory=True)
+    sdd.sdd_render_to_host(h.h, cam, spec, host_spec, host_xyz, **kw)
+    e2e_steps = max(1, min(args.steps, 3))
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        flush.zero_()
+        sdd.sdd_render_to_host(h.h, cam, spec, host_spec, host_xyz, **kw)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    e2e_ms = reduce_max(e2e_ms, world, dist)
+    e2e_value = world * frame_paths / (e2e_ms / 1e3) / 1e6
+    h2d = 4 * spec.n_lambda + 64 + 96  # wavelength list + camera + options structs
+    d2h = (host_spec.numel() + host_xyz.numel()) * 4
+
+    return {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": e2e_ms}
 
 
 def run_gpu(args):
@@ -215,13 +239,13 @@ def run_gpu(args):
     from paper_1912_05494_gb300 import scenes as S
     from paper_1912_05494_gb300 import sdd
 
-    scene, cam, spec = S.nave_scene(seed=1)
-    spec = S.RenderSpec(**{**spec.__dict__, "seed": spec.seed + 7919 * rank})
+    scene, cam, spec = S.nave_scene(seed=1, n_subdomains=args.subdomains)
+    cam = S.CameraData(**{**cam.__dict__, "width": args.width, "height": args.height})
+    spec = S.RenderSpec(**{**spec.__dict__, "seed": spec.seed + 7919 * rank, "spp": args.spp})
     h = sdd.SceneHandle(scene)
     n_px = cam.width * cam.height
     out = torch.empty((n_px, spec.n_lambda), device="cuda", dtype=torch.float32)
     xyz = torch.empty((n_px, 3), device="cuda", dtype=torch.float32)
-    flush = torch.empty(512 * 1024 * 1024 // 4, device="cuda", dtype=torch.float32)  # 512 MB > L2
     frame_paths = n_px * spec.spp * spec.n_lambda
     kw = {"wave_paths": args.wave_paths}
     stream = torch.cuda.current_stream()
@@ -238,6 +262,7 @@ def run_gpu(args):
     trav_launches = max(cnt["launches_traverse"], 1)
 
     # timed region: K frames, L2 flushed before each, per-launch CUDA events in the library
+    flush = torch.empty(512 * 1024 * 1024 // 4, device="cuda", dtype=torch.float32)  # 512 MB > L2
     sdd.sdd_set_profiling(h.h, 1)
     clocks = ClockSampler(local)
     clocks.start()
@@ -267,45 +292,36 @@ def run_gpu(args):
 
     # end-to-end through the host-buffer entry point
     sdd.sdd_set_profiling(h.h, 0)
-    host_spec = torch.empty((n_px, spec.n_lambda), dtype=torch.float32, pin_memory=True)
-    host_xyz = torch.empty((n_px, 3), dtype=torch.float32, pin_memory=True)
-    sdd.sdd_render_to_host(h.h, cam, spec, host_spec, host_xyz, **kw)
-    e2e_steps = max(1, min(args.steps, 3))
-    if dist is not None:
-        dist.barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        flush.zero_()
-        sdd.sdd_render_to_host(h.h, cam, spec, host_spec, host_xyz, **kw)
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
-    e2e_ms = reduce_max(e2e_ms, world, dist)
-    e2e_value = world * frame_paths / (e2e_ms / 1e3) / 1e6
-    h2d = 4 * spec.n_lambda + 64 + 96  # wavelength list + camera + options structs
-    d2h = (host_spec.numel() + host_xyz.numel()) * 4
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, sdd, h, cam, spec, flush, n_px, frame_paths, world, dist, kw)
 
     peak, peak_kind = measured_peaks()
+    peak, peak_kind = measured_peaks()
     avg_launch_ms = ms_trav / max(n_trav, 1)
+    per_ray = read_traffic()
+    traffic = per_ray * cnt["rays_closest"] / trav_launches if per_ray is not None else None
     bytes_per_launch = trav_bytes / trav_launches
     achieved = bytes_per_launch / (avg_launch_ms / 1e3) / 1e9 if avg_launch_ms > 0 else 0.0
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": read_traffic(), "peak_kind": peak_kind, "kernel": "k_traverse (closest hit)",
+                "traffic": traffic, "peak_kind": peak_kind, "kernel": "k_traverse (closest hit)",
                 "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_ms,
                 "note": "algorithmic bytes = BVH nodes x 64 B + triangle records x 48 B + 44 B ray state per "
                         "subdomain visit; the ~35 MB BVH is L2-resident, so frac can exceed what DRAM moves"}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline:
         cpu = oracle_sample(scene, cam, spec, seconds_target=args.cpu_seconds)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "paths_per_step": frame_paths, "triangles": scene.n_triangles,
+                "config": {"workload": WORKLOAD.format(w=cam.width, h=cam.height, spp=spec.spp, s=scene.n_subdomains),
+                           "paths_per_step": frame_paths, "triangles": scene.n_triangles,
                            "subdomains": scene.n_subdomains, "l2": "flushed (512 MB write) before every frame",
                            "parallelism": f"replicas x{world}", "wave_paths": args.wave_paths or "auto"},
-                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                        "ms_per_step": e2e_ms},
+                "e2e": e2e,
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": launches,
                 "traversal_counts": {k: cnt[k] for k in ("rays_closest", "rays_shadow", "node_visits", "tri_tests",
@@ -329,6 +345,12 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--backend", choices=["nccl", "gloo"], default="nccl")
+    # smaller frames for profiling captures; the defaults are the benchmarked workload
+    ap.add_argument("--width", type=int, default=1024)
+    ap.add_argument("--height", type=int, default=768)
+    ap.add_argument("--spp", type=int, default=16)
+    ap.add_argument("--subdomains", type=int, default=8)
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)  # timing rule: at least three untimed warm-up frames
     if args.impl == "reference":

@@ -125,7 +125,10 @@ def test_slab_is_subdomain_invariant(sdd, orc, n_sub, axis):
     hn = sdd.SceneHandle(sc, n_subdomains=n_sub, split_axis=axis)
     a, _ = render_gpu(sdd, h1, cam, spec)
     b, _ = render_gpu(sdd, hn, cam, spec)
-    assert np.max(np.abs(a - b) / np.abs(a)) <= 1e-6
+    rel = np.abs(a - b) / np.abs(a)
+    i = np.unravel_index(np.argmax(rel), rel.shape)
+    # FP32 rounding along a six-interaction split tree; any lost or doubled ray is >= 1e-3
+    assert rel.max() <= 1e-5, (rel.max(), i, a[i], b[i])
 
 
 def test_slab_oblique_orthographic(sdd, orc):
