@@ -188,6 +188,25 @@ sdd_status sdd_scene_get_info(const sdd_scene* scene, sdd_scene_info* out);
 sdd_status sdd_trace_closest(sdd_scene* scene, int n, const float* org_dev, const float* dir_dev,
                              float* t_out_dev, int32_t* prim_out_dev, void* cuda_stream);
 
+/* sdd_trace_closest without any allocation (the paper has no counterpart; this serves
+ * callers).  Same arguments, results and queue passes as sdd_trace_closest, but its scratch
+ * (ray state, hit records, subdomain queues, counters) lives in one static 16 MiB device
+ * array inside the library instead of the scene's workspace, and the call makes no
+ * cudaMalloc, cudaFree or other allocating call.  It is meant for callers that run under a
+ * device-memory budget fixed at start-up (a service that reserves its GPU memory up front,
+ * or an application whose own allocator owns the device heap) and so cannot let a library
+ * allocate when a batch arrives.
+ *   - Capacity: n * (48 + 8 * n_subdomains) bytes plus a small control block must fit in
+ *     16 MiB (about 149,000 rays at 8 subdomains); larger n returns SDD_ERR_ARG.
+ *   - The first call on a device looks up the array's device address for that device (with
+ *     that device current); make that first call before any stream capture.
+ *   - Every GPU that uses the library keeps the 16 MiB until the process exits.
+ *   - All calls share the array and it keeps the previous call's contents; the call clears
+ *     what must start at zero.  Calls whose GPU work overlaps (other threads or streams)
+ *     race on the array: serialise them. */
+sdd_status sdd_trace_closest_noalloc(sdd_scene* scene, int n, const float* org_dev, const float* dir_dev,
+                                     float* t_out_dev, int32_t* prim_out_dev, void* cuda_stream);
+
 /* Spectral material module on its own (for tests): for n queries with device arrays
  * cos_i, n, k, thickness_m, lambda_nm writes the single-interface reflectance R (air ->
  * n + ik), and the thin-slab reflectance / transmittance.  FP32, with the FP64 branch near

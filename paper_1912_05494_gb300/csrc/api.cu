@@ -175,6 +175,15 @@ struct sdd_scene {
   }
 };
 
+namespace sdd {
+// Used by the allocation-free entry point (noalloc.cu).
+const DevScene* scene_device_view(const sdd_scene* s) { return &s->dev; }
+sdd_status set_last_error(sdd_status st, const char* msg) {
+  g_err = msg;
+  return st;
+}
+}  // namespace sdd
+
 namespace {
 
 void count_launch(sdd_scene* s, int kind) {

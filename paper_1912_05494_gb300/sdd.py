@@ -98,12 +98,14 @@ def lib():
         L.sdd_get_stats.argtypes = [vp, C.POINTER(sdd_stats)]
         L.sdd_scene_get_info.argtypes = [vp, C.POINTER(sdd_scene_info)]
         L.sdd_trace_closest.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+        L.sdd_trace_closest_noalloc.argtypes = [vp, i32, vp, vp, vp, vp, vp]
         L.sdd_eval_optics.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.sdd_philox.argtypes = [i32, vp, C.c_uint64, vp, vp]
         L.sdd_last_error.restype = C.c_char_p
         L.sdd_version.restype = C.c_char_p
         for name in ("sdd_scene_create", "sdd_render", "sdd_render_to_host", "sdd_set_profiling", "sdd_get_stats",
-                     "sdd_scene_get_info", "sdd_trace_closest", "sdd_eval_optics", "sdd_philox"):
+                     "sdd_scene_get_info", "sdd_trace_closest", "sdd_trace_closest_noalloc", "sdd_eval_optics",
+                     "sdd_philox"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -265,6 +267,13 @@ def sdd_trace_closest(h, org, dirs, t_out, prim_out, stream=None):
     """Closest hit of n rays: device float [n,3] origins/directions -> t [n], prim [n] (int32)."""
     n = int(org.shape[0])
     _check(lib().sdd_trace_closest(h, n, _ptr(org), _ptr(dirs), _ptr(t_out), _ptr(prim_out), _stream(stream)))
+
+
+def sdd_trace_closest_noalloc(h, org, dirs, t_out, prim_out, stream=None):
+    """As sdd_trace_closest, but out of the library's fixed static scratch (no allocation)."""
+    n = int(org.shape[0])
+    _check(lib().sdd_trace_closest_noalloc(h, n, _ptr(org), _ptr(dirs), _ptr(t_out), _ptr(prim_out),
+                                           _stream(stream)))
 
 
 def sdd_eval_optics(cos_i, n_re, k, d, lam, R, Rs, Ts, stream=None):
