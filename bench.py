@@ -168,12 +168,13 @@ def oracle_sample(scene, cam, spec, seconds_target=15.0, seed=5):
     n = int(max(16, min(n_pix, 256 * seconds_target / dt)))
     pixels = np.sort(rng.choice(n_pix, n, replace=False)).astype(np.int32)
     t0 = time.perf_counter()
-    osc.render(cam, spec, pixels=pixels, n_threads=threads)
+    film, path_L, path_hash = osc.render(cam, spec, pixels=pixels, n_threads=threads, want_paths=True)
     dt = time.perf_counter() - t0
     paths = n * spec.spp * spec.n_lambda
-    return {"value": paths / dt / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{n} seeded pixels of the {cam.width}x{cam.height} frame x {spec.spp} spp x {spec.n_lambda} lambda "
-                      f"({paths} paths, {dt:.1f} s)"}
+    res = {"value": paths / dt / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"{n} seeded pixels of the {cam.width}x{cam.height} frame x {spec.spp} spp x {spec.n_lambda} lambda "
+                     f"({paths} paths, {dt:.1f} s)"}
+    return res, (pixels, film, path_hash, path_L)
 
 
 def run_reference(args):
@@ -187,7 +188,7 @@ def run_reference(args):
     vals = []
     last = None
     for k in range(args.steps):
-        last = oracle_sample(scene, cam, spec, seconds_target=8.0, seed=200 + k)
+        last, _ = oracle_sample(scene, cam, spec, seconds_target=8.0, seed=200 + k)
         vals.append(last["value"])
     v = float(np.mean(vals))
     frame_paths = cam.width * cam.height * spec.spp * spec.n_lambda
@@ -201,6 +202,31 @@ def run_reference(args):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def gpu_parity_on_pixels(sdd, h, cam, spec, pixels, ref_film, ref_hash, ref_paths, kw):
+    """The GPU frame restricted to the oracle's sampled pixels (paths are keyed per pixel, so
+    this is the same computation): image error and branch flips against the FP64 oracle."""
+    import torch
+    n = len(pixels)
+    out = torch.empty((n, spec.n_lambda), device="cuda", dtype=torch.float32)
+    pr = torch.empty((n, spec.spp, spec.n_lambda), device="cuda", dtype=torch.float32)
+    ph = torch.empty((n, spec.spp, spec.n_lambda), device="cuda", dtype=torch.int32)
+    sdd.sdd_set_profiling(h.h, 0)
+    sdd.sdd_render(h.h, cam, spec, out, pixels=pixels, path_radiance_out=pr, path_hash_out=ph, **kw)
+    torch.cuda.synchronize()
+    g = out.cpu().numpy().astype(np.float64)
+    gp = pr.cpu().numpy().astype(np.float64)
+    rel_mae = float(np.abs(g - ref_film).sum() / np.abs(ref_film).sum())
+    eps = 1e-3 * np.abs(ref_film).mean()
+    per_cell = float(np.mean(np.abs(g - ref_film) / (np.abs(ref_film) + eps)))
+    flips = float(np.mean(ph.cpu().numpy().view(np.uint32) != ref_hash))
+    changed = float(np.mean(np.abs(gp - ref_paths) > 1e-6 * np.abs(ref_paths) + 1e-12))
+    return {"mean_rel_image_error": rel_mae, "branch_flip_fraction": flips, "radiance_changing_paths": changed,
+            "per_cell_rel_error": per_cell, "zero_cells": float(np.mean(ref_film == 0)), "pixels": n,
+            "definition": "sum|gpu - oracle| / sum|oracle| over the sampled pixels and wavelengths; per_cell_rel_error "
+                          "is mean |gpu - oracle| / (|oracle| + 1e-3 mean|oracle|), dominated by single flipped paths "
+                          "in cells that are exactly zero"}
 
 
 def run_e2e(args, sdd, h, cam, spec, flush, n_px, frame_paths, world, dist, kw):
@@ -247,7 +273,7 @@ def run_gpu(args):
     out = torch.empty((n_px, spec.n_lambda), device="cuda", dtype=torch.float32)
     xyz = torch.empty((n_px, 3), device="cuda", dtype=torch.float32)
     frame_paths = n_px * spec.spp * spec.n_lambda
-    kw = {"wave_paths": args.wave_paths}
+    kw = {"wave_paths": args.wave_paths, "batched": args.batched}
     stream = torch.cuda.current_stream()
 
     for _ in range(args.warmup):
@@ -260,6 +286,9 @@ def run_gpu(args):
     cnt = sdd.sdd_get_stats(h.h)
     trav_bytes = cnt["node_visits"] * 64 + cnt["tri_tests"] * 48 + cnt["rays_closest"] * 44
     trav_launches = max(cnt["launches_traverse"], 1)
+    if args.batched:  # one persistent launch per wave carries both traversals
+        trav_bytes += cnt["shadow_node_visits"] * 64 + cnt["shadow_tri_tests"] * 48 + cnt["rays_shadow"] * 44
+        trav_launches = max(cnt["launches_persistent"], 1)
 
     # timed region: K frames, L2 flushed before each, per-launch CUDA events in the library
     flush = torch.empty(512 * 1024 * 1024 // 4, device="cuda", dtype=torch.float32)  # 512 MB > L2
@@ -278,8 +307,8 @@ def run_gpu(args):
         flush.zero_()
         sdd.sdd_render(h.h, cam, spec, out, xyz, **kw)
         st = sdd.sdd_get_stats(h.h)
-        ms_trav += st["ms_traverse"]
-        n_trav += st["launches_traverse"]
+        ms_trav += st["ms_traverse"] if not args.batched else st["ms_persistent"]
+        n_trav += st["launches_traverse"] if not args.batched else st["launches_persistent"]
         launches += st["launches_total"] + 1
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -304,14 +333,17 @@ def run_gpu(args):
     bytes_per_launch = trav_bytes / trav_launches
     achieved = bytes_per_launch / (avg_launch_ms / 1e3) / 1e9 if avg_launch_ms > 0 else 0.0
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_kind": peak_kind, "kernel": "k_traverse (closest hit)",
+                "traffic": traffic if not args.batched else None, "peak_kind": peak_kind,
+                "kernel": "k_persistent_wave (all steps of a wave)" if args.batched else "k_traverse (closest hit)",
                 "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_ms,
                 "note": "algorithmic bytes = BVH nodes x 64 B + triangle records x 48 B + 44 B ray state per "
                         "subdomain visit; the ~35 MB BVH is L2-resident, so frac can exceed what DRAM moves"}
 
     cpu = None
+    parity = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = oracle_sample(scene, cam, spec, seconds_target=args.cpu_seconds)
+        cpu, (pixels, ref_film, ref_hash, ref_paths) = oracle_sample(scene, cam, spec, seconds_target=args.cpu_seconds)
+        parity = gpu_parity_on_pixels(sdd, h, cam, spec, pixels, ref_film, ref_hash, ref_paths, kw)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -322,7 +354,7 @@ def run_gpu(args):
                            "subdomains": scene.n_subdomains, "l2": "flushed (512 MB write) before every frame",
                            "parallelism": f"replicas x{world}", "wave_paths": args.wave_paths or "auto"},
                 "e2e": e2e,
-                "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
+                "roofline": roofline, "cpu_baseline": cpu, "parity": parity, "clocks": clk,
                 "gpu_launches": launches,
                 "traversal_counts": {k: cnt[k] for k in ("rays_closest", "rays_shadow", "node_visits", "tri_tests",
                                                            "shadow_node_visits", "shadow_tri_tests", "crossings")},
@@ -351,6 +383,7 @@ def main(argv=None):
     ap.add_argument("--spp", type=int, default=16)
     ap.add_argument("--subdomains", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batched", type=int, default=0, help="1: persistent kernels + CUDA graph; 0: host-driven")
     args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)  # timing rule: at least three untimed warm-up frames
     if args.impl == "reference":

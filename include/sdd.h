@@ -121,7 +121,11 @@ typedef struct {
   int mode;                /* SDD_MODE_* */
   int rr_start_depth;      /* Russian roulette from this interaction on (Monte Carlo) */
   int use_surrogate;       /* reserved: must be 0 for now */
-  int batched;             /* 0: host-driven wavefront; 1: persistent drain kernels */
+  int batched;             /* 0: host-driven wavefront (one launch per subdomain pass, queue counts
+                              read back between launches); 1: one persistent cooperative launch
+                              per wave drains every generation and pass on the device, and the
+                              frame is captured as a CUDA graph and replayed while its parameters
+                              and buffers are unchanged */
   int n_pixels;            /* 0: whole image; else render only these pixel indices */
   const int32_t* pixels;   /* host [n_pixels] row-major pixel indices (y * width + x) */
   int wave_paths;          /* paths per wave; 0 = automatic */
@@ -152,6 +156,22 @@ sdd_status sdd_render(sdd_scene* scene, const sdd_camera* cam, const sdd_render_
 sdd_status sdd_render_to_host(sdd_scene* scene, const sdd_camera* cam, const sdd_render_opts* opts,
                               float* spectral_out_host, float* xyz_out_host, void* cuda_stream);
 
+/* Launch-shape knobs of a scene (chosen by the autotuner; the defaults are safe):
+ *   traverse_block: threads per block of the traversal kernels: 64, 128 (default) or 256;
+ *   top_nodes:      BVH nodes per subdomain (the top levels, stored breadth-first) that each
+ *                   traversal block stages in shared memory, 0..640 (0 = none, default);
+ *   wave_paths:     paths per wave when sdd_render_opts.wave_paths is 0 (0 = 2^26);
+ *   no_graph:       batched form only: 1 = launch the frame's kernels directly instead of
+ *                   capturing and replaying them as a CUDA graph (default 0). */
+typedef struct {
+  int traverse_block;
+  int top_nodes;
+  int wave_paths;
+  int no_graph;
+} sdd_tuning;
+sdd_status sdd_set_tuning(sdd_scene* scene, const sdd_tuning* tuning);
+sdd_status sdd_get_tuning(const sdd_scene* scene, sdd_tuning* out);
+
 /* Per-kernel timing and counters of the most recent render. */
 typedef struct {
   double ms_raygen, ms_traverse, ms_shade, ms_shadow, ms_film, ms_total;
@@ -166,6 +186,9 @@ typedef struct {
   int64_t paths;           /* spectral paths traced */
   int64_t waves;
   int64_t bytes_ray_state; /* ray/queue/hit bytes read+written by the traversal kernels */
+  double ms_persistent;    /* batched form: persistent drain kernels (all steps of a wave) */
+  int64_t launches_persistent;
+  int64_t graph_replays;   /* batched form: frames replayed from a captured CUDA graph */
 } sdd_stats;
 
 /* level 0: nothing; 1: CUDA-event timing of every launch; 2: also count BVH nodes and

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "../../include/sdd.h"
+#include "persistent.cuh"
 #include "render_kernels.cuh"
 #include "scene_build.h"
 #include "sdd_internal.h"
@@ -117,7 +118,14 @@ struct sdd_scene {
   DevArr<float> out_spec, out_xyz;
   Control* d_ctl = nullptr;
   Control* h_ctl = nullptr;
-  int top_nodes = 0;
+  sdd_tuning tuning{128, 0, 0, 0};
+  // batched form: persistent-wave bookkeeping, internal stream and the captured frame graph
+  PersistCtl* d_pc = nullptr;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gevent = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  std::vector<unsigned char> graph_key;
+  cudaEvent_t pev[2] = {nullptr, nullptr};
   // profiling
   int profiling = 0;
   sdd_stats stats{};
@@ -137,6 +145,12 @@ struct sdd_scene {
     }
     sb_o.release(); sb_d.release(); sb_info.release(); hits.release(); path_L.release();
     path_hash.release(); film.release(); pixel_list.release(); out_spec.release(); out_xyz.release();
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
+    if (d_pc) cudaFree(d_pc);
+    if (gevent) cudaEventDestroy(gevent);
+    for (auto e : pev)
+      if (e) cudaEventDestroy(e);
+    if (gstream) cudaStreamDestroy(gstream);
     if (d_ctl) cudaFree(d_ctl);
     if (h_ctl) cudaFreeHost(h_ctl);
     for (auto e : ev_pool) cudaEventDestroy(e);
@@ -237,8 +251,6 @@ Sched make_sched(int n_sub, const int* counts, int cap, int block, int* total_bl
   return sc;
 }
 
-constexpr int kTravBlock = 128;
-
 // Closest-hit passes: the queues in q[a] (counts in ctl->q_count[a]) are traversed and
 // rays crossing an interface move to q[1-a], until every ray has a hit record.
 sdd_status run_closest_passes(sdd_scene* s, const RenderParams& p, RayBuf rb, int qcap, cudaStream_t st) {
@@ -249,12 +261,13 @@ sdd_status run_closest_passes(sdd_scene* s, const RenderParams& p, RayBuf rb, in
     if (s->h_ctl->error) return device_error(s->h_ctl->error);
     int nb;
     long long total;
-    Sched sch = make_sched(s->n_sub, s->h_ctl->q_count[a], qcap, kTravBlock, &nb, &total);
+    const int blk = s->tuning.traverse_block;
+    Sched sch = make_sched(s->n_sub, s->h_ctl->q_count[a], qcap, blk, &nb, &total);
     if (total == 0) return SDD_OK;
     CK(cudaMemsetAsync(s->d_ctl->q_count[1 - a], 0, sizeof(int) * kMaxSubdomains, st));
     QueuePair qp{s->q[a].p, s->q[1 - a].p, s->d_ctl->q_count[1 - a], qcap};
     int ev = s->ev_begin(TK_TRAVERSE, st);
-    launch_traverse(p, sch, nb, kTravBlock, s->top_nodes, qp, rb, s->hits.p, s->d_ctl, st);
+    launch_traverse(p, sch, nb, blk, s->tuning.top_nodes, qp, rb, s->hits.p, s->d_ctl, st);
     s->ev_end(ev, st);
     CK(cudaGetLastError());
     count_launch(s, TK_TRAVERSE);
@@ -272,12 +285,13 @@ sdd_status run_shadow_passes(sdd_scene* s, const RenderParams& p, const WaveDesc
     if (s->h_ctl->error) return device_error(s->h_ctl->error);
     int nb;
     long long total;
-    Sched sch = make_sched(s->n_sub, s->h_ctl->sq_count[a], qcap, kTravBlock, &nb, &total);
+    const int blk = s->tuning.traverse_block;
+    Sched sch = make_sched(s->n_sub, s->h_ctl->sq_count[a], qcap, blk, &nb, &total);
     if (total == 0) return SDD_OK;
     CK(cudaMemsetAsync(s->d_ctl->sq_count[1 - a], 0, sizeof(int) * kMaxSubdomains, st));
     QueuePair qp{s->sq[a].p, s->sq[1 - a].p, s->d_ctl->sq_count[1 - a], qcap};
     int ev = s->ev_begin(TK_SHADOW, st);
-    launch_shadow(p, w, sch, nb, kTravBlock, qp, sb, s->path_L.p, s->d_ctl, st);
+    launch_shadow(p, w, sch, nb, blk, s->tuning.top_nodes, qp, sb, s->path_L.p, s->d_ctl, st);
     s->ev_end(ev, st);
     CK(cudaGetLastError());
     count_launch(s, TK_SHADOW);
@@ -381,6 +395,115 @@ sdd_status ensure_workspace(sdd_scene* s, size_t cap, size_t paths, int n_slots,
   return ensure_ctl(s);
 }
 
+// Enqueue the whole frame of the batched form on stream `gs`: per wave, clear the wave's
+// bookkeeping and path radiance, one persistent cooperative launch, film accumulation; then
+// the final film resolve.
+sdd_status enqueue_batched_frame(sdd_scene* s, const RenderParams& p, const std::vector<WaveDesc>& waves,
+                                 const PersistBuffers& b, int n_slots, int grid, const sdd_render_opts* o,
+                                 float* spectral_out, float* xyz_out, cudaStream_t gs) {
+  CK(cudaMemsetAsync(s->d_ctl, 0, sizeof(Control), gs));
+  CK(cudaMemsetAsync(s->film.p, 0, sizeof(double) * (size_t)p.n_px * p.sp.n_lambda, gs));
+  for (const WaveDesc& w : waves) {
+    CK(cudaMemsetAsync(s->d_pc, 0, sizeof(PersistCtl), gs));
+    CK(cudaMemsetAsync(s->path_L.p, 0, sizeof(float) * (size_t)w.n_paths * n_slots, gs));
+    CK(launch_persistent_wave(p, w, b, s->d_pc, s->d_ctl, grid, gs));
+    launch_film_accum(p, w, s->path_L.p, s->film.p, o->path_radiance_out, o->path_hash_out, gs);
+    CK(cudaGetLastError());
+  }
+  launch_film_finalize(p, s->film.p, s->cmf_w.p, spectral_out, xyz_out, gs);
+  CK(cudaGetLastError());
+  return SDD_OK;
+}
+
+// The batched form: the frame runs on the scene's internal stream (ordered after the
+// caller's stream), captured once as a CUDA graph and replayed while the key -- every kernel
+// parameter and buffer address of the frame -- is unchanged.
+sdd_status render_batched(sdd_scene* s, const RenderParams& p, const std::vector<WaveDesc>& waves, int n_slots,
+                          int qcap, const sdd_render_opts* o, float* spectral_out, float* xyz_out, cudaStream_t st) {
+  if (!s->gstream) {
+    CK(cudaStreamCreateWithFlags(&s->gstream, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&s->gevent, cudaEventDisableTiming));
+    CK(cudaEventCreate(&s->pev[0]));
+    CK(cudaEventCreate(&s->pev[1]));
+  }
+  if (!s->d_pc) CK(cudaMalloc(&s->d_pc, sizeof(PersistCtl)));
+  const int grid = persistent_grid(p.stats >= 2);
+  if (grid <= 0) return fail(SDD_ERR_CUDA, "persistent kernel does not fit on this device");
+  PersistBuffers b;
+  for (int i = 0; i < 2; ++i) {
+    b.rb[i] = RayBuf{s->rb_o[i].p, s->rb_d[i].p, s->rb_info[i].p, qcap};
+    b.q[i] = s->q[i].p;
+    b.sq[i] = s->sq[i].p;
+  }
+  b.hits = s->hits.p;
+  b.sb = ShadowBuf{s->sb_o.p, s->sb_d.p, s->sb_info.p, qcap};
+  b.path_L = s->path_L.p;
+  b.qcap = qcap;
+  // graph key: everything the captured frame depends on
+  std::vector<unsigned char> key;
+  auto put = [&key](const void* d, size_t n) {
+    const unsigned char* c = static_cast<const unsigned char*>(d);
+    key.insert(key.end(), c, c + n);
+  };
+  put(&p, sizeof(p));
+  put(&b, sizeof(b));
+  put(&grid, sizeof(grid));
+  put(&n_slots, sizeof(n_slots));
+  for (const WaveDesc& w : waves) put(&w, sizeof(w));
+  const void* ptrs[] = {spectral_out, xyz_out, o->path_radiance_out, o->path_hash_out, s->film.p, s->cmf_w.p,
+                        s->d_pc, s->d_ctl};
+  put(ptrs, sizeof(ptrs));
+
+  CK(cudaEventRecord(s->gevent, st));
+  CK(cudaStreamWaitEvent(s->gstream, s->gevent, 0));
+  if (s->profiling >= 1) CK(cudaEventRecord(s->pev[0], s->gstream));
+  bool replay = s->graph_exec && key == s->graph_key;
+  if (!replay) {
+    if (s->graph_exec) {
+      cudaGraphExecDestroy(s->graph_exec);
+      s->graph_exec = nullptr;
+      s->graph_key.clear();
+    }
+    cudaGraph_t graph = nullptr;
+    bool captured = false;
+    if (!s->tuning.no_graph && cudaStreamBeginCapture(s->gstream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      sdd_status r = enqueue_batched_frame(s, p, waves, b, n_slots, grid, o, spectral_out, xyz_out, s->gstream);
+      cudaError_t ec = cudaStreamEndCapture(s->gstream, &graph);
+      if (r == SDD_OK && ec == cudaSuccess && graph &&
+          cudaGraphInstantiate(&s->graph_exec, graph, 0) == cudaSuccess) {
+        captured = true;
+        s->graph_key = key;
+      }
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();  // a failed capture leaves a sticky-free error; clear it
+    }
+    if (!captured) {
+      // capture not available: enqueue the same frame directly
+      s->graph_exec = nullptr;
+      sdd_status r = enqueue_batched_frame(s, p, waves, b, n_slots, grid, o, spectral_out, xyz_out, s->gstream);
+      if (r) return r;
+    }
+  }
+  if (s->graph_exec) {
+    CK(cudaGraphLaunch(s->graph_exec, s->gstream));
+    if (replay) s->stats.graph_replays++;
+  }
+  if (s->profiling >= 1) CK(cudaEventRecord(s->pev[1], s->gstream));
+  CK(cudaStreamSynchronize(s->gstream));
+  s->stats.launches_persistent += (int64_t)waves.size();
+  s->stats.launches_film += (int64_t)waves.size() + 1;
+  s->stats.launches_total += 2 * (int64_t)waves.size() + 1;
+  if (s->profiling >= 1) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, s->pev[0], s->pev[1]);
+    s->stats.ms_persistent = ms;
+  }
+  PersistCtl hpc;
+  CK(cudaMemcpy(&hpc, s->d_pc, sizeof(PersistCtl), cudaMemcpyDeviceToHost));
+  if (hpc.abort) return fail(SDD_ERR_TIMEOUT, "persistent wave abandoned: a grid barrier hit its time limit");
+  return SDD_OK;
+}
+
 sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opts* o, float* spectral_out,
                        float* xyz_out, cudaStream_t st) {
   if (!s || !cam || !o) return fail(SDD_ERR_ARG, "NULL scene, camera or options");
@@ -417,7 +540,7 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
 
   // waves
   const bool det = o->mode == SDD_MODE_DETERMINISTIC;
-  long long wmax = o->wave_paths > 0 ? o->wave_paths : (1LL << 26);
+  long long wmax = o->wave_paths > 0 ? o->wave_paths : (s->tuning.wave_paths > 0 ? s->tuning.wave_paths : (1LL << 26));
   wmax = std::min<long long>(wmax, 1LL << 28);
   std::vector<WaveDesc> waves;
   if (n_cells <= wmax) {
@@ -491,8 +614,29 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
   p.path_hash = want_hash ? s->path_hash.p : nullptr;
 
   s->stats = sdd_stats{};
-  CK(cudaMemsetAsync(s->d_ctl, 0, sizeof(Control), st));
   const int qcap = (int)cap;
+  if (o->batched) {
+    r = render_batched(s, p, waves, n_slots, qcap, o, spectral_out, xyz_out, st);
+    if (r) return r;
+    for (const WaveDesc& w : waves) {
+      s->stats.waves++;
+      s->stats.paths += w.n_paths;
+    }
+    r = read_ctl(s, s->gstream);
+    if (r) return r;
+    if (s->h_ctl->error) return device_error(s->h_ctl->error);
+    s->stats.node_visits = (int64_t)s->h_ctl->node_visits;
+    s->stats.tri_tests = (int64_t)s->h_ctl->tri_tests;
+    s->stats.shadow_node_visits = (int64_t)s->h_ctl->shadow_node_visits;
+    s->stats.shadow_tri_tests = (int64_t)s->h_ctl->shadow_tri_tests;
+    s->stats.rays_closest = (int64_t)s->h_ctl->rays_closest;
+    s->stats.rays_shadow = (int64_t)s->h_ctl->rays_shadow;
+    s->stats.crossings = (int64_t)s->h_ctl->crossings;
+    s->stats.bytes_ray_state = s->stats.rays_closest * 44 + s->stats.rays_shadow * 44;
+    s->stats.ms_total = s->stats.ms_persistent;
+    return SDD_OK;
+  }
+  CK(cudaMemsetAsync(s->d_ctl, 0, sizeof(Control), st));
   for (const WaveDesc& w : waves) {
     CK(cudaMemsetAsync(s->d_ctl, 0, offsetof(Control, node_visits), st));
     CK(cudaMemsetAsync(s->path_L.p, 0, sizeof(float) * (size_t)w.n_paths * n_slots, st));
@@ -772,6 +916,23 @@ sdd_status sdd_render_to_host(sdd_scene* s, const sdd_camera* cam, const sdd_ren
   if (spec_host) CK(cudaMemcpyAsync(spec_host, s->out_spec.p, ns * sizeof(float), cudaMemcpyDeviceToHost, st));
   if (xyz_host) CK(cudaMemcpyAsync(xyz_host, s->out_xyz.p, nx * sizeof(float), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  return SDD_OK;
+}
+
+sdd_status sdd_set_tuning(sdd_scene* s, const sdd_tuning* t) {
+  if (!s || !t) return fail(SDD_ERR_ARG, "NULL argument");
+  if (t->traverse_block != 64 && t->traverse_block != 128 && t->traverse_block != 256)
+    return fail(SDD_ERR_ARG, "traverse_block must be 64, 128 or 256");
+  if (t->top_nodes < 0 || t->top_nodes > 640) return fail(SDD_ERR_ARG, "top_nodes must be in [0, 640]");
+  if (t->wave_paths < 0) return fail(SDD_ERR_ARG, "wave_paths must be >= 0");
+  if (t->no_graph != 0 && t->no_graph != 1) return fail(SDD_ERR_ARG, "no_graph must be 0 or 1");
+  s->tuning = *t;
+  return SDD_OK;
+}
+
+sdd_status sdd_get_tuning(const sdd_scene* s, sdd_tuning* t) {
+  if (!s || !t) return fail(SDD_ERR_ARG, "NULL argument");
+  *t = s->tuning;
   return SDD_OK;
 }
 

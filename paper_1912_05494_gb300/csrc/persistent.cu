@@ -1,0 +1,223 @@
+// persistent.cu -- the batched form of the wavefront: one cooperative launch drains a
+// whole wave.
+//
+// Sec. 5 of the paper lets a processor keep several sub-domains loaded, work on whichever
+// still has many rays, and gather results while other rays are processed; Sec. 4 asks for
+// dynamic job balancing so that faster workers take more work.  On one GB300 this becomes a
+// persistent kernel: every block loops over
+//   raygen -> per generation: [closest-hit passes over all subdomain queues, blocks taking
+//   128-ray chunks from a shared work counter] -> shade -> [shadow passes] -> film
+// with grid-wide barriers between the steps instead of host round trips.  The per-ray work
+// is the same device code as the host-driven kernels (render_device.cuh), so both forms
+// produce bit-identical images.
+//
+// Queue bookkeeping without races: queue counts rotate through three buffers.  The step
+// that consumes buffer c appends hand-offs into c+1 and clears c+2 (consumed two steps ago,
+// copied by every block before the barrier that ended that step), so a buffer is always
+// cleared one barrier before anyone appends to it.  Work counters rotate the same way.  A
+// pass that finds its input empty ends without a barrier, so nothing may write its input
+// buffer until the next barrier: the following step writes the next buffer instead.
+//
+// Every grid barrier waits at most kBarrierTimeoutNs; on expiry the block sets the abort
+// flag and the frame's error word, all blocks leave at their next barrier and the host
+// reports SDD_ERR_TIMEOUT.
+#include <cooperative_groups.h>
+
+#include "persistent.cuh"
+#include "render_device.cuh"
+
+namespace sdd {
+
+namespace {
+
+constexpr int kPB = 128;  // threads per block
+constexpr unsigned long long kBarrierTimeoutNs = 5ull * 1000 * 1000 * 1000;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier with a time limit.  Returns false when the wave must be abandoned.
+__device__ bool grid_barrier(PersistCtl* pc, Control* ctl) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = &pc->bar_gen;
+    volatile int* vabort = &pc->abort;
+    unsigned g = *vgen;
+    __threadfence();
+    unsigned arrived = atomicAdd(&pc->bar_count, 1u);
+    if (arrived == gridDim.x - 1) {
+      pc->bar_count = 0;
+      __threadfence();
+      atomicAdd(&pc->bar_gen, 1u);
+    } else {
+      unsigned long long t0 = global_ns();
+      while (*vgen == g) {
+        if (*vabort) break;
+        if (global_ns() - t0 > kBarrierTimeoutNs) {
+          atomicExch(&pc->abort, 1);
+          atomicOr(&ctl->error, ERR_TIMEOUT);  // survives the next wave's reset of pc
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = *vabort == 0;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Exclusive prefix sums of the n_sub queue counts into shared memory; returns the total.
+__device__ int load_prefix(const int* counts, int n_sub, int cap, int* s_prefix) {
+  __shared__ int s_total;
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int s = 0; s < n_sub; ++s) {
+      s_prefix[s] = acc;
+      acc += min(max(((volatile const int*)counts)[s], 0), cap);
+    }
+    s_prefix[n_sub] = acc;
+    s_total = acc;
+  }
+  __syncthreads();
+  return s_total;
+}
+
+__device__ __forceinline__ int find_subdomain(const int* s_prefix, int n_sub, int j) {
+  int lo = 0, hi = n_sub - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (s_prefix[mid] <= j) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Clear the count buffer and work counter that the step after next will write.
+__device__ __forceinline__ void clear_ahead(int (*counts)[kMaxSubdomains], int* work, int idx) {
+  if (blockIdx.x == 0) {
+    for (int s = threadIdx.x; s < kMaxSubdomains; s += blockDim.x) counts[idx][s] = 0;
+    if (threadIdx.x == 0) work[idx] = 0;
+  }
+}
+
+}  // namespace
+
+template <bool kStats>
+__global__ void __launch_bounds__(kPB) k_persistent_wave(RenderParams p, WaveDesc w, PersistBuffers b,
+                                                         PersistCtl* pc, Control* ctl) {
+  __shared__ int s_prefix[kMaxSubdomains + 1];
+  __shared__ int s_chunk;
+  const int n_sub = p.sc.n_sub;
+  const uint32_t nthreads = gridDim.x * blockDim.x;
+
+  // raygen: primary rays into generation 0 and the closest queues (counts buffer 0)
+  for (uint32_t base = blockIdx.x * blockDim.x; base < w.n_paths; base += nthreads) {
+    uint32_t i = base + threadIdx.x;
+    dev_raygen(p, w, i, i < w.n_paths, b.rb[0], b.q[0], pc->qc[0], b.qcap, ctl);
+  }
+  if (!grid_barrier(pc, ctl)) return;
+
+  int cq = 0, qe = 0;  // closest queues: input counts buffer, input entries buffer
+  int sq = 0, se = 0;  // shadow queues
+  int cur = 0;         // ray generation buffer
+  int n_rays = (int)w.n_paths;
+  for (int gen = 0; n_rays > 0; ++gen) {
+    if (gen > p.max_depth + 1) {
+      if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(&ctl->error, ERR_TIMEOUT);
+      break;
+    }
+    const int par = gen & 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      pc->next_rays[par] = 0;
+      pc->next_shadow[par] = 0;
+    }
+    bool ran_pass = false;
+    for (int pass = 0; pass <= 2 * kMaxSubdomains + 2; ++pass) {
+      int total = load_prefix(pc->qc[cq], n_sub, b.qcap, s_prefix);
+      clear_ahead(pc->qc, pc->wq, (cq + 2) % 3);
+      if (total == 0) break;
+      QueuePair qp{b.q[qe], b.q[1 - qe], pc->qc[(cq + 1) % 3], b.qcap};
+      for (;;) {
+        if (threadIdx.x == 0) s_chunk = atomicAdd(&pc->wq[cq], (int)blockDim.x);
+        __syncthreads();
+        const int c0 = s_chunk;
+        __syncthreads();
+        if (c0 >= total) break;
+        const int j = c0 + (int)threadIdx.x;
+        const bool act = j < total;
+        const int s = find_subdomain(s_prefix, n_sub, act ? j : 0);
+        dev_traverse<kStats>(p, s, j - s_prefix[s], act, nullptr, 0, qp, b.rb[cur], b.hits, ctl);
+      }
+      ran_pass = true;
+      if (!grid_barrier(pc, ctl)) return;
+      cq = (cq + 1) % 3;
+      qe = 1 - qe;
+    }
+    if (!ran_pass && !grid_barrier(pc, ctl)) return;
+
+    // Shade every ray of this generation.  The last closest pass found its input buffer cq
+    // empty and left without a barrier, so slower blocks may still be reading cq: children
+    // go to the next buffer in the rotation instead (cleared two steps ago, read by nobody),
+    // and the rotation moves past the empty pass.  Shadow rays go to the shadow queues.
+    for (uint32_t base = blockIdx.x * blockDim.x; base < (uint32_t)n_rays; base += nthreads) {
+      int r = (int)(base + threadIdx.x);
+      dev_shade(p, w, r, r < n_rays, b.rb[cur], b.hits, b.rb[1 - cur], &pc->next_rays[par], b.q[1 - qe],
+                pc->qc[(cq + 1) % 3], b.qcap, b.sb, &pc->next_shadow[par], b.sq[se], pc->sqc[sq], b.path_L, ctl);
+    }
+    cq = (cq + 1) % 3;
+    qe = 1 - qe;
+    if (!grid_barrier(pc, ctl)) return;
+
+    for (int pass = 0; pass <= 2 * kMaxSubdomains + 2; ++pass) {
+      int total = load_prefix(pc->sqc[sq], n_sub, b.qcap, s_prefix);
+      clear_ahead(pc->sqc, pc->wsq, (sq + 2) % 3);
+      if (total == 0) break;
+      QueuePair qp{b.sq[se], b.sq[1 - se], pc->sqc[(sq + 1) % 3], b.qcap};
+      for (;;) {
+        if (threadIdx.x == 0) s_chunk = atomicAdd(&pc->wsq[sq], (int)blockDim.x);
+        __syncthreads();
+        const int c0 = s_chunk;
+        __syncthreads();
+        if (c0 >= total) break;
+        const int j = c0 + (int)threadIdx.x;
+        const bool act = j < total;
+        const int s = find_subdomain(s_prefix, n_sub, act ? j : 0);
+        dev_shadow<kStats>(p, w, s, j - s_prefix[s], act, nullptr, 0, qp, b.sb, b.path_L, ctl);
+      }
+      if (!grid_barrier(pc, ctl)) return;
+      sq = (sq + 1) % 3;
+      se = 1 - se;
+    }
+    n_rays = min(*(volatile int*)&pc->next_rays[par], b.qcap);
+    if (*(volatile int*)&pc->next_rays[par] > b.qcap && threadIdx.x == 0 && blockIdx.x == 0)
+      atomicOr(&ctl->error, ERR_QUEUE_OVERFLOW);
+    cur = 1 - cur;
+  }
+}
+
+template <bool kStats>
+static int persistent_blocks() {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent_wave<kStats>, kPB, 0);
+  return sms * per_sm;
+}
+
+int persistent_grid(bool stats) { return stats ? persistent_blocks<true>() : persistent_blocks<false>(); }
+
+cudaError_t launch_persistent_wave(const RenderParams& p, const WaveDesc& w, const PersistBuffers& b, PersistCtl* pc,
+                                   Control* ctl, int grid, cudaStream_t st) {
+  void* args[] = {(void*)&p, (void*)&w, (void*)&b, (void*)&pc, (void*)&ctl};
+  if (p.stats >= 2)
+    return cudaLaunchCooperativeKernel((const void*)k_persistent_wave<true>, dim3(grid), dim3(kPB), args, 0, st);
+  return cudaLaunchCooperativeKernel((const void*)k_persistent_wave<false>, dim3(grid), dim3(kPB), args, 0, st);
+}
+
+}  // namespace sdd

@@ -1,0 +1,604 @@
+// render_device.cuh -- per-ray device functions of the wavefront path, shared by the
+// host-driven kernels (render_kernels.cu) and the persistent drain kernel (persistent.cu).
+//
+// One generation of rays is processed by:
+//   dev_traverse  closest hit per subdomain queue (Sec. 3.1: the cost of ray tracing lies in
+//                 the intersectors); a ray that leaves its slab without a hit is handed,
+//                 unchanged, to the neighbouring slab's queue (Sec. 5: interface conditions
+//                 keep the ray properties continuous)
+//   dev_shade     per-wavelength shading: complex Fresnel, Snell, Beer-Lambert (Eq. 1),
+//                 thin-slab series, Lambertian walls with a shadow ray to the sun (Eq. 3),
+//                 deterministic splitting (Sec. 3.1) or Philox-driven choices (Sec. 3.2);
+//                 children are compacted into the next generation and binned by subdomain
+//   dev_shadow    any-hit transmittance toward the sun per subdomain queue, with hand-off
+// Queue appends are warp-aggregated: one atomic per distinct target queue per warp (ballot /
+// match_any / popc).  Every function that appends must be called by all 32 lanes of a warp.
+#pragma once
+
+#include <math_constants.h>
+
+#include "device_math.cuh"
+#include "render_kernels.cuh"
+
+namespace sdd {
+
+namespace {
+
+constexpr float kInvPi = 0.31830988618379067f;
+constexpr int kBlock = 128;
+
+enum Event : uint32_t {
+  EV_REFLECT = 0, EV_TRANSMIT = 1, EV_DIFFUSE = 2, EV_ABSORB = 3, EV_RR_KILL = 4,
+  EV_DEPTH_CAP = 5, EV_ESCAPE = 6, EV_SHADOW_BLOCKED = 7, EV_SHADOW_OPEN = 8
+};
+
+__device__ __forceinline__ uint32_t fnv_byte(uint32_t h, uint32_t b) { return (h ^ (b & 0xFFu)) * 0x01000193u; }
+__device__ __forceinline__ uint32_t fnv_word(uint32_t h, uint32_t w) {
+  h = fnv_byte(h, w);
+  h = fnv_byte(h, w >> 8);
+  h = fnv_byte(h, w >> 16);
+  return fnv_byte(h, w >> 24);
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Warp-aggregated append.  Every lane of the warp calls it (converged); lanes with `want`
+// get consecutive slots of counters[key], one atomicAdd per distinct key in the warp.
+__device__ __forceinline__ int warp_append(int* counters, int key, bool want) {
+  unsigned act = __ballot_sync(0xffffffffu, want);
+  int pos = -1;
+  if (want) {
+    unsigned peers = __match_any_sync(act, key);
+    int leader = __ffs(peers) - 1;
+    int base = 0;
+    if ((int)(threadIdx.x & 31) == leader) base = atomicAdd(&counters[key], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    pos = base + __popc(peers & lanemask_lt());
+  }
+  return pos;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ int subdomain_of(const DevScene& sc, float3 o) {
+  float x = comp3(o, sc.axis);
+  int s = 0;
+  for (int i = 1; i < sc.n_sub; ++i) s += (x >= sc.planes[i]) ? 1 : 0;
+  return s;
+}
+
+// The part of the ray inside slab s: t in (t0, t1]; `next` is the slab it enters at t1
+// (-1 when it leaves the outermost slab, i.e. it escapes).
+__device__ __forceinline__ void slab_interval(const DevScene& sc, int s, float3 o, float3 d, float* t0, float* t1,
+                                              int* next) {
+  float oa = comp3(o, sc.axis), da = comp3(d, sc.axis);
+  *t0 = 0.f;
+  *t1 = CUDART_INF_F;
+  *next = -1;
+  if (da > 0.f) {
+    if (s + 1 < sc.n_sub) {
+      *t1 = (sc.planes[s + 1] - oa) / da;
+      *next = s + 1;
+    }
+    if (s > 0) *t0 = fmaxf(0.f, (sc.planes[s] - oa) / da);
+  } else if (da < 0.f) {
+    if (s > 0) {
+      *t1 = (sc.planes[s] - oa) / da;
+      *next = s - 1;
+    }
+    if (s + 1 < sc.n_sub) *t0 = fmaxf(0.f, (sc.planes[s + 1] - oa) / da);
+  }
+}
+
+__device__ __forceinline__ Node load_node(const Node* __restrict__ g, const Node* s_nodes, int idx, int root,
+                                          int n_staged) {
+  int local = idx - root;
+  if (local >= 0 && local < n_staged) return s_nodes[local];
+  const float4* p = reinterpret_cast<const float4*>(g + idx);
+  Node n;
+  n.a = __ldg(p);
+  n.b = __ldg(p + 1);
+  n.c = __ldg(p + 2);
+  float4 d = __ldg(p + 3);
+  n.d = make_int4(__float_as_int(d.x), __float_as_int(d.y), __float_as_int(d.z), __float_as_int(d.w));
+  return n;
+}
+
+// Stage the first `want` nodes (the top BVH levels, stored breadth-first) of subdomain s.
+__device__ __forceinline__ int stage_top(const DevScene& sc, Node* s_nodes, int s, int want) {
+  int n = min(want, sc.n_nodes_sub[s]);
+  const float4* src = reinterpret_cast<const float4*>(sc.nodes + sc.root[s]);
+  float4* dst = reinterpret_cast<float4*>(s_nodes);
+  for (int i = threadIdx.x; i < 4 * n; i += blockDim.x) dst[i] = __ldg(src + i);
+  __syncthreads();
+  return n;
+}
+
+// Closest hit in (t0, t1] against subdomain s's BVH.  Ties in t go to the lower primitive.
+template <bool kStats>
+__device__ __forceinline__ uint32_t closest_hit(const DevScene& sc, const Node* s_nodes, int n_staged, int s,
+                                                const RayPre& rp, float t0, float t1, float* t_out,
+                                                uint32_t* n_nodes, uint32_t* n_tris, bool* overflow) {
+  int stack[kStackSize];
+  int sp = 0;
+  const int root = sc.root[s];
+  int node = root;
+  float tbest = t1;
+  uint32_t best = kMissPrim;
+  for (;;) {
+    Node n = load_node(sc.nodes, s_nodes, node, root, n_staged);
+    if (kStats) ++*n_nodes;
+    float tn0, tn1;
+    bool h0 = n.d.x >= 0 && box_hit(rp, n.a.x, n.a.y, n.a.z, n.a.w, n.c.x, n.c.y, t0, tbest, &tn0);
+    bool h1 = n.d.y >= 0 && box_hit(rp, n.b.x, n.b.y, n.b.z, n.b.w, n.c.z, n.c.w, t0, tbest, &tn1);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      bool hc = c == 0 ? h0 : h1;
+      int cnt = c == 0 ? n.d.z : n.d.w;
+      if (hc && cnt > 0) {
+        int first = c == 0 ? n.d.x : n.d.y;
+        for (int i = first; i < first + cnt; ++i) {
+          const float4* tp = reinterpret_cast<const float4*>(sc.tris + i);
+          float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
+          if (kStats) ++*n_tris;
+          float t = tri_hit(rp, v0, v1, v2, t0, tbest);
+          if (t >= 0.f) {
+            uint32_t prim = __float_as_uint(v0.w);
+            if (t < tbest || prim < best) {
+              tbest = t;
+              best = prim;
+            }
+          }
+        }
+        if (c == 0) h0 = false; else h1 = false;
+      }
+    }
+    if (h0 && h1) {
+      bool first0 = tn0 <= tn1;
+      if (sp < kStackSize) stack[sp++] = first0 ? n.d.y : n.d.x;
+      else *overflow = true;
+      node = first0 ? n.d.x : n.d.y;
+    } else if (h0) {
+      node = n.d.x;
+    } else if (h1) {
+      node = n.d.y;
+    } else {
+      if (sp == 0) break;
+      node = stack[--sp];
+    }
+  }
+  *t_out = tbest;
+  return best;
+}
+
+// Transmittance of a shadow ray across subdomain s over (t0, t1]: thin-slab tiles
+// multiply their slab transmittance; anything else blocks (returns 0).
+template <bool kStats>
+__device__ __forceinline__ float shadow_T(const DevScene& sc, const DevSpectral& sp, int lam, float lambda_nm,
+                                          const Node* s_nodes, int n_staged, int s, const RayPre& rp, float3 d,
+                                          float t0, float t1, uint32_t* n_nodes, uint32_t* n_tris,
+                                          bool* overflow) {
+  int stack[kStackSize];
+  int spn = 0;
+  const int root = sc.root[s];
+  int node = root;
+  float T = 1.f;
+  for (;;) {
+    Node n = load_node(sc.nodes, s_nodes, node, root, n_staged);
+    if (kStats) ++*n_nodes;
+    float tn0, tn1;
+    bool h0 = n.d.x >= 0 && box_hit(rp, n.a.x, n.a.y, n.a.z, n.a.w, n.c.x, n.c.y, t0, t1, &tn0);
+    bool h1 = n.d.y >= 0 && box_hit(rp, n.b.x, n.b.y, n.b.z, n.b.w, n.c.z, n.c.w, t0, t1, &tn1);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      bool hc = c == 0 ? h0 : h1;
+      int cnt = c == 0 ? n.d.z : n.d.w;
+      if (hc && cnt > 0) {
+        int first = c == 0 ? n.d.x : n.d.y;
+        for (int i = first; i < first + cnt; ++i) {
+          const float4* tp = reinterpret_cast<const float4*>(sc.tris + i);
+          float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
+          if (kStats) ++*n_tris;
+          float t = tri_hit(rp, v0, v1, v2, t0, t1);
+          if (t >= 0.f) {
+            uint32_t prim = __float_as_uint(v0.w);
+            float4 nm = __ldg(sc.prim_nrm_mat + prim);
+            int mat = __float_as_int(nm.w);
+            if (__ldg(sp.mat_kind + mat) != MAT_SLAB) return 0.f;
+            float cos_i = fabsf(dot3(d, f3(nm)));
+            size_t mi = (size_t)mat * sp.n_lambda + lam;
+            float Rs, Ts;
+            slab_RT(cos_i, __ldg(sp.mat_n + mi), __ldg(sp.mat_k + mi), __ldg(sp.mat_thick + mat), lambda_nm, &Rs,
+                    &Ts);
+            T *= Ts;
+          }
+        }
+        if (c == 0) h0 = false; else h1 = false;
+      }
+    }
+    if (h0 && h1) {
+      if (spn < kStackSize) stack[spn++] = n.d.x;
+      else *overflow = true;
+      node = n.d.y;
+    } else if (h0) {
+      node = n.d.x;
+    } else if (h1) {
+      node = n.d.y;
+    } else {
+      if (spn == 0) break;
+      node = stack[--spn];
+    }
+  }
+  return T;
+}
+
+__device__ __forceinline__ float3 offset_point(float3 p, float3 ng, float3 dir, float eps) {
+  return dot3(dir, ng) >= 0.f ? p + eps * ng : p - eps * ng;
+}
+__device__ __forceinline__ float seg0_of(float3 ng, float3 dir, float eps) {
+  return eps / fmaxf(fabsf(dot3(ng, dir)), 1e-6f);
+}
+__device__ __forceinline__ float3 reflect3(float3 d, float3 n) { return d - (2.f * dot3(d, n)) * n; }
+
+struct PathId {
+  uint32_t sample, cell, px_i, lam, pixel;
+};
+__device__ __forceinline__ PathId path_id(const RenderParams& p, const WaveDesc& w, uint32_t path) {
+  PathId r;
+  uint32_t ls = path / w.nc;
+  uint32_t lc = path - ls * w.nc;
+  r.sample = w.s0 + ls;
+  r.cell = w.c0 + lc;
+  r.px_i = r.cell / (uint32_t)p.sp.n_lambda;
+  r.lam = r.cell - r.px_i * (uint32_t)p.sp.n_lambda;
+  r.pixel = p.pixel_list ? (uint32_t)p.pixel_list[r.px_i] : r.px_i;
+  return r;
+}
+
+__device__ __forceinline__ float escape_radiance(const DevSpectral& sp, float3 d, int lam, bool sun_counted) {
+  float L = (sp.sky_mode == 0 || d.z > 0.f) ? __ldg(sp.sky + lam) : 0.f;
+  if (!sun_counted && sp.sun_h > 0.f) {
+    float3 c = d - sp.sun_dir;
+    if (dot3(c, c) <= 2.f * sp.sun_h) L += __ldg(sp.sun + lam);
+  }
+  return L;
+}
+
+// Append a ray to the next generation and bin it by the subdomain of its origin.
+__device__ __forceinline__ void emit_ray(bool want, const DevScene& sc, RayBuf nb, int* next_count, uint32_t* q,
+                                         int* q_count, int qcap, float3 o, float seg0, float3 d, float thr,
+                                         uint32_t path, uint32_t meta, Control* ctl) {
+  int pos = warp_append(next_count, 0, want);
+  bool ok = want && pos < nb.cap;
+  if (want && !ok) atomicOr(&ctl->error, ERR_QUEUE_OVERFLOW);
+  if (ok) {
+    nb.o[pos] = make_float4(o.x, o.y, o.z, seg0);
+    nb.d[pos] = make_float4(d.x, d.y, d.z, thr);
+    nb.info[pos] = make_uint2(path, meta);
+  }
+  int s = ok ? subdomain_of(sc, o) : 0;
+  int qpos = warp_append(q_count, s, ok);
+  if (ok) {
+    if (qpos < qcap) q[(size_t)s * qcap + qpos] = (uint32_t)pos;
+    else atomicOr(&ctl->error, ERR_QUEUE_OVERFLOW);
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ raygen
+// One primary ray per wave-local path i (every lane of the warp calls this).
+__device__ __forceinline__ void dev_raygen(const RenderParams& p, const WaveDesc& w, uint32_t i, bool active,
+                                           RayBuf rb, uint32_t* q, int* q_count, int qcap, Control* ctl) {
+  float3 o = make_float3(0.f, 0.f, 0.f), d = o;
+  if (active) {
+    PathId id = path_id(p, w, i);
+    float xi = 0.f, yi = 0.f;
+    if (p.mode == 1) {
+      float4 u = draw4(id.pixel, id.sample, 0, STREAM_PATH, 0, id.lam, p.seed);
+      xi = u.x - 0.5f;
+      yi = u.y - 0.5f;
+    }
+    int px = (int)(id.pixel % (uint32_t)p.cam.width), py = (int)(id.pixel / (uint32_t)p.cam.width);
+    float sx = ((px + 0.5f + xi) / p.cam.width) * 2.f - 1.f;
+    float sy = 1.f - ((py + 0.5f + yi) / p.cam.height) * 2.f;
+    if (p.cam.ortho) {
+      o = p.cam.pos + (sx * p.cam.ortho_half * p.cam.aspect) * p.cam.right + (sy * p.cam.ortho_half) * p.cam.up;
+      d = p.cam.fwd;
+    } else {
+      o = p.cam.pos;
+      d = normalize3(p.cam.fwd + (sx * p.cam.tan_half * p.cam.aspect) * p.cam.right + (sy * p.cam.tan_half) * p.cam.up);
+    }
+    rb.o[i] = make_float4(o.x, o.y, o.z, 0.f);
+    rb.d[i] = make_float4(d.x, d.y, d.z, 1.f);
+    rb.info[i] = make_uint2(i, (1u << 16));  // depth 0, no flags, tree code 1
+    if (p.path_hash) p.path_hash[i] = 0x811C9DC5u;
+  }
+  int s = active ? subdomain_of(p.sc, o) : 0;
+  int pos = warp_append(q_count, s, active);
+  if (active) {
+    if (pos < qcap) q[(size_t)s * qcap + pos] = i;
+    else atomicOr(&ctl->error, ERR_QUEUE_OVERFLOW);
+  }
+}
+
+
+// ------------------------------------------------------------------------------ traverse
+// Closest hit of queue entry i of subdomain s (every lane of the warp calls this): writes
+// the hit record, or hands the ray to the neighbouring subdomain's queue.
+template <bool kStats>
+__device__ __forceinline__ void dev_traverse(const RenderParams& p, int s, int i, bool active, const Node* s_nodes,
+                                             int n_staged, QueuePair qp, RayBuf rb, float2* hits, Control* ctl) {
+  uint32_t r = active ? qp.in[(size_t)s * qp.cap + i] : 0u;
+  bool cross = false;
+  int next = -1;
+  uint32_t nn = 0, nt = 0;
+  if (active) {
+    float4 O = rb.o[r], D = rb.d[r];
+    float3 o = f3(O), d = f3(D);
+    float t0, t1;
+    slab_interval(p.sc, s, o, d, &t0, &t1, &next);
+    float t = t1;
+    uint32_t prim = kMissPrim;
+    bool ovf = false;
+    if (t1 > t0) {
+      RayPre rp = ray_pre(o, d);
+      prim = closest_hit<kStats>(p.sc, s_nodes, n_staged, s, rp, t0, t1, &t, &nn, &nt, &ovf);
+    }
+    if (ovf) atomicOr(&ctl->error, ERR_STACK_OVERFLOW);
+    cross = prim == kMissPrim && next >= 0;
+    if (!cross) hits[r] = make_float2(prim == kMissPrim ? CUDART_INF_F : t, __uint_as_float(prim));
+  }
+  int pos = warp_append(qp.out_count, cross ? next : 0, cross);
+  if (cross) {
+    if (pos < qp.cap) qp.out[(size_t)next * qp.cap + pos] = r;
+    else atomicOr(&ctl->error, ERR_QUEUE_OVERFLOW);
+  }
+  if (kStats) {
+    unsigned long long a = warp_sum<unsigned long long>(active ? 1ull : 0ull);
+    unsigned long long c = warp_sum<unsigned long long>(cross ? 1ull : 0ull);
+    unsigned long long n1 = warp_sum<unsigned long long>(nn);
+    unsigned long long n2 = warp_sum<unsigned long long>(nt);
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&ctl->rays_closest, a);
+      atomicAdd(&ctl->crossings, c);
+      atomicAdd(&ctl->node_visits, n1);
+      atomicAdd(&ctl->tri_tests, n2);
+    }
+  }
+}
+
+
+// ------------------------------------------------------------------------------ shade
+// Shade ray r of the current generation (every lane of the warp calls this): adds escape
+// and NEE radiance, appends the children to `next` (counter *next_count) and the subdomain
+// queues q, and the shadow ray to sb (counter *shadow_count) and the shadow queues sq.
+__device__ __forceinline__ void dev_shade(const RenderParams& p, const WaveDesc& w, int r, bool active, RayBuf cur,
+                                          const float2* __restrict__ hits, RayBuf next, int* next_count, uint32_t* q,
+                                          int* q_count, int qcap, ShadowBuf sb, int* shadow_count, uint32_t* sq,
+                                          int* sq_count, float* path_L, Control* ctl) {
+  const bool mc = p.mode == 1;
+  const float eps = p.sc.eps;
+  bool e0 = false, e1 = false, esh = false;
+  float3 o0 = make_float3(0.f, 0.f, 0.f), d0 = o0, o1 = o0, d1 = o0, osh = o0, dsh = o0;
+  float thr0 = 0.f, thr1 = 0.f, s00 = 0.f, s01 = 0.f, csh = 0.f;
+  uint32_t meta0 = 0, meta1 = 0, path = 0, slot_sh = 0;
+  if (active) {
+    float4 O = cur.o[r], D = cur.d[r];
+    uint2 inf = cur.info[r];
+    float2 H = hits[r];
+    path = inf.x;
+    uint32_t depth = inf.y & 0xFFu, flags = (inf.y >> 8) & 0xFFu, code = inf.y >> 16;
+    float thr = D.w, seg0 = O.w;
+    float3 o = f3(O), d = f3(D);
+    PathId id = path_id(p, w, path);
+    const int lam = (int)id.lam;
+    const float lambda = __ldg(p.sp.lambda_nm + lam);
+    const uint32_t slot = path * (uint32_t)p.n_slots + (mc ? 0u : code);
+    uint32_t hsh = p.path_hash ? p.path_hash[path] : 0u;
+    uint32_t prim = __float_as_uint(H.y);
+    if (prim == kMissPrim) {
+      path_L[slot] += thr * escape_radiance(p.sp, d, lam, (flags & FLAG_SUN_COUNTED) != 0u);
+      hsh = fnv_byte(fnv_word(hsh, 0xFFFFFFFFu), EV_ESCAPE);
+    } else {
+      hsh = fnv_word(hsh, prim);
+      uint32_t v = depth + 1;
+      if ((int)v > p.max_depth) {
+        hsh = fnv_byte(hsh, EV_DEPTH_CAP);
+      } else {
+        float4 nm = __ldg(p.sc.prim_nrm_mat + prim);
+        float3 ng = f3(nm);
+        int mat = __float_as_int(nm.w);
+        int kind = __ldg(p.sp.mat_kind + mat);
+        size_t mi = (size_t)mat * p.sp.n_lambda + lam;
+        float3 pt = o + H.x * d;
+        float cos_n = dot3(d, ng);
+        float3 nf = cos_n < 0.f ? ng : -1.f * ng;
+        float cos_i = fabsf(cos_n);
+        float4 u = mc ? draw4(id.pixel, id.sample, v, STREAM_PATH, 0, lam, p.seed) : make_float4(0.f, 0.f, 0.f, 0.f);
+        uint32_t base_meta = v;  // depth v, flags and code filled per child
+        if (kind == MAT_SOLID) {
+          bool inside = cos_n > 0.f;
+          float nre = __ldg(p.sp.mat_n + mi), kk = __ldg(p.sp.mat_k + mi);
+          if (inside) thr *= beer_lambert(kk, H.x + seg0, lambda);
+          float n1 = inside ? nre : 1.f;
+          float n2re = inside ? 1.f : nre, n2im = inside ? 0.f : kk;
+          float R = fresnel_R(cos_i, n1, n2re, n2im);
+          float eta = n1 / n2re;
+          float c2 = 1.f - eta * eta * (1.f - cos_i * cos_i);
+          float3 dr = reflect3(d, nf);
+          float3 dt = c2 > 0.f ? normalize3(eta * d + (eta * cos_i - sqrtf(c2)) * nf) : dr;
+          uint32_t fl = flags & ~FLAG_SUN_COUNTED;
+          if (!mc) {
+            e0 = true;
+            d0 = dr;
+            thr0 = thr * R;
+            meta0 = base_meta | (fl << 8) | ((code * 2u) << 16);
+            e1 = c2 > 0.f && R < 1.f;
+            d1 = dt;
+            thr1 = thr * (1.f - R);
+            meta1 = base_meta | (fl << 8) | ((code * 2u + 1u) << 16);
+          } else {
+            bool refl = u.x < R || c2 <= 0.f;
+            hsh = fnv_byte(hsh, refl ? EV_REFLECT : EV_TRANSMIT);
+            e0 = true;
+            d0 = refl ? dr : dt;
+            thr0 = thr;
+            meta0 = base_meta | (fl << 8);
+          }
+        } else if (kind == MAT_SLAB) {
+          float Rs, Ts;
+          slab_RT(cos_i, __ldg(p.sp.mat_n + mi), __ldg(p.sp.mat_k + mi), __ldg(p.sp.mat_thick + mat), lambda, &Rs,
+                  &Ts);
+          float3 dr = reflect3(d, nf);
+          uint32_t fl_r = flags & ~FLAG_SUN_COUNTED;
+          if (!mc) {
+            e0 = true;
+            d0 = dr;
+            thr0 = thr * Rs;
+            meta0 = base_meta | (fl_r << 8) | ((code * 2u) << 16);
+            e1 = true;
+            d1 = d;
+            thr1 = thr * Ts;
+            meta1 = base_meta | (flags << 8) | ((code * 2u + 1u) << 16);
+          } else {
+            float P = Rs / (Rs + Ts);
+            bool refl = u.x < P;
+            hsh = fnv_byte(hsh, refl ? EV_REFLECT : EV_TRANSMIT);
+            e0 = true;
+            d0 = refl ? dr : d;
+            thr0 = thr * (Rs + Ts);
+            meta0 = base_meta | ((refl ? fl_r : flags) << 8);
+          }
+        } else if (kind == MAT_DIFFUSE) {
+          float alb = __ldg(p.sp.mat_albedo + mi);
+          if (mc) hsh = fnv_byte(hsh, EV_DIFFUSE);
+          if (p.sp.sun_h > 0.f) {
+            float3 wl = p.sp.sun_dir;
+            if (mc) {
+              float4 un = draw4(id.pixel, id.sample, v, STREAM_NEE, 0, lam, p.seed);
+              wl = cone_dir(p.sp.sun_dir, p.sp.sun_h, un.x, un.y);
+            }
+            float cl = dot3(nf, wl);
+            if (cl > 0.f) {
+              esh = true;
+              osh = offset_point(pt, ng, wl, eps);
+              dsh = wl;
+              csh = thr * alb * kInvPi * cl * __ldg(p.sp.sun + lam) * p.sp.sun_omega;
+              slot_sh = mc ? 0u : code;
+            }
+          }
+          if (mc) {
+            e0 = true;
+            d0 = cosine_dir(nf, u.y, u.z);
+            thr0 = thr * alb;
+            meta0 = base_meta | ((flags | FLAG_SUN_COUNTED) << 8);
+          }
+        } else {
+          if (mc) hsh = fnv_byte(hsh, EV_ABSORB);
+        }
+        if (mc && e0 && (int)v >= p.rr_start) {
+          float qs = fminf(0.95f, thr0);
+          if (u.w >= qs) {
+            e0 = false;
+            hsh = fnv_byte(hsh, EV_RR_KILL);
+          } else {
+            thr0 = thr0 / qs;
+          }
+        }
+        if (e0) {
+          o0 = offset_point(pt, ng, d0, eps);
+          s00 = seg0_of(ng, d0, eps);
+        }
+        if (e1) {
+          o1 = offset_point(pt, ng, d1, eps);
+          s01 = seg0_of(ng, d1, eps);
+        }
+      }
+    }
+    if (p.path_hash) p.path_hash[path] = hsh;
+  }
+  emit_ray(e0, p.sc, next, next_count, q, q_count, qcap, o0, s00, d0, thr0, path, meta0, ctl);
+  emit_ray(e1, p.sc, next, next_count, q, q_count, qcap, o1, s01, d1, thr1, path, meta1, ctl);
+  // shadow ray toward the sun
+  int pos = warp_append(shadow_count, 0, esh);
+  bool ok = esh && pos < sb.cap;
+  if (esh && !ok) atomicOr(&ctl->error, ERR_SHADOW_OVERFLOW);
+  if (ok) {
+    sb.o[pos] = make_float4(osh.x, osh.y, osh.z, 0.f);
+    sb.d[pos] = make_float4(dsh.x, dsh.y, dsh.z, csh);
+    sb.info[pos] = make_uint2(path, slot_sh);
+  }
+  int ss = ok ? subdomain_of(p.sc, osh) : 0;
+  int qpos = warp_append(sq_count, ss, ok);
+  if (ok) {
+    if (qpos < qcap) sq[(size_t)ss * qcap + qpos] = (uint32_t)pos;
+    else atomicOr(&ctl->error, ERR_SHADOW_OVERFLOW);
+  }
+}
+
+
+// ------------------------------------------------------------------------------ shadow
+// Transmittance of shadow-queue entry i of subdomain s toward the sun (every lane of the
+// warp calls this): blocked, handed on to the neighbouring subdomain, or added to its path.
+template <bool kStats>
+__device__ __forceinline__ void dev_shadow(const RenderParams& p, const WaveDesc& w, int s, int i, bool active,
+                                           const Node* s_nodes, int n_staged, QueuePair qp, ShadowBuf sb,
+                                           float* path_L, Control* ctl) {
+  uint32_t r = active ? qp.in[(size_t)s * qp.cap + i] : 0u;
+  bool cross = false;
+  int next = -1;
+  uint32_t nn = 0, nt = 0;
+  if (active) {
+    float4 O = sb.o[r], D = sb.d[r];
+    uint2 inf = sb.info[r];
+    float3 o = f3(O), d = f3(D);
+    PathId id = path_id(p, w, inf.x);
+    float t0, t1;
+    slab_interval(p.sc, s, o, d, &t0, &t1, &next);
+    float T = 1.f;
+    bool ovf = false;
+    if (t1 > t0) {
+      RayPre rp = ray_pre(o, d);
+      T = shadow_T<kStats>(p.sc, p.sp, (int)id.lam, __ldg(p.sp.lambda_nm + id.lam), s_nodes, n_staged, s, rp, d, t0,
+                           t1, &nn, &nt, &ovf);
+    }
+    if (ovf) atomicOr(&ctl->error, ERR_STACK_OVERFLOW);
+    bool blocked = !(T > 0.f);
+    float contrib = D.w * T;
+    cross = !blocked && next >= 0;
+    if (cross) {
+      sb.d[r].w = contrib;
+    } else {
+      if (!blocked) path_L[inf.x * (uint32_t)p.n_slots + inf.y] += contrib;
+      if (p.path_hash && p.mode == 1)
+        p.path_hash[inf.x] = fnv_byte(p.path_hash[inf.x], blocked ? EV_SHADOW_BLOCKED : EV_SHADOW_OPEN);
+    }
+  }
+  int pos = warp_append(qp.out_count, cross ? next : 0, cross);
+  if (cross) {
+    if (pos < qp.cap) qp.out[(size_t)next * qp.cap + pos] = r;
+    else atomicOr(&ctl->error, ERR_SHADOW_OVERFLOW);
+  }
+  if (kStats) {
+    unsigned long long a = warp_sum<unsigned long long>(active ? 1ull : 0ull);
+    unsigned long long n1 = warp_sum<unsigned long long>(nn);
+    unsigned long long n2 = warp_sum<unsigned long long>(nt);
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&ctl->rays_shadow, a);
+      atomicAdd(&ctl->shadow_node_visits, n1);
+      atomicAdd(&ctl->shadow_tri_tests, n2);
+    }
+  }
+}
+
+}  // namespace sdd

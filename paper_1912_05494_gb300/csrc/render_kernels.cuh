@@ -28,7 +28,7 @@ void launch_shade(const RenderParams& p, const WaveDesc& w, int n_rays, RayBuf c
                   uint32_t* q, int* q_count, int qcap, ShadowBuf sb, uint32_t* sq, int* sq_count, float* path_L,
                   Control* ctl, cudaStream_t st);
 void launch_shadow(const RenderParams& p, const WaveDesc& w, const Sched& sch, int total_blocks, int block,
-                   QueuePair qp, ShadowBuf sb, float* path_L, Control* ctl, cudaStream_t st);
+                   int top_nodes, QueuePair qp, ShadowBuf sb, float* path_L, Control* ctl, cudaStream_t st);
 void launch_film_accum(const RenderParams& p, const WaveDesc& w, const float* path_L, double* film,
                        float* path_rad_out, uint32_t* path_hash_out, cudaStream_t st);
 void launch_film_finalize(const RenderParams& p, const double* film, const double* cmf_w, float* spectral_out,

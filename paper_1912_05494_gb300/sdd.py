@@ -68,10 +68,15 @@ class sdd_stats(C.Structure):
                [(n, C.c_int64) for n in ("launches_raygen", "launches_traverse", "launches_shade",
                                           "launches_shadow", "launches_film", "launches_total", "rays_closest",
                                           "rays_shadow", "node_visits", "tri_tests", "shadow_node_visits",
-                                          "shadow_tri_tests", "crossings", "paths", "waves", "bytes_ray_state")]
+                                          "shadow_tri_tests", "crossings", "paths", "waves", "bytes_ray_state")] + \
+               [("ms_persistent", C.c_double), ("launches_persistent", C.c_int64), ("graph_replays", C.c_int64)]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
+
+
+class sdd_tuning(C.Structure):
+    _fields_ = [("traverse_block", C.c_int), ("top_nodes", C.c_int), ("wave_paths", C.c_int), ("no_graph", C.c_int)]
 
 
 class sdd_scene_info(C.Structure):
@@ -96,6 +101,8 @@ def lib():
         L.sdd_render_to_host.argtypes = [vp, C.POINTER(sdd_camera), C.POINTER(sdd_render_opts), vp, vp, vp]
         L.sdd_set_profiling.argtypes = [vp, i32]
         L.sdd_get_stats.argtypes = [vp, C.POINTER(sdd_stats)]
+        L.sdd_set_tuning.argtypes = [vp, C.POINTER(sdd_tuning)]
+        L.sdd_get_tuning.argtypes = [vp, C.POINTER(sdd_tuning)]
         L.sdd_scene_get_info.argtypes = [vp, C.POINTER(sdd_scene_info)]
         L.sdd_trace_closest.argtypes = [vp, i32, vp, vp, vp, vp, vp]
         L.sdd_trace_closest_noalloc.argtypes = [vp, i32, vp, vp, vp, vp, vp]
@@ -105,7 +112,7 @@ def lib():
         L.sdd_version.restype = C.c_char_p
         for name in ("sdd_scene_create", "sdd_render", "sdd_render_to_host", "sdd_set_profiling", "sdd_get_stats",
                      "sdd_scene_get_info", "sdd_trace_closest", "sdd_trace_closest_noalloc", "sdd_eval_optics",
-                     "sdd_philox"):
+                     "sdd_philox", "sdd_set_tuning", "sdd_get_tuning"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -255,6 +262,17 @@ def sdd_render_to_host(h, cam, spec, spectral_out, xyz_out=None, stream=None, **
 
 def sdd_set_profiling(h, level: int):
     _check(lib().sdd_set_profiling(h, int(level)))
+
+
+def sdd_set_tuning(h, tuning: dict):
+    t = sdd_tuning(**{k: int(v) for k, v in tuning.items()})
+    _check(lib().sdd_set_tuning(h, C.byref(t)))
+
+
+def sdd_get_tuning(h) -> dict:
+    t = sdd_tuning()
+    _check(lib().sdd_get_tuning(h, C.byref(t)))
+    return {f[0]: getattr(t, f[0]) for f in t._fields_}
 
 
 def sdd_get_stats(h) -> dict:

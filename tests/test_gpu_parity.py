@@ -2,8 +2,9 @@
 
 Tolerances:
   * deterministic configs: per-pixel relative error <= 1e-4;
-  * Monte Carlo configs on the same Philox streams: mean relative image error <= 1e-3 and
-    branch flips (paths whose event hash differs) <= 0.1 % of paths;
+  * Monte Carlo configs on the same Philox streams: mean relative image error
+    sum|a - b| / sum|b| over pixels and wavelengths <= 1e-3, and branch flips (paths whose
+    event hash differs) <= 0.1 % of paths;
   * single-interface optics: the FP32 evaluation of R, R_slab, T_slab to 2e-6 absolute
     (a few float ulps of quantities of order 1);
   * Philox: bit-exact.
@@ -29,9 +30,10 @@ def sdd():
 
 
 def mean_rel_image_error(a, b):
-    """Mean over pixels and wavelengths of |a - b| / (|b| + eps), eps = 1e-3 mean|b|."""
-    eps = 1e-3 * np.abs(b).mean()
-    return float(np.mean(np.abs(a - b) / (np.abs(b) + eps)))
+    """Mean absolute error over pixels and wavelengths relative to the mean absolute
+    reference: sum|a - b| / sum|b|.  (A per-cell ratio is meaningless here: at 16 spp most
+    cells of the dim interior are exactly zero, and one flipped path there scores ~1e3.)"""
+    return float(np.abs(a - b).sum() / np.abs(b).sum())
 
 
 def render_gpu(sdd, h, cam, spec, pixels=None, paths=False, **kw):
@@ -167,6 +169,8 @@ def mc_compare(sdd, orc, sc, cam, spec, pixels, n_sub=None, **kw):
     ref, rp, rh = orc.OracleScene(sc).render(cam, spec, pixels=pixels, want_paths=True)
     flips = float(np.mean(gh != rh))
     err = mean_rel_image_error(gpu, ref)
+    changed = float(np.mean(np.abs(gp - rp) > 1e-6 * np.abs(rp) + 1e-12))  # radiance-changing flips
+    assert changed <= flips + 1e-12 or changed <= 1e-4
     same = gh == rh
     path_rel = np.abs(gp[same] - rp[same]) / (np.abs(rp[same]) + 1e-6 * np.abs(rp).mean() + 1e-30)
     return flips, err, path_rel, gpu, ref
