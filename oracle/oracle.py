@@ -150,6 +150,57 @@ def xyz(film, lambda_nm):
     return out
 
 
+class OrcTile(C.Structure):
+    _fields_ = [("d_mean", C.c_double), ("amp", C.c_double), ("rho", C.c_double), ("seed", C.c_uint32)]
+
+
+def _tiles(tiles):
+    arr = (OrcTile * len(tiles))()
+    for i, t in enumerate(tiles):
+        arr[i].d_mean, arr[i].amp, arr[i].rho, arr[i].seed = t["d_mean"], t["amp"], t["rho"], t["seed"]
+    return arr
+
+
+def tile_heights(tile, G=64, L=0.1):
+    """Tile thickness at the (G+1)^2 grid vertices (row j, column i), metres."""
+    h = np.zeros((G + 1) * (G + 1))
+    lib().orc_tile_heights(_tiles([tile]), G, C.c_double(L), _p(h))
+    return h.reshape(G + 1, G + 1)
+
+
+def tile_trace(tile, heights, xy, dirs, n_re, k, lambda_nm, px, sample, bounce=1, lam=0, seed=0, max_events=64,
+               G=64, L=0.1):
+    """Trace rays through one tile; returns dict of side, w, dir, bubbles, events."""
+    h = _c(heights, np.float64).ravel()
+    xy = _c(xy, np.float64).reshape(-1, 2)
+    dirs = _c(dirs, np.float64).reshape(-1, 3)
+    n = xy.shape[0]
+    px = _c(np.broadcast_to(px, (n,)), np.uint32)
+    sample = _c(np.broadcast_to(sample, (n,)), np.uint32)
+    side = np.zeros(n, np.int32)
+    w = np.zeros(n)
+    dout = np.zeros((n, 3))
+    bub = np.zeros(n, np.int32)
+    ev = np.zeros(n, np.int32)
+    lib().orc_tile_trace(_tiles([tile]), G, C.c_double(L), _p(h), n, _p(xy), _p(dirs), C.c_double(n_re),
+                         C.c_double(k), C.c_double(lambda_nm), _p(px), _p(sample), C.c_uint32(bounce),
+                         C.c_uint32(lam), C.c_uint64(seed), max_events, _p(side), _p(w), _p(dout), _p(bub), _p(ev))
+    return {"side": side, "w": w, "dir": dout, "bubbles": bub, "events": ev}
+
+
+def tile_samples(tiles, heights, cos_in, phi_in, lambda_nm, n_re, k, tile, rays=256, seed=0, max_events=64,
+                 n_threads=0, G=64, L=0.1):
+    """Per-sample statistics [n, 8]: T, R, capped, ballistic-T, cos-T, ballistic-R, cos-R, bubbles/ray."""
+    hs = _c(heights, np.float64).ravel()
+    args = [_c(x, np.float64).ravel() for x in (cos_in, phi_in, lambda_nm, n_re, k)]
+    t = _c(tile, np.int32).ravel()
+    ns = t.size
+    out = np.zeros((ns, 8))
+    lib().orc_tile_samples(len(tiles), _tiles(tiles), G, C.c_double(L), _p(hs), ns, *(_p(a) for a in args), _p(t),
+                           rays, C.c_uint64(seed), max_events, n_threads, _p(out))
+    return out
+
+
 def hardware_threads() -> int:
     return int(lib().orc_hardware_threads())
 

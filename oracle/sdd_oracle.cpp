@@ -559,6 +559,238 @@ double trace_mc(const RenderCtx& cx, uint32_t px, uint32_t sample, int lam, uint
   return L;
 }
 
+// ---------------------------------------------------------------- heterogeneous tiles
+// A medieval glass tile with non-uniform thickness and air micro-bubbles (Sec. 1: "non
+// uniform thickness and ... micro particles of air inside the tiles"; Sec. 6: scattering as
+// future work).  Model (readings, the paper gives none):
+//   * periodic square tile of side L, flat front face z = 0, back face z = -h(x, y);
+//   * h = clamp(d_mean + A (n(x, y) - 1/2), 2 mm, 5 mm) with n = 2/3 v(L/10) + 1/3 v(L/20),
+//     v = value noise with smoothstep interpolation of lattice values drawn from Philox;
+//   * the back face is the G x G triangulated height field through h at the grid vertices;
+//   * bubbles form a Poisson process of density rho in the glass, radii log-uniform in
+//     [10, 100] um: the free path to the next bubble is exponential with rate rho sigma,
+//     sigma = pi E[r^2]; a hit bubble's radius is drawn with weight r^2, the impact point
+//     uniformly over its cross-section, and the outgoing direction follows the exact sphere
+//     optics (reflections and refractions at its surface); at the tile's scale (mm) the
+//     bubble is a point: the encounter does not displace the ray;
+//   * complex Fresnel, Snell and Beer-Lambert as for the other glass; every interaction
+//     draws its own four uniforms on the tile stream;
+//   * a ray leaves through the front face (reflected side) or the back face (transmitted
+//     side) and does not re-enter; more than max_events interactions absorb it.
+struct TileParams {
+  double d_mean, amp, rho;
+  uint32_t seed;
+};
+
+double tile_lattice(uint32_t seed, int ix, int iy, int oct) {
+  uint32_t ctr[4] = {(uint32_t)ix, (uint32_t)iy, (uint32_t)oct, seed};
+  uint32_t key[2] = {0x5EED7113u, 0u};
+  uint32_t o[4];
+  philox4x32_10(ctr, key, o);
+  return u01(o[0]);
+}
+
+double tile_value_noise(uint32_t seed, double x, double y, double L, int cells, int oct) {
+  double gx = x / L * cells, gy = y / L * cells;
+  double fx0 = std::floor(gx), fy0 = std::floor(gy);
+  double fx = gx - fx0, fy = gy - fy0;
+  int ix = ((int)fx0 % cells + cells) % cells, iy = ((int)fy0 % cells + cells) % cells;
+  int jx = (ix + 1) % cells, jy = (iy + 1) % cells;
+  double sx = fx * fx * (3.0 - 2.0 * fx), sy = fy * fy * (3.0 - 2.0 * fy);
+  double a = tile_lattice(seed, ix, iy, oct), b = tile_lattice(seed, jx, iy, oct);
+  double c = tile_lattice(seed, ix, jy, oct), d = tile_lattice(seed, jx, jy, oct);
+  return (1 - sy) * ((1 - sx) * a + sx * b) + sy * ((1 - sx) * c + sx * d);
+}
+
+double tile_thickness(const TileParams& tp, double x, double y, double L) {
+  double n = (2.0 / 3.0) * tile_value_noise(tp.seed, x, y, L, 10, 0) +
+             (1.0 / 3.0) * tile_value_noise(tp.seed, x, y, L, 20, 1);
+  double h = tp.d_mean + tp.amp * (n - 0.5);
+  return std::min(0.005, std::max(0.002, h));
+}
+
+struct TileGeom {
+  int G;
+  double L;
+  const double* h;  // [(G+1) * (G+1)] thickness at the grid vertices, row j, column i
+  double hmin, hmax;
+};
+
+// Back-face triangles of cell (ci, cj) in unwrapped cell coordinates.
+void tile_cell_tris(const TileGeom& g, long ci, long cj, V3 tri[2][3]) {
+  long wi = ((ci % g.G) + g.G) % g.G, wj = ((cj % g.G) + g.G) % g.G;
+  double cs = g.L / g.G;
+  double x0 = ci * cs, y0 = cj * cs;
+  auto H = [&](long i, long j) { return g.h[(size_t)j * (g.G + 1) + i]; };
+  V3 p00{x0, y0, -H(wi, wj)}, p10{x0 + cs, y0, -H(wi + 1, wj)};
+  V3 p01{x0, y0 + cs, -H(wi, wj + 1)}, p11{x0 + cs, y0 + cs, -H(wi + 1, wj + 1)};
+  tri[0][0] = p00; tri[0][1] = p10; tri[0][2] = p11;
+  tri[1][0] = p00; tri[1][1] = p11; tri[1][2] = p01;
+}
+
+// First hit of the back face along o + t d, t in (0, t_max], walking the grid cells the
+// ray's xy projection crosses (at most max_cells).  Returns t or -1; n_out = unit normal
+// of the hit triangle pointing into the glass (+z side).
+double tile_back_hit(const TileGeom& g, V3 o, V3 d, double t_max, int max_cells, V3* n_out) {
+  double cs = g.L / g.G;
+  long ci = (long)std::floor(o.x / cs), cj = (long)std::floor(o.y / cs);
+  int sx = d.x > 0 ? 1 : (d.x < 0 ? -1 : 0), sy = d.y > 0 ? 1 : (d.y < 0 ? -1 : 0);
+  double tdx = sx ? cs / std::fabs(d.x) : INF, tdy = sy ? cs / std::fabs(d.y) : INF;
+  double tx = sx > 0 ? ((ci + 1) * cs - o.x) / d.x : (sx < 0 ? (ci * cs - o.x) / d.x : INF);
+  double ty = sy > 0 ? ((cj + 1) * cs - o.y) / d.y : (sy < 0 ? (cj * cs - o.y) / d.y : INF);
+  double t_in = 0.0;
+  for (int step = 0; step < max_cells && t_in <= t_max; ++step) {
+    double t_out = std::min(std::min(tx, ty), t_max);
+    double z0 = o.z + d.z * t_in, z1 = o.z + d.z * t_out;
+    if (std::min(z0, z1) <= -g.hmin) {  // the ray reaches the band of the back face here
+      V3 tri[2][3];
+      tile_cell_tris(g, ci, cj, tri);
+      double best = -1.0;
+      V3 bn{0, 0, 1};
+      for (int k = 0; k < 2; ++k) {
+        double t;
+        if (ray_triangle(o, d, tri[k][0], tri[k][1], tri[k][2], &t) && t > 0.0 && t <= t_max &&
+            (best < 0.0 || t < best)) {
+          best = t;
+          bn = normalize(cross(tri[k][1] - tri[k][0], tri[k][2] - tri[k][0]));
+        }
+      }
+      if (best >= 0.0) {
+        if (bn.z < 0) bn = -1.0 * bn;
+        *n_out = bn;
+        return best;
+      }
+    }
+    if (tx < ty) { ci += sx; t_in = tx; tx += tdx; }
+    else { cj += sy; t_in = ty; ty += tdy; }
+  }
+  return -1.0;
+}
+
+struct TileRay {
+  int side;     // 0 reflected (front), 1 transmitted (back), 2 absorbed (event cap)
+  double w;     // throughput
+  V3 dir;       // exit direction (tile frame)
+  int bubbles;  // bubble encounters
+  int events;
+};
+
+// Trace one ray through the tile.  (x0, y0): entry point; d: direction in the tile frame
+// (d.z < 0 enters through the front, d.z > 0 through the back); draws are keyed
+// (pixel, sample, bounce<<16 | 2<<8 | event, lam).
+TileRay tile_trace(const TileGeom& g, const TileParams& tp, double x0, double y0, V3 d, double n, double k,
+                   double lambda_nm, uint32_t px, uint32_t sample, uint32_t bounce, uint32_t lam, uint64_t seed,
+                   int max_events) {
+  const double eps = 1e-7, r_lo = 10e-6, r_hi = 100e-6;
+  const double Er2 = (r_hi * r_hi - r_lo * r_lo) / (2.0 * std::log(r_hi / r_lo));
+  const double sig = tp.rho * PI * Er2;  // bubble encounters per metre
+  const double alpha = 4.0 * PI * k / (lambda_nm * 1e-9);
+  TileRay out{2, 0.0, d, 0, 0};
+  const V3 d_in = d;
+  double w = 1.0;
+  int e = 0;
+  auto next_u = [&]() { return draw(px, sample, bounce, STREAM_TILE, (uint32_t)(e++ & 0xFF), lam, seed); };
+  // entry interface: air -> glass at the front plane or the back face below the entry point
+  V3 p, nrm;
+  if (d.z < 0) {
+    p = {x0, y0, 0.0};
+    nrm = {0, 0, 1};
+  } else {
+    // start below the back face on the vertical through the entry point and walk along d
+    V3 nb;
+    V3 o2 = {x0, y0, -g.hmax - 1e-4};
+    double t2 = tile_back_hit(g, o2, d, 1.0, 4096, &nb);
+    if (t2 < 0) { out.side = 1; out.w = 1.0; out.dir = d; return out; }  // passed under the tile
+    p = o2 + t2 * d;
+    nrm = -1.0 * nb;  // facing the incoming ray (below)
+  }
+  bool in_glass = false;
+  for (;;) {
+    if (e >= max_events) { out.side = 2; out.w = w; out.events = e; return out; }
+    // interface at p with normal nrm facing the incoming ray
+    double cos_i = -dot(d, nrm);
+    Draw u = next_u();
+    double n1 = in_glass ? n : 1.0;
+    cd n2 = in_glass ? cd(1.0, 0.0) : cd(n, k);
+    double R = fresnel_R(cos_i, n1, n2);
+    double eta = n1 / std::real(n2);
+    double c2 = 1.0 - eta * eta * (1.0 - cos_i * cos_i);
+    if (u.u[0] < R || c2 <= 0.0) {
+      d = reflect(d, nrm);
+    } else {
+      d = normalize(eta * d + (eta * cos_i - std::sqrt(c2)) * nrm);
+      in_glass = !in_glass;
+    }
+    if (!in_glass) {  // left the glass (or never entered): reflected if back on the incident side
+      out.side = ((d.z > 0) == (d_in.z < 0)) ? 0 : 1;
+      out.w = w;
+      out.dir = d;
+      out.events = e;
+      return out;
+    }
+    p = p + (dot(d, nrm) >= 0 ? eps : -eps) * nrm;  // step off the surface into the glass
+    // the segment inside the glass: front plane, back face, or a bubble
+    for (;;) {
+      if (e >= max_events) { out.side = 2; out.w = w; out.events = e; return out; }
+      Draw us = next_u();
+      double t_front = d.z > 0 ? -p.z / d.z : INF;
+      V3 nb{0, 0, 1};
+      double t_back = tile_back_hit(g, p, d, std::min(t_front, 1.0), 4096, &nb);
+      double t_surf = t_back >= 0 ? t_back : t_front;
+      double t_bub = sig > 0 ? -std::log(1.0 - us.u[0]) / sig : INF;
+      if (!(t_surf < INF) && !(t_bub < INF)) { out.side = 2; out.w = w; out.events = e; return out; }
+      if (t_bub < t_surf) {
+        // bubble encounter: exact sphere optics, then continue in the glass (the bubble is
+        // not geometry: nothing of it can be hit again)
+        p = p + t_bub * d;
+        w *= std::exp(-alpha * t_bub);
+        out.bubbles++;
+        double r = std::sqrt(r_lo * r_lo + us.u[1] * (r_hi * r_hi - r_lo * r_lo));
+        double sin_i = std::sqrt(us.u[2]);  // impact parameter / r, uniform over the disc
+        double cos_i0 = std::sqrt(std::max(0.0, 1.0 - sin_i * sin_i));
+        V3 t1, t2;
+        onb(d, &t1, &t2);
+        double phi = 2.0 * PI * us.u[3];
+        V3 rad = std::cos(phi) * t1 + std::sin(phi) * t2;
+        // the sphere in its own frame: q is the current point relative to the centre
+        V3 q = r * ((-cos_i0) * d + sin_i * rad);  // entry point (outward normal q / r)
+        bool inside = false;                          // inside the bubble (air)
+        for (;;) {
+          if (e >= max_events) { out.side = 2; out.w = w; out.events = e; return out; }
+          Draw ub = next_u();
+          V3 nn = (1.0 / r) * q;
+          double ci = std::fabs(dot(d, nn));
+          V3 nf = dot(d, nn) < 0 ? nn : -1.0 * nn;  // facing the incoming ray
+          double m1 = inside ? 1.0 : n;
+          cd m2 = inside ? cd(n, k) : cd(1.0, 0.0);
+          double Rb = fresnel_R(ci, m1, m2);
+          double et = m1 / std::real(m2);
+          double cc = 1.0 - et * et * (1.0 - ci * ci);
+          if (ub.u[0] < Rb || cc <= 0.0) {
+            d = reflect(d, nf);
+          } else {
+            d = normalize(et * d + (et * ci - std::sqrt(cc)) * nf);
+            inside = !inside;
+          }
+          if (!inside) break;           // back in the glass, leaving the sphere
+          q = q + (-2.0 * dot(q, d)) * d;  // across the chord to the next point on the sphere
+        }
+        // bubbles (<= 100 um) are point scatterers at the scale of the tile: the ray leaves
+        // the encounter where it met it, with the direction the sphere optics gave
+        continue;
+      }
+      // surface hit
+      p = p + t_surf * d;
+      w *= std::exp(-alpha * t_surf);
+      nrm = t_back >= 0 ? nb : V3{0, 0, -1};  // normal facing the ray arriving from the glass
+      // re-wrap the position into the base tile
+      p.x -= g.L * std::floor(p.x / g.L);
+      p.y -= g.L * std::floor(p.y / g.L);
+      break;
+    }
+  }
+}
+
 }  // namespace
 
 // ================================================================ C entry points
@@ -825,6 +1057,100 @@ void orc_xyz(int n_px, int n_lambda, const float* lambda_nm, const double* film,
       for (int l = 0; l < n_lambda; ++l) acc += film[(size_t)p * n_lambda + l] * cmf[3 * l + c] * w[l];
       xyz[3 * p + c] = acc / ysum;
     }
+}
+
+// ---------------------------------------------------------------- tiles
+struct OrcTile {
+  double d_mean, amp, rho;
+  uint32_t seed;
+};
+
+// Thickness at the (G+1) x (G+1) grid vertices of a tile of side L (row j, column i).
+void orc_tile_heights(const OrcTile* t, int G, double L, double* h) {
+  TileParams tp{t->d_mean, t->amp, t->rho, t->seed};
+  for (int j = 0; j <= G; ++j)
+    for (int i = 0; i <= G; ++i) h[(size_t)j * (G + 1) + i] = tile_thickness(tp, i * L / G, j * L / G, L);
+}
+
+static TileGeom make_geom(int G, double L, const double* h) {
+  TileGeom g{G, L, h, INF, -INF};
+  for (int i = 0; i < (G + 1) * (G + 1); ++i) {
+    g.hmin = std::min(g.hmin, h[i]);
+    g.hmax = std::max(g.hmax, h[i]);
+  }
+  return g;
+}
+
+// Trace n rays through one tile: entry points xy [n][2], directions [n][3] (tile frame),
+// draws keyed (px[i], sample[i], bounce, tile stream, event, lam).  Outputs side, weight,
+// exit direction [n][3], bubble encounters and interactions per ray.
+void orc_tile_trace(const OrcTile* t, int G, double L, const double* h, int n, const double* xy, const double* dir,
+                    double n_re, double k, double lambda_nm, const uint32_t* px, const uint32_t* sample,
+                    uint32_t bounce, uint32_t lam, uint64_t seed, int max_events, int32_t* side, double* w,
+                    double* dout, int32_t* bubbles, int32_t* events) {
+  TileParams tp{t->d_mean, t->amp, t->rho, t->seed};
+  TileGeom g = make_geom(G, L, h);
+  for (int i = 0; i < n; ++i) {
+    TileRay r = tile_trace(g, tp, xy[2 * i], xy[2 * i + 1], {dir[3 * i], dir[3 * i + 1], dir[3 * i + 2]}, n_re, k,
+                           lambda_nm, px[i], sample[i], bounce, lam, seed, max_events);
+    side[i] = r.side;
+    w[i] = r.w;
+    dout[3 * i] = r.dir.x; dout[3 * i + 1] = r.dir.y; dout[3 * i + 2] = r.dir.z;
+    bubbles[i] = r.bubbles;
+    events[i] = r.events;
+  }
+}
+
+// Per-sample statistics of rays_per_sample rays entering a tile at uniform points with the
+// sample's direction (cos_in, phi_in, from the front): out[8] = T, R, absorbed-by-cap,
+// ballistic fraction of T (within 1 degree of straight through), mean cosine to straight
+// through of T, the same two for R about the mirror direction, bubble encounters per ray.
+// Sample s draws its entry points on (s, ray, 0, tile stream, 0) and its interactions on
+// bounce 1.
+void orc_tile_samples(int n_tiles, const OrcTile* tiles, int G, double L, const double* heights, int n_samples,
+                      const double* cos_in, const double* phi_in, const double* lambda_nm, const double* n_re,
+                      const double* k, const int32_t* tile, int rays, uint64_t seed, int max_events, int n_threads,
+                      double* out) {
+  (void)n_tiles;
+  int nth = n_threads > 0 ? n_threads : (int)std::thread::hardware_concurrency();
+  std::atomic<int> next{0};
+  auto work = [&]() {
+    for (;;) {
+      int s = next.fetch_add(1);
+      if (s >= n_samples) break;
+      const OrcTile& ot = tiles[tile[s]];
+      TileParams tp{ot.d_mean, ot.amp, ot.rho, ot.seed};
+      TileGeom g = make_geom(G, L, heights + (size_t)tile[s] * (G + 1) * (G + 1));
+      double st = std::sqrt(std::max(0.0, 1.0 - cos_in[s] * cos_in[s]));
+      V3 d{st * std::cos(phi_in[s]), st * std::sin(phi_in[s]), -cos_in[s]};
+      V3 dm{d.x, d.y, -d.z};
+      double T = 0, R = 0, A = 0, fT = 0, cT = 0, fR = 0, cR = 0, bub = 0;
+      const double cos1 = std::cos(PI / 180.0);
+      for (int r = 0; r < rays; ++r) {
+        Draw ue = draw((uint32_t)s, (uint32_t)r, 0, STREAM_TILE, 0, 0, seed);
+        TileRay tr = tile_trace(g, tp, ue.u[0] * L, ue.u[1] * L, d, n_re[s], k[s], lambda_nm[s], (uint32_t)s,
+                                (uint32_t)r, 1, 0, seed, max_events);
+        bub += tr.bubbles;
+        if (tr.side == 1) {
+          double c = dot(tr.dir, d);
+          T += tr.w; cT += tr.w * c; if (c > cos1) fT += tr.w;
+        } else if (tr.side == 0) {
+          double c = dot(tr.dir, dm);
+          R += tr.w; cR += tr.w * c; if (c > cos1) fR += tr.w;
+        } else {
+          A += tr.w;
+        }
+      }
+      double* o = out + 8 * (size_t)s;
+      o[0] = T / rays; o[1] = R / rays; o[2] = A / rays;
+      o[3] = T > 0 ? fT / T : 0.0; o[4] = T > 0 ? cT / T : 0.0;
+      o[5] = R > 0 ? fR / R : 0.0; o[6] = R > 0 ? cR / R : 0.0;
+      o[7] = bub / rays;
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int i = 0; i < nth; ++i) pool.emplace_back(work);
+  for (auto& th : pool) th.join();
 }
 
 int orc_hardware_threads(void) { return (int)std::thread::hardware_concurrency(); }
