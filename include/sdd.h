@@ -211,6 +211,84 @@ sdd_status sdd_scene_get_info(const sdd_scene* scene, sdd_scene_info* out);
 sdd_status sdd_trace_closest(sdd_scene* scene, int n, const float* org_dev, const float* dir_dev,
                              float* t_out_dev, int32_t* prim_out_dev, void* cuda_stream);
 
+/* ---------------------------------------------------------------- heterogeneous tiles
+ * Medieval glass tiles with non-uniform thickness and air micro-bubbles (Sec. 1; Sec. 6
+ * names light scattering as the missing part of the glass model).  A tile is periodic with
+ * side tile_size_m: flat front face z = 0, back face z = -h(x, y) a grid x grid triangulated
+ * height field of h = clamp(d_mean + amplitude (n(x, y) - 1/2), 2 mm, 5 mm), n a 2-octave
+ * value noise whose lattice values are Philox draws keyed by the tile's seed; air bubbles
+ * are a Poisson process of the given density with radii log-uniform in [10, 100] um, met at
+ * exponential free paths and scattered with exact sphere optics (no displacement); Fresnel
+ * (complex index), Snell and Beer-Lambert as for other glass.  Rays are traced by brute
+ * force, one Philox draw per interaction on the tile stream. */
+typedef struct sdd_tileset sdd_tileset;
+typedef struct {
+  int n_tiles;
+  const float* d_mean_m;          /* [n_tiles] mean thickness (host) */
+  const float* amplitude_m;       /* [n_tiles] peak-to-peak thickness variation */
+  const float* bubble_density_m3; /* [n_tiles] bubbles per cubic metre (1e10 = 1e4 per cm^3) */
+  const uint32_t* seed;           /* [n_tiles] noise seed */
+  int grid;                       /* back-face cells per side (64) */
+  float tile_size_m;              /* side of the periodic tile (0.1) */
+} sdd_tileset_desc;
+
+/* Build the tile set: height fields are computed on the device.  Allocates device memory. */
+sdd_status sdd_tileset_create(const sdd_tileset_desc* desc, sdd_tileset** out);
+void sdd_tileset_destroy(sdd_tileset* tiles);
+/* Copy tile `tile`'s (grid+1)^2 vertex thicknesses (row j, column i) to host memory. */
+sdd_status sdd_tileset_heights(const sdd_tileset* tiles, int tile, float* out_host);
+
+/* Trace n rays through tile `tile` (all arrays device): entry points xy [n][2] in [0, L),
+ * directions [n][3] in the tile frame (z < 0 enters through the front), draws keyed
+ * (px[i], sample[i], bounce, tile stream, interaction, lam).  Outputs: side (0 reflected,
+ * 1 transmitted, 2 absorbed after max_events interactions, max_events <= 256), weight,
+ * exit direction [n][3], bubble encounters and interactions. */
+sdd_status sdd_tile_trace_rays(sdd_tileset* tiles, int tile, int n, const float* xy, const float* dir, float n_re,
+                               float k, float lambda_nm, const uint32_t* px, const uint32_t* sample, uint32_t bounce,
+                               uint32_t lam, uint64_t seed, int max_events, int32_t* side, float* w, float* dir_out,
+                               int32_t* bubbles, int32_t* events, void* cuda_stream);
+
+/* Surrogate training data: for each of n_samples queries (device arrays: cosine of the
+ * incidence angle, azimuth, wavelength, n, k, tile index) trace rays_per_sample rays from
+ * uniform entry points through the front face; out[n][8] (device) = transmittance,
+ * reflectance, fraction absorbed at the interaction cap, ballistic fraction of the
+ * transmitted weight (within 1 degree of straight through), its weighted mean cosine to
+ * straight through, the same two for the reflected weight about the mirror direction, and
+ * bubble encounters per ray.  Sample s draws its entry points on (s, ray, 0, tile stream, 0)
+ * and its interactions on bounce 1. */
+sdd_status sdd_tile_generate(sdd_tileset* tiles, int n_samples, const float* cos_in, const float* phi_in,
+                             const float* lambda_nm, const float* n_re, const float* k, const int32_t* tile,
+                             int rays_per_sample, uint64_t seed, int max_events, float* out, void* cuda_stream);
+
+/* ---------------------------------------------------------------- BTDF surrogate
+ * A small network that predicts a heterogeneous tile's BTDF statistics from (cos theta_in,
+ * phi_in, lambda nm, mean thickness m, bubble density m^-3, n, k) -- the raw inputs, [n][7]
+ * row-major: T, R, ballistic fraction and mean cosine (to straight through) of T, the same
+ * two of R (the outputs of sdd_tile_generate, columns 0, 1, 3, 4, 5, 6).  Fourier features
+ * (16 frequencies of the inputs normalised to [0, 1]) -> 48 -> 4 x 128 GELU -> 16; BF16
+ * weights and activations, FP32 accumulation on the tensor cores, Adam on FP32 master
+ * weights.  Parameters: one FP32 array, per layer W [in][out] row-major then b [out]
+ * (sdd_surrogate_param_count() values).  The paper has no network; it names scattering in
+ * the glass as future work (Sec. 6). */
+typedef struct sdd_surrogate sdd_surrogate;
+int sdd_surrogate_param_count(void);
+/* fourier_B: host [16][7]; init_params: host flat parameters; max_batch rows per call. */
+sdd_status sdd_surrogate_create(const float* fourier_B, const float* init_params, int n_params, int max_batch,
+                                sdd_surrogate** out);
+void sdd_surrogate_destroy(sdd_surrogate* s);
+sdd_status sdd_surrogate_get_params(const sdd_surrogate* s, float* host_out, int n_params);
+sdd_status sdd_surrogate_set_params(sdd_surrogate* s, const float* host_in, int n_params);
+/* Loss (mean over rows of the summed squared error of the six sigmoid outputs) and its
+ * gradient for n <= max_batch rows (raw inputs and targets [n][6] on the device), without
+ * updating the weights; grad_host may be NULL. */
+sdd_status sdd_surrogate_gradients(sdd_surrogate* s, int n, const float* raw_dev, const float* y_dev, float* grad_host,
+                                   float* loss_host, void* cuda_stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, learning rate lr) on a batch of n rows. */
+sdd_status sdd_surrogate_train_step(sdd_surrogate* s, int n, const float* raw_dev, const float* y_dev, float lr,
+                                    float* loss_host, void* cuda_stream);
+/* Predictions [n][6] (device) for n rows of raw inputs (any n; processed max_batch at a time). */
+sdd_status sdd_surrogate_infer(sdd_surrogate* s, int n, const float* raw_dev, float* out_dev, void* cuda_stream);
+
 /* sdd_trace_closest without any allocation (the paper has no counterpart; this serves
  * callers).  Same arguments, results and queue passes as sdd_trace_closest, but its scratch
  * (ray state, hit records, subdomain queues, counters) lives in one static 16 MiB device

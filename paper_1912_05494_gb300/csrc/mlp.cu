@@ -1,0 +1,537 @@
+// mlp.cu -- the tile-BTDF surrogate network on BF16 tensor cores: training (forward,
+// backward, Adam) and inference.
+//
+// The paper models glass as refractive only and names scattering in heterogeneous tiles as
+// future work (Sec. 6).  The brute-force tile tracer (tile.cu) resolves it exactly but is
+// costly at every tile hit; this network learns the tile's BTDF statistics from the
+// tracer's samples:
+//   inputs   cos(theta_in), phi_in, lambda, mean thickness, bubble density, n, k, normalised
+//            to [0, 1]: cos, phi / 2 pi, (lambda - 380) / 400, (d - 2 mm) / 3 mm,
+//            rho / 2e10 m^-3, (n - 1.45) / 0.2, (log10 k + 8) / 4
+//   features [sin(2 pi B x), cos(2 pi B x), x, 0 pad] (B: 16 x 7), 48 wide
+//   layers   48 -> 128 -> 128 -> 128 -> 128 -> 16, exact GELU after the hidden layers
+//   outputs  sigmoid of outputs 0..5: T, R, ballistic fraction and mean cosine of T, the
+//            same two of R
+//   loss     mean over the batch of sum_j (p_j - y_j)^2; Adam on FP32 master weights
+// Weights and activations are BF16, products accumulate in FP32 (mma.sync m16n8k16,
+// fragments loaded with ldmatrix from padded shared-memory tiles).  Parameters are one flat
+// FP32 array: for each layer W [in][out] row-major, then b [out].
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "../../include/sdd.h"
+
+namespace sdd {
+sdd_status set_last_error(sdd_status st, const char* msg);
+}
+using namespace sdd;
+
+namespace {
+
+constexpr int kFeat = 48, kHid = 128, kOut = 16, kTargets = 6, kLayers = 5;
+__host__ __device__ constexpr int layer_in(int l) { return l == 0 ? kFeat : kHid; }
+__host__ __device__ constexpr int layer_out(int l) { return l == kLayers - 1 ? kOut : kHid; }
+constexpr int kRows = 128;    // batch rows per block
+constexpr int kThreads = 256;  // 8 warps, 16 rows each
+
+__host__ __device__ constexpr int layer_offset(int l) {
+  int o = 0;
+  for (int i = 0; i < l; ++i) o += layer_in(i) * layer_out(i) + layer_out(i);
+  return o;
+}
+constexpr int kParams = layer_offset(kLayers);
+
+// ------------------------------------------------------------------ warp MMA helpers
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void ldmatrix_x4(uint32_t r[4], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_addr(p)));
+}
+__device__ __forceinline__ void ldmatrix_x2(uint32_t r[2], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r[0]), "=r"(r[1]) : "r"(smem_addr(p)));
+}
+__device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], const uint32_t b[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// acc[j] (j = n-tile of 8 columns) += A[16 rows of the warp][0..Kd) * Bt[cols][0..Kd)^T, with
+// A at sa (row stride lda elements) and Bt at sb (row stride ldb elements), both shared memory.
+template <int Kd, int NT>
+__device__ __forceinline__ void warp_gemm(float (*acc)[4], const __nv_bfloat16* sa, int lda, const __nv_bfloat16* sb,
+                                          int ldb) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int kk = 0; kk < Kd; kk += 16) {
+    uint32_t a[4];
+    ldmatrix_x4(a, sa + (lane & 15) * lda + kk + (lane >> 4) * 8);
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      uint32_t b[2];
+      ldmatrix_x2(b, sb + (j * 8 + (lane & 7)) * ldb + kk + ((lane >> 3) & 1) * 8);
+      mma16816(acc[j], a, b);
+    }
+  }
+}
+
+// Copy a [rows][cols] BF16 tile (row-major, `cols` contiguous, cols % 8 == 0) into shared
+// memory with row stride ld; rows beyond `valid` are zero.
+__device__ __forceinline__ void load_tile(__nv_bfloat16* dst, int ld, const __nv_bfloat16* src, int src_ld, int rows,
+                                          int cols, int valid) {
+  const int vec = cols / 8;
+  for (int i = threadIdx.x; i < rows * vec; i += blockDim.x) {
+    int r = i / vec, c = (i - r * vec) * 8;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (r < valid) v = *reinterpret_cast<const uint4*>(src + (size_t)r * src_ld + c);
+    *reinterpret_cast<uint4*>(dst + r * ld + c) = v;
+  }
+}
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float z) {
+  return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * 0.3989422804014327f * expf(-0.5f * z * z);
+}
+
+// ------------------------------------------------------------------ kernels
+__global__ void k_features(int n, const float* __restrict__ raw, const float* __restrict__ Bm,
+                           __nv_bfloat16* __restrict__ feat) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const float* q = raw + 7 * (size_t)r;
+  float x[7] = {q[0], q[1] * 0.15915494309189535f, (q[2] - 380.f) / 400.f, (q[3] - 2e-3f) / 3e-3f, q[4] / 2e10f,
+                (q[5] - 1.45f) / 0.2f, (log10f(fmaxf(q[6], 1e-30f)) + 8.f) / 4.f};
+  __nv_bfloat16* f = feat + (size_t)r * kFeat;
+  for (int i = 0; i < 16; ++i) {
+    float p = 0.f;
+    for (int j = 0; j < 7; ++j) p += Bm[i * 7 + j] * x[j];
+    float s, c;
+    sincospif(2.f * p, &s, &c);
+    f[i] = __float2bfloat16(s);
+    f[16 + i] = __float2bfloat16(c);
+  }
+  for (int j = 0; j < 7; ++j) f[32 + j] = __float2bfloat16(x[j]);
+  for (int j = 39; j < kFeat; ++j) f[j] = __float2bfloat16(0.f);
+}
+
+// Z = X W + b (X [n][K] bf16, Wt = W^T [N][K] bf16); hidden layers store Z (bf16) and GELU(Z)
+// (bf16), the output layer stores Z in FP32.
+template <int K, int N, bool kHidden>
+__global__ void __launch_bounds__(kThreads) k_layer_fwd(int n, const __nv_bfloat16* __restrict__ X,
+                                                         const __nv_bfloat16* __restrict__ Wt,
+                                                         const float* __restrict__ bias, __nv_bfloat16* Zb, float* Zf,
+                                                         __nv_bfloat16* A) {
+  constexpr int LD = K + 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __nv_bfloat16* sx = reinterpret_cast<__nv_bfloat16*>(smem_raw);
+  __nv_bfloat16* sw = sx + kRows * LD;
+  const int row0 = blockIdx.x * kRows;
+  load_tile(sx, LD, X + (size_t)row0 * K, K, kRows, K, min(kRows, n - row0));
+  load_tile(sw, LD, Wt, K, N, K, N);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float acc[N / 8][4];
+#pragma unroll
+  for (int j = 0; j < N / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+  warp_gemm<K, N / 8>(acc, sx + warp * 16 * LD, LD, sw, LD);
+#pragma unroll
+  for (int j = 0; j < N / 8; ++j) {
+    const int col = j * 8 + (lane & 3) * 2;
+    const float b0 = bias[col], b1 = bias[col + 1];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = row0 + warp * 16 + (lane >> 2) + h * 8;
+      if (r >= n) continue;
+      float z0 = acc[j][2 * h] + b0, z1 = acc[j][2 * h + 1] + b1;
+      size_t o = (size_t)r * N + col;
+      if (kHidden) {
+        *reinterpret_cast<__nv_bfloat162*>(Zb + o) = __floats2bfloat162_rn(z0, z1);
+        *reinterpret_cast<__nv_bfloat162*>(A + o) = __floats2bfloat162_rn(gelu(z0), gelu(z1));
+      } else {
+        Zf[o] = z0;
+        Zf[o + 1] = z1;
+      }
+    }
+  }
+}
+
+// Loss sum_j (sigmoid(z_j) - y_j)^2 per row; dZ = d(mean loss)/dZ for the output layer.
+__global__ void k_loss(int n, float inv_batch, const float* __restrict__ Z, const float* __restrict__ Y,
+                       __nv_bfloat16* __restrict__ dZ, float* loss_sum) {
+  int r = blockIdx.x * blockDim.x + threadIdx.x;
+  float l = 0.f;
+  if (r < n) {
+    for (int j = 0; j < kOut; ++j) {
+      float g = 0.f;
+      if (j < kTargets) {
+        float p = 1.f / (1.f + expf(-Z[(size_t)r * kOut + j]));
+        float d = p - Y[(size_t)r * kTargets + j];
+        l += d * d;
+        g = 2.f * d * p * (1.f - p) * inv_batch;
+      }
+      dZ[(size_t)r * kOut + j] = __float2bfloat16(g);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss_sum, l);
+}
+
+// dZ_prev = (dZ W^T) * GELU'(Z_prev): dZ [n][N], W [K][N] (as the B operand, K output
+// columns, N reduction), Z_prev [n][K].
+template <int N, int K>
+__global__ void __launch_bounds__(kThreads) k_layer_bwd_data(int n, const __nv_bfloat16* __restrict__ dZ,
+                                                              const __nv_bfloat16* __restrict__ W,
+                                                              const __nv_bfloat16* __restrict__ Zprev,
+                                                              __nv_bfloat16* __restrict__ dZprev) {
+  constexpr int LD = N + 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __nv_bfloat16* sd = reinterpret_cast<__nv_bfloat16*>(smem_raw);
+  __nv_bfloat16* sw = sd + kRows * LD;
+  const int row0 = blockIdx.x * kRows;
+  load_tile(sd, LD, dZ + (size_t)row0 * N, N, kRows, N, min(kRows, n - row0));
+  load_tile(sw, LD, W, N, K, N, K);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float acc[K / 8][4];
+#pragma unroll
+  for (int j = 0; j < K / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+  warp_gemm<N, K / 8>(acc, sd + warp * 16 * LD, LD, sw, LD);
+#pragma unroll
+  for (int j = 0; j < K / 8; ++j) {
+    const int col = j * 8 + (lane & 3) * 2;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = row0 + warp * 16 + (lane >> 2) + h * 8;
+      if (r >= n) continue;
+      size_t o = (size_t)r * K + col;
+      __nv_bfloat162 zp = *reinterpret_cast<const __nv_bfloat162*>(Zprev + o);
+      float g0 = acc[j][2 * h] * gelu_grad(__bfloat162float(zp.x));
+      float g1 = acc[j][2 * h + 1] * gelu_grad(__bfloat162float(zp.y));
+      *reinterpret_cast<__nv_bfloat162*>(dZprev + o) = __floats2bfloat162_rn(g0, g1);
+    }
+  }
+}
+
+// dW += X^T dZ and db += column sums of dZ over this block's row chunks (X [n][K], dZ [n][N]).
+template <int K, int N>
+__global__ void __launch_bounds__(kThreads) k_layer_bwd_weight(int n, const __nv_bfloat16* __restrict__ X,
+                                                                const __nv_bfloat16* __restrict__ dZ, float* dW,
+                                                                float* db) {
+  constexpr int LD = kRows + 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __nv_bfloat16* sxt = reinterpret_cast<__nv_bfloat16*>(smem_raw);  // [K][LD]: X^T of the chunk
+  __nv_bfloat16* sdt = sxt + K * LD;                                // [N][LD]: dZ^T of the chunk
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float acc[N / 8][4];
+#pragma unroll
+  for (int j = 0; j < N / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+  float bsum = 0.f;  // thread t < N sums column t
+  const int chunks = (n + kRows - 1) / kRows;
+  for (int c = blockIdx.x; c < chunks; c += gridDim.x) {
+    const int row0 = c * kRows, valid = min(kRows, n - row0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kRows * K; i += blockDim.x) {
+      int r = i / K, k = i - r * K;
+      sxt[k * LD + r] = r < valid ? X[(size_t)(row0 + r) * K + k] : __float2bfloat16(0.f);
+    }
+    for (int i = threadIdx.x; i < kRows * N; i += blockDim.x) {
+      int r = i / N, k = i - r * N;
+      sdt[k * LD + r] = r < valid ? dZ[(size_t)(row0 + r) * N + k] : __float2bfloat16(0.f);
+    }
+    __syncthreads();
+    if (warp < K / 16) warp_gemm<kRows, N / 8>(acc, sxt + warp * 16 * LD, LD, sdt, LD);
+    if (threadIdx.x < N)
+      for (int r = 0; r < valid; ++r) bsum += __bfloat162float(sdt[threadIdx.x * LD + r]);
+  }
+  if (warp < K / 16) {
+#pragma unroll
+    for (int j = 0; j < N / 8; ++j) {
+      const int col = j * 8 + (lane & 3) * 2;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = warp * 16 + (lane >> 2) + h * 8;
+        atomicAdd(dW + (size_t)k * N + col, acc[j][2 * h]);
+        atomicAdd(dW + (size_t)k * N + col + 1, acc[j][2 * h + 1]);
+      }
+    }
+  }
+  if (threadIdx.x < N) atomicAdd(db + threadIdx.x, bsum);
+}
+
+__global__ void k_adam(int n, float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float gi = g[i];
+  float mi = b1 * m[i] + (1.f - b1) * gi;
+  float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// BF16 copies of the weights in both layouts: W [K][N] and Wt [N][K].
+__global__ void k_weights_bf16(const float* __restrict__ p, __nv_bfloat16* __restrict__ Wb,
+                               __nv_bfloat16* __restrict__ Wtb) {
+  int l = blockIdx.y;
+  const int K = layer_in(l), N = layer_out(l);
+  const float* W = p + layer_offset(l);
+  __nv_bfloat16* wb = Wb + layer_offset(l);
+  __nv_bfloat16* wt = Wtb + layer_offset(l);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K * N; i += gridDim.x * blockDim.x) {
+    int k = i / N, c = i - k * N;
+    __nv_bfloat16 v = __float2bfloat16(W[i]);
+    wb[i] = v;
+    wt[c * K + k] = v;
+  }
+}
+
+__global__ void k_predict(int n, const float* __restrict__ Z, float* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * kTargets) return;
+  int r = i / kTargets, j = i - r * kTargets;
+  out[i] = 1.f / (1.f + expf(-Z[(size_t)r * kOut + j]));
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t n) {
+  return cudaMalloc(p, sizeof(T) * (n > 0 ? n : 1));
+}
+
+}  // namespace
+
+struct sdd_surrogate {
+  int max_batch = 0;
+  float* params = nullptr;  // FP32 master weights
+  float* grads = nullptr;
+  float* m = nullptr;
+  float* v = nullptr;
+  float* Bm = nullptr;      // Fourier matrix [16][7]
+  __nv_bfloat16* Wb = nullptr;
+  __nv_bfloat16* Wtb = nullptr;
+  __nv_bfloat16* feat = nullptr;            // [batch][48]
+  __nv_bfloat16* Z[kLayers - 1] = {};        // hidden pre-activations [batch][128]
+  __nv_bfloat16* A[kLayers - 1] = {};        // hidden activations
+  float* Zout = nullptr;                     // [batch][16]
+  __nv_bfloat16* dZ[2] = {};                 // [batch][128]
+  float* loss = nullptr;
+  int step = 0;
+  ~sdd_surrogate() {
+    cudaFree(params); cudaFree(grads); cudaFree(m); cudaFree(v); cudaFree(Bm); cudaFree(Wb); cudaFree(Wtb);
+    cudaFree(feat); cudaFree(Zout); cudaFree(loss);
+    for (auto* p : Z) cudaFree(p);
+    for (auto* p : A) cudaFree(p);
+    for (auto* p : dZ) cudaFree(p);
+  }
+};
+
+namespace {
+
+size_t fwd_smem(int K, int N) { return sizeof(__nv_bfloat16) * (size_t)(kRows + N) * (K + 8); }
+size_t bwdd_smem(int N, int K) { return sizeof(__nv_bfloat16) * (size_t)(kRows + K) * (N + 8); }
+size_t bwdw_smem(int K, int N) { return sizeof(__nv_bfloat16) * (size_t)(K + N) * (kRows + 8); }
+
+template <int K, int N, bool H>
+void set_fwd_attr() {
+  cudaFuncSetAttribute(k_layer_fwd<K, N, H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem(K, N));
+}
+
+sdd_status check(cudaError_t e) {
+  return e == cudaSuccess ? SDD_OK : set_last_error(e == cudaErrorMemoryAllocation ? SDD_ERR_OOM : SDD_ERR_CUDA,
+                                                    cudaGetErrorString(e));
+}
+
+// Forward pass of n rows of raw inputs; leaves Zout (FP32) and the hidden Z/A buffers.
+cudaError_t forward(sdd_surrogate* s, int n, const float* raw, cudaStream_t st) {
+  k_features<<<(n + 127) / 128, 128, 0, st>>>(n, raw, s->Bm, s->feat);
+  const int blocks = (n + kRows - 1) / kRows;
+  k_layer_fwd<kFeat, kHid, true><<<blocks, kThreads, fwd_smem(kFeat, kHid), st>>>(
+      n, s->feat, s->Wtb + layer_offset(0), s->params + layer_offset(0) + kFeat * kHid, s->Z[0], nullptr, s->A[0]);
+  for (int l = 1; l < kLayers - 1; ++l)
+    k_layer_fwd<kHid, kHid, true><<<blocks, kThreads, fwd_smem(kHid, kHid), st>>>(
+        n, s->A[l - 1], s->Wtb + layer_offset(l), s->params + layer_offset(l) + kHid * kHid, s->Z[l], nullptr,
+        s->A[l]);
+  k_layer_fwd<kHid, kOut, false><<<blocks, kThreads, fwd_smem(kHid, kOut), st>>>(
+      n, s->A[kLayers - 2], s->Wtb + layer_offset(4), s->params + layer_offset(4) + kHid * kOut, nullptr, s->Zout,
+      nullptr);
+  return cudaGetLastError();
+}
+
+// Loss and gradients of n rows into s->grads (zeroed first); loss sum in s->loss.
+cudaError_t backward(sdd_surrogate* s, int n, const float* raw, const float* y, cudaStream_t st) {
+  cudaError_t e = forward(s, n, raw, st);
+  if (e != cudaSuccess) return e;
+  cudaMemsetAsync(s->grads, 0, sizeof(float) * kParams, st);
+  cudaMemsetAsync(s->loss, 0, sizeof(float), st);
+  k_loss<<<(n + 127) / 128, 128, 0, st>>>(n, 1.f / n, s->Zout, y, s->dZ[0], s->loss);
+  const int blocks = (n + kRows - 1) / kRows;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int wblocks = std::min(blocks, 2 * sms);
+  // output layer
+  float* g4 = s->grads + layer_offset(4);
+  k_layer_bwd_weight<kHid, kOut><<<wblocks, kThreads, bwdw_smem(kHid, kOut), st>>>(n, s->A[3], s->dZ[0], g4,
+                                                                                  g4 + kHid * kOut);
+  k_layer_bwd_data<kOut, kHid><<<blocks, kThreads, bwdd_smem(kOut, kHid), st>>>(n, s->dZ[0], s->Wb + layer_offset(4),
+                                                                               s->Z[3], s->dZ[1]);
+  int cur = 1;
+  for (int l = kLayers - 2; l >= 1; --l) {
+    float* g = s->grads + layer_offset(l);
+    k_layer_bwd_weight<kHid, kHid><<<wblocks, kThreads, bwdw_smem(kHid, kHid), st>>>(n, s->A[l - 1], s->dZ[cur], g,
+                                                                                    g + kHid * kHid);
+    k_layer_bwd_data<kHid, kHid><<<blocks, kThreads, bwdd_smem(kHid, kHid), st>>>(
+        n, s->dZ[cur], s->Wb + layer_offset(l), s->Z[l - 1], s->dZ[1 - cur]);
+    cur = 1 - cur;
+  }
+  float* g0 = s->grads;
+  k_layer_bwd_weight<kFeat, kHid><<<wblocks, kThreads, bwdw_smem(kFeat, kHid), st>>>(n, s->feat, s->dZ[cur], g0,
+                                                                                    g0 + kFeat * kHid);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+sdd_status sdd_surrogate_create(const float* fourier_B, const float* init_params, int n_params, int max_batch,
+                                sdd_surrogate** out) {
+  if (!fourier_B || !init_params || !out || max_batch < 1) return set_last_error(SDD_ERR_ARG, "bad arguments");
+  if (n_params != kParams)
+    return set_last_error(SDD_ERR_ARG, ("n_params must be " + std::to_string(kParams)).c_str());
+  *out = nullptr;
+  static bool attrs = false;
+  if (!attrs) {
+    set_fwd_attr<kFeat, kHid, true>();
+    set_fwd_attr<kHid, kHid, true>();
+    set_fwd_attr<kHid, kOut, false>();
+    cudaFuncSetAttribute(k_layer_bwd_data<kHid, kHid>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)bwdd_smem(kHid, kHid));
+    cudaFuncSetAttribute(k_layer_bwd_data<kOut, kHid>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)bwdd_smem(kOut, kHid));
+    cudaFuncSetAttribute(k_layer_bwd_weight<kHid, kHid>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)bwdw_smem(kHid, kHid));
+    cudaFuncSetAttribute(k_layer_bwd_weight<kHid, kOut>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)bwdw_smem(kHid, kOut));
+    cudaFuncSetAttribute(k_layer_bwd_weight<kFeat, kHid>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)bwdw_smem(kFeat, kHid));
+    attrs = true;
+  }
+  sdd_surrogate* s = new sdd_surrogate;
+  s->max_batch = max_batch;
+  const size_t mb = (size_t)max_batch;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](cudaError_t x) {
+    if (e == cudaSuccess) e = x;
+  };
+  A(dalloc(&s->params, kParams));
+  A(dalloc(&s->grads, kParams));
+  A(dalloc(&s->m, kParams));
+  A(dalloc(&s->v, kParams));
+  A(dalloc(&s->Bm, 16 * 7));
+  A(dalloc(&s->Wb, kParams));
+  A(dalloc(&s->Wtb, kParams));
+  A(dalloc(&s->feat, mb * kFeat));
+  for (int l = 0; l < kLayers - 1; ++l) {
+    A(dalloc(&s->Z[l], mb * kHid));
+    A(dalloc(&s->A[l], mb * kHid));
+  }
+  A(dalloc(&s->Zout, mb * kOut));
+  A(dalloc(&s->dZ[0], mb * kHid));
+  A(dalloc(&s->dZ[1], mb * kHid));
+  A(dalloc(&s->loss, 1));
+  if (e == cudaSuccess) e = cudaMemcpy(s->params, init_params, sizeof(float) * kParams, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->Bm, fourier_B, sizeof(float) * 16 * 7, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(s->m, 0, sizeof(float) * kParams);
+  if (e == cudaSuccess) e = cudaMemset(s->v, 0, sizeof(float) * kParams);
+  if (e == cudaSuccess) {
+    k_weights_bf16<<<dim3(16, kLayers), 256>>>(s->params, s->Wb, s->Wtb);
+    e = cudaDeviceSynchronize();
+  }
+  if (e != cudaSuccess) {
+    delete s;
+    return check(e);
+  }
+  *out = s;
+  return SDD_OK;
+}
+
+void sdd_surrogate_destroy(sdd_surrogate* s) { delete s; }
+
+int sdd_surrogate_param_count(void) { return kParams; }
+
+sdd_status sdd_surrogate_get_params(const sdd_surrogate* s, float* host_out, int n) {
+  if (!s || !host_out || n != kParams) return set_last_error(SDD_ERR_ARG, "bad arguments");
+  return check(cudaMemcpy(host_out, s->params, sizeof(float) * kParams, cudaMemcpyDeviceToHost));
+}
+
+sdd_status sdd_surrogate_set_params(sdd_surrogate* s, const float* host_in, int n) {
+  if (!s || !host_in || n != kParams) return set_last_error(SDD_ERR_ARG, "bad arguments");
+  cudaError_t e = cudaMemcpy(s->params, host_in, sizeof(float) * kParams, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_weights_bf16<<<dim3(16, kLayers), 256>>>(s->params, s->Wb, s->Wtb);
+    e = cudaDeviceSynchronize();
+  }
+  return check(e);
+}
+
+sdd_status sdd_surrogate_gradients(sdd_surrogate* s, int n, const float* raw_dev, const float* y_dev, float* grad_host,
+                                   float* loss_host, void* stream) {
+  if (!s || n < 1 || n > s->max_batch || !raw_dev || !y_dev) return set_last_error(SDD_ERR_ARG, "bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = backward(s, n, raw_dev, y_dev, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && grad_host)
+    e = cudaMemcpy(grad_host, s->grads, sizeof(float) * kParams, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && loss_host) {
+    e = cudaMemcpy(loss_host, s->loss, sizeof(float), cudaMemcpyDeviceToHost);
+    *loss_host /= n;
+  }
+  return check(e);
+}
+
+sdd_status sdd_surrogate_train_step(sdd_surrogate* s, int n, const float* raw_dev, const float* y_dev, float lr,
+                                    float* loss_host, void* stream) {
+  if (!s || n < 1 || n > s->max_batch || !raw_dev || !y_dev || !(lr > 0.f))
+    return set_last_error(SDD_ERR_ARG, "bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = backward(s, n, raw_dev, y_dev, st);
+  if (e != cudaSuccess) return check(e);
+  s->step++;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)s->step), c2 = 1.f - powf(b2, (float)s->step);
+  k_adam<<<(kParams + 255) / 256, 256, 0, st>>>(kParams, s->params, s->grads, s->m, s->v, lr, b1, b2, 1e-8f, c1, c2);
+  k_weights_bf16<<<dim3(16, kLayers), 256, 0, st>>>(s->params, s->Wb, s->Wtb);
+  e = cudaGetLastError();
+  if (e == cudaSuccess && loss_host) {
+    e = cudaMemcpyAsync(loss_host, s->loss, sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    *loss_host /= n;
+  }
+  return check(e);
+}
+
+sdd_status sdd_surrogate_infer(sdd_surrogate* s, int n, const float* raw_dev, float* out_dev, void* stream) {
+  if (!s || n < 0 || !raw_dev || !out_dev) return set_last_error(SDD_ERR_ARG, "bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int off = 0; off < n; off += s->max_batch) {
+    int m = std::min(s->max_batch, n - off);
+    cudaError_t e = forward(s, m, raw_dev + 7 * (size_t)off, st);
+    if (e != cudaSuccess) return check(e);
+    k_predict<<<(m * kTargets + 255) / 256, 256, 0, st>>>(m, s->Zout, out_dev + kTargets * (size_t)off);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return check(e);
+}
+
+}  // extern "C"

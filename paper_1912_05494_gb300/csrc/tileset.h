@@ -1,0 +1,22 @@
+// tileset.h -- device view of a set of heterogeneous tiles (tile.cu).
+#pragma once
+
+#include <stdint.h>
+
+struct sdd_tileset;
+
+namespace sdd {
+
+struct TileSetDev {
+  const float* heights;  // [n_tiles][(G+1)^2] thickness at the grid vertices
+  const float* hmin;     // [n_tiles]
+  const float* hmax;     // [n_tiles]
+  const float* rho;      // [n_tiles] bubbles per cubic metre
+  int n_tiles;
+  int G;
+  float L;
+};
+
+const TileSetDev* tileset_device_view(const sdd_tileset* t);
+
+}  // namespace sdd

@@ -306,6 +306,53 @@ def nave_scene(seed: int = 1, cell: float = 0.25, windows_per_wall: int = 12,
     return scene, cam, spec
 
 
+def tile_set(seed: int = 3, n_tiles: int = 512):
+    """Heterogeneous tiles: mean thickness U[2.5, 4.5] mm, thickness variation U[0.5, 3] mm
+    peak to peak (the field is clamped to 2-5 mm), bubble density 1e4 per cm^3 scaled by
+    U[0.5, 1.5], and per-tile Cauchy n(lambda) / banded k(lambda) on the 81-sample grid."""
+    rng = np.random.default_rng(seed)
+    lam = SPECTRAL_GRID_81
+    tiles = [{"d_mean": float(rng.uniform(2.5e-3, 4.5e-3)), "amp": float(rng.uniform(0.5e-3, 3e-3)),
+              "rho": float(1e10 * rng.uniform(0.5, 1.5)), "seed": int(rng.integers(1, 2**31))}
+             for _ in range(n_tiles)]
+    a = rng.uniform(1.50, 1.58, n_tiles)
+    b = rng.uniform(0.003, 0.006, n_tiles)
+    n = cauchy_n(lam[None, :], a[:, None], b[:, None])
+    base = np.exp(rng.uniform(np.log(1e-7), np.log(1e-5), n_tiles))
+    centre = rng.uniform(400.0, 700.0, (n_tiles, 3))
+    sigma = rng.uniform(15.0, 60.0, (n_tiles, 3))
+    amp = rng.uniform(0.5, 3.0, (n_tiles, 3))
+    k = base[:, None] * (1.0 + (amp[:, :, None] * np.exp(-((lam[None, None, :] - centre[:, :, None]) ** 2)
+                                                          / (2.0 * sigma[:, :, None] ** 2))).sum(axis=1))
+    return tiles, n.astype(np.float32), k.astype(np.float32)
+
+
+def tile_queries(seed: int, n_samples: int, n_tiles: int, tile_n, tile_k):
+    """Seeded surrogate queries: cos(theta_in) ~ U(0, 1], phi_in ~ U[0, 2 pi), lambda uniform on
+    the 81-sample grid, tile uniform; n and k looked up from the tile's tables."""
+    rng = np.random.default_rng(seed)
+    cos_in = (1.0 - rng.uniform(0.0, 1.0, n_samples)).astype(np.float32)
+    phi = rng.uniform(0.0, 2.0 * math.pi, n_samples).astype(np.float32)
+    li = rng.integers(0, SPECTRAL_GRID_81.size, n_samples)
+    tile = rng.integers(0, n_tiles, n_samples).astype(np.int32)
+    return {"cos_in": cos_in, "phi_in": phi, "lambda_nm": SPECTRAL_GRID_81[li].astype(np.float32),
+            "lambda_index": li.astype(np.int32), "n": tile_n[tile, li].astype(np.float32),
+            "k": tile_k[tile, li].astype(np.float32), "tile": tile}
+
+
+def surrogate_init(seed: int = 4):
+    """Initial state of the tile-BTDF network: Fourier matrix B [16, 7] ~ N(0, 1) and layer
+    weights W [in, out] ~ U(-a, a), a = sqrt(6 / (in + out)) (Glorot), biases 0.  Layer
+    widths 48 -> 128 -> 128 -> 128 -> 128 -> 16."""
+    rng = np.random.default_rng(seed)
+    B = rng.normal(0.0, 1.0, (16, 7))
+    params = []
+    for n_in, n_out in ((48, 128), (128, 128), (128, 128), (128, 128), (128, 16)):
+        a = math.sqrt(6.0 / (n_in + n_out))
+        params.append((rng.uniform(-a, a, (n_in, n_out)), np.zeros(n_out)))
+    return B, params
+
+
 def tiny_scene(seed: int = 0, n_triangles: int = 32, kinds=(MAT_DIFFUSE,)):
     """A few random triangles inside the unit cube, for intersection tests."""
     rng = np.random.default_rng(seed)

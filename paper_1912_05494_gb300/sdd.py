@@ -75,6 +75,12 @@ class sdd_stats(C.Structure):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
 
 
+class sdd_tileset_desc(C.Structure):
+    _fields_ = [("n_tiles", C.c_int), ("d_mean_m", C.c_void_p), ("amplitude_m", C.c_void_p),
+                ("bubble_density_m3", C.c_void_p), ("seed", C.c_void_p), ("grid", C.c_int),
+                ("tile_size_m", C.c_float)]
+
+
 class sdd_tuning(C.Structure):
     _fields_ = [("traverse_block", C.c_int), ("top_nodes", C.c_int), ("wave_paths", C.c_int), ("no_graph", C.c_int)]
 
@@ -108,11 +114,31 @@ def lib():
         L.sdd_trace_closest_noalloc.argtypes = [vp, i32, vp, vp, vp, vp, vp]
         L.sdd_eval_optics.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.sdd_philox.argtypes = [i32, vp, C.c_uint64, vp, vp]
+        L.sdd_tileset_create.argtypes = [C.POINTER(sdd_tileset_desc), C.POINTER(vp)]
+        L.sdd_tileset_destroy.argtypes = [vp]
+        L.sdd_tileset_destroy.restype = None
+        L.sdd_tileset_heights.argtypes = [vp, i32, vp]
+        u32, u64, f32 = C.c_uint32, C.c_uint64, C.c_float
+        L.sdd_tile_trace_rays.argtypes = [vp, i32, i32, vp, vp, f32, f32, f32, vp, vp, u32, u32, u64, i32, vp, vp, vp,
+                                          vp, vp, vp]
+        L.sdd_tile_generate.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, i32, u64, i32, vp, vp]
+        L.sdd_surrogate_param_count.restype = i32
+        L.sdd_surrogate_create.argtypes = [vp, vp, i32, i32, C.POINTER(vp)]
+        L.sdd_surrogate_destroy.argtypes = [vp]
+        L.sdd_surrogate_destroy.restype = None
+        L.sdd_surrogate_get_params.argtypes = [vp, vp, i32]
+        L.sdd_surrogate_set_params.argtypes = [vp, vp, i32]
+        L.sdd_surrogate_gradients.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+        L.sdd_surrogate_train_step.argtypes = [vp, i32, vp, vp, f32, vp, vp]
+        L.sdd_surrogate_infer.argtypes = [vp, i32, vp, vp, vp]
         L.sdd_last_error.restype = C.c_char_p
         L.sdd_version.restype = C.c_char_p
         for name in ("sdd_scene_create", "sdd_render", "sdd_render_to_host", "sdd_set_profiling", "sdd_get_stats",
                      "sdd_scene_get_info", "sdd_trace_closest", "sdd_trace_closest_noalloc", "sdd_eval_optics",
-                     "sdd_philox", "sdd_set_tuning", "sdd_get_tuning"):
+                     "sdd_philox", "sdd_set_tuning", "sdd_get_tuning", "sdd_tileset_create", "sdd_tileset_heights",
+                     "sdd_tile_trace_rays", "sdd_tile_generate", "sdd_surrogate_create", "sdd_surrogate_get_params",
+                     "sdd_surrogate_set_params", "sdd_surrogate_gradients", "sdd_surrogate_train_step",
+                     "sdd_surrogate_infer"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -303,6 +329,124 @@ def sdd_eval_optics(cos_i, n_re, k, d, lam, R, Rs, Ts, stream=None):
 def sdd_philox(ctr, key: int, out, stream=None):
     n = int(ctr.shape[0])
     _check(lib().sdd_philox(n, _ptr(ctr), C.c_uint64(key), _ptr(out), _stream(stream)))
+
+
+# ----------------------------------------------------------------------------- tiles
+def sdd_tileset_create(tiles, grid=64, tile_size_m=0.1):
+    """tiles: list of dicts with d_mean, amp, rho, seed (host values)."""
+    keep = [np.ascontiguousarray([t[key] for t in tiles], dtype=dt)
+            for key, dt in (("d_mean", np.float32), ("amp", np.float32), ("rho", np.float32), ("seed", np.uint32))]
+    d = sdd_tileset_desc(len(tiles), *(C.c_void_p(a.ctypes.data) for a in keep), grid, tile_size_m)
+    h = C.c_void_p()
+    _check(lib().sdd_tileset_create(C.byref(d), C.byref(h)))
+    return h
+
+
+def sdd_tileset_destroy(h):
+    lib().sdd_tileset_destroy(h)
+
+
+def sdd_tileset_heights(h, tile, grid=64):
+    out = np.zeros((grid + 1) * (grid + 1), np.float32)
+    _check(lib().sdd_tileset_heights(h, int(tile), C.c_void_p(out.ctypes.data)))
+    return out.reshape(grid + 1, grid + 1)
+
+
+def sdd_tile_trace_rays(h, tile, xy, dirs, n_re, k, lambda_nm, px, sample, bounce, lam, seed, max_events, side, w,
+                        dir_out, bubbles, events, stream=None):
+    n = int(xy.shape[0])
+    _check(lib().sdd_tile_trace_rays(h, int(tile), n, _ptr(xy), _ptr(dirs), float(n_re), float(k), float(lambda_nm),
+                                     _ptr(px), _ptr(sample), int(bounce), int(lam), int(seed), int(max_events),
+                                     _ptr(side), _ptr(w), _ptr(dir_out), _ptr(bubbles), _ptr(events), _stream(stream)))
+
+
+def sdd_tile_generate(h, cos_in, phi_in, lambda_nm, n_re, k, tile, rays, seed, max_events, out, stream=None):
+    n = int(cos_in.shape[0])
+    _check(lib().sdd_tile_generate(h, n, _ptr(cos_in), _ptr(phi_in), _ptr(lambda_nm), _ptr(n_re), _ptr(k), _ptr(tile),
+                                   int(rays), int(seed), int(max_events), _ptr(out), _stream(stream)))
+
+
+class TileSetHandle:
+    def __init__(self, tiles, grid=64, tile_size_m=0.1):
+        self.h = sdd_tileset_create(tiles, grid, tile_size_m)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            sdd_tileset_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------------------- surrogate
+def flatten_params(params):
+    """[(W [in, out], b [out]), ...] -> flat float32 array in the library's layout."""
+    return np.concatenate([np.concatenate([np.asarray(W, np.float32).ravel(), np.asarray(b, np.float32)])
+                           for W, b in params]).astype(np.float32)
+
+
+def unflatten_params(flat, shapes=((48, 128), (128, 128), (128, 128), (128, 128), (128, 16))):
+    out, o = [], 0
+    for n_in, n_out in shapes:
+        W = flat[o:o + n_in * n_out].reshape(n_in, n_out)
+        o += n_in * n_out
+        b = flat[o:o + n_out]
+        o += n_out
+        out.append((W, b))
+    return out
+
+
+class Surrogate:
+    """The tile-BTDF network on the GPU (thin wrapper of the sdd_surrogate_* calls)."""
+
+    def __init__(self, fourier_B, params, max_batch=65536):
+        flat = flatten_params(params)
+        Bm = np.ascontiguousarray(fourier_B, np.float32)
+        self.n_params = int(lib().sdd_surrogate_param_count())
+        h = C.c_void_p()
+        _check(lib().sdd_surrogate_create(C.c_void_p(Bm.ctypes.data), C.c_void_p(flat.ctypes.data), flat.size,
+                                          max_batch, C.byref(h)))
+        self.h = h
+
+    def params(self):
+        out = np.zeros(self.n_params, np.float32)
+        _check(lib().sdd_surrogate_get_params(self.h, C.c_void_p(out.ctypes.data), self.n_params))
+        return out
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, np.float32)
+        _check(lib().sdd_surrogate_set_params(self.h, C.c_void_p(flat.ctypes.data), flat.size))
+
+    def gradients(self, raw, y, stream=None):
+        g = np.zeros(self.n_params, np.float32)
+        loss = C.c_float()
+        _check(lib().sdd_surrogate_gradients(self.h, int(raw.shape[0]), _ptr(raw), _ptr(y), C.c_void_p(g.ctypes.data),
+                                             C.byref(loss), _stream(stream)))
+        return float(loss.value), g
+
+    def train_step(self, raw, y, lr=1e-3, stream=None):
+        loss = C.c_float()
+        _check(lib().sdd_surrogate_train_step(self.h, int(raw.shape[0]), _ptr(raw), _ptr(y), C.c_float(lr),
+                                              C.byref(loss), _stream(stream)))
+        return float(loss.value)
+
+    def infer(self, raw, out, stream=None):
+        _check(lib().sdd_surrogate_infer(self.h, int(raw.shape[0]), _ptr(raw), _ptr(out), _stream(stream)))
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().sdd_surrogate_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def sdd_last_error() -> str:

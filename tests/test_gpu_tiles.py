@@ -1,0 +1,103 @@
+"""GPU heterogeneous-tile tracer against the FP64 oracle on the same Philox streams."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1912_05494_gb300 import scenes as S  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def sdd():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1912_05494_gb300 import sdd as m
+    return m
+
+
+ROUGH = {"d_mean": 0.0035, "amp": 0.003, "rho": 1e10, "seed": 17}
+
+
+def test_height_fields_match_the_oracle(sdd, orc):
+    tiles, _, _ = S.tile_set(3, 8)
+    ts = sdd.TileSetHandle(tiles)
+    for t in range(len(tiles)):
+        g = sdd.sdd_tileset_heights(ts.h, t)
+        r = orc.tile_heights(tiles[t])
+        assert np.max(np.abs(g - r)) < 5e-9  # metres
+
+
+def trace_gpu(sdd, ts, tile, xy, dirs, n_re, k, lam, px, seed, max_events=64):
+    n = xy.shape[0]
+    dev = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dt)).cuda()  # noqa: E731
+    side = torch.empty(n, dtype=torch.int32, device="cuda")
+    w = torch.empty(n, device="cuda")
+    dout = torch.empty((n, 3), device="cuda")
+    bub = torch.empty(n, dtype=torch.int32, device="cuda")
+    ev = torch.empty(n, dtype=torch.int32, device="cuda")
+    sdd.sdd_tile_trace_rays(ts.h, tile, dev(xy, np.float32), dev(dirs, np.float32), n_re, k, lam,
+                            dev(px, np.uint32), dev(np.zeros(n), np.uint32), 1, 0, seed, max_events, side, w, dout,
+                            bub, ev)
+    torch.cuda.synchronize()
+    return {"side": side.cpu().numpy(), "w": w.cpu().numpy(), "dir": dout.cpu().numpy(),
+            "bubbles": bub.cpu().numpy(), "events": ev.cpu().numpy()}
+
+
+@pytest.mark.parametrize("cos_in,from_back", [(0.9, False), (0.4, False), (0.7, True)])
+def test_rays_match_the_oracle(sdd, orc, cos_in, from_back):
+    ts = sdd.TileSetHandle([ROUGH])
+    N = 40000
+    rng = np.random.default_rng(1)
+    xy = rng.uniform(0, 0.1, (N, 2))
+    st = math.sqrt(1 - cos_in**2)
+    dz = cos_in if from_back else -cos_in
+    dirs = np.tile([st * math.cos(0.7), st * math.sin(0.7), dz], (N, 1)).astype(np.float32)
+    xy = xy.astype(np.float32)
+    g = trace_gpu(sdd, ts, 0, xy, dirs, 1.53, 3e-6, 550.0, np.arange(N), seed=11)
+    h = orc.tile_heights(ROUGH)
+    r = orc.tile_trace(ROUGH, h, xy.astype(np.float64), dirs.astype(np.float64), float(np.float32(1.53)),
+                       float(np.float32(3e-6)), 550.0, px=np.arange(N), sample=0, seed=11)
+    same = (g["side"] == r["side"]) & (g["events"] == r["events"]) & (g["bubbles"] == r["bubbles"])
+    assert same.mean() >= 0.998, same.mean()
+    rel = np.abs(g["w"][same] - r["w"][same]) / np.maximum(np.abs(r["w"][same]), 1e-6)
+    # FP32 against FP64 over up to 64 interactions: typically ~1e-7, a few long paths ~1e-4
+    assert np.quantile(rel, 0.999) < 1e-3 and rel.mean() < 1e-5
+    ok = same & (r["side"] != 2)
+    assert np.max(np.abs(g["dir"][ok] - r["dir"][ok])) < 1e-3
+    assert np.quantile(np.abs(g["dir"][ok] - r["dir"][ok]).max(axis=1), 0.999) < 1e-4
+    assert (r["bubbles"] > 0).mean() > 0.05
+
+
+def test_flat_tile_is_the_thin_slab_on_the_gpu(sdd, orc):
+    ts = sdd.TileSetHandle([{"d_mean": 0.003, "amp": 0.0, "rho": 0.0, "seed": 1}])
+    N = 200000
+    xy = np.random.default_rng(2).uniform(0, 0.1, (N, 2)).astype(np.float32)
+    dirs = np.tile([0.0, 0.0, -1.0], (N, 1)).astype(np.float32)
+    g = trace_gpu(sdd, ts, 0, xy, dirs, 1.52, 2e-6, 600.0, np.arange(N), seed=4)
+    Rs, Ts = orc.slab(1.0, 1.52, 2e-6, 0.003, 600.0)
+    T = g["w"][g["side"] == 1].sum() / N
+    R = g["w"][g["side"] == 0].sum() / N
+    assert abs(T - Ts) < 3e-3 and abs(R - Rs) < 3e-3
+
+
+def test_sample_statistics_match_the_oracle_on_10k_samples(sdd, orc):
+    """Config-3 check: 10k samples of the 512-tile set, 256 rays each, GPU vs FP64 oracle."""
+    tiles, tn, tk = S.tile_set(3, 512)
+    q = S.tile_queries(5, 10000, len(tiles), tn, tk)
+    ts = sdd.TileSetHandle(tiles)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    out = torch.empty((10000, 8), device="cuda")
+    sdd.sdd_tile_generate(ts.h, dev(q["cos_in"]), dev(q["phi_in"]), dev(q["lambda_nm"]), dev(q["n"]), dev(q["k"]),
+                          dev(q["tile"]), 256, 21, 64, out)
+    g = out.cpu().numpy().astype(np.float64)
+    hs = np.stack([orc.tile_heights(t) for t in tiles])
+    r = orc.tile_samples(tiles, hs, q["cos_in"], q["phi_in"], q["lambda_nm"], q["n"], q["k"], q["tile"], rays=256,
+                         seed=21)
+    for col, tol in ((0, 2e-3), (1, 2e-3)):  # T, R: mean absolute difference over samples
+        assert np.mean(np.abs(g[:, col] - r[:, col])) < tol, col
+    assert np.quantile(np.abs(g[:, 0] - r[:, 0]), 0.99) <= 2.0 / 256
+    assert abs(g[:, 7].mean() - r[:, 7].mean()) < 0.01
+    assert 0.3 < r[:, 0].mean() < 0.95 and r[:, 3].mean() < 0.99  # transmission with scattering
