@@ -35,7 +35,9 @@
 extern "C" {
 #endif
 
-typedef struct sdd_scene sdd_scene; /* opaque, owned by the library */
+typedef struct sdd_scene sdd_scene;         /* opaque, owned by the library */
+typedef struct sdd_tileset sdd_tileset;     /* heterogeneous glass tiles (see below) */
+typedef struct sdd_surrogate sdd_surrogate; /* tile-BTDF network (see below) */
 
 typedef enum {
   SDD_OK = 0,
@@ -97,6 +99,9 @@ typedef struct {
   int split_axis;     /* 0, 1, 2, or -1 = longest axis of the scene box */
   float ray_epsilon_m;/* spawned rays start this far off the surface along its normal;
                          0 = 2e-6 x the largest absolute scene coordinate (at least 1e-5) */
+  const sdd_tileset* tiles; /* tile set of the HETERO_TILE materials (tile_param_id indexes it), or
+                               NULL; must outlive the scene.  A tile's front face is on the +n side
+                               of its triangles' geometric normal, its frame the normal's Duff basis */
 } sdd_scene_desc;
 
 typedef struct {
@@ -120,7 +125,10 @@ typedef struct {
   int max_depth;           /* surface interactions per path; deterministic mode: <= 10 */
   int mode;                /* SDD_MODE_* */
   int rr_start_depth;      /* Russian roulette from this interaction on (Monte Carlo) */
-  int use_surrogate;       /* reserved: must be 0 for now */
+  int use_surrogate;       /* heterogeneous tiles: 0 = one brute-force ray through the tile per hit
+                              (and per shadow ray); 1 = the BTDF network (opts->surrogate): T, R
+                              and a ballistic + von Mises-Fisher lobe per side at hits, T x
+                              ballistic fraction for shadow rays */
   int batched;             /* 0: host-driven wavefront (one launch per subdomain pass, queue counts
                               read back between launches); 1: one persistent cooperative launch
                               per wave drains every generation and pass on the device, and the
@@ -132,6 +140,8 @@ typedef struct {
   float* path_radiance_out;/* optional device [pixels][spp][n_lambda] radiance of every path */
   uint32_t* path_hash_out; /* optional device [pixels][spp][n_lambda] event hash of every path
                               (Monte Carlo; FNV-1a over hit primitives and branch events) */
+  const sdd_surrogate* surrogate; /* with use_surrogate = 1: the network that replaces brute-force
+                                     tracing at heterogeneous-tile hits (host-driven form only) */
 } sdd_render_opts;
 
 /* Build the scene: validates, partitions the geometry into n_subdomains slabs (Sec. 5:
@@ -221,7 +231,6 @@ sdd_status sdd_trace_closest(sdd_scene* scene, int n, const float* org_dev, cons
  * exponential free paths and scattered with exact sphere optics (no displacement); Fresnel
  * (complex index), Snell and Beer-Lambert as for other glass.  Rays are traced by brute
  * force, one Philox draw per interaction on the tile stream. */
-typedef struct sdd_tileset sdd_tileset;
 typedef struct {
   int n_tiles;
   const float* d_mean_m;          /* [n_tiles] mean thickness (host) */
@@ -248,29 +257,34 @@ sdd_status sdd_tile_trace_rays(sdd_tileset* tiles, int tile, int n, const float*
                                uint32_t lam, uint64_t seed, int max_events, int32_t* side, float* w, float* dir_out,
                                int32_t* bubbles, int32_t* events, void* cuda_stream);
 
-/* Surrogate training data: for each of n_samples queries (device arrays: cosine of the
+/* Surrogate training data: for each of n_samples queries (device arrays: signed cosine of the
  * incidence angle, azimuth, wavelength, n, k, tile index) trace rays_per_sample rays from
- * uniform entry points through the front face; out[n][8] (device) = transmittance,
- * reflectance, fraction absorbed at the interaction cap, ballistic fraction of the
- * transmitted weight (within 1 degree of straight through), its weighted mean cosine to
- * straight through, the same two for the reflected weight about the mirror direction, and
- * bubble encounters per ray.  Sample s draws its entry points on (s, ray, 0, tile stream, 0)
- * and its interactions on bounce 1. */
+ * uniform entry points; cos_in > 0 enters through the flat front face travelling toward
+ * -z, cos_in < 0 through the rough (height-field) back face travelling toward +z.  out[n][20]
+ * (device) = transmittance, reflectance, weight absorbed or left at the interaction cap,
+ * bubble encounters per ray, then the fraction of the transmitted weight in each of 8
+ * deflection-angle bins about the straight-through direction (edges 0, 1, 2, 4, 8, 16, 32,
+ * 64, 180 degrees), then the same 8 fractions of the reflected weight about the mirror
+ * direction (a side with no weight has zero fractions).  Sample s draws its entry points on
+ * (s, ray, 0, tile stream, 0) and its interactions on bounce 1. */
 sdd_status sdd_tile_generate(sdd_tileset* tiles, int n_samples, const float* cos_in, const float* phi_in,
                              const float* lambda_nm, const float* n_re, const float* k, const int32_t* tile,
                              int rays_per_sample, uint64_t seed, int max_events, float* out, void* cuda_stream);
 
 /* ---------------------------------------------------------------- BTDF surrogate
- * A small network that predicts a heterogeneous tile's BTDF statistics from (cos theta_in,
- * phi_in, lambda nm, mean thickness m, bubble density m^-3, n, k) -- the raw inputs, [n][7]
- * row-major: T, R, ballistic fraction and mean cosine (to straight through) of T, the same
- * two of R (the outputs of sdd_tile_generate, columns 0, 1, 3, 4, 5, 6).  Fourier features
- * (16 frequencies of the inputs normalised to [0, 1]) -> 48 -> 4 x 128 GELU -> 16; BF16
- * weights and activations, FP32 accumulation on the tensor cores, Adam on FP32 master
- * weights.  Parameters: one FP32 array, per layer W [in][out] row-major then b [out]
- * (sdd_surrogate_param_count() values).  The paper has no network; it names scattering in
- * the glass as future work (Sec. 6). */
-typedef struct sdd_surrogate sdd_surrogate;
+ * A small network that predicts a heterogeneous tile's BTDF from (signed cos theta_in as in
+ * sdd_tile_generate, phi_in, lambda nm, mean thickness m, bubble density m^-3, n, k) -- the
+ * raw inputs, [n][7] row-major.  Predictions, [n][8]: T, R, then for the transmitted side
+ * the weight w of its first lobe and log kappa of its two von Mises-Fisher lobes about the
+ * straight-through direction, then the same three for the reflected side about the mirror
+ * direction.  Training targets, [n][18]: T, R and the 8 + 8 deflection-bin fractions
+ * (sdd_tile_generate columns 0, 1, 4..19).  Loss per row: squared errors of T and R plus
+ * 0.05 x (T KL(bins_T | lobe mass_T) + R KL(bins_R | lobe mass_R)), KL with 1e-4 added to
+ * both sides.  Fourier features (16 frequencies of the inputs normalised to [0, 1]) -> 48 ->
+ * 4 x 128 GELU -> 16; BF16 weights and activations, FP32 accumulation on the tensor cores,
+ * Adam on FP32 master weights.  Parameters: one FP32 array, per layer W [in][out] row-major
+ * then b [out] (sdd_surrogate_param_count() values).  The paper has no network; it names
+ * scattering in the glass as future work (Sec. 6). */
 int sdd_surrogate_param_count(void);
 /* fourier_B: host [16][7]; init_params: host flat parameters; max_batch rows per call. */
 sdd_status sdd_surrogate_create(const float* fourier_B, const float* init_params, int n_params, int max_batch,
@@ -278,15 +292,14 @@ sdd_status sdd_surrogate_create(const float* fourier_B, const float* init_params
 void sdd_surrogate_destroy(sdd_surrogate* s);
 sdd_status sdd_surrogate_get_params(const sdd_surrogate* s, float* host_out, int n_params);
 sdd_status sdd_surrogate_set_params(sdd_surrogate* s, const float* host_in, int n_params);
-/* Loss (mean over rows of the summed squared error of the six sigmoid outputs) and its
- * gradient for n <= max_batch rows (raw inputs and targets [n][6] on the device), without
- * updating the weights; grad_host may be NULL. */
+/* Loss (mean over rows) and its gradient for n <= max_batch rows (raw inputs [n][7] and
+ * targets [n][18] on the device), without updating the weights; grad_host may be NULL. */
 sdd_status sdd_surrogate_gradients(sdd_surrogate* s, int n, const float* raw_dev, const float* y_dev, float* grad_host,
                                    float* loss_host, void* cuda_stream);
 /* One Adam step (beta 0.9 / 0.999, eps 1e-8, learning rate lr) on a batch of n rows. */
 sdd_status sdd_surrogate_train_step(sdd_surrogate* s, int n, const float* raw_dev, const float* y_dev, float lr,
                                     float* loss_host, void* cuda_stream);
-/* Predictions [n][6] (device) for n rows of raw inputs (any n; processed max_batch at a time). */
+/* Predictions [n][8] (device) for n rows of raw inputs (any n; processed max_batch at a time). */
 sdd_status sdd_surrogate_infer(sdd_surrogate* s, int n, const float* raw_dev, float* out_dev, void* cuda_stream);
 
 /* sdd_trace_closest without any allocation (the paper has no counterpart; this serves

@@ -37,7 +37,8 @@ class OrcScene(C.Structure):
         ("mat_n", C.c_void_p), ("mat_k", C.c_void_p), ("mat_albedo", C.c_void_p),
         ("sky", C.c_void_p), ("sky_mode", C.c_int),
         ("sun_dir", C.c_float * 3), ("sun_half_angle", C.c_float), ("sun", C.c_void_p),
-        ("ray_eps", C.c_float),
+        ("ray_eps", C.c_float), ("n_tiles", C.c_int), ("tiles", C.c_void_p), ("mat_tile", C.c_void_p),
+        ("tile_grid", C.c_int), ("tile_size", C.c_double),
     ]
 
 
@@ -154,6 +155,10 @@ class OrcTile(C.Structure):
     _fields_ = [("d_mean", C.c_double), ("amp", C.c_double), ("rho", C.c_double), ("seed", C.c_uint32)]
 
 
+TILE_BINS = 8
+TILE_STAT_COLS = 4 + 2 * TILE_BINS
+
+
 def _tiles(tiles):
     arr = (OrcTile * len(tiles))()
     for i, t in enumerate(tiles):
@@ -190,12 +195,14 @@ def tile_trace(tile, heights, xy, dirs, n_re, k, lambda_nm, px, sample, bounce=1
 
 def tile_samples(tiles, heights, cos_in, phi_in, lambda_nm, n_re, k, tile, rays=256, seed=0, max_events=64,
                  n_threads=0, G=64, L=0.1):
-    """Per-sample statistics [n, 8]: T, R, capped, ballistic-T, cos-T, ballistic-R, cos-R, bubbles/ray."""
+    """Per-sample statistics [n, 20]: T, R, absorbed, bubbles/ray, then the fraction of T and of R
+    in each of 8 deflection-angle bins (edges 0, 1, 2, 4, 8, 16, 32, 64, 180 degrees).
+    cos_in > 0 enters through the tile's flat front face, < 0 through its rough back face."""
     hs = _c(heights, np.float64).ravel()
     args = [_c(x, np.float64).ravel() for x in (cos_in, phi_in, lambda_nm, n_re, k)]
     t = _c(tile, np.int32).ravel()
     ns = t.size
-    out = np.zeros((ns, 8))
+    out = np.zeros((ns, TILE_STAT_COLS))
     lib().orc_tile_samples(len(tiles), _tiles(tiles), G, C.c_double(L), _p(hs), ns, *(_p(a) for a in args), _p(t),
                            rays, C.c_uint64(seed), max_events, n_threads, _p(out))
     return out
@@ -238,6 +245,14 @@ class OracleScene:
         d.sun_half_angle = float(sd.sun_half_angle)
         d.sun = keep(sd.sun, np.float32) if sd.sun is not None else None
         d.ray_eps = float(sd.ray_eps)
+        if getattr(sd, "tiles", None):
+            arr = _tiles(sd.tiles)
+            self._keep.append(arr)
+            d.n_tiles = len(sd.tiles)
+            d.tiles = C.cast(arr, C.c_void_p)
+            d.mat_tile = keep(sd.mat_tile, np.int32)
+            d.tile_grid = int(sd.tile_grid)
+            d.tile_size = float(sd.tile_size)
         self.h = lib().orc_scene_create(C.byref(d))
 
     def __del__(self):

@@ -52,6 +52,7 @@ V3 cross(V3 a, V3 b) {
 }
 V3 normalize(V3 a) { return (1.0 / std::sqrt(dot(a, a))) * a; }
 double comp(V3 a, int i) { return i == 0 ? a.x : (i == 1 ? a.y : a.z); }
+V3 reflect(V3 d, V3 n) { return d - (2.0 * dot(d, n)) * n; }
 
 // ---------------------------------------------------------------- Philox4x32-10
 // Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11.
@@ -89,7 +90,7 @@ Draw draw(uint32_t pixel, uint32_t sample, uint32_t bounce, uint32_t stream, uin
   philox4x32_10(ctr, key, o);
   return Draw{{u01(o[0]), u01(o[1]), u01(o[2]), u01(o[3])}};
 }
-enum { STREAM_PATH = 0, STREAM_NEE = 1, STREAM_TILE = 2 };
+enum { STREAM_PATH = 0, STREAM_NEE = 1, STREAM_TILE = 2, STREAM_SHADOW_TILE = 3 };
 
 // ---------------------------------------------------------------- optics
 // Unpolarised Fresnel reflectance at a plane interface, incident medium with real index
@@ -232,6 +233,238 @@ struct Material {
 };
 enum { MAT_SOLID = 0, MAT_SLAB = 1, MAT_TILE = 2, MAT_DIFFUSE = 3, MAT_OPAQUE = 4 };
 
+// ---------------------------------------------------------------- heterogeneous tiles
+// A medieval glass tile with non-uniform thickness and air micro-bubbles (Sec. 1: "non
+// uniform thickness and ... micro particles of air inside the tiles"; Sec. 6: scattering as
+// future work).  Model (readings, the paper gives none):
+//   * periodic square tile of side L, flat front face z = 0, back face z = -h(x, y);
+//   * h = clamp(d_mean + A (n(x, y) - 1/2), 2 mm, 5 mm) with n = 2/3 v(L/10) + 1/3 v(L/20),
+//     v = value noise with smoothstep interpolation of lattice values drawn from Philox;
+//   * the back face is the G x G triangulated height field through h at the grid vertices;
+//   * bubbles form a Poisson process of density rho in the glass, radii log-uniform in
+//     [10, 100] um: the free path to the next bubble is exponential with rate rho sigma,
+//     sigma = pi E[r^2]; a hit bubble's radius is drawn with weight r^2, the impact point
+//     uniformly over its cross-section, and the outgoing direction follows the exact sphere
+//     optics (reflections and refractions at its surface); at the tile's scale (mm) the
+//     bubble is a point: the encounter does not displace the ray;
+//   * complex Fresnel, Snell and Beer-Lambert as for the other glass; every interaction
+//     draws its own four uniforms on the tile stream;
+//   * a ray leaves through the front face (reflected side) or the back face (transmitted
+//     side) and does not re-enter; more than max_events interactions absorb it.
+struct TileParams {
+  double d_mean, amp, rho;
+  uint32_t seed;
+};
+
+double tile_lattice(uint32_t seed, int ix, int iy, int oct) {
+  uint32_t ctr[4] = {(uint32_t)ix, (uint32_t)iy, (uint32_t)oct, seed};
+  uint32_t key[2] = {0x5EED7113u, 0u};
+  uint32_t o[4];
+  philox4x32_10(ctr, key, o);
+  return u01(o[0]);
+}
+
+double tile_value_noise(uint32_t seed, double x, double y, double L, int cells, int oct) {
+  double gx = x / L * cells, gy = y / L * cells;
+  double fx0 = std::floor(gx), fy0 = std::floor(gy);
+  double fx = gx - fx0, fy = gy - fy0;
+  int ix = ((int)fx0 % cells + cells) % cells, iy = ((int)fy0 % cells + cells) % cells;
+  int jx = (ix + 1) % cells, jy = (iy + 1) % cells;
+  double sx = fx * fx * (3.0 - 2.0 * fx), sy = fy * fy * (3.0 - 2.0 * fy);
+  double a = tile_lattice(seed, ix, iy, oct), b = tile_lattice(seed, jx, iy, oct);
+  double c = tile_lattice(seed, ix, jy, oct), d = tile_lattice(seed, jx, jy, oct);
+  return (1 - sy) * ((1 - sx) * a + sx * b) + sy * ((1 - sx) * c + sx * d);
+}
+
+double tile_thickness(const TileParams& tp, double x, double y, double L) {
+  double n = (2.0 / 3.0) * tile_value_noise(tp.seed, x, y, L, 10, 0) +
+             (1.0 / 3.0) * tile_value_noise(tp.seed, x, y, L, 20, 1);
+  double h = tp.d_mean + tp.amp * (n - 0.5);
+  return std::min(0.005, std::max(0.002, h));
+}
+
+struct TileGeom {
+  int G;
+  double L;
+  const double* h;  // [(G+1) * (G+1)] thickness at the grid vertices, row j, column i
+  double hmin, hmax;
+};
+
+// Back-face triangles of cell (ci, cj) in unwrapped cell coordinates.
+void tile_cell_tris(const TileGeom& g, long ci, long cj, V3 tri[2][3]) {
+  long wi = ((ci % g.G) + g.G) % g.G, wj = ((cj % g.G) + g.G) % g.G;
+  double cs = g.L / g.G;
+  double x0 = ci * cs, y0 = cj * cs;
+  auto H = [&](long i, long j) { return g.h[(size_t)j * (g.G + 1) + i]; };
+  V3 p00{x0, y0, -H(wi, wj)}, p10{x0 + cs, y0, -H(wi + 1, wj)};
+  V3 p01{x0, y0 + cs, -H(wi, wj + 1)}, p11{x0 + cs, y0 + cs, -H(wi + 1, wj + 1)};
+  tri[0][0] = p00; tri[0][1] = p10; tri[0][2] = p11;
+  tri[1][0] = p00; tri[1][1] = p11; tri[1][2] = p01;
+}
+
+// First hit of the back face along o + t d, t in (0, t_max], walking the grid cells the
+// ray's xy projection crosses (at most max_cells).  Returns t or -1; n_out = unit normal
+// of the hit triangle pointing into the glass (+z side).
+double tile_back_hit(const TileGeom& g, V3 o, V3 d, double t_max, int max_cells, V3* n_out) {
+  double cs = g.L / g.G;
+  long ci = (long)std::floor(o.x / cs), cj = (long)std::floor(o.y / cs);
+  int sx = d.x > 0 ? 1 : (d.x < 0 ? -1 : 0), sy = d.y > 0 ? 1 : (d.y < 0 ? -1 : 0);
+  double tdx = sx ? cs / std::fabs(d.x) : INF, tdy = sy ? cs / std::fabs(d.y) : INF;
+  double tx = sx > 0 ? ((ci + 1) * cs - o.x) / d.x : (sx < 0 ? (ci * cs - o.x) / d.x : INF);
+  double ty = sy > 0 ? ((cj + 1) * cs - o.y) / d.y : (sy < 0 ? (cj * cs - o.y) / d.y : INF);
+  double t_in = 0.0;
+  for (int step = 0; step < max_cells && t_in <= t_max; ++step) {
+    double t_out = std::min(std::min(tx, ty), t_max);
+    double z0 = o.z + d.z * t_in, z1 = o.z + d.z * t_out;
+    if (std::min(z0, z1) <= -g.hmin) {  // the ray reaches the band of the back face here
+      V3 tri[2][3];
+      tile_cell_tris(g, ci, cj, tri);
+      double best = -1.0;
+      V3 bn{0, 0, 1};
+      for (int k = 0; k < 2; ++k) {
+        double t;
+        if (ray_triangle(o, d, tri[k][0], tri[k][1], tri[k][2], &t) && t > 0.0 && t <= t_max &&
+            (best < 0.0 || t < best)) {
+          best = t;
+          bn = normalize(cross(tri[k][1] - tri[k][0], tri[k][2] - tri[k][0]));
+        }
+      }
+      if (best >= 0.0) {
+        if (bn.z < 0) bn = -1.0 * bn;
+        *n_out = bn;
+        return best;
+      }
+    }
+    if (tx < ty) { ci += sx; t_in = tx; tx += tdx; }
+    else { cj += sy; t_in = ty; ty += tdy; }
+  }
+  return -1.0;
+}
+
+struct TileRay {
+  int side;     // 0 reflected (front), 1 transmitted (back), 2 absorbed (event cap)
+  double w;     // throughput
+  V3 dir;       // exit direction (tile frame)
+  int bubbles;  // bubble encounters
+  int events;
+};
+
+// Trace one ray through the tile.  (x0, y0): entry point; d: direction in the tile frame
+// (d.z < 0 enters through the front, d.z > 0 through the back); draws are keyed
+// (pixel, sample, bounce<<16 | 2<<8 | event, lam).
+TileRay tile_trace(const TileGeom& g, const TileParams& tp, double x0, double y0, V3 d, double n, double k,
+                   double lambda_nm, uint32_t px, uint32_t sample, uint32_t bounce, uint32_t lam, uint64_t seed,
+                   int max_events, uint32_t stream = STREAM_TILE) {
+  const double eps = 1e-7, r_lo = 10e-6, r_hi = 100e-6;
+  const double Er2 = (r_hi * r_hi - r_lo * r_lo) / (2.0 * std::log(r_hi / r_lo));
+  const double sig = tp.rho * PI * Er2;  // bubble encounters per metre
+  const double alpha = 4.0 * PI * k / (lambda_nm * 1e-9);
+  TileRay out{2, 0.0, d, 0, 0};
+  const V3 d_in = d;
+  double w = 1.0;
+  int e = 0;
+  auto next_u = [&]() { return draw(px, sample, bounce, stream, (uint32_t)(e++ & 0xFF), lam, seed); };
+  // entry interface: air -> glass at the front plane or the back face below the entry point
+  V3 p, nrm;
+  if (d.z < 0) {
+    p = {x0, y0, 0.0};
+    nrm = {0, 0, 1};
+  } else {
+    // start below the back face on the vertical through the entry point and walk along d
+    V3 nb;
+    V3 o2 = {x0, y0, -g.hmax - 1e-4};
+    double t2 = tile_back_hit(g, o2, d, 1.0, 4096, &nb);
+    if (t2 < 0) { out.side = 1; out.w = 1.0; out.dir = d; return out; }  // passed under the tile
+    p = o2 + t2 * d;
+    nrm = -1.0 * nb;  // facing the incoming ray (below)
+  }
+  bool in_glass = false;
+  for (;;) {
+    if (e >= max_events) { out.side = 2; out.w = w; out.events = e; return out; }
+    // interface at p with normal nrm facing the incoming ray
+    double cos_i = -dot(d, nrm);
+    Draw u = next_u();
+    double n1 = in_glass ? n : 1.0;
+    cd n2 = in_glass ? cd(1.0, 0.0) : cd(n, k);
+    double R = fresnel_R(cos_i, n1, n2);
+    double eta = n1 / std::real(n2);
+    double c2 = 1.0 - eta * eta * (1.0 - cos_i * cos_i);
+    if (u.u[0] < R || c2 <= 0.0) {
+      d = reflect(d, nrm);
+    } else {
+      d = normalize(eta * d + (eta * cos_i - std::sqrt(c2)) * nrm);
+      in_glass = !in_glass;
+    }
+    if (!in_glass) {  // left the glass (or never entered): reflected if back on the incident side
+      out.side = ((d.z > 0) == (d_in.z < 0)) ? 0 : 1;
+      out.w = w;
+      out.dir = d;
+      out.events = e;
+      return out;
+    }
+    p = p + (dot(d, nrm) >= 0 ? eps : -eps) * nrm;  // step off the surface into the glass
+    // the segment inside the glass: front plane, back face, or a bubble
+    for (;;) {
+      if (e >= max_events) { out.side = 2; out.w = w; out.events = e; return out; }
+      Draw us = next_u();
+      double t_front = d.z > 0 ? -p.z / d.z : INF;
+      V3 nb{0, 0, 1};
+      double t_back = tile_back_hit(g, p, d, std::min(t_front, 1.0), 4096, &nb);
+      double t_surf = t_back >= 0 ? t_back : t_front;
+      double t_bub = sig > 0 ? -std::log(1.0 - us.u[0]) / sig : INF;
+      if (!(t_surf < INF) && !(t_bub < INF)) { out.side = 2; out.w = w; out.events = e; return out; }
+      if (t_bub < t_surf) {
+        // bubble encounter: exact sphere optics, then continue in the glass (the bubble is
+        // not geometry: nothing of it can be hit again)
+        p = p + t_bub * d;
+        w *= std::exp(-alpha * t_bub);
+        out.bubbles++;
+        double r = std::sqrt(r_lo * r_lo + us.u[1] * (r_hi * r_hi - r_lo * r_lo));
+        double sin_i = std::sqrt(us.u[2]);  // impact parameter / r, uniform over the disc
+        double cos_i0 = std::sqrt(std::max(0.0, 1.0 - sin_i * sin_i));
+        V3 t1, t2;
+        onb(d, &t1, &t2);
+        double phi = 2.0 * PI * us.u[3];
+        V3 rad = std::cos(phi) * t1 + std::sin(phi) * t2;
+        // the sphere in its own frame: q is the current point relative to the centre
+        V3 q = r * ((-cos_i0) * d + sin_i * rad);  // entry point (outward normal q / r)
+        bool inside = false;                          // inside the bubble (air)
+        for (;;) {
+          if (e >= max_events) { out.side = 2; out.w = w; out.events = e; return out; }
+          Draw ub = next_u();
+          V3 nn = (1.0 / r) * q;
+          double ci = std::fabs(dot(d, nn));
+          V3 nf = dot(d, nn) < 0 ? nn : -1.0 * nn;  // facing the incoming ray
+          double m1 = inside ? 1.0 : n;
+          cd m2 = inside ? cd(n, k) : cd(1.0, 0.0);
+          double Rb = fresnel_R(ci, m1, m2);
+          double et = m1 / std::real(m2);
+          double cc = 1.0 - et * et * (1.0 - ci * ci);
+          if (ub.u[0] < Rb || cc <= 0.0) {
+            d = reflect(d, nf);
+          } else {
+            d = normalize(et * d + (et * ci - std::sqrt(cc)) * nf);
+            inside = !inside;
+          }
+          if (!inside) break;           // back in the glass, leaving the sphere
+          q = q + (-2.0 * dot(q, d)) * d;  // across the chord to the next point on the sphere
+        }
+        // bubbles (<= 100 um) are point scatterers at the scale of the tile: the ray leaves
+        // the encounter where it met it, with the direction the sphere optics gave
+        continue;
+      }
+      // surface hit
+      p = p + t_surf * d;
+      w *= std::exp(-alpha * t_surf);
+      nrm = t_back >= 0 ? nb : V3{0, 0, -1};  // normal facing the ray arriving from the glass
+      // re-wrap the position into the base tile
+      p.x -= g.L * std::floor(p.x / g.L);
+      p.y -= g.L * std::floor(p.y / g.L);
+      break;
+    }
+  }
+}
+
 struct Scene {
   std::vector<V3> v0, v1, v2, nrm;  // per triangle, and unit geometric normal
   std::vector<int> mat;
@@ -243,7 +476,25 @@ struct Scene {
   V3 sun_dir{0, 0, 1};
   double sun_h = 0.0;            // 1 - cos(sun half-angle)
   double eps = 1e-5;             // origin offset along the geometric normal (m)
+  // heterogeneous tiles: per material the tile index (-1 for other kinds)
+  std::vector<int> mat_tile;
+  std::vector<TileParams> tiles;
+  std::vector<std::vector<double>> tile_h;  // per tile, (G+1)^2 vertex thicknesses
+  std::vector<TileGeom> tile_geom;
+  int tile_G = 64;
+  double tile_L = 0.1;
 };
+
+// Tile-frame coordinates of a hit: the tile's front face is the +n side of the geometric
+// normal; (t1, t2) = Duff basis of n; positions wrap with the tile period.
+void tile_frame(const Scene& s, V3 p, V3 n, V3 d, double* x, double* y, V3* dl, V3* t1, V3* t2) {
+  onb(n, t1, t2);
+  double a = dot(p, *t1), b = dot(p, *t2);
+  *x = a - s.tile_L * std::floor(a / s.tile_L);
+  *y = b - s.tile_L * std::floor(b / s.tile_L);
+  *dl = {dot(d, *t1), dot(d, *t2), dot(d, n)};
+}
+const double kCos1Deg = 0.99984769515639124;
 
 int build_node(Scene& s, std::vector<int>& idx, int first, int count,
                const std::vector<V3>& cen) {
@@ -305,7 +556,12 @@ Hit closest(const Scene& s, V3 o, V3 d) {
 
 // Transmittance of a shadow ray to infinity: thin-slab tiles multiply their slab
 // transmittance, anything else blocks it (returns 0).
-void shadow_rec(const Scene& s, int ni, V3 o, V3 d, int lam, double lambda_nm, double& T) {
+struct ShadowKey {
+  uint32_t px, sample, bounce;
+  uint64_t seed;
+};
+
+void shadow_rec(const Scene& s, int ni, V3 o, V3 d, int lam, double lambda_nm, const ShadowKey& key, double& T) {
   if (T == 0.0) return;
   const BNode& nd = s.nodes[ni];
   if (!ray_box(o, d, nd.box, 0.0, INF)) return;
@@ -320,6 +576,17 @@ void shadow_rec(const Scene& s, int ni, V3 o, V3 d, int lam, double lambda_nm, d
         double Rs, Ts;
         slab_RT(cos_i, m.n[lam], m.k[lam], m.thickness, lambda_nm, &Rs, &Ts);
         T *= Ts;
+      } else if (m.kind == MAT_TILE) {
+        // one brute-force ray through the tile: it counts only if it leaves on the far side
+        // within 1 degree of the shadow direction (ballistic), with its throughput
+        int ti = s.mat_tile[s.mat[t]];
+        double x, y;
+        V3 dl, t1, t2;
+        tile_frame(s, o + th * d, s.nrm[t], d, &x, &y, &dl, &t1, &t2);
+        TileRay r = tile_trace(s.tile_geom[ti], s.tiles[ti], x, y, dl, m.n[lam], m.k[lam], lambda_nm, key.px,
+                               key.sample, key.bounce, (uint32_t)lam, key.seed, 64, STREAM_SHADOW_TILE);
+        if (r.side == 1 && dot(r.dir, dl) > kCos1Deg) T *= r.w;
+        else { T = 0.0; return; }
       } else {
         T = 0.0;
         return;
@@ -327,12 +594,12 @@ void shadow_rec(const Scene& s, int ni, V3 o, V3 d, int lam, double lambda_nm, d
     }
     return;
   }
-  shadow_rec(s, nd.left, o, d, lam, lambda_nm, T);
-  shadow_rec(s, nd.right, o, d, lam, lambda_nm, T);
+  shadow_rec(s, nd.left, o, d, lam, lambda_nm, key, T);
+  shadow_rec(s, nd.right, o, d, lam, lambda_nm, key, T);
 }
-double shadow_T(const Scene& s, V3 o, V3 d, int lam, double lambda_nm) {
+double shadow_T(const Scene& s, V3 o, V3 d, int lam, double lambda_nm, const ShadowKey& key = ShadowKey{0, 0, 0, 0}) {
   double T = 1.0;
-  if (!s.nodes.empty()) shadow_rec(s, 0, o, d, lam, lambda_nm, T);
+  if (!s.nodes.empty()) shadow_rec(s, 0, o, d, lam, lambda_nm, key, T);
   return T;
 }
 
@@ -390,7 +657,6 @@ double escape_radiance(const Scene& s, V3 d, int lam, bool sun_counted) {
 V3 offset(const Scene& s, V3 p, V3 n, V3 dir) {
   return dot(dir, n) >= 0.0 ? p + s.eps * n : p - s.eps * n;
 }
-V3 reflect(V3 d, V3 n) { return d - (2.0 * dot(d, n)) * n; }
 // A spawned ray starts eps off the surface along the normal; seen from the new ray, the
 // surface plane lies eps / |n.d| behind its origin.  Absorption lengths inside glass are
 // measured from that plane: l = t_hit + seg0.
@@ -526,7 +792,7 @@ double trace_mc(const RenderCtx& cx, uint32_t px, uint32_t sample, int lam, uint
         V3 wl = cone_dir(s.sun_dir, s.sun_h, un.u[0], un.u[1]);
         double cl = dot(nf, wl);
         if (cl > 0.0) {
-          double T = shadow_T(s, offset(s, p, ng, wl), wl, lam, lambda);
+          double T = shadow_T(s, offset(s, p, ng, wl), wl, lam, lambda, ShadowKey{px, sample, (uint32_t)v, cx.seed});
           double omega = 2.0 * PI * s.sun_h;
           L += thr * m.albedo[lam] / PI * cl * s.sun[lam] * omega * T;
           nee_event = T > 0.0 ? EV_SHADOW_OPEN : EV_SHADOW_BLOCKED;
@@ -535,6 +801,19 @@ double trace_mc(const RenderCtx& cx, uint32_t px, uint32_t sample, int lam, uint
       thr *= m.albedo[lam];
       nd = cosine_dir(nf, u.u[1], u.u[2]);
       sun_counted = true;
+    } else if (m.kind == MAT_TILE) {
+      // heterogeneous tile: one brute-force ray through the tile on the tile stream
+      int ti = s.mat_tile[s.mat[h.prim]];
+      double x, y;
+      V3 dl, t1, t2;
+      tile_frame(s, p, ng, d, &x, &y, &dl, &t1, &t2);
+      TileRay r = tile_trace(s.tile_geom[ti], s.tiles[ti], x, y, dl, m.n[lam], m.k[lam], lambda, px, sample,
+                             (uint32_t)v, (uint32_t)lam, cx.seed, 64);
+      if (r.side == 2) { ph.byte(EV_ABSORB); break; }
+      thr *= r.w;
+      nd = normalize(r.dir.x * t1 + r.dir.y * t2 + r.dir.z * ng);
+      ph.byte(r.side == 0 ? EV_REFLECT : EV_TRANSMIT);
+      if (!(r.side == 1 && dot(r.dir, dl) > kCos1Deg)) sun_counted = false;
     } else {
       ph.byte(EV_ABSORB);
       break;
@@ -559,242 +838,19 @@ double trace_mc(const RenderCtx& cx, uint32_t px, uint32_t sample, int lam, uint
   return L;
 }
 
-// ---------------------------------------------------------------- heterogeneous tiles
-// A medieval glass tile with non-uniform thickness and air micro-bubbles (Sec. 1: "non
-// uniform thickness and ... micro particles of air inside the tiles"; Sec. 6: scattering as
-// future work).  Model (readings, the paper gives none):
-//   * periodic square tile of side L, flat front face z = 0, back face z = -h(x, y);
-//   * h = clamp(d_mean + A (n(x, y) - 1/2), 2 mm, 5 mm) with n = 2/3 v(L/10) + 1/3 v(L/20),
-//     v = value noise with smoothstep interpolation of lattice values drawn from Philox;
-//   * the back face is the G x G triangulated height field through h at the grid vertices;
-//   * bubbles form a Poisson process of density rho in the glass, radii log-uniform in
-//     [10, 100] um: the free path to the next bubble is exponential with rate rho sigma,
-//     sigma = pi E[r^2]; a hit bubble's radius is drawn with weight r^2, the impact point
-//     uniformly over its cross-section, and the outgoing direction follows the exact sphere
-//     optics (reflections and refractions at its surface); at the tile's scale (mm) the
-//     bubble is a point: the encounter does not displace the ray;
-//   * complex Fresnel, Snell and Beer-Lambert as for the other glass; every interaction
-//     draws its own four uniforms on the tile stream;
-//   * a ray leaves through the front face (reflected side) or the back face (transmitted
-//     side) and does not re-enter; more than max_events interactions absorb it.
-struct TileParams {
-  double d_mean, amp, rho;
-  uint32_t seed;
-};
-
-double tile_lattice(uint32_t seed, int ix, int iy, int oct) {
-  uint32_t ctr[4] = {(uint32_t)ix, (uint32_t)iy, (uint32_t)oct, seed};
-  uint32_t key[2] = {0x5EED7113u, 0u};
-  uint32_t o[4];
-  philox4x32_10(ctr, key, o);
-  return u01(o[0]);
-}
-
-double tile_value_noise(uint32_t seed, double x, double y, double L, int cells, int oct) {
-  double gx = x / L * cells, gy = y / L * cells;
-  double fx0 = std::floor(gx), fy0 = std::floor(gy);
-  double fx = gx - fx0, fy = gy - fy0;
-  int ix = ((int)fx0 % cells + cells) % cells, iy = ((int)fy0 % cells + cells) % cells;
-  int jx = (ix + 1) % cells, jy = (iy + 1) % cells;
-  double sx = fx * fx * (3.0 - 2.0 * fx), sy = fy * fy * (3.0 - 2.0 * fy);
-  double a = tile_lattice(seed, ix, iy, oct), b = tile_lattice(seed, jx, iy, oct);
-  double c = tile_lattice(seed, ix, jy, oct), d = tile_lattice(seed, jx, jy, oct);
-  return (1 - sy) * ((1 - sx) * a + sx * b) + sy * ((1 - sx) * c + sx * d);
-}
-
-double tile_thickness(const TileParams& tp, double x, double y, double L) {
-  double n = (2.0 / 3.0) * tile_value_noise(tp.seed, x, y, L, 10, 0) +
-             (1.0 / 3.0) * tile_value_noise(tp.seed, x, y, L, 20, 1);
-  double h = tp.d_mean + tp.amp * (n - 0.5);
-  return std::min(0.005, std::max(0.002, h));
-}
-
-struct TileGeom {
-  int G;
-  double L;
-  const double* h;  // [(G+1) * (G+1)] thickness at the grid vertices, row j, column i
-  double hmin, hmax;
-};
-
-// Back-face triangles of cell (ci, cj) in unwrapped cell coordinates.
-void tile_cell_tris(const TileGeom& g, long ci, long cj, V3 tri[2][3]) {
-  long wi = ((ci % g.G) + g.G) % g.G, wj = ((cj % g.G) + g.G) % g.G;
-  double cs = g.L / g.G;
-  double x0 = ci * cs, y0 = cj * cs;
-  auto H = [&](long i, long j) { return g.h[(size_t)j * (g.G + 1) + i]; };
-  V3 p00{x0, y0, -H(wi, wj)}, p10{x0 + cs, y0, -H(wi + 1, wj)};
-  V3 p01{x0, y0 + cs, -H(wi, wj + 1)}, p11{x0 + cs, y0 + cs, -H(wi + 1, wj + 1)};
-  tri[0][0] = p00; tri[0][1] = p10; tri[0][2] = p11;
-  tri[1][0] = p00; tri[1][1] = p11; tri[1][2] = p01;
-}
-
-// First hit of the back face along o + t d, t in (0, t_max], walking the grid cells the
-// ray's xy projection crosses (at most max_cells).  Returns t or -1; n_out = unit normal
-// of the hit triangle pointing into the glass (+z side).
-double tile_back_hit(const TileGeom& g, V3 o, V3 d, double t_max, int max_cells, V3* n_out) {
-  double cs = g.L / g.G;
-  long ci = (long)std::floor(o.x / cs), cj = (long)std::floor(o.y / cs);
-  int sx = d.x > 0 ? 1 : (d.x < 0 ? -1 : 0), sy = d.y > 0 ? 1 : (d.y < 0 ? -1 : 0);
-  double tdx = sx ? cs / std::fabs(d.x) : INF, tdy = sy ? cs / std::fabs(d.y) : INF;
-  double tx = sx > 0 ? ((ci + 1) * cs - o.x) / d.x : (sx < 0 ? (ci * cs - o.x) / d.x : INF);
-  double ty = sy > 0 ? ((cj + 1) * cs - o.y) / d.y : (sy < 0 ? (cj * cs - o.y) / d.y : INF);
-  double t_in = 0.0;
-  for (int step = 0; step < max_cells && t_in <= t_max; ++step) {
-    double t_out = std::min(std::min(tx, ty), t_max);
-    double z0 = o.z + d.z * t_in, z1 = o.z + d.z * t_out;
-    if (std::min(z0, z1) <= -g.hmin) {  // the ray reaches the band of the back face here
-      V3 tri[2][3];
-      tile_cell_tris(g, ci, cj, tri);
-      double best = -1.0;
-      V3 bn{0, 0, 1};
-      for (int k = 0; k < 2; ++k) {
-        double t;
-        if (ray_triangle(o, d, tri[k][0], tri[k][1], tri[k][2], &t) && t > 0.0 && t <= t_max &&
-            (best < 0.0 || t < best)) {
-          best = t;
-          bn = normalize(cross(tri[k][1] - tri[k][0], tri[k][2] - tri[k][0]));
-        }
-      }
-      if (best >= 0.0) {
-        if (bn.z < 0) bn = -1.0 * bn;
-        *n_out = bn;
-        return best;
-      }
-    }
-    if (tx < ty) { ci += sx; t_in = tx; tx += tdx; }
-    else { cj += sy; t_in = ty; ty += tdy; }
-  }
-  return -1.0;
-}
-
-struct TileRay {
-  int side;     // 0 reflected (front), 1 transmitted (back), 2 absorbed (event cap)
-  double w;     // throughput
-  V3 dir;       // exit direction (tile frame)
-  int bubbles;  // bubble encounters
-  int events;
-};
-
-// Trace one ray through the tile.  (x0, y0): entry point; d: direction in the tile frame
-// (d.z < 0 enters through the front, d.z > 0 through the back); draws are keyed
-// (pixel, sample, bounce<<16 | 2<<8 | event, lam).
-TileRay tile_trace(const TileGeom& g, const TileParams& tp, double x0, double y0, V3 d, double n, double k,
-                   double lambda_nm, uint32_t px, uint32_t sample, uint32_t bounce, uint32_t lam, uint64_t seed,
-                   int max_events) {
-  const double eps = 1e-7, r_lo = 10e-6, r_hi = 100e-6;
-  const double Er2 = (r_hi * r_hi - r_lo * r_lo) / (2.0 * std::log(r_hi / r_lo));
-  const double sig = tp.rho * PI * Er2;  // bubble encounters per metre
-  const double alpha = 4.0 * PI * k / (lambda_nm * 1e-9);
-  TileRay out{2, 0.0, d, 0, 0};
-  const V3 d_in = d;
-  double w = 1.0;
-  int e = 0;
-  auto next_u = [&]() { return draw(px, sample, bounce, STREAM_TILE, (uint32_t)(e++ & 0xFF), lam, seed); };
-  // entry interface: air -> glass at the front plane or the back face below the entry point
-  V3 p, nrm;
-  if (d.z < 0) {
-    p = {x0, y0, 0.0};
-    nrm = {0, 0, 1};
-  } else {
-    // start below the back face on the vertical through the entry point and walk along d
-    V3 nb;
-    V3 o2 = {x0, y0, -g.hmax - 1e-4};
-    double t2 = tile_back_hit(g, o2, d, 1.0, 4096, &nb);
-    if (t2 < 0) { out.side = 1; out.w = 1.0; out.dir = d; return out; }  // passed under the tile
-    p = o2 + t2 * d;
-    nrm = -1.0 * nb;  // facing the incoming ray (below)
-  }
-  bool in_glass = false;
-  for (;;) {
-    if (e >= max_events) { out.side = 2; out.w = w; out.events = e; return out; }
-    // interface at p with normal nrm facing the incoming ray
-    double cos_i = -dot(d, nrm);
-    Draw u = next_u();
-    double n1 = in_glass ? n : 1.0;
-    cd n2 = in_glass ? cd(1.0, 0.0) : cd(n, k);
-    double R = fresnel_R(cos_i, n1, n2);
-    double eta = n1 / std::real(n2);
-    double c2 = 1.0 - eta * eta * (1.0 - cos_i * cos_i);
-    if (u.u[0] < R || c2 <= 0.0) {
-      d = reflect(d, nrm);
-    } else {
-      d = normalize(eta * d + (eta * cos_i - std::sqrt(c2)) * nrm);
-      in_glass = !in_glass;
-    }
-    if (!in_glass) {  // left the glass (or never entered): reflected if back on the incident side
-      out.side = ((d.z > 0) == (d_in.z < 0)) ? 0 : 1;
-      out.w = w;
-      out.dir = d;
-      out.events = e;
-      return out;
-    }
-    p = p + (dot(d, nrm) >= 0 ? eps : -eps) * nrm;  // step off the surface into the glass
-    // the segment inside the glass: front plane, back face, or a bubble
-    for (;;) {
-      if (e >= max_events) { out.side = 2; out.w = w; out.events = e; return out; }
-      Draw us = next_u();
-      double t_front = d.z > 0 ? -p.z / d.z : INF;
-      V3 nb{0, 0, 1};
-      double t_back = tile_back_hit(g, p, d, std::min(t_front, 1.0), 4096, &nb);
-      double t_surf = t_back >= 0 ? t_back : t_front;
-      double t_bub = sig > 0 ? -std::log(1.0 - us.u[0]) / sig : INF;
-      if (!(t_surf < INF) && !(t_bub < INF)) { out.side = 2; out.w = w; out.events = e; return out; }
-      if (t_bub < t_surf) {
-        // bubble encounter: exact sphere optics, then continue in the glass (the bubble is
-        // not geometry: nothing of it can be hit again)
-        p = p + t_bub * d;
-        w *= std::exp(-alpha * t_bub);
-        out.bubbles++;
-        double r = std::sqrt(r_lo * r_lo + us.u[1] * (r_hi * r_hi - r_lo * r_lo));
-        double sin_i = std::sqrt(us.u[2]);  // impact parameter / r, uniform over the disc
-        double cos_i0 = std::sqrt(std::max(0.0, 1.0 - sin_i * sin_i));
-        V3 t1, t2;
-        onb(d, &t1, &t2);
-        double phi = 2.0 * PI * us.u[3];
-        V3 rad = std::cos(phi) * t1 + std::sin(phi) * t2;
-        // the sphere in its own frame: q is the current point relative to the centre
-        V3 q = r * ((-cos_i0) * d + sin_i * rad);  // entry point (outward normal q / r)
-        bool inside = false;                          // inside the bubble (air)
-        for (;;) {
-          if (e >= max_events) { out.side = 2; out.w = w; out.events = e; return out; }
-          Draw ub = next_u();
-          V3 nn = (1.0 / r) * q;
-          double ci = std::fabs(dot(d, nn));
-          V3 nf = dot(d, nn) < 0 ? nn : -1.0 * nn;  // facing the incoming ray
-          double m1 = inside ? 1.0 : n;
-          cd m2 = inside ? cd(n, k) : cd(1.0, 0.0);
-          double Rb = fresnel_R(ci, m1, m2);
-          double et = m1 / std::real(m2);
-          double cc = 1.0 - et * et * (1.0 - ci * ci);
-          if (ub.u[0] < Rb || cc <= 0.0) {
-            d = reflect(d, nf);
-          } else {
-            d = normalize(et * d + (et * ci - std::sqrt(cc)) * nf);
-            inside = !inside;
-          }
-          if (!inside) break;           // back in the glass, leaving the sphere
-          q = q + (-2.0 * dot(q, d)) * d;  // across the chord to the next point on the sphere
-        }
-        // bubbles (<= 100 um) are point scatterers at the scale of the tile: the ray leaves
-        // the encounter where it met it, with the direction the sphere optics gave
-        continue;
-      }
-      // surface hit
-      p = p + t_surf * d;
-      w *= std::exp(-alpha * t_surf);
-      nrm = t_back >= 0 ? nb : V3{0, 0, -1};  // normal facing the ray arriving from the glass
-      // re-wrap the position into the base tile
-      p.x -= g.L * std::floor(p.x / g.L);
-      p.y -= g.L * std::floor(p.y / g.L);
-      break;
-    }
-  }
-}
-
 }  // namespace
 
 // ================================================================ C entry points
 // Flat arrays in, doubles out.  All pointers are host memory owned by the caller.
+// Deflection-angle bins of the tile statistics: bin b holds angles in [e_b, e_{b+1}).
+constexpr int kTileBins = 8, kTileStatCols = 4 + 2 * kTileBins;
+static int deflection_bin(double c) {
+  static const double edges_deg[kTileBins + 1] = {0, 1, 2, 4, 8, 16, 32, 64, 180};
+  int b = 0;
+  while (b < kTileBins - 1 && c < std::cos(edges_deg[b + 1] * PI / 180.0)) ++b;
+  return b;
+}
+
 extern "C" {
 
 // Philox4x32-10 on n counters (4 words each) under one key (2 words).
@@ -856,6 +912,16 @@ struct OrcScene {
   float sun_half_angle;       // radians; <= 0 means no sun
   const float* sun;           // [n_table] or NULL
   float ray_eps;              // offset of spawned origins along the normal (m)
+  int n_tiles;                // heterogeneous tiles (0 = none)
+  const void* tiles;          // OrcTile[n_tiles]
+  const int32_t* mat_tile;    // [M] tile index of HETERO_TILE materials, -1 otherwise (or NULL)
+  int tile_grid;
+  double tile_size;
+};
+
+struct OrcTile {
+  double d_mean, amp, rho;
+  uint32_t seed;
 };
 
 struct OrcCamera {
@@ -924,6 +990,30 @@ void* orc_scene_create(const OrcScene* d) {
   }
   if (d->n_triangles > 0) build_node(s, idx, 0, d->n_triangles, cen);
   s.order = idx;
+  s.mat_tile.assign(d->n_materials, -1);
+  if (d->n_tiles > 0 && d->tiles && d->mat_tile) {
+    s.mat_tile.assign(d->mat_tile, d->mat_tile + d->n_materials);
+    s.tile_G = d->tile_grid;
+    s.tile_L = d->tile_size;
+    const OrcTile* ot = static_cast<const OrcTile*>(d->tiles);
+    for (int t = 0; t < d->n_tiles; ++t) {
+      TileParams tp{ot[t].d_mean, ot[t].amp, ot[t].rho, ot[t].seed};
+      s.tiles.push_back(tp);
+      std::vector<double> hh((size_t)(s.tile_G + 1) * (s.tile_G + 1));
+      for (int j = 0; j <= s.tile_G; ++j)
+        for (int i = 0; i <= s.tile_G; ++i)
+          hh[(size_t)j * (s.tile_G + 1) + i] = tile_thickness(tp, i * s.tile_L / s.tile_G, j * s.tile_L / s.tile_G, s.tile_L);
+      s.tile_h.push_back(hh);
+    }
+    for (int t = 0; t < d->n_tiles; ++t) {
+      TileGeom g{s.tile_G, s.tile_L, s.tile_h[t].data(), INF, -INF};
+      for (double v : s.tile_h[t]) {
+        g.hmin = std::min(g.hmin, v);
+        g.hmax = std::max(g.hmax, v);
+      }
+      s.tile_geom.push_back(g);
+    }
+  }
   return h;
 }
 
@@ -1060,10 +1150,6 @@ void orc_xyz(int n_px, int n_lambda, const float* lambda_nm, const double* film,
 }
 
 // ---------------------------------------------------------------- tiles
-struct OrcTile {
-  double d_mean, amp, rho;
-  uint32_t seed;
-};
 
 // Thickness at the (G+1) x (G+1) grid vertices of a tile of side L (row j, column i).
 void orc_tile_heights(const OrcTile* t, int G, double L, double* h) {
@@ -1107,6 +1193,9 @@ void orc_tile_trace(const OrcTile* t, int G, double L, const double* h, int n, c
 // through of T, the same two for R about the mirror direction, bubble encounters per ray.
 // Sample s draws its entry points on (s, ray, 0, tile stream, 0) and its interactions on
 // bounce 1.
+// Per-query tile statistics: T, R, absorbed weight and bubbles per ray, then per side the
+// fraction of its weight in each deflection-angle bin (angle to the straight-through or
+// mirror direction; edges 0, 1, 2, 4, 8, 16, 32, 64, 180 degrees).
 void orc_tile_samples(int n_tiles, const OrcTile* tiles, int G, double L, const double* heights, int n_samples,
                       const double* cos_in, const double* phi_in, const double* lambda_nm, const double* n_re,
                       const double* k, const int32_t* tile, int rays, uint64_t seed, int max_events, int n_threads,
@@ -1121,31 +1210,32 @@ void orc_tile_samples(int n_tiles, const OrcTile* tiles, int G, double L, const 
       const OrcTile& ot = tiles[tile[s]];
       TileParams tp{ot.d_mean, ot.amp, ot.rho, ot.seed};
       TileGeom g = make_geom(G, L, heights + (size_t)tile[s] * (G + 1) * (G + 1));
+      // cos_in < 0: the ray enters through the rough back face (travelling toward +z)
       double st = std::sqrt(std::max(0.0, 1.0 - cos_in[s] * cos_in[s]));
       V3 d{st * std::cos(phi_in[s]), st * std::sin(phi_in[s]), -cos_in[s]};
       V3 dm{d.x, d.y, -d.z};
-      double T = 0, R = 0, A = 0, fT = 0, cT = 0, fR = 0, cR = 0, bub = 0;
-      const double cos1 = std::cos(PI / 180.0);
+      double T = 0, R = 0, A = 0, bub = 0, hT[kTileBins] = {}, hR[kTileBins] = {};
       for (int r = 0; r < rays; ++r) {
         Draw ue = draw((uint32_t)s, (uint32_t)r, 0, STREAM_TILE, 0, 0, seed);
         TileRay tr = tile_trace(g, tp, ue.u[0] * L, ue.u[1] * L, d, n_re[s], k[s], lambda_nm[s], (uint32_t)s,
                                 (uint32_t)r, 1, 0, seed, max_events);
         bub += tr.bubbles;
         if (tr.side == 1) {
-          double c = dot(tr.dir, d);
-          T += tr.w; cT += tr.w * c; if (c > cos1) fT += tr.w;
+          T += tr.w;
+          hT[deflection_bin(dot(tr.dir, d))] += tr.w;
         } else if (tr.side == 0) {
-          double c = dot(tr.dir, dm);
-          R += tr.w; cR += tr.w * c; if (c > cos1) fR += tr.w;
+          R += tr.w;
+          hR[deflection_bin(dot(tr.dir, dm))] += tr.w;
         } else {
           A += tr.w;
         }
       }
-      double* o = out + 8 * (size_t)s;
-      o[0] = T / rays; o[1] = R / rays; o[2] = A / rays;
-      o[3] = T > 0 ? fT / T : 0.0; o[4] = T > 0 ? cT / T : 0.0;
-      o[5] = R > 0 ? fR / R : 0.0; o[6] = R > 0 ? cR / R : 0.0;
-      o[7] = bub / rays;
+      double* o = out + kTileStatCols * (size_t)s;
+      o[0] = T / rays; o[1] = R / rays; o[2] = A / rays; o[3] = bub / rays;
+      for (int b = 0; b < kTileBins; ++b) {
+        o[4 + b] = T > 0 ? hT[b] / T : 0.0;
+        o[4 + kTileBins + b] = R > 0 ? hR[b] / R : 0.0;
+      }
     }
   };
   std::vector<std::thread> pool;

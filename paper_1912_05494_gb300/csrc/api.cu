@@ -22,6 +22,8 @@
 #include "persistent.cuh"
 #include "render_kernels.cuh"
 #include "scene_build.h"
+#include "surrogate_render.cuh"
+#include "surrogate_head.cuh"
 #include "sdd_internal.h"
 
 using namespace sdd;
@@ -94,6 +96,17 @@ struct sdd_scene {
   float sun_dir[3] = {0, 0, 1};
   float sun_half = 0.f;
   float eps = 1e-5f;
+  // heterogeneous tiles
+  const sdd_tileset* tiles = nullptr;
+  std::vector<int> mat_tile;           // tile index per material, -1 otherwise
+  std::vector<int> tile_mats;          // the HETERO_TILE materials
+  std::vector<float3> tile_mat_normal; // their first triangle's normal
+  DevArr<int> t_mat_tile, t_tile_mats;
+  DevArr<float3> t_tile_normal;
+  DevArr<uint32_t> tile_queue;
+  DevArr<float> tile_raw, tile_pred, sun_T;
+  unsigned sun_T_version = ~0u;
+  const sdd_surrogate* sun_T_net = nullptr;
   // device scene
   DevArr<Node> nodes;
   DevArr<TriRec> tris;
@@ -140,6 +153,8 @@ struct sdd_scene {
     prim.release();
     t_lambda.release(); t_thick.release(); t_n.release(); t_k.release(); t_alb.release();
     t_sky.release(); t_sun.release(); t_kind.release(); cmf_w.release();
+    t_mat_tile.release(); t_tile_mats.release(); t_tile_normal.release(); tile_queue.release(); tile_raw.release();
+    tile_pred.release(); sun_T.release();
     for (int i = 0; i < 2; ++i) {
       rb_o[i].release(); rb_d[i].release(); rb_info[i].release(); q[i].release(); sq[i].release();
     }
@@ -338,6 +353,17 @@ sdd_status prepare_spectral(sdd_scene* s, int L, const float* lam, cudaStream_t 
   CK(cudaMemcpyAsync(s->t_alb.p, ta.data(), sizeof(float) * M * L, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(s->t_sky.p, sky.data(), sizeof(float) * L, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(s->t_sun.p, sun.data(), sizeof(float) * L, cudaMemcpyHostToDevice, st));
+  if (!s->tile_mats.empty()) {
+    CK(s->t_mat_tile.ensure(M));
+    CK(cudaMemcpyAsync(s->t_mat_tile.p, s->mat_tile.data(), sizeof(int) * M, cudaMemcpyHostToDevice, st));
+    CK(s->t_tile_mats.ensure(s->tile_mats.size()));
+    CK(cudaMemcpyAsync(s->t_tile_mats.p, s->tile_mats.data(), sizeof(int) * s->tile_mats.size(),
+                       cudaMemcpyHostToDevice, st));
+    CK(s->t_tile_normal.ensure(s->tile_mats.size()));
+    CK(cudaMemcpyAsync(s->t_tile_normal.p, s->tile_mat_normal.data(), sizeof(float3) * s->tile_mats.size(),
+                       cudaMemcpyHostToDevice, st));
+  }
+  s->sun_T_version = ~0u;  // the network's sun table depends on the wavelengths
   launch_cmf_table(L, s->t_lambda.p, s->cmf_w.p, st);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));  // host vectors above go out of scope
@@ -427,7 +453,7 @@ sdd_status render_batched(sdd_scene* s, const RenderParams& p, const std::vector
     CK(cudaEventCreate(&s->pev[1]));
   }
   if (!s->d_pc) CK(cudaMalloc(&s->d_pc, sizeof(PersistCtl)));
-  const int grid = persistent_grid(p.stats >= 2);
+  const int grid = persistent_grid(p.stats >= 2, tile_mode(p));
   if (grid <= 0) return fail(SDD_ERR_CUDA, "persistent kernel does not fit on this device");
   PersistBuffers b;
   for (int i = 0; i < 2; ++i) {
@@ -522,7 +548,11 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
   if (o->max_depth < 0 || o->max_depth > 255) return fail(SDD_ERR_ARG, "max_depth must be in [0, 255]");
   if (o->mode == SDD_MODE_DETERMINISTIC && o->max_depth > 10)
     return fail(SDD_ERR_ARG, "deterministic mode supports max_depth <= 10");
-  if (o->use_surrogate) return fail(SDD_ERR_ARG, "use_surrogate is not available in this build");
+  if (o->use_surrogate && !o->surrogate) return fail(SDD_ERR_ARG, "use_surrogate needs opts->surrogate");
+  if (o->use_surrogate && o->batched)
+    return fail(SDD_ERR_ARG, "the network runs between shading and shadow rays: use_surrogate needs batched = 0");
+  if (!s->tile_mats.empty() && o->mode == SDD_MODE_DETERMINISTIC)
+    return fail(SDD_ERR_ARG, "heterogeneous tiles need Monte Carlo mode");
   if (o->n_pixels < 0) return fail(SDD_ERR_ARG, "n_pixels < 0");
   if (o->n_pixels > 0 && !o->pixels) return fail(SDD_ERR_ARG, "pixels is NULL");
   const long long img = (long long)cam->width * cam->height;
@@ -612,6 +642,39 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
   p.n_slots = n_slots;
   p.stats = s->profiling;
   p.path_hash = want_hash ? s->path_hash.p : nullptr;
+  if (!s->tile_mats.empty()) {
+    p.tiles = *tileset_device_view(s->tiles);
+    p.mat_tile = s->t_mat_tile.p;
+    p.use_surrogate = o->use_surrogate ? 1 : 0;
+  }
+  if (p.use_surrogate) {
+    CK(s->tile_queue.ensure(cap));
+    CK(s->tile_raw.ensure(cap * 7));
+    CK(s->tile_pred.ensure(cap * kHeadPred));
+    p.tile_queue = s->tile_queue.p;
+    p.tile_count = &s->d_ctl->tile_hits;
+    p.tile_cap = (int)cap;
+    // network transmittance toward the sun per tile material and wavelength
+    sdd_surrogate* net = const_cast<sdd_surrogate*>(o->surrogate);
+    const int nm = (int)s->tile_mats.size();
+    if (s->sun_T_net != net || s->sun_T_version != surrogate_version(net)) {
+      CK(s->sun_T.ensure(s->mats.size() * (size_t)L));
+      CK(cudaMemsetAsync(s->sun_T.p, 0, sizeof(float) * s->mats.size() * L, st));
+      DevArr<float> raw, pred;
+      CK(raw.ensure((size_t)nm * L * 7));
+      CK(pred.ensure((size_t)nm * L * kHeadPred));
+      launch_sun_queries(p, s->t_tile_mats.p, s->t_tile_normal.p, nm, raw.p, st);
+      CK(surrogate_predict(net, nm * L, raw.p, pred.p, st));
+      launch_sun_table(s->t_tile_mats.p, nm, L, pred.p, s->sun_T.p, st);
+      CK(cudaGetLastError());
+      CK(cudaStreamSynchronize(st));
+      raw.release();
+      pred.release();
+      s->sun_T_net = net;
+      s->sun_T_version = surrogate_version(net);
+    }
+    p.tile_sun_T = s->sun_T.p;
+  }
 
   s->stats = sdd_stats{};
   const int qcap = (int)cap;
@@ -656,6 +719,7 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
       if (r) return r;
       // the closest passes left every count at zero; shade refills q[0] and sq[0]
       CK(cudaMemsetAsync(s->d_ctl, 0, offsetof(Control, error), st));
+      CK(cudaMemsetAsync(&s->d_ctl->tile_hits, 0, sizeof(int), st));
       ShadowBuf sb{s->sb_o.p, s->sb_d.p, s->sb_info.p, qcap};
       ev = s->ev_begin(TK_SHADE, st);
       launch_shade(p, w, n_rays, rc, s->hits.p, rn, s->q[0].p, s->d_ctl->q_count[0], qcap, sb, s->sq[0].p,
@@ -663,6 +727,19 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
       s->ev_end(ev, st);
       CK(cudaGetLastError());
       count_launch(s, TK_SHADE);
+      if (p.use_surrogate) {
+        r = read_ctl(s, st);
+        if (r) return r;
+        const int nt = std::min(s->h_ctl->tile_hits, qcap);
+        if (nt > 0) {
+          launch_tile_inputs(p, w, rc, s->hits.p, s->tile_queue.p, nt, s->tile_raw.p, st);
+          CK(surrogate_predict(const_cast<sdd_surrogate*>(o->surrogate), nt, s->tile_raw.p, s->tile_pred.p, st));
+          launch_tile_apply(p, w, rc, s->hits.p, s->tile_queue.p, nt, s->tile_pred.p, rn, &s->d_ctl->next_rays,
+                            s->q[0].p, s->d_ctl->q_count[0], qcap, s->d_ctl, st);
+          CK(cudaGetLastError());
+          s->stats.launches_total += 7;  // inputs, network (features + 5 layers folded), apply
+        }
+      }
       r = run_shadow_passes(s, p, w, qcap, st);
       if (r) return r;
       n_rays = s->h_ctl->next_rays;
@@ -733,11 +810,12 @@ sdd_status sdd_scene_create(const sdd_scene_desc* d, sdd_scene** out) {
       delete s;
       return fail(SDD_ERR_ARG, "material " + std::to_string(m) + ": unknown kind");
     }
-    if (sm.kind == SDD_MAT_HETERO_TILE) {
+    if (sm.kind == SDD_MAT_HETERO_TILE &&
+        (!d->tiles || sm.tile_param_id < 0 || sm.tile_param_id >= tileset_device_view(d->tiles)->n_tiles)) {
       delete s;
-      return fail(SDD_ERR_ARG, "material " + std::to_string(m) + ": HETERO_TILE is not available in this build");
+      return fail(SDD_ERR_ARG, "material " + std::to_string(m) + ": HETERO_TILE needs desc->tiles and a tile_param_id in range");
     }
-    bool glass = sm.kind == SDD_MAT_DIELECTRIC_SOLID || sm.kind == SDD_MAT_THIN_SLAB;
+    bool glass = sm.kind == SDD_MAT_DIELECTRIC_SOLID || sm.kind == SDD_MAT_THIN_SLAB || sm.kind == SDD_MAT_HETERO_TILE;
     sdd_status v = validate_table("material n", sm.n_lambda, sm.lambda_nm, sm.n, glass);
     if (!v) v = validate_table("material k", sm.n_lambda, sm.lambda_nm, sm.k, glass);
     if (!v) v = validate_table("material albedo", sm.n_lambda, sm.lambda_nm, sm.albedo, sm.kind == SDD_MAT_DIFFUSE);
@@ -770,6 +848,8 @@ sdd_status sdd_scene_create(const sdd_scene_desc* d, sdd_scene** out) {
     hm.thick = sm.thickness_m;
     hm.tile_id = sm.tile_param_id;
     s->mats.push_back(hm);
+    s->mat_tile.push_back(sm.kind == SDD_MAT_HETERO_TILE ? sm.tile_param_id : -1);
+    if (sm.kind == SDD_MAT_HETERO_TILE) s->tile_mats.push_back(m);
   }
   const sdd_illuminant& il = d->illum;
   sdd_status v = validate_table("sky_radiance", il.n_lambda, il.lambda_nm, il.sky_radiance, true);
@@ -838,6 +918,16 @@ sdd_status sdd_scene_create(const sdd_scene_desc* d, sdd_scene** out) {
     int mi = d->material_of_triangle[t];
     std::memcpy(&mf, &mi, 4);
     prim[t] = make_float4((float)(n[0] / l), (float)(n[1] / l), (float)(n[2] / l), mf);
+  }
+  s->tiles = d->tiles;
+  s->tile_mat_normal.assign(s->tile_mats.size(), make_float3(0.f, 0.f, 1.f));
+  {
+    std::vector<int> first(d->n_materials, -1);
+    for (int t = d->n_triangles - 1; t >= 0; --t) first[d->material_of_triangle[t]] = t;
+    for (size_t j = 0; j < s->tile_mats.size(); ++j) {
+      int t = first[s->tile_mats[j]];
+      if (t >= 0) s->tile_mat_normal[j] = make_float3(prim[t].x, prim[t].y, prim[t].z);
+    }
   }
   s->n_tris = d->n_triangles;
   s->n_sub = d->n_subdomains;

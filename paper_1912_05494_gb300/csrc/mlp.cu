@@ -5,14 +5,16 @@
 // future work (Sec. 6).  The brute-force tile tracer (tile.cu) resolves it exactly but is
 // costly at every tile hit; this network learns the tile's BTDF statistics from the
 // tracer's samples:
-//   inputs   cos(theta_in), phi_in, lambda, mean thickness, bubble density, n, k, normalised
-//            to [0, 1]: cos, phi / 2 pi, (lambda - 380) / 400, (d - 2 mm) / 3 mm,
+//   inputs   signed cos(theta_in) (> 0 through the flat front face, < 0 through the rough back),
+//            phi_in, lambda, mean thickness, bubble density, n, k, normalised to [0, 1]:
+//            (cos + 1) / 2, phi / 2 pi, (lambda - 380) / 400, (d - 2 mm) / 3 mm,
 //            rho / 2e10 m^-3, (n - 1.45) / 0.2, (log10 k + 8) / 4
 //   features [sin(2 pi B x), cos(2 pi B x), x, 0 pad] (B: 16 x 7), 48 wide
 //   layers   48 -> 128 -> 128 -> 128 -> 128 -> 16, exact GELU after the hidden layers
-//   outputs  sigmoid of outputs 0..5: T, R, ballistic fraction and mean cosine of T, the
-//            same two of R
-//   loss     mean over the batch of sum_j (p_j - y_j)^2; Adam on FP32 master weights
+//   head     T, R and a two-lobe vMF mixture per side (surrogate_head.cuh)
+//   loss     mean over the batch of (T - y_T)^2 + (R - y_R)^2
+//            + 0.05 [y_T KL(h_T | m_T) + y_R KL(h_R | m_R)], h the tracer's deflection-bin
+//            fractions, m the mixture's mass per bin; Adam on FP32 master weights
 // Weights and activations are BF16, products accumulate in FP32 (mma.sync m16n8k16,
 // fragments loaded with ldmatrix from padded shared-memory tiles).  Parameters are one flat
 // FP32 array: for each layer W [in][out] row-major, then b [out].
@@ -24,6 +26,7 @@
 #include <vector>
 
 #include "../../include/sdd.h"
+#include "surrogate_head.cuh"
 
 namespace sdd {
 sdd_status set_last_error(sdd_status st, const char* msg);
@@ -32,7 +35,7 @@ using namespace sdd;
 
 namespace {
 
-constexpr int kFeat = 48, kHid = 128, kOut = 16, kTargets = 6, kLayers = 5;
+constexpr int kFeat = 48, kHid = 128, kOut = 16, kTargets = kHeadTargets, kPred = kHeadPred, kLayers = 5;
 __host__ __device__ constexpr int layer_in(int l) { return l == 0 ? kFeat : kHid; }
 __host__ __device__ constexpr int layer_out(int l) { return l == kLayers - 1 ? kOut : kHid; }
 constexpr int kRows = 128;    // batch rows per block
@@ -107,7 +110,7 @@ __global__ void k_features(int n, const float* __restrict__ raw, const float* __
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
   const float* q = raw + 7 * (size_t)r;
-  float x[7] = {q[0], q[1] * 0.15915494309189535f, (q[2] - 380.f) / 400.f, (q[3] - 2e-3f) / 3e-3f, q[4] / 2e10f,
+  float x[7] = {0.5f * (q[0] + 1.f), q[1] * 0.15915494309189535f, (q[2] - 380.f) / 400.f, (q[3] - 2e-3f) / 3e-3f, q[4] / 2e10f,
                 (q[5] - 1.45f) / 0.2f, (log10f(fmaxf(q[6], 1e-30f)) + 8.f) / 4.f};
   __nv_bfloat16* f = feat + (size_t)r * kFeat;
   for (int i = 0; i < 16; ++i) {
@@ -163,22 +166,61 @@ __global__ void __launch_bounds__(kThreads) k_layer_fwd(int n, const __nv_bfloat
   }
 }
 
-// Loss sum_j (sigmoid(z_j) - y_j)^2 per row; dZ = d(mean loss)/dZ for the output layer.
+// Loss of one row (head and loss in surrogate_head.cuh) and dZ = d(mean loss)/dZ for the
+// output layer.
 __global__ void k_loss(int n, float inv_batch, const float* __restrict__ Z, const float* __restrict__ Y,
                        __nv_bfloat16* __restrict__ dZ, float* loss_sum) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   float l = 0.f;
   if (r < n) {
-    for (int j = 0; j < kOut; ++j) {
-      float g = 0.f;
-      if (j < kTargets) {
-        float p = 1.f / (1.f + expf(-Z[(size_t)r * kOut + j]));
-        float d = p - Y[(size_t)r * kTargets + j];
-        l += d * d;
-        g = 2.f * d * p * (1.f - p) * inv_batch;
-      }
-      dZ[(size_t)r * kOut + j] = __float2bfloat16(g);
+    const float* z = Z + (size_t)r * kOut;
+    const float* y = Y + (size_t)r * kTargets;
+    float g[kOut];
+#pragma unroll
+    for (int j = 0; j < kOut; ++j) g[j] = 0.f;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {  // T, R
+      const float p = head_sigmoid(z[j]);
+      const float d = p - y[j];
+      l += d * d;
+      g[j] = 2.f * d * p * (1.f - p);
     }
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int jw = 2 + 3 * side;
+      const float wt = kLobeWeight * y[side];
+      const float w = head_sigmoid(z[jw]);
+      const float u1 = z[jw + 1] + kLkOffset1, u2 = z[jw + 2] + kLkOffset2;
+      const float k1 = expf(fminf(kLkMax, fmaxf(kLkMin, u1))), k2 = expf(fminf(kLkMax, fmaxf(kLkMin, u2)));
+      const float* h = y + 2 + side * kHeadBins;
+      float F1p = 0.f, F2p = 0.f, dF1p = 0.f, dF2p = 0.f;  // CDFs at the bin's lower edge
+      float gw = 0.f, gk1 = 0.f, gk2 = 0.f;
+      for (int b = 0; b < kHeadBins; ++b) {
+        float F1, F2, dF1, dF2;
+        if (b == kHeadBins - 1) {
+          F1 = F2 = 1.f;
+          dF1 = dF2 = 0.f;
+        } else {
+          const float a = head_bin_a(b + 1);
+          vmf_cdf(a, k1, &F1, &dF1);
+          vmf_cdf(a, k2, &F2, &dF2);
+        }
+        const float P1 = F1 - F1p, P2 = F2 - F2p;
+        const float m = w * P1 + (1.f - w) * P2;
+        const float hb = h[b];
+        l += wt * hb * (logf(hb + kKlDelta) - logf(m + kKlDelta));
+        const float gm = -wt * hb / (m + kKlDelta);
+        gw += gm * (P1 - P2);
+        gk1 += gm * w * (dF1 - dF1p);
+        gk2 += gm * (1.f - w) * (dF2 - dF2p);
+        F1p = F1; F2p = F2; dF1p = dF1; dF2p = dF2;
+      }
+      g[jw] = gw * w * (1.f - w);
+      g[jw + 1] = (u1 > kLkMin && u1 < kLkMax) ? gk1 * k1 : 0.f;
+      g[jw + 2] = (u2 > kLkMin && u2 < kLkMax) ? gk2 * k2 : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < kOut; ++j) dZ[(size_t)r * kOut + j] = __float2bfloat16(g[j] * inv_batch);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
@@ -295,11 +337,17 @@ __global__ void k_weights_bf16(const float* __restrict__ p, __nv_bfloat16* __res
   }
 }
 
+// Predictions [n][8]: T, R, w_T, log kappa_T1, log kappa_T2, w_R, log kappa_R1, log kappa_R2.
 __global__ void k_predict(int n, const float* __restrict__ Z, float* __restrict__ out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n * kTargets) return;
-  int r = i / kTargets, j = i - r * kTargets;
-  out[i] = 1.f / (1.f + expf(-Z[(size_t)r * kOut + j]));
+  if (i >= n * kPred) return;
+  int r = i / kPred, j = i - r * kPred;
+  const float z = Z[(size_t)r * kOut + j];
+  float v;
+  if (j == 3 || j == 6) v = head_log_kappa(z, kLkOffset1);
+  else if (j == 4 || j == 7) v = head_log_kappa(z, kLkOffset2);
+  else v = head_sigmoid(z);
+  out[i] = v;
 }
 
 template <typename T>
@@ -325,6 +373,7 @@ struct sdd_surrogate {
   __nv_bfloat16* dZ[2] = {};                 // [batch][128]
   float* loss = nullptr;
   int step = 0;
+  unsigned version = 0;  // bumped whenever the weights change
   ~sdd_surrogate() {
     cudaFree(params); cudaFree(grads); cudaFree(m); cudaFree(v); cudaFree(Bm); cudaFree(Wb); cudaFree(Wtb);
     cudaFree(feat); cudaFree(Zout); cudaFree(loss);
@@ -400,6 +449,20 @@ cudaError_t backward(sdd_surrogate* s, int n, const float* raw, const float* y, 
 }
 
 }  // namespace
+
+namespace sdd {
+// Predictions [n][8] for raw inputs [n][7], max_batch rows at a time, enqueued on st.
+cudaError_t surrogate_predict(sdd_surrogate* s, int n, const float* raw, float* out, cudaStream_t st) {
+  for (int off = 0; off < n; off += s->max_batch) {
+    int m = std::min(s->max_batch, n - off);
+    cudaError_t e = forward(s, m, raw + 7 * (size_t)off, st);
+    if (e != cudaSuccess) return e;
+    k_predict<<<(m * kPred + 255) / 256, 256, 0, st>>>(m, s->Zout, out + kPred * (size_t)off);
+  }
+  return cudaGetLastError();
+}
+unsigned surrogate_version(const sdd_surrogate* s) { return s->version; }
+}  // namespace sdd
 
 extern "C" {
 
@@ -477,6 +540,7 @@ sdd_status sdd_surrogate_get_params(const sdd_surrogate* s, float* host_out, int
 sdd_status sdd_surrogate_set_params(sdd_surrogate* s, const float* host_in, int n) {
   if (!s || !host_in || n != kParams) return set_last_error(SDD_ERR_ARG, "bad arguments");
   cudaError_t e = cudaMemcpy(s->params, host_in, sizeof(float) * kParams, cudaMemcpyHostToDevice);
+  s->version++;
   if (e == cudaSuccess) {
     k_weights_bf16<<<dim3(16, kLayers), 256>>>(s->params, s->Wb, s->Wtb);
     e = cudaDeviceSynchronize();
@@ -510,6 +574,7 @@ sdd_status sdd_surrogate_train_step(sdd_surrogate* s, int n, const float* raw_de
   const float b1 = 0.9f, b2 = 0.999f;
   const float c1 = 1.f - powf(b1, (float)s->step), c2 = 1.f - powf(b2, (float)s->step);
   k_adam<<<(kParams + 255) / 256, 256, 0, st>>>(kParams, s->params, s->grads, s->m, s->v, lr, b1, b2, 1e-8f, c1, c2);
+  s->version++;
   k_weights_bf16<<<dim3(16, kLayers), 256, 0, st>>>(s->params, s->Wb, s->Wtb);
   e = cudaGetLastError();
   if (e == cudaSuccess && loss_host) {
@@ -527,7 +592,7 @@ sdd_status sdd_surrogate_infer(sdd_surrogate* s, int n, const float* raw_dev, fl
     int m = std::min(s->max_batch, n - off);
     cudaError_t e = forward(s, m, raw_dev + 7 * (size_t)off, st);
     if (e != cudaSuccess) return check(e);
-    k_predict<<<(m * kTargets + 255) / 256, 256, 0, st>>>(m, s->Zout, out_dev + kTargets * (size_t)off);
+    k_predict<<<(m * kPred + 255) / 256, 256, 0, st>>>(m, s->Zout, out_dev + kPred * (size_t)off);
   }
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

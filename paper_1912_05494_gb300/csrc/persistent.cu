@@ -108,7 +108,7 @@ __device__ __forceinline__ void clear_ahead(int (*counts)[kMaxSubdomains], int* 
 
 }  // namespace
 
-template <bool kStats>
+template <bool kStats, int kTM>
 __global__ void __launch_bounds__(kPB) k_persistent_wave(RenderParams p, WaveDesc w, PersistBuffers b,
                                                          PersistCtl* pc, Control* ctl) {
   __shared__ int s_prefix[kMaxSubdomains + 1];
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(kPB) k_persistent_wave(RenderParams p, WaveDes
     // and the rotation moves past the empty pass.  Shadow rays go to the shadow queues.
     for (uint32_t base = blockIdx.x * blockDim.x; base < (uint32_t)n_rays; base += nthreads) {
       int r = (int)(base + threadIdx.x);
-      dev_shade(p, w, r, r < n_rays, b.rb[cur], b.hits, b.rb[1 - cur], &pc->next_rays[par], b.q[1 - qe],
+      dev_shade<kTM>(p, w, r, r < n_rays, b.rb[cur], b.hits, b.rb[1 - cur], &pc->next_rays[par], b.q[1 - qe],
                 pc->qc[(cq + 1) % 3], b.qcap, b.sb, &pc->next_shadow[par], b.sq[se], pc->sqc[sq], b.path_L, ctl);
     }
     cq = (cq + 1) % 3;
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kPB) k_persistent_wave(RenderParams p, WaveDes
         const int j = c0 + (int)threadIdx.x;
         const bool act = j < total;
         const int s = find_subdomain(s_prefix, n_sub, act ? j : 0);
-        dev_shadow<kStats>(p, w, s, j - s_prefix[s], act, nullptr, 0, qp, b.sb, b.path_L, ctl);
+        dev_shadow<kStats, kTM>(p, w, s, j - s_prefix[s], act, nullptr, 0, qp, b.sb, b.path_L, ctl);
       }
       if (!grid_barrier(pc, ctl)) return;
       sq = (sq + 1) % 3;
@@ -201,23 +201,30 @@ __global__ void __launch_bounds__(kPB) k_persistent_wave(RenderParams p, WaveDes
   }
 }
 
-template <bool kStats>
+template <bool kStats, int kTM>
 static int persistent_blocks() {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent_wave<kStats>, kPB, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent_wave<kStats, kTM>, kPB, 0);
   return sms * per_sm;
 }
 
-int persistent_grid(bool stats) { return stats ? persistent_blocks<true>() : persistent_blocks<false>(); }
+// The batched form supports scenes without heterogeneous tiles and with brute-force tiles
+// (the network runs between shading and shadow rays, outside one launch).
+int persistent_grid(bool stats, int tile_mode) {
+  if (tile_mode == 1) return stats ? persistent_blocks<true, 1>() : persistent_blocks<false, 1>();
+  return stats ? persistent_blocks<true, 0>() : persistent_blocks<false, 0>();
+}
 
 cudaError_t launch_persistent_wave(const RenderParams& p, const WaveDesc& w, const PersistBuffers& b, PersistCtl* pc,
                                    Control* ctl, int grid, cudaStream_t st) {
   void* args[] = {(void*)&p, (void*)&w, (void*)&b, (void*)&pc, (void*)&ctl};
-  if (p.stats >= 2)
-    return cudaLaunchCooperativeKernel((const void*)k_persistent_wave<true>, dim3(grid), dim3(kPB), args, 0, st);
-  return cudaLaunchCooperativeKernel((const void*)k_persistent_wave<false>, dim3(grid), dim3(kPB), args, 0, st);
+  const void* fn;
+  const int tm = tile_mode(p);
+  if (tm == 1) fn = p.stats >= 2 ? (const void*)k_persistent_wave<true, 1> : (const void*)k_persistent_wave<false, 1>;
+  else fn = p.stats >= 2 ? (const void*)k_persistent_wave<true, 0> : (const void*)k_persistent_wave<false, 0>;
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPB), args, 0, st);
 }
 
 }  // namespace sdd

@@ -26,7 +26,7 @@ struct PersistCtl {
   int pad;
 };
 
-int persistent_grid(bool stats);
+int persistent_grid(bool stats, int tile_mode);
 cudaError_t launch_persistent_wave(const RenderParams& p, const WaveDesc& w, const PersistBuffers& b, PersistCtl* pc,
                                    Control* ctl, int grid, cudaStream_t st);
 

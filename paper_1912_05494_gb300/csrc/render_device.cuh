@@ -19,6 +19,7 @@
 
 #include "device_math.cuh"
 #include "render_kernels.cuh"
+#include "tile_device.cuh"
 
 namespace sdd {
 
@@ -123,6 +124,36 @@ __device__ __forceinline__ int stage_top(const DevScene& sc, Node* s_nodes, int 
   return n;
 }
 
+__device__ __forceinline__ TileDev tile_of(const TileSetDev& ts, int t) {
+  TileDev g;
+  g.h = ts.heights + (size_t)t * (ts.G + 1) * (ts.G + 1);
+  g.hmin = __ldg(ts.hmin + t);
+  g.hmax = __ldg(ts.hmax + t);
+  g.rho = __ldg(ts.rho + t);
+  g.G = ts.G;
+  g.L = ts.L;
+  return g;
+}
+
+// Tile frame of a hit: front face on the +n side of the geometric normal, (t1, t2) its Duff
+// basis, positions wrapped with the tile period.
+__device__ __forceinline__ void tile_frame(float L, float3 p, float3 n, float3 d, float* x, float* y, float3* dl,
+                                           float3* t1, float3* t2) {
+  onb(n, t1, t2);
+  float a = dot3(p, *t1), b = dot3(p, *t2);
+  *x = a - L * floorf(a / L);
+  *y = b - L * floorf(b / L);
+  *dl = make_float3(dot3(d, *t1), dot3(d, *t2), dot3(d, n));
+}
+
+constexpr float kCos1Deg = 0.99984769515639124f;
+constexpr int kTileEvents = 64;
+
+struct ShadowKey {
+  uint32_t pixel, sample, bounce;
+  uint64_t seed;
+};
+
 // Closest hit in (t0, t1] against subdomain s's BVH.  Ties in t go to the lower primitive.
 template <bool kStats>
 __device__ __forceinline__ uint32_t closest_hit(const DevScene& sc, const Node* s_nodes, int n_staged, int s,
@@ -182,11 +213,12 @@ __device__ __forceinline__ uint32_t closest_hit(const DevScene& sc, const Node* 
 
 // Transmittance of a shadow ray across subdomain s over (t0, t1]: thin-slab tiles
 // multiply their slab transmittance; anything else blocks (returns 0).
-template <bool kStats>
-__device__ __forceinline__ float shadow_T(const DevScene& sc, const DevSpectral& sp, int lam, float lambda_nm,
-                                          const Node* s_nodes, int n_staged, int s, const RayPre& rp, float3 d,
-                                          float t0, float t1, uint32_t* n_nodes, uint32_t* n_tris,
-                                          bool* overflow) {
+// kTM: heterogeneous-tile mode of the scene: 0 none, 1 brute-force tile tracing, 2 network.
+template <bool kStats, int kTM>
+__device__ __forceinline__ float shadow_T(const RenderParams& p, const DevScene& sc, const DevSpectral& sp, int lam,
+                                          float lambda_nm, const ShadowKey& key, const Node* s_nodes, int n_staged,
+                                          int s, const RayPre& rp, float3 d, float t0, float t1, uint32_t* n_nodes,
+                                          uint32_t* n_tris, bool* overflow) {
   int stack[kStackSize];
   int spn = 0;
   const int root = sc.root[s];
@@ -213,13 +245,32 @@ __device__ __forceinline__ float shadow_T(const DevScene& sc, const DevSpectral&
             uint32_t prim = __float_as_uint(v0.w);
             float4 nm = __ldg(sc.prim_nrm_mat + prim);
             int mat = __float_as_int(nm.w);
-            if (__ldg(sp.mat_kind + mat) != MAT_SLAB) return 0.f;
-            float cos_i = fabsf(dot3(d, f3(nm)));
+            int kind = __ldg(sp.mat_kind + mat);
             size_t mi = (size_t)mat * sp.n_lambda + lam;
-            float Rs, Ts;
-            slab_RT(cos_i, __ldg(sp.mat_n + mi), __ldg(sp.mat_k + mi), __ldg(sp.mat_thick + mat), lambda_nm, &Rs,
-                    &Ts);
-            T *= Ts;
+            if (kind == MAT_SLAB) {
+              float cos_i = fabsf(dot3(d, f3(nm)));
+              float Rs, Ts;
+              slab_RT(cos_i, __ldg(sp.mat_n + mi), __ldg(sp.mat_k + mi), __ldg(sp.mat_thick + mat), lambda_nm, &Rs,
+                      &Ts);
+              T *= Ts;
+            } else if (kTM != 0 && kind == MAT_TILE) {
+              if (kTM == 2) {
+                T *= __ldg(p.tile_sun_T + mi);  // network: transmittance x ballistic fraction
+              } else {
+                // one brute-force ray through the tile: counts if it leaves on the far side
+                // within 1 degree of the shadow direction
+                float x, y;
+                float3 dl, t1v, t2v;
+                tile_frame(p.tiles.L, rp.o + t * d, f3(nm), d, &x, &y, &dl, &t1v, &t2v);
+                TileOut r = tile_trace(tile_of(p.tiles, __ldg(p.mat_tile + mat)), x, y, dl, __ldg(sp.mat_n + mi),
+                                       __ldg(sp.mat_k + mi), lambda_nm, key.pixel, key.sample, key.bounce, lam,
+                                       key.seed, kTileEvents, STREAM_SHADOW_TILE);
+                if (r.side == 1 && dot3(r.dir, dl) > kCos1Deg) T *= r.w;
+                else return 0.f;
+              }
+            } else {
+              return 0.f;
+            }
           }
         }
         if (c == 0) h0 = false; else h1 = false;
@@ -382,6 +433,7 @@ __device__ __forceinline__ void dev_traverse(const RenderParams& p, int s, int i
 // Shade ray r of the current generation (every lane of the warp calls this): adds escape
 // and NEE radiance, appends the children to `next` (counter *next_count) and the subdomain
 // queues q, and the shadow ray to sb (counter *shadow_count) and the shadow queues sq.
+template <int kTM>
 __device__ __forceinline__ void dev_shade(const RenderParams& p, const WaveDesc& w, int r, bool active, RayBuf cur,
                                           const float2* __restrict__ hits, RayBuf next, int* next_count, uint32_t* q,
                                           int* q_count, int qcap, ShadowBuf sb, int* shadow_count, uint32_t* sq,
@@ -391,7 +443,8 @@ __device__ __forceinline__ void dev_shade(const RenderParams& p, const WaveDesc&
   bool e0 = false, e1 = false, esh = false;
   float3 o0 = make_float3(0.f, 0.f, 0.f), d0 = o0, o1 = o0, d1 = o0, osh = o0, dsh = o0;
   float thr0 = 0.f, thr1 = 0.f, s00 = 0.f, s01 = 0.f, csh = 0.f;
-  uint32_t meta0 = 0, meta1 = 0, path = 0, slot_sh = 0;
+  uint32_t meta0 = 0, meta1 = 0, path = 0, slot_sh = 0, bounce_sh = 0;
+  bool tile_q = false;  // tile hit deferred to the BTDF network
   if (active) {
     float4 O = cur.o[r], D = cur.d[r];
     uint2 inf = cur.info[r];
@@ -495,6 +548,7 @@ __device__ __forceinline__ void dev_shade(const RenderParams& p, const WaveDesc&
               dsh = wl;
               csh = thr * alb * kInvPi * cl * __ldg(p.sp.sun + lam) * p.sp.sun_omega;
               slot_sh = mc ? 0u : code;
+              bounce_sh = v;
             }
           }
           if (mc) {
@@ -503,6 +557,26 @@ __device__ __forceinline__ void dev_shade(const RenderParams& p, const WaveDesc&
             thr0 = thr * alb;
             meta0 = base_meta | ((flags | FLAG_SUN_COUNTED) << 8);
           }
+        } else if (kTM == 1 && kind == MAT_TILE && mc) {
+          // heterogeneous tile: one brute-force ray through it on the tile stream
+          float x, y;
+          float3 dl, t1v, t2v;
+          tile_frame(p.tiles.L, pt, ng, d, &x, &y, &dl, &t1v, &t2v);
+          TileOut r = tile_trace(tile_of(p.tiles, __ldg(p.mat_tile + mat)), x, y, dl, __ldg(p.sp.mat_n + mi),
+                                 __ldg(p.sp.mat_k + mi), lambda, id.pixel, id.sample, v, lam, p.seed, kTileEvents,
+                                 STREAM_TILE);
+          if (r.side == 2) {
+            hsh = fnv_byte(hsh, EV_ABSORB);
+          } else {
+            hsh = fnv_byte(hsh, r.side == 0 ? EV_REFLECT : EV_TRANSMIT);
+            e0 = true;
+            d0 = normalize3(r.dir.x * t1v + r.dir.y * t2v + r.dir.z * ng);
+            thr0 = thr * r.w;
+            bool keep = r.side == 1 && dot3(r.dir, dl) > kCos1Deg;
+            meta0 = base_meta | ((keep ? flags : (flags & ~FLAG_SUN_COUNTED)) << 8);
+          }
+        } else if (kTM == 2 && kind == MAT_TILE && mc) {
+          tile_q = true;  // surrogate form: shaded after the network has run on all tile hits
         } else {
           if (mc) hsh = fnv_byte(hsh, EV_ABSORB);
         }
@@ -536,7 +610,7 @@ __device__ __forceinline__ void dev_shade(const RenderParams& p, const WaveDesc&
   if (ok) {
     sb.o[pos] = make_float4(osh.x, osh.y, osh.z, 0.f);
     sb.d[pos] = make_float4(dsh.x, dsh.y, dsh.z, csh);
-    sb.info[pos] = make_uint2(path, slot_sh);
+    sb.info[pos] = make_uint2(path, slot_sh | (bounce_sh << 16));
   }
   int ss = ok ? subdomain_of(p.sc, osh) : 0;
   int qpos = warp_append(sq_count, ss, ok);
@@ -544,13 +618,20 @@ __device__ __forceinline__ void dev_shade(const RenderParams& p, const WaveDesc&
     if (qpos < qcap) sq[(size_t)ss * qcap + qpos] = (uint32_t)pos;
     else atomicOr(&ctl->error, ERR_SHADOW_OVERFLOW);
   }
+  if (kTM == 2) {
+    int tpos = warp_append(p.tile_count, 0, tile_q);
+    if (tile_q) {
+      if (tpos < p.tile_cap) p.tile_queue[tpos] = (uint32_t)r;
+      else atomicOr(&ctl->error, ERR_QUEUE_OVERFLOW);
+    }
+  }
 }
 
 
 // ------------------------------------------------------------------------------ shadow
 // Transmittance of shadow-queue entry i of subdomain s toward the sun (every lane of the
 // warp calls this): blocked, handed on to the neighbouring subdomain, or added to its path.
-template <bool kStats>
+template <bool kStats, int kTM>
 __device__ __forceinline__ void dev_shadow(const RenderParams& p, const WaveDesc& w, int s, int i, bool active,
                                            const Node* s_nodes, int n_staged, QueuePair qp, ShadowBuf sb,
                                            float* path_L, Control* ctl) {
@@ -569,8 +650,9 @@ __device__ __forceinline__ void dev_shadow(const RenderParams& p, const WaveDesc
     bool ovf = false;
     if (t1 > t0) {
       RayPre rp = ray_pre(o, d);
-      T = shadow_T<kStats>(p.sc, p.sp, (int)id.lam, __ldg(p.sp.lambda_nm + id.lam), s_nodes, n_staged, s, rp, d, t0,
-                           t1, &nn, &nt, &ovf);
+      ShadowKey key{id.pixel, id.sample, inf.y >> 16, p.seed};
+      T = shadow_T<kStats, kTM>(p, p.sc, p.sp, (int)id.lam, __ldg(p.sp.lambda_nm + id.lam), key, s_nodes, n_staged, s, rp,
+                           d, t0, t1, &nn, &nt, &ovf);
     }
     if (ovf) atomicOr(&ctl->error, ERR_STACK_OVERFLOW);
     bool blocked = !(T > 0.f);
@@ -579,7 +661,7 @@ __device__ __forceinline__ void dev_shadow(const RenderParams& p, const WaveDesc
     if (cross) {
       sb.d[r].w = contrib;
     } else {
-      if (!blocked) path_L[inf.x * (uint32_t)p.n_slots + inf.y] += contrib;
+      if (!blocked) path_L[inf.x * (uint32_t)p.n_slots + (inf.y & 0xFFFFu)] += contrib;
       if (p.path_hash && p.mode == 1)
         p.path_hash[inf.x] = fnv_byte(p.path_hash[inf.x], blocked ? EV_SHADOW_BLOCKED : EV_SHADOW_OPEN);
     }

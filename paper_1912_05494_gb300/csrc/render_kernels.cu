@@ -35,16 +35,17 @@ __global__ void __launch_bounds__(kB) k_traverse(RenderParams p, Sched sch, int 
   dev_traverse<kStats>(p, s, i, i < sch.count[s], s_nodes, n_staged, qp, rb, hits, ctl);
 }
 
+template <int kTM>
 __global__ void __launch_bounds__(kBlock) k_shade(RenderParams p, WaveDesc w, int n_rays, RayBuf cur,
                                                   const float2* __restrict__ hits, RayBuf next, uint32_t* q,
                                                   int* q_count, int qcap, ShadowBuf sb, uint32_t* sq, int* sq_count,
                                                   float* path_L, Control* ctl) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
-  dev_shade(p, w, r, r < n_rays, cur, hits, next, &ctl->next_rays, q, q_count, qcap, sb, &ctl->next_shadow, sq,
-            sq_count, path_L, ctl);
+  dev_shade<kTM>(p, w, r, r < n_rays, cur, hits, next, &ctl->next_rays, q, q_count, qcap, sb, &ctl->next_shadow, sq,
+                 sq_count, path_L, ctl);
 }
 
-template <bool kStats, int kB>
+template <bool kStats, int kB, int kTM>
 __global__ void __launch_bounds__(kB) k_shadow(RenderParams p, WaveDesc w, Sched sch, int top_nodes, QueuePair qp,
                                                    ShadowBuf sb, float* path_L, Control* ctl) {
   extern __shared__ Node s_nodes[];
@@ -53,7 +54,7 @@ __global__ void __launch_bounds__(kB) k_shadow(RenderParams p, WaveDesc w, Sched
   while (s + 1 < sch.n_sub && sch.blk_start[s + 1] <= b) ++s;
   int n_staged = top_nodes > 0 ? stage_top(p.sc, s_nodes, s, top_nodes) : 0;
   int i = (b - sch.blk_start[s]) * blockDim.x + threadIdx.x;
-  dev_shadow<kStats>(p, w, s, i, i < sch.count[s], s_nodes, n_staged, qp, sb, path_L, ctl);
+  dev_shadow<kStats, kTM>(p, w, s, i, i < sch.count[s], s_nodes, n_staged, qp, sb, path_L, ctl);
 }
 
 // ------------------------------------------------------------------------------ film
@@ -202,25 +203,42 @@ void launch_shade(const RenderParams& p, const WaveDesc& w, int n_rays, RayBuf c
                   uint32_t* q, int* q_count, int qcap, ShadowBuf sb, uint32_t* sq, int* sq_count, float* path_L,
                   Control* ctl, cudaStream_t st) {
   if (n_rays <= 0) return;
-  k_shade<<<blocks_for(n_rays, kBlock), kBlock, 0, st>>>(p, w, n_rays, cur, hits, next, q, q_count, qcap, sb, sq,
-                                                         sq_count, path_L, ctl);
+  const int tm = tile_mode(p);
+  if (tm == 1)
+    k_shade<1><<<blocks_for(n_rays, kBlock), kBlock, 0, st>>>(p, w, n_rays, cur, hits, next, q, q_count, qcap, sb, sq,
+                                                              sq_count, path_L, ctl);
+  else if (tm == 2)
+    k_shade<2><<<blocks_for(n_rays, kBlock), kBlock, 0, st>>>(p, w, n_rays, cur, hits, next, q, q_count, qcap, sb, sq,
+                                                              sq_count, path_L, ctl);
+  else
+    k_shade<0><<<blocks_for(n_rays, kBlock), kBlock, 0, st>>>(p, w, n_rays, cur, hits, next, q, q_count, qcap, sb, sq,
+                                                              sq_count, path_L, ctl);
 }
 
-template <int kB>
+template <int kB, int kTM>
 static void launch_shadow_b(const RenderParams& p, const WaveDesc& w, const Sched& sch, int total_blocks,
                             int top_nodes, QueuePair qp, ShadowBuf sb, float* path_L, Control* ctl, cudaStream_t st) {
   size_t smem = (size_t)top_nodes * sizeof(Node);
   if (p.stats >= 2)
-    k_shadow<true, kB><<<total_blocks, kB, smem, st>>>(p, w, sch, top_nodes, qp, sb, path_L, ctl);
+    k_shadow<true, kB, kTM><<<total_blocks, kB, smem, st>>>(p, w, sch, top_nodes, qp, sb, path_L, ctl);
   else
-    k_shadow<false, kB><<<total_blocks, kB, smem, st>>>(p, w, sch, top_nodes, qp, sb, path_L, ctl);
+    k_shadow<false, kB, kTM><<<total_blocks, kB, smem, st>>>(p, w, sch, top_nodes, qp, sb, path_L, ctl);
+}
+
+template <int kTM>
+static void launch_shadow_m(const RenderParams& p, const WaveDesc& w, const Sched& sch, int total_blocks, int block,
+                            int top_nodes, QueuePair qp, ShadowBuf sb, float* path_L, Control* ctl, cudaStream_t st) {
+  if (block == 64) launch_shadow_b<64, kTM>(p, w, sch, total_blocks, top_nodes, qp, sb, path_L, ctl, st);
+  else if (block == 256) launch_shadow_b<256, kTM>(p, w, sch, total_blocks, top_nodes, qp, sb, path_L, ctl, st);
+  else launch_shadow_b<128, kTM>(p, w, sch, total_blocks, top_nodes, qp, sb, path_L, ctl, st);
 }
 
 void launch_shadow(const RenderParams& p, const WaveDesc& w, const Sched& sch, int total_blocks, int block,
                    int top_nodes, QueuePair qp, ShadowBuf sb, float* path_L, Control* ctl, cudaStream_t st) {
-  if (block == 64) launch_shadow_b<64>(p, w, sch, total_blocks, top_nodes, qp, sb, path_L, ctl, st);
-  else if (block == 256) launch_shadow_b<256>(p, w, sch, total_blocks, top_nodes, qp, sb, path_L, ctl, st);
-  else launch_shadow_b<128>(p, w, sch, total_blocks, top_nodes, qp, sb, path_L, ctl, st);
+  const int tm = tile_mode(p);
+  if (tm == 1) launch_shadow_m<1>(p, w, sch, total_blocks, block, top_nodes, qp, sb, path_L, ctl, st);
+  else if (tm == 2) launch_shadow_m<2>(p, w, sch, total_blocks, block, top_nodes, qp, sb, path_L, ctl, st);
+  else launch_shadow_m<0>(p, w, sch, total_blocks, block, top_nodes, qp, sb, path_L, ctl, st);
 }
 
 void launch_film_accum(const RenderParams& p, const WaveDesc& w, const float* path_L, double* film,

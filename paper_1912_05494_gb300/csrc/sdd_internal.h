@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include "tileset.h"
+
 namespace sdd {
 
 constexpr int kMaxSubdomains = 64;
@@ -89,7 +91,8 @@ struct RayBuf {
 struct ShadowBuf {
   float4* o;      // origin xyz, w unused
   float4* d;      // direction xyz, w = contribution carried so far
-  uint2* info;    // x = wave-local path id, y = contribution slot (deterministic mode)
+  uint2* info;    // x = wave-local path id, y = contribution slot (deterministic mode, low 16
+                  // bits) | bounce of the vertex that cast it << 16
   int cap;
 };
 
@@ -100,7 +103,7 @@ struct Control {
   int next_rays;                        // rays written into the next generation buffer
   int next_shadow;                      // shadow rays written this generation
   uint32_t error;
-  int pad;
+  int tile_hits;                        // tile hits queued for the network this generation
   unsigned long long node_visits, tri_tests, shadow_node_visits, shadow_tri_tests;
   unsigned long long rays_closest, rays_shadow, crossings;
 };
@@ -127,6 +130,18 @@ struct RenderParams {
   int n_slots;                 // contribution slots per path (deterministic: 2^(max_depth+1))
   int stats;                   // profiling level
   uint32_t* path_hash;         // wave-local hash per path or nullptr
+  // heterogeneous tiles
+  TileSetDev tiles;            // tile set (heights, ranges, densities), or n_tiles = 0
+  const int* mat_tile;         // [M] tile index of HETERO_TILE materials, -1 otherwise
+  int use_surrogate;           // 1: tile hits are queued for the BTDF network
+  const float* tile_sun_T;     // [M][L] network transmittance x ballistic fraction toward the sun
+  uint32_t* tile_queue;        // ray slots of the generation's tile hits (surrogate form)
+  int* tile_count;
+  int tile_cap;
 };
+
+// Heterogeneous-tile mode compiled into the shading and shadow kernels: 0 the scene has no
+// such tiles, 1 brute-force tracing through them, 2 the BTDF network.
+inline int tile_mode(const RenderParams& p) { return p.tiles.n_tiles > 0 ? (p.use_surrogate ? 2 : 1) : 0; }
 
 }  // namespace sdd

@@ -67,6 +67,18 @@ __device__ __forceinline__ T warp_sum_all(T v) {
   return v;
 }
 
+// Deflection-angle bin of the statistics from the cosine c of the angle: edges 0, 1, 2, 4, 8,
+// 16, 32, 64, 180 degrees (cosines of the inner edges below).
+__device__ __forceinline__ int deflection_bin(float c) {
+  const float ce[kTileBins - 1] = {0.99984769515639124f, 0.99939082701909576f, 0.99756405025982420f,
+                                   0.99026806874157036f, 0.96126169593831889f, 0.84804809615642596f,
+                                   0.43837114678907746f};
+  int b = 0;
+#pragma unroll
+  for (int j = 0; j < kTileBins - 1; ++j) b += c < ce[j] ? 1 : 0;
+  return b;
+}
+
 // One warp per sample; lane l traces rays l, l + 32, ...; statistics reduced across the warp.
 __global__ void k_tile_samples(TileSetDev ts, int n_samples, const float* cos_in, const float* phi_in,
                                const float* lambda_nm, const float* n_re, const float* k, const int32_t* tile, int rays,
@@ -76,29 +88,30 @@ __global__ void k_tile_samples(TileSetDev ts, int n_samples, const float* cos_in
   if (warp >= n_samples) return;  // whole warps leave together
   const int s = warp;
   TileDev g = tile_view(ts, tile[s]);
-  const float ci = cos_in[s];
+  const float ci = cos_in[s];  // < 0: enters through the rough back face
   const float st = sqrtf(fmaxf(0.f, 1.f - ci * ci));
   float sp, cp;
   sincosf(phi_in[s], &sp, &cp);
   const float3 d = make_float3(st * cp, st * sp, -ci);
   const float3 dm = make_float3(d.x, d.y, -d.z);
-  const float cos1 = 0.99984769515639f;  // cos(1 degree)
-  float T = 0.f, R = 0.f, A = 0.f, fT = 0.f, cT = 0.f, fR = 0.f, cR = 0.f, bub = 0.f;
+  float T = 0.f, R = 0.f, A = 0.f, bub = 0.f, hT[kTileBins], hR[kTileBins];
+#pragma unroll
+  for (int b = 0; b < kTileBins; ++b) hT[b] = hR[b] = 0.f;
   for (int r = lane; r < rays; r += 32) {
     float4 ue = draw4((uint32_t)s, (uint32_t)r, 0, STREAM_TILE, 0, 0, seed);
     TileOut tr = tile_trace(g, ue.x * g.L, ue.y * g.L, d, n_re[s], k[s], lambda_nm[s], (uint32_t)s, (uint32_t)r, 1, 0,
                             seed, max_events);
     bub += (float)tr.bubbles;
     if (tr.side == 1) {
-      float c = dot3(tr.dir, d);
       T += tr.w;
-      cT += tr.w * c;
-      if (c > cos1) fT += tr.w;
+      const int b = deflection_bin(dot3(tr.dir, d));
+#pragma unroll
+      for (int j = 0; j < kTileBins; ++j) hT[j] += j == b ? tr.w : 0.f;
     } else if (tr.side == 0) {
-      float c = dot3(tr.dir, dm);
       R += tr.w;
-      cR += tr.w * c;
-      if (c > cos1) fR += tr.w;
+      const int b = deflection_bin(dot3(tr.dir, dm));
+#pragma unroll
+      for (int j = 0; j < kTileBins; ++j) hR[j] += j == b ? tr.w : 0.f;
     } else {
       A += tr.w;
     }
@@ -106,21 +119,23 @@ __global__ void k_tile_samples(TileSetDev ts, int n_samples, const float* cos_in
   T = warp_sum_all(T);
   R = warp_sum_all(R);
   A = warp_sum_all(A);
-  fT = warp_sum_all(fT);
-  cT = warp_sum_all(cT);
-  fR = warp_sum_all(fR);
-  cR = warp_sum_all(cR);
   bub = warp_sum_all(bub);
+#pragma unroll
+  for (int b = 0; b < kTileBins; ++b) {
+    hT[b] = warp_sum_all(hT[b]);
+    hR[b] = warp_sum_all(hR[b]);
+  }
   if (lane == 0) {
-    float* o = out + 8 * (size_t)s;
+    float* o = out + kTileStatCols * (size_t)s;
     o[0] = T / rays;
     o[1] = R / rays;
     o[2] = A / rays;
-    o[3] = T > 0.f ? fT / T : 0.f;
-    o[4] = T > 0.f ? cT / T : 0.f;
-    o[5] = R > 0.f ? fR / R : 0.f;
-    o[6] = R > 0.f ? cR / R : 0.f;
-    o[7] = bub / rays;
+    o[3] = bub / rays;
+#pragma unroll
+    for (int b = 0; b < kTileBins; ++b) {
+      o[4 + b] = T > 0.f ? hT[b] / T : 0.f;
+      o[4 + kTileBins + b] = R > 0.f ? hR[b] / R : 0.f;
+    }
   }
 }
 
@@ -206,6 +221,7 @@ sdd_status sdd_tileset_create(const sdd_tileset_desc* d, sdd_tileset** out) {
   ts->dev.hmin = dmin;
   ts->dev.hmax = dmax;
   ts->dev.rho = drho;
+  ts->dev.d_mean = ts->d_mean;
   ts->dev.n_tiles = n;
   ts->dev.G = G;
   ts->dev.L = d->tile_size_m;

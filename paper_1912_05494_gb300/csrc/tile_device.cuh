@@ -124,9 +124,9 @@ __device__ __forceinline__ float tile_back_hit(const TileDev& g, float3 o, float
 // One ray through the tile from entry point (x0, y0) with direction d in the tile frame
 // (d.z < 0: through the front, d.z > 0: through the back).  Draws keyed (px, sample,
 // bounce | tile stream | event, lam).
-__device__ TileOut tile_trace(const TileDev& g, float x0, float y0, float3 d, float n, float k, float lambda_nm,
+static __device__ inline TileOut tile_trace(const TileDev& g, float x0, float y0, float3 d, float n, float k, float lambda_nm,
                               uint32_t px, uint32_t sample, uint32_t bounce, uint32_t lam, uint64_t seed,
-                              int max_events) {
+                              int max_events, uint32_t stream = STREAM_TILE) {
   const float r_lo = 10e-6f, r_hi = 100e-6f;
   const float Er2 = (r_hi * r_hi - r_lo * r_lo) / (2.f * logf(r_hi / r_lo));
   const float sig = g.rho * 3.14159265358979f * Er2;
@@ -155,7 +155,7 @@ __device__ TileOut tile_trace(const TileDev& g, float x0, float y0, float3 d, fl
   for (;;) {
     if (e >= max_events) break;
     const float cos_i = -dot3(d, nrm);
-    float4 u = draw4(px, sample, bounce, STREAM_TILE, (uint32_t)(e++ & 0xFF), lam, seed);
+    float4 u = draw4(px, sample, bounce, stream, (uint32_t)(e++ & 0xFF), lam, seed);
     const float n1 = in_glass ? n : 1.f;
     const float n2re = in_glass ? 1.f : n, n2im = in_glass ? 0.f : k;
     const float R = fresnel_R(cos_i, n1, n2re, n2im);
@@ -182,7 +182,7 @@ __device__ TileOut tile_trace(const TileDev& g, float x0, float y0, float3 d, fl
         out.events = e;
         return out;
       }
-      float4 us = draw4(px, sample, bounce, STREAM_TILE, (uint32_t)(e++ & 0xFF), lam, seed);
+      float4 us = draw4(px, sample, bounce, stream, (uint32_t)(e++ & 0xFF), lam, seed);
       float t_front = d.z > 0.f ? -p.z / d.z : CUDART_INF_F;
       float3 nb = make_float3(0.f, 0.f, 1.f);
       float t_back = tile_back_hit(g, p, d, fminf(t_front, 1.f), &nb);
@@ -213,7 +213,7 @@ __device__ TileOut tile_trace(const TileDev& g, float x0, float y0, float3 d, fl
             out.events = e;
             return out;
           }
-          float4 ub = draw4(px, sample, bounce, STREAM_TILE, (uint32_t)(e++ & 0xFF), lam, seed);
+          float4 ub = draw4(px, sample, bounce, stream, (uint32_t)(e++ & 0xFF), lam, seed);
           float3 nn = (1.f / r) * q;
           float dn = dot3(d, nn);
           float ci = fabsf(dn);

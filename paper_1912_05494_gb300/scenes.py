@@ -51,6 +51,10 @@ class SceneData:
     n_subdomains: int = 1
     split_axis: int = 0
     info: dict = dataclasses.field(default_factory=dict)
+    tiles: list | None = None      # heterogeneous tile parameters (dicts d_mean, amp, rho, seed)
+    mat_tile: np.ndarray | None = None  # int32 [M] tile index of HETERO_TILE materials, -1 otherwise
+    tile_grid: int = 64
+    tile_size: float = 0.1
 
     @property
     def n_triangles(self) -> int:
@@ -185,7 +189,8 @@ def slab_scene(seed: int = 0):
 def nave_scene(seed: int = 1, cell: float = 0.25, windows_per_wall: int = 12,
                tiles_x: int = 10, tiles_z: int = 20, length: float = 60.0,
                n_subdomains: int = 8, width: int = 1024, height: int = 768, spp: int = 16,
-               max_depth: int = 12, rr_start_depth: int = 3, pier_sides: int = 16):
+               max_depth: int = 12, rr_start_depth: int = 3, pier_sides: int = 16,
+               sills=(6.0,), hetero_tiles: int = 0, tile_seed: int = 3):
     """Procedural nave with stained-glass windows of thin-slab tiles.
 
     Nave 60 m (x) x 12 m (y); walls up to z = 14 m under a semicircular barrel vault
@@ -200,12 +205,12 @@ def nave_scene(seed: int = 1, cell: float = 0.25, windows_per_wall: int = 12,
     wall_h, width_y = 14.0, 12.0
     nx = int(round(length / cell))
     tile = 0.1
-    win_w, win_h, sill = tiles_x * tile, tiles_z * tile, 6.0
+    win_w, win_h = tiles_x * tile, tiles_z * tile
     spacing = length / windows_per_wall
     win_x0 = [spacing * (i + 0.5) - 0.5 * win_w for i in range(windows_per_wall)]
 
     def in_window(x_lo, z_lo):
-        if not (sill - 1e-6 <= z_lo < sill + win_h - 1e-6):
+        if not any(sl - 1e-6 <= z_lo < sl + win_h - 1e-6 for sl in sills):
             return False
         return any(x0 - 1e-6 <= x_lo < x0 + win_w - 1e-6 for x0 in win_x0)
 
@@ -245,12 +250,12 @@ def nave_scene(seed: int = 1, cell: float = 0.25, windows_per_wall: int = 12,
                     mesh.quad((p0[0], p0[1], za), (p1[0], p1[1], za), (p1[0], p1[1], zb),
                               (p0[0], p0[1], zb), STONE)
     # windows: thin-slab tiles (one material each) and lead came
-    n_tiles = 2 * windows_per_wall * tiles_x * tiles_z
+    n_tiles = 2 * len(sills) * windows_per_wall * tiles_x * tiles_z
     tile_mat0 = 2
     tm = tile_mat0
     half_w, half_d = 0.003, 0.005
-    for wall_y in (0.0, width_y):
-        for x0 in win_x0:
+    for wall_y, sill, x0 in [(wy, sl, x) for wy in (0.0, width_y) for sl in sills for x in win_x0]:
+        if True:
             for i in range(tiles_x):
                 for j in range(tiles_z):
                     xa, za = x0 + i * tile, sill + j * tile
@@ -291,6 +296,17 @@ def nave_scene(seed: int = 1, cell: float = 0.25, windows_per_wall: int = 12,
     sky = blackbody_normalised(lam).astype(np.float32)
     elev = math.radians(35.0)
     sun_dir = np.array([0.0, -math.cos(elev), math.sin(elev)], np.float32)
+    tiles = mat_tile = None
+    if hetero_tiles:
+        # heterogeneous tiles: each window tile takes one of the tile set's tiles in turn
+        tiles, tn, tk = tile_set(tile_seed, hetero_tiles)
+        mat_tile = np.full(n_mat, -1, np.int32)
+        ids = np.arange(n_tiles) % hetero_tiles
+        mat_tile[tile_mat0:] = ids
+        kind[tile_mat0:] = MAT_TILE
+        thick[tile_mat0:] = np.array([tiles[i]["d_mean"] for i in ids], np.float32)
+        mat_n[tile_mat0:] = tn[ids]
+        mat_k[tile_mat0:] = tk[ids]
     scene = SceneData(
         vertices=v, indices=t, tri_material=m, mat_kind=kind, mat_thickness=thick,
         table_nm=lam, mat_n=mat_n, mat_k=mat_k, mat_albedo=albedo,
@@ -298,11 +314,64 @@ def nave_scene(seed: int = 1, cell: float = 0.25, windows_per_wall: int = 12,
         sun=(5e4 * sky).astype(np.float32), ray_eps=2e-6 * length,
         n_subdomains=n_subdomains, split_axis=0,
         info={"triangles": int(t.shape[0]), "tiles": n_tiles, "materials": n_mat},
+        tiles=tiles, mat_tile=mat_tile,
     )
     cam = CameraData(pos=(3.0, 6.0, 1.7), look_at=(4.0, 6.0, 1.7), up=(0.0, 0.0, 1.0),
                      vfov_deg=50.0, width=width, height=height)
     spec = RenderSpec(lambda_nm=lam, spp=spp, seed=seed, max_depth=max_depth, mode=RENDER_MC,
                       rr_start_depth=rr_start_depth)
+    return scene, cam, spec
+
+
+def tile_room_scene(seed: int = 2, n_tiles: int = 16, width: int = 48, height: int = 32, spp: int = 4):
+    """A 6 x 6 x 4 m room whose y = 0 wall holds a 1 m x 1 m window of 10 x 10 heterogeneous
+    tiles (tiles drawn from a seeded tile set), lit by the sky and a sun at 35 degrees that
+    shines through the window onto the floor; camera inside looking at the window."""
+    tiles, tn, tk = tile_set(seed, n_tiles)
+    lam = SPECTRAL_GRID_81.copy()
+    mesh = _Mesh()
+    STONE = 0
+    c = 0.25
+    _grid(mesh, (0, 0, 0), (c, 0, 0), (0, c, 0), 24, 24, STONE)                 # floor
+    _grid(mesh, (0, 0, 4), (0, c, 0), (c, 0, 0), 24, 24, STONE)                 # ceiling
+    _grid(mesh, (0, 6, 0), (c, 0, 0), (0, 0, c), 24, 16, STONE)                 # back wall
+    _grid(mesh, (0, 0, 0), (0, 0, c), (0, c, 0), 16, 24, STONE)                 # x = 0
+    _grid(mesh, (6, 0, 0), (0, c, 0), (0, 0, c), 24, 16, STONE)                 # x = 6
+    win = lambda i, j: 10 <= i < 14 and 6 <= j < 10  # noqa: E731  (x in [2.5, 3.5), z in [1.5, 2.5))
+    _grid(mesh, (0, 0, 0), (0, 0, c), (c, 0, 0), 16, 24, STONE, skip=lambda i, j: win(j, i))
+    tm = 1
+    for i in range(10):
+        for j in range(10):
+            xa, za = 2.5 + 0.1 * i, 1.5 + 0.1 * j
+            mesh.quad((xa, 0.0, za), (xa + 0.1, 0.0, za), (xa + 0.1, 0.0, za + 0.1), (xa, 0.0, za + 0.1), tm)
+            tm += 1
+    v, t, m = mesh.arrays()
+    n_mat = tm
+    ids = np.arange(100) % n_tiles
+    kind = np.full(n_mat, MAT_TILE, np.int32)
+    kind[STONE] = MAT_DIFFUSE
+    mat_tile = np.full(n_mat, -1, np.int32)
+    mat_tile[1:] = ids
+    thick = np.zeros(n_mat, np.float32)
+    thick[1:] = [tiles[i]["d_mean"] for i in ids]
+    mat_n = np.ones((n_mat, lam.size), np.float32)
+    mat_k = np.zeros((n_mat, lam.size), np.float32)
+    mat_n[1:] = tn[ids]
+    mat_k[1:] = tk[ids]
+    albedo = np.zeros((n_mat, lam.size), np.float32)
+    albedo[STONE] = 0.5
+    sky = blackbody_normalised(lam).astype(np.float32)
+    elev = math.radians(35.0)
+    scene = SceneData(
+        vertices=v, indices=t, tri_material=m, mat_kind=kind, mat_thickness=thick, table_nm=lam,
+        mat_n=mat_n, mat_k=mat_k, mat_albedo=albedo, sky=sky, sky_mode=1,
+        sun_dir=np.array([0.0, -math.cos(elev), math.sin(elev)], np.float32), sun_half_angle=math.radians(0.2665),
+        sun=(5e4 * sky).astype(np.float32), ray_eps=1e-5, n_subdomains=2, split_axis=0,
+        info={"triangles": int(t.shape[0])}, tiles=tiles, mat_tile=mat_tile,
+    )
+    cam = CameraData(pos=(3.0, 4.5, 1.2), look_at=(3.0, 0.0, 1.6), up=(0.0, 0.0, 1.0), vfov_deg=70.0,
+                     width=width, height=height)
+    spec = RenderSpec(lambda_nm=lam, spp=spp, seed=seed, max_depth=8, mode=RENDER_MC, rr_start_depth=3)
     return scene, cam, spec
 
 
@@ -328,10 +397,12 @@ def tile_set(seed: int = 3, n_tiles: int = 512):
 
 
 def tile_queries(seed: int, n_samples: int, n_tiles: int, tile_n, tile_k):
-    """Seeded surrogate queries: cos(theta_in) ~ U(0, 1], phi_in ~ U[0, 2 pi), lambda uniform on
-    the 81-sample grid, tile uniform; n and k looked up from the tile's tables."""
+    """Seeded surrogate queries: |cos(theta_in)| ~ U(0, 1] with either face equally likely (the
+    sign: > 0 the flat front face, < 0 the rough back), phi_in ~ U[0, 2 pi), lambda uniform on the
+    81-sample grid, tile uniform; n and k looked up from the tile's tables."""
     rng = np.random.default_rng(seed)
-    cos_in = (1.0 - rng.uniform(0.0, 1.0, n_samples)).astype(np.float32)
+    cos_in = (1.0 - rng.uniform(0.0, 1.0, n_samples)) * np.where(rng.uniform(0.0, 1.0, n_samples) < 0.5, 1.0, -1.0)
+    cos_in = cos_in.astype(np.float32)
     phi = rng.uniform(0.0, 2.0 * math.pi, n_samples).astype(np.float32)
     li = rng.integers(0, SPECTRAL_GRID_81.size, n_samples)
     tile = rng.integers(0, n_tiles, n_samples).astype(np.int32)

@@ -45,7 +45,8 @@ class sdd_scene_desc(C.Structure):
     _fields_ = [("n_vertices", C.c_int), ("vertices", C.c_void_p), ("n_triangles", C.c_int),
                 ("indices", C.c_void_p), ("material_of_triangle", C.c_void_p),
                 ("n_materials", C.c_int), ("materials", C.c_void_p), ("illum", sdd_illuminant),
-                ("n_subdomains", C.c_int), ("split_axis", C.c_int), ("ray_epsilon_m", C.c_float)]
+                ("n_subdomains", C.c_int), ("split_axis", C.c_int), ("ray_epsilon_m", C.c_float),
+                ("tiles", C.c_void_p)]
 
 
 class sdd_camera(C.Structure):
@@ -59,7 +60,7 @@ class sdd_render_opts(C.Structure):
                 ("seed", C.c_uint64), ("max_depth", C.c_int), ("mode", C.c_int),
                 ("rr_start_depth", C.c_int), ("use_surrogate", C.c_int), ("batched", C.c_int),
                 ("n_pixels", C.c_int), ("pixels", C.c_void_p), ("wave_paths", C.c_int),
-                ("path_radiance_out", C.c_void_p), ("path_hash_out", C.c_void_p)]
+                ("path_radiance_out", C.c_void_p), ("path_hash_out", C.c_void_p), ("surrogate", C.c_void_p)]
 
 
 class sdd_stats(C.Structure):
@@ -171,8 +172,9 @@ def _c(a, dt):
 
 
 # ----------------------------------------------------------------------------- scene
-def sdd_scene_create(sd, n_subdomains=None, split_axis=None, ray_epsilon_m=None):
-    """Create a device scene from a ``scenes.SceneData``; returns the opaque handle."""
+def sdd_scene_create(sd, n_subdomains=None, split_axis=None, ray_epsilon_m=None, tileset=None):
+    """Create a device scene from a ``scenes.SceneData``; returns the opaque handle.  Scenes
+    with heterogeneous tiles need ``tileset`` (an sdd_tileset handle built from sd.tiles)."""
     keep = []
 
     def P(a, dt):
@@ -196,7 +198,7 @@ def sdd_scene_create(sd, n_subdomains=None, split_axis=None, ray_epsilon_m=None)
         mats[m].k = C.c_void_p(mat_k.ctypes.data + 4 * nt * m)
         mats[m].albedo = C.c_void_p(alb.ctypes.data + 4 * nt * m)
         mats[m].thickness_m = float(sd.mat_thickness[m])
-        mats[m].tile_param_id = 0
+        mats[m].tile_param_id = int(sd.mat_tile[m]) if sd.mat_tile is not None else 0
     d = sdd_scene_desc()
     d.n_vertices = int(sd.vertices.shape[0])
     d.vertices = P(sd.vertices, np.float32)
@@ -217,6 +219,7 @@ def sdd_scene_create(sd, n_subdomains=None, split_axis=None, ray_epsilon_m=None)
     d.n_subdomains = int(sd.n_subdomains if n_subdomains is None else n_subdomains)
     d.split_axis = int(sd.split_axis if split_axis is None else split_axis)
     d.ray_epsilon_m = float(sd.ray_eps if ray_epsilon_m is None else ray_epsilon_m)
+    d.tiles = tileset
     h = C.c_void_p()
     _check(lib().sdd_scene_create(C.byref(d), C.byref(h)))
     return h
@@ -246,7 +249,7 @@ def make_camera(cam) -> sdd_camera:
 
 
 def make_opts(spec, pixels=None, wave_paths=0, batched=0, path_radiance_out=None, path_hash_out=None,
-              use_surrogate=0):
+              use_surrogate=0, surrogate=None):
     keep = []
     o = sdd_render_opts()
     lam = _c(spec.lambda_nm, np.float32)
@@ -268,6 +271,7 @@ def make_opts(spec, pixels=None, wave_paths=0, batched=0, path_radiance_out=None
     o.wave_paths = wave_paths
     o.path_radiance_out = _ptr(path_radiance_out)
     o.path_hash_out = _ptr(path_hash_out)
+    o.surrogate = surrogate.h if surrogate is not None else None
     o._keep = keep
     return o
 
@@ -458,15 +462,22 @@ def sdd_version() -> str:
 
 
 class SceneHandle:
-    """RAII wrapper around an sdd_scene handle."""
+    """RAII wrapper around an sdd_scene handle (and the tile set of its heterogeneous tiles)."""
 
     def __init__(self, sd, **kw):
+        self.tiles = None
+        if sd.tiles:
+            self.tiles = sdd_tileset_create(sd.tiles, sd.tile_grid, sd.tile_size)
+            kw["tileset"] = self.tiles
         self.h = sdd_scene_create(sd, **kw)
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
             sdd_scene_destroy(self.h)
         self.h = None
+        if getattr(self, "tiles", None) is not None and self.tiles.value:
+            sdd_tileset_destroy(self.tiles)
+        self.tiles = None
 
     def __del__(self):
         try:

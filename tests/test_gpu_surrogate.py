@@ -1,7 +1,8 @@
 """The tile-BTDF surrogate on BF16 tensor cores against the FP64 oracle network.
 
 Tolerances (BF16 weights and activations carry 8 significant bits, ~0.4 % per value):
-forward predictions within 2e-2 absolute; loss within 2 % relative; gradients within 5 %
+forward predictions within 2e-2 absolute for the probabilities (T, R, lobe weights) and 6e-2
+for the log concentrations (values up to ~14); loss within 2 % relative; gradients within 5 %
 relative L2 per tensor (the oracle runs on the same BF16-rounded weights in FP64)."""
 import numpy as np
 import pytest
@@ -27,9 +28,25 @@ def bf16(a):
 
 def raw_inputs(seed, n):
     rng = np.random.default_rng(seed)
-    return np.column_stack([rng.uniform(0.01, 1, n), rng.uniform(0, 2 * np.pi, n), rng.uniform(380, 780, n),
+    return np.column_stack([rng.uniform(0.01, 1, n) * rng.choice([-1.0, 1.0], n), rng.uniform(0, 2 * np.pi, n), rng.uniform(380, 780, n),
                             rng.uniform(2.5e-3, 4.5e-3, n), rng.uniform(5e9, 1.5e10, n), rng.uniform(1.5, 1.6, n),
                             np.exp(rng.uniform(np.log(1e-7), np.log(1e-5), n))]).astype(np.float32)
+
+
+def targets(rng, n):
+    """T, R and two histograms (Dirichlet rows) per side."""
+    y = np.zeros((n, M.N_TARGET), np.float32)
+    y[:, 0] = rng.uniform(0.2, 0.9, n)
+    y[:, 1] = rng.uniform(0.0, 0.5, n)
+    y[:, 2:10] = rng.dirichlet(np.full(8, 0.5), n)
+    y[:, 10:18] = rng.dirichlet(np.full(8, 0.5), n)
+    return y
+
+
+def close_predictions(a, b):
+    prob = [0, 1, 2, 5]
+    logk = [3, 4, 6, 7]
+    return np.max(np.abs(a[:, prob] - b[:, prob])) < 2e-2 and np.max(np.abs(a[:, logk] - b[:, logk])) < 6e-2
 
 
 def oracle_params(params):
@@ -47,7 +64,7 @@ def test_gradients_match_the_oracle(sdd, n):
     rng = np.random.default_rng(1)
     params = [(W, rng.normal(0, 0.05, b.shape)) for W, b in params]
     raw = raw_inputs(2, n)
-    y = rng.uniform(0, 1, (n, 6)).astype(np.float32)
+    y = targets(rng, n)
     net = sdd.Surrogate(B, params, max_batch=8192)
     loss, g = net.gradients(torch.from_numpy(raw).cuda(), torch.from_numpy(y).cuda())
     lo, go = M.loss_and_grads(oracle_params(params), oracle_features(raw, B), y.astype(np.float64))
@@ -63,16 +80,16 @@ def test_inference_matches_the_oracle(sdd):
     B, params = S.surrogate_init(7)
     raw = raw_inputs(3, 3000)
     net = sdd.Surrogate(B, params, max_batch=1024)  # several internal batches
-    out = torch.empty((3000, 6), device="cuda")
+    out = torch.empty((3000, 8), device="cuda")
     net.infer(torch.from_numpy(raw).cuda(), out)
     _, _, p = M.forward(oracle_params(params), oracle_features(raw, B))
-    assert np.max(np.abs(out.cpu().numpy() - p)) < 2e-2
+    assert close_predictions(out.cpu().numpy(), p)
 
 
 def test_adam_steps_match_the_oracle(sdd):
     B, params = S.surrogate_init(9)
     raw = raw_inputs(4, 2048)
-    y = np.random.default_rng(5).uniform(0, 1, (2048, 6)).astype(np.float32)
+    y = targets(np.random.default_rng(5), 2048)
     net = sdd.Surrogate(B, params, max_batch=2048)
     r, t = torch.from_numpy(raw).cuda(), torch.from_numpy(y).cuda()
     for _ in range(3):
@@ -96,21 +113,13 @@ def test_adam_steps_match_the_oracle(sdd):
 
 
 def test_training_on_tile_data_reduces_the_loss(sdd):
+    from paper_1912_05494_gb300 import surrogate as SG
     tiles, tn, tk = S.tile_set(3, 64)
-    q = S.tile_queries(6, 65536, len(tiles), tn, tk)
     ts = sdd.TileSetHandle(tiles)
-    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
-    stats = torch.empty((65536, 8), device="cuda")
-    sdd.sdd_tile_generate(ts.h, dev(q["cos_in"]), dev(q["phi_in"]), dev(q["lambda_nm"]), dev(q["n"]), dev(q["k"]),
-                          dev(q["tile"]), 64, 8, 64, stats)
-    d_mean = np.array([t["d_mean"] for t in tiles], np.float32)[q["tile"]]
-    rho = np.array([t["rho"] for t in tiles], np.float32)[q["tile"]]
-    raw = np.column_stack([q["cos_in"], q["phi_in"], q["lambda_nm"], d_mean, rho, q["n"], q["k"]]).astype(np.float32)
-    y = stats[:, [0, 1, 3, 4, 5, 6]].contiguous()
+    raw, y = SG.generate(ts.h, tiles, tn, tk, 65536, seed=6, rays=64)
     B, params = S.surrogate_init(4)
     net = sdd.Surrogate(B, params, max_batch=65536)
-    r = dev(raw)
-    first = net.train_step(r, y, lr=1e-3)
+    first = net.train_step(raw, y, lr=1e-3)
     for _ in range(300):
-        last = net.train_step(r, y, lr=1e-3)
+        last = net.train_step(raw, y, lr=1e-3)
     assert last < 0.3 * first, (first, last)

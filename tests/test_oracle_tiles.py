@@ -120,5 +120,22 @@ def test_tile_samples_statistics(orc):
                            rays=4000, seed=2)
     Rs, Ts = slab_closed_form(1.0, 1.53, 2e-6, 0.0035, 550.0)
     assert abs(out[0, 0] - Ts) < 0.02 and abs(out[0, 1] - Rs) < 0.02
-    assert out[0, 3] == 1.0 and abs(out[0, 4] - 1.0) < 1e-12  # flat: all transmission ballistic
-    assert out[1, 3] < 0.99 and out[1, 7] > 0.05                 # rough, bubbly tile scatters
+    assert out[0, 4] == 1.0 and np.all(out[0, 5:12] == 0.0)   # flat: all transmission within 1 degree
+    assert out[0, 12] == 1.0                                   # and all reflection specular
+    assert out[1, 4] < 0.99 and out[1, 3] > 0.05               # rough, bubbly tile scatters
+    for r in range(2):                                         # each side's bins partition its weight
+        assert abs(out[r, 4:12].sum() - 1.0) < 1e-12 and abs(out[r, 12:20].sum() - 1.0) < 1e-12
+
+
+def test_tile_sample_faces(orc):
+    """A bubble-free tile entered through either face: a flat one is the thin slab both ways
+    (closed form, within Monte Carlo error of 3000 rays), and reflection off the flat front
+    face of a rough tile stays specular while its rough back face spreads it."""
+    tiles = [{"d_mean": 0.0035, "amp": 0.0, "rho": 0.0, "seed": 1}, {"d_mean": 0.0035, "amp": 0.003, "rho": 0.0, "seed": 9}]
+    hs = np.stack([orc.tile_heights(t) for t in tiles])
+    out = orc.tile_samples(tiles, hs, [0.8, -0.8, 0.8, -0.8], [0.4] * 4, [550.0] * 4, [1.53] * 4, [2e-6] * 4,
+                           [0, 0, 1, 1], rays=3000, seed=4)
+    Rs, Ts = slab_closed_form(0.8, 1.53, 2e-6, 0.0035, 550.0)
+    for r in (0, 1):
+        assert abs(out[r, 0] - Ts) < 0.03 and abs(out[r, 1] - Rs) < 0.03 and out[r, 4] == 1.0
+    assert out[2, 12] > out[3, 12] + 0.2   # the flat front face reflects specularly first
