@@ -127,13 +127,15 @@ typedef struct {
   int rr_start_depth;      /* Russian roulette from this interaction on (Monte Carlo) */
   int use_surrogate;       /* heterogeneous tiles: 0 = one brute-force ray through the tile per hit
                               (and per shadow ray); 1 = the BTDF network (opts->surrogate): T, R
-                              and a ballistic + von Mises-Fisher lobe per side at hits, T x
-                              ballistic fraction for shadow rays */
+                              and a two-lobe von Mises-Fisher mixture per side at hits, shaded by
+                              one fused launch per generation; for shadow rays T x the
+                              transmitted mixture's mass within 1 degree of straight through */
   int batched;             /* 0: host-driven wavefront (one launch per subdomain pass, queue counts
-                              read back between launches); 1: one persistent cooperative launch
-                              per wave drains every generation and pass on the device, and the
-                              frame is captured as a CUDA graph and replayed while its parameters
-                              and buffers are unchanged */
+                              read back between launches); 1: a persistent cooperative kernel
+                              drains every pass on the device -- the whole wave in one launch, or
+                              with use_surrogate two launches per generation around the fused
+                              tile shading -- and the frame is captured as a CUDA graph and
+                              replayed while its parameters and buffers are unchanged */
   int n_pixels;            /* 0: whole image; else render only these pixel indices */
   const int32_t* pixels;   /* host [n_pixels] row-major pixel indices (y * width + x) */
   int wave_paths;          /* paths per wave; 0 = automatic */
@@ -141,7 +143,8 @@ typedef struct {
   uint32_t* path_hash_out; /* optional device [pixels][spp][n_lambda] event hash of every path
                               (Monte Carlo; FNV-1a over hit primitives and branch events) */
   const sdd_surrogate* surrogate; /* with use_surrogate = 1: the network that replaces brute-force
-                                     tracing at heterogeneous-tile hits (host-driven form only) */
+                                     tracing at heterogeneous-tile hits; its weights are read at
+                                     render time (a replayed frame uses the current weights) */
 } sdd_render_opts;
 
 /* Build the scene: validates, partitions the geometry into n_subdomains slabs (Sec. 5:
@@ -199,6 +202,8 @@ typedef struct {
   double ms_persistent;    /* batched form: persistent drain kernels (all steps of a wave) */
   int64_t launches_persistent;
   int64_t graph_replays;   /* batched form: frames replayed from a captured CUDA graph */
+  double ms_tile;          /* network form: fused tile-shading launches (host-driven form) */
+  int64_t launches_tile;   /* network form: fused tile-shading launches */
 } sdd_stats;
 
 /* level 0: nothing; 1: CUDA-event timing of every launch; 2: also count BVH nodes and

@@ -83,7 +83,7 @@ double interp_table(const std::vector<float>& grid, const std::vector<float>& va
   return (1.0 - f) * val[i] + f * val[i + 1];
 }
 
-enum TimedKind { TK_RAYGEN = 0, TK_TRAVERSE, TK_SHADE, TK_SHADOW, TK_FILM, TK_COUNT };
+enum TimedKind { TK_RAYGEN = 0, TK_TRAVERSE, TK_SHADE, TK_SHADOW, TK_FILM, TK_TILE, TK_COUNT };
 
 }  // namespace
 
@@ -104,7 +104,7 @@ struct sdd_scene {
   DevArr<int> t_mat_tile, t_tile_mats;
   DevArr<float3> t_tile_normal;
   DevArr<uint32_t> tile_queue;
-  DevArr<float> tile_raw, tile_pred, sun_T;
+  DevArr<float> sun_T;
   unsigned sun_T_version = ~0u;
   const sdd_surrogate* sun_T_net = nullptr;
   // device scene
@@ -153,8 +153,7 @@ struct sdd_scene {
     prim.release();
     t_lambda.release(); t_thick.release(); t_n.release(); t_k.release(); t_alb.release();
     t_sky.release(); t_sun.release(); t_kind.release(); cmf_w.release();
-    t_mat_tile.release(); t_tile_mats.release(); t_tile_normal.release(); tile_queue.release(); tile_raw.release();
-    tile_pred.release(); sun_T.release();
+    t_mat_tile.release(); t_tile_mats.release(); t_tile_normal.release(); tile_queue.release(); sun_T.release();
     for (int i = 0; i < 2; ++i) {
       rb_o[i].release(); rb_d[i].release(); rb_info[i].release(); q[i].release(); sq[i].release();
     }
@@ -196,7 +195,7 @@ struct sdd_scene {
       float ms = 0.f;
       cudaEventElapsedTime(&ms, ev_pool[u.second], ev_pool[u.second + 1]);
       double* dst[TK_COUNT] = {&stats.ms_raygen, &stats.ms_traverse, &stats.ms_shade, &stats.ms_shadow,
-                               &stats.ms_film};
+                               &stats.ms_film, &stats.ms_tile};
       *dst[u.first] += ms;
     }
     ev_used.clear();
@@ -217,7 +216,7 @@ namespace {
 
 void count_launch(sdd_scene* s, int kind) {
   int64_t* dst[TK_COUNT] = {&s->stats.launches_raygen, &s->stats.launches_traverse, &s->stats.launches_shade,
-                            &s->stats.launches_shadow, &s->stats.launches_film};
+                            &s->stats.launches_shadow, &s->stats.launches_film, &s->stats.launches_tile};
   ++*dst[kind];
   ++s->stats.launches_total;
 }
@@ -432,7 +431,18 @@ sdd_status enqueue_batched_frame(sdd_scene* s, const RenderParams& p, const std:
   for (const WaveDesc& w : waves) {
     CK(cudaMemsetAsync(s->d_pc, 0, sizeof(PersistCtl), gs));
     CK(cudaMemsetAsync(s->path_L.p, 0, sizeof(float) * (size_t)w.n_paths * n_slots, gs));
-    CK(launch_persistent_wave(p, w, b, s->d_pc, s->d_ctl, grid, gs));
+    if (!p.use_surrogate) {
+      CK(launch_persistent_wave(p, w, b, s->d_pc, s->d_ctl, grid, gs, SEG_WAVE));
+    } else {
+      // the network runs between shading and the shadow rays of every generation
+      CK(launch_persistent_wave(p, w, b, s->d_pc, s->d_ctl, grid, gs, SEG_RAYGEN));
+      for (int g = 0; g <= p.max_depth + 1; ++g) {
+        CK(cudaMemsetAsync(&s->d_ctl->tile_hits, 0, sizeof(int), gs));
+        CK(launch_persistent_wave(p, w, b, s->d_pc, s->d_ctl, grid, gs, SEG_CLOSEST_SHADE));
+        CK(launch_tile_shade_persistent(p, w, b, s->d_pc, s->d_ctl, o->surrogate, gs));
+        CK(launch_persistent_wave(p, w, b, s->d_pc, s->d_ctl, grid, gs, SEG_SHADOW));
+      }
+    }
     launch_film_accum(p, w, s->path_L.p, s->film.p, o->path_radiance_out, o->path_hash_out, gs);
     CK(cudaGetLastError());
   }
@@ -477,7 +487,7 @@ sdd_status render_batched(sdd_scene* s, const RenderParams& p, const std::vector
   put(&n_slots, sizeof(n_slots));
   for (const WaveDesc& w : waves) put(&w, sizeof(w));
   const void* ptrs[] = {spectral_out, xyz_out, o->path_radiance_out, o->path_hash_out, s->film.p, s->cmf_w.p,
-                        s->d_pc, s->d_ctl};
+                        s->d_pc, s->d_ctl, o->surrogate};
   put(ptrs, sizeof(ptrs));
 
   CK(cudaEventRecord(s->gevent, st));
@@ -516,9 +526,11 @@ sdd_status render_batched(sdd_scene* s, const RenderParams& p, const std::vector
   }
   if (s->profiling >= 1) CK(cudaEventRecord(s->pev[1], s->gstream));
   CK(cudaStreamSynchronize(s->gstream));
-  s->stats.launches_persistent += (int64_t)waves.size();
+  const int64_t per_wave = p.use_surrogate ? 1 + 2 * (int64_t)(p.max_depth + 2) : 1;
+  s->stats.launches_persistent += per_wave * (int64_t)waves.size();
+  if (p.use_surrogate) s->stats.launches_tile += (int64_t)(p.max_depth + 2) * (int64_t)waves.size();
   s->stats.launches_film += (int64_t)waves.size() + 1;
-  s->stats.launches_total += 2 * (int64_t)waves.size() + 1;
+  s->stats.launches_total += (per_wave + (p.use_surrogate ? p.max_depth + 2 : 0) + 1) * (int64_t)waves.size() + 1;
   if (s->profiling >= 1) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, s->pev[0], s->pev[1]);
@@ -549,8 +561,6 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
   if (o->mode == SDD_MODE_DETERMINISTIC && o->max_depth > 10)
     return fail(SDD_ERR_ARG, "deterministic mode supports max_depth <= 10");
   if (o->use_surrogate && !o->surrogate) return fail(SDD_ERR_ARG, "use_surrogate needs opts->surrogate");
-  if (o->use_surrogate && o->batched)
-    return fail(SDD_ERR_ARG, "the network runs between shading and shadow rays: use_surrogate needs batched = 0");
   if (!s->tile_mats.empty() && o->mode == SDD_MODE_DETERMINISTIC)
     return fail(SDD_ERR_ARG, "heterogeneous tiles need Monte Carlo mode");
   if (o->n_pixels < 0) return fail(SDD_ERR_ARG, "n_pixels < 0");
@@ -649,8 +659,6 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
   }
   if (p.use_surrogate) {
     CK(s->tile_queue.ensure(cap));
-    CK(s->tile_raw.ensure(cap * 7));
-    CK(s->tile_pred.ensure(cap * kHeadPred));
     p.tile_queue = s->tile_queue.p;
     p.tile_count = &s->d_ctl->tile_hits;
     p.tile_cap = (int)cap;
@@ -728,17 +736,12 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
       CK(cudaGetLastError());
       count_launch(s, TK_SHADE);
       if (p.use_surrogate) {
-        r = read_ctl(s, st);
-        if (r) return r;
-        const int nt = std::min(s->h_ctl->tile_hits, qcap);
-        if (nt > 0) {
-          launch_tile_inputs(p, w, rc, s->hits.p, s->tile_queue.p, nt, s->tile_raw.p, st);
-          CK(surrogate_predict(const_cast<sdd_surrogate*>(o->surrogate), nt, s->tile_raw.p, s->tile_pred.p, st));
-          launch_tile_apply(p, w, rc, s->hits.p, s->tile_queue.p, nt, s->tile_pred.p, rn, &s->d_ctl->next_rays,
-                            s->q[0].p, s->d_ctl->q_count[0], qcap, s->d_ctl, st);
-          CK(cudaGetLastError());
-          s->stats.launches_total += 7;  // inputs, network (features + 5 layers folded), apply
-        }
+        // the generation's tile hits: inputs, network and exit sampling in one launch
+        ev = s->ev_begin(TK_TILE, st);
+        CK(launch_tile_shade(p, w, rc, s->hits.p, rn, &s->d_ctl->next_rays, s->q[0].p, s->d_ctl->q_count[0], qcap,
+                             s->d_ctl, o->surrogate, st));
+        s->ev_end(ev, st);
+        count_launch(s, TK_TILE);
       }
       r = run_shadow_passes(s, p, w, qcap, st);
       if (r) return r;
@@ -775,7 +778,7 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
   s->stats.bytes_ray_state = s->stats.rays_closest * 44 + s->stats.rays_shadow * 44;
   s->ev_collect();
   s->stats.ms_total = s->stats.ms_raygen + s->stats.ms_traverse + s->stats.ms_shade + s->stats.ms_shadow +
-                      s->stats.ms_film;
+                      s->stats.ms_film + s->stats.ms_tile;
   return SDD_OK;
 }
 

@@ -27,6 +27,7 @@
 
 #include "../../include/sdd.h"
 #include "surrogate_head.cuh"
+#include "surrogate_net.cuh"
 
 namespace sdd {
 sdd_status set_last_error(sdd_status st, const char* msg);
@@ -35,94 +36,19 @@ using namespace sdd;
 
 namespace {
 
-constexpr int kFeat = 48, kHid = 128, kOut = 16, kTargets = kHeadTargets, kPred = kHeadPred, kLayers = 5;
-__host__ __device__ constexpr int layer_in(int l) { return l == 0 ? kFeat : kHid; }
-__host__ __device__ constexpr int layer_out(int l) { return l == kLayers - 1 ? kOut : kHid; }
+using namespace sdd::net;
+constexpr int kTargets = kHeadTargets, kPred = kHeadPred;
 constexpr int kRows = 128;    // batch rows per block
 constexpr int kThreads = 256;  // 8 warps, 16 rows each
-
-__host__ __device__ constexpr int layer_offset(int l) {
-  int o = 0;
-  for (int i = 0; i < l; ++i) o += layer_in(i) * layer_out(i) + layer_out(i);
-  return o;
-}
-constexpr int kParams = layer_offset(kLayers);
-
-// ------------------------------------------------------------------ warp MMA helpers
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void ldmatrix_x4(uint32_t r[4], const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(smem_addr(p)));
-}
-__device__ __forceinline__ void ldmatrix_x2(uint32_t r[2], const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r[0]), "=r"(r[1]) : "r"(smem_addr(p)));
-}
-__device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], const uint32_t b[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-// acc[j] (j = n-tile of 8 columns) += A[16 rows of the warp][0..Kd) * Bt[cols][0..Kd)^T, with
-// A at sa (row stride lda elements) and Bt at sb (row stride ldb elements), both shared memory.
-template <int Kd, int NT>
-__device__ __forceinline__ void warp_gemm(float (*acc)[4], const __nv_bfloat16* sa, int lda, const __nv_bfloat16* sb,
-                                          int ldb) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int kk = 0; kk < Kd; kk += 16) {
-    uint32_t a[4];
-    ldmatrix_x4(a, sa + (lane & 15) * lda + kk + (lane >> 4) * 8);
-#pragma unroll
-    for (int j = 0; j < NT; ++j) {
-      uint32_t b[2];
-      ldmatrix_x2(b, sb + (j * 8 + (lane & 7)) * ldb + kk + ((lane >> 3) & 1) * 8);
-      mma16816(acc[j], a, b);
-    }
-  }
-}
-
-// Copy a [rows][cols] BF16 tile (row-major, `cols` contiguous, cols % 8 == 0) into shared
-// memory with row stride ld; rows beyond `valid` are zero.
-__device__ __forceinline__ void load_tile(__nv_bfloat16* dst, int ld, const __nv_bfloat16* src, int src_ld, int rows,
-                                          int cols, int valid) {
-  const int vec = cols / 8;
-  for (int i = threadIdx.x; i < rows * vec; i += blockDim.x) {
-    int r = i / vec, c = (i - r * vec) * 8;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (r < valid) v = *reinterpret_cast<const uint4*>(src + (size_t)r * src_ld + c);
-    *reinterpret_cast<uint4*>(dst + r * ld + c) = v;
-  }
-}
-
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_grad(float z) {
-  return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * 0.3989422804014327f * expf(-0.5f * z * z);
-}
 
 // ------------------------------------------------------------------ kernels
 __global__ void k_features(int n, const float* __restrict__ raw, const float* __restrict__ Bm,
                            __nv_bfloat16* __restrict__ feat) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
-  const float* q = raw + 7 * (size_t)r;
-  float x[7] = {0.5f * (q[0] + 1.f), q[1] * 0.15915494309189535f, (q[2] - 380.f) / 400.f, (q[3] - 2e-3f) / 3e-3f, q[4] / 2e10f,
-                (q[5] - 1.45f) / 0.2f, (log10f(fmaxf(q[6], 1e-30f)) + 8.f) / 4.f};
-  __nv_bfloat16* f = feat + (size_t)r * kFeat;
-  for (int i = 0; i < 16; ++i) {
-    float p = 0.f;
-    for (int j = 0; j < 7; ++j) p += Bm[i * 7 + j] * x[j];
-    float s, c;
-    sincospif(2.f * p, &s, &c);
-    f[i] = __float2bfloat16(s);
-    f[16 + i] = __float2bfloat16(c);
-  }
-  for (int j = 0; j < 7; ++j) f[32 + j] = __float2bfloat16(x[j]);
-  for (int j = 39; j < kFeat; ++j) f[j] = __float2bfloat16(0.f);
+  float q[kIn];
+  for (int j = 0; j < kIn; ++j) q[j] = raw[(size_t)r * kIn + j];
+  features_row(q, Bm, feat + (size_t)r * kFeat);
 }
 
 // Z = X W + b (X [n][K] bf16, Wt = W^T [N][K] bf16); hidden layers store Z (bf16) and GELU(Z)
@@ -337,19 +263,6 @@ __global__ void k_weights_bf16(const float* __restrict__ p, __nv_bfloat16* __res
   }
 }
 
-// Predictions [n][8]: T, R, w_T, log kappa_T1, log kappa_T2, w_R, log kappa_R1, log kappa_R2.
-__global__ void k_predict(int n, const float* __restrict__ Z, float* __restrict__ out) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n * kPred) return;
-  int r = i / kPred, j = i - r * kPred;
-  const float z = Z[(size_t)r * kOut + j];
-  float v;
-  if (j == 3 || j == 6) v = head_log_kappa(z, kLkOffset1);
-  else if (j == 4 || j == 7) v = head_log_kappa(z, kLkOffset2);
-  else v = head_sigmoid(z);
-  out[i] = v;
-}
-
 template <typename T>
 cudaError_t dalloc(T** p, size_t n) {
   return cudaMalloc(p, sizeof(T) * (n > 0 ? n : 1));
@@ -451,17 +364,34 @@ cudaError_t backward(sdd_surrogate* s, int n, const float* raw, const float* y, 
 }  // namespace
 
 namespace sdd {
-// Predictions [n][8] for raw inputs [n][7], max_batch rows at a time, enqueued on st.
-cudaError_t surrogate_predict(sdd_surrogate* s, int n, const float* raw, float* out, cudaStream_t st) {
-  for (int off = 0; off < n; off += s->max_batch) {
-    int m = std::min(s->max_batch, n - off);
-    cudaError_t e = forward(s, m, raw + 7 * (size_t)off, st);
-    if (e != cudaSuccess) return e;
-    k_predict<<<(m * kPred + 255) / 256, 256, 0, st>>>(m, s->Zout, out + kPred * (size_t)off);
+SurrogateView surrogate_view(const sdd_surrogate* s) { return SurrogateView{s->Wtb, s->params, s->Bm}; }
+unsigned surrogate_version(const sdd_surrogate* s) { return s->version; }
+
+int infer_grid(int n_max) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
+  return std::max(1, std::min(sms, (n_max + kInferRows - 1) / kInferRows));
+}
+
+// Predictions [n][8] for raw inputs [n][7] (fused inference), enqueued on st; with n_dev the
+// row count is read on the device (at most n).
+cudaError_t surrogate_predict(sdd_surrogate* s, int n, const float* raw, float* out, cudaStream_t st,
+                              const int* n_dev) {
+  static bool prepared = false;
+  if (!prepared) {
+    cudaError_t e = infer_prepare<RawPolicy>();
+    if (e != cudaSuccess) return e;
+    prepared = true;
+  }
+  if (n <= 0) return cudaSuccess;
+  k_infer_fused<RawPolicy><<<infer_grid(n), kInferThreads, kInferSmem, st>>>(surrogate_view(s),
+                                                                             RawPolicy{raw, out, n, n_dev});
   return cudaGetLastError();
 }
-unsigned surrogate_version(const sdd_surrogate* s) { return s->version; }
 }  // namespace sdd
 
 extern "C" {
@@ -588,13 +518,7 @@ sdd_status sdd_surrogate_train_step(sdd_surrogate* s, int n, const float* raw_de
 sdd_status sdd_surrogate_infer(sdd_surrogate* s, int n, const float* raw_dev, float* out_dev, void* stream) {
   if (!s || n < 0 || !raw_dev || !out_dev) return set_last_error(SDD_ERR_ARG, "bad arguments");
   cudaStream_t st = (cudaStream_t)stream;
-  for (int off = 0; off < n; off += s->max_batch) {
-    int m = std::min(s->max_batch, n - off);
-    cudaError_t e = forward(s, m, raw_dev + 7 * (size_t)off, st);
-    if (e != cudaSuccess) return check(e);
-    k_predict<<<(m * kPred + 255) / 256, 256, 0, st>>>(m, s->Zout, out_dev + kPred * (size_t)off);
-  }
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = surrogate_predict(s, n, raw_dev, out_dev, st, nullptr);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return check(e);
 }

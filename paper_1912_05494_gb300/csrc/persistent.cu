@@ -110,77 +110,95 @@ __device__ __forceinline__ void clear_ahead(int (*counts)[kMaxSubdomains], int* 
 
 template <bool kStats, int kTM>
 __global__ void __launch_bounds__(kPB) k_persistent_wave(RenderParams p, WaveDesc w, PersistBuffers b,
-                                                         PersistCtl* pc, Control* ctl) {
+                                                         PersistCtl* pc, Control* ctl, int seg) {
   __shared__ int s_prefix[kMaxSubdomains + 1];
   __shared__ int s_chunk;
   const int n_sub = p.sc.n_sub;
   const uint32_t nthreads = gridDim.x * blockDim.x;
+  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
 
-  // raygen: primary rays into generation 0 and the closest queues (counts buffer 0)
-  for (uint32_t base = blockIdx.x * blockDim.x; base < w.n_paths; base += nthreads) {
-    uint32_t i = base + threadIdx.x;
-    dev_raygen(p, w, i, i < w.n_paths, b.rb[0], b.q[0], pc->qc[0], b.qcap, ctl);
+  PersistState S;
+  if (seg == SEG_WAVE || seg == SEG_RAYGEN) {
+    // raygen: primary rays into generation 0 and the closest queues (counts buffer 0)
+    for (uint32_t base = blockIdx.x * blockDim.x; base < w.n_paths; base += nthreads) {
+      uint32_t i = base + threadIdx.x;
+      dev_raygen(p, w, i, i < w.n_paths, b.rb[0], b.q[0], pc->qc[0], b.qcap, ctl);
+    }
+    if (!grid_barrier(pc, ctl)) return;
+    S = PersistState{0, 0, 0, 0, 0, (int)w.n_paths, 0, 0};
+    if (seg == SEG_RAYGEN) {
+      if (leader) pc->st = S;
+      return;
+    }
+  } else {
+    const volatile PersistState* vs = &pc->st;
+    S = PersistState{vs->cq, vs->qe, vs->sq, vs->se, vs->cur, vs->n_rays, vs->gen, 0};
+    if (S.n_rays <= 0 || *(volatile int*)&pc->abort) return;  // drained or abandoned
   }
-  if (!grid_barrier(pc, ctl)) return;
 
-  int cq = 0, qe = 0;  // closest queues: input counts buffer, input entries buffer
-  int sq = 0, se = 0;  // shadow queues
-  int cur = 0;         // ray generation buffer
-  int n_rays = (int)w.n_paths;
-  for (int gen = 0; n_rays > 0; ++gen) {
-    if (gen > p.max_depth + 1) {
-      if (threadIdx.x == 0 && blockIdx.x == 0) atomicOr(&ctl->error, ERR_TIMEOUT);
+  while (S.n_rays > 0) {
+    if (S.gen > p.max_depth + 1) {
+      if (leader) atomicOr(&ctl->error, ERR_TIMEOUT);
+      S.n_rays = 0;
       break;
     }
-    const int par = gen & 1;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      pc->next_rays[par] = 0;
-      pc->next_shadow[par] = 0;
-    }
-    bool ran_pass = false;
-    for (int pass = 0; pass <= 2 * kMaxSubdomains + 2; ++pass) {
-      int total = load_prefix(pc->qc[cq], n_sub, b.qcap, s_prefix);
-      clear_ahead(pc->qc, pc->wq, (cq + 2) % 3);
-      if (total == 0) break;
-      QueuePair qp{b.q[qe], b.q[1 - qe], pc->qc[(cq + 1) % 3], b.qcap};
-      for (;;) {
-        if (threadIdx.x == 0) s_chunk = atomicAdd(&pc->wq[cq], (int)blockDim.x);
-        __syncthreads();
-        const int c0 = s_chunk;
-        __syncthreads();
-        if (c0 >= total) break;
-        const int j = c0 + (int)threadIdx.x;
-        const bool act = j < total;
-        const int s = find_subdomain(s_prefix, n_sub, act ? j : 0);
-        dev_traverse<kStats>(p, s, j - s_prefix[s], act, nullptr, 0, qp, b.rb[cur], b.hits, ctl);
+    const int par = S.gen & 1;
+    if (seg != SEG_SHADOW) {
+      if (leader) {
+        pc->next_rays[par] = 0;
+        pc->next_shadow[par] = 0;
       }
-      ran_pass = true;
-      if (!grid_barrier(pc, ctl)) return;
-      cq = (cq + 1) % 3;
-      qe = 1 - qe;
-    }
-    if (!ran_pass && !grid_barrier(pc, ctl)) return;
+      bool ran_pass = false;
+      for (int pass = 0; pass <= 2 * kMaxSubdomains + 2; ++pass) {
+        int total = load_prefix(pc->qc[S.cq], n_sub, b.qcap, s_prefix);
+        clear_ahead(pc->qc, pc->wq, (S.cq + 2) % 3);
+        if (total == 0) break;
+        QueuePair qp{b.q[S.qe], b.q[1 - S.qe], pc->qc[(S.cq + 1) % 3], b.qcap};
+        for (;;) {
+          if (threadIdx.x == 0) s_chunk = atomicAdd(&pc->wq[S.cq], (int)blockDim.x);
+          __syncthreads();
+          const int c0 = s_chunk;
+          __syncthreads();
+          if (c0 >= total) break;
+          const int j = c0 + (int)threadIdx.x;
+          const bool act = j < total;
+          const int s = find_subdomain(s_prefix, n_sub, act ? j : 0);
+          dev_traverse<kStats>(p, s, j - s_prefix[s], act, nullptr, 0, qp, b.rb[S.cur], b.hits, ctl);
+        }
+        ran_pass = true;
+        if (!grid_barrier(pc, ctl)) return;
+        S.cq = (S.cq + 1) % 3;
+        S.qe = 1 - S.qe;
+      }
+      if (!ran_pass && !grid_barrier(pc, ctl)) return;
 
-    // Shade every ray of this generation.  The last closest pass found its input buffer cq
-    // empty and left without a barrier, so slower blocks may still be reading cq: children
-    // go to the next buffer in the rotation instead (cleared two steps ago, read by nobody),
-    // and the rotation moves past the empty pass.  Shadow rays go to the shadow queues.
-    for (uint32_t base = blockIdx.x * blockDim.x; base < (uint32_t)n_rays; base += nthreads) {
-      int r = (int)(base + threadIdx.x);
-      dev_shade<kTM>(p, w, r, r < n_rays, b.rb[cur], b.hits, b.rb[1 - cur], &pc->next_rays[par], b.q[1 - qe],
-                pc->qc[(cq + 1) % 3], b.qcap, b.sb, &pc->next_shadow[par], b.sq[se], pc->sqc[sq], b.path_L, ctl);
+      // Shade every ray of this generation.  The last closest pass found its input buffer
+      // cq empty and left without a barrier, so slower blocks may still be reading cq:
+      // children go to the next buffer in the rotation instead (cleared two steps ago, read
+      // by nobody), and the rotation moves past the empty pass.  Shadow rays go to the
+      // shadow queues; tile hits for the network go to the tile queue.
+      for (uint32_t base = blockIdx.x * blockDim.x; base < (uint32_t)S.n_rays; base += nthreads) {
+        int r = (int)(base + threadIdx.x);
+        dev_shade<kTM>(p, w, r, r < S.n_rays, b.rb[S.cur], b.hits, b.rb[1 - S.cur], &pc->next_rays[par],
+                       b.q[1 - S.qe], pc->qc[(S.cq + 1) % 3], b.qcap, b.sb, &pc->next_shadow[par], b.sq[S.se],
+                       pc->sqc[S.sq], b.path_L, ctl);
+      }
+      S.cq = (S.cq + 1) % 3;
+      S.qe = 1 - S.qe;
+      if (!grid_barrier(pc, ctl)) return;
+      if (seg == SEG_CLOSEST_SHADE) {
+        if (leader) pc->st = S;  // every block holds the same state
+        return;
+      }
     }
-    cq = (cq + 1) % 3;
-    qe = 1 - qe;
-    if (!grid_barrier(pc, ctl)) return;
 
     for (int pass = 0; pass <= 2 * kMaxSubdomains + 2; ++pass) {
-      int total = load_prefix(pc->sqc[sq], n_sub, b.qcap, s_prefix);
-      clear_ahead(pc->sqc, pc->wsq, (sq + 2) % 3);
+      int total = load_prefix(pc->sqc[S.sq], n_sub, b.qcap, s_prefix);
+      clear_ahead(pc->sqc, pc->wsq, (S.sq + 2) % 3);
       if (total == 0) break;
-      QueuePair qp{b.sq[se], b.sq[1 - se], pc->sqc[(sq + 1) % 3], b.qcap};
+      QueuePair qp{b.sq[S.se], b.sq[1 - S.se], pc->sqc[(S.sq + 1) % 3], b.qcap};
       for (;;) {
-        if (threadIdx.x == 0) s_chunk = atomicAdd(&pc->wsq[sq], (int)blockDim.x);
+        if (threadIdx.x == 0) s_chunk = atomicAdd(&pc->wsq[S.sq], (int)blockDim.x);
         __syncthreads();
         const int c0 = s_chunk;
         __syncthreads();
@@ -191,14 +209,16 @@ __global__ void __launch_bounds__(kPB) k_persistent_wave(RenderParams p, WaveDes
         dev_shadow<kStats, kTM>(p, w, s, j - s_prefix[s], act, nullptr, 0, qp, b.sb, b.path_L, ctl);
       }
       if (!grid_barrier(pc, ctl)) return;
-      sq = (sq + 1) % 3;
-      se = 1 - se;
+      S.sq = (S.sq + 1) % 3;
+      S.se = 1 - S.se;
     }
-    n_rays = min(*(volatile int*)&pc->next_rays[par], b.qcap);
-    if (*(volatile int*)&pc->next_rays[par] > b.qcap && threadIdx.x == 0 && blockIdx.x == 0)
-      atomicOr(&ctl->error, ERR_QUEUE_OVERFLOW);
-    cur = 1 - cur;
+    S.n_rays = min(*(volatile int*)&pc->next_rays[par], b.qcap);
+    if (*(volatile int*)&pc->next_rays[par] > b.qcap && leader) atomicOr(&ctl->error, ERR_QUEUE_OVERFLOW);
+    S.cur = 1 - S.cur;
+    S.gen++;
+    if (seg == SEG_SHADOW) break;
   }
+  if (seg != SEG_WAVE && leader) pc->st = S;
 }
 
 template <bool kStats, int kTM>
@@ -210,20 +230,23 @@ static int persistent_blocks() {
   return sms * per_sm;
 }
 
-// The batched form supports scenes without heterogeneous tiles and with brute-force tiles
-// (the network runs between shading and shadow rays, outside one launch).
+// Blocks of the cooperative launch for a scene's tile mode (0 none, 1 brute force, 2 network).
 int persistent_grid(bool stats, int tile_mode) {
   if (tile_mode == 1) return stats ? persistent_blocks<true, 1>() : persistent_blocks<false, 1>();
+  if (tile_mode == 2) return stats ? persistent_blocks<true, 2>() : persistent_blocks<false, 2>();
   return stats ? persistent_blocks<true, 0>() : persistent_blocks<false, 0>();
 }
 
 cudaError_t launch_persistent_wave(const RenderParams& p, const WaveDesc& w, const PersistBuffers& b, PersistCtl* pc,
-                                   Control* ctl, int grid, cudaStream_t st) {
-  void* args[] = {(void*)&p, (void*)&w, (void*)&b, (void*)&pc, (void*)&ctl};
+                                   Control* ctl, int grid, cudaStream_t st, int seg) {
+  void* args[] = {(void*)&p, (void*)&w, (void*)&b, (void*)&pc, (void*)&ctl, (void*)&seg};
   const void* fn;
-  const int tm = tile_mode(p);
-  if (tm == 1) fn = p.stats >= 2 ? (const void*)k_persistent_wave<true, 1> : (const void*)k_persistent_wave<false, 1>;
-  else fn = p.stats >= 2 ? (const void*)k_persistent_wave<true, 0> : (const void*)k_persistent_wave<false, 0>;
+  const bool stats = p.stats >= 2;
+  switch (tile_mode(p)) {
+    case 1: fn = stats ? (const void*)k_persistent_wave<true, 1> : (const void*)k_persistent_wave<false, 1>; break;
+    case 2: fn = stats ? (const void*)k_persistent_wave<true, 2> : (const void*)k_persistent_wave<false, 2>; break;
+    default: fn = stats ? (const void*)k_persistent_wave<true, 0> : (const void*)k_persistent_wave<false, 0>;
+  }
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPB), args, 0, st);
 }
 

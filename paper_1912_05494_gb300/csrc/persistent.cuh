@@ -15,7 +15,24 @@ struct PersistBuffers {
   int qcap;
 };
 
-// Device-side bookkeeping of one persistent wave; the host clears it before each launch.
+// Queue-rotation state of a wave between segment launches (see SEG_* below).
+struct PersistState {
+  int cq, qe;   // closest queues: counts buffer and entries buffer of the next input
+  int sq, se;   // shadow queues
+  int cur;      // ray generation buffer being shaded
+  int n_rays;   // rays of the current generation; 0 when the wave is drained
+  int gen;
+  int pad;
+};
+
+// What one launch of the persistent kernel covers.  SEG_WAVE drains the whole wave.  For
+// scenes whose tile hits go to the network the wave is split: SEG_RAYGEN, then per
+// generation SEG_CLOSEST_SHADE (closest passes and shading) and SEG_SHADOW (shadow passes),
+// with the fused tile-shading launch between the two; launches after the wave is drained
+// return at once, so a fixed sequence of max_depth + 2 generations covers every wave.
+enum PersistSegment : int { SEG_WAVE = 0, SEG_RAYGEN = 1, SEG_CLOSEST_SHADE = 2, SEG_SHADOW = 3 };
+
+// Device-side bookkeeping of one persistent wave; the host clears it before each wave.
 struct PersistCtl {
   int qc[3][kMaxSubdomains];   // closest queue counts, three rotating buffers
   int sqc[3][kMaxSubdomains];  // shadow queue counts
@@ -24,10 +41,11 @@ struct PersistCtl {
   unsigned bar_count, bar_gen;
   int abort;
   int pad;
+  PersistState st;
 };
 
 int persistent_grid(bool stats, int tile_mode);
 cudaError_t launch_persistent_wave(const RenderParams& p, const WaveDesc& w, const PersistBuffers& b, PersistCtl* pc,
-                                   Control* ctl, int grid, cudaStream_t st);
+                                   Control* ctl, int grid, cudaStream_t st, int seg = SEG_WAVE);
 
 }  // namespace sdd

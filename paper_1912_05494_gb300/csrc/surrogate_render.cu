@@ -1,14 +1,20 @@
 // surrogate_render.cu -- heterogeneous tiles in the renderer through the BTDF network.
 //
-// A generation's tile hits are queued by the shading kernel; this file gathers their network
-// inputs, and after the network has predicted T, R and the two von Mises-Fisher lobes of
-// each side (surrogate_head.cuh), samples the exit: the side with probability R / (R + T) and
-// throughput x (R + T), a lobe by its weight, then a direction from it about the
-// straight-through or mirror direction.  Shadow rays through a tile use the network's
-// transmittance x the transmitted mixture's mass within 1 degree of straight through
-// toward the sun (sun_table), the same ballistic convention as the brute-force form.
+// The shading kernel queues a generation's tile hits.  One fused launch then shades them
+// all (k_infer_fused with TileShadePolicy): per chunk of 128 hits it gathers the network's
+// inputs from the ray state and the tile's material, runs the network, and samples the
+// exit from the prediction -- the side with probability R / (R + T) and throughput
+// x (R + T), a von Mises-Fisher lobe by its weight (surrogate_head.cuh), then a direction
+// from that lobe about the straight-through or mirror direction -- and appends the ray to
+// the next generation.  The hit count is read on the device, so the launch needs no host
+// round trip and can sit in a captured frame; in the batched form the buffers are taken
+// from the persistent kernel's saved queue state.  Shadow rays through a tile use the
+// network's transmittance x the transmitted mixture's mass within 1 degree of straight
+// through toward the sun (sun table), the same ballistic convention as the brute-force form.
+#include "persistent.cuh"
 #include "render_device.cuh"
 #include "surrogate_head.cuh"
+#include "surrogate_net.cuh"
 #include "surrogate_render.cuh"
 
 namespace sdd {
@@ -32,114 +38,179 @@ __device__ float3 vmf_sample(float3 a, float kappa, float u1, float u2, float* a
   return (st * cp) * b1 + (st * sp) * b2 + (1.f - v) * a;
 }
 
-__device__ __forceinline__ void tile_query(const RenderParams& p, const WaveDesc& w, RayBuf cur, const float2* hits,
-                                           uint32_t r, PathId* id, float3* pt, float3* ng, float3* dl, float3* t1,
-                                           float3* t2, int* mat, float4* O, float4* D, uint2* inf) {
-  *O = cur.o[r];
-  *D = cur.d[r];
-  *inf = cur.info[r];
-  float2 H = hits[r];
-  *id = path_id(p, w, inf->x);
-  uint32_t prim = __float_as_uint(H.y);
-  float4 nm = __ldg(p.sc.prim_nrm_mat + prim);
-  *ng = f3(nm);
-  *mat = __float_as_int(nm.w);
-  float3 d = f3(*D);
-  *pt = f3(*O) + H.x * d;
+struct TileHit {
+  PathId id;
+  float3 pt, ng, dl, t1, t2;
+  int mat;
+  float thr;
+  uint2 info;
+};
+
+__device__ __forceinline__ TileHit tile_hit(const RenderParams& p, const WaveDesc& w, const RayBuf& cur,
+                                            const float2* hits, uint32_t r) {
+  TileHit h;
+  const float4 O = cur.o[r], D = cur.d[r];
+  h.info = cur.info[r];
+  const float2 H = hits[r];
+  h.id = path_id(p, w, h.info.x);
+  const float4 nm = __ldg(p.sc.prim_nrm_mat + __float_as_uint(H.y));
+  h.ng = f3(nm);
+  h.mat = __float_as_int(nm.w);
+  const float3 d = f3(D);
+  h.pt = f3(O) + H.x * d;
+  h.thr = D.w;
   float x, y;
-  tile_frame(p.tiles.L, *pt, *ng, d, &x, &y, dl, t1, t2);
+  tile_frame(p.tiles.L, h.pt, h.ng, d, &x, &y, &h.dl, &h.t1, &h.t2);
+  return h;
 }
 
 }  // namespace
 
-__global__ void k_tile_inputs(RenderParams p, WaveDesc w, RayBuf cur, const float2* hits, const uint32_t* queue, int n,
-                              float* raw) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  PathId id;
-  float3 pt, ng, dl, t1, t2;
-  int mat;
-  float4 O, D;
-  uint2 inf;
-  tile_query(p, w, cur, hits, queue[i], &id, &pt, &ng, &dl, &t1, &t2, &mat, &O, &D, &inf);
-  int tile = __ldg(p.mat_tile + mat);
-  size_t mi = (size_t)mat * p.sp.n_lambda + id.lam;
-  float phi = atan2f(dl.y, dl.x);
-  if (phi < 0.f) phi += 6.283185307179586f;
-  float* q = raw + 7 * (size_t)i;
-  q[0] = -dl.z;  // signed: > 0 arrives at the flat front face (the side the normal points to)
-  q[1] = phi;
-  q[2] = __ldg(p.sp.lambda_nm + id.lam);
-  q[3] = __ldg(p.tiles.d_mean + tile);
-  q[4] = __ldg(p.tiles.rho + tile);
-  q[5] = __ldg(p.sp.mat_n + mi);
-  q[6] = __ldg(p.sp.mat_k + mi);
-}
+// Fused shading of a generation's tile hits (see the file comment).  With pc set, the ray
+// and queue buffers are those of the persistent kernel's saved state (batched form).
+struct TileShadePolicy {
+  RenderParams p;
+  WaveDesc w;
+  RayBuf cur, next;
+  const float2* hits;
+  int* next_count;
+  uint32_t* q;
+  int* q_count;
+  int qcap;
+  Control* ctl;
+  PersistBuffers b;
+  PersistCtl* pc;
 
-__global__ void k_tile_apply(RenderParams p, WaveDesc w, RayBuf cur, const float2* hits, const uint32_t* queue, int n,
-                             const float* pred, RayBuf next, int* next_count, uint32_t* q, int* q_count, int qcap,
-                             Control* ctl) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  bool active = i < n;
-  bool e0 = false;
-  float3 o0 = make_float3(0.f, 0.f, 0.f), d0 = o0;
-  float thr0 = 0.f, s00 = 0.f;
-  uint32_t meta0 = 0, path = 0;
-  if (active) {
-    PathId id;
-    float3 pt, ng, dl, t1, t2;
-    int mat;
-    float4 O, D;
-    uint2 inf;
-    tile_query(p, w, cur, hits, queue[i], &id, &pt, &ng, &dl, &t1, &t2, &mat, &O, &D, &inf);
-    path = inf.x;
-    uint32_t depth = inf.y & 0xFFu, flags = (inf.y >> 8) & 0xFFu;
-    uint32_t v = depth + 1;
-    const float* pr = pred + kHeadPred * (size_t)i;
-    float T = clamp01(pr[0]), R = clamp01(pr[1]);
-    uint32_t hsh = p.path_hash ? p.path_hash[path] : 0u;
-    float4 u = draw4(id.pixel, id.sample, v, STREAM_TILE, 0, id.lam, p.seed);
-    float4 up = draw4(id.pixel, id.sample, v, STREAM_PATH, 0, id.lam, p.seed);
-    float tot = T + R;
-    if (tot > 0.f) {
-      bool refl = u.x * tot < R;
-      const float* lobe = pr + (refl ? 5 : 2);
-      float kappa = expf(u.y < lobe[0] ? lobe[1] : lobe[2]);
-      float3 ref = refl ? make_float3(dl.x, dl.y, -dl.z) : dl;  // mirror or straight through (tile frame)
-      float a;
-      float3 dir = vmf_sample(ref, kappa, u.z, u.w, &a);
-      if ((dir.z > 0.f) != (ref.z > 0.f)) dir.z = -dir.z;  // keep the lobe on its side of the tile
-      bool ballistic = a < head_bin_a(1);                    // within 1 degree
-      hsh = fnv_byte(hsh, refl ? EV_REFLECT : EV_TRANSMIT);
-      float thr = D.w * tot;
-      bool keep = !refl && ballistic;
-      uint32_t fl = keep ? flags : (flags & ~FLAG_SUN_COUNTED);
-      e0 = true;
-      d0 = normalize3(dir.x * t1 + dir.y * t2 + dir.z * ng);
-      meta0 = v | (fl << 8);
-      if ((int)v >= p.rr_start) {
-        float qs = fminf(0.95f, thr);
-        if (up.w >= qs) {
-          e0 = false;
-          hsh = fnv_byte(hsh, EV_RR_KILL);
-        } else {
-          thr = thr / qs;
-        }
-      }
-      thr0 = thr;
-      if (e0) {
-        o0 = offset_point(pt, ng, d0, p.sc.eps);
-        s00 = seg0_of(ng, d0, p.sc.eps);
-      }
-    } else {
-      hsh = fnv_byte(hsh, EV_ABSORB);
-    }
-    if (p.path_hash) p.path_hash[path] = hsh;
+  struct Ctx {
+    RayBuf cur, next;
+    int* next_count;
+    uint32_t* q;
+    int* q_count;
+  };
+  __device__ Ctx resolve() const {
+    if (!pc) return Ctx{cur, next, next_count, q, q_count};
+    const volatile PersistState* st = &pc->st;
+    const int c = st->cur, gen = st->gen, qe = st->qe, cq = st->cq;
+    return Ctx{b.rb[c], b.rb[1 - c], &pc->next_rays[gen & 1], b.q[qe], pc->qc[cq]};
   }
-  emit_ray(e0, p.sc, next, next_count, q, q_count, qcap, o0, s00, d0, thr0, path, meta0, ctl);
+  __device__ int count(const Ctx&) const { return min(*(volatile const int*)p.tile_count, p.tile_cap); }
+  __device__ void load(const Ctx& c, int row, float qv[net::kIn]) const {
+    const TileHit h = tile_hit(p, w, c.cur, hits, p.tile_queue[row]);
+    const int tile = __ldg(p.mat_tile + h.mat);
+    const size_t mi = (size_t)h.mat * p.sp.n_lambda + h.id.lam;
+    float phi = atan2f(h.dl.y, h.dl.x);
+    if (phi < 0.f) phi += 6.283185307179586f;
+    qv[0] = -h.dl.z;  // signed: > 0 arrives at the flat front face (the side the normal points to)
+    qv[1] = phi;
+    qv[2] = __ldg(p.sp.lambda_nm + h.id.lam);
+    qv[3] = __ldg(p.tiles.d_mean + tile);
+    qv[4] = __ldg(p.tiles.rho + tile);
+    qv[5] = __ldg(p.sp.mat_n + mi);
+    qv[6] = __ldg(p.sp.mat_k + mi);
+  }
+  // Threads 0..127 (whole warps) take one row each and append its exit ray.
+  __device__ void consume(const Ctx& c, int row0, int valid, const float* pred) const {
+    if (threadIdx.x >= kInferRows) return;
+    const int i = threadIdx.x;
+    const bool active = i < valid;
+    bool e0 = false;
+    float3 o0 = make_float3(0.f, 0.f, 0.f), d0 = o0;
+    float thr0 = 0.f, s00 = 0.f;
+    uint32_t meta0 = 0, path = 0;
+    if (active) {
+      const TileHit h = tile_hit(p, w, c.cur, hits, p.tile_queue[row0 + i]);
+      path = h.info.x;
+      const uint32_t depth = h.info.y & 0xFFu, flags = (h.info.y >> 8) & 0xFFu;
+      const uint32_t v = depth + 1;
+      const float* pr = pred + i * kInferZLd;
+      const float T = clamp01(pr[0]), R = clamp01(pr[1]);
+      uint32_t hsh = p.path_hash ? p.path_hash[path] : 0u;
+      const float4 u = draw4(h.id.pixel, h.id.sample, v, STREAM_TILE, 0, h.id.lam, p.seed);
+      const float4 up = draw4(h.id.pixel, h.id.sample, v, STREAM_PATH, 0, h.id.lam, p.seed);
+      const float tot = T + R;
+      if (tot > 0.f) {
+        const bool refl = u.x * tot < R;
+        const float* lobe = pr + (refl ? 5 : 2);
+        const float kappa = expf(u.y < lobe[0] ? lobe[1] : lobe[2]);
+        const float3 ref = refl ? make_float3(h.dl.x, h.dl.y, -h.dl.z) : h.dl;  // tile frame
+        float a;
+        float3 dir = vmf_sample(ref, kappa, u.z, u.w, &a);
+        if ((dir.z > 0.f) != (ref.z > 0.f)) dir.z = -dir.z;  // keep the lobe on its side of the tile
+        const bool ballistic = a < head_bin_a(1);             // within 1 degree
+        hsh = fnv_byte(hsh, refl ? EV_REFLECT : EV_TRANSMIT);
+        float thr = h.thr * tot;
+        const uint32_t fl = (!refl && ballistic) ? flags : (flags & ~FLAG_SUN_COUNTED);
+        e0 = true;
+        d0 = normalize3(dir.x * h.t1 + dir.y * h.t2 + dir.z * h.ng);
+        meta0 = v | (fl << 8);
+        if ((int)v >= p.rr_start) {
+          const float qs = fminf(0.95f, thr);
+          if (up.w >= qs) {
+            e0 = false;
+            hsh = fnv_byte(hsh, EV_RR_KILL);
+          } else {
+            thr = thr / qs;
+          }
+        }
+        thr0 = thr;
+        if (e0) {
+          o0 = offset_point(h.pt, h.ng, d0, p.sc.eps);
+          s00 = seg0_of(h.ng, d0, p.sc.eps);
+        }
+      } else {
+        hsh = fnv_byte(hsh, EV_ABSORB);
+      }
+      if (p.path_hash) p.path_hash[path] = hsh;
+    }
+    emit_ray(e0, p.sc, c.next, c.next_count, c.q, c.q_count, qcap, o0, s00, d0, thr0, path, meta0, ctl);
+  }
+};
+
+namespace {
+cudaError_t launch_tile_shade_policy(const TileShadePolicy& pol, const sdd_surrogate* net, cudaStream_t st) {
+  static bool prepared = false;
+  if (!prepared) {
+    cudaError_t e = infer_prepare<TileShadePolicy>();
+    if (e != cudaSuccess) return e;
+    prepared = true;
+  }
+  k_infer_fused<TileShadePolicy><<<infer_grid(pol.p.tile_cap), kInferThreads, kInferSmem, st>>>(surrogate_view(net),
+                                                                                                 pol);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_tile_shade(const RenderParams& p, const WaveDesc& w, RayBuf cur, const float2* hits, RayBuf next,
+                              int* next_count, uint32_t* q, int* q_count, int qcap, Control* ctl,
+                              const sdd_surrogate* net, cudaStream_t st) {
+  TileShadePolicy pol{};
+  pol.p = p;
+  pol.w = w;
+  pol.cur = cur;
+  pol.next = next;
+  pol.hits = hits;
+  pol.next_count = next_count;
+  pol.q = q;
+  pol.q_count = q_count;
+  pol.qcap = qcap;
+  pol.ctl = ctl;
+  pol.pc = nullptr;
+  return launch_tile_shade_policy(pol, net, st);
 }
 
-// Network queries toward the sun for every tile material and wavelength.
+cudaError_t launch_tile_shade_persistent(const RenderParams& p, const WaveDesc& w, const PersistBuffers& b,
+                                         PersistCtl* pc, Control* ctl, const sdd_surrogate* net, cudaStream_t st) {
+  TileShadePolicy pol{};
+  pol.p = p;
+  pol.w = w;
+  pol.hits = b.hits;
+  pol.qcap = b.qcap;
+  pol.ctl = ctl;
+  pol.b = b;
+  pol.pc = pc;
+  return launch_tile_shade_policy(pol, net, st);
+}
+
 __global__ void k_sun_queries(RenderParams p, const int* mats, const float3* mat_normal, int n_mats, float* raw) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int L = p.sp.n_lambda;
@@ -172,19 +243,6 @@ __global__ void k_sun_table(const int* mats, int n_mats, int L, const float* pre
   const float* pr = pred + kHeadPred * (size_t)i;
   const float ball = lobe_mass_within(pr[2], expf(pr[3]), expf(pr[4]), head_bin_a(1));
   table[(size_t)mats[j] * L + l] = clamp01(pr[0]) * clamp01(ball);
-}
-
-void launch_tile_inputs(const RenderParams& p, const WaveDesc& w, RayBuf cur, const float2* hits,
-                        const uint32_t* queue, int n, float* raw, cudaStream_t st) {
-  if (n > 0) k_tile_inputs<<<(n + 127) / 128, 128, 0, st>>>(p, w, cur, hits, queue, n, raw);
-}
-
-void launch_tile_apply(const RenderParams& p, const WaveDesc& w, RayBuf cur, const float2* hits,
-                       const uint32_t* queue, int n, const float* pred, RayBuf next, int* next_count, uint32_t* q,
-                       int* q_count, int qcap, Control* ctl, cudaStream_t st) {
-  if (n > 0)
-    k_tile_apply<<<(n + 127) / 128, 128, 0, st>>>(p, w, cur, hits, queue, n, pred, next, next_count, q, q_count, qcap,
-                                                  ctl);
 }
 
 void launch_sun_queries(const RenderParams& p, const int* mats, const float3* mat_normal, int n_mats, float* raw,

@@ -139,3 +139,23 @@ def test_network_form_is_deterministic_and_counts_launches(sdd, trained):
     a = render(sdd, h, cam, spec, use_surrogate=1, surrogate=net)
     b = render(sdd, h, cam, spec, use_surrogate=1, surrogate=net)
     assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("use_net", [False, True])
+def test_batched_form_is_bit_identical_with_tiles(sdd, trained, use_net):
+    """The persistent form (one launch per wave for brute-force tiles; two per generation
+    around the fused tile shading for the network) runs the same per-ray code: images and
+    path hashes equal the host-driven form's bit for bit, frame after frame."""
+    net = trained[0] if use_net else None
+    sc, cam, spec = S.tile_room_scene(width=40, height=24, spp=4)
+    h = sdd.SceneHandle(sc)
+    kw = {"use_surrogate": 1, "surrogate": net} if use_net else {}
+    a, _, ha = render(sdd, h, cam, spec, paths=True, **kw)
+    b, _, hb = render(sdd, h, cam, spec, paths=True, batched=1, wave_paths=40 * 24 * 81, **kw)
+    c, _, hc = render(sdd, h, cam, spec, paths=True, batched=1, wave_paths=40 * 24 * 81, **kw)
+    assert np.array_equal(a, b) and np.array_equal(ha, hb)
+    assert np.array_equal(b, c) and np.array_equal(hb, hc)
+    st = sdd.sdd_get_stats(h.h)
+    assert st["launches_persistent"] >= 1
+    if use_net:
+        assert st["launches_tile"] > 0
