@@ -15,6 +15,17 @@ Printed JSON line (rank 0):
              state) / its CUDA-event time, against the measured HBM copy bandwidth
   cpu_baseline  the FP64 oracle on the host cores on a bounded pixel sample of the same frame
 
+--workload large runs the large batched frame instead: the nave refined to ~1.07M triangles
+with 96 windows of 400 heterogeneous tiles (38,400 tiles), 3840 x 2160, 81 wavelengths,
+depth 16.  The BTDF network is trained on the GPU first (tile-tracer data of the 512-tile
+set), the subdomain count is autotuned for the network + batched form, and both forms render
+the full frame at --spp samples per pixel (throughput per spectral sample does not depend on
+spp): the plain GPU form (host-driven wavefront, one brute-force ray through the tile at
+every tile hit) and the network + batched form (persistent kernels, CUDA graph, fused tile
+shading).  The line reports both throughputs, their ratio, and the 8 x 8 block-averaged
+image error of the network form against the plain form beside the noise floor of two plain
+renders with different seeds.
+
 --impl reference times the oracle alone (the CPU reference of this method) on the same
 workload and prints its line.  N > 1 GPUs: independent replicas (each rank renders a full
 frame with its own Philox key); no collective on the data path.
@@ -367,6 +378,134 @@ def run_gpu(args):
     return 0
 
 
+def block_avg(film, cam, b=8):
+    """Per-wavelength means of b x b pixel blocks of a [pixels, L] film."""
+    L = film.shape[1]
+    img = film.reshape(cam.height, cam.width, L)
+    H, W = cam.height // b, cam.width // b
+    return img[:H * b, :W * b].reshape(H, b, W, b, L).mean(axis=(1, 3))
+
+
+def rel_err(a, b):
+    return float(np.abs(a - b).sum() / np.abs(b).sum())
+
+
+def run_large(args):
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as g
+    g.build()
+    from paper_1912_05494_gb300 import autotune as A
+    from paper_1912_05494_gb300 import scenes as S
+    from paper_1912_05494_gb300 import sdd
+    from paper_1912_05494_gb300 import surrogate as SG
+
+    t0 = time.time()
+    scene, cam, spec = S.large_nave_scene(seed=5, n_subdomains=args.subdomains)
+    spec = S.RenderSpec(**{**spec.__dict__, "spp": args.spp})
+    if args.large_frame:  # smaller frames of the same scene, for profiling captures
+        w, hgt = (int(x) for x in args.large_frame.split("x"))
+        cam = S.CameraData(**{**cam.__dict__, "width": w, "height": hgt})
+    t_scene = time.time() - t0
+    tiles, tn, tk = S.tile_set(3, 512)
+    # the network: trained on tile-tracer samples of the tile set the windows draw on
+    t0 = time.time()
+    ts = sdd.TileSetHandle(tiles)
+    net, hist, (hr, hy) = SG.train_for_tileset(ts.h, tiles, tn, tk, n_samples=args.train_samples,
+                                               steps=args.train_steps, rays=256)
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    pred = torch.empty((hr.shape[0], 8), device="cuda")
+    net.infer(hr, pred)
+    p, y = pred.cpu().numpy(), hy.cpu().numpy()
+    held = {"mae_T": float(np.abs(p[:, 0] - y[:, 0]).mean()), "mae_R": float(np.abs(p[:, 1] - y[:, 1]).mean()),
+            "samples": int(hr.shape[0])}
+    net_kw = {"use_surrogate": 1, "surrogate": net, "batched": 1}
+    tuned = None
+    if args.autotune:
+        tuned = A.autotune(scene, cam, spec, subdomains=(4, 8, 16, 32), blocks=(128,), top_nodes=(0,),
+                           wave_paths=(0,), sample_pixels=1 << 17, sample_spp=1, use_cache=False,
+                           render_kw=net_kw)
+        scene.n_subdomains = tuned["n_subdomains"]
+    t0 = time.time()
+    h = sdd.SceneHandle(scene)
+    t_build = time.time() - t0
+    n_px = cam.width * cam.height
+    out = torch.empty((n_px, spec.n_lambda), device="cuda", dtype=torch.float32)
+    xyz = torch.empty((n_px, 3), device="cuda", dtype=torch.float32)
+    flush = torch.empty(512 * 1024 * 1024 // 4, device="cuda", dtype=torch.float32)
+    frame_paths = n_px * spec.spp * spec.n_lambda
+    stream = torch.cuda.current_stream()
+
+    def timed(kw, steps, warmup):
+        for _ in range(warmup):
+            sdd.sdd_render(h.h, cam, spec, out, xyz, **kw)
+        torch.cuda.synchronize()
+        sdd.sdd_set_profiling(h.h, 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        launches = 0
+        ms_tile = 0.0
+        e0.record(stream)
+        for _ in range(steps):
+            flush.zero_()
+            sdd.sdd_render(h.h, cam, spec, out, xyz, **kw)
+            st = sdd.sdd_get_stats(h.h)
+            launches += st["launches_total"] + 1
+            ms_tile += st["ms_tile"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sdd.sdd_set_profiling(h.h, 0)
+        ms = e0.elapsed_time(e1) / steps
+        return ms, launches, out.cpu().numpy().astype(np.float64), ms_tile / steps
+
+    if args.forms != "both":  # one form only (profiling); no comparison
+        kw = net_kw if args.forms == "net" else {"batched": 0}
+        ms, launches, _, _ = timed(kw, args.steps, args.warmup)
+        print(json.dumps({"workload": "large", "form": args.forms, "frame": [cam.width, cam.height, spec.spp],
+                          "ms_per_step": ms, "value": frame_paths / (ms / 1e3) / 1e6, "unit": UNIT,
+                          "gpu_launches": launches}), flush=True)
+        h.close()
+        return 0
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms_net, launches_net, img_net, _ = timed(net_kw, args.steps, args.warmup)
+    ms_plain, launches_plain, img_plain, _ = timed({"batched": 0}, args.steps, args.warmup)
+    clk = clocks.stop()
+    spec2 = S.RenderSpec(**{**spec.__dict__, "seed": spec.seed + 4099})
+    sdd.sdd_render(h.h, cam, spec2, out, xyz, batched=0)
+    torch.cuda.synchronize()
+    img_plain2 = out.cpu().numpy().astype(np.float64)
+    value_net = frame_paths / (ms_net / 1e3) / 1e6
+    value_plain = frame_paths / (ms_plain / 1e3) / 1e6
+    bn, bp, bp2 = block_avg(img_net, cam), block_avg(img_plain, cam), block_avg(img_plain2, cam)
+    line = {"metric": METRIC, "value": value_net, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_net, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"large nave {scene.n_triangles} triangles, 96 windows x 400 heterogeneous tiles, "
+                                   f"{cam.width}x{cam.height} {spec.spp}spp 81lambda depth16 RR, network + batched",
+                       "paths_per_step": frame_paths, "subdomains": scene.n_subdomains,
+                       "l2": "flushed (512 MB write) before every frame; the FP64 film alone is 5.4 GB"},
+            "comparison": {"plain": {"value": value_plain, "ms_per_step": ms_plain, "gpu_launches": launches_plain,
+                                     "form": "host-driven wavefront, brute-force ray through the tile per tile hit"},
+                           "network_batched": {"value": value_net, "ms_per_step": ms_net,
+                                               "gpu_launches": launches_net,
+                                               "form": "persistent kernels + CUDA graph, fused tile shading"},
+                           "speedup": ms_plain / ms_net,
+                           "image_error_block8": rel_err(bn, bp), "noise_floor_block8": rel_err(bp2, bp),
+                           "image_error_full": rel_err(img_net, img_plain), "noise_floor_full": rel_err(img_plain2,
+                                                                                                     img_plain)},
+            "network": {"train_steps": args.train_steps, "train_samples": args.train_samples, "rays_per_sample": 256,
+                        "loss_first": hist[0], "loss_last50": float(np.mean(hist[-50:])), "train_s": t_train,
+                        "held_out": held},
+            "autotune": {"n_subdomains": tuned["n_subdomains"], "trials": [(t["n_subdomains"], t["seconds"])
+                                                                          for t in tuned["trials"]]} if tuned else None,
+            "setup_s": {"scene_python": t_scene, "scene_create": t_build},
+            "clocks": clk, "gpu_launches": launches_net}
+    print(json.dumps(line), flush=True)
+    h.close()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -384,10 +523,21 @@ def main(argv=None):
     ap.add_argument("--subdomains", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batched", type=int, default=0, help="1: persistent kernels + CUDA graph; 0: host-driven")
+    ap.add_argument("--workload", choices=["nave", "large"], default="nave")
+    ap.add_argument("--train-steps", type=int, default=20000, help="large workload: network training steps")
+    ap.add_argument("--train-samples", type=int, default=1 << 21, help="large workload: tile-tracer samples")
+    ap.add_argument("--autotune", type=int, default=1, help="large workload: autotune the subdomain count")
+    ap.add_argument("--forms", choices=["both", "net", "plain"], default="both",
+                    help="large workload: time both forms and compare (default), or one form alone")
+    ap.add_argument("--large-frame", default="", help="large workload: WxH instead of 3840x2160 (profiling)")
     args = ap.parse_args(argv)
+    if args.workload == "large" and "--spp" not in (argv if argv is not None else sys.argv):
+        args.spp = 4
     args.warmup = max(args.warmup, 3)  # timing rule: at least three untimed warm-up frames
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "large":
+        return run_large(args)
     return run_gpu(args)
 
 

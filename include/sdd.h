@@ -204,6 +204,7 @@ typedef struct {
   int64_t graph_replays;   /* batched form: frames replayed from a captured CUDA graph */
   double ms_tile;          /* network form: fused tile-shading launches (host-driven form) */
   int64_t launches_tile;   /* network form: fused tile-shading launches */
+  int64_t tile_shaded;     /* network form: tile hits shaded by the network (level >= 2) */
 } sdd_stats;
 
 /* level 0: nothing; 1: CUDA-event timing of every launch; 2: also count BVH nodes and

@@ -49,18 +49,19 @@ def _store(path, db):
     os.replace(tmp, path)
 
 
-def time_frame(h, cam, spec, pixels, tuning, repeats=2):
+def time_frame(h, cam, spec, pixels, tuning, repeats=2, render_kw=None):
     """Median seconds of `repeats` renders of the reduced frame with the given tuning."""
     import torch
+    kw = render_kw or {}
     sdd.sdd_set_tuning(h, tuning)
     n_px = len(pixels)
     out = torch.empty((n_px, spec.n_lambda), device="cuda", dtype=torch.float32)
-    sdd.sdd_render(h, cam, spec, out, pixels=pixels)  # warm-up (workspace, caches)
+    sdd.sdd_render(h, cam, spec, out, pixels=pixels, **kw)  # warm-up (workspace, caches, graph)
     ts = []
     for _ in range(repeats):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        sdd.sdd_render(h, cam, spec, out, pixels=pixels)
+        sdd.sdd_render(h, cam, spec, out, pixels=pixels, **kw)
         torch.cuda.synchronize()
         ts.append(time.perf_counter() - t0)
     return float(np.median(ts))
@@ -68,15 +69,19 @@ def time_frame(h, cam, spec, pixels, tuning, repeats=2):
 
 def autotune(sd, cam, spec, *, subdomains=(1, 2, 4, 8, 16, 32, 64), blocks=(64, 128, 256),
              top_nodes=(0, 63, 255), wave_paths=(1 << 22, 1 << 24, 1 << 26), sample_pixels=65536,
-             sample_spp=None, cache_path=DEFAULT_CACHE, use_cache=True, log=None):
+             sample_spp=None, cache_path=DEFAULT_CACHE, use_cache=True, log=None, render_kw=None):
     """Pick the fastest launch shape for rendering `sd` with `cam` / `spec` on this GPU.
+    render_kw: extra sdd_render options of the form being tuned (batched, use_surrogate, ...);
+    a network passed there is not part of the cache key.
 
     Returns {"n_subdomains", "tuning": {...}, "seconds", "trials": [...]}.
     """
     import torch
     dev = torch.cuda.get_device_name()
+    form = {k: v for k, v in (render_kw or {}).items() if isinstance(v, (int, float, str))}
     key = scene_key(sd, cam, spec, dev, json.dumps([list(subdomains), list(blocks), list(top_nodes),
-                                                    list(wave_paths), sample_pixels, sample_spp]))
+                                                    list(wave_paths), sample_pixels, sample_spp, form],
+                                                   sort_keys=True))
     db = _load(cache_path) if use_cache else {}
     if use_cache and key in db:
         return db[key]
@@ -95,7 +100,7 @@ def autotune(sd, cam, spec, *, subdomains=(1, 2, 4, 8, 16, 32, 64), blocks=(64, 
     best_sub = None
     for ns in subdomains:
         h = sdd.SceneHandle(sd, n_subdomains=ns)
-        t = time_frame(h.h, cam, spec_s, pixels, base)
+        t = time_frame(h.h, cam, spec_s, pixels, base, render_kw=render_kw)
         trials.append({"n_subdomains": ns, **base, "seconds": t})
         note(f"S={ns}: {t * 1e3:.1f} ms")
         if best is None or t < best:
@@ -108,7 +113,7 @@ def autotune(sd, cam, spec, *, subdomains=(1, 2, 4, 8, 16, 32, 64), blocks=(64, 
             cand = {**cur, knob: v}
             if cand == cur and any(t["n_subdomains"] == best_sub and all(t[k] == cur[k] for k in cur) for t in trials):
                 continue
-            t = time_frame(h.h, cam, spec_s, pixels, cand)
+            t = time_frame(h.h, cam, spec_s, pixels, cand, render_kw=render_kw)
             trials.append({"n_subdomains": best_sub, **cand, "seconds": t})
             note(f"S={best_sub} {knob}={v}: {t * 1e3:.1f} ms")
             if t < best:

@@ -19,6 +19,11 @@ ROOT = os.path.dirname(HERE)
 CUDA_SOURCES = ["api.cu", "render_kernels.cu", "noalloc.cu", "persistent.cu", "tile.cu", "mlp.cu", "surrogate_render.cu"]
 CXX_SOURCES = ["scene_build.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# The persistent kernel reads, within one launch, ray / hit / queue / path data that other
+# blocks (other SMs) wrote before a grid barrier; plain global loads are made to bypass the
+# SM's L1 (cache at L2 only) so that no stale L1 line is read.  Read-only scene data is
+# fetched with __ldg and keeps its caching.
+PER_FILE_FLAGS = {"persistent.cu": ["-Xptxas", "-dlcm=cg"]}
 
 
 def _cuda_home() -> str:
@@ -53,7 +58,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         objs.append(obj)
         if force or _stale(obj, [src] + headers):
             cmd = [nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
-                   "-I", SRC, "-I", os.path.join(ROOT, "include"), *ptxas_v, "-c", src, "-o", obj]
+                   "-I", SRC, "-I", os.path.join(ROOT, "include"), *ptxas_v, *PER_FILE_FLAGS.get(f, []),
+                   "-c", src, "-o", obj]
             jobs.append(cmd)
     for f in CXX_SOURCES:
         src = os.path.join(SRC, f)

@@ -703,6 +703,8 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
     s->stats.rays_closest = (int64_t)s->h_ctl->rays_closest;
     s->stats.rays_shadow = (int64_t)s->h_ctl->rays_shadow;
     s->stats.crossings = (int64_t)s->h_ctl->crossings;
+  s->stats.tile_shaded = (int64_t)s->h_ctl->tile_shaded;
+    s->stats.tile_shaded = (int64_t)s->h_ctl->tile_shaded;
     s->stats.bytes_ray_state = s->stats.rays_closest * 44 + s->stats.rays_shadow * 44;
     s->stats.ms_total = s->stats.ms_persistent;
     return SDD_OK;
@@ -773,6 +775,7 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
   s->stats.rays_closest = (int64_t)s->h_ctl->rays_closest;
   s->stats.rays_shadow = (int64_t)s->h_ctl->rays_shadow;
   s->stats.crossings = (int64_t)s->h_ctl->crossings;
+  s->stats.tile_shaded = (int64_t)s->h_ctl->tile_shaded;
   // traversal ray-state traffic: per closest visit read queue index 4 B + origin/direction
   // 32 B, write hit 8 B or hand-off 4 B; per shadow visit read 4 + 32 + 8 B.
   s->stats.bytes_ray_state = s->stats.rays_closest * 44 + s->stats.rays_shadow * 44;

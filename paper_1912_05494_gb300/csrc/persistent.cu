@@ -73,8 +73,12 @@ __device__ bool grid_barrier(PersistCtl* pc, Control* ctl) {
 }
 
 // Exclusive prefix sums of the n_sub queue counts into shared memory; returns the total.
+// The leading barrier keeps thread 0 from overwriting s_prefix / s_total while another
+// thread still reads the previous call's values: a pass that finds its queues empty leaves
+// without a grid barrier, so two calls can follow each other with no barrier in between.
 __device__ int load_prefix(const int* counts, int n_sub, int cap, int* s_prefix) {
   __shared__ int s_total;
+  __syncthreads();
   if (threadIdx.x == 0) {
     int acc = 0;
     for (int s = 0; s < n_sub; ++s) {

@@ -147,6 +147,9 @@ __device__ __forceinline__ void tile_frame(float L, float3 p, float3 n, float3 d
 }
 
 constexpr float kCos1Deg = 0.99984769515639124f;
+// Node steps of one warp-uniform walk beyond which it is abandoned with the stack-overflow
+// error (a walk visits each node at most once; the largest trees have ~2M nodes).
+constexpr int kMaxTraversalSteps = 1 << 22;
 constexpr int kTileEvents = 64;
 
 struct ShadowKey {
@@ -292,6 +295,177 @@ __device__ __forceinline__ float shadow_T(const RenderParams& p, const DevScene&
   return T;
 }
 
+// closest_hit as a warp-uniform walk, for the host-driven traversal kernel (whose subdomain
+// is the block's, so the lanes enter converged).  Every lane of the warp calls it (live =
+// false for lanes without a ray).  Each iteration every lane still traversing takes one node
+// step (box tests of both children, the triangles of any leaf child, then push / pop) and
+// the warp reconverges at the vote that ends the step.  A data-dependent loop per lane lets
+// the warp split into groups that each iterate on their own: on incoherent rays of large
+// scenes only ~3 of 32 lanes then issue together.
+template <bool kStats>
+__device__ __forceinline__ uint32_t closest_hit_warp(const DevScene& sc, const Node* s_nodes, int n_staged, int s,
+                                                const RayPre& rp, float t0, float t1, bool live, float* t_out,
+                                                uint32_t* n_nodes, uint32_t* n_tris, bool* overflow) {
+  int stack[kStackSize];
+  int sp = 0;
+  const int root = sc.root[s];
+  int node = root;
+  float tbest = t1;
+  uint32_t best = kMissPrim;
+  bool done = !live;
+  int steps = 0;
+  // One vote per step, executed by all 32 lanes at the same instruction (no lane skips to
+  // it by another path): finished lanes only wait at the bottom of the loop.
+  bool any = __any_sync(0xffffffffu, !done);
+  while (any) {
+   if (!done && ++steps > kMaxTraversalSteps) {
+    *overflow = true;  // a tree walk never takes this many steps: report it and stop
+    done = true;
+   }
+   if (!done) {
+    Node n = load_node(sc.nodes, s_nodes, node, root, n_staged);
+    if (kStats) ++*n_nodes;
+    float tn0, tn1;
+    bool h0 = n.d.x >= 0 && box_hit(rp, n.a.x, n.a.y, n.a.z, n.a.w, n.c.x, n.c.y, t0, tbest, &tn0);
+    bool h1 = n.d.y >= 0 && box_hit(rp, n.b.x, n.b.y, n.b.z, n.b.w, n.c.z, n.c.w, t0, tbest, &tn1);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      bool hc = c == 0 ? h0 : h1;
+      int cnt = c == 0 ? n.d.z : n.d.w;
+      if (hc && cnt > 0) {
+        int first = c == 0 ? n.d.x : n.d.y;
+        for (int i = first; i < first + cnt; ++i) {
+          const float4* tp = reinterpret_cast<const float4*>(sc.tris + i);
+          float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
+          if (kStats) ++*n_tris;
+          float t = tri_hit(rp, v0, v1, v2, t0, tbest);
+          if (t >= 0.f) {
+            uint32_t prim = __float_as_uint(v0.w);
+            if (t < tbest || prim < best) {
+              tbest = t;
+              best = prim;
+            }
+          }
+        }
+        if (c == 0) h0 = false; else h1 = false;
+      }
+    }
+    if (h0 && h1) {
+      bool first0 = tn0 <= tn1;
+      if (sp < kStackSize) stack[sp++] = first0 ? n.d.y : n.d.x;
+      else *overflow = true;
+      node = first0 ? n.d.x : n.d.y;
+    } else if (h0) {
+      node = n.d.x;
+    } else if (h1) {
+      node = n.d.y;
+    } else if (sp == 0) {
+      done = true;
+    } else {
+      node = stack[--sp];
+    }
+   }
+    any = __any_sync(0xffffffffu, !done);
+  }
+  *t_out = tbest;
+  return best;
+}
+
+// shadow_T as a warp-uniform walk (see closest_hit_warp); every lane of the warp calls it.
+template <bool kStats, int kTM>
+__device__ __forceinline__ float shadow_T_warp(const RenderParams& p, const DevScene& sc, const DevSpectral& sp, int lam,
+                                          float lambda_nm, const ShadowKey& key, const Node* s_nodes, int n_staged,
+                                          int s, const RayPre& rp, float3 d, float t0, float t1, bool live,
+                                          uint32_t* n_nodes, uint32_t* n_tris, bool* overflow) {
+  int stack[kStackSize];
+  int spn = 0;
+  const int root = sc.root[s];
+  int node = root;
+  float T = 1.f;
+  bool done = !live;
+  int steps = 0;
+  bool any = __any_sync(0xffffffffu, !done);
+  while (any) {
+   if (!done && ++steps > kMaxTraversalSteps) {
+    *overflow = true;
+    T = 0.f;
+    done = true;
+   }
+   if (!done) {
+    Node n = load_node(sc.nodes, s_nodes, node, root, n_staged);
+    if (kStats) ++*n_nodes;
+    float tn0, tn1;
+    bool h0 = n.d.x >= 0 && box_hit(rp, n.a.x, n.a.y, n.a.z, n.a.w, n.c.x, n.c.y, t0, t1, &tn0);
+    bool h1 = n.d.y >= 0 && box_hit(rp, n.b.x, n.b.y, n.b.z, n.b.w, n.c.z, n.c.w, t0, t1, &tn1);
+    bool blocked = false;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      bool hc = c == 0 ? h0 : h1;
+      int cnt = c == 0 ? n.d.z : n.d.w;
+      if (hc && cnt > 0 && !blocked) {
+        int first = c == 0 ? n.d.x : n.d.y;
+        for (int i = first; i < first + cnt && !blocked; ++i) {
+          const float4* tp = reinterpret_cast<const float4*>(sc.tris + i);
+          float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
+          if (kStats) ++*n_tris;
+          float t = tri_hit(rp, v0, v1, v2, t0, t1);
+          if (t >= 0.f) {
+            uint32_t prim = __float_as_uint(v0.w);
+            float4 nm = __ldg(sc.prim_nrm_mat + prim);
+            int mat = __float_as_int(nm.w);
+            int kind = __ldg(sp.mat_kind + mat);
+            size_t mi = (size_t)mat * sp.n_lambda + lam;
+            if (kind == MAT_SLAB) {
+              float cos_i = fabsf(dot3(d, f3(nm)));
+              float Rs, Ts;
+              slab_RT(cos_i, __ldg(sp.mat_n + mi), __ldg(sp.mat_k + mi), __ldg(sp.mat_thick + mat), lambda_nm, &Rs,
+                      &Ts);
+              T *= Ts;
+            } else if (kTM != 0 && kind == MAT_TILE) {
+              if (kTM == 2) {
+                T *= __ldg(p.tile_sun_T + mi);  // network: transmittance x ballistic fraction
+              } else {
+                // one brute-force ray through the tile: counts if it leaves on the far side
+                // within 1 degree of the shadow direction
+                float x, y;
+                float3 dl, t1v, t2v;
+                tile_frame(p.tiles.L, rp.o + t * d, f3(nm), d, &x, &y, &dl, &t1v, &t2v);
+                TileOut r = tile_trace(tile_of(p.tiles, __ldg(p.mat_tile + mat)), x, y, dl, __ldg(sp.mat_n + mi),
+                                       __ldg(sp.mat_k + mi), lambda_nm, key.pixel, key.sample, key.bounce, lam,
+                                       key.seed, kTileEvents, STREAM_SHADOW_TILE);
+                if (r.side == 1 && dot3(r.dir, dl) > kCos1Deg) T *= r.w;
+                else blocked = true;
+              }
+            } else {
+              blocked = true;
+            }
+          }
+        }
+        if (c == 0) h0 = false; else h1 = false;
+      }
+    }
+    if (blocked) {
+      T = 0.f;
+      done = true;
+    } else if (h0 && h1) {
+      if (spn < kStackSize) stack[spn++] = n.d.x;
+      else *overflow = true;
+      node = n.d.y;
+    } else if (h0) {
+      node = n.d.x;
+    } else if (h1) {
+      node = n.d.y;
+    } else if (spn == 0) {
+      done = true;
+    } else {
+      node = stack[--spn];
+    }
+   }
+    any = __any_sync(0xffffffffu, !done);
+  }
+  return T;
+}
+
 __device__ __forceinline__ float3 offset_point(float3 p, float3 ng, float3 dir, float eps) {
   return dot3(dir, ng) >= 0.f ? p + eps * ng : p - eps * ng;
 }
@@ -405,6 +579,52 @@ __device__ __forceinline__ void dev_traverse(const RenderParams& p, int s, int i
       RayPre rp = ray_pre(o, d);
       prim = closest_hit<kStats>(p.sc, s_nodes, n_staged, s, rp, t0, t1, &t, &nn, &nt, &ovf);
     }
+    if (ovf) atomicOr(&ctl->error, ERR_STACK_OVERFLOW);
+    cross = prim == kMissPrim && next >= 0;
+    if (!cross) hits[r] = make_float2(prim == kMissPrim ? CUDART_INF_F : t, __uint_as_float(prim));
+  }
+  int pos = warp_append(qp.out_count, cross ? next : 0, cross);
+  if (cross) {
+    if (pos < qp.cap) qp.out[(size_t)next * qp.cap + pos] = r;
+    else atomicOr(&ctl->error, ERR_QUEUE_OVERFLOW);
+  }
+  if (kStats) {
+    unsigned long long a = warp_sum<unsigned long long>(active ? 1ull : 0ull);
+    unsigned long long c = warp_sum<unsigned long long>(cross ? 1ull : 0ull);
+    unsigned long long n1 = warp_sum<unsigned long long>(nn);
+    unsigned long long n2 = warp_sum<unsigned long long>(nt);
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&ctl->rays_closest, a);
+      atomicAdd(&ctl->crossings, c);
+      atomicAdd(&ctl->node_visits, n1);
+      atomicAdd(&ctl->tri_tests, n2);
+    }
+  }
+}
+
+
+// dev_traverse with the warp-uniform walk (host-driven traversal kernel).
+template <bool kStats>
+__device__ __forceinline__ void dev_traverse_warp(const RenderParams& p, int s, int i, bool active, const Node* s_nodes,
+                                             int n_staged, QueuePair qp, RayBuf rb, float2* hits, Control* ctl) {
+  uint32_t r = active ? qp.in[(size_t)s * qp.cap + i] : 0u;
+  bool cross = false;
+  int next = -1;
+  uint32_t nn = 0, nt = 0;
+  float t0 = 0.f, t1 = 0.f;
+  float3 o = make_float3(0.f, 0.f, 0.f), d = make_float3(0.f, 0.f, 1.f);
+  if (active) {
+    float4 O = rb.o[r], D = rb.d[r];
+    o = f3(O);
+    d = f3(D);
+    slab_interval(p.sc, s, o, d, &t0, &t1, &next);
+  }
+  const bool live = active && t1 > t0;
+  float t = t1;
+  bool ovf = false;
+  const RayPre rp = ray_pre(o, d);
+  const uint32_t prim = closest_hit_warp<kStats>(p.sc, s_nodes, n_staged, s, rp, t0, t1, live, &t, &nn, &nt, &ovf);
+  if (active) {
     if (ovf) atomicOr(&ctl->error, ERR_STACK_OVERFLOW);
     cross = prim == kMissPrim && next >= 0;
     if (!cross) hits[r] = make_float2(prim == kMissPrim ? CUDART_INF_F : t, __uint_as_float(prim));
@@ -654,6 +874,63 @@ __device__ __forceinline__ void dev_shadow(const RenderParams& p, const WaveDesc
       T = shadow_T<kStats, kTM>(p, p.sc, p.sp, (int)id.lam, __ldg(p.sp.lambda_nm + id.lam), key, s_nodes, n_staged, s, rp,
                            d, t0, t1, &nn, &nt, &ovf);
     }
+    if (ovf) atomicOr(&ctl->error, ERR_STACK_OVERFLOW);
+    bool blocked = !(T > 0.f);
+    float contrib = D.w * T;
+    cross = !blocked && next >= 0;
+    if (cross) {
+      sb.d[r].w = contrib;
+    } else {
+      if (!blocked) path_L[inf.x * (uint32_t)p.n_slots + (inf.y & 0xFFFFu)] += contrib;
+      if (p.path_hash && p.mode == 1)
+        p.path_hash[inf.x] = fnv_byte(p.path_hash[inf.x], blocked ? EV_SHADOW_BLOCKED : EV_SHADOW_OPEN);
+    }
+  }
+  int pos = warp_append(qp.out_count, cross ? next : 0, cross);
+  if (cross) {
+    if (pos < qp.cap) qp.out[(size_t)next * qp.cap + pos] = r;
+    else atomicOr(&ctl->error, ERR_SHADOW_OVERFLOW);
+  }
+  if (kStats) {
+    unsigned long long a = warp_sum<unsigned long long>(active ? 1ull : 0ull);
+    unsigned long long n1 = warp_sum<unsigned long long>(nn);
+    unsigned long long n2 = warp_sum<unsigned long long>(nt);
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&ctl->rays_shadow, a);
+      atomicAdd(&ctl->shadow_node_visits, n1);
+      atomicAdd(&ctl->shadow_tri_tests, n2);
+    }
+  }
+}
+
+
+// dev_shadow with the warp-uniform walk (host-driven shadow kernel).
+template <bool kStats, int kTM>
+__device__ __forceinline__ void dev_shadow_warp(const RenderParams& p, const WaveDesc& w, int s, int i, bool active,
+                                           const Node* s_nodes, int n_staged, QueuePair qp, ShadowBuf sb,
+                                           float* path_L, Control* ctl) {
+  uint32_t r = active ? qp.in[(size_t)s * qp.cap + i] : 0u;
+  bool cross = false;
+  int next = -1;
+  uint32_t nn = 0, nt = 0;
+  float4 O = make_float4(0.f, 0.f, 0.f, 0.f), D = make_float4(0.f, 0.f, 1.f, 0.f);
+  uint2 inf = make_uint2(0u, 0u);
+  float t0 = 0.f, t1 = 0.f;
+  if (active) {
+    O = sb.o[r];
+    D = sb.d[r];
+    inf = sb.info[r];
+    slab_interval(p.sc, s, f3(O), f3(D), &t0, &t1, &next);
+  }
+  const float3 o = f3(O), d = f3(D);
+  const PathId id = path_id(p, w, inf.x);
+  const ShadowKey key{id.pixel, id.sample, inf.y >> 16, p.seed};
+  const bool live = active && t1 > t0;
+  bool ovf = false;
+  const RayPre rp = ray_pre(o, d);
+  const float T = shadow_T_warp<kStats, kTM>(p, p.sc, p.sp, (int)id.lam, __ldg(p.sp.lambda_nm + id.lam), key,
+                                             s_nodes, n_staged, s, rp, d, t0, t1, live, &nn, &nt, &ovf);
+  if (active) {
     if (ovf) atomicOr(&ctl->error, ERR_STACK_OVERFLOW);
     bool blocked = !(T > 0.f);
     float contrib = D.w * T;

@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(kB) k_traverse(RenderParams p, Sched sch, int 
   while (s + 1 < sch.n_sub && sch.blk_start[s + 1] <= b) ++s;
   int n_staged = top_nodes > 0 ? stage_top(p.sc, s_nodes, s, top_nodes) : 0;
   int i = (b - sch.blk_start[s]) * blockDim.x + threadIdx.x;
-  dev_traverse<kStats>(p, s, i, i < sch.count[s], s_nodes, n_staged, qp, rb, hits, ctl);
+  dev_traverse_warp<kStats>(p, s, i, i < sch.count[s], s_nodes, n_staged, qp, rb, hits, ctl);
 }
 
 template <int kTM>
@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(kB) k_shadow(RenderParams p, WaveDesc w, Sched
   while (s + 1 < sch.n_sub && sch.blk_start[s + 1] <= b) ++s;
   int n_staged = top_nodes > 0 ? stage_top(p.sc, s_nodes, s, top_nodes) : 0;
   int i = (b - sch.blk_start[s]) * blockDim.x + threadIdx.x;
-  dev_shadow<kStats, kTM>(p, w, s, i, i < sch.count[s], s_nodes, n_staged, qp, sb, path_L, ctl);
+  dev_shadow_warp<kStats, kTM>(p, w, s, i, i < sch.count[s], s_nodes, n_staged, qp, sb, path_L, ctl);
 }
 
 // ------------------------------------------------------------------------------ film

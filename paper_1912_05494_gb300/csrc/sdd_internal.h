@@ -106,6 +106,7 @@ struct Control {
   int tile_hits;                        // tile hits queued for the network this generation
   unsigned long long node_visits, tri_tests, shadow_node_visits, shadow_tri_tests;
   unsigned long long rays_closest, rays_shadow, crossings;
+  unsigned long long tile_shaded;       // tile hits shaded by the network (profiling level >= 2)
 };
 
 enum RayFlags : uint32_t { FLAG_SUN_COUNTED = 1u };

@@ -110,6 +110,7 @@ struct TileShadePolicy {
   }
   // Threads 0..127 (whole warps) take one row each and append its exit ray.
   __device__ void consume(const Ctx& c, int row0, int valid, const float* pred) const {
+    if (p.stats >= 2 && threadIdx.x == 0) atomicAdd(&ctl->tile_shaded, (unsigned long long)valid);
     if (threadIdx.x >= kInferRows) return;
     const int i = threadIdx.x;
     const bool active = i < valid;

@@ -323,6 +323,16 @@ def nave_scene(seed: int = 1, cell: float = 0.25, windows_per_wall: int = 12,
     return scene, cam, spec
 
 
+def large_nave_scene(seed: int = 5, n_subdomains: int = 8, spp: int = 64):
+    """The large batched frame: the procedural nave refined to ~1.07M triangles (0.1 m wall
+    cells) with 96 windows (two rows of 24 per long wall, sills at 2 m and 8 m) of 10 x 40
+    heterogeneous tiles each (38,400 tiles drawing on the 512-tile set of seed 3);
+    3840 x 2160, 81 wavelengths, depth 16, Russian roulette from depth 3."""
+    return nave_scene(seed=seed, cell=0.1, windows_per_wall=24, tiles_x=10, tiles_z=40, sills=(2.0, 8.0),
+                      hetero_tiles=512, tile_seed=3, n_subdomains=n_subdomains, width=3840, height=2160, spp=spp,
+                      max_depth=16, rr_start_depth=3)
+
+
 def tile_room_scene(seed: int = 2, n_tiles: int = 16, width: int = 48, height: int = 32, spp: int = 4):
     """A 6 x 6 x 4 m room whose y = 0 wall holds a 1 m x 1 m window of 10 x 10 heterogeneous
     tiles (tiles drawn from a seeded tile set), lit by the sky and a sun at 35 degrees that
