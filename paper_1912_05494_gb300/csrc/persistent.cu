@@ -72,18 +72,23 @@ __device__ bool grid_barrier(PersistCtl* pc, Control* ctl) {
   return s_ok != 0;
 }
 
-// Exclusive prefix sums of the n_sub queue counts into shared memory; returns the total.
-// The leading barrier keeps thread 0 from overwriting s_prefix / s_total while another
+// Per-subdomain queue counts (clamped to cap) into s_count and the exclusive prefix sums of
+// the counts rounded up to whole chunks of kPB rays into s_prefix; returns the padded total.
+// A chunk then never straddles two subdomains, so every block works on one subdomain's
+// queue at a time and its warps enter the traversal converged.
+// The leading barrier keeps thread 0 from overwriting the shared arrays while another
 // thread still reads the previous call's values: a pass that finds its queues empty leaves
 // without a grid barrier, so two calls can follow each other with no barrier in between.
-__device__ int load_prefix(const int* counts, int n_sub, int cap, int* s_prefix) {
+__device__ int load_prefix(const int* counts, int n_sub, int cap, int* s_prefix, int* s_count) {
   __shared__ int s_total;
   __syncthreads();
   if (threadIdx.x == 0) {
     int acc = 0;
     for (int s = 0; s < n_sub; ++s) {
+      const int c = min(max(((volatile const int*)counts)[s], 0), cap);
+      s_count[s] = c;
       s_prefix[s] = acc;
-      acc += min(max(((volatile const int*)counts)[s], 0), cap);
+      acc += (c + kPB - 1) / kPB * kPB;
     }
     s_prefix[n_sub] = acc;
     s_total = acc;
@@ -112,10 +117,13 @@ __device__ __forceinline__ void clear_ahead(int (*counts)[kMaxSubdomains], int* 
 
 }  // namespace
 
+// Six resident blocks per SM (registers bounded at 80, no spills) for scenes without
+// brute-force tiles; the brute-force tile tracer needs 128 registers (four blocks).
 template <bool kStats, int kTM>
-__global__ void __launch_bounds__(kPB) k_persistent_wave(RenderParams p, WaveDesc w, PersistBuffers b,
+__global__ void __launch_bounds__(kPB, kTM == 1 ? 4 : 6) k_persistent_wave(RenderParams p, WaveDesc w, PersistBuffers b,
                                                          PersistCtl* pc, Control* ctl, int seg) {
   __shared__ int s_prefix[kMaxSubdomains + 1];
+  __shared__ int s_count[kMaxSubdomains];
   __shared__ int s_chunk;
   const int n_sub = p.sc.n_sub;
   const uint32_t nthreads = gridDim.x * blockDim.x;
@@ -154,7 +162,7 @@ __global__ void __launch_bounds__(kPB) k_persistent_wave(RenderParams p, WaveDes
       }
       bool ran_pass = false;
       for (int pass = 0; pass <= 2 * kMaxSubdomains + 2; ++pass) {
-        int total = load_prefix(pc->qc[S.cq], n_sub, b.qcap, s_prefix);
+        int total = load_prefix(pc->qc[S.cq], n_sub, b.qcap, s_prefix, s_count);
         clear_ahead(pc->qc, pc->wq, (S.cq + 2) % 3);
         if (total == 0) break;
         QueuePair qp{b.q[S.qe], b.q[1 - S.qe], pc->qc[(S.cq + 1) % 3], b.qcap};
@@ -164,10 +172,9 @@ __global__ void __launch_bounds__(kPB) k_persistent_wave(RenderParams p, WaveDes
           const int c0 = s_chunk;
           __syncthreads();
           if (c0 >= total) break;
-          const int j = c0 + (int)threadIdx.x;
-          const bool act = j < total;
-          const int s = find_subdomain(s_prefix, n_sub, act ? j : 0);
-          dev_traverse<kStats>(p, s, j - s_prefix[s], act, nullptr, 0, qp, b.rb[S.cur], b.hits, ctl);
+          const int s = find_subdomain(s_prefix, n_sub, c0);  // the whole chunk's subdomain
+          const int i = c0 - s_prefix[s] + (int)threadIdx.x;
+          dev_traverse_warp<kStats>(p, s, i, i < s_count[s], nullptr, 0, qp, b.rb[S.cur], b.hits, ctl);
         }
         ran_pass = true;
         if (!grid_barrier(pc, ctl)) return;
@@ -197,7 +204,7 @@ __global__ void __launch_bounds__(kPB) k_persistent_wave(RenderParams p, WaveDes
     }
 
     for (int pass = 0; pass <= 2 * kMaxSubdomains + 2; ++pass) {
-      int total = load_prefix(pc->sqc[S.sq], n_sub, b.qcap, s_prefix);
+      int total = load_prefix(pc->sqc[S.sq], n_sub, b.qcap, s_prefix, s_count);
       clear_ahead(pc->sqc, pc->wsq, (S.sq + 2) % 3);
       if (total == 0) break;
       QueuePair qp{b.sq[S.se], b.sq[1 - S.se], pc->sqc[(S.sq + 1) % 3], b.qcap};
@@ -207,10 +214,13 @@ __global__ void __launch_bounds__(kPB) k_persistent_wave(RenderParams p, WaveDes
         const int c0 = s_chunk;
         __syncthreads();
         if (c0 >= total) break;
-        const int j = c0 + (int)threadIdx.x;
-        const bool act = j < total;
-        const int s = find_subdomain(s_prefix, n_sub, act ? j : 0);
-        dev_shadow<kStats, kTM>(p, w, s, j - s_prefix[s], act, nullptr, 0, qp, b.sb, b.path_L, ctl);
+        const int s = find_subdomain(s_prefix, n_sub, c0);
+        const int i = c0 - s_prefix[s] + (int)threadIdx.x;
+        if constexpr (kTM == 1) {  // the same walk choice as the host-driven shadow kernel
+          dev_shadow_warp<kStats, kTM>(p, w, s, i, i < s_count[s], nullptr, 0, qp, b.sb, b.path_L, ctl);
+        } else {
+          dev_shadow<kStats, kTM>(p, w, s, i, i < s_count[s], nullptr, 0, qp, b.sb, b.path_L, ctl);
+        }
       }
       if (!grid_barrier(pc, ctl)) return;
       S.sq = (S.sq + 1) % 3;

@@ -54,7 +54,13 @@ __global__ void __launch_bounds__(kB) k_shadow(RenderParams p, WaveDesc w, Sched
   while (s + 1 < sch.n_sub && sch.blk_start[s + 1] <= b) ++s;
   int n_staged = top_nodes > 0 ? stage_top(p.sc, s_nodes, s, top_nodes) : 0;
   int i = (b - sch.blk_start[s]) * blockDim.x + threadIdx.x;
-  dev_shadow_warp<kStats, kTM>(p, w, s, i, i < sch.count[s], s_nodes, n_staged, qp, sb, path_L, ctl);
+  // Any-hit rays without brute-force tiles are short and end early: the per-lane walk is
+  // faster for them; with brute-force tile tracing inside the walk the warp-uniform one is.
+  if constexpr (kTM == 1) {
+    dev_shadow_warp<kStats, kTM>(p, w, s, i, i < sch.count[s], s_nodes, n_staged, qp, sb, path_L, ctl);
+  } else {
+    dev_shadow<kStats, kTM>(p, w, s, i, i < sch.count[s], s_nodes, n_staged, qp, sb, path_L, ctl);
+  }
 }
 
 // ------------------------------------------------------------------------------ film
