@@ -51,8 +51,8 @@ sys.path.insert(0, ROOT)
 METRIC = "Mspectral-samples/s at <=1% rel. image error vs FP64 oracle; surrogate vs plain"
 UNIT = "Mspectral-samples/s"
 WORKLOAD = "nave-200k {w}x{h} {spp}spp 81lambda depth12 RR S={s} (plain Monte Carlo)"
-TRAVERSE_SOURCES = ["paper_1912_05494_gb300/csrc/render_kernels.cu", "paper_1912_05494_gb300/csrc/device_math.cuh",
-                    "paper_1912_05494_gb300/csrc/sdd_internal.h"]
+TRAVERSE_SOURCES = ["paper_1912_05494_gb300/csrc/render_kernels.cu", "paper_1912_05494_gb300/csrc/render_device.cuh",
+                    "paper_1912_05494_gb300/csrc/device_math.cuh", "paper_1912_05494_gb300/csrc/sdd_internal.h"]
 NCU_SUMMARY = os.path.join(ROOT, "profiles", "traverse_nave_ncu.md")
 
 
