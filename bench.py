@@ -469,6 +469,7 @@ def run_large(args):
     clocks = ClockSampler(0)
     clocks.start()
     ms_net, launches_net, img_net, _ = timed(net_kw, args.steps, args.warmup)
+    ms_net_host, launches_net_host, _, ms_tile = timed({**net_kw, "batched": 0}, args.steps, args.warmup)
     ms_plain, launches_plain, img_plain, _ = timed({"batched": 0}, args.steps, args.warmup)
     clk = clocks.stop()
     spec2 = S.RenderSpec(**{**spec.__dict__, "seed": spec.seed + 4099})
@@ -490,7 +491,12 @@ def run_large(args):
                            "network_batched": {"value": value_net, "ms_per_step": ms_net,
                                                "gpu_launches": launches_net,
                                                "form": "persistent kernels + CUDA graph, fused tile shading"},
+                           "network_host_driven": {"value": frame_paths / (ms_net_host / 1e3) / 1e6,
+                                                   "ms_per_step": ms_net_host, "gpu_launches": launches_net_host,
+                                                   "ms_tile_shading": ms_tile,
+                                                   "form": "host-driven wavefront, fused tile shading"},
                            "speedup": ms_plain / ms_net,
+                           "speedup_host_driven_network": ms_plain / ms_net_host,
                            "image_error_block8": rel_err(bn, bp), "noise_floor_block8": rel_err(bp2, bp),
                            "image_error_full": rel_err(img_net, img_plain), "noise_floor_full": rel_err(img_plain2,
                                                                                                      img_plain)},
