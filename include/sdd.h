@@ -175,15 +175,26 @@ sdd_status sdd_render_to_host(sdd_scene* scene, const sdd_camera* cam, const sdd
  *                   traversal block stages in shared memory, 0..640 (0 = none, default);
  *   wave_paths:     paths per wave when sdd_render_opts.wave_paths is 0 (0 = 2^26);
  *   no_graph:       batched form only: 1 = launch the frame's kernels directly instead of
- *                   capturing and replaying them as a CUDA graph (default 0). */
+ *                   capturing and replaying them as a CUDA graph (default 0);
+ *   queue_capacity: upper bound on the entries of each ray / subdomain queue (0 = automatic:
+ *                   the wave size, 4x in deterministic mode).  Buffers keep their automatic
+ *                   size; a frame that needs more returns SDD_ERR_QUEUE_OVERFLOW. */
 typedef struct {
   int traverse_block;
   int top_nodes;
   int wave_paths;
   int no_graph;
+  int queue_capacity;
 } sdd_tuning;
 sdd_status sdd_set_tuning(sdd_scene* scene, const sdd_tuning* tuning);
 sdd_status sdd_get_tuning(const sdd_scene* scene, sdd_tuning* out);
+
+/* Self-test of the persistent kernel's watchdog (the paper has no counterpart): a grid
+ * barrier of the batched form is run by four blocks, one of which never arrives; the waiting
+ * blocks give up after timeout_ms (1..10000) and raise the timeout error bit.  Returns
+ * SDD_ERR_TIMEOUT when that happened, SDD_OK if the barrier had completed (it cannot), or
+ * SDD_ERR_CUDA / SDD_ERR_ARG.  No GPU fault or hang is involved: every wait is bounded. */
+sdd_status sdd_watchdog_selftest(int timeout_ms);
 
 /* Per-kernel timing and counters of the most recent render. */
 typedef struct {

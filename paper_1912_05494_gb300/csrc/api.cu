@@ -685,7 +685,9 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
   }
 
   s->stats = sdd_stats{};
-  const int qcap = (int)cap;
+  // queue capacity seen by the kernels (every append is checked against it); the buffers
+  // above keep the automatic size
+  const int qcap = (int)(s->tuning.queue_capacity > 0 ? std::min<size_t>(cap, (size_t)s->tuning.queue_capacity) : cap);
   if (o->batched) {
     r = render_batched(s, p, waves, n_slots, qcap, o, spectral_out, xyz_out, st);
     if (r) return r;
@@ -1015,6 +1017,25 @@ sdd_status sdd_render_to_host(sdd_scene* s, const sdd_camera* cam, const sdd_ren
   return SDD_OK;
 }
 
+sdd_status sdd_watchdog_selftest(int timeout_ms) {
+  if (timeout_ms < 1 || timeout_ms > 10000) return fail(SDD_ERR_ARG, "timeout_ms must be in [1, 10000]");
+  PersistCtl* pc = nullptr;
+  Control* ctl = nullptr;
+  cudaError_t e = cudaMalloc(&pc, sizeof(PersistCtl));
+  if (e == cudaSuccess) e = cudaMalloc(&ctl, sizeof(Control));
+  if (e == cudaSuccess) e = cudaMemset(pc, 0, sizeof(PersistCtl));
+  if (e == cudaSuccess) e = cudaMemset(ctl, 0, sizeof(Control));
+  if (e == cudaSuccess) e = barrier_selftest(pc, ctl, timeout_ms);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  Control h{};
+  if (e == cudaSuccess) e = cudaMemcpy(&h, ctl, sizeof(Control), cudaMemcpyDeviceToHost);
+  cudaFree(pc);
+  cudaFree(ctl);
+  if (e != cudaSuccess) return fail(SDD_ERR_CUDA, cudaGetErrorString(e));
+  if (h.error & ERR_TIMEOUT) return fail(SDD_ERR_TIMEOUT, "grid barrier gave up after its time limit");
+  return SDD_OK;
+}
+
 sdd_status sdd_set_tuning(sdd_scene* s, const sdd_tuning* t) {
   if (!s || !t) return fail(SDD_ERR_ARG, "NULL argument");
   if (t->traverse_block != 64 && t->traverse_block != 128 && t->traverse_block != 256)
@@ -1022,6 +1043,7 @@ sdd_status sdd_set_tuning(sdd_scene* s, const sdd_tuning* t) {
   if (t->top_nodes < 0 || t->top_nodes > 640) return fail(SDD_ERR_ARG, "top_nodes must be in [0, 640]");
   if (t->wave_paths < 0) return fail(SDD_ERR_ARG, "wave_paths must be >= 0");
   if (t->no_graph != 0 && t->no_graph != 1) return fail(SDD_ERR_ARG, "no_graph must be 0 or 1");
+  if (t->queue_capacity < 0) return fail(SDD_ERR_ARG, "queue_capacity must be >= 0");
   s->tuning = *t;
   return SDD_OK;
 }

@@ -40,7 +40,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Grid-wide barrier with a time limit.  Returns false when the wave must be abandoned.
-__device__ bool grid_barrier(PersistCtl* pc, Control* ctl) {
+__device__ bool grid_barrier(PersistCtl* pc, Control* ctl, unsigned long long timeout_ns = kBarrierTimeoutNs) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -57,7 +57,7 @@ __device__ bool grid_barrier(PersistCtl* pc, Control* ctl) {
       unsigned long long t0 = global_ns();
       while (*vgen == g) {
         if (*vabort) break;
-        if (global_ns() - t0 > kBarrierTimeoutNs) {
+        if (global_ns() - t0 > timeout_ns) {
           atomicExch(&pc->abort, 1);
           atomicOr(&ctl->error, ERR_TIMEOUT);  // survives the next wave's reset of pc
           break;
@@ -242,6 +242,18 @@ static int persistent_blocks() {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent_wave<kStats, kTM>, kPB, 0);
   return sms * per_sm;
+}
+
+// Watchdog self-test: every block but the last enters a grid barrier that the last block
+// never reaches; the waiting blocks give up after timeout_ns.
+__global__ void k_barrier_selftest(PersistCtl* pc, Control* ctl, unsigned long long timeout_ns) {
+  if (blockIdx.x == gridDim.x - 1) return;
+  grid_barrier(pc, ctl, timeout_ns);
+}
+
+cudaError_t barrier_selftest(PersistCtl* pc, Control* ctl, int timeout_ms) {
+  k_barrier_selftest<<<4, kPB>>>(pc, ctl, (unsigned long long)timeout_ms * 1000000ull);
+  return cudaGetLastError();
 }
 
 // Blocks of the cooperative launch for a scene's tile mode (0 none, 1 brute force, 2 network).

@@ -45,6 +45,8 @@ struct PersistCtl {
 };
 
 int persistent_grid(bool stats, int tile_mode);
+// Runs k_barrier_selftest (four blocks, the last never arrives) on the legacy stream.
+cudaError_t barrier_selftest(PersistCtl* pc, Control* ctl, int timeout_ms);
 cudaError_t launch_persistent_wave(const RenderParams& p, const WaveDesc& w, const PersistBuffers& b, PersistCtl* pc,
                                    Control* ctl, int grid, cudaStream_t st, int seg = SEG_WAVE);
 

@@ -679,7 +679,11 @@ __device__ __forceinline__ void dev_shade(const RenderParams& p, const WaveDesc&
     const uint32_t slot = path * (uint32_t)p.n_slots + (mc ? 0u : code);
     uint32_t hsh = p.path_hash ? p.path_hash[path] : 0u;
     uint32_t prim = __float_as_uint(H.y);
-    if (prim == kMissPrim) {
+    if (prim != kMissPrim && prim >= (uint32_t)p.sc.n_prims) {
+      // a ray dropped by a full queue was never traced and its hit record is stale: the frame
+      // already carries the overflow error; nothing is read through the stale index
+      atomicOr(&ctl->error, ERR_QUEUE_OVERFLOW);
+    } else if (prim == kMissPrim) {
       path_L[slot] += thr * escape_radiance(p.sp, d, lam, (flags & FLAG_SUN_COUNTED) != 0u);
       hsh = fnv_byte(fnv_word(hsh, 0xFFFFFFFFu), EV_ESCAPE);
     } else {

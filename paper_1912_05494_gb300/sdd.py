@@ -84,7 +84,8 @@ class sdd_tileset_desc(C.Structure):
 
 
 class sdd_tuning(C.Structure):
-    _fields_ = [("traverse_block", C.c_int), ("top_nodes", C.c_int), ("wave_paths", C.c_int), ("no_graph", C.c_int)]
+    _fields_ = [("traverse_block", C.c_int), ("top_nodes", C.c_int), ("wave_paths", C.c_int), ("no_graph", C.c_int),
+                ("queue_capacity", C.c_int)]
 
 
 class sdd_scene_info(C.Structure):
@@ -140,8 +141,9 @@ def lib():
                      "sdd_philox", "sdd_set_tuning", "sdd_get_tuning", "sdd_tileset_create", "sdd_tileset_heights",
                      "sdd_tile_trace_rays", "sdd_tile_generate", "sdd_surrogate_create", "sdd_surrogate_get_params",
                      "sdd_surrogate_set_params", "sdd_surrogate_gradients", "sdd_surrogate_train_step",
-                     "sdd_surrogate_infer"):
+                     "sdd_surrogate_infer", "sdd_watchdog_selftest"):
             getattr(L, name).restype = C.c_int
+        L.sdd_watchdog_selftest.argtypes = [C.c_int]
         _lib = L
     return _lib
 
@@ -293,6 +295,12 @@ def sdd_render_to_host(h, cam, spec, spectral_out, xyz_out=None, stream=None, **
 
 def sdd_set_profiling(h, level: int):
     _check(lib().sdd_set_profiling(h, int(level)))
+
+
+def sdd_watchdog_selftest(timeout_ms: int = 200):
+    """Runs the batched form's grid barrier with one block that never arrives; raises
+    SddError(SDD_ERR_TIMEOUT) when the watchdog fired (the expected outcome)."""
+    _check(lib().sdd_watchdog_selftest(int(timeout_ms)))
 
 
 def sdd_set_tuning(h, tuning: dict):
