@@ -28,6 +28,7 @@
 #include "../../include/sdd.h"
 #include "surrogate_head.cuh"
 #include "surrogate_net.cuh"
+#include "surrogate_tc.cuh"
 
 namespace sdd {
 sdd_status set_last_error(sdd_status st, const char* msg);
@@ -285,11 +286,12 @@ struct sdd_surrogate {
   float* Zout = nullptr;                     // [batch][16]
   __nv_bfloat16* dZ[2] = {};                 // [batch][128]
   float* loss = nullptr;
+  uint32_t* err = nullptr;  // timeout bit of the inference kernel's bounded waits
   int step = 0;
   unsigned version = 0;  // bumped whenever the weights change
   ~sdd_surrogate() {
     cudaFree(params); cudaFree(grads); cudaFree(m); cudaFree(v); cudaFree(Bm); cudaFree(Wb); cudaFree(Wtb);
-    cudaFree(feat); cudaFree(Zout); cudaFree(loss);
+    cudaFree(feat); cudaFree(Zout); cudaFree(loss); cudaFree(err);
     for (auto* p : Z) cudaFree(p);
     for (auto* p : A) cudaFree(p);
     for (auto* p : dZ) cudaFree(p);
@@ -377,19 +379,20 @@ int infer_grid(int n_max) {
   return std::max(1, std::min(sms, (n_max + kInferRows - 1) / kInferRows));
 }
 
-// Predictions [n][8] for raw inputs [n][7] (fused inference), enqueued on st; with n_dev the
-// row count is read on the device (at most n).
+// Predictions [n][8] for raw inputs [n][7] (fused tcgen05 inference), enqueued on st; with
+// n_dev the row count is read on the device (at most n).  A timeout of the kernel's bounded
+// waits sets the surrogate's error word (checked by sdd_surrogate_infer).
 cudaError_t surrogate_predict(sdd_surrogate* s, int n, const float* raw, float* out, cudaStream_t st,
                               const int* n_dev) {
   static bool prepared = false;
   if (!prepared) {
-    cudaError_t e = infer_prepare<RawPolicy>();
+    cudaError_t e = infer_tc_prepare<RawPolicy>();
     if (e != cudaSuccess) return e;
     prepared = true;
   }
   if (n <= 0) return cudaSuccess;
-  k_infer_fused<RawPolicy><<<infer_grid(n), kInferThreads, kInferSmem, st>>>(surrogate_view(s),
-                                                                             RawPolicy{raw, out, n, n_dev});
+  k_infer_tc<RawPolicy><<<infer_grid(n), tc::kThreads, tc::kSmem, st>>>(surrogate_view(s),
+                                                                       RawPolicy{raw, out, n, n_dev, s->err});
   return cudaGetLastError();
 }
 }  // namespace sdd
@@ -442,10 +445,12 @@ sdd_status sdd_surrogate_create(const float* fourier_B, const float* init_params
   A(dalloc(&s->dZ[0], mb * kHid));
   A(dalloc(&s->dZ[1], mb * kHid));
   A(dalloc(&s->loss, 1));
+  A(dalloc(&s->err, 1));
   if (e == cudaSuccess) e = cudaMemcpy(s->params, init_params, sizeof(float) * kParams, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(s->Bm, fourier_B, sizeof(float) * 16 * 7, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(s->m, 0, sizeof(float) * kParams);
   if (e == cudaSuccess) e = cudaMemset(s->v, 0, sizeof(float) * kParams);
+  if (e == cudaSuccess) e = cudaMemset(s->err, 0, sizeof(uint32_t));
   if (e == cudaSuccess) {
     k_weights_bf16<<<dim3(16, kLayers), 256>>>(s->params, s->Wb, s->Wtb);
     e = cudaDeviceSynchronize();
@@ -520,7 +525,14 @@ sdd_status sdd_surrogate_infer(sdd_surrogate* s, int n, const float* raw_dev, fl
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = surrogate_predict(s, n, raw_dev, out_dev, st, nullptr);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  return check(e);
+  uint32_t err = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&err, s->err, sizeof(err), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return check(e);
+  if (err) {
+    cudaMemset(s->err, 0, sizeof(uint32_t));
+    return set_last_error(SDD_ERR_TIMEOUT, "tensor-core wait gave up after its time limit");
+  }
+  return SDD_OK;
 }
 
 }  // extern "C"

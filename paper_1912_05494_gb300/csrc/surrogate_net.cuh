@@ -1,19 +1,12 @@
-// surrogate_net.cuh -- the tile-BTDF network's shape, its BF16 warp-MMA building blocks, and
-// the fused inference kernel used by the renderer and by sdd_surrogate_infer.
+// surrogate_net.cuh -- the tile-BTDF network's shape, its BF16 warp-MMA building blocks (the
+// training kernels of mlp.cu), the feature map, and the policy interface of the fused
+// inference kernel (surrogate_tc.cuh).
 //
 // Network: Fourier features of the 7 normalised inputs (48 wide) -> 4 x 128 GELU -> 16, the
 // first 8 outputs mapped by the head of surrogate_head.cuh.  Parameters are one FP32 array,
 // per layer W [in][out] row-major then b [out]; the BF16 copy Wt used here holds each layer
 // transposed, [out][in].
-//
-// Fused inference: one block per SM keeps every layer's weights resident in shared memory
-// (about 120 KB) and loops over chunks of 128 rows.  Each of its 8 warps owns 16 rows: it
-// builds their features, runs the five layers on the tensor cores (mma.sync m16n8k16, BF16
-// operands from shared memory by ldmatrix, FP32 accumulation), writes each layer's
-// activations back over its own rows, and leaves the head's predictions in shared memory
-// for the policy's consumer.  A policy supplies the row count (possibly read from device
-// memory), each row's raw inputs and what happens to the predictions, so the renderer can
-// gather its inputs from the ray state and sample the exit in the same launch.
+
 #pragma once
 
 #include <cuda_bf16.h>
@@ -125,117 +118,17 @@ SurrogateView surrogate_view(const sdd_surrogate* s);
 unsigned surrogate_version(const sdd_surrogate* s);
 
 // ------------------------------------------------------------------ fused inference
-constexpr int kInferWarps = 8;
-constexpr int kInferRows = 16 * kInferWarps;
-constexpr int kInferThreads = 32 * kInferWarps;
-constexpr int kInferXLd = net::kHid + 8;  // activation tile row stride (elements)
-constexpr int kInferZLd = net::kOut;      // output staging row stride (floats)
+constexpr int kInferRows = 128;          // rows per chunk (one M = 128 tensor-core tile)
+constexpr int kInferZLd = net::kOut;     // output staging row stride (floats)
 
-__host__ __device__ constexpr int infer_w_ld(int l) { return net::layer_in(l) + 8; }
-__host__ __device__ constexpr int infer_w_offset(int l) {
-  int o = 0;
-  for (int i = 0; i < l; ++i) o += net::layer_out(i) * infer_w_ld(i);
-  return o;
-}
-constexpr size_t kInferSmem = sizeof(__nv_bfloat16) * ((size_t)infer_w_offset(net::kLayers) + kInferRows * kInferXLd) +
-                              sizeof(float) * (size_t)kInferRows * kInferZLd;
-
-namespace net {
-// One hidden layer over the warp's 16 rows in place: x <- GELU(x W + b).
-template <int K>
-__device__ __forceinline__ void hidden_layer(__nv_bfloat16* xw, const __nv_bfloat16* w, const float* __restrict__ bias) {
-  const int lane = threadIdx.x & 31;
-  float acc[kHid / 8][4];
-#pragma unroll
-  for (int j = 0; j < kHid / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-  warp_gemm<K, kHid / 8>(acc, xw, kInferXLd, w, K + 8);
-  __syncwarp();
-#pragma unroll
-  for (int j = 0; j < kHid / 8; ++j) {
-    const int col = j * 8 + (lane & 3) * 2;
-    const float b0 = __ldg(bias + col), b1 = __ldg(bias + col + 1);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int r = (lane >> 2) + h * 8;
-      *reinterpret_cast<__nv_bfloat162*>(xw + r * kInferXLd + col) =
-          __floats2bfloat162_rn(gelu(acc[j][2 * h] + b0), gelu(acc[j][2 * h + 1] + b1));
-    }
-  }
-  __syncwarp();
-}
-}  // namespace net
-
-// Policy interface (device members, the policy itself stays in kernel parameter space):
+// Policy interface of the fused inference kernel (k_infer_tc, surrogate_tc.cuh); the
+// policy stays in kernel parameter space:
 //   Ctx resolve() const                       buffers the launch works on (small)
 //   int count(const Ctx&) const               rows to process
 //   void load(const Ctx&, int row, float q[7]) const
 //   void consume(const Ctx&, int row0, int valid, const float* pred) const
-//     pred = [kInferRows][kInferZLd] staging, called by every thread of the block.
-template <class Policy>
-__global__ void __launch_bounds__(kInferThreads, 1) k_infer_fused(SurrogateView v, const Policy pol) {
-  using namespace net;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __nv_bfloat16* sw = reinterpret_cast<__nv_bfloat16*>(smem_raw);
-  __nv_bfloat16* sx = sw + infer_w_offset(kLayers);
-  float* sz = reinterpret_cast<float*>(sx + kInferRows * kInferXLd);
-  const typename Policy::Ctx ctx = pol.resolve();
-  const int n = pol.count(ctx);
-  if ((int)blockIdx.x * kInferRows >= n) return;  // whole block
-#pragma unroll
-  for (int l = 0; l < kLayers; ++l)
-    load_tile(sw + infer_w_offset(l), infer_w_ld(l), v.Wt + layer_offset(l), layer_in(l), layer_out(l), layer_in(l),
-              layer_out(l));
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __nv_bfloat16* xw = sx + warp * 16 * kInferXLd;
-  for (int row0 = blockIdx.x * kInferRows; row0 < n; row0 += gridDim.x * kInferRows) {
-    const int valid = min(kInferRows, n - row0);
-    __syncthreads();  // weights staged; the previous chunk's consumer is done with sx and sz
-    for (int r = threadIdx.x; r < kInferRows; r += blockDim.x) {
-      float q[kIn] = {0.f, 0.f, 380.f, 2e-3f, 0.f, 1.45f, 1e-8f};
-      if (r < valid) pol.load(ctx, row0 + r, q);
-      features_row(q, v.Bm, sx + r * kInferXLd);
-    }
-    __syncthreads();
-    hidden_layer<kFeat>(xw, sw + infer_w_offset(0), v.params + layer_offset(0) + kFeat * kHid);
-#pragma unroll 1
-    for (int l = 1; l < kLayers - 1; ++l)
-      hidden_layer<kHid>(xw, sw + infer_w_offset(l), v.params + layer_offset(l) + kHid * kHid);
-    {
-      float acc[kOut / 8][4];
-#pragma unroll
-      for (int j = 0; j < kOut / 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-      warp_gemm<kHid, kOut / 8>(acc, xw, kInferXLd, sw + infer_w_offset(kLayers - 1), kHid + 8);
-      const float* bias = v.params + layer_offset(kLayers - 1) + kHid * kOut;
-#pragma unroll
-      for (int j = 0; j < kOut / 8; ++j) {
-        const int col = j * 8 + (lane & 3) * 2;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int r = warp * 16 + (lane >> 2) + h * 8;
-          sz[r * kInferZLd + col] = acc[j][2 * h] + __ldg(bias + col);
-          sz[r * kInferZLd + col + 1] = acc[j][2 * h + 1] + __ldg(bias + col + 1);
-        }
-      }
-      __syncwarp();
-      if (lane < 16) {  // the head, in place over the first 8 outputs of the row
-        float* z = sz + (warp * 16 + lane) * kInferZLd;
-        float p[kHeadPred];
-        p[0] = head_sigmoid(z[0]);
-        p[1] = head_sigmoid(z[1]);
-        p[2] = head_sigmoid(z[2]);
-        p[3] = head_log_kappa(z[3], kLkOffset1);
-        p[4] = head_log_kappa(z[4], kLkOffset2);
-        p[5] = head_sigmoid(z[5]);
-        p[6] = head_log_kappa(z[6], kLkOffset1);
-        p[7] = head_log_kappa(z[7], kLkOffset2);
-#pragma unroll
-        for (int j = 0; j < kHeadPred; ++j) z[j] = p[j];
-      }
-    }
-    __syncthreads();
-    pol.consume(ctx, row0, valid, sz);
-  }
-}
+//     pred = [kInferRows][kInferZLd] staging, called by every thread of the block
+//   uint32_t* err(const Ctx&) const           error word for the timeout bit
 
 // Rows of raw inputs [n][7] to predictions [n][8]; n read from n_dev when given (capped at n).
 struct RawPolicy {
@@ -243,6 +136,7 @@ struct RawPolicy {
   float* out;
   int n;
   const int* n_dev;
+  uint32_t* errw;
   struct Ctx {};
   __device__ Ctx resolve() const { return Ctx{}; }
   __device__ int count(const Ctx&) const { return n_dev ? min(*(volatile const int*)n_dev, n) : n; }
@@ -254,14 +148,10 @@ struct RawPolicy {
     for (int i = threadIdx.x; i < valid * kHeadPred; i += blockDim.x)
       out[(size_t)row0 * kHeadPred + i] = pred[(i / kHeadPred) * kInferZLd + i % kHeadPred];
   }
+  __device__ uint32_t* err(const Ctx&) const { return errw; }
 };
 
 // Blocks for a fused launch over at most n_max rows: one per SM, fewer for small n.
 int infer_grid(int n_max);
-// Sets the fused kernel's shared-memory limit (once per instantiation).
-template <class Policy>
-cudaError_t infer_prepare() {
-  return cudaFuncSetAttribute(k_infer_fused<Policy>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInferSmem);
-}
 
 }  // namespace sdd

@@ -1,7 +1,7 @@
 // surrogate_render.cu -- heterogeneous tiles in the renderer through the BTDF network.
 //
 // The shading kernel queues a generation's tile hits.  One fused launch then shades them
-// all (k_infer_fused with TileShadePolicy): per chunk of 128 hits it gathers the network's
+// all (k_infer_tc with TileShadePolicy, on the tcgen05 tensor cores): per chunk of 128 hits it gathers the network's
 // inputs from the ray state and the tile's material, runs the network, and samples the
 // exit from the prediction -- the side with probability R / (R + T) and throughput
 // x (R + T), a von Mises-Fisher lobe by its weight (surrogate_head.cuh), then a direction
@@ -15,6 +15,7 @@
 #include "render_device.cuh"
 #include "surrogate_head.cuh"
 #include "surrogate_net.cuh"
+#include "surrogate_tc.cuh"
 #include "surrogate_render.cuh"
 
 namespace sdd {
@@ -165,18 +166,18 @@ struct TileShadePolicy {
     }
     emit_ray(e0, p.sc, c.next, c.next_count, c.q, c.q_count, qcap, o0, s00, d0, thr0, path, meta0, ctl);
   }
+  __device__ uint32_t* err(const Ctx&) const { return &ctl->error; }
 };
 
 namespace {
 cudaError_t launch_tile_shade_policy(const TileShadePolicy& pol, const sdd_surrogate* net, cudaStream_t st) {
   static bool prepared = false;
   if (!prepared) {
-    cudaError_t e = infer_prepare<TileShadePolicy>();
+    cudaError_t e = infer_tc_prepare<TileShadePolicy>();
     if (e != cudaSuccess) return e;
     prepared = true;
   }
-  k_infer_fused<TileShadePolicy><<<infer_grid(pol.p.tile_cap), kInferThreads, kInferSmem, st>>>(surrogate_view(net),
-                                                                                                 pol);
+  k_infer_tc<TileShadePolicy><<<infer_grid(pol.p.tile_cap), tc::kThreads, tc::kSmem, st>>>(surrogate_view(net), pol);
   return cudaGetLastError();
 }
 }  // namespace
