@@ -512,6 +512,60 @@ def run_large(args):
     return 0
 
 
+def run_network(args):
+    """Throughput of the tile-BTDF network alone: fused tcgen05 inference (rows/s and
+    tensor FLOP/s) and Adam training steps on 65,536-row batches."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as g
+    g.build()
+    from paper_1912_05494_gb300 import scenes as S
+    from paper_1912_05494_gb300 import sdd
+
+    macs = 48 * 128 + 3 * 128 * 128 + 128 * 16  # per row
+    flop_row = 2 * macs
+    B, params = S.surrogate_init(4)
+    n_inf = args.net_rows
+    rng = np.random.default_rng(7)
+    raw = np.column_stack([rng.uniform(-1, 1, n_inf), rng.uniform(0, 2 * math.pi, n_inf), rng.uniform(380, 780, n_inf),
+                           rng.uniform(2.5e-3, 4.5e-3, n_inf), rng.uniform(5e9, 1.5e10, n_inf),
+                           rng.uniform(1.5, 1.6, n_inf), np.exp(rng.uniform(math.log(1e-7), math.log(1e-5), n_inf))])
+    raw_d = torch.from_numpy(raw.astype(np.float32)).cuda()
+    out = torch.empty((n_inf, 8), device="cuda")
+    net = sdd.Surrogate(B, params, max_batch=65536)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        net.infer(raw_d, out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        net.infer(raw_d, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_inf = e0.elapsed_time(e1) / args.steps
+    y = torch.rand((65536, 18), device="cuda")
+    xb = raw_d[:65536].contiguous()
+    for _ in range(args.warmup):
+        net.train_step(xb, y, lr=1e-3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n_train = max(20, args.steps * 10)
+    for _ in range(n_train):
+        net.train_step(xb, y, lr=1e-3)
+    torch.cuda.synchronize()
+    ms_train = (time.perf_counter() - t0) * 1e3 / n_train
+    line = {"workload": "network", "rows_inference": n_inf,
+            "inference": {"ms": ms_inf, "rows_per_s": n_inf / (ms_inf / 1e3),
+                          "tflops": n_inf * flop_row / (ms_inf / 1e3) / 1e12,
+                          "kernel": "k_infer_tc (tcgen05.mma kind::f16, TMEM accumulator)"},
+            "training": {"batch": 65536, "ms_per_step": ms_train,
+                         "tflops": 3 * 65536 * flop_row / (ms_train / 1e3) / 1e12,
+                         "kernels": "mma.sync m16n8k16 BF16 forward / backward + Adam (host-timed, includes the loss read-back)"},
+            "flop_per_row": flop_row}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -529,7 +583,8 @@ def main(argv=None):
     ap.add_argument("--subdomains", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batched", type=int, default=0, help="1: persistent kernels + CUDA graph; 0: host-driven")
-    ap.add_argument("--workload", choices=["nave", "large"], default="nave")
+    ap.add_argument("--workload", choices=["nave", "large", "network"], default="nave")
+    ap.add_argument("--net-rows", type=int, default=1 << 24, help="network workload: inference rows per step")
     ap.add_argument("--train-steps", type=int, default=20000, help="large workload: network training steps")
     ap.add_argument("--train-samples", type=int, default=1 << 21, help="large workload: tile-tracer samples")
     ap.add_argument("--autotune", type=int, default=1, help="large workload: autotune the subdomain count")
@@ -544,6 +599,8 @@ def main(argv=None):
         return run_reference(args)
     if args.workload == "large":
         return run_large(args)
+    if args.workload == "network":
+        return run_network(args)
     return run_gpu(args)
 
 
