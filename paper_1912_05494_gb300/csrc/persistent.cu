@@ -117,10 +117,11 @@ __device__ __forceinline__ void clear_ahead(int (*counts)[kMaxSubdomains], int* 
 
 }  // namespace
 
-// Six resident blocks per SM (registers bounded at 80, no spills) for scenes without
-// brute-force tiles; the brute-force tile tracer needs 128 registers (four blocks).
+// Eight resident blocks per SM (registers bounded at 64; ~150 B of spills) for scenes
+// without brute-force tiles: measured faster than 6 (80 registers, no spills), 10 or 12 (more
+// spills); the brute-force tile tracer needs 128 registers (four blocks).
 template <bool kStats, int kTM>
-__global__ void __launch_bounds__(kPB, kTM == 1 ? 4 : 6) k_persistent_wave(RenderParams p, WaveDesc w, PersistBuffers b,
+__global__ void __launch_bounds__(kPB, kTM == 1 ? 4 : 8) k_persistent_wave(RenderParams p, WaveDesc w, PersistBuffers b,
                                                          PersistCtl* pc, Control* ctl, int seg) {
   __shared__ int s_prefix[kMaxSubdomains + 1];
   __shared__ int s_count[kMaxSubdomains];
