@@ -23,8 +23,11 @@ __global__ void __launch_bounds__(kBlock) k_raygen(RenderParams p, WaveDesc w, R
   dev_raygen(p, w, i, i < w.n_paths, rb, q, q_count, qcap, ctl);
 }
 
+// Resident blocks per SM measured best: 12 x 128 threads for traversal (40 registers, small
+// spills; 9 without the bound), 8 x 128 for shadow rays without brute-force tiles (64
+// registers; 6 without).
 template <bool kStats, int kB>
-__global__ void __launch_bounds__(kB) k_traverse(RenderParams p, Sched sch, int top_nodes, QueuePair qp,
+__global__ void __launch_bounds__(kB, 12 * 128 / kB) k_traverse(RenderParams p, Sched sch, int top_nodes, QueuePair qp,
                                                      RayBuf rb, float2* hits, Control* ctl) {
   extern __shared__ Node s_nodes[];
   int b = blockIdx.x;
@@ -45,9 +48,10 @@ __global__ void __launch_bounds__(kBlock) k_shade(RenderParams p, WaveDesc w, in
                  sq_count, path_L, ctl);
 }
 
-template <bool kStats, int kB, int kTM>
-__global__ void __launch_bounds__(kB) k_shadow(RenderParams p, WaveDesc w, Sched sch, int top_nodes, QueuePair qp,
-                                                   ShadowBuf sb, float* path_L, Control* ctl) {
+template <bool kStats, int kTM>
+__device__ __forceinline__ void shadow_entry(const RenderParams& p, const WaveDesc& w, const Sched& sch,
+                                             int top_nodes, const QueuePair& qp, const ShadowBuf& sb, float* path_L,
+                                             Control* ctl) {
   extern __shared__ Node s_nodes[];
   int b = blockIdx.x;
   int s = 0;
@@ -61,6 +65,22 @@ __global__ void __launch_bounds__(kB) k_shadow(RenderParams p, WaveDesc w, Sched
   } else {
     dev_shadow<kStats, kTM>(p, w, s, i, i < sch.count[s], s_nodes, n_staged, qp, sb, path_L, ctl);
   }
+}
+
+// Shadow rays of scenes without brute-force tiles: 8 x 128-thread blocks per SM.
+template <bool kStats, int kB, int kTM>
+__global__ void __launch_bounds__(kB, 8 * 128 / kB) k_shadow(RenderParams p, WaveDesc w, Sched sch, int top_nodes,
+                                                             QueuePair qp, ShadowBuf sb, float* path_L, Control* ctl) {
+  shadow_entry<kStats, kTM>(p, w, sch, top_nodes, qp, sb, path_L, ctl);
+}
+
+// Shadow rays through brute-force tiles: no occupancy bound.  The tile tracer is also
+// compiled into the persistent kernel, and the two forms give bit-identical paths with the
+// register budgets both kernels had when that was verified.
+template <bool kStats, int kB>
+__global__ void __launch_bounds__(kB) k_shadow_bf(RenderParams p, WaveDesc w, Sched sch, int top_nodes, QueuePair qp,
+                                                  ShadowBuf sb, float* path_L, Control* ctl) {
+  shadow_entry<kStats, 1>(p, w, sch, top_nodes, qp, sb, path_L, ctl);
 }
 
 // ------------------------------------------------------------------------------ film
@@ -225,10 +245,17 @@ template <int kB, int kTM>
 static void launch_shadow_b(const RenderParams& p, const WaveDesc& w, const Sched& sch, int total_blocks,
                             int top_nodes, QueuePair qp, ShadowBuf sb, float* path_L, Control* ctl, cudaStream_t st) {
   size_t smem = (size_t)top_nodes * sizeof(Node);
-  if (p.stats >= 2)
-    k_shadow<true, kB, kTM><<<total_blocks, kB, smem, st>>>(p, w, sch, top_nodes, qp, sb, path_L, ctl);
-  else
-    k_shadow<false, kB, kTM><<<total_blocks, kB, smem, st>>>(p, w, sch, top_nodes, qp, sb, path_L, ctl);
+  if constexpr (kTM == 1) {
+    if (p.stats >= 2)
+      k_shadow_bf<true, kB><<<total_blocks, kB, smem, st>>>(p, w, sch, top_nodes, qp, sb, path_L, ctl);
+    else
+      k_shadow_bf<false, kB><<<total_blocks, kB, smem, st>>>(p, w, sch, top_nodes, qp, sb, path_L, ctl);
+  } else {
+    if (p.stats >= 2)
+      k_shadow<true, kB, kTM><<<total_blocks, kB, smem, st>>>(p, w, sch, top_nodes, qp, sb, path_L, ctl);
+    else
+      k_shadow<false, kB, kTM><<<total_blocks, kB, smem, st>>>(p, w, sch, top_nodes, qp, sb, path_L, ctl);
+  }
 }
 
 template <int kTM>
