@@ -15,9 +15,10 @@
 //   loss     mean over the batch of (T - y_T)^2 + (R - y_R)^2
 //            + 0.05 [y_T KL(h_T | m_T) + y_R KL(h_R | m_R)], h the tracer's deflection-bin
 //            fractions, m the mixture's mass per bin; Adam on FP32 master weights
-// Weights and activations are BF16, products accumulate in FP32 (mma.sync m16n8k16,
-// fragments loaded with ldmatrix from padded shared-memory tiles).  Parameters are one flat
-// FP32 array: for each layer W [in][out] row-major, then b [out].
+// Training: weights and activations are BF16, products accumulate in FP32 (mma.sync
+// m16n8k16, fragments loaded with ldmatrix from padded shared-memory tiles).  Inference
+// (sdd_surrogate_infer and the renderer) runs the fused tcgen05 kernel of surrogate_tc.cuh.
+// Parameters are one flat FP32 array: for each layer W [in][out] row-major, then b [out].
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 

@@ -2,15 +2,16 @@
 // host-driven kernels (render_kernels.cu) and the persistent drain kernel (persistent.cu).
 //
 // One generation of rays is processed by:
-//   dev_traverse  closest hit per subdomain queue (Sec. 3.1: the cost of ray tracing lies in
-//                 the intersectors); a ray that leaves its slab without a hit is handed,
-//                 unchanged, to the neighbouring slab's queue (Sec. 5: interface conditions
-//                 keep the ray properties continuous)
+//   dev_traverse_warp  closest hit per subdomain queue (Sec. 3.1: the cost of ray tracing
+//                 lies in the intersectors) as a warp-uniform BVH walk; a ray that leaves its
+//                 slab without a hit is handed, unchanged, to the neighbouring slab's queue
+//                 (Sec. 5: interface conditions keep the ray properties continuous)
 //   dev_shade     per-wavelength shading: complex Fresnel, Snell, Beer-Lambert (Eq. 1),
 //                 thin-slab series, Lambertian walls with a shadow ray to the sun (Eq. 3),
 //                 deterministic splitting (Sec. 3.1) or Philox-driven choices (Sec. 3.2);
 //                 children are compacted into the next generation and binned by subdomain
 //   dev_shadow    any-hit transmittance toward the sun per subdomain queue, with hand-off
+//                 (per-lane walk; dev_shadow_warp: warp-uniform, used with brute-force tiles)
 // Queue appends are warp-aggregated: one atomic per distinct target queue per warp (ballot /
 // match_any / popc).  Every function that appends must be called by all 32 lanes of a warp.
 #pragma once
@@ -157,63 +158,6 @@ struct ShadowKey {
   uint64_t seed;
 };
 
-// Closest hit in (t0, t1] against subdomain s's BVH.  Ties in t go to the lower primitive.
-template <bool kStats>
-__device__ __forceinline__ uint32_t closest_hit(const DevScene& sc, const Node* s_nodes, int n_staged, int s,
-                                                const RayPre& rp, float t0, float t1, float* t_out,
-                                                uint32_t* n_nodes, uint32_t* n_tris, bool* overflow) {
-  int stack[kStackSize];
-  int sp = 0;
-  const int root = sc.root[s];
-  int node = root;
-  float tbest = t1;
-  uint32_t best = kMissPrim;
-  for (;;) {
-    Node n = load_node(sc.nodes, s_nodes, node, root, n_staged);
-    if (kStats) ++*n_nodes;
-    float tn0, tn1;
-    bool h0 = n.d.x >= 0 && box_hit(rp, n.a.x, n.a.y, n.a.z, n.a.w, n.c.x, n.c.y, t0, tbest, &tn0);
-    bool h1 = n.d.y >= 0 && box_hit(rp, n.b.x, n.b.y, n.b.z, n.b.w, n.c.z, n.c.w, t0, tbest, &tn1);
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      bool hc = c == 0 ? h0 : h1;
-      int cnt = c == 0 ? n.d.z : n.d.w;
-      if (hc && cnt > 0) {
-        int first = c == 0 ? n.d.x : n.d.y;
-        for (int i = first; i < first + cnt; ++i) {
-          const float4* tp = reinterpret_cast<const float4*>(sc.tris + i);
-          float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
-          if (kStats) ++*n_tris;
-          float t = tri_hit(rp, v0, v1, v2, t0, tbest);
-          if (t >= 0.f) {
-            uint32_t prim = __float_as_uint(v0.w);
-            if (t < tbest || prim < best) {
-              tbest = t;
-              best = prim;
-            }
-          }
-        }
-        if (c == 0) h0 = false; else h1 = false;
-      }
-    }
-    if (h0 && h1) {
-      bool first0 = tn0 <= tn1;
-      if (sp < kStackSize) stack[sp++] = first0 ? n.d.y : n.d.x;
-      else *overflow = true;
-      node = first0 ? n.d.x : n.d.y;
-    } else if (h0) {
-      node = n.d.x;
-    } else if (h1) {
-      node = n.d.y;
-    } else {
-      if (sp == 0) break;
-      node = stack[--sp];
-    }
-  }
-  *t_out = tbest;
-  return best;
-}
-
 // Transmittance of a shadow ray across subdomain s over (t0, t1]: thin-slab tiles
 // multiply their slab transmittance; anything else blocks (returns 0).
 // kTM: heterogeneous-tile mode of the scene: 0 none, 1 brute-force tile tracing, 2 network.
@@ -295,9 +239,10 @@ __device__ __forceinline__ float shadow_T(const RenderParams& p, const DevScene&
   return T;
 }
 
-// closest_hit as a warp-uniform walk, for the host-driven traversal kernel (whose subdomain
-// is the block's, so the lanes enter converged).  Every lane of the warp calls it (live =
-// false for lanes without a ray).  Each iteration every lane still traversing takes one node
+// Closest hit in (t0, t1] against subdomain s's BVH as a warp-uniform walk; ties in t go to
+// the lower primitive.  The lanes must enter converged (the host-driven traversal kernel,
+// whose subdomain is the block's, and the persistent kernel's subdomain-aligned chunks).
+// Every lane of the warp calls it (live = false for lanes without a ray).  Each iteration every lane still traversing takes one node
 // step (box tests of both children, the triangles of any leaf child, then push / pop) and
 // the warp reconverges at the vote that ends the step.  A data-dependent loop per lane lets
 // the warp split into groups that each iterate on their own: on incoherent rays of large
@@ -558,52 +503,8 @@ __device__ __forceinline__ void dev_raygen(const RenderParams& p, const WaveDesc
 
 
 // ------------------------------------------------------------------------------ traverse
-// Closest hit of queue entry i of subdomain s (every lane of the warp calls this): writes
-// the hit record, or hands the ray to the neighbouring subdomain's queue.
-template <bool kStats>
-__device__ __forceinline__ void dev_traverse(const RenderParams& p, int s, int i, bool active, const Node* s_nodes,
-                                             int n_staged, QueuePair qp, RayBuf rb, float2* hits, Control* ctl) {
-  uint32_t r = active ? qp.in[(size_t)s * qp.cap + i] : 0u;
-  bool cross = false;
-  int next = -1;
-  uint32_t nn = 0, nt = 0;
-  if (active) {
-    float4 O = rb.o[r], D = rb.d[r];
-    float3 o = f3(O), d = f3(D);
-    float t0, t1;
-    slab_interval(p.sc, s, o, d, &t0, &t1, &next);
-    float t = t1;
-    uint32_t prim = kMissPrim;
-    bool ovf = false;
-    if (t1 > t0) {
-      RayPre rp = ray_pre(o, d);
-      prim = closest_hit<kStats>(p.sc, s_nodes, n_staged, s, rp, t0, t1, &t, &nn, &nt, &ovf);
-    }
-    if (ovf) atomicOr(&ctl->error, ERR_STACK_OVERFLOW);
-    cross = prim == kMissPrim && next >= 0;
-    if (!cross) hits[r] = make_float2(prim == kMissPrim ? CUDART_INF_F : t, __uint_as_float(prim));
-  }
-  int pos = warp_append(qp.out_count, cross ? next : 0, cross);
-  if (cross) {
-    if (pos < qp.cap) qp.out[(size_t)next * qp.cap + pos] = r;
-    else atomicOr(&ctl->error, ERR_QUEUE_OVERFLOW);
-  }
-  if (kStats) {
-    unsigned long long a = warp_sum<unsigned long long>(active ? 1ull : 0ull);
-    unsigned long long c = warp_sum<unsigned long long>(cross ? 1ull : 0ull);
-    unsigned long long n1 = warp_sum<unsigned long long>(nn);
-    unsigned long long n2 = warp_sum<unsigned long long>(nt);
-    if ((threadIdx.x & 31) == 0) {
-      atomicAdd(&ctl->rays_closest, a);
-      atomicAdd(&ctl->crossings, c);
-      atomicAdd(&ctl->node_visits, n1);
-      atomicAdd(&ctl->tri_tests, n2);
-    }
-  }
-}
-
-
-// dev_traverse with the warp-uniform walk (host-driven traversal kernel).
+// Closest hit of queue entry i of subdomain s (every lane of the warp calls this, the lanes
+// converged): writes the hit record, or hands the ray to the neighbouring subdomain's queue.
 template <bool kStats>
 __device__ __forceinline__ void dev_traverse_warp(const RenderParams& p, int s, int i, bool active, const Node* s_nodes,
                                              int n_staged, QueuePair qp, RayBuf rb, float2* hits, Control* ctl) {
