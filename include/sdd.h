@@ -316,6 +316,22 @@ sdd_status sdd_surrogate_gradients(sdd_surrogate* s, int n, const float* raw_dev
 /* One Adam step (beta 0.9 / 0.999, eps 1e-8, learning rate lr) on a batch of n rows. */
 sdd_status sdd_surrogate_train_step(sdd_surrogate* s, int n, const float* raw_dev, const float* y_dev, float lr,
                                     float* loss_host, void* cuda_stream);
+/* A training run: opts->steps Adam steps (learning rate opts->lr) on minibatches of
+ * opts->batch rows (<= min(n, max_batch)) of the n device-resident samples raw_dev [n][7],
+ * y_dev [n][18]; each epoch visits the rows in the order (a i + c) mod n with gcd(a, n) = 1,
+ * a and c drawn from opts->seed.  loss_host (may be NULL) receives the loss of every step;
+ * the host synchronises once, at the end. */
+typedef struct {
+  int steps;
+  int batch;
+  float lr;
+  uint64_t seed;
+} sdd_train_opts;
+sdd_status sdd_surrogate_train(sdd_surrogate* s, int n, const float* raw_dev, const float* y_dev,
+                               const sdd_train_opts* opts, float* loss_host, void* cuda_stream);
+/* The FP32 parameters as bytes (4 x sdd_surrogate_param_count()); same layout as _get_params. */
+sdd_status sdd_surrogate_get_weights(const sdd_surrogate* s, void* host_out, size_t bytes);
+sdd_status sdd_surrogate_set_weights(sdd_surrogate* s, const void* host_in, size_t bytes);
 /* Predictions [n][8] (device) for n rows of raw inputs (any n; processed max_batch at a time). */
 sdd_status sdd_surrogate_infer(sdd_surrogate* s, int n, const float* raw_dev, float* out_dev, void* cuda_stream);
 

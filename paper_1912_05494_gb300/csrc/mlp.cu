@@ -265,6 +265,19 @@ __global__ void k_weights_bf16(const float* __restrict__ p, __nv_bfloat16* __res
   }
 }
 
+// Rows of one minibatch: row j of the batch is row (a (off + j) + c) mod n of the samples,
+// a bijection of [0, n) when gcd(a, n) = 1.
+__global__ void k_gather_batch(int n, int batch, long long off, long long a, long long c, const float* __restrict__ raw,
+                               const float* __restrict__ y, float* __restrict__ braw, float* __restrict__ by) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= batch) return;
+  const long long src = (a * ((off + j) % n) + c) % n;
+  for (int k = 0; k < 7; ++k) braw[(size_t)j * 7 + k] = raw[(size_t)src * 7 + k];
+  for (int k = 0; k < kTargets; ++k) by[(size_t)j * kTargets + k] = y[(size_t)src * kTargets + k];
+}
+
+__global__ void k_record_loss(const float* loss_sum, float inv_batch, float* out) { *out = *loss_sum * inv_batch; }
+
 template <typename T>
 cudaError_t dalloc(T** p, size_t n) {
   return cudaMalloc(p, sizeof(T) * (n > 0 ? n : 1));
@@ -288,11 +301,13 @@ struct sdd_surrogate {
   __nv_bfloat16* dZ[2] = {};                 // [batch][128]
   float* loss = nullptr;
   uint32_t* err = nullptr;  // timeout bit of the inference kernel's bounded waits
+  float* batch_raw = nullptr;  // minibatch scratch of sdd_surrogate_train [max_batch][7]
+  float* batch_y = nullptr;    // [max_batch][18]
   int step = 0;
   unsigned version = 0;  // bumped whenever the weights change
   ~sdd_surrogate() {
     cudaFree(params); cudaFree(grads); cudaFree(m); cudaFree(v); cudaFree(Bm); cudaFree(Wb); cudaFree(Wtb);
-    cudaFree(feat); cudaFree(Zout); cudaFree(loss); cudaFree(err);
+    cudaFree(feat); cudaFree(Zout); cudaFree(loss); cudaFree(err); cudaFree(batch_raw); cudaFree(batch_y);
     for (auto* p : Z) cudaFree(p);
     for (auto* p : A) cudaFree(p);
     for (auto* p : dZ) cudaFree(p);
@@ -362,6 +377,28 @@ cudaError_t backward(sdd_surrogate* s, int n, const float* raw, const float* y, 
   k_layer_bwd_weight<kFeat, kHid><<<wblocks, kThreads, bwdw_smem(kFeat, kHid), st>>>(n, s->feat, s->dZ[cur], g0,
                                                                                     g0 + kFeat * kHid);
   return cudaGetLastError();
+}
+
+// One Adam step on n rows (enqueued on st): gradients, moments, parameters, BF16 copies.
+cudaError_t adam_step(sdd_surrogate* s, int n, const float* raw, const float* y, float lr, cudaStream_t st) {
+  cudaError_t e = backward(s, n, raw, y, st);
+  if (e != cudaSuccess) return e;
+  s->step++;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)s->step), c2 = 1.f - powf(b2, (float)s->step);
+  k_adam<<<(kParams + 255) / 256, 256, 0, st>>>(kParams, s->params, s->grads, s->m, s->v, lr, b1, b2, 1e-8f, c1, c2);
+  s->version++;
+  k_weights_bf16<<<dim3(16, kLayers), 256, 0, st>>>(s->params, s->Wb, s->Wtb);
+  return cudaGetLastError();
+}
+
+long long gcd_ll(long long a, long long b) {
+  while (b) {
+    long long t = a % b;
+    a = b;
+    b = t;
+  }
+  return a;
 }
 
 }  // namespace
@@ -504,21 +541,73 @@ sdd_status sdd_surrogate_train_step(sdd_surrogate* s, int n, const float* raw_de
   if (!s || n < 1 || n > s->max_batch || !raw_dev || !y_dev || !(lr > 0.f))
     return set_last_error(SDD_ERR_ARG, "bad arguments");
   cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = backward(s, n, raw_dev, y_dev, st);
-  if (e != cudaSuccess) return check(e);
-  s->step++;
-  const float b1 = 0.9f, b2 = 0.999f;
-  const float c1 = 1.f - powf(b1, (float)s->step), c2 = 1.f - powf(b2, (float)s->step);
-  k_adam<<<(kParams + 255) / 256, 256, 0, st>>>(kParams, s->params, s->grads, s->m, s->v, lr, b1, b2, 1e-8f, c1, c2);
-  s->version++;
-  k_weights_bf16<<<dim3(16, kLayers), 256, 0, st>>>(s->params, s->Wb, s->Wtb);
-  e = cudaGetLastError();
+  cudaError_t e = adam_step(s, n, raw_dev, y_dev, lr, st);
   if (e == cudaSuccess && loss_host) {
     e = cudaMemcpyAsync(loss_host, s->loss, sizeof(float), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     *loss_host /= n;
   }
   return check(e);
+}
+
+sdd_status sdd_surrogate_train(sdd_surrogate* s, int n, const float* raw_dev, const float* y_dev,
+                               const sdd_train_opts* opts, float* loss_host, void* stream) {
+  if (!s || n < 1 || !raw_dev || !y_dev || !opts) return set_last_error(SDD_ERR_ARG, "NULL argument or n < 1");
+  if (opts->steps < 1) return set_last_error(SDD_ERR_ARG, "steps must be >= 1");
+  if (opts->batch < 1 || opts->batch > s->max_batch || opts->batch > n)
+    return set_last_error(SDD_ERR_ARG, "batch must be in [1, min(n, max_batch)]");
+  if (!(opts->lr > 0.f)) return set_last_error(SDD_ERR_ARG, "lr must be > 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (!s->batch_raw) e = dalloc(&s->batch_raw, (size_t)s->max_batch * 7);
+  if (e == cudaSuccess && !s->batch_y) e = dalloc(&s->batch_y, (size_t)s->max_batch * kTargets);
+  float* losses = nullptr;
+  if (e == cudaSuccess) e = dalloc(&losses, (size_t)opts->steps);
+  if (e != cudaSuccess) {
+    cudaFree(losses);
+    return check(e);
+  }
+  // each epoch visits the rows in the order (a i + c) mod n, a and c drawn from the seed
+  uint64_t rng = opts->seed * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+  auto next = [&rng]() {
+    rng ^= rng >> 12;
+    rng ^= rng << 25;
+    rng ^= rng >> 27;
+    return rng * 0x2545F4914F6CDD1Dull;
+  };
+  long long a = 1, c = 0, pos = (long long)n;  // pos >= n forces a new epoch
+  for (int step = 0; step < opts->steps && e == cudaSuccess; ++step) {
+    if (pos + opts->batch > n) {
+      do {
+        a = (long long)(next() % (uint64_t)n) | 1;
+      } while (n > 1 && gcd_ll(a, n) != 1);
+      c = (long long)(next() % (uint64_t)n);
+      pos = 0;
+    }
+    k_gather_batch<<<(opts->batch + 255) / 256, 256, 0, st>>>(n, opts->batch, pos, a, c, raw_dev, y_dev,
+                                                              s->batch_raw, s->batch_y);
+    pos += opts->batch;
+    e = adam_step(s, opts->batch, s->batch_raw, s->batch_y, opts->lr, st);
+    if (e == cudaSuccess) k_record_loss<<<1, 1, 0, st>>>(s->loss, 1.f / opts->batch, losses + step);
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess && loss_host)
+    e = cudaMemcpyAsync(loss_host, losses, sizeof(float) * opts->steps, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(losses);
+  return check(e);
+}
+
+sdd_status sdd_surrogate_get_weights(const sdd_surrogate* s, void* host_out, size_t bytes) {
+  if (!s || !host_out || bytes != sizeof(float) * (size_t)kParams)
+    return set_last_error(SDD_ERR_ARG, "bytes must be 4 x sdd_surrogate_param_count()");
+  return sdd_surrogate_get_params(s, static_cast<float*>(host_out), kParams);
+}
+
+sdd_status sdd_surrogate_set_weights(sdd_surrogate* s, const void* host_in, size_t bytes) {
+  if (!s || !host_in || bytes != sizeof(float) * (size_t)kParams)
+    return set_last_error(SDD_ERR_ARG, "bytes must be 4 x sdd_surrogate_param_count()");
+  return sdd_surrogate_set_params(s, static_cast<const float*>(host_in), kParams);
 }
 
 sdd_status sdd_surrogate_infer(sdd_surrogate* s, int n, const float* raw_dev, float* out_dev, void* stream) {

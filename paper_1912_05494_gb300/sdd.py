@@ -77,6 +77,10 @@ class sdd_stats(C.Structure):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
 
 
+class sdd_train_opts(C.Structure):
+    _fields_ = [("steps", C.c_int), ("batch", C.c_int), ("lr", C.c_float), ("seed", C.c_uint64)]
+
+
 class sdd_tileset_desc(C.Structure):
     _fields_ = [("n_tiles", C.c_int), ("d_mean_m", C.c_void_p), ("amplitude_m", C.c_void_p),
                 ("bubble_density_m3", C.c_void_p), ("seed", C.c_void_p), ("grid", C.c_int),
@@ -141,7 +145,8 @@ def lib():
                      "sdd_philox", "sdd_set_tuning", "sdd_get_tuning", "sdd_tileset_create", "sdd_tileset_heights",
                      "sdd_tile_trace_rays", "sdd_tile_generate", "sdd_surrogate_create", "sdd_surrogate_get_params",
                      "sdd_surrogate_set_params", "sdd_surrogate_gradients", "sdd_surrogate_train_step",
-                     "sdd_surrogate_infer", "sdd_watchdog_selftest"):
+                     "sdd_surrogate_infer", "sdd_watchdog_selftest", "sdd_surrogate_train",
+                     "sdd_surrogate_get_weights", "sdd_surrogate_set_weights"):
             getattr(L, name).restype = C.c_int
         L.sdd_watchdog_selftest.argtypes = [C.c_int]
         _lib = L
@@ -446,6 +451,23 @@ class Surrogate:
         _check(lib().sdd_surrogate_train_step(self.h, int(raw.shape[0]), _ptr(raw), _ptr(y), C.c_float(lr),
                                               C.byref(loss), _stream(stream)))
         return float(loss.value)
+
+    def train(self, raw, y, steps, batch=65536, lr=1e-3, seed=4, stream=None):
+        """A whole training run through sdd_surrogate_train; returns the per-step losses."""
+        n = int(raw.shape[0])
+        o = sdd_train_opts(int(steps), int(min(batch, n)), float(lr), int(seed))
+        losses = np.zeros(int(steps), np.float32)
+        _check(lib().sdd_surrogate_train(self.h, n, _ptr(raw), _ptr(y), C.byref(o), C.c_void_p(losses.ctypes.data),
+                                         _stream(stream)))
+        return losses
+
+    def weights(self) -> bytes:
+        buf = C.create_string_buffer(4 * self.n_params)
+        _check(lib().sdd_surrogate_get_weights(self.h, buf, C.c_size_t(4 * self.n_params)))
+        return buf.raw
+
+    def set_weights(self, data: bytes):
+        _check(lib().sdd_surrogate_set_weights(self.h, C.c_char_p(data), C.c_size_t(len(data))))
 
     def infer(self, raw, out, stream=None):
         _check(lib().sdd_surrogate_infer(self.h, int(raw.shape[0]), _ptr(raw), _ptr(out), _stream(stream)))

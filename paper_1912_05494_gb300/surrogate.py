@@ -3,12 +3,11 @@
 Data come from the brute-force tile tracer (``sdd_tile_generate``): each query
 (cos theta_in, phi_in, lambda, tile) is traced with ``rays`` rays through the tile's height
 field and bubbles, and the per-query statistics (T, R, and the deflection-angle histograms of
-the transmitted and reflected weight) are the training targets.  Training runs Adam on
-shuffled minibatches through ``sdd_surrogate_train_step``; everything stays on the device.
+the transmitted and reflected weight) are the training targets.  Training is one
+``sdd_surrogate_train`` call: Adam on minibatches drawn by a seeded permutation of the
+rows; everything stays on the device.
 """
 from __future__ import annotations
-
-import time
 
 import numpy as np
 
@@ -42,28 +41,11 @@ def generate(tileset_h, tiles, tile_n, tile_k, n_samples, seed=3, rays=256, max_
     return dev(raw_inputs(q, tiles)), stats[:, TARGET_COLUMNS].contiguous()
 
 
-def train(net, raw, y, steps, batch=65536, lr=1e-3, seed=4, log_every=0):
-    """Adam steps on minibatches drawn without replacement per epoch; returns the loss history
+def train(net, raw, y, steps, batch=65536, lr=1e-3, seed=4):
+    """Adam steps on minibatches of the device-resident samples (sdd_surrogate_train: the
+    whole loop, minibatch gathering included, runs in the library); returns the loss history
     (one value per step)."""
-    import torch
-    n = raw.shape[0]
-    batch = min(batch, n)
-    g = torch.Generator(device=raw.device)
-    g.manual_seed(seed)
-    perm = torch.randperm(n, device=raw.device, generator=g)
-    pos = 0
-    hist = []
-    t0 = time.time()
-    for s in range(steps):
-        if pos + batch > n:
-            perm = torch.randperm(n, device=raw.device, generator=g)
-            pos = 0
-        idx = perm[pos:pos + batch]
-        pos += batch
-        hist.append(net.train_step(raw[idx].contiguous(), y[idx].contiguous(), lr=lr))
-        if log_every and (s + 1) % log_every == 0:
-            print(f"step {s + 1}: loss {hist[-1]:.5f} ({time.time() - t0:.1f} s)", flush=True)
-    return hist
+    return [float(v) for v in net.train(raw, y, steps, batch=batch, lr=lr, seed=seed)]
 
 
 def train_for_tileset(tileset_h, tiles, tile_n, tile_k, n_samples=1 << 20, steps=2000, rays=256, batch=65536,

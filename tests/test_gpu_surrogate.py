@@ -123,3 +123,28 @@ def test_training_on_tile_data_reduces_the_loss(sdd):
     for _ in range(300):
         last = net.train_step(raw, y, lr=1e-3)
     assert last < 0.3 * first, (first, last)
+
+
+def test_native_training_run_matches_single_steps_and_learns(sdd):
+    """sdd_surrogate_train with one full-batch minibatch per step is the same Adam update as
+    sdd_surrogate_train_step (row order inside the batch only changes FP32 summation order),
+    and a longer run on tile data reduces the loss."""
+    from paper_1912_05494_gb300 import surrogate as SG
+    tiles, tn, tk = S.tile_set(3, 16)
+    ts = sdd.TileSetHandle(tiles)
+    raw, y = SG.generate(ts.h, tiles, tn, tk, 4096, seed=8, rays=64)
+    B, params = S.surrogate_init(4)
+    a = sdd.Surrogate(B, params, max_batch=4096)
+    b = sdd.Surrogate(B, params, max_batch=4096)
+    for _ in range(3):
+        a.train_step(raw, y, lr=1e-3)
+    losses = b.train(raw, y, steps=3, batch=4096, lr=1e-3, seed=1)
+    assert losses.shape == (3,) and np.all(np.isfinite(losses))
+    pa, pb = a.params(), b.params()
+    assert np.max(np.abs(pa - pb)) < 2e-4  # three Adam steps of ~1e-3; summation order only
+    w = b.weights()
+    assert len(w) == 4 * b.n_params and np.array_equal(np.frombuffer(w, np.float32), pb)
+    a.set_weights(w)
+    assert np.array_equal(a.params(), pb)
+    hist = b.train(raw, y, steps=200, batch=1024, lr=1e-3, seed=2)
+    assert np.mean(hist[-20:]) < 0.5 * hist[0], (hist[0], hist[-20:])
