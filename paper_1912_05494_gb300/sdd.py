@@ -138,6 +138,9 @@ def lib():
         L.sdd_surrogate_gradients.argtypes = [vp, i32, vp, vp, vp, vp, vp]
         L.sdd_surrogate_train_step.argtypes = [vp, i32, vp, vp, f32, vp, vp]
         L.sdd_surrogate_infer.argtypes = [vp, i32, vp, vp, vp]
+        L.sdd_surrogate_train.argtypes = [vp, i32, vp, vp, C.POINTER(sdd_train_opts), vp, vp]
+        L.sdd_surrogate_get_weights.argtypes = [vp, vp, C.c_size_t]
+        L.sdd_surrogate_set_weights.argtypes = [vp, vp, C.c_size_t]
         L.sdd_last_error.restype = C.c_char_p
         L.sdd_version.restype = C.c_char_p
         for name in ("sdd_scene_create", "sdd_render", "sdd_render_to_host", "sdd_set_profiling", "sdd_get_stats",
@@ -467,7 +470,8 @@ class Surrogate:
         return buf.raw
 
     def set_weights(self, data: bytes):
-        _check(lib().sdd_surrogate_set_weights(self.h, C.c_char_p(data), C.c_size_t(len(data))))
+        buf = C.create_string_buffer(bytes(data), len(data))
+        _check(lib().sdd_surrogate_set_weights(self.h, buf, C.c_size_t(len(data))))
 
     def infer(self, raw, out, stream=None):
         _check(lib().sdd_surrogate_infer(self.h, int(raw.shape[0]), _ptr(raw), _ptr(out), _stream(stream)))
