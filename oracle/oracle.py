@@ -55,7 +55,7 @@ class OrcOpts(C.Structure):
         ("n_lambda", C.c_int), ("lambda_nm", C.c_void_p), ("spp", C.c_int),
         ("seed", C.c_uint64), ("max_depth", C.c_int), ("mode", C.c_int),
         ("rr_start_depth", C.c_int), ("n_pixels", C.c_int), ("pixels", C.c_void_p),
-        ("n_threads", C.c_int),
+        ("n_threads", C.c_int), ("bundle", C.c_int),
     ]
 
 
@@ -286,6 +286,7 @@ class OracleScene:
         o.n_pixels = 0 if px is None else px.size
         o.pixels = _p(px)
         o.n_threads = n_threads
+        o.bundle = getattr(spec, "bundle", 1)
         npx = cam.width * cam.height if px is None else px.size
         film = np.zeros((npx, lam.size))
         path_L = np.zeros((npx, spec.spp, lam.size)) if want_paths else None

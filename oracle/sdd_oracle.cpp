@@ -556,9 +556,12 @@ Hit closest(const Scene& s, V3 o, V3 d) {
 
 // Transmittance of a shadow ray to infinity: thin-slab tiles multiply their slab
 // transmittance, anything else blocks it (returns 0).
+// Counter words of the shadow ray's draws; `word` is the wavelength word (the wavelength
+// index, or its bundle's index when wavelengths share draws).
 struct ShadowKey {
   uint32_t px, sample, bounce;
   uint64_t seed;
+  uint32_t word;
 };
 
 void shadow_rec(const Scene& s, int ni, V3 o, V3 d, int lam, double lambda_nm, const ShadowKey& key, double& T) {
@@ -584,7 +587,7 @@ void shadow_rec(const Scene& s, int ni, V3 o, V3 d, int lam, double lambda_nm, c
         V3 dl, t1, t2;
         tile_frame(s, o + th * d, s.nrm[t], d, &x, &y, &dl, &t1, &t2);
         TileRay r = tile_trace(s.tile_geom[ti], s.tiles[ti], x, y, dl, m.n[lam], m.k[lam], lambda_nm, key.px,
-                               key.sample, key.bounce, (uint32_t)lam, key.seed, 64, STREAM_SHADOW_TILE);
+                               key.sample, key.bounce, key.word, key.seed, 64, STREAM_SHADOW_TILE);
         if (r.side == 1 && dot(r.dir, dl) > kCos1Deg) T *= r.w;
         else { T = 0.0; return; }
       } else {
@@ -597,7 +600,7 @@ void shadow_rec(const Scene& s, int ni, V3 o, V3 d, int lam, double lambda_nm, c
   shadow_rec(s, nd.left, o, d, lam, lambda_nm, key, T);
   shadow_rec(s, nd.right, o, d, lam, lambda_nm, key, T);
 }
-double shadow_T(const Scene& s, V3 o, V3 d, int lam, double lambda_nm, const ShadowKey& key = ShadowKey{0, 0, 0, 0}) {
+double shadow_T(const Scene& s, V3 o, V3 d, int lam, double lambda_nm, const ShadowKey& key = ShadowKey{0, 0, 0, 0, 0}) {
   double T = 1.0;
   if (!s.nodes.empty()) shadow_rec(s, 0, o, d, lam, lambda_nm, key, T);
   return T;
@@ -670,6 +673,7 @@ struct RenderCtx {
   const double* lambda_nm;
   int n_lambda, spp, max_depth, rr_start;
   uint64_t seed;
+  int bundle;  // wavelengths per draw bundle (1: every wavelength draws on its own)
 };
 
 // Deterministic splitting (Sec. 3.1): the radiance carried back along one ray, spawning
@@ -729,11 +733,17 @@ double trace_split(const RenderCtx& cx, V3 o, V3 d, double seg0, int vertex, int
 
 // Monte Carlo path (Sec. 3.2): one chain per (pixel, sample, wavelength) with the same
 // Philox draws the GPU uses.  Returns the path radiance; optionally its event hash.
+// Spectral bundling: with cx.bundle = B > 1 the wavelengths l = jB .. jB + B - 1 draw every
+// random number on the counter word j instead of l (one draw serves the B wavelengths, Sec. 5
+// cuts the spectral array into groups).  Each wavelength still follows its own chain with its
+// own decisions; only the uniforms are shared, so each chain has the distribution it has with
+// B = 1 and the wavelengths of a bundle are correlated.
 double trace_mc(const RenderCtx& cx, uint32_t px, uint32_t sample, int lam, uint32_t* hash_out) {
   const Scene& s = *cx.s;
   double lambda = cx.lambda_nm[lam];
+  const uint32_t word = (uint32_t)lam / (uint32_t)cx.bundle;
   PathHash ph;
-  Draw jit = draw(px, sample, 0, STREAM_PATH, 0, lam, cx.seed);  // pixel jitter
+  Draw jit = draw(px, sample, 0, STREAM_PATH, 0, word, cx.seed);  // pixel jitter
   V3 o, d;
   camera_ray(*cx.cam, (int)px, jit.u[0] - 0.5, jit.u[1] - 0.5, &o, &d);
   double thr = 1.0, L = 0.0, seg0 = 0.0;
@@ -753,7 +763,7 @@ double trace_mc(const RenderCtx& cx, uint32_t px, uint32_t sample, int lam, uint
     double cos_n = dot(d, ng);
     V3 nf = cos_n < 0.0 ? ng : -1.0 * ng;
     double cos_i = std::fabs(cos_n);
-    Draw u = draw(px, sample, (uint32_t)v, STREAM_PATH, 0, lam, cx.seed);
+    Draw u = draw(px, sample, (uint32_t)v, STREAM_PATH, 0, word, cx.seed);
     V3 nd;
     int nee_event = -1;  // shadow outcome, hashed after the roulette decision of this vertex
     if (m.kind == MAT_SOLID) {
@@ -788,11 +798,11 @@ double trace_mc(const RenderCtx& cx, uint32_t px, uint32_t sample, int lam, uint
     } else if (m.kind == MAT_DIFFUSE) {
       ph.byte(EV_DIFFUSE);
       if (s.sun_h > 0.0) {
-        Draw un = draw(px, sample, (uint32_t)v, STREAM_NEE, 0, lam, cx.seed);
+        Draw un = draw(px, sample, (uint32_t)v, STREAM_NEE, 0, word, cx.seed);
         V3 wl = cone_dir(s.sun_dir, s.sun_h, un.u[0], un.u[1]);
         double cl = dot(nf, wl);
         if (cl > 0.0) {
-          double T = shadow_T(s, offset(s, p, ng, wl), wl, lam, lambda, ShadowKey{px, sample, (uint32_t)v, cx.seed});
+          double T = shadow_T(s, offset(s, p, ng, wl), wl, lam, lambda, ShadowKey{px, sample, (uint32_t)v, cx.seed, word});
           double omega = 2.0 * PI * s.sun_h;
           L += thr * m.albedo[lam] / PI * cl * s.sun[lam] * omega * T;
           nee_event = T > 0.0 ? EV_SHADOW_OPEN : EV_SHADOW_BLOCKED;
@@ -808,7 +818,7 @@ double trace_mc(const RenderCtx& cx, uint32_t px, uint32_t sample, int lam, uint
       V3 dl, t1, t2;
       tile_frame(s, p, ng, d, &x, &y, &dl, &t1, &t2);
       TileRay r = tile_trace(s.tile_geom[ti], s.tiles[ti], x, y, dl, m.n[lam], m.k[lam], lambda, px, sample,
-                             (uint32_t)v, (uint32_t)lam, cx.seed, 64);
+                             (uint32_t)v, word, cx.seed, 64);
       if (r.side == 2) { ph.byte(EV_ABSORB); break; }
       thr *= r.w;
       nd = normalize(r.dir.x * t1 + r.dir.y * t2 + r.dir.z * ng);
@@ -943,6 +953,7 @@ struct OrcOpts {
   int n_pixels;        // number of entries in `pixels`; 0 = every pixel in row-major order
   const int32_t* pixels;
   int n_threads;       // 0 = hardware concurrency
+  int bundle;          // Monte Carlo: wavelengths sharing their draws (0 or 1: none)
 };
 
 struct OrcHandle {
@@ -1053,6 +1064,7 @@ int orc_render(void* hp, const OrcCamera* cam_in, const OrcOpts* op, double* fil
   Scene& s = h->s;
   if (op->n_lambda <= 0 || op->spp <= 0 || op->max_depth < 0) return -1;
   if (op->mode == 0 && op->spp != 1) return -1;
+  if (op->bundle < 0 || op->bundle > 64 || (op->bundle > 1 && op->mode == 0)) return -1;
   // Resample every table to the render wavelengths.
   s.mats.assign(h->mat_kind.size(), Material{});
   for (size_t m = 0; m < h->mat_kind.size(); ++m) {
@@ -1088,7 +1100,8 @@ int orc_render(void* hp, const OrcCamera* cam_in, const OrcOpts* op, double* fil
   cam.width = cam_in->width;
   cam.height = cam_in->height;
   std::vector<double> lam_d(op->lambda_nm, op->lambda_nm + op->n_lambda);
-  RenderCtx cx{&s, &cam, lam_d.data(), op->n_lambda, op->spp, op->max_depth, op->rr_start_depth, op->seed};
+  RenderCtx cx{&s, &cam, lam_d.data(), op->n_lambda, op->spp, op->max_depth, op->rr_start_depth, op->seed,
+               op->bundle > 1 ? op->bundle : 1};
 
   int npx = op->n_pixels > 0 ? op->n_pixels : cam.width * cam.height;
   int nth = op->n_threads > 0 ? op->n_threads : (int)std::thread::hardware_concurrency();

@@ -81,6 +81,7 @@ class RenderSpec:
     max_depth: int
     mode: int                     # RENDER_DETERMINISTIC or RENDER_MC
     rr_start_depth: int = 1 << 30
+    bundle: int = 1               # Monte Carlo: consecutive wavelengths that share their draws
 
     @property
     def n_lambda(self) -> int:

@@ -246,6 +246,43 @@ def test_mc_estimator_is_unbiased_against_splitting(orc):
     assert abs(mc.mean() - det.mean()) < 4 * se + 1e-9, (mc.mean(), det.mean(), se)
 
 
+def _solid_box(orc, n=1.55, k=1e-5, d=3e-3):
+    sc = custom_scene(box_tris((-0.5, 0.0, -0.5), (0.5, d, 0.5), 0), [{"kind": S.MAT_SOLID, "n": n, "k": k}])
+    return orc.OracleScene(sc)
+
+
+def test_bundle_shares_the_draws_of_its_wavelengths(orc):
+    """Spectral bundling keys every draw on the bundle index l // B: with four copies of one
+    wavelength and B = 2, wavelengths 0 and 1 repeat the unbundled chain of index 0 and
+    wavelengths 2 and 3 the chain of index 1, event for event."""
+    osc = _solid_box(orc)
+    cam = _ortho_cam(40.0, w=3, h=2)
+    one = dict(spp=64, seed=11, max_depth=8, mode=1, rr_start_depth=2)
+    _, p1, h1 = osc.render(cam, S.RenderSpec(lambda_nm=np.full(2, 550.0, np.float32), **one), want_paths=True)
+    _, pb, hb = osc.render(cam, S.RenderSpec(lambda_nm=np.full(4, 550.0, np.float32), bundle=2, **one),
+                           want_paths=True)
+    for lb, lu in ((0, 0), (1, 0), (2, 1), (3, 1)):
+        assert np.array_equal(pb[:, :, lb], p1[:, :, lu]) and np.array_equal(hb[:, :, lb], h1[:, :, lu])
+    assert not np.array_equal(h1[:, :, 0], h1[:, :, 1])  # the two unbundled chains do differ
+
+
+def test_bundled_estimator_is_unbiased_per_wavelength(orc):
+    """Shared draws leave every wavelength's chain with its own distribution: per wavelength,
+    bundled Monte Carlo averages to the deterministic split tree (Beer-Lambert makes the
+    wavelengths differ)."""
+    osc = _solid_box(orc, k=2e-4, d=5e-3)
+    cam = _ortho_cam(40.0, w=2, h=2)
+    lam = np.array([420.0, 520.0, 620.0, 720.0], np.float32)
+    det, _, _ = osc.render(cam, S.RenderSpec(lambda_nm=lam, spp=1, seed=0, max_depth=8, mode=0))
+    mc, paths, _ = osc.render(cam, S.RenderSpec(lambda_nm=lam, spp=20000, seed=9, max_depth=8, mode=1, bundle=4),
+                              want_paths=True)
+    for li in range(lam.size):
+        p = paths[:, :, li]
+        se = p.std() / math.sqrt(p.size)
+        assert abs(mc[:, li].mean() - det[:, li].mean()) < 4 * se + 1e-9, (li, mc[:, li].mean(), det[:, li].mean())
+    assert np.mean(det[:, 0]) != np.mean(det[:, 3])
+
+
 # ----------------------------------------------------------------------------- NEE / sun (Eq. 3)
 def _floor_scene(orc, extra=(), extra_mats=(), sky=1.0, sun=1000.0):
     elev = math.radians(35.0)
