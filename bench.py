@@ -278,7 +278,7 @@ def run_gpu(args):
 
     scene, cam, spec = S.nave_scene(seed=1, n_subdomains=args.subdomains)
     cam = S.CameraData(**{**cam.__dict__, "width": args.width, "height": args.height})
-    spec = S.RenderSpec(**{**spec.__dict__, "seed": spec.seed + 7919 * rank, "spp": args.spp})
+    spec = S.RenderSpec(**{**spec.__dict__, "seed": spec.seed + 7919 * rank, "spp": args.spp, "bundle": args.bundle})
     h = sdd.SceneHandle(scene)
     n_px = cam.width * cam.height
     out = torch.empty((n_px, spec.n_lambda), device="cuda", dtype=torch.float32)
@@ -363,7 +363,8 @@ def run_gpu(args):
                 "config": {"workload": WORKLOAD.format(w=cam.width, h=cam.height, spp=spec.spp, s=scene.n_subdomains),
                            "paths_per_step": frame_paths, "triangles": scene.n_triangles,
                            "subdomains": scene.n_subdomains, "l2": "flushed (512 MB write) before every frame",
-                           "parallelism": f"replicas x{world}", "wave_paths": args.wave_paths or "auto"},
+                           "parallelism": f"replicas x{world}", "wave_paths": args.wave_paths or "auto",
+                           "spectral_bundle": args.bundle},
                 "e2e": e2e,
                 "roofline": roofline, "cpu_baseline": cpu, "parity": parity, "clocks": clk,
                 "gpu_launches": launches,
@@ -583,6 +584,8 @@ def main(argv=None):
     ap.add_argument("--subdomains", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batched", type=int, default=0, help="1: persistent kernels + CUDA graph; 0: host-driven")
+    ap.add_argument("--bundle", type=int, default=1,
+                    help="nave workload: wavelengths per spectral bundle (1 = every wavelength its own path)")
     ap.add_argument("--workload", choices=["nave", "large", "network"], default="nave")
     ap.add_argument("--net-rows", type=int, default=1 << 24, help="network workload: inference rows per step")
     ap.add_argument("--train-steps", type=int, default=20000, help="large workload: network training steps")

@@ -121,6 +121,7 @@ struct sdd_scene {
   DevArr<double> cmf_w;
   // workspace
   DevArr<float4> rb_o[2], rb_d[2], sb_o, sb_d;
+  DevArr<float> rb_w[2], sb_c;  // spectral bundles: per-member throughput / shadow contribution
   DevArr<uint2> rb_info[2], sb_info;
   DevArr<float2> hits;
   DevArr<uint32_t> q[2], sq[2];
@@ -156,7 +157,9 @@ struct sdd_scene {
     t_mat_tile.release(); t_tile_mats.release(); t_tile_normal.release(); tile_queue.release(); sun_T.release();
     for (int i = 0; i < 2; ++i) {
       rb_o[i].release(); rb_d[i].release(); rb_info[i].release(); q[i].release(); sq[i].release();
+      rb_w[i].release();
     }
+    sb_c.release();
     sb_o.release(); sb_d.release(); sb_info.release(); hits.release(); path_L.release();
     path_hash.release(); film.release(); pixel_list.release(); out_spec.release(); out_xyz.release();
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
@@ -292,7 +295,7 @@ sdd_status run_closest_passes(sdd_scene* s, const RenderParams& p, RayBuf rb, in
 
 sdd_status run_shadow_passes(sdd_scene* s, const RenderParams& p, const WaveDesc& w, int qcap, cudaStream_t st) {
   int a = 0;
-  ShadowBuf sb{s->sb_o.p, s->sb_d.p, s->sb_info.p, qcap};
+  ShadowBuf sb{s->sb_o.p, s->sb_d.p, s->sb_info.p, qcap, s->sb_c.p};
   for (int pass = 0; pass <= 2 * kMaxSubdomains + 2; ++pass) {
     sdd_status r = read_ctl(s, st);
     if (r) return r;
@@ -403,20 +406,22 @@ sdd_status ensure_ctl(sdd_scene* s) {
 }
 
 // Workspace for `cap` rays per generation and `paths` paths per wave.
-sdd_status ensure_workspace(sdd_scene* s, size_t cap, size_t paths, int n_slots, bool hash) {
+sdd_status ensure_workspace(sdd_scene* s, size_t cap, size_t paths, int n_slots, bool hash, int bundle) {
   for (int i = 0; i < 2; ++i) {
+    if (bundle > 1) CK(s->rb_w[i].ensure(cap * (size_t)bundle));
     CK(s->rb_o[i].ensure(cap));
     CK(s->rb_d[i].ensure(cap));
     CK(s->rb_info[i].ensure(cap));
     CK(s->q[i].ensure(cap * (size_t)s->n_sub));
     CK(s->sq[i].ensure(cap * (size_t)s->n_sub));
   }
+  if (bundle > 1) CK(s->sb_c.ensure(cap * (size_t)bundle));
   CK(s->sb_o.ensure(cap));
   CK(s->sb_d.ensure(cap));
   CK(s->sb_info.ensure(cap));
   CK(s->hits.ensure(cap));
   CK(s->path_L.ensure(paths * (size_t)n_slots));
-  if (hash) CK(s->path_hash.ensure(paths));
+  if (hash) CK(s->path_hash.ensure(paths * (size_t)std::max(bundle, 1)));
   return ensure_ctl(s);
 }
 
@@ -467,12 +472,12 @@ sdd_status render_batched(sdd_scene* s, const RenderParams& p, const std::vector
   if (grid <= 0) return fail(SDD_ERR_CUDA, "persistent kernel does not fit on this device");
   PersistBuffers b;
   for (int i = 0; i < 2; ++i) {
-    b.rb[i] = RayBuf{s->rb_o[i].p, s->rb_d[i].p, s->rb_info[i].p, qcap};
+    b.rb[i] = RayBuf{s->rb_o[i].p, s->rb_d[i].p, s->rb_info[i].p, qcap, s->rb_w[i].p};
     b.q[i] = s->q[i].p;
     b.sq[i] = s->sq[i].p;
   }
   b.hits = s->hits.p;
-  b.sb = ShadowBuf{s->sb_o.p, s->sb_d.p, s->sb_info.p, qcap};
+  b.sb = ShadowBuf{s->sb_o.p, s->sb_d.p, s->sb_info.p, qcap, s->sb_c.p};
   b.path_L = s->path_L.p;
   b.qcap = qcap;
   // graph key: everything the captured frame depends on
@@ -568,10 +573,17 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
   const long long img = (long long)cam->width * cam->height;
   for (int i = 0; i < o->n_pixels; ++i)
     if (o->pixels[i] < 0 || o->pixels[i] >= img) return fail(SDD_ERR_ARG, "pixel index out of range");
+  if (o->bundle < 0 || o->bundle > kMaxBundle) return fail(SDD_ERR_ARG, "bundle must be in [0, 16]");
+  const int B = o->bundle > 1 ? o->bundle : 1;
+  if (B > 1 && o->mode != SDD_MODE_MONTE_CARLO) return fail(SDD_ERR_ARG, "spectral bundles need Monte Carlo mode");
+  if (B > 1 && o->use_surrogate) return fail(SDD_ERR_ARG, "spectral bundles do not support use_surrogate");
+  if (B > 1 && o->batched) return fail(SDD_ERR_ARG, "spectral bundles do not support the batched form");
   const int L = o->n_lambda;
+  const int n_bundles = (L + B - 1) / B;
   const long long n_px = o->n_pixels > 0 ? o->n_pixels : img;
-  const long long n_cells = n_px * L;
-  if (n_cells > 0x7FFFFFFFLL) return fail(SDD_ERR_ARG, "pixels x wavelengths exceeds 2^31");
+  if (n_px * L > 0x7FFFFFFFLL) return fail(SDD_ERR_ARG, "pixels x wavelengths exceeds 2^31");
+  // cells of the wave partition: (pixel, wavelength), or (pixel, bundle) with bundles
+  const long long n_cells = n_px * n_bundles;
 
   sdd_status r = prepare_spectral(s, L, o->lambda_nm, st);
   if (r) return r;
@@ -580,7 +592,9 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
 
   // waves
   const bool det = o->mode == SDD_MODE_DETERMINISTIC;
-  long long wmax = o->wave_paths > 0 ? o->wave_paths : (s->tuning.wave_paths > 0 ? s->tuning.wave_paths : (1LL << 26));
+  // default: 2^26 spectral paths per wave (2^26 / B bundle rays)
+  long long wmax =
+      o->wave_paths > 0 ? o->wave_paths : (s->tuning.wave_paths > 0 ? s->tuning.wave_paths : (1LL << 26) / B);
   wmax = std::min<long long>(wmax, 1LL << 28);
   std::vector<WaveDesc> waves;
   if (n_cells <= wmax) {
@@ -608,13 +622,15 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
   }
   size_t wave_paths = 0;
   for (auto& w : waves) wave_paths = std::max<size_t>(wave_paths, w.n_paths);
-  const int n_slots = det ? (1 << (o->max_depth + 1)) : 1;
-  const size_t cap = det ? wave_paths * 4 : wave_paths;
+  // contribution slots per path: the deterministic tree's leaves, or one per bundle member
+  const int n_slots = det ? (1 << (o->max_depth + 1)) : B;
+  // rays of one generation: a Monte Carlo path has one ray, a bundle at most one per member
+  const size_t cap = det ? wave_paths * 4 : wave_paths * (size_t)B;
   const bool want_hash = o->path_hash_out != nullptr;
-  r = ensure_workspace(s, cap, wave_paths, n_slots, want_hash);
+  r = ensure_workspace(s, cap, wave_paths, n_slots, want_hash, B);
   if (r) return r;
-  CK(s->film.ensure((size_t)n_cells));
-  CK(cudaMemsetAsync(s->film.p, 0, sizeof(double) * n_cells, st));
+  CK(s->film.ensure((size_t)(n_px * L)));
+  CK(cudaMemsetAsync(s->film.p, 0, sizeof(double) * n_px * L, st));
   if (o->n_pixels > 0) {
     CK(s->pixel_list.ensure(o->n_pixels));
     CK(cudaMemcpyAsync(s->pixel_list.p, o->pixels, sizeof(int32_t) * o->n_pixels, cudaMemcpyHostToDevice, st));
@@ -652,6 +668,8 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
   p.n_slots = n_slots;
   p.stats = s->profiling;
   p.path_hash = want_hash ? s->path_hash.p : nullptr;
+  p.bundle = B;
+  p.n_bundles = n_bundles;
   if (!s->tile_mats.empty()) {
     p.tiles = *tileset_device_view(s->tiles);
     p.mat_tile = s->t_mat_tile.p;
@@ -716,7 +734,7 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
     CK(cudaMemsetAsync(s->d_ctl, 0, offsetof(Control, node_visits), st));
     CK(cudaMemsetAsync(s->path_L.p, 0, sizeof(float) * (size_t)w.n_paths * n_slots, st));
     int cur = 0;
-    RayBuf rb0{s->rb_o[0].p, s->rb_d[0].p, s->rb_info[0].p, qcap};
+    RayBuf rb0{s->rb_o[0].p, s->rb_d[0].p, s->rb_info[0].p, qcap, s->rb_w[0].p};
     int ev = s->ev_begin(TK_RAYGEN, st);
     launch_raygen(p, w, rb0, s->q[0].p, s->d_ctl->q_count[0], qcap, s->d_ctl, st);
     s->ev_end(ev, st);
@@ -725,14 +743,14 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
     int n_rays = (int)w.n_paths;
     for (int gen = 0; n_rays > 0; ++gen) {
       if (gen > o->max_depth + 1) return fail(SDD_ERR_TIMEOUT, "generation count exceeded max_depth + 1");
-      RayBuf rc{s->rb_o[cur].p, s->rb_d[cur].p, s->rb_info[cur].p, qcap};
-      RayBuf rn{s->rb_o[1 - cur].p, s->rb_d[1 - cur].p, s->rb_info[1 - cur].p, qcap};
+      RayBuf rc{s->rb_o[cur].p, s->rb_d[cur].p, s->rb_info[cur].p, qcap, s->rb_w[cur].p};
+      RayBuf rn{s->rb_o[1 - cur].p, s->rb_d[1 - cur].p, s->rb_info[1 - cur].p, qcap, s->rb_w[1 - cur].p};
       r = run_closest_passes(s, p, rc, qcap, st);
       if (r) return r;
       // the closest passes left every count at zero; shade refills q[0] and sq[0]
       CK(cudaMemsetAsync(s->d_ctl, 0, offsetof(Control, error), st));
       CK(cudaMemsetAsync(&s->d_ctl->tile_hits, 0, sizeof(int), st));
-      ShadowBuf sb{s->sb_o.p, s->sb_d.p, s->sb_info.p, qcap};
+      ShadowBuf sb{s->sb_o.p, s->sb_d.p, s->sb_info.p, qcap, s->sb_c.p};
       ev = s->ev_begin(TK_SHADE, st);
       launch_shade(p, w, n_rays, rc, s->hits.p, rn, s->q[0].p, s->d_ctl->q_count[0], qcap, sb, s->sq[0].p,
                    s->d_ctl->sq_count[0], s->path_L.p, s->d_ctl, st);
@@ -1072,7 +1090,7 @@ sdd_status sdd_trace_closest(sdd_scene* s, int n, const float* org, const float*
   if (!s || n < 0 || (n > 0 && (!org || !dir || !t_out || !prim_out))) return fail(SDD_ERR_ARG, "bad arguments");
   if (n == 0) return SDD_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  sdd_status r = ensure_workspace(s, (size_t)n, (size_t)n, 1, false);
+  sdd_status r = ensure_workspace(s, (size_t)n, (size_t)n, 1, false, 1);
   if (r) return r;
   CK(cudaMemsetAsync(s->d_ctl, 0, sizeof(Control), st));
   RayBuf rb{s->rb_o[0].p, s->rb_d[0].p, s->rb_info[0].p, n};

@@ -1,0 +1,486 @@
+// bundle_device.cuh -- spectral bundles: the wavefront path with several wavelengths per ray.
+//
+// Sec. 5 of the paper cuts the spectral array into groups that are traced together.  Here a
+// bundle is B consecutive wavelengths (B = RenderParams::bundle, 2..16) of one (pixel,
+// sample).  Every random number of the bundle's chains is drawn on the bundle index j in
+// place of the wavelength index (the rule the oracle follows), so as long as their decisions
+// agree the B chains share every vertex and one traversal serves them all.  A ray carries the
+// mask of the members that still follow it (the high 16 bits of its meta word) and one
+// throughput per member (RayBuf::w, [cap][B]).  At a vertex the members are split:
+//   thin-slab glass    reflected members and transmitted members (at most two rays);
+//   diffuse            one ray (the cosine direction does not depend on the wavelength) and
+//                      one shadow ray whose per-member contributions (ShadowBuf::c) the
+//                      shadow walk multiplies by each member's slab transmittance;
+//   solid dielectric   the reflected members in one ray, each transmitted member on its own
+//                      ray (Snell's direction depends on n(lambda));
+//   brute-force tiles  each member on its own ray (its own trace through the tile).
+// Russian roulette is decided per member with the shared uniform.  Path radiance goes to
+// path_L[path][B] and, with event hashes enabled, each member keeps its own hash, so every
+// member's chain can be compared with the oracle's chain of that wavelength event for event.
+// Every function that appends must be called by all 32 lanes of a warp.
+#pragma once
+
+#include "render_device.cuh"
+
+namespace sdd {
+
+namespace {
+
+// Path id of a bundle ray: the `lam` field holds the bundle index j (cells are
+// pixel_index * n_bundles + j).
+__device__ __forceinline__ PathId path_id_bundle(const RenderParams& p, const WaveDesc& w, uint32_t path) {
+  PathId r;
+  uint32_t ls = path / w.nc;
+  uint32_t lc = path - ls * w.nc;
+  r.sample = w.s0 + ls;
+  r.cell = w.c0 + lc;
+  r.px_i = r.cell / (uint32_t)p.n_bundles;
+  r.lam = r.cell - r.px_i * (uint32_t)p.n_bundles;
+  r.pixel = p.pixel_list ? (uint32_t)p.pixel_list[r.px_i] : r.px_i;
+  return r;
+}
+
+// Members of bundle j: wavelengths j B .. min(j B + B, L) - 1.
+__device__ __forceinline__ uint32_t bundle_members(const RenderParams& p, uint32_t j) {
+  int n = min(p.bundle, p.sp.n_lambda - (int)j * p.bundle);
+  return n >= 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
+}
+
+// Hash updates of every member in `mask` (no-op without hashes).
+__device__ __forceinline__ void hash_word(uint32_t* hp, uint32_t mask, uint32_t w) {
+  if (!hp) return;
+  for (uint32_t m = mask; m; m &= m - 1) {
+    int b = __ffs(m) - 1;
+    hp[b] = fnv_word(hp[b], w);
+  }
+}
+__device__ __forceinline__ void hash_event(uint32_t* hp, uint32_t mask, uint32_t ev) {
+  if (!hp) return;
+  for (uint32_t m = mask; m; m &= m - 1) {
+    int b = __ffs(m) - 1;
+    hp[b] = fnv_byte(hp[b], ev);
+  }
+}
+
+// Append a bundle ray to the next generation and bin it by the subdomain of its origin;
+// returns its slot (-1 when not appended).  The caller writes its throughputs.
+__device__ __forceinline__ int emit_bundle_ray(bool want, const DevScene& sc, RayBuf nb, int* next_count, uint32_t* q,
+                                               int* q_count, int qcap, float3 o, float seg0, float3 d, uint32_t path,
+                                               uint32_t meta, Control* ctl) {
+  int pos = warp_append(next_count, 0, want);
+  bool ok = want && pos < nb.cap;
+  if (want && !ok) atomicOr(&ctl->error, ERR_QUEUE_OVERFLOW);
+  if (ok) {
+    nb.o[pos] = make_float4(o.x, o.y, o.z, seg0);
+    nb.d[pos] = make_float4(d.x, d.y, d.z, 0.f);
+    nb.info[pos] = make_uint2(path, meta);
+  }
+  int s = ok ? subdomain_of(sc, o) : 0;
+  int qpos = warp_append(q_count, s, ok);
+  if (ok) {
+    if (qpos < qcap) q[(size_t)s * qcap + qpos] = (uint32_t)pos;
+    else atomicOr(&ctl->error, ERR_QUEUE_OVERFLOW);
+  }
+  return ok ? pos : -1;
+}
+
+// Child throughput of a member after the roulette it survived (q = min(0.95, t)).
+__device__ __forceinline__ float after_roulette(float t, bool roulette) { return roulette ? t / fminf(0.95f, t) : t; }
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ raygen
+// One primary ray per wave-local bundle path i (every lane of the warp calls this).
+__device__ __forceinline__ void dev_raygen_bundle(const RenderParams& p, const WaveDesc& w, uint32_t i, bool active,
+                                                  RayBuf rb, uint32_t* q, int* q_count, int qcap, Control* ctl) {
+  const int B = p.bundle;
+  float3 o = make_float3(0.f, 0.f, 0.f), d = o;
+  if (active) {
+    PathId id = path_id_bundle(p, w, i);
+    float4 u = draw4(id.pixel, id.sample, 0, STREAM_PATH, 0, id.lam, p.seed);
+    primary_ray(p, id.pixel, u.x - 0.5f, u.y - 0.5f, &o, &d);
+    rb.o[i] = make_float4(o.x, o.y, o.z, 0.f);
+    rb.d[i] = make_float4(d.x, d.y, d.z, 0.f);
+    rb.info[i] = make_uint2(i, bundle_members(p, id.lam) << 16);  // depth 0, no flags
+    for (int b = 0; b < B; ++b) rb.w[(size_t)i * B + b] = 1.f;
+    if (p.path_hash)
+      for (int b = 0; b < B; ++b) p.path_hash[(size_t)i * B + b] = 0x811C9DC5u;
+  }
+  int s = active ? subdomain_of(p.sc, o) : 0;
+  int pos = warp_append(q_count, s, active);
+  if (active) {
+    if (pos < qcap) q[(size_t)s * qcap + pos] = i;
+    else atomicOr(&ctl->error, ERR_QUEUE_OVERFLOW);
+  }
+}
+
+// ------------------------------------------------------------------------------ shade
+// Shade bundle ray r of the current generation (every lane of the warp calls this).  The
+// per-member loop over the vertex's material (Eq. 1 with the complex index, the thin-slab
+// series, Beer-Lambert, the Lambertian albedo) decides each member's branch with the shared
+// uniforms; the members are then grouped into child rays as the header describes.  The
+// parent's throughput slots (cur.w) are reused to hold each member's throughput after the
+// vertex and before the roulette.
+template <int kTM>
+__device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const WaveDesc& w, int r, bool active,
+                                                 RayBuf cur, const float2* __restrict__ hits, RayBuf next,
+                                                 int* next_count, uint32_t* q, int* q_count, int qcap, ShadowBuf sb,
+                                                 int* shadow_count, uint32_t* sq, int* sq_count, float* path_L,
+                                                 Control* ctl) {
+  const int B = p.bundle;
+  const float eps = p.sc.eps;
+  // children: group 0 / 1 (members leaving in one direction) and singles (each member on its
+  // own direction)
+  uint32_t gm[2] = {0u, 0u}, singles = 0u, msh = 0u;
+  float3 gd[2], go[2], osh = make_float3(0.f, 0.f, 0.f), dsh = osh;
+  float gs[2] = {0.f, 0.f};
+  uint32_t gf[2] = {0u, 0u};
+  gd[0] = gd[1] = go[0] = go[1] = osh;
+  uint32_t path = 0, v = 0, flags = 0, j = 0, lam0 = 0;
+  int kind = -1, mat = 0;
+  bool roulette = false;
+  float uw = 0.f, cl_sh = 0.f, cos_i = 0.f, hit_t = 0.f, seg0 = 0.f;
+  float3 pt = osh, ng = osh, nf = osh, d = osh;
+  float* wr = cur.w + (size_t)(active ? r : 0) * B;
+  uint32_t* hp = nullptr;
+  PathId id{};
+  if (active) {
+    float4 O = cur.o[r], D = cur.d[r];
+    uint2 inf = cur.info[r];
+    float2 H = hits[r];
+    path = inf.x;
+    const uint32_t depth = inf.y & 0xFFu, mask = inf.y >> 16;
+    flags = (inf.y >> 8) & 0xFFu;
+    seg0 = O.w;
+    hit_t = H.x;
+    const float3 o = f3(O);
+    d = f3(D);
+    id = path_id_bundle(p, w, path);
+    j = id.lam;
+    lam0 = j * (uint32_t)B;
+    hp = p.path_hash ? p.path_hash + (size_t)path * B : nullptr;
+    float* Lp = path_L + (size_t)path * B;
+    const uint32_t prim = __float_as_uint(H.y);
+    if (prim != kMissPrim && prim >= (uint32_t)p.sc.n_prims) {
+      atomicOr(&ctl->error, ERR_QUEUE_OVERFLOW);  // stale hit record of a dropped ray
+    } else if (prim == kMissPrim) {
+      const bool sun_counted = (flags & FLAG_SUN_COUNTED) != 0u;
+      for (uint32_t m = mask; m; m &= m - 1) {
+        int b = __ffs(m) - 1;
+        Lp[b] += wr[b] * escape_radiance(p.sp, d, (int)lam0 + b, sun_counted);
+      }
+      hash_word(hp, mask, 0xFFFFFFFFu);
+      hash_event(hp, mask, EV_ESCAPE);
+    } else {
+      hash_word(hp, mask, prim);
+      v = depth + 1;
+      if ((int)v > p.max_depth) {
+        hash_event(hp, mask, EV_DEPTH_CAP);
+      } else {
+        float4 nm = __ldg(p.sc.prim_nrm_mat + prim);
+        ng = f3(nm);
+        mat = __float_as_int(nm.w);
+        kind = __ldg(p.sp.mat_kind + mat);
+        pt = o + H.x * d;
+        const float cos_n = dot3(d, ng);
+        nf = cos_n < 0.f ? ng : -1.f * ng;
+        cos_i = fabsf(cos_n);
+        const float4 u = draw4(id.pixel, id.sample, v, STREAM_PATH, 0, j, p.seed);
+        uw = u.w;
+        const float* mn = p.sp.mat_n + (size_t)mat * p.sp.n_lambda + lam0;
+        const float* mk = p.sp.mat_k + (size_t)mat * p.sp.n_lambda + lam0;
+        if (kind == MAT_SOLID) {
+          const bool inside = cos_n > 0.f;
+          for (uint32_t m = mask; m; m &= m - 1) {
+            int b = __ffs(m) - 1;
+            float nre = __ldg(mn + b), kk = __ldg(mk + b);
+            float thr = wr[b];
+            if (inside) thr *= beer_lambert(kk, H.x + seg0, __ldg(p.sp.lambda_nm + lam0 + b));
+            float n1 = inside ? nre : 1.f;
+            float n2re = inside ? 1.f : nre, n2im = inside ? 0.f : kk;
+            float R = fresnel_R(cos_i, n1, n2re, n2im);
+            float eta = n1 / n2re;
+            float c2 = 1.f - eta * eta * (1.f - cos_i * cos_i);
+            wr[b] = thr;
+            if (u.x < R || c2 <= 0.f) gm[0] |= 1u << b;
+            else singles |= 1u << b;
+          }
+          hash_event(hp, gm[0], EV_REFLECT);
+          hash_event(hp, singles, EV_TRANSMIT);
+          gd[0] = reflect3(d, nf);
+          gf[0] = flags & ~FLAG_SUN_COUNTED;
+        } else if (kind == MAT_SLAB) {
+          const float thick = __ldg(p.sp.mat_thick + mat);
+          for (uint32_t m = mask; m; m &= m - 1) {
+            int b = __ffs(m) - 1;
+            float Rs, Ts;
+            slab_RT(cos_i, __ldg(mn + b), __ldg(mk + b), thick, __ldg(p.sp.lambda_nm + lam0 + b), &Rs, &Ts);
+            float P = Rs / (Rs + Ts);
+            wr[b] = wr[b] * (Rs + Ts);
+            gm[u.x < P ? 0 : 1] |= 1u << b;
+          }
+          hash_event(hp, gm[0], EV_REFLECT);
+          hash_event(hp, gm[1], EV_TRANSMIT);
+          gd[0] = reflect3(d, nf);
+          gf[0] = flags & ~FLAG_SUN_COUNTED;
+          gd[1] = d;
+          gf[1] = flags;
+        } else if (kind == MAT_DIFFUSE) {
+          const float* ma = p.sp.mat_albedo + (size_t)mat * p.sp.n_lambda + lam0;
+          hash_event(hp, mask, EV_DIFFUSE);
+          for (uint32_t m = mask; m; m &= m - 1) {
+            int b = __ffs(m) - 1;
+            wr[b] = wr[b] * __ldg(ma + b);
+          }
+          if (p.sp.sun_h > 0.f) {
+            float4 un = draw4(id.pixel, id.sample, v, STREAM_NEE, 0, j, p.seed);
+            float3 wl = cone_dir(p.sp.sun_dir, p.sp.sun_h, un.x, un.y);
+            float cl = dot3(nf, wl);
+            if (cl > 0.f) {
+              msh = mask;
+              osh = offset_point(pt, ng, wl, eps);
+              dsh = wl;
+              cl_sh = cl;
+            }
+          }
+          gm[0] = mask;
+          gd[0] = cosine_dir(nf, u.y, u.z);
+          gf[0] = flags | FLAG_SUN_COUNTED;
+        } else if (kTM == 1 && kind == MAT_TILE) {
+          singles = mask;  // each member traces its own ray through the tile
+        } else {
+          hash_event(hp, mask, EV_ABSORB);
+        }
+        if ((int)v >= p.rr_start) {
+          roulette = true;
+          // tile members meet their roulette after their own trace (singles loop)
+          const uint32_t cand = gm[0] | gm[1] | (kind == MAT_SOLID ? singles : 0u);
+          for (uint32_t m = cand; m; m &= m - 1) {
+            int b = __ffs(m) - 1;
+            if (uw >= fminf(0.95f, wr[b])) {
+              const uint32_t bit = 1u << b;
+              gm[0] &= ~bit;
+              gm[1] &= ~bit;
+              if (kind == MAT_SOLID) singles &= ~bit;
+              hash_event(hp, bit, EV_RR_KILL);
+            }
+          }
+        }
+        for (int g = 0; g < 2; ++g)
+          if (gm[g]) {
+            go[g] = offset_point(pt, ng, gd[g], eps);
+            gs[g] = seg0_of(ng, gd[g], eps);
+          }
+      }
+    }
+  }
+  // group children
+#pragma unroll
+  for (int g = 0; g < 2; ++g) {
+    const int pos = emit_bundle_ray(gm[g] != 0u, p.sc, next, next_count, q, q_count, qcap, go[g], gs[g], gd[g], path,
+                                    v | (gf[g] << 8) | (gm[g] << 16), ctl);
+    if (pos >= 0) {
+      float* cw = next.w + (size_t)pos * B;
+      for (int b = 0; b < B; ++b) cw[b] = ((gm[g] >> b) & 1u) ? after_roulette(wr[b], roulette) : 0.f;
+    }
+  }
+  // singles: each member on its own direction (transmission into or out of solid glass,
+  // brute-force tiles)
+  if (__any_sync(0xffffffffu, singles != 0u)) {
+    const float* mn = p.sp.mat_n + (size_t)mat * p.sp.n_lambda + lam0;
+    const float* mk = p.sp.mat_k + (size_t)mat * p.sp.n_lambda + lam0;
+    for (int b = 0; b < B; ++b) {
+      bool want = (singles >> b) & 1u;
+      float3 ds = d, os = d;
+      float ts = 0.f, ss = 0.f;
+      uint32_t fs = 0u;
+      if (want) {
+        const float lambda = __ldg(p.sp.lambda_nm + lam0 + b);
+        if (kind == MAT_SOLID) {
+          const bool inside = dot3(d, ng) > 0.f;
+          const float nre = __ldg(mn + b);
+          const float eta = inside ? nre : 1.f / nre;
+          const float c2 = 1.f - eta * eta * (1.f - cos_i * cos_i);
+          ds = normalize3(eta * d + (eta * cos_i - sqrtf(c2)) * nf);
+          ts = after_roulette(wr[b], roulette);
+          fs = flags & ~FLAG_SUN_COUNTED;
+        } else {
+          float x, y;
+          float3 dl, t1v, t2v;
+          tile_frame(p.tiles.L, pt, ng, d, &x, &y, &dl, &t1v, &t2v);
+          TileOut tr = tile_trace(tile_of(p.tiles, __ldg(p.mat_tile + mat)), x, y, dl, __ldg(mn + b), __ldg(mk + b),
+                                  lambda, id.pixel, id.sample, v, j, p.seed, kTileEvents, STREAM_TILE);
+          const uint32_t bit = 1u << b;
+          if (tr.side == 2) {
+            hash_event(hp, bit, EV_ABSORB);
+            want = false;
+          } else {
+            hash_event(hp, bit, tr.side == 0 ? EV_REFLECT : EV_TRANSMIT);
+            ds = normalize3(tr.dir.x * t1v + tr.dir.y * t2v + tr.dir.z * ng);
+            ts = wr[b] * tr.w;
+            const bool keep = tr.side == 1 && dot3(tr.dir, dl) > kCos1Deg;
+            fs = keep ? flags : (flags & ~FLAG_SUN_COUNTED);
+            if (roulette) {
+              const float qs = fminf(0.95f, ts);
+              if (uw >= qs) {
+                hash_event(hp, bit, EV_RR_KILL);
+                want = false;
+              } else {
+                ts = ts / qs;
+              }
+            }
+          }
+        }
+        if (want) {
+          os = offset_point(pt, ng, ds, eps);
+          ss = seg0_of(ng, ds, eps);
+        }
+      }
+      const int pos = emit_bundle_ray(want, p.sc, next, next_count, q, q_count, qcap, os, ss, ds, path,
+                                      v | (fs << 8) | ((1u << b) << 16), ctl);
+      if (pos >= 0) {
+        float* cw = next.w + (size_t)pos * B;
+        for (int k = 0; k < B; ++k) cw[k] = k == b ? ts : 0.f;
+      }
+    }
+  }
+  // shadow ray toward the sun, one contribution per member
+  const bool esh = msh != 0u;
+  int pos = warp_append(shadow_count, 0, esh);
+  bool ok = esh && pos < sb.cap;
+  if (esh && !ok) atomicOr(&ctl->error, ERR_SHADOW_OVERFLOW);
+  if (ok) {
+    sb.o[pos] = make_float4(osh.x, osh.y, osh.z, 0.f);
+    sb.d[pos] = make_float4(dsh.x, dsh.y, dsh.z, 0.f);
+    sb.info[pos] = make_uint2(path, msh | (v << 16));
+    float* c = sb.c + (size_t)pos * B;
+    for (int b = 0; b < B; ++b)
+      c[b] = ((msh >> b) & 1u) ? wr[b] * kInvPi * cl_sh * __ldg(p.sp.sun + lam0 + b) * p.sp.sun_omega : 0.f;
+  }
+  int ss = ok ? subdomain_of(p.sc, osh) : 0;
+  int qpos = warp_append(sq_count, ss, ok);
+  if (ok) {
+    if (qpos < qcap) sq[(size_t)ss * qcap + qpos] = (uint32_t)pos;
+    else atomicOr(&ctl->error, ERR_SHADOW_OVERFLOW);
+  }
+}
+
+// ------------------------------------------------------------------------------ shadow
+// Shadow-queue entry i of subdomain s toward the sun for a bundle (every lane of the warp
+// calls this): each surface met multiplies every live member's contribution by that
+// member's transmittance; a brute-force tile trace that fails for a member drops that
+// member only; opaque geometry blocks them all.  Survivors are handed on to the neighbouring
+// subdomain or added to their paths.  kWarp selects the warp-uniform walk.
+template <bool kStats, int kTM, bool kWarp>
+__device__ __forceinline__ void dev_shadow_bundle(const RenderParams& p, const WaveDesc& w, int s, int i, bool active,
+                                                  const Node* s_nodes, int n_staged, QueuePair qp, ShadowBuf sb,
+                                                  float* path_L, Control* ctl) {
+  const int B = p.bundle;
+  uint32_t r = active ? qp.in[(size_t)s * qp.cap + i] : 0u;
+  bool cross = false;
+  int next = -1;
+  uint32_t nn = 0, nt = 0;
+  float4 O = make_float4(0.f, 0.f, 0.f, 0.f), D = make_float4(0.f, 0.f, 1.f, 0.f);
+  uint2 inf = make_uint2(0u, 0u);
+  float t0 = 0.f, t1 = 0.f;
+  if (active) {
+    O = sb.o[r];
+    D = sb.d[r];
+    inf = sb.info[r];
+    slab_interval(p.sc, s, f3(O), f3(D), &t0, &t1, &next);
+  }
+  const float3 o = f3(O), d = f3(D);
+  const PathId id = path_id_bundle(p, w, inf.x);
+  const uint32_t lam0 = id.lam * (uint32_t)B;
+  const uint32_t bounce = inf.y >> 16;
+  const ShadowKey key{id.pixel, id.sample, bounce, p.seed, id.lam};
+  uint32_t live = inf.y & 0xFFFFu;
+  float* c = sb.c + (size_t)r * B;
+  uint32_t* hp = (active && p.path_hash && p.mode == 1) ? p.path_hash + (size_t)inf.x * B : nullptr;
+  const RayPre rp = ray_pre(o, d);
+  auto hit = [&](float t, uint32_t prim) -> bool {
+    float4 nm = __ldg(p.sc.prim_nrm_mat + prim);
+    int mat = __float_as_int(nm.w);
+    int kind = __ldg(p.sp.mat_kind + mat);
+    const size_t m0 = (size_t)mat * p.sp.n_lambda + lam0;
+    if (kind == MAT_SLAB) {
+      const float cos_i = fabsf(dot3(d, f3(nm)));
+      const float thick = __ldg(p.sp.mat_thick + mat);
+      for (uint32_t m = live; m; m &= m - 1) {
+        int b = __ffs(m) - 1;
+        float Rs, Ts;
+        slab_RT(cos_i, __ldg(p.sp.mat_n + m0 + b), __ldg(p.sp.mat_k + m0 + b), thick,
+                __ldg(p.sp.lambda_nm + lam0 + b), &Rs, &Ts);
+        c[b] *= Ts;
+      }
+      return false;
+    }
+    if (kTM == 2 && kind == MAT_TILE) {
+      for (uint32_t m = live; m; m &= m - 1) {
+        int b = __ffs(m) - 1;
+        c[b] *= __ldg(p.tile_sun_T + m0 + b);
+      }
+      return false;
+    }
+    if (kTM == 1 && kind == MAT_TILE) {
+      float x, y;
+      float3 dl, t1v, t2v;
+      tile_frame(p.tiles.L, rp.o + t * d, f3(nm), d, &x, &y, &dl, &t1v, &t2v);
+      const TileDev tile = tile_of(p.tiles, __ldg(p.mat_tile + mat));
+      for (uint32_t m = live; m; m &= m - 1) {
+        int b = __ffs(m) - 1;
+        TileOut tr = tile_trace(tile, x, y, dl, __ldg(p.sp.mat_n + m0 + b), __ldg(p.sp.mat_k + m0 + b),
+                                __ldg(p.sp.lambda_nm + lam0 + b), key.pixel, key.sample, key.bounce, key.word,
+                                key.seed, kTileEvents, STREAM_SHADOW_TILE);
+        if (tr.side == 1 && dot3(tr.dir, dl) > kCos1Deg) {
+          c[b] *= tr.w;
+        } else {
+          live &= ~(1u << b);
+          hash_event(hp, 1u << b, EV_SHADOW_BLOCKED);
+        }
+      }
+      return live == 0u;
+    }
+    return true;
+  };
+  const bool walk = active && t1 > t0;
+  bool ovf = false, blocked = false;
+  if constexpr (kWarp) {
+    blocked = any_hit_walk_warp<kStats>(p.sc, s_nodes, n_staged, s, rp, t0, t1, walk, &nn, &nt, &ovf, hit);
+  } else {
+    if (walk) blocked = any_hit_walk<kStats>(p.sc, s_nodes, n_staged, s, rp, t0, t1, &nn, &nt, &ovf, hit);
+  }
+  if (active) {
+    if (ovf) atomicOr(&ctl->error, ERR_STACK_OVERFLOW);
+    cross = !blocked && next >= 0;
+    if (cross) {
+      sb.info[r].y = live | (bounce << 16);
+    } else if (!blocked) {
+      float* Lp = path_L + (size_t)inf.x * B;
+      for (uint32_t m = live; m; m &= m - 1) {
+        int b = __ffs(m) - 1;
+        Lp[b] += c[b];
+      }
+      hash_event(hp, live, EV_SHADOW_OPEN);
+    } else {
+      hash_event(hp, live, EV_SHADOW_BLOCKED);
+    }
+  }
+  int pos = warp_append(qp.out_count, cross ? next : 0, cross);
+  if (cross) {
+    if (pos < qp.cap) qp.out[(size_t)next * qp.cap + pos] = r;
+    else atomicOr(&ctl->error, ERR_SHADOW_OVERFLOW);
+  }
+  if (kStats) {
+    unsigned long long a = warp_sum<unsigned long long>(active ? 1ull : 0ull);
+    unsigned long long n1 = warp_sum<unsigned long long>(nn);
+    unsigned long long n2 = warp_sum<unsigned long long>(nt);
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&ctl->rays_shadow, a);
+      atomicAdd(&ctl->shadow_node_visits, n1);
+      atomicAdd(&ctl->shadow_tri_tests, n2);
+    }
+  }
+}
+
+}  // namespace sdd

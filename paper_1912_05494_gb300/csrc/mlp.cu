@@ -191,11 +191,14 @@ __global__ void __launch_bounds__(kThreads) k_layer_bwd_data(int n, const __nv_b
   }
 }
 
-// dW += X^T dZ and db += column sums of dZ over this block's row chunks (X [n][K], dZ [n][N]).
+// This block's share of dW = X^T dZ and db = column sums of dZ over its row chunks (X [n][K],
+// dZ [n][N]), written to part + blockIdx.x (K N + N) as [K][N] then [N]; k_reduce_partials
+// sums the blocks' shares in block order, so the gradients do not depend on scheduling.
 template <int K, int N>
 __global__ void __launch_bounds__(kThreads) k_layer_bwd_weight(int n, const __nv_bfloat16* __restrict__ X,
-                                                                const __nv_bfloat16* __restrict__ dZ, float* dW,
-                                                                float* db) {
+                                                                const __nv_bfloat16* __restrict__ dZ, float* part) {
+  float* dW = part + (size_t)blockIdx.x * (K * N + N);
+  float* db = dW + K * N;
   constexpr int LD = kRows + 8;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __nv_bfloat16* sxt = reinterpret_cast<__nv_bfloat16*>(smem_raw);  // [K][LD]: X^T of the chunk
@@ -229,12 +232,21 @@ __global__ void __launch_bounds__(kThreads) k_layer_bwd_weight(int n, const __nv
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int k = warp * 16 + (lane >> 2) + h * 8;
-        atomicAdd(dW + (size_t)k * N + col, acc[j][2 * h]);
-        atomicAdd(dW + (size_t)k * N + col + 1, acc[j][2 * h + 1]);
+        dW[(size_t)k * N + col] = acc[j][2 * h];
+        dW[(size_t)k * N + col + 1] = acc[j][2 * h + 1];
       }
     }
   }
-  if (threadIdx.x < N) atomicAdd(db + threadIdx.x, bsum);
+  if (threadIdx.x < N) db[threadIdx.x] = bsum;
+}
+
+// out[i] = sum over the blocks b = 0 .. nblk - 1, in order, of part[b len + i].
+__global__ void k_reduce_partials(int nblk, int len, const float* __restrict__ part, float* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= len) return;
+  float acc = 0.f;
+  for (int b = 0; b < nblk; ++b) acc += part[(size_t)b * len + i];
+  out[i] = acc;
 }
 
 __global__ void k_adam(int n, float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
@@ -289,6 +301,8 @@ struct sdd_surrogate {
   int max_batch = 0;
   float* params = nullptr;  // FP32 master weights
   float* grads = nullptr;
+  float* partial = nullptr;  // per-block shares of one layer's gradient [partial_blocks][K N + N]
+  int partial_blocks = 0;
   float* m = nullptr;
   float* v = nullptr;
   float* Bm = nullptr;      // Fourier matrix [16][7]
@@ -306,7 +320,7 @@ struct sdd_surrogate {
   int step = 0;
   unsigned version = 0;  // bumped whenever the weights change
   ~sdd_surrogate() {
-    cudaFree(params); cudaFree(grads); cudaFree(m); cudaFree(v); cudaFree(Bm); cudaFree(Wb); cudaFree(Wtb);
+    cudaFree(params); cudaFree(grads); cudaFree(partial); cudaFree(m); cudaFree(v); cudaFree(Bm); cudaFree(Wb); cudaFree(Wtb);
     cudaFree(feat); cudaFree(Zout); cudaFree(loss); cudaFree(err); cudaFree(batch_raw); cudaFree(batch_y);
     for (auto* p : Z) cudaFree(p);
     for (auto* p : A) cudaFree(p);
@@ -350,32 +364,31 @@ cudaError_t forward(sdd_surrogate* s, int n, const float* raw, cudaStream_t st) 
 cudaError_t backward(sdd_surrogate* s, int n, const float* raw, const float* y, cudaStream_t st) {
   cudaError_t e = forward(s, n, raw, st);
   if (e != cudaSuccess) return e;
-  cudaMemsetAsync(s->grads, 0, sizeof(float) * kParams, st);
   cudaMemsetAsync(s->loss, 0, sizeof(float), st);
   k_loss<<<(n + 127) / 128, 128, 0, st>>>(n, 1.f / n, s->Zout, y, s->dZ[0], s->loss);
   const int blocks = (n + kRows - 1) / kRows;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int wblocks = std::min(blocks, 2 * sms);
+  const int wblocks = std::min(blocks, s->partial_blocks);
+  auto reduce = [&](int l) {
+    const int len = layer_in(l) * layer_out(l) + layer_out(l);
+    k_reduce_partials<<<(len + 255) / 256, 256, 0, st>>>(wblocks, len, s->partial, s->grads + layer_offset(l));
+  };
   // output layer
-  float* g4 = s->grads + layer_offset(4);
-  k_layer_bwd_weight<kHid, kOut><<<wblocks, kThreads, bwdw_smem(kHid, kOut), st>>>(n, s->A[3], s->dZ[0], g4,
-                                                                                  g4 + kHid * kOut);
+  k_layer_bwd_weight<kHid, kOut><<<wblocks, kThreads, bwdw_smem(kHid, kOut), st>>>(n, s->A[3], s->dZ[0], s->partial);
+  reduce(4);
   k_layer_bwd_data<kOut, kHid><<<blocks, kThreads, bwdd_smem(kOut, kHid), st>>>(n, s->dZ[0], s->Wb + layer_offset(4),
                                                                                s->Z[3], s->dZ[1]);
   int cur = 1;
   for (int l = kLayers - 2; l >= 1; --l) {
-    float* g = s->grads + layer_offset(l);
-    k_layer_bwd_weight<kHid, kHid><<<wblocks, kThreads, bwdw_smem(kHid, kHid), st>>>(n, s->A[l - 1], s->dZ[cur], g,
-                                                                                    g + kHid * kHid);
+    k_layer_bwd_weight<kHid, kHid><<<wblocks, kThreads, bwdw_smem(kHid, kHid), st>>>(n, s->A[l - 1], s->dZ[cur],
+                                                                                    s->partial);
+    reduce(l);
     k_layer_bwd_data<kHid, kHid><<<blocks, kThreads, bwdd_smem(kHid, kHid), st>>>(
         n, s->dZ[cur], s->Wb + layer_offset(l), s->Z[l - 1], s->dZ[1 - cur]);
     cur = 1 - cur;
   }
-  float* g0 = s->grads;
-  k_layer_bwd_weight<kFeat, kHid><<<wblocks, kThreads, bwdw_smem(kFeat, kHid), st>>>(n, s->feat, s->dZ[cur], g0,
-                                                                                    g0 + kFeat * kHid);
+  k_layer_bwd_weight<kFeat, kHid><<<wblocks, kThreads, bwdw_smem(kFeat, kHid), st>>>(n, s->feat, s->dZ[cur],
+                                                                                    s->partial);
+  reduce(0);
   return cudaGetLastError();
 }
 
@@ -469,6 +482,13 @@ sdd_status sdd_surrogate_create(const float* fourier_B, const float* init_params
   };
   A(dalloc(&s->params, kParams));
   A(dalloc(&s->grads, kParams));
+  {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    s->partial_blocks = std::max(1, 2 * sms);
+    A(dalloc(&s->partial, (size_t)s->partial_blocks * (kHid * kHid + kHid)));
+  }
   A(dalloc(&s->m, kParams));
   A(dalloc(&s->v, kParams));
   A(dalloc(&s->Bm, 16 * 7));

@@ -156,21 +156,60 @@ constexpr int kTileEvents = 64;
 struct ShadowKey {
   uint32_t pixel, sample, bounce;
   uint64_t seed;
+  uint32_t word;  // wavelength word of the draws: the wavelength index, or its bundle's index
 };
 
-// Transmittance of a shadow ray across subdomain s over (t0, t1]: thin-slab tiles
-// multiply their slab transmittance; anything else blocks (returns 0).
+// A surface met by a shadow ray of wavelength lam at distance t: multiplies *T by its
+// transmittance and returns false (thin-slab tiles; heterogeneous tiles through the network's
+// table or one brute-force ray through the tile), or returns true when it blocks the ray.
 // kTM: heterogeneous-tile mode of the scene: 0 none, 1 brute-force tile tracing, 2 network.
-template <bool kStats, int kTM>
-__device__ __forceinline__ float shadow_T(const RenderParams& p, const DevScene& sc, const DevSpectral& sp, int lam,
-                                          float lambda_nm, const ShadowKey& key, const Node* s_nodes, int n_staged,
-                                          int s, const RayPre& rp, float3 d, float t0, float t1, uint32_t* n_nodes,
-                                          uint32_t* n_tris, bool* overflow) {
+template <int kTM>
+__device__ __forceinline__ bool shadow_surface(const RenderParams& p, const DevSpectral& sp, int lam, float lambda_nm,
+                                               const ShadowKey& key, const RayPre& rp, float3 d, float t,
+                                               uint32_t prim, float* T) {
+  float4 nm = __ldg(p.sc.prim_nrm_mat + prim);
+  int mat = __float_as_int(nm.w);
+  int kind = __ldg(sp.mat_kind + mat);
+  size_t mi = (size_t)mat * sp.n_lambda + lam;
+  if (kind == MAT_SLAB) {
+    float cos_i = fabsf(dot3(d, f3(nm)));
+    float Rs, Ts;
+    slab_RT(cos_i, __ldg(sp.mat_n + mi), __ldg(sp.mat_k + mi), __ldg(sp.mat_thick + mat), lambda_nm, &Rs, &Ts);
+    *T *= Ts;
+    return false;
+  }
+  if (kTM == 2 && kind == MAT_TILE) {
+    *T *= __ldg(p.tile_sun_T + mi);  // network: transmittance x ballistic fraction
+    return false;
+  }
+  if (kTM == 1 && kind == MAT_TILE) {
+    // one brute-force ray through the tile: counts if it leaves on the far side within 1
+    // degree of the shadow direction
+    float x, y;
+    float3 dl, t1v, t2v;
+    tile_frame(p.tiles.L, rp.o + t * d, f3(nm), d, &x, &y, &dl, &t1v, &t2v);
+    TileOut r = tile_trace(tile_of(p.tiles, __ldg(p.mat_tile + mat)), x, y, dl, __ldg(sp.mat_n + mi),
+                           __ldg(sp.mat_k + mi), lambda_nm, key.pixel, key.sample, key.bounce, key.word, key.seed,
+                           kTileEvents, STREAM_SHADOW_TILE);
+    if (r.side == 1 && dot3(r.dir, dl) > kCos1Deg) {
+      *T *= r.w;
+      return false;
+    }
+  }
+  return true;
+}
+
+// Any-hit walk of subdomain s's BVH over (t0, t1] for one lane: `hit(t, prim)` is called for
+// every triangle the ray meets (in walk order) and returns true when that surface blocks the
+// ray, which ends the walk.  Returns true when the ray was blocked.
+template <bool kStats, class Hit>
+__device__ __forceinline__ bool any_hit_walk(const DevScene& sc, const Node* s_nodes, int n_staged, int s,
+                                             const RayPre& rp, float t0, float t1, uint32_t* n_nodes,
+                                             uint32_t* n_tris, bool* overflow, Hit& hit) {
   int stack[kStackSize];
   int spn = 0;
   const int root = sc.root[s];
   int node = root;
-  float T = 1.f;
   for (;;) {
     Node n = load_node(sc.nodes, s_nodes, node, root, n_staged);
     if (kStats) ++*n_nodes;
@@ -188,37 +227,7 @@ __device__ __forceinline__ float shadow_T(const RenderParams& p, const DevScene&
           float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
           if (kStats) ++*n_tris;
           float t = tri_hit(rp, v0, v1, v2, t0, t1);
-          if (t >= 0.f) {
-            uint32_t prim = __float_as_uint(v0.w);
-            float4 nm = __ldg(sc.prim_nrm_mat + prim);
-            int mat = __float_as_int(nm.w);
-            int kind = __ldg(sp.mat_kind + mat);
-            size_t mi = (size_t)mat * sp.n_lambda + lam;
-            if (kind == MAT_SLAB) {
-              float cos_i = fabsf(dot3(d, f3(nm)));
-              float Rs, Ts;
-              slab_RT(cos_i, __ldg(sp.mat_n + mi), __ldg(sp.mat_k + mi), __ldg(sp.mat_thick + mat), lambda_nm, &Rs,
-                      &Ts);
-              T *= Ts;
-            } else if (kTM != 0 && kind == MAT_TILE) {
-              if (kTM == 2) {
-                T *= __ldg(p.tile_sun_T + mi);  // network: transmittance x ballistic fraction
-              } else {
-                // one brute-force ray through the tile: counts if it leaves on the far side
-                // within 1 degree of the shadow direction
-                float x, y;
-                float3 dl, t1v, t2v;
-                tile_frame(p.tiles.L, rp.o + t * d, f3(nm), d, &x, &y, &dl, &t1v, &t2v);
-                TileOut r = tile_trace(tile_of(p.tiles, __ldg(p.mat_tile + mat)), x, y, dl, __ldg(sp.mat_n + mi),
-                                       __ldg(sp.mat_k + mi), lambda_nm, key.pixel, key.sample, key.bounce, lam,
-                                       key.seed, kTileEvents, STREAM_SHADOW_TILE);
-                if (r.side == 1 && dot3(r.dir, dl) > kCos1Deg) T *= r.w;
-                else return 0.f;
-              }
-            } else {
-              return 0.f;
-            }
-          }
+          if (t >= 0.f && hit(t, __float_as_uint(v0.w))) return true;
         }
         if (c == 0) h0 = false; else h1 = false;
       }
@@ -236,7 +245,21 @@ __device__ __forceinline__ float shadow_T(const RenderParams& p, const DevScene&
       node = stack[--spn];
     }
   }
-  return T;
+  return false;
+}
+
+// Transmittance of a shadow ray of wavelength lam across subdomain s over (t0, t1] (0 when
+// blocked), as a per-lane walk.
+template <bool kStats, int kTM>
+__device__ __forceinline__ float shadow_T(const RenderParams& p, const DevScene& sc, const DevSpectral& sp, int lam,
+                                          float lambda_nm, const ShadowKey& key, const Node* s_nodes, int n_staged,
+                                          int s, const RayPre& rp, float3 d, float t0, float t1, uint32_t* n_nodes,
+                                          uint32_t* n_tris, bool* overflow) {
+  float T = 1.f;
+  auto hit = [&](float t, uint32_t prim) {
+    return shadow_surface<kTM>(p, sp, lam, lambda_nm, key, rp, d, t, prim, &T);
+  };
+  return any_hit_walk<kStats>(sc, s_nodes, n_staged, s, rp, t0, t1, n_nodes, n_tris, overflow, hit) ? 0.f : T;
 }
 
 // Closest hit in (t0, t1] against subdomain s's BVH as a warp-uniform walk; ties in t go to
@@ -316,24 +339,24 @@ __device__ __forceinline__ uint32_t closest_hit_warp(const DevScene& sc, const N
   return best;
 }
 
-// shadow_T as a warp-uniform walk (see closest_hit_warp); every lane of the warp calls it.
-template <bool kStats, int kTM>
-__device__ __forceinline__ float shadow_T_warp(const RenderParams& p, const DevScene& sc, const DevSpectral& sp, int lam,
-                                          float lambda_nm, const ShadowKey& key, const Node* s_nodes, int n_staged,
-                                          int s, const RayPre& rp, float3 d, float t0, float t1, bool live,
-                                          uint32_t* n_nodes, uint32_t* n_tris, bool* overflow) {
+// any_hit_walk as a warp-uniform walk (see closest_hit_warp); every lane of the warp calls it
+// (live = false for lanes without a ray).  A walk that exceeds kMaxTraversalSteps raises
+// *overflow and counts as blocked.
+template <bool kStats, class Hit>
+__device__ __forceinline__ bool any_hit_walk_warp(const DevScene& sc, const Node* s_nodes, int n_staged, int s,
+                                                  const RayPre& rp, float t0, float t1, bool live, uint32_t* n_nodes,
+                                                  uint32_t* n_tris, bool* overflow, Hit& hit) {
   int stack[kStackSize];
   int spn = 0;
   const int root = sc.root[s];
   int node = root;
-  float T = 1.f;
-  bool done = !live;
+  bool done = !live, res = false;
   int steps = 0;
   bool any = __any_sync(0xffffffffu, !done);
   while (any) {
    if (!done && ++steps > kMaxTraversalSteps) {
     *overflow = true;
-    T = 0.f;
+    res = true;
     done = true;
    }
    if (!done) {
@@ -354,43 +377,13 @@ __device__ __forceinline__ float shadow_T_warp(const RenderParams& p, const DevS
           float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
           if (kStats) ++*n_tris;
           float t = tri_hit(rp, v0, v1, v2, t0, t1);
-          if (t >= 0.f) {
-            uint32_t prim = __float_as_uint(v0.w);
-            float4 nm = __ldg(sc.prim_nrm_mat + prim);
-            int mat = __float_as_int(nm.w);
-            int kind = __ldg(sp.mat_kind + mat);
-            size_t mi = (size_t)mat * sp.n_lambda + lam;
-            if (kind == MAT_SLAB) {
-              float cos_i = fabsf(dot3(d, f3(nm)));
-              float Rs, Ts;
-              slab_RT(cos_i, __ldg(sp.mat_n + mi), __ldg(sp.mat_k + mi), __ldg(sp.mat_thick + mat), lambda_nm, &Rs,
-                      &Ts);
-              T *= Ts;
-            } else if (kTM != 0 && kind == MAT_TILE) {
-              if (kTM == 2) {
-                T *= __ldg(p.tile_sun_T + mi);  // network: transmittance x ballistic fraction
-              } else {
-                // one brute-force ray through the tile: counts if it leaves on the far side
-                // within 1 degree of the shadow direction
-                float x, y;
-                float3 dl, t1v, t2v;
-                tile_frame(p.tiles.L, rp.o + t * d, f3(nm), d, &x, &y, &dl, &t1v, &t2v);
-                TileOut r = tile_trace(tile_of(p.tiles, __ldg(p.mat_tile + mat)), x, y, dl, __ldg(sp.mat_n + mi),
-                                       __ldg(sp.mat_k + mi), lambda_nm, key.pixel, key.sample, key.bounce, lam,
-                                       key.seed, kTileEvents, STREAM_SHADOW_TILE);
-                if (r.side == 1 && dot3(r.dir, dl) > kCos1Deg) T *= r.w;
-                else blocked = true;
-              }
-            } else {
-              blocked = true;
-            }
-          }
+          if (t >= 0.f) blocked = hit(t, __float_as_uint(v0.w));
         }
         if (c == 0) h0 = false; else h1 = false;
       }
     }
     if (blocked) {
-      T = 0.f;
+      res = true;
       done = true;
     } else if (h0 && h1) {
       if (spn < kStackSize) stack[spn++] = n.d.x;
@@ -408,7 +401,21 @@ __device__ __forceinline__ float shadow_T_warp(const RenderParams& p, const DevS
    }
     any = __any_sync(0xffffffffu, !done);
   }
-  return T;
+  return res;
+}
+
+// shadow_T as a warp-uniform walk; every lane of the warp calls it.
+template <bool kStats, int kTM>
+__device__ __forceinline__ float shadow_T_warp(const RenderParams& p, const DevScene& sc, const DevSpectral& sp, int lam,
+                                          float lambda_nm, const ShadowKey& key, const Node* s_nodes, int n_staged,
+                                          int s, const RayPre& rp, float3 d, float t0, float t1, bool live,
+                                          uint32_t* n_nodes, uint32_t* n_tris, bool* overflow) {
+  float T = 1.f;
+  auto hit = [&](float t, uint32_t prim) {
+    return shadow_surface<kTM>(p, sp, lam, lambda_nm, key, rp, d, t, prim, &T);
+  };
+  return any_hit_walk_warp<kStats>(sc, s_nodes, n_staged, s, rp, t0, t1, live, n_nodes, n_tris, overflow, hit) ? 0.f
+                                                                                                                : T;
 }
 
 __device__ __forceinline__ float3 offset_point(float3 p, float3 ng, float3 dir, float eps) {
@@ -466,6 +473,21 @@ __device__ __forceinline__ void emit_ray(bool want, const DevScene& sc, RayBuf n
 }  // namespace
 
 // ------------------------------------------------------------------------------ raygen
+// Camera ray through pixel `pixel` offset by (xi, yi) pixels from its centre.
+__device__ __forceinline__ void primary_ray(const RenderParams& p, uint32_t pixel, float xi, float yi, float3* o,
+                                            float3* d) {
+  int px = (int)(pixel % (uint32_t)p.cam.width), py = (int)(pixel / (uint32_t)p.cam.width);
+  float sx = ((px + 0.5f + xi) / p.cam.width) * 2.f - 1.f;
+  float sy = 1.f - ((py + 0.5f + yi) / p.cam.height) * 2.f;
+  if (p.cam.ortho) {
+    *o = p.cam.pos + (sx * p.cam.ortho_half * p.cam.aspect) * p.cam.right + (sy * p.cam.ortho_half) * p.cam.up;
+    *d = p.cam.fwd;
+  } else {
+    *o = p.cam.pos;
+    *d = normalize3(p.cam.fwd + (sx * p.cam.tan_half * p.cam.aspect) * p.cam.right + (sy * p.cam.tan_half) * p.cam.up);
+  }
+}
+
 // One primary ray per wave-local path i (every lane of the warp calls this).
 __device__ __forceinline__ void dev_raygen(const RenderParams& p, const WaveDesc& w, uint32_t i, bool active,
                                            RayBuf rb, uint32_t* q, int* q_count, int qcap, Control* ctl) {
@@ -478,16 +500,7 @@ __device__ __forceinline__ void dev_raygen(const RenderParams& p, const WaveDesc
       xi = u.x - 0.5f;
       yi = u.y - 0.5f;
     }
-    int px = (int)(id.pixel % (uint32_t)p.cam.width), py = (int)(id.pixel / (uint32_t)p.cam.width);
-    float sx = ((px + 0.5f + xi) / p.cam.width) * 2.f - 1.f;
-    float sy = 1.f - ((py + 0.5f + yi) / p.cam.height) * 2.f;
-    if (p.cam.ortho) {
-      o = p.cam.pos + (sx * p.cam.ortho_half * p.cam.aspect) * p.cam.right + (sy * p.cam.ortho_half) * p.cam.up;
-      d = p.cam.fwd;
-    } else {
-      o = p.cam.pos;
-      d = normalize3(p.cam.fwd + (sx * p.cam.tan_half * p.cam.aspect) * p.cam.right + (sy * p.cam.tan_half) * p.cam.up);
-    }
+    primary_ray(p, id.pixel, xi, yi, &o, &d);
     rb.o[i] = make_float4(o.x, o.y, o.z, 0.f);
     rb.d[i] = make_float4(d.x, d.y, d.z, 1.f);
     rb.info[i] = make_uint2(i, (1u << 16));  // depth 0, no flags, tree code 1
@@ -775,7 +788,7 @@ __device__ __forceinline__ void dev_shadow(const RenderParams& p, const WaveDesc
     bool ovf = false;
     if (t1 > t0) {
       RayPre rp = ray_pre(o, d);
-      ShadowKey key{id.pixel, id.sample, inf.y >> 16, p.seed};
+      ShadowKey key{id.pixel, id.sample, inf.y >> 16, p.seed, id.lam};
       T = shadow_T<kStats, kTM>(p, p.sc, p.sp, (int)id.lam, __ldg(p.sp.lambda_nm + id.lam), key, s_nodes, n_staged, s, rp,
                            d, t0, t1, &nn, &nt, &ovf);
     }
@@ -829,7 +842,7 @@ __device__ __forceinline__ void dev_shadow_warp(const RenderParams& p, const Wav
   }
   const float3 o = f3(O), d = f3(D);
   const PathId id = path_id(p, w, inf.x);
-  const ShadowKey key{id.pixel, id.sample, inf.y >> 16, p.seed};
+  const ShadowKey key{id.pixel, id.sample, inf.y >> 16, p.seed, id.lam};
   const bool live = active && t1 > t0;
   bool ovf = false;
   const RayPre rp = ray_pre(o, d);

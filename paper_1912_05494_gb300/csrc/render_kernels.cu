@@ -204,6 +204,7 @@ static inline int blocks_for(long long n, int b) { return (int)((n + b - 1) / b)
 
 void launch_raygen(const RenderParams& p, const WaveDesc& w, RayBuf rb, uint32_t* q, int* q_count, int qcap,
                    Control* ctl, cudaStream_t st) {
+  if (p.bundle > 1) return launch_raygen_bundle(p, w, rb, q, q_count, qcap, ctl, st);
   if (w.n_paths == 0) return;
   k_raygen<<<blocks_for(w.n_paths, kBlock), kBlock, 0, st>>>(p, w, rb, q, q_count, qcap, ctl);
 }
@@ -228,6 +229,8 @@ void launch_traverse(const RenderParams& p, const Sched& sch, int total_blocks, 
 void launch_shade(const RenderParams& p, const WaveDesc& w, int n_rays, RayBuf cur, const float2* hits, RayBuf next,
                   uint32_t* q, int* q_count, int qcap, ShadowBuf sb, uint32_t* sq, int* sq_count, float* path_L,
                   Control* ctl, cudaStream_t st) {
+  if (p.bundle > 1)
+    return launch_shade_bundle(p, w, n_rays, cur, hits, next, q, q_count, qcap, sb, sq, sq_count, path_L, ctl, st);
   if (n_rays <= 0) return;
   const int tm = tile_mode(p);
   if (tm == 1)
@@ -268,6 +271,8 @@ static void launch_shadow_m(const RenderParams& p, const WaveDesc& w, const Sche
 
 void launch_shadow(const RenderParams& p, const WaveDesc& w, const Sched& sch, int total_blocks, int block,
                    int top_nodes, QueuePair qp, ShadowBuf sb, float* path_L, Control* ctl, cudaStream_t st) {
+  if (p.bundle > 1)
+    return launch_shadow_bundle(p, w, sch, total_blocks, block, top_nodes, qp, sb, path_L, ctl, st);
   const int tm = tile_mode(p);
   if (tm == 1) launch_shadow_m<1>(p, w, sch, total_blocks, block, top_nodes, qp, sb, path_L, ctl, st);
   else if (tm == 2) launch_shadow_m<2>(p, w, sch, total_blocks, block, top_nodes, qp, sb, path_L, ctl, st);
@@ -276,6 +281,7 @@ void launch_shadow(const RenderParams& p, const WaveDesc& w, const Sched& sch, i
 
 void launch_film_accum(const RenderParams& p, const WaveDesc& w, const float* path_L, double* film,
                        float* path_rad_out, uint32_t* path_hash_out, cudaStream_t st) {
+  if (p.bundle > 1) return launch_film_accum_bundle(p, w, path_L, film, path_rad_out, path_hash_out, st);
   k_film_accum<<<blocks_for(w.nc, 256), 256, 0, st>>>(p, w, path_L, film, path_rad_out, path_hash_out);
 }
 

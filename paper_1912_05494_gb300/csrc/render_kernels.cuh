@@ -33,6 +33,17 @@ void launch_film_accum(const RenderParams& p, const WaveDesc& w, const float* pa
                        float* path_rad_out, uint32_t* path_hash_out, cudaStream_t st);
 void launch_film_finalize(const RenderParams& p, const double* film, const double* cmf_w, float* spectral_out,
                           float* xyz_out, cudaStream_t st);
+// Spectral-bundle variants (bundle_kernels.cu); the launchers above forward to them when
+// p.bundle > 1.
+void launch_raygen_bundle(const RenderParams& p, const WaveDesc& w, RayBuf rb, uint32_t* q, int* q_count, int qcap,
+                          Control* ctl, cudaStream_t st);
+void launch_shade_bundle(const RenderParams& p, const WaveDesc& w, int n_rays, RayBuf cur, const float2* hits,
+                         RayBuf next, uint32_t* q, int* q_count, int qcap, ShadowBuf sb, uint32_t* sq, int* sq_count,
+                         float* path_L, Control* ctl, cudaStream_t st);
+void launch_shadow_bundle(const RenderParams& p, const WaveDesc& w, const Sched& sch, int total_blocks, int block,
+                          int top_nodes, QueuePair qp, ShadowBuf sb, float* path_L, Control* ctl, cudaStream_t st);
+void launch_film_accum_bundle(const RenderParams& p, const WaveDesc& w, const float* path_L, double* film,
+                              float* path_rad_out, uint32_t* path_hash_out, cudaStream_t st);
 void launch_cmf_table(int n_lambda, const float* lambda_nm, double* cmf_w, cudaStream_t st);
 void launch_rays_from_arrays(int n, const float* org, const float* dir, const DevScene sc, RayBuf rb, uint32_t* q,
                              int* q_count, int qcap, cudaStream_t st);

@@ -13,6 +13,7 @@
 namespace sdd {
 
 constexpr int kMaxSubdomains = 64;
+constexpr int kMaxBundle = 16;            // wavelengths per spectral bundle (member mask bits)
 constexpr int kStackSize = 64;            // BVH traversal stack entries per ray
 constexpr uint32_t kMissPrim = 0xFFFFFFFFu;
 
@@ -83,17 +84,21 @@ struct DevCamera {
 // Ray state, structure of arrays with capacity `cap`.
 struct RayBuf {
   float4* o;      // origin xyz, w = seg0 (distance back to the previous surface plane)
-  float4* d;      // direction xyz, w = throughput
-  uint2* info;    // x = wave-local path id, y = depth(8) | flags(8) << 8 | code(16) << 16
+  float4* d;      // direction xyz, w = throughput (unused with spectral bundles)
+  uint2* info;    // x = wave-local path id, y = depth(8) | flags(8) << 8 | code(16) << 16;
+                  // with spectral bundles the high 16 bits are the member mask instead
   int cap;
+  float* w;       // spectral bundles: per-member throughput [cap][bundle], else unused
 };
 
 struct ShadowBuf {
   float4* o;      // origin xyz, w unused
-  float4* d;      // direction xyz, w = contribution carried so far
+  float4* d;      // direction xyz, w = contribution carried so far (unused with bundles)
   uint2* info;    // x = wave-local path id, y = contribution slot (deterministic mode, low 16
-                  // bits) | bounce of the vertex that cast it << 16
+                  // bits; with spectral bundles the live member mask) | bounce of the vertex
+                  // that cast it << 16
   int cap;
+  float* c;       // spectral bundles: per-member contribution [cap][bundle], else unused
 };
 
 // Device control block: queue counters and error word, read back by the host.
@@ -113,7 +118,8 @@ enum RayFlags : uint32_t { FLAG_SUN_COUNTED = 1u };
 
 struct WaveDesc {
   uint32_t s0, ns;        // samples [s0, s0 + ns)
-  uint32_t c0, nc;        // cells [c0, c0 + nc) with cell = pixel_index * L + lambda
+  uint32_t c0, nc;        // cells [c0, c0 + nc) with cell = pixel_index * L + lambda, or with
+                          // spectral bundles cell = pixel_index * n_bundles + bundle
   uint32_t n_paths;       // ns * nc
 };
 
@@ -139,6 +145,10 @@ struct RenderParams {
   uint32_t* tile_queue;        // ray slots of the generation's tile hits (surrogate form)
   int* tile_count;
   int tile_cap;
+  // spectral bundles (Monte Carlo): `bundle` consecutive wavelengths share one ray while their
+  // chains agree; 1 = every wavelength is its own path
+  int bundle;
+  int n_bundles;               // ceil(L / bundle)
 };
 
 // Heterogeneous-tile mode compiled into the shading and shadow kernels: 0 the scene has no

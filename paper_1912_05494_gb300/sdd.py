@@ -60,7 +60,8 @@ class sdd_render_opts(C.Structure):
                 ("seed", C.c_uint64), ("max_depth", C.c_int), ("mode", C.c_int),
                 ("rr_start_depth", C.c_int), ("use_surrogate", C.c_int), ("batched", C.c_int),
                 ("n_pixels", C.c_int), ("pixels", C.c_void_p), ("wave_paths", C.c_int),
-                ("path_radiance_out", C.c_void_p), ("path_hash_out", C.c_void_p), ("surrogate", C.c_void_p)]
+                ("path_radiance_out", C.c_void_p), ("path_hash_out", C.c_void_p), ("surrogate", C.c_void_p),
+                ("bundle", C.c_int)]
 
 
 class sdd_stats(C.Structure):
@@ -283,6 +284,7 @@ def make_opts(spec, pixels=None, wave_paths=0, batched=0, path_radiance_out=None
     o.path_radiance_out = _ptr(path_radiance_out)
     o.path_hash_out = _ptr(path_hash_out)
     o.surrogate = surrogate.h if surrogate is not None else None
+    o.bundle = getattr(spec, "bundle", 1)
     o._keep = keep
     return o
 

@@ -1,0 +1,128 @@
+"""Spectral bundles on the GPU (through the C ABI) against the FP64 oracle's bundling rule.
+
+With bundle B the wavelengths jB .. jB+B-1 of a (pixel, sample) draw every random number on
+counter word j; the oracle still traces each wavelength's chain on its own, so every member
+of a GPU bundle is compared with the oracle's chain of that wavelength path by path, on the
+Monte Carlo bars of the unbundled path (relative image error <= 1e-3, branch flips <= 0.1 %
+of paths).  Cases cover full and partial last bundles (81 = 9 x 9 = 20 x 4 + 1 = 5 x 16 + 1),
+the split into reflected and transmitted members at thin slabs, the per-member rays of solid
+glass and brute-force tiles, the subdomain hand-off and the host-side argument checks.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1912_05494_gb300 import scenes as S  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def sdd():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1912_05494_gb300 import sdd as m
+    assert torch.cuda.is_available()
+    return m
+
+
+def rel_err(a, b):
+    return float(np.abs(a - b).sum() / np.abs(b).sum())
+
+
+def render(sdd, h, cam, spec, pixels=None, **kw):
+    n = cam.width * cam.height if pixels is None else len(pixels)
+    out = torch.empty((n, spec.n_lambda), device="cuda")
+    pr = torch.empty((n, spec.spp, spec.n_lambda), device="cuda")
+    ph = torch.empty((n, spec.spp, spec.n_lambda), device="cuda", dtype=torch.int32)
+    sdd.sdd_render(h.h, cam, spec, out, None, pixels=pixels, path_radiance_out=pr, path_hash_out=ph, **kw)
+    torch.cuda.synchronize()
+    return (out.cpu().numpy().astype(np.float64), pr.cpu().numpy().astype(np.float64),
+            ph.cpu().numpy().view(np.uint32))
+
+
+def compare(sdd, orc, sc, cam, spec, pixels=None, n_sub=None):
+    h = sdd.SceneHandle(sc, n_subdomains=n_sub)
+    gpu, gp, gh = render(sdd, h, cam, spec, pixels=pixels)
+    ref, rp, rh = orc.OracleScene(sc).render(cam, spec, pixels=pixels, want_paths=True)
+    flips = float(np.mean(gh != rh))
+    same = gh == rh
+    path_rel = np.abs(gp[same] - rp[same]) / (np.abs(rp[same]) + 1e-6 * np.abs(rp).mean() + 1e-30)
+    return flips, rel_err(gpu, ref), path_rel, gpu, ref
+
+
+@pytest.fixture(scope="module")
+def nave():
+    return S.nave_scene(seed=1)
+
+
+@pytest.mark.parametrize("bundle", [9, 4, 16, 2])
+def test_bundled_nave_matches_the_oracle(sdd, orc, nave, bundle):
+    sc, cam, spec = nave
+    cam = S.CameraData(**{**cam.__dict__, "width": 48, "height": 32})
+    spec = S.RenderSpec(**{**spec.__dict__, "spp": 4, "bundle": bundle})
+    flips, err, path_rel, gpu, ref = compare(sdd, orc, sc, cam, spec)
+    assert flips <= 1e-3, flips
+    assert err <= 1e-3, err
+    assert np.quantile(path_rel, 0.999) < 1e-3
+
+
+def test_bundled_nave_full_size_sampled_pixels(sdd, orc, nave):
+    """The full 1024x768, 16 spp, 81-wavelength frame with bundles of 9 on a seeded pixel
+    subset (each pixel's paths are the same computation in a subset)."""
+    sc, cam, spec = nave
+    spec = S.RenderSpec(**{**spec.__dict__, "bundle": 9})
+    pixels = np.sort(np.random.default_rng(12).choice(cam.width * cam.height, 300, replace=False)).astype(np.int32)
+    flips, err, _, _, _ = compare(sdd, orc, sc, cam, spec, pixels=pixels)
+    assert flips <= 1e-3, flips
+    assert err <= 1e-3, err
+
+
+@pytest.mark.parametrize("n_sub", [1, 5])
+def test_bundles_are_subdomain_invariant(sdd, nave, n_sub):
+    sc, cam, spec = nave
+    cam = S.CameraData(**{**cam.__dict__, "width": 40, "height": 24})
+    spec = S.RenderSpec(**{**spec.__dict__, "spp": 2, "bundle": 9})
+    a, pa, ha = render(sdd, sdd.SceneHandle(sc, n_subdomains=8), cam, spec)
+    b, pb, hb = render(sdd, sdd.SceneHandle(sc, n_subdomains=n_sub), cam, spec)
+    assert np.mean(ha != hb) <= 1e-3
+    same = ha == hb
+    assert np.allclose(pa[same], pb[same], rtol=1e-6, atol=0)
+
+
+def test_bundles_through_solid_glass(sdd, orc):
+    """The slab of solid glass (refraction depends on n(lambda)): transmitted members leave
+    on their own rays, reflected members stay together."""
+    sc, cam, spec = S.slab_scene(0)
+    cam = S.CameraData(**{**cam.__dict__, "width": 24, "height": 24})
+    spec = S.RenderSpec(**{**spec.__dict__, "mode": S.RENDER_MC, "spp": 16, "bundle": 4, "rr_start_depth": 3,
+                           "max_depth": 8})
+    flips, err, path_rel, _, _ = compare(sdd, orc, sc, cam, spec)
+    assert flips <= 1e-3, flips
+    assert err <= 1e-3, err
+    assert np.quantile(path_rel, 0.999) < 1e-3
+
+
+def test_bundles_through_brute_force_tiles(sdd, orc):
+    """Heterogeneous tiles traced by brute force: every member traces its own ray through the
+    tile (and its own shadow ray), on the bundle's tile stream."""
+    sc, cam, spec = S.tile_room_scene(width=40, height=24, spp=4)
+    spec = S.RenderSpec(**{**spec.__dict__, "bundle": 8})
+    flips, err, path_rel, _, _ = compare(sdd, orc, sc, cam, spec, n_sub=2)
+    assert flips <= 1e-3, flips
+    assert err <= 1e-3, err
+
+
+def test_bundle_argument_checks(sdd, nave):
+    sc, cam, spec = nave
+    cam = S.CameraData(**{**cam.__dict__, "width": 8, "height": 8})
+    h = sdd.SceneHandle(sc)
+    out = torch.empty((64, spec.n_lambda), device="cuda")
+    with pytest.raises(sdd.SddError, match="bundle"):
+        sdd.sdd_render(h.h, cam, S.RenderSpec(**{**spec.__dict__, "bundle": 17}), out)
+    with pytest.raises(sdd.SddError, match="bundle"):
+        sdd.sdd_render(h.h, cam, S.RenderSpec(**{**spec.__dict__, "bundle": 4}), out, batched=1)
+    dsc, dcam, dspec = S.slab_scene(0)
+    with pytest.raises(sdd.SddError, match="bundle"):
+        sdd.sdd_render(sdd.SceneHandle(dsc).h, dcam, S.RenderSpec(**{**dspec.__dict__, "bundle": 4}),
+                       torch.empty((dcam.width * dcam.height, dspec.n_lambda), device="cuda"))

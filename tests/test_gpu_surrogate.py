@@ -148,3 +148,17 @@ def test_native_training_run_matches_single_steps_and_learns(sdd):
     assert np.array_equal(a.params(), pb)
     hist = b.train(raw, y, steps=200, batch=1024, lr=1e-3, seed=2)
     assert np.mean(hist[-20:]) < 0.5 * hist[0], (hist[0], hist[-20:])
+
+
+def test_training_is_deterministic(sdd):
+    """Gradients are reduced over blocks in a fixed order: two runs from the same weights on
+    the same data give the same weights bit for bit."""
+    raw = torch.from_numpy(raw_inputs(5, 3000)).cuda()
+    y = torch.from_numpy(targets(np.random.default_rng(5), 3000)).cuda()
+    B, params = S.surrogate_init(4)
+    a = sdd.Surrogate(B, params, max_batch=2048)
+    b = sdd.Surrogate(B, params, max_batch=2048)
+    la = a.train(raw, y, steps=20, batch=2048, lr=1e-3, seed=3)
+    lb = b.train(raw, y, steps=20, batch=2048, lr=1e-3, seed=3)
+    assert np.array_equal(a.params(), b.params())
+    assert np.allclose(la, lb, rtol=1e-5)
