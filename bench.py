@@ -4,7 +4,10 @@ Workload (one step = one frame): the procedural nave (60 x 12 x 20 m, 24 lancet 
 200 thin-slab glass tiles with lead came, ~200k triangles), 6500 K sky + sun at 35 degrees,
 81 wavelengths 380-780 nm, 1024 x 768 pixels, 16 samples per pixel, depth 12 with Russian
 roulette, 8 subdomains along the nave.  One frame is 1024*768*16*81 = 1,019,215,872
-spectral samples (one (pixel, sample, wavelength) path each).
+spectral samples (one (pixel, sample, wavelength) path each).  Default form: spectral bundles
+of 14 wavelengths (one ray serves a bundle's chains while their branches agree; --bundle 1
+traces every wavelength on its own) in the batched form (one persistent launch per wave,
+frames replayed as a CUDA graph; --batched 0 for the host-driven wavefront).
 
 Printed JSON line (rank 0):
   value      Mspectral-samples/s of the device-resident frame (scene built, outputs allocated
@@ -50,10 +53,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Mspectral-samples/s at <=1% rel. image error vs FP64 oracle; surrogate vs plain"
 UNIT = "Mspectral-samples/s"
-WORKLOAD = "nave-200k {w}x{h} {spp}spp 81lambda depth12 RR S={s} (plain Monte Carlo)"
+WORKLOAD = "nave-200k {w}x{h} {spp}spp 81lambda depth12 RR S={s} (Monte Carlo, spectral bundles of {b}, {form})"
 TRAVERSE_SOURCES = ["paper_1912_05494_gb300/csrc/render_kernels.cu", "paper_1912_05494_gb300/csrc/render_device.cuh",
                     "paper_1912_05494_gb300/csrc/device_math.cuh", "paper_1912_05494_gb300/csrc/sdd_internal.h"]
 NCU_SUMMARY = os.path.join(ROOT, "profiles", "traverse_nave_ncu.md")
+FORMS = {0: "host-driven", 1: "batched: persistent kernel + CUDA graph"}
 
 
 def dist_env():
@@ -194,6 +198,7 @@ def run_reference(args):
         return 0
     from paper_1912_05494_gb300 import scenes as S
     scene, cam, spec = S.nave_scene(seed=1)
+    spec = S.RenderSpec(**{**spec.__dict__, "bundle": args.bundle})
     for _ in range(args.warmup):
         oracle_sample(scene, cam, spec, seconds_target=2.0, seed=100)
     vals = []
@@ -206,7 +211,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": frame_paths / (v * 1e6) * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD.format(w=cam.width, h=cam.height, spp=spec.spp, s=scene.n_subdomains),
+            "config": {"workload": WORKLOAD.format(w=cam.width, h=cam.height, spp=spec.spp, s=scene.n_subdomains, b=spec.bundle,
+                                           form=FORMS[getattr(args, "batched", 1)]),
                        "note": "each step renders a bounded seeded pixel sample; ms_per_step is "
                                                      "the full-frame time at that rate"},
             "cpu_baseline": {**last, "value": v},
@@ -360,7 +366,8 @@ def run_gpu(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD.format(w=cam.width, h=cam.height, spp=spec.spp, s=scene.n_subdomains),
+                "config": {"workload": WORKLOAD.format(w=cam.width, h=cam.height, spp=spec.spp, s=scene.n_subdomains, b=spec.bundle,
+                                           form=FORMS[getattr(args, "batched", 1)]),
                            "paths_per_step": frame_paths, "triangles": scene.n_triangles,
                            "subdomains": scene.n_subdomains, "l2": "flushed (512 MB write) before every frame",
                            "parallelism": f"replicas x{world}", "wave_paths": args.wave_paths or "auto",
@@ -583,8 +590,8 @@ def main(argv=None):
     ap.add_argument("--spp", type=int, default=16)
     ap.add_argument("--subdomains", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--batched", type=int, default=0, help="1: persistent kernels + CUDA graph; 0: host-driven")
-    ap.add_argument("--bundle", type=int, default=1,
+    ap.add_argument("--batched", type=int, default=1, help="1: persistent kernels + CUDA graph; 0: host-driven")
+    ap.add_argument("--bundle", type=int, default=14,
                     help="nave workload: wavelengths per spectral bundle (1 = every wavelength its own path)")
     ap.add_argument("--workload", choices=["nave", "large", "network"], default="nave")
     ap.add_argument("--net-rows", type=int, default=1 << 24, help="network workload: inference rows per step")

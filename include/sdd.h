@@ -181,12 +181,15 @@ sdd_status sdd_render_to_host(sdd_scene* scene, const sdd_camera* cam, const sdd
  *   traverse_block: threads per block of the traversal kernels: 64, 128 (default) or 256;
  *   top_nodes:      BVH nodes per subdomain (the top levels, stored breadth-first) that each
  *                   traversal block stages in shared memory, 0..640 (0 = none, default);
- *   wave_paths:     paths per wave when sdd_render_opts.wave_paths is 0 (0 = 2^26);
+ *   wave_paths:     paths per wave when sdd_render_opts.wave_paths is 0 (0 = 2^26, or 2^25
+ *                   bundle paths with spectral bundles);
  *   no_graph:       batched form only: 1 = launch the frame's kernels directly instead of
  *                   capturing and replaying them as a CUDA graph (default 0);
  *   queue_capacity: upper bound on the entries of each ray / subdomain queue (0 = automatic:
- *                   the wave size, 4x in deterministic mode).  Buffers keep their automatic
- *                   size; a frame that needs more returns SDD_ERR_QUEUE_OVERFLOW. */
+ *                   the wave size, 4x in deterministic mode, 2x with spectral bundles, and a
+ *                   host-driven wave that needs more is rendered again as two halves).
+ *                   Buffers keep their automatic size; with a bound set, a frame that needs
+ *                   more returns SDD_ERR_QUEUE_OVERFLOW. */
 typedef struct {
   int traverse_block;
   int top_nodes;
@@ -215,7 +218,7 @@ typedef struct {
   int64_t tri_tests;       /* triangles tested by closest-hit traversal (level >= 2) */
   int64_t shadow_node_visits, shadow_tri_tests;
   int64_t crossings;       /* interface hand-offs between subdomain queues */
-  int64_t paths;           /* spectral paths traced */
+  int64_t paths;           /* spectral paths traced ((pixel, sample, wavelength) chains) */
   int64_t waves;
   int64_t bytes_ray_state; /* ray/queue/hit bytes read+written by the traversal kernels */
   double ms_persistent;    /* batched form: persistent drain kernels (all steps of a wave) */
@@ -224,6 +227,8 @@ typedef struct {
   double ms_tile;          /* network form: fused tile-shading launches (host-driven form) */
   int64_t launches_tile;   /* network form: fused tile-shading launches */
   int64_t tile_shaded;     /* network form: tile hits shaded by the network (level >= 2) */
+  int64_t wave_splits;     /* host-driven form: waves rendered again as two halves after their
+                              rays outgrew the queues (spectral bundles that split often) */
 } sdd_stats;
 
 /* level 0: nothing; 1: CUDA-event timing of every launch; 2: also count BVH nodes and

@@ -16,14 +16,14 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsdd.so")
 ROOT = os.path.dirname(HERE)
 
-CUDA_SOURCES = ["api.cu", "render_kernels.cu", "bundle_kernels.cu", "noalloc.cu", "persistent.cu", "tile.cu", "mlp.cu", "surrogate_render.cu"]
+CUDA_SOURCES = ["api.cu", "render_kernels.cu", "bundle_kernels.cu", "noalloc.cu", "persistent.cu", "persistent_bundle.cu", "tile.cu", "mlp.cu", "surrogate_render.cu"]
 CXX_SOURCES = ["scene_build.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # The persistent kernel reads, within one launch, ray / hit / queue / path data that other
 # blocks (other SMs) wrote before a grid barrier; plain global loads are made to bypass the
 # SM's L1 (cache at L2 only) so that no stale L1 line is read.  Read-only scene data is
 # fetched with __ldg and keeps its caching.
-PER_FILE_FLAGS = {"persistent.cu": ["-Xptxas", "-dlcm=cg"]}
+PER_FILE_FLAGS = {"persistent.cu": ["-Xptxas", "-dlcm=cg"], "persistent_bundle.cu": ["-Xptxas", "-dlcm=cg"]}
 
 
 def _cuda_home() -> str:

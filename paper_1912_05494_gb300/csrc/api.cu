@@ -468,7 +468,7 @@ sdd_status render_batched(sdd_scene* s, const RenderParams& p, const std::vector
     CK(cudaEventCreate(&s->pev[1]));
   }
   if (!s->d_pc) CK(cudaMalloc(&s->d_pc, sizeof(PersistCtl)));
-  const int grid = persistent_grid(p.stats >= 2, tile_mode(p));
+  const int grid = persistent_grid(p.stats >= 2, tile_mode(p), p.bundle > 1);
   if (grid <= 0) return fail(SDD_ERR_CUDA, "persistent kernel does not fit on this device");
   PersistBuffers b;
   for (int i = 0; i < 2; ++i) {
@@ -547,6 +547,43 @@ sdd_status render_batched(sdd_scene* s, const RenderParams& p, const std::vector
   return SDD_OK;
 }
 
+// Each wave as two halves, in order: by samples when it has several (each cell still
+// accumulates its samples in order), else by cells.  A wave of one path stays whole.
+std::vector<WaveDesc> halve_waves(const std::vector<WaveDesc>& in) {
+  std::vector<WaveDesc> out;
+  for (const WaveDesc& w : in) {
+    if (w.ns <= 1 && w.nc <= 1) {
+      out.push_back(w);
+      continue;
+    }
+    WaveDesc a = w, b = w;
+    if (w.ns > 1) {
+      a.ns = w.ns / 2;
+      b.s0 = w.s0 + a.ns;
+      b.ns = w.ns - a.ns;
+    } else {
+      a.nc = w.nc / 2;
+      b.c0 = w.c0 + a.nc;
+      b.nc = w.nc - a.nc;
+    }
+    a.n_paths = a.ns * a.nc;
+    b.n_paths = b.ns * b.nc;
+    out.push_back(a);
+    out.push_back(b);
+  }
+  return out;
+}
+
+// (pixel, sample, wavelength) chains of a wave: its cells times the samples, with bundles the
+// members of each cell's bundle (the last bundle of a pixel may be partial).
+int64_t spectral_paths(const RenderParams& p, const WaveDesc& w) {
+  if (p.bundle <= 1) return (int64_t)w.n_paths;
+  const int64_t nb = p.n_bundles, c0 = w.c0, c1 = (int64_t)w.c0 + w.nc;
+  const int64_t last = c1 / nb - c0 / nb;  // cells in [c0, c1) holding a pixel's last bundle
+  const int64_t members = (int64_t)w.nc * p.bundle - last * (nb * p.bundle - p.sp.n_lambda);
+  return members * (int64_t)w.ns;
+}
+
 sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opts* o, float* spectral_out,
                        float* xyz_out, cudaStream_t st) {
   if (!s || !cam || !o) return fail(SDD_ERR_ARG, "NULL scene, camera or options");
@@ -577,7 +614,6 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
   const int B = o->bundle > 1 ? o->bundle : 1;
   if (B > 1 && o->mode != SDD_MODE_MONTE_CARLO) return fail(SDD_ERR_ARG, "spectral bundles need Monte Carlo mode");
   if (B > 1 && o->use_surrogate) return fail(SDD_ERR_ARG, "spectral bundles do not support use_surrogate");
-  if (B > 1 && o->batched) return fail(SDD_ERR_ARG, "spectral bundles do not support the batched form");
   const int L = o->n_lambda;
   const int n_bundles = (L + B - 1) / B;
   const long long n_px = o->n_pixels > 0 ? o->n_pixels : img;
@@ -592,9 +628,9 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
 
   // waves
   const bool det = o->mode == SDD_MODE_DETERMINISTIC;
-  // default: 2^26 spectral paths per wave (2^26 / B bundle rays)
-  long long wmax =
-      o->wave_paths > 0 ? o->wave_paths : (s->tuning.wave_paths > 0 ? s->tuning.wave_paths : (1LL << 26) / B);
+  // default: 2^26 paths per wave, 2^25 with bundles (each carrying up to B wavelengths)
+  long long wmax = o->wave_paths > 0 ? o->wave_paths
+                                     : (s->tuning.wave_paths > 0 ? s->tuning.wave_paths : (B > 1 ? 1LL << 25 : 1LL << 26));
   wmax = std::min<long long>(wmax, 1LL << 28);
   std::vector<WaveDesc> waves;
   if (n_cells <= wmax) {
@@ -624,8 +660,9 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
   for (auto& w : waves) wave_paths = std::max<size_t>(wave_paths, w.n_paths);
   // contribution slots per path: the deterministic tree's leaves, or one per bundle member
   const int n_slots = det ? (1 << (o->max_depth + 1)) : B;
-  // rays of one generation: a Monte Carlo path has one ray, a bundle at most one per member
-  const size_t cap = det ? wave_paths * 4 : wave_paths * (size_t)B;
+  // rays of one generation: a Monte Carlo path has one ray; a bundle has one per group of
+  // members that agree, queued for twice the paths (a wave that needs more is split, below)
+  const size_t cap = det ? wave_paths * 4 : wave_paths * (size_t)(B > 1 ? 2 : 1);
   const bool want_hash = o->path_hash_out != nullptr;
   r = ensure_workspace(s, cap, wave_paths, n_slots, want_hash, B);
   if (r) return r;
@@ -707,15 +744,30 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
   // above keep the automatic size
   const int qcap = (int)(s->tuning.queue_capacity > 0 ? std::min<size_t>(cap, (size_t)s->tuning.queue_capacity) : cap);
   if (o->batched) {
-    r = render_batched(s, p, waves, n_slots, qcap, o, spectral_out, xyz_out, st);
-    if (r) return r;
-    for (const WaveDesc& w : waves) {
-      s->stats.waves++;
-      s->stats.paths += w.n_paths;
+    // A frame whose rays outgrew the queues is rendered again with every wave halved (see the
+    // host-driven form below); the frame's film is cleared at its start.
+    std::vector<WaveDesc> bw = waves;
+    for (int attempt = 0;; ++attempt) {
+      r = render_batched(s, p, bw, n_slots, qcap, o, spectral_out, xyz_out, st);
+      if (r) return r;
+      r = read_ctl(s, s->gstream);
+      if (r) return r;
+      const uint32_t e = s->h_ctl->error;
+      const bool overflow = (e & (ERR_QUEUE_OVERFLOW | ERR_SHADOW_OVERFLOW)) != 0u && !(e & ~(ERR_QUEUE_OVERFLOW | ERR_SHADOW_OVERFLOW));
+      bool splittable = false;
+      for (const WaveDesc& w : bw) splittable = splittable || w.ns > 1 || w.nc > 1;
+      if (overflow && s->tuning.queue_capacity == 0 && attempt < 12 && splittable) {
+        bw = halve_waves(bw);
+        s->stats.wave_splits++;
+        continue;
+      }
+      if (e) return device_error(e);
+      break;
     }
-    r = read_ctl(s, s->gstream);
-    if (r) return r;
-    if (s->h_ctl->error) return device_error(s->h_ctl->error);
+    for (const WaveDesc& w : bw) {
+      s->stats.waves++;
+      s->stats.paths += spectral_paths(p, w);
+    }
     s->stats.node_visits = (int64_t)s->h_ctl->node_visits;
     s->stats.tri_tests = (int64_t)s->h_ctl->tri_tests;
     s->stats.shadow_node_visits = (int64_t)s->h_ctl->shadow_node_visits;
@@ -730,7 +782,7 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
     return SDD_OK;
   }
   CK(cudaMemsetAsync(s->d_ctl, 0, sizeof(Control), st));
-  for (const WaveDesc& w : waves) {
+  auto run_wave = [&](const WaveDesc& w) -> sdd_status {
     CK(cudaMemsetAsync(s->d_ctl, 0, offsetof(Control, node_visits), st));
     CK(cudaMemsetAsync(s->path_L.p, 0, sizeof(float) * (size_t)w.n_paths * n_slots, st));
     int cur = 0;
@@ -778,7 +830,27 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
     CK(cudaGetLastError());
     count_launch(s, TK_FILM);
     s->stats.waves++;
-    s->stats.paths += w.n_paths;
+    s->stats.paths += spectral_paths(p, w);
+    return SDD_OK;
+  };
+  // A wave whose rays outgrow the queues (spectral bundles split into more rays than they
+  // have paths only where their members' branches differ, so their queues are sized for twice
+  // the paths) is abandoned before its film accumulation and rendered again as two halves:
+  // per cell the samples are still accumulated in order, so the image is the same.
+  std::vector<std::pair<WaveDesc, int>> work;
+  for (auto it = waves.rbegin(); it != waves.rend(); ++it) work.push_back({*it, 0});
+  while (!work.empty()) {
+    const WaveDesc w = work.back().first;
+    const int depth = work.back().second;
+    work.pop_back();
+    r = run_wave(w);
+    if (r == SDD_OK) continue;
+    const bool can_split = r == SDD_ERR_QUEUE_OVERFLOW && s->tuning.queue_capacity == 0 && depth < 24 &&
+                           (w.ns > 1 || w.nc > 1);
+    if (!can_split) return r;
+    s->stats.wave_splits++;
+    const std::vector<WaveDesc> halves = halve_waves({w});
+    for (auto it = halves.rbegin(); it != halves.rend(); ++it) work.push_back({*it, depth + 1});
   }
   int ev = s->ev_begin(TK_FILM, st);
   launch_film_finalize(p, s->film.p, s->cmf_w.p, spectral_out, xyz_out, st);

@@ -129,18 +129,17 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
                                                  Control* ctl) {
   const int B = p.bundle;
   const float eps = p.sc.eps;
-  // children: group 0 / 1 (members leaving in one direction) and singles (each member on its
-  // own direction)
+  // children: group 0 (members leaving in direction gd0), group 1 (thin-slab transmission:
+  // members going straight on) and singles (each member on its own direction).  Origins and
+  // the facing normal are recomputed where needed rather than kept live.
   uint32_t gm[2] = {0u, 0u}, singles = 0u, msh = 0u;
-  float3 gd[2], go[2], osh = make_float3(0.f, 0.f, 0.f), dsh = osh;
-  float gs[2] = {0.f, 0.f};
   uint32_t gf[2] = {0u, 0u};
-  gd[0] = gd[1] = go[0] = go[1] = osh;
+  float3 gd0 = make_float3(0.f, 0.f, 0.f), dsh = gd0;
   uint32_t path = 0, v = 0, flags = 0, j = 0, lam0 = 0;
   int kind = -1, mat = 0;
   bool roulette = false;
-  float uw = 0.f, cl_sh = 0.f, cos_i = 0.f, hit_t = 0.f, seg0 = 0.f;
-  float3 pt = osh, ng = osh, nf = osh, d = osh;
+  float uw = 0.f, cl_sh = 0.f, cos_i = 0.f, seg0 = 0.f;
+  float3 pt = gd0, ng = gd0, d = gd0;
   float* wr = cur.w + (size_t)(active ? r : 0) * B;
   uint32_t* hp = nullptr;
   PathId id{};
@@ -152,7 +151,6 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
     const uint32_t depth = inf.y & 0xFFu, mask = inf.y >> 16;
     flags = (inf.y >> 8) & 0xFFu;
     seg0 = O.w;
-    hit_t = H.x;
     const float3 o = f3(O);
     d = f3(D);
     id = path_id_bundle(p, w, path);
@@ -183,7 +181,7 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
         kind = __ldg(p.sp.mat_kind + mat);
         pt = o + H.x * d;
         const float cos_n = dot3(d, ng);
-        nf = cos_n < 0.f ? ng : -1.f * ng;
+        const float3 nf = cos_n < 0.f ? ng : -1.f * ng;
         cos_i = fabsf(cos_n);
         const float4 u = draw4(id.pixel, id.sample, v, STREAM_PATH, 0, j, p.seed);
         uw = u.w;
@@ -207,7 +205,7 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
           }
           hash_event(hp, gm[0], EV_REFLECT);
           hash_event(hp, singles, EV_TRANSMIT);
-          gd[0] = reflect3(d, nf);
+          gd0 = reflect3(d, nf);
           gf[0] = flags & ~FLAG_SUN_COUNTED;
         } else if (kind == MAT_SLAB) {
           const float thick = __ldg(p.sp.mat_thick + mat);
@@ -221,9 +219,8 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
           }
           hash_event(hp, gm[0], EV_REFLECT);
           hash_event(hp, gm[1], EV_TRANSMIT);
-          gd[0] = reflect3(d, nf);
+          gd0 = reflect3(d, nf);
           gf[0] = flags & ~FLAG_SUN_COUNTED;
-          gd[1] = d;
           gf[1] = flags;
         } else if (kind == MAT_DIFFUSE) {
           const float* ma = p.sp.mat_albedo + (size_t)mat * p.sp.n_lambda + lam0;
@@ -238,13 +235,12 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
             float cl = dot3(nf, wl);
             if (cl > 0.f) {
               msh = mask;
-              osh = offset_point(pt, ng, wl, eps);
               dsh = wl;
               cl_sh = cl;
             }
           }
           gm[0] = mask;
-          gd[0] = cosine_dir(nf, u.y, u.z);
+          gd0 = cosine_dir(nf, u.y, u.z);
           gf[0] = flags | FLAG_SUN_COUNTED;
         } else if (kTM == 1 && kind == MAT_TILE) {
           singles = mask;  // each member traces its own ray through the tile
@@ -266,18 +262,20 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
             }
           }
         }
-        for (int g = 0; g < 2; ++g)
-          if (gm[g]) {
-            go[g] = offset_point(pt, ng, gd[g], eps);
-            gs[g] = seg0_of(ng, gd[g], eps);
-          }
       }
     }
   }
   // group children
 #pragma unroll
   for (int g = 0; g < 2; ++g) {
-    const int pos = emit_bundle_ray(gm[g] != 0u, p.sc, next, next_count, q, q_count, qcap, go[g], gs[g], gd[g], path,
+    const float3 dg = g == 0 ? gd0 : d;
+    float3 og = dg;
+    float sg = 0.f;
+    if (gm[g]) {
+      og = offset_point(pt, ng, dg, eps);
+      sg = seg0_of(ng, dg, eps);
+    }
+    const int pos = emit_bundle_ray(gm[g] != 0u, p.sc, next, next_count, q, q_count, qcap, og, sg, dg, path,
                                     v | (gf[g] << 8) | (gm[g] << 16), ctl);
     if (pos >= 0) {
       float* cw = next.w + (size_t)pos * B;
@@ -296,6 +294,7 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
       uint32_t fs = 0u;
       if (want) {
         const float lambda = __ldg(p.sp.lambda_nm + lam0 + b);
+        const float3 nf = dot3(d, ng) < 0.f ? ng : -1.f * ng;
         if (kind == MAT_SOLID) {
           const bool inside = dot3(d, ng) > 0.f;
           const float nre = __ldg(mn + b);
@@ -346,6 +345,7 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
   }
   // shadow ray toward the sun, one contribution per member
   const bool esh = msh != 0u;
+  const float3 osh = esh ? offset_point(pt, ng, dsh, eps) : dsh;
   int pos = warp_append(shadow_count, 0, esh);
   bool ok = esh && pos < sb.cap;
   if (esh && !ok) atomicOr(&ctl->error, ERR_SHADOW_OVERFLOW);

@@ -1,248 +1,18 @@
 // persistent.cu -- the batched form of the wavefront: one cooperative launch drains a
-// whole wave.
-//
-// Sec. 5 of the paper lets a processor keep several sub-domains loaded, work on whichever
-// still has many rays, and gather results while other rays are processed; Sec. 4 asks for
-// dynamic job balancing so that faster workers take more work.  On one GB300 this becomes a
-// persistent kernel: every block loops over
-//   raygen -> per generation: [closest-hit passes over all subdomain queues, blocks taking
-//   128-ray chunks from a shared work counter] -> shade -> [shadow passes] -> film
-// with grid-wide barriers between the steps instead of host round trips.  The per-ray work
-// is the same device code as the host-driven kernels (render_device.cuh), so both forms
-// produce bit-identical images.
-//
-// Queue bookkeeping without races: queue counts rotate through three buffers.  The step
-// that consumes buffer c appends hand-offs into c+1 and clears c+2 (consumed two steps ago,
-// copied by every block before the barrier that ended that step), so a buffer is always
-// cleared one barrier before anyone appends to it.  Work counters rotate the same way.  A
-// pass that finds its input empty ends without a barrier, so nothing may write its input
-// buffer until the next barrier: the following step writes the next buffer instead.
-//
-// Every grid barrier waits at most kBarrierTimeoutNs; on expiry the block sets the abort
-// flag and the frame's error word, all blocks leave at their next barrier and the host
-// reports SDD_ERR_TIMEOUT.
-#include <cooperative_groups.h>
-
-#include "persistent.cuh"
-#include "render_device.cuh"
+// whole wave (the kernel is in persistent_kernel.cuh; its spectral-bundle instantiations are
+// compiled in persistent_bundle.cu).
+#include "persistent_kernel.cuh"
 
 namespace sdd {
 
-namespace {
-
-constexpr int kPB = 128;  // threads per block
-constexpr unsigned long long kBarrierTimeoutNs = 5ull * 1000 * 1000 * 1000;
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Grid-wide barrier with a time limit.  Returns false when the wave must be abandoned.
-__device__ bool grid_barrier(PersistCtl* pc, Control* ctl, unsigned long long timeout_ns = kBarrierTimeoutNs) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned* vgen = &pc->bar_gen;
-    volatile int* vabort = &pc->abort;
-    unsigned g = *vgen;
-    __threadfence();
-    unsigned arrived = atomicAdd(&pc->bar_count, 1u);
-    if (arrived == gridDim.x - 1) {
-      pc->bar_count = 0;
-      __threadfence();
-      atomicAdd(&pc->bar_gen, 1u);
-    } else {
-      unsigned long long t0 = global_ns();
-      while (*vgen == g) {
-        if (*vabort) break;
-        if (global_ns() - t0 > timeout_ns) {
-          atomicExch(&pc->abort, 1);
-          atomicOr(&ctl->error, ERR_TIMEOUT);  // survives the next wave's reset of pc
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-    s_ok = *vabort == 0;
+// The kernel for a scene's tile mode (0 none, 1 brute force, 2 network) and path layout.
+static const void* persistent_kernel(bool stats, int tile_mode, bool bundle) {
+  if (bundle) return persistent_bundle_kernel(stats, tile_mode);
+  switch (tile_mode) {
+    case 1: return stats ? (const void*)k_persistent_wave<true, 1, false> : (const void*)k_persistent_wave<false, 1, false>;
+    case 2: return stats ? (const void*)k_persistent_wave<true, 2, false> : (const void*)k_persistent_wave<false, 2, false>;
+    default: return stats ? (const void*)k_persistent_wave<true, 0, false> : (const void*)k_persistent_wave<false, 0, false>;
   }
-  __syncthreads();
-  return s_ok != 0;
-}
-
-// Per-subdomain queue counts (clamped to cap) into s_count and the exclusive prefix sums of
-// the counts rounded up to whole chunks of kPB rays into s_prefix; returns the padded total.
-// A chunk then never straddles two subdomains, so every block works on one subdomain's
-// queue at a time and its warps enter the traversal converged.
-// The leading barrier keeps thread 0 from overwriting the shared arrays while another
-// thread still reads the previous call's values: a pass that finds its queues empty leaves
-// without a grid barrier, so two calls can follow each other with no barrier in between.
-__device__ int load_prefix(const int* counts, int n_sub, int cap, int* s_prefix, int* s_count) {
-  __shared__ int s_total;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int acc = 0;
-    for (int s = 0; s < n_sub; ++s) {
-      const int c = min(max(((volatile const int*)counts)[s], 0), cap);
-      s_count[s] = c;
-      s_prefix[s] = acc;
-      acc += (c + kPB - 1) / kPB * kPB;
-    }
-    s_prefix[n_sub] = acc;
-    s_total = acc;
-  }
-  __syncthreads();
-  return s_total;
-}
-
-__device__ __forceinline__ int find_subdomain(const int* s_prefix, int n_sub, int j) {
-  int lo = 0, hi = n_sub - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (s_prefix[mid] <= j) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
-// Clear the count buffer and work counter that the step after next will write.
-__device__ __forceinline__ void clear_ahead(int (*counts)[kMaxSubdomains], int* work, int idx) {
-  if (blockIdx.x == 0) {
-    for (int s = threadIdx.x; s < kMaxSubdomains; s += blockDim.x) counts[idx][s] = 0;
-    if (threadIdx.x == 0) work[idx] = 0;
-  }
-}
-
-}  // namespace
-
-// Eight resident blocks per SM (registers bounded at 64; ~150 B of spills) for scenes
-// without brute-force tiles: measured faster than 6 (80 registers, no spills), 10 or 12 (more
-// spills); the brute-force tile tracer needs 128 registers (four blocks).
-template <bool kStats, int kTM>
-__global__ void __launch_bounds__(kPB, kTM == 1 ? 4 : 8) k_persistent_wave(RenderParams p, WaveDesc w, PersistBuffers b,
-                                                         PersistCtl* pc, Control* ctl, int seg) {
-  __shared__ int s_prefix[kMaxSubdomains + 1];
-  __shared__ int s_count[kMaxSubdomains];
-  __shared__ int s_chunk;
-  const int n_sub = p.sc.n_sub;
-  const uint32_t nthreads = gridDim.x * blockDim.x;
-  const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
-
-  PersistState S;
-  if (seg == SEG_WAVE || seg == SEG_RAYGEN) {
-    // raygen: primary rays into generation 0 and the closest queues (counts buffer 0)
-    for (uint32_t base = blockIdx.x * blockDim.x; base < w.n_paths; base += nthreads) {
-      uint32_t i = base + threadIdx.x;
-      dev_raygen(p, w, i, i < w.n_paths, b.rb[0], b.q[0], pc->qc[0], b.qcap, ctl);
-    }
-    if (!grid_barrier(pc, ctl)) return;
-    S = PersistState{0, 0, 0, 0, 0, (int)w.n_paths, 0, 0};
-    if (seg == SEG_RAYGEN) {
-      if (leader) pc->st = S;
-      return;
-    }
-  } else {
-    const volatile PersistState* vs = &pc->st;
-    S = PersistState{vs->cq, vs->qe, vs->sq, vs->se, vs->cur, vs->n_rays, vs->gen, 0};
-    if (S.n_rays <= 0 || *(volatile int*)&pc->abort) return;  // drained or abandoned
-  }
-
-  while (S.n_rays > 0) {
-    if (S.gen > p.max_depth + 1) {
-      if (leader) atomicOr(&ctl->error, ERR_TIMEOUT);
-      S.n_rays = 0;
-      break;
-    }
-    const int par = S.gen & 1;
-    if (seg != SEG_SHADOW) {
-      if (leader) {
-        pc->next_rays[par] = 0;
-        pc->next_shadow[par] = 0;
-      }
-      bool ran_pass = false;
-      for (int pass = 0; pass <= 2 * kMaxSubdomains + 2; ++pass) {
-        int total = load_prefix(pc->qc[S.cq], n_sub, b.qcap, s_prefix, s_count);
-        clear_ahead(pc->qc, pc->wq, (S.cq + 2) % 3);
-        if (total == 0) break;
-        QueuePair qp{b.q[S.qe], b.q[1 - S.qe], pc->qc[(S.cq + 1) % 3], b.qcap};
-        for (;;) {
-          if (threadIdx.x == 0) s_chunk = atomicAdd(&pc->wq[S.cq], (int)blockDim.x);
-          __syncthreads();
-          const int c0 = s_chunk;
-          __syncthreads();
-          if (c0 >= total) break;
-          const int s = find_subdomain(s_prefix, n_sub, c0);  // the whole chunk's subdomain
-          const int i = c0 - s_prefix[s] + (int)threadIdx.x;
-          dev_traverse_warp<kStats>(p, s, i, i < s_count[s], nullptr, 0, qp, b.rb[S.cur], b.hits, ctl);
-        }
-        ran_pass = true;
-        if (!grid_barrier(pc, ctl)) return;
-        S.cq = (S.cq + 1) % 3;
-        S.qe = 1 - S.qe;
-      }
-      if (!ran_pass && !grid_barrier(pc, ctl)) return;
-
-      // Shade every ray of this generation.  The last closest pass found its input buffer
-      // cq empty and left without a barrier, so slower blocks may still be reading cq:
-      // children go to the next buffer in the rotation instead (cleared two steps ago, read
-      // by nobody), and the rotation moves past the empty pass.  Shadow rays go to the
-      // shadow queues; tile hits for the network go to the tile queue.
-      for (uint32_t base = blockIdx.x * blockDim.x; base < (uint32_t)S.n_rays; base += nthreads) {
-        int r = (int)(base + threadIdx.x);
-        dev_shade<kTM>(p, w, r, r < S.n_rays, b.rb[S.cur], b.hits, b.rb[1 - S.cur], &pc->next_rays[par],
-                       b.q[1 - S.qe], pc->qc[(S.cq + 1) % 3], b.qcap, b.sb, &pc->next_shadow[par], b.sq[S.se],
-                       pc->sqc[S.sq], b.path_L, ctl);
-      }
-      S.cq = (S.cq + 1) % 3;
-      S.qe = 1 - S.qe;
-      if (!grid_barrier(pc, ctl)) return;
-      if (seg == SEG_CLOSEST_SHADE) {
-        if (leader) pc->st = S;  // every block holds the same state
-        return;
-      }
-    }
-
-    for (int pass = 0; pass <= 2 * kMaxSubdomains + 2; ++pass) {
-      int total = load_prefix(pc->sqc[S.sq], n_sub, b.qcap, s_prefix, s_count);
-      clear_ahead(pc->sqc, pc->wsq, (S.sq + 2) % 3);
-      if (total == 0) break;
-      QueuePair qp{b.sq[S.se], b.sq[1 - S.se], pc->sqc[(S.sq + 1) % 3], b.qcap};
-      for (;;) {
-        if (threadIdx.x == 0) s_chunk = atomicAdd(&pc->wsq[S.sq], (int)blockDim.x);
-        __syncthreads();
-        const int c0 = s_chunk;
-        __syncthreads();
-        if (c0 >= total) break;
-        const int s = find_subdomain(s_prefix, n_sub, c0);
-        const int i = c0 - s_prefix[s] + (int)threadIdx.x;
-        if constexpr (kTM == 1) {  // the same walk choice as the host-driven shadow kernel
-          dev_shadow_warp<kStats, kTM>(p, w, s, i, i < s_count[s], nullptr, 0, qp, b.sb, b.path_L, ctl);
-        } else {
-          dev_shadow<kStats, kTM>(p, w, s, i, i < s_count[s], nullptr, 0, qp, b.sb, b.path_L, ctl);
-        }
-      }
-      if (!grid_barrier(pc, ctl)) return;
-      S.sq = (S.sq + 1) % 3;
-      S.se = 1 - S.se;
-    }
-    S.n_rays = min(*(volatile int*)&pc->next_rays[par], b.qcap);
-    if (*(volatile int*)&pc->next_rays[par] > b.qcap && leader) atomicOr(&ctl->error, ERR_QUEUE_OVERFLOW);
-    S.cur = 1 - S.cur;
-    S.gen++;
-    if (seg == SEG_SHADOW) break;
-  }
-  if (seg != SEG_WAVE && leader) pc->st = S;
-}
-
-template <bool kStats, int kTM>
-static int persistent_blocks() {
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent_wave<kStats, kTM>, kPB, 0);
-  return sms * per_sm;
 }
 
 // Watchdog self-test: every block but the last enters a grid barrier that the last block
@@ -257,23 +27,22 @@ cudaError_t barrier_selftest(PersistCtl* pc, Control* ctl, int timeout_ms) {
   return cudaGetLastError();
 }
 
-// Blocks of the cooperative launch for a scene's tile mode (0 none, 1 brute force, 2 network).
-int persistent_grid(bool stats, int tile_mode) {
-  if (tile_mode == 1) return stats ? persistent_blocks<true, 1>() : persistent_blocks<false, 1>();
-  if (tile_mode == 2) return stats ? persistent_blocks<true, 2>() : persistent_blocks<false, 2>();
-  return stats ? persistent_blocks<true, 0>() : persistent_blocks<false, 0>();
+// Blocks of the cooperative launch: every SM times the blocks of the kernel that fit on one.
+int persistent_grid(bool stats, int tile_mode, bool bundle) {
+  const void* fn = persistent_kernel(stats, tile_mode, bundle);
+  if (!fn) return 0;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPB, 0);
+  return sms * per_sm;
 }
 
 cudaError_t launch_persistent_wave(const RenderParams& p, const WaveDesc& w, const PersistBuffers& b, PersistCtl* pc,
                                    Control* ctl, int grid, cudaStream_t st, int seg) {
   void* args[] = {(void*)&p, (void*)&w, (void*)&b, (void*)&pc, (void*)&ctl, (void*)&seg};
-  const void* fn;
-  const bool stats = p.stats >= 2;
-  switch (tile_mode(p)) {
-    case 1: fn = stats ? (const void*)k_persistent_wave<true, 1> : (const void*)k_persistent_wave<false, 1>; break;
-    case 2: fn = stats ? (const void*)k_persistent_wave<true, 2> : (const void*)k_persistent_wave<false, 2>; break;
-    default: fn = stats ? (const void*)k_persistent_wave<true, 0> : (const void*)k_persistent_wave<false, 0>;
-  }
+  const void* fn = persistent_kernel(p.stats >= 2, tile_mode(p), p.bundle > 1);
+  if (!fn) return cudaErrorInvalidValue;
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPB), args, 0, st);
 }
 

@@ -72,7 +72,8 @@ class sdd_stats(C.Structure):
                                           "rays_shadow", "node_visits", "tri_tests", "shadow_node_visits",
                                           "shadow_tri_tests", "crossings", "paths", "waves", "bytes_ray_state")] + \
                [("ms_persistent", C.c_double), ("launches_persistent", C.c_int64), ("graph_replays", C.c_int64),
-                ("ms_tile", C.c_double), ("launches_tile", C.c_int64), ("tile_shaded", C.c_int64)]
+                ("ms_tile", C.c_double), ("launches_tile", C.c_int64), ("tile_shaded", C.c_int64),
+                ("wave_splits", C.c_int64)]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
