@@ -429,9 +429,11 @@ def run_large(args):
     held = {"mae_T": float(np.abs(p[:, 0] - y[:, 0]).mean()), "mae_R": float(np.abs(p[:, 1] - y[:, 1]).mean()),
             "samples": int(hr.shape[0])}
     net_kw = {"use_surrogate": 1, "surrogate": net, "batched": 1}
+    # the network forms trace spectral bundles; the plain form every wavelength on its own
+    spec_net = S.RenderSpec(**{**spec.__dict__, "bundle": args.bundle})
     tuned = None
     if args.autotune:
-        tuned = A.autotune(scene, cam, spec, subdomains=(4, 8, 16, 32), blocks=(128,), top_nodes=(0,),
+        tuned = A.autotune(scene, cam, spec_net, subdomains=(4, 8, 16, 32), blocks=(128,), top_nodes=(0,),
                            wave_paths=(0,), sample_pixels=1 << 17, sample_spp=1, use_cache=False,
                            render_kw=net_kw)
         scene.n_subdomains = tuned["n_subdomains"]
@@ -445,7 +447,7 @@ def run_large(args):
     frame_paths = n_px * spec.spp * spec.n_lambda
     stream = torch.cuda.current_stream()
 
-    def timed(kw, steps, warmup):
+    def timed(kw, steps, warmup, spec=spec):
         for _ in range(warmup):
             sdd.sdd_render(h.h, cam, spec, out, xyz, **kw)
         torch.cuda.synchronize()
@@ -468,7 +470,7 @@ def run_large(args):
 
     if args.forms != "both":  # one form only (profiling); no comparison
         kw = net_kw if args.forms == "net" else {"batched": 0}
-        ms, launches, _, _ = timed(kw, args.steps, args.warmup)
+        ms, launches, _, _ = timed(kw, args.steps, args.warmup, spec_net if args.forms == "net" else spec)
         print(json.dumps({"workload": "large", "form": args.forms, "frame": [cam.width, cam.height, spec.spp],
                           "ms_per_step": ms, "value": frame_paths / (ms / 1e3) / 1e6, "unit": UNIT,
                           "gpu_launches": launches}), flush=True)
@@ -476,8 +478,9 @@ def run_large(args):
         return 0
     clocks = ClockSampler(0)
     clocks.start()
-    ms_net, launches_net, img_net, _ = timed(net_kw, args.steps, args.warmup)
-    ms_net_host, launches_net_host, _, ms_tile = timed({**net_kw, "batched": 0}, args.steps, args.warmup)
+    ms_net, launches_net, img_net, _ = timed(net_kw, args.steps, args.warmup, spec_net)
+    ms_net_host, launches_net_host, _, ms_tile = timed({**net_kw, "batched": 0}, args.steps, args.warmup, spec_net)
+    ms_net1, _, img_net1, _ = timed(net_kw, args.steps, args.warmup)  # network + batched, no bundles
     ms_plain, launches_plain, img_plain, _ = timed({"batched": 0}, args.steps, args.warmup)
     clk = clocks.stop()
     spec2 = S.RenderSpec(**{**spec.__dict__, "seed": spec.seed + 4099})
@@ -491,18 +494,24 @@ def run_large(args):
             "warmup": args.warmup, "ms_per_step": ms_net, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"large nave {scene.n_triangles} triangles, 96 windows x 400 heterogeneous tiles, "
-                                   f"{cam.width}x{cam.height} {spec.spp}spp 81lambda depth16 RR, network + batched",
+                                   f"{cam.width}x{cam.height} {spec.spp}spp 81lambda depth16 RR, network + batched, "
+                                   f"spectral bundles of {args.bundle}",
                        "paths_per_step": frame_paths, "subdomains": scene.n_subdomains,
                        "l2": "flushed (512 MB write) before every frame; the FP64 film alone is 5.4 GB"},
             "comparison": {"plain": {"value": value_plain, "ms_per_step": ms_plain, "gpu_launches": launches_plain,
                                      "form": "host-driven wavefront, brute-force ray through the tile per tile hit"},
                            "network_batched": {"value": value_net, "ms_per_step": ms_net,
                                                "gpu_launches": launches_net,
-                                               "form": "persistent kernels + CUDA graph, fused tile shading"},
+                                               "form": "persistent kernels + CUDA graph, fused tile shading, "
+                                                       f"spectral bundles of {args.bundle}"},
+                           "network_batched_unbundled": {"value": frame_paths / (ms_net1 / 1e3) / 1e6,
+                                                         "ms_per_step": ms_net1,
+                                                         "image_error_block8": rel_err(block_avg(img_net1, cam), bp)},
                            "network_host_driven": {"value": frame_paths / (ms_net_host / 1e3) / 1e6,
                                                    "ms_per_step": ms_net_host, "gpu_launches": launches_net_host,
                                                    "ms_tile_shading": ms_tile,
-                                                   "form": "host-driven wavefront, fused tile shading"},
+                                                   "form": "host-driven wavefront, fused tile shading, "
+                                                           f"spectral bundles of {args.bundle}"},
                            "speedup": ms_plain / ms_net,
                            "speedup_host_driven_network": ms_plain / ms_net_host,
                            "image_error_block8": rel_err(bn, bp), "noise_floor_block8": rel_err(bp2, bp),

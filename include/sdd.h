@@ -151,8 +151,8 @@ typedef struct {
                               and share one ray while their decisions agree (one traversal for the
                               group); a member whose branch differs continues on its own ray.
                               Each wavelength's chain keeps its distribution; the wavelengths of a
-                              bundle become correlated.  Host-driven form, scenes whose tiles (if
-                              any) are traced by brute force */
+                              bundle become correlated.  Every form; at heterogeneous tiles each
+                              member leaves on its own ray (brute force or network) */
 } sdd_render_opts;
 
 /* Build the scene: validates, partitions the geometry into n_subdomains slabs (Sec. 5:

@@ -613,7 +613,6 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
   if (o->bundle < 0 || o->bundle > kMaxBundle) return fail(SDD_ERR_ARG, "bundle must be in [0, 16]");
   const int B = o->bundle > 1 ? o->bundle : 1;
   if (B > 1 && o->mode != SDD_MODE_MONTE_CARLO) return fail(SDD_ERR_ARG, "spectral bundles need Monte Carlo mode");
-  if (B > 1 && o->use_surrogate) return fail(SDD_ERR_ARG, "spectral bundles do not support use_surrogate");
   const int L = o->n_lambda;
   const int n_bundles = (L + B - 1) / B;
   const long long n_px = o->n_pixels > 0 ? o->n_pixels : img;
@@ -713,10 +712,14 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
     p.use_surrogate = o->use_surrogate ? 1 : 0;
   }
   if (p.use_surrogate) {
-    CK(s->tile_queue.ensure(cap));
+    // one entry per tile hit, with bundles one per member (entries ray << 4 | member)
+    const size_t tcap = cap * (size_t)B;
+    if (B > 1 && cap > (1u << 28)) return fail(SDD_ERR_ARG, "wave too large for spectral bundles with the network");
+    if (tcap > 0x7FFFFFFFu) return fail(SDD_ERR_ARG, "wave too large for the tile queue");
+    CK(s->tile_queue.ensure(tcap));
     p.tile_queue = s->tile_queue.p;
     p.tile_count = &s->d_ctl->tile_hits;
-    p.tile_cap = (int)cap;
+    p.tile_cap = (int)tcap;
     // network transmittance toward the sun per tile material and wavelength
     sdd_surrogate* net = const_cast<sdd_surrogate*>(o->surrogate);
     const int nm = (int)s->tile_mats.size();

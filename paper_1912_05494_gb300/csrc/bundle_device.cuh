@@ -132,7 +132,7 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
   // children: group 0 (members leaving in direction gd0), group 1 (thin-slab transmission:
   // members going straight on) and singles (each member on its own direction).  Origins and
   // the facing normal are recomputed where needed rather than kept live.
-  uint32_t gm[2] = {0u, 0u}, singles = 0u, msh = 0u;
+  uint32_t gm[2] = {0u, 0u}, singles = 0u, msh = 0u, tile_m = 0u;
   uint32_t gf[2] = {0u, 0u};
   float3 gd0 = make_float3(0.f, 0.f, 0.f), dsh = gd0;
   uint32_t path = 0, v = 0, flags = 0, j = 0, lam0 = 0;
@@ -244,6 +244,8 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
           gf[0] = flags | FLAG_SUN_COUNTED;
         } else if (kTM == 1 && kind == MAT_TILE) {
           singles = mask;  // each member traces its own ray through the tile
+        } else if (kTM == 2 && kind == MAT_TILE) {
+          tile_m = mask;  // each member is shaded from the network's prediction for its wavelength
         } else {
           hash_event(hp, mask, EV_ABSORB);
         }
@@ -340,6 +342,17 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
       if (pos >= 0) {
         float* cw = next.w + (size_t)pos * B;
         for (int k = 0; k < B; ++k) cw[k] = k == b ? ts : 0.f;
+      }
+    }
+  }
+  // network form: one tile-queue entry (ray << 4 | member) per member at a tile hit
+  if (kTM == 2 && __any_sync(0xffffffffu, tile_m != 0u)) {
+    for (int b = 0; b < B; ++b) {
+      const bool want = (tile_m >> b) & 1u;
+      const int tpos = warp_append(p.tile_count, 0, want);
+      if (want) {
+        if (tpos < p.tile_cap) p.tile_queue[tpos] = ((uint32_t)r << 4) | (uint32_t)b;
+        else atomicOr(&ctl->error, ERR_QUEUE_OVERFLOW);
       }
     }
   }

@@ -84,6 +84,9 @@ void launch_shade_bundle(const RenderParams& p, const WaveDesc& w, int n_rays, R
   if (tile_mode(p) == 1)
     k_shade_bundle<1><<<blocks_for(n_rays, kBlock), kBlock, 0, st>>>(p, w, n_rays, cur, hits, next, q, q_count, qcap,
                                                                      sb, sq, sq_count, path_L, ctl);
+  else if (tile_mode(p) == 2)
+    k_shade_bundle<2><<<blocks_for(n_rays, kBlock), kBlock, 0, st>>>(p, w, n_rays, cur, hits, next, q, q_count, qcap,
+                                                                     sb, sq, sq_count, path_L, ctl);
   else
     k_shade_bundle<0><<<blocks_for(n_rays, kBlock), kBlock, 0, st>>>(p, w, n_rays, cur, hits, next, q, q_count, qcap,
                                                                      sb, sq, sq_count, path_L, ctl);
@@ -113,6 +116,8 @@ void launch_shadow_bundle(const RenderParams& p, const WaveDesc& w, const Sched&
                           int top_nodes, QueuePair qp, ShadowBuf sb, float* path_L, Control* ctl, cudaStream_t st) {
   if (tile_mode(p) == 1)
     launch_shadow_bundle_m<1>(p, w, sch, total_blocks, block, top_nodes, qp, sb, path_L, ctl, st);
+  else if (tile_mode(p) == 2)
+    launch_shadow_bundle_m<2>(p, w, sch, total_blocks, block, top_nodes, qp, sb, path_L, ctl, st);
   else
     launch_shadow_bundle_m<0>(p, w, sch, total_blocks, block, top_nodes, qp, sb, path_L, ctl, st);
 }

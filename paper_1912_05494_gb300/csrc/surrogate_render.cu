@@ -11,8 +11,8 @@
 // from the persistent kernel's saved queue state.  Shadow rays through a tile use the
 // network's transmittance x the transmitted mixture's mass within 1 degree of straight
 // through toward the sun (sun table), the same ballistic convention as the brute-force form.
+#include "bundle_device.cuh"
 #include "persistent.cuh"
-#include "render_device.cuh"
 #include "surrogate_head.cuh"
 #include "surrogate_net.cuh"
 #include "surrogate_tc.cuh"
@@ -45,21 +45,28 @@ struct TileHit {
   int mat;
   float thr;
   uint2 info;
+  int lam;     // wavelength index
+  int member;  // spectral bundles: the member of the ray's bundle (0 otherwise)
 };
 
+// The tile hit of tile-queue entry e: a ray slot, or with spectral bundles ray << 4 | member.
 __device__ __forceinline__ TileHit tile_hit(const RenderParams& p, const WaveDesc& w, const RayBuf& cur,
-                                            const float2* hits, uint32_t r) {
+                                            const float2* hits, uint32_t e) {
   TileHit h;
+  const bool bund = p.bundle > 1;
+  const uint32_t r = bund ? e >> 4 : e;
+  h.member = bund ? (int)(e & 15u) : 0;
   const float4 O = cur.o[r], D = cur.d[r];
   h.info = cur.info[r];
   const float2 H = hits[r];
-  h.id = path_id(p, w, h.info.x);
+  h.id = bund ? path_id_bundle(p, w, h.info.x) : path_id(p, w, h.info.x);
+  h.lam = bund ? (int)h.id.lam * p.bundle + h.member : (int)h.id.lam;
   const float4 nm = __ldg(p.sc.prim_nrm_mat + __float_as_uint(H.y));
   h.ng = f3(nm);
   h.mat = __float_as_int(nm.w);
   const float3 d = f3(D);
   h.pt = f3(O) + H.x * d;
-  h.thr = D.w;
+  h.thr = bund ? cur.w[(size_t)r * p.bundle + h.member] : D.w;
   float x, y;
   tile_frame(p.tiles.L, h.pt, h.ng, d, &x, &y, &h.dl, &h.t1, &h.t2);
   return h;
@@ -98,18 +105,19 @@ struct TileShadePolicy {
   __device__ void load(const Ctx& c, int row, float qv[net::kIn]) const {
     const TileHit h = tile_hit(p, w, c.cur, hits, p.tile_queue[row]);
     const int tile = __ldg(p.mat_tile + h.mat);
-    const size_t mi = (size_t)h.mat * p.sp.n_lambda + h.id.lam;
+    const size_t mi = (size_t)h.mat * p.sp.n_lambda + h.lam;
     float phi = atan2f(h.dl.y, h.dl.x);
     if (phi < 0.f) phi += 6.283185307179586f;
     qv[0] = -h.dl.z;  // signed: > 0 arrives at the flat front face (the side the normal points to)
     qv[1] = phi;
-    qv[2] = __ldg(p.sp.lambda_nm + h.id.lam);
+    qv[2] = __ldg(p.sp.lambda_nm + h.lam);
     qv[3] = __ldg(p.tiles.d_mean + tile);
     qv[4] = __ldg(p.tiles.rho + tile);
     qv[5] = __ldg(p.sp.mat_n + mi);
     qv[6] = __ldg(p.sp.mat_k + mi);
   }
-  // Threads 0..127 (whole warps) take one row each and append its exit ray.
+  // Threads 0..127 (whole warps) take one row each and append its exit ray (with spectral
+  // bundles a ray of the one member, drawing on the bundle's counter word).
   __device__ void consume(const Ctx& c, int row0, int valid, const float* pred) const {
     if (p.stats >= 2 && threadIdx.x == 0) atomicAdd(&ctl->tile_shaded, (unsigned long long)valid);
     if (threadIdx.x >= kInferRows) return;
@@ -119,14 +127,18 @@ struct TileShadePolicy {
     float3 o0 = make_float3(0.f, 0.f, 0.f), d0 = o0;
     float thr0 = 0.f, s00 = 0.f;
     uint32_t meta0 = 0, path = 0;
+    int member = 0;
+    const bool bund = p.bundle > 1;
     if (active) {
       const TileHit h = tile_hit(p, w, c.cur, hits, p.tile_queue[row0 + i]);
       path = h.info.x;
+      member = h.member;
       const uint32_t depth = h.info.y & 0xFFu, flags = (h.info.y >> 8) & 0xFFu;
       const uint32_t v = depth + 1;
       const float* pr = pred + i * kInferZLd;
       const float T = clamp01(pr[0]), R = clamp01(pr[1]);
-      uint32_t hsh = p.path_hash ? p.path_hash[path] : 0u;
+      uint32_t* hp = p.path_hash ? p.path_hash + (bund ? (size_t)path * p.bundle + member : (size_t)path) : nullptr;
+      uint32_t hsh = hp ? *hp : 0u;
       const float4 u = draw4(h.id.pixel, h.id.sample, v, STREAM_TILE, 0, h.id.lam, p.seed);
       const float4 up = draw4(h.id.pixel, h.id.sample, v, STREAM_PATH, 0, h.id.lam, p.seed);
       const float tot = T + R;
@@ -144,7 +156,7 @@ struct TileShadePolicy {
         const uint32_t fl = (!refl && ballistic) ? flags : (flags & ~FLAG_SUN_COUNTED);
         e0 = true;
         d0 = normalize3(dir.x * h.t1 + dir.y * h.t2 + dir.z * h.ng);
-        meta0 = v | (fl << 8);
+        meta0 = v | (fl << 8) | (bund ? (1u << member) << 16 : 0u);
         if ((int)v >= p.rr_start) {
           const float qs = fminf(0.95f, thr);
           if (up.w >= qs) {
@@ -162,9 +174,18 @@ struct TileShadePolicy {
       } else {
         hsh = fnv_byte(hsh, EV_ABSORB);
       }
-      if (p.path_hash) p.path_hash[path] = hsh;
+      if (hp) *hp = hsh;
     }
-    emit_ray(e0, p.sc, c.next, c.next_count, c.q, c.q_count, qcap, o0, s00, d0, thr0, path, meta0, ctl);
+    if (bund) {
+      const int pos = emit_bundle_ray(e0, p.sc, c.next, c.next_count, c.q, c.q_count, qcap, o0, s00, d0, path, meta0,
+                                      ctl);
+      if (pos >= 0) {
+        float* cw = c.next.w + (size_t)pos * p.bundle;
+        for (int k = 0; k < p.bundle; ++k) cw[k] = k == member ? thr0 : 0.f;
+      }
+    } else {
+      emit_ray(e0, p.sc, c.next, c.next_count, c.q, c.q_count, qcap, o0, s00, d0, thr0, path, meta0, ctl);
+    }
   }
   __device__ uint32_t* err(const Ctx&) const { return &ctl->error; }
 };

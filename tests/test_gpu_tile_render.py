@@ -159,3 +159,43 @@ def test_batched_form_is_bit_identical_with_tiles(sdd, trained, use_net):
     assert st["launches_persistent"] >= 1
     if use_net:
         assert st["launches_tile"] > 0
+
+
+@pytest.mark.parametrize("use_net", [False, True])
+def test_bundled_batched_form_is_bit_identical_with_tiles(sdd, trained, use_net):
+    """Spectral bundles of 8 through heterogeneous tiles: every member leaves a tile on its own
+    ray (its own brute-force trace, or its own network prediction).  With the network the
+    batched form equals the host-driven one bit for bit (the tile shading is one kernel for
+    both).  The brute-force tile tracer is inlined into differently register-bounded kernels
+    in the two forms, and the compiler may then contract its arithmetic differently, so there
+    the paths agree up to float rounding: at most 0.1 % of branch decisions flip."""
+    net = trained[0] if use_net else None
+    sc, cam, spec = S.tile_room_scene(width=40, height=24, spp=4)
+    spec = S.RenderSpec(**{**spec.__dict__, "bundle": 8})
+    h = sdd.SceneHandle(sc)
+    kw = {"use_surrogate": 1, "surrogate": net} if use_net else {}
+    a, pa, ha = render(sdd, h, cam, spec, paths=True, **kw)
+    b, pb, hb = render(sdd, h, cam, spec, paths=True, batched=1, **kw)
+    if use_net:
+        assert np.array_equal(a, b) and np.array_equal(ha, hb)
+    else:
+        flips = float(np.mean(ha != hb))
+        assert flips <= 1e-3, flips
+        assert rel_err(a, b) <= 1e-3, rel_err(a, b)
+
+
+def test_bundled_network_form_matches_brute_force(sdd, trained):
+    """Sky-lit room as in the gain test, with bundles of 9 in the network form against the
+    unbundled brute-force image: block averages within 3 %, like the unbundled network form.
+    The wavelengths of a bundle share their draws, so its noise is correlated across the
+    spectrum and the wavelength-summed blocks are noisier at equal spp: the bundled render
+    takes 256 spp to the reference's 128."""
+    net, _, _ = trained
+    sc, cam, spec = S.tile_room_scene(width=96, height=64, spp=128)
+    sc.sun = np.zeros_like(sc.sun)
+    h = sdd.SceneHandle(sc)
+    bf = render(sdd, h, cam, spec)
+    net_img = render(sdd, h, cam, S.RenderSpec(**{**spec.__dict__, "bundle": 9, "spp": 256}), use_surrogate=1,
+                     surrogate=net, batched=1)
+    e_net = rel_err(blocks(net_img, cam), blocks(bf, cam))
+    assert e_net < 0.03, e_net
