@@ -6,8 +6,9 @@ Workload (one step = one frame): the procedural nave (60 x 12 x 20 m, 24 lancet 
 roulette, 8 subdomains along the nave.  One frame is 1024*768*16*81 = 1,019,215,872
 spectral samples (one (pixel, sample, wavelength) path each).  Default form: spectral bundles
 of 14 wavelengths (one ray serves a bundle's chains while their branches agree; --bundle 1
-traces every wavelength on its own) in the batched form (one persistent launch per wave,
-frames replayed as a CUDA graph; --batched 0 for the host-driven wavefront).
+traces every wavelength on its own) in the graph form (--batched 2: fixed-grid kernels that
+read their queue counts on the device, the passes in conditional loops of one CUDA graph per
+frame; --batched 1 runs one persistent kernel per wave, --batched 0 the host-driven wavefront).
 
 Printed JSON line (rank 0):
   value      Mspectral-samples/s of the device-resident frame (scene built, outputs allocated
@@ -57,7 +58,10 @@ WORKLOAD = "nave-200k {w}x{h} {spp}spp 81lambda depth12 RR S={s} (Monte Carlo, s
 TRAVERSE_SOURCES = ["paper_1912_05494_gb300/csrc/render_kernels.cu", "paper_1912_05494_gb300/csrc/render_device.cuh",
                     "paper_1912_05494_gb300/csrc/device_math.cuh", "paper_1912_05494_gb300/csrc/sdd_internal.h"]
 NCU_SUMMARY = os.path.join(ROOT, "profiles", "traverse_nave_ncu.md")
-FORMS = {0: "host-driven", 1: "batched: persistent kernel + CUDA graph"}
+FORMS = {0: "host-driven", 1: "batched: persistent kernel + CUDA graph",
+         2: "graph form: fixed-grid kernels reading device counts, CUDA graph"}
+TRAVERSE_KERNEL = {0: "k_traverse (closest hit)", 1: "k_persistent_wave (all steps of a wave)",
+                   2: "k_traverse_g (closest hit, device-read counts)"}
 
 
 def dist_env():
@@ -303,13 +307,16 @@ def run_gpu(args):
     cnt = sdd.sdd_get_stats(h.h)
     trav_bytes = cnt["node_visits"] * 64 + cnt["tri_tests"] * 48 + cnt["rays_closest"] * 44
     trav_launches = max(cnt["launches_traverse"], 1)
-    if args.batched:  # one persistent launch per wave carries both traversals
+    persistent = args.batched == 1
+    if persistent:  # one persistent launch per wave carries both traversals
         trav_bytes += cnt["shadow_node_visits"] * 64 + cnt["shadow_tri_tests"] * 48 + cnt["rays_shadow"] * 44
         trav_launches = max(cnt["launches_persistent"], 1)
 
     # timed region: K frames, L2 flushed before each, per-launch CUDA events in the library
     flush = torch.empty(512 * 1024 * 1024 // 4, device="cuda", dtype=torch.float32)  # 512 MB > L2
     sdd.sdd_set_profiling(h.h, 1)
+    # the profiling level is part of a captured frame: one untimed frame captures it again
+    sdd.sdd_render(h.h, cam, spec, out, xyz, **kw)
     clocks = ClockSampler(local)
     clocks.start()
     if dist is not None:
@@ -324,8 +331,8 @@ def run_gpu(args):
         flush.zero_()
         sdd.sdd_render(h.h, cam, spec, out, xyz, **kw)
         st = sdd.sdd_get_stats(h.h)
-        ms_trav += st["ms_traverse"] if not args.batched else st["ms_persistent"]
-        n_trav += st["launches_traverse"] if not args.batched else st["launches_persistent"]
+        ms_trav += st["ms_traverse"] if not persistent else st["ms_persistent"]
+        n_trav += st["launches_traverse"] if not persistent else st["launches_persistent"]
         launches += st["launches_total"] + 1
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -350,8 +357,8 @@ def run_gpu(args):
     bytes_per_launch = trav_bytes / trav_launches
     achieved = bytes_per_launch / (avg_launch_ms / 1e3) / 1e9 if avg_launch_ms > 0 else 0.0
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic if not args.batched else None, "peak_kind": peak_kind,
-                "kernel": "k_persistent_wave (all steps of a wave)" if args.batched else "k_traverse (closest hit)",
+                "traffic": traffic if not persistent else None, "peak_kind": peak_kind,
+                "kernel": TRAVERSE_KERNEL[args.batched],
                 "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_ms,
                 "note": "algorithmic bytes = BVH nodes x 64 B + triangle records x 48 B + 44 B ray state per "
                         "subdomain visit; the ~35 MB BVH is L2-resident, so frac can exceed what DRAM moves"}
@@ -448,10 +455,10 @@ def run_large(args):
     stream = torch.cuda.current_stream()
 
     def timed(kw, steps, warmup, spec=spec):
+        sdd.sdd_set_profiling(h.h, 1)  # before the warm-up: captured frames include the timing events
         for _ in range(warmup):
             sdd.sdd_render(h.h, cam, spec, out, xyz, **kw)
         torch.cuda.synchronize()
-        sdd.sdd_set_profiling(h.h, 1)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         launches = 0
         ms_tile = 0.0
@@ -599,7 +606,8 @@ def main(argv=None):
     ap.add_argument("--spp", type=int, default=16)
     ap.add_argument("--subdomains", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--batched", type=int, default=1, help="1: persistent kernels + CUDA graph; 0: host-driven")
+    ap.add_argument("--batched", type=int, default=2, choices=[0, 1, 2],
+                    help="0: host-driven; 1: persistent kernels + CUDA graph; 2: graph form")
     ap.add_argument("--bundle", type=int, default=14,
                     help="nave workload: wavelengths per spectral bundle (1 = every wavelength its own path)")
     ap.add_argument("--workload", choices=["nave", "large", "network"], default="nave")

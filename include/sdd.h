@@ -134,8 +134,12 @@ typedef struct {
                               read back between launches); 1: a persistent cooperative kernel
                               drains every pass on the device -- the whole wave in one launch, or
                               with use_surrogate two launches per generation around the fused
-                              tile shading -- and the frame is captured as a CUDA graph and
-                              replayed while its parameters and buffers are unchanged */
+                              tile shading; 2: the graph form -- the host-driven steps as
+                              fixed-grid kernels that read their queue counts on the device, a
+                              fixed sequence per generation (n_subdomains + 1 closest-hit passes,
+                              shading, n_subdomains + 1 shadow passes; empty launches return at
+                              once).  Forms 1 and 2 capture the frame as a CUDA graph and replay
+                              it while its parameters and buffers are unchanged */
   int n_pixels;            /* 0: whole image; else render only these pixel indices */
   const int32_t* pixels;   /* host [n_pixels] row-major pixel indices (y * width + x) */
   int wave_paths;          /* paths per wave; 0 = automatic */

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "../../include/sdd.h"
+#include "graph_form.h"
 #include "persistent.cuh"
 #include "render_kernels.cuh"
 #include "scene_build.h"
@@ -138,7 +139,10 @@ struct sdd_scene {
   cudaStream_t gstream = nullptr;
   cudaEvent_t gevent = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
+  cudaStream_t bstream = nullptr;  // graph form: captures the bodies of the pass loops
   std::vector<unsigned char> graph_key;
+  std::vector<std::pair<int, int>> graph_ev;  // graph form: (kind, event pair) recorded in the graph
+  int64_t graph_launches[TK_COUNT] = {};       // graph form: launches per frame by kind
   cudaEvent_t pev[2] = {nullptr, nullptr};
   // profiling
   int profiling = 0;
@@ -168,6 +172,7 @@ struct sdd_scene {
     for (auto e : pev)
       if (e) cudaEventDestroy(e);
     if (gstream) cudaStreamDestroy(gstream);
+    if (bstream) cudaStreamDestroy(bstream);
     if (d_ctl) cudaFree(d_ctl);
     if (h_ctl) cudaFreeHost(h_ctl);
     for (auto e : ev_pool) cudaEventDestroy(e);
@@ -185,12 +190,20 @@ struct sdd_scene {
     }
     int idx = (int)ev_next;
     ev_next += 2;
-    cudaEventRecord(ev_pool[idx], st);
+    record(ev_pool[idx], st);
     ev_used.push_back({kind, idx});
     return idx;
   }
   void ev_end(int idx, cudaStream_t st) {
-    if (idx >= 0) cudaEventRecord(ev_pool[idx + 1], st);
+    if (idx >= 0) record(ev_pool[idx + 1], st);
+  }
+  // In a stream capture a plain event record only orders captured work; an external record
+  // becomes an event node of the graph that records at every replay.
+  static void record(cudaEvent_t e, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else cudaEventRecord(e, st);
   }
   // Called after a stream sync: fold every recorded pair into the stats.
   void ev_collect() {
@@ -428,18 +441,126 @@ sdd_status ensure_workspace(sdd_scene* s, size_t cap, size_t paths, int n_slots,
 // Enqueue the whole frame of the batched form on stream `gs`: per wave, clear the wave's
 // bookkeeping and path radiance, one persistent cooperative launch, film accumulation; then
 // the final film resolve.
+// The closest-hit (shadow = false) or shadow passes of one generation of the graph form,
+// until its queues drain.  In a graph capture: a conditional 'while' node whose body runs two
+// passes (queue buffer 0 to 1, then 1 to 0) and the loop condition, which reads the counts on
+// the device (at most n_sub / 2 + 2 iterations; a ray crosses each slab at most once).
+// Enqueued directly: n_sub + 1 passes and a drain check.  Timed as a whole.
+sdd_status graph_passes(sdd_scene* s, const RenderParams& p, const GraphGrids& gg, const WaveDesc& w,
+                        const PersistBuffers& b, int cur, bool shadow, cudaStream_t gs, int64_t* cnt) {
+  Control* c = s->d_ctl;
+  const int nsub = p.sc.n_sub, qcap = b.qcap;
+  int(*counts)[kMaxSubdomains] = shadow ? c->sq_count : c->q_count;
+  uint32_t* const* qs = shadow ? b.sq : b.q;
+  auto pass = [&](int a, cudaStream_t st) -> sdd_status {
+    CK(cudaMemsetAsync(counts[1 - a], 0, sizeof(int) * kMaxSubdomains, st));
+    QueuePair qp{qs[a], qs[1 - a], counts[1 - a], qcap};
+    if (shadow) CK(launch_shadow_g(p, gg, w, counts[a], qp, b.sb, b.path_L, c, st));
+    else CK(launch_traverse_g(p, gg, counts[a], qp, b.rb[cur], b.hits, c, st));
+    return SDD_OK;
+  };
+  const int kind = shadow ? TK_SHADOW : TK_TRAVERSE;
+  int ev = s->ev_begin(kind, gs);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(gs, &cs));
+  if (cs == cudaStreamCaptureStatusActive) {
+    CK(cudaMemsetAsync(&c->loop_iter, 0, sizeof(int), gs));
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edges = nullptr;
+    size_t nd = 0;
+    CK(cudaStreamGetCaptureInfo(gs, &cs, nullptr, &g, &deps, &edges, &nd));
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, deps, edges, nd, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    CK(cudaStreamUpdateCaptureDependencies(gs, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    CK(cudaStreamBeginCaptureToGraph(s->bstream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    sdd_status r = pass(0, s->bstream);
+    if (r == SDD_OK) r = pass(1, s->bstream);
+    if (r == SDD_OK) launch_loop_cond(h, counts[0], nsub, nsub / 2 + 2, shadow ? 1 : 0, c, s->bstream);
+    cudaGraph_t out = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s->bstream, &out);
+    if (r != SDD_OK) return r;
+    CK(e);
+  } else {
+    for (int i = 0, a = 0; i <= nsub; ++i, a = 1 - a) {
+      sdd_status r = pass(a, gs);
+      if (r != SDD_OK) return r;
+      cnt[kind]++;
+    }
+    launch_check_drained(counts[(nsub + 1) & 1], nsub, c, gs);
+  }
+  s->ev_end(ev, gs);
+  CK(cudaGetLastError());
+  return SDD_OK;
+}
+
+// One wave of the graph form (graph_kernels.cu): raygen, then per generation the closest-hit
+// passes, shading (and the fused tile shading) and the shadow passes, every launch with a
+// fixed grid that reads its counts on the device.  Counts host-known launches into cnt.
+sdd_status enqueue_graph_wave(sdd_scene* s, const RenderParams& p, const WaveDesc& w, const PersistBuffers& b,
+                              const GraphGrids& gg, const sdd_render_opts* o, cudaStream_t gs, int64_t* cnt) {
+  Control* c = s->d_ctl;
+  const int qcap = b.qcap;
+  int ev = s->ev_begin(TK_RAYGEN, gs);
+  launch_raygen(p, w, b.rb[0], b.q[0], c->q_count[0], qcap, c, gs);
+  launch_set_int(&c->gen_rays[0], (int)w.n_paths, gs);
+  s->ev_end(ev, gs);
+  CK(cudaGetLastError());
+  cnt[TK_RAYGEN] += 2;
+  int cur = 0;
+  for (int g = 0; g <= p.max_depth + 1; ++g) {
+    sdd_status r = graph_passes(s, p, gg, w, b, cur, false, gs, cnt);
+    if (r != SDD_OK) return r;
+    // shading refills q[0] and sq[0] from cleared counts
+    CK(cudaMemsetAsync(c, 0, offsetof(Control, error), gs));
+    CK(cudaMemsetAsync(&c->gen_rays[(g + 1) & 1], 0, sizeof(int), gs));
+    if (p.use_surrogate) CK(cudaMemsetAsync(&c->tile_hits, 0, sizeof(int), gs));
+    ev = s->ev_begin(TK_SHADE, gs);
+    CK(launch_shade_g(p, gg, w, &c->gen_rays[g & 1], b.rb[cur], b.hits, b.rb[1 - cur], &c->gen_rays[(g + 1) & 1],
+                      b.q[0], c->q_count[0], qcap, b.sb, b.sq[0], c->sq_count[0], b.path_L, c, gs));
+    s->ev_end(ev, gs);
+    cnt[TK_SHADE]++;
+    if (p.use_surrogate) {
+      ev = s->ev_begin(TK_TILE, gs);
+      CK(launch_tile_shade(p, w, b.rb[cur], b.hits, b.rb[1 - cur], &c->gen_rays[(g + 1) & 1], b.q[0],
+                           c->q_count[0], qcap, c, o->surrogate, gs));
+      s->ev_end(ev, gs);
+      cnt[TK_TILE]++;
+    }
+    r = graph_passes(s, p, gg, w, b, cur, true, gs, cnt);
+    if (r != SDD_OK) return r;
+    cur = 1 - cur;
+  }
+  return SDD_OK;
+}
+
 sdd_status enqueue_batched_frame(sdd_scene* s, const RenderParams& p, const std::vector<WaveDesc>& waves,
-                                 const PersistBuffers& b, int n_slots, int grid, const sdd_render_opts* o,
-                                 float* spectral_out, float* xyz_out, cudaStream_t gs) {
+                                 const PersistBuffers& b, int n_slots, int grid, const GraphGrids& gg,
+                                 const sdd_render_opts* o, float* spectral_out, float* xyz_out, cudaStream_t gs,
+                                 int64_t* cnt) {
   CK(cudaMemsetAsync(s->d_ctl, 0, sizeof(Control), gs));
   CK(cudaMemsetAsync(s->film.p, 0, sizeof(double) * (size_t)p.n_px * p.sp.n_lambda, gs));
   for (const WaveDesc& w : waves) {
-    CK(cudaMemsetAsync(s->d_pc, 0, sizeof(PersistCtl), gs));
     CK(cudaMemsetAsync(s->path_L.p, 0, sizeof(float) * (size_t)w.n_paths * n_slots, gs));
-    if (!p.use_surrogate) {
+    if (o->batched == 2) {
+      // queue counts of the wave; the error word keeps what earlier waves raised
+      CK(cudaMemsetAsync(s->d_ctl, 0, offsetof(Control, error), gs));
+      sdd_status r = enqueue_graph_wave(s, p, w, b, gg, o, gs, cnt);
+      if (r) return r;
+    } else if (!p.use_surrogate) {
+      CK(cudaMemsetAsync(s->d_pc, 0, sizeof(PersistCtl), gs));
       CK(launch_persistent_wave(p, w, b, s->d_pc, s->d_ctl, grid, gs, SEG_WAVE));
     } else {
       // the network runs between shading and the shadow rays of every generation
+      CK(cudaMemsetAsync(s->d_pc, 0, sizeof(PersistCtl), gs));
       CK(launch_persistent_wave(p, w, b, s->d_pc, s->d_ctl, grid, gs, SEG_RAYGEN));
       for (int g = 0; g <= p.max_depth + 1; ++g) {
         CK(cudaMemsetAsync(&s->d_ctl->tile_hits, 0, sizeof(int), gs));
@@ -448,11 +569,15 @@ sdd_status enqueue_batched_frame(sdd_scene* s, const RenderParams& p, const std:
         CK(launch_persistent_wave(p, w, b, s->d_pc, s->d_ctl, grid, gs, SEG_SHADOW));
       }
     }
+    int ev = o->batched == 2 ? s->ev_begin(TK_FILM, gs) : -1;
     launch_film_accum(p, w, s->path_L.p, s->film.p, o->path_radiance_out, o->path_hash_out, gs);
+    s->ev_end(ev, gs);
     CK(cudaGetLastError());
+    cnt[TK_FILM]++;
   }
   launch_film_finalize(p, s->film.p, s->cmf_w.p, spectral_out, xyz_out, gs);
   CK(cudaGetLastError());
+  cnt[TK_FILM]++;
   return SDD_OK;
 }
 
@@ -463,13 +588,21 @@ sdd_status render_batched(sdd_scene* s, const RenderParams& p, const std::vector
                           int qcap, const sdd_render_opts* o, float* spectral_out, float* xyz_out, cudaStream_t st) {
   if (!s->gstream) {
     CK(cudaStreamCreateWithFlags(&s->gstream, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&s->bstream, cudaStreamNonBlocking));
     CK(cudaEventCreateWithFlags(&s->gevent, cudaEventDisableTiming));
     CK(cudaEventCreate(&s->pev[0]));
     CK(cudaEventCreate(&s->pev[1]));
   }
   if (!s->d_pc) CK(cudaMalloc(&s->d_pc, sizeof(PersistCtl)));
-  const int grid = persistent_grid(p.stats >= 2, tile_mode(p), p.bundle > 1);
-  if (grid <= 0) return fail(SDD_ERR_CUDA, "persistent kernel does not fit on this device");
+  const int form = o->batched;  // 1 persistent kernel, 2 graph form
+  int grid = 0;
+  GraphGrids gg{};
+  if (form == 2) {
+    gg = graph_grids(p);  // occupancy queries stay outside the capture
+  } else {
+    grid = persistent_grid(p.stats >= 2, tile_mode(p), p.bundle > 1);
+    if (grid <= 0) return fail(SDD_ERR_CUDA, "persistent kernel does not fit on this device");
+  }
   PersistBuffers b;
   for (int i = 0; i < 2; ++i) {
     b.rb[i] = RayBuf{s->rb_o[i].p, s->rb_d[i].p, s->rb_info[i].p, qcap, s->rb_w[i].p};
@@ -489,6 +622,8 @@ sdd_status render_batched(sdd_scene* s, const RenderParams& p, const std::vector
   put(&p, sizeof(p));
   put(&b, sizeof(b));
   put(&grid, sizeof(grid));
+  put(&gg, sizeof(gg));
+  put(&form, sizeof(form));
   put(&n_slots, sizeof(n_slots));
   for (const WaveDesc& w : waves) put(&w, sizeof(w));
   const void* ptrs[] = {spectral_out, xyz_out, o->path_radiance_out, o->path_hash_out, s->film.p, s->cmf_w.p,
@@ -498,7 +633,7 @@ sdd_status render_batched(sdd_scene* s, const RenderParams& p, const std::vector
   CK(cudaEventRecord(s->gevent, st));
   CK(cudaStreamWaitEvent(s->gstream, s->gevent, 0));
   if (s->profiling >= 1) CK(cudaEventRecord(s->pev[0], s->gstream));
-  bool replay = s->graph_exec && key == s->graph_key;
+  bool replay = !s->tuning.no_graph && s->graph_exec && key == s->graph_key;
   if (!replay) {
     if (s->graph_exec) {
       cudaGraphExecDestroy(s->graph_exec);
@@ -507,13 +642,19 @@ sdd_status render_batched(sdd_scene* s, const RenderParams& p, const std::vector
     }
     cudaGraph_t graph = nullptr;
     bool captured = false;
+    int64_t cnt[TK_COUNT] = {};
+    s->ev_used.clear();
+    s->ev_next = 0;
     if (!s->tuning.no_graph && cudaStreamBeginCapture(s->gstream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-      sdd_status r = enqueue_batched_frame(s, p, waves, b, n_slots, grid, o, spectral_out, xyz_out, s->gstream);
+      sdd_status r = enqueue_batched_frame(s, p, waves, b, n_slots, grid, gg, o, spectral_out, xyz_out, s->gstream,
+                                           cnt);
       cudaError_t ec = cudaStreamEndCapture(s->gstream, &graph);
       if (r == SDD_OK && ec == cudaSuccess && graph &&
           cudaGraphInstantiate(&s->graph_exec, graph, 0) == cudaSuccess) {
         captured = true;
         s->graph_key = key;
+        s->graph_ev = s->ev_used;  // event nodes of the graph, re-recorded at every replay
+        for (int k = 0; k < TK_COUNT; ++k) s->graph_launches[k] = cnt[k];
       }
       if (graph) cudaGraphDestroy(graph);
       cudaGetLastError();  // a failed capture leaves a sticky-free error; clear it
@@ -521,8 +662,14 @@ sdd_status render_batched(sdd_scene* s, const RenderParams& p, const std::vector
     if (!captured) {
       // capture not available: enqueue the same frame directly
       s->graph_exec = nullptr;
-      sdd_status r = enqueue_batched_frame(s, p, waves, b, n_slots, grid, o, spectral_out, xyz_out, s->gstream);
+      s->ev_used.clear();
+      s->ev_next = 0;
+      for (int k = 0; k < TK_COUNT; ++k) cnt[k] = 0;
+      sdd_status r = enqueue_batched_frame(s, p, waves, b, n_slots, grid, gg, o, spectral_out, xyz_out, s->gstream,
+                                           cnt);
       if (r) return r;
+      s->graph_ev.clear();
+      for (int k = 0; k < TK_COUNT; ++k) s->graph_launches[k] = cnt[k];
     }
   }
   if (s->graph_exec) {
@@ -531,6 +678,22 @@ sdd_status render_batched(sdd_scene* s, const RenderParams& p, const std::vector
   }
   if (s->profiling >= 1) CK(cudaEventRecord(s->pev[1], s->gstream));
   CK(cudaStreamSynchronize(s->gstream));
+  if (form == 2) {
+    if (s->graph_exec) s->ev_used = s->graph_ev;
+    s->ev_collect();
+    int64_t* dst[TK_COUNT] = {&s->stats.launches_raygen, &s->stats.launches_traverse, &s->stats.launches_shade,
+                              &s->stats.launches_shadow, &s->stats.launches_film, &s->stats.launches_tile};
+    for (int k = 0; k < TK_COUNT; ++k) {
+      *dst[k] += s->graph_launches[k];
+      s->stats.launches_total += s->graph_launches[k];
+    }
+    if (s->profiling >= 1) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, s->pev[0], s->pev[1]);
+      s->stats.ms_persistent = ms;
+    }
+    return SDD_OK;
+  }
   const int64_t per_wave = p.use_surrogate ? 1 + 2 * (int64_t)(p.max_depth + 2) : 1;
   s->stats.launches_persistent += per_wave * (int64_t)waves.size();
   if (p.use_surrogate) s->stats.launches_tile += (int64_t)(p.max_depth + 2) * (int64_t)waves.size();
@@ -610,6 +773,7 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
   const long long img = (long long)cam->width * cam->height;
   for (int i = 0; i < o->n_pixels; ++i)
     if (o->pixels[i] < 0 || o->pixels[i] >= img) return fail(SDD_ERR_ARG, "pixel index out of range");
+  if (o->batched < 0 || o->batched > 2) return fail(SDD_ERR_ARG, "batched must be 0, 1 or 2");
   if (o->bundle < 0 || o->bundle > kMaxBundle) return fail(SDD_ERR_ARG, "bundle must be in [0, 16]");
   const int B = o->bundle > 1 ? o->bundle : 1;
   if (B > 1 && o->mode != SDD_MODE_MONTE_CARLO) return fail(SDD_ERR_ARG, "spectral bundles need Monte Carlo mode");
@@ -771,6 +935,11 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
       s->stats.waves++;
       s->stats.paths += spectral_paths(p, w);
     }
+    // graph form: passes run by the conditional loops, and their condition launches
+    const int64_t gp0 = (int64_t)s->h_ctl->graph_passes[0], gp1 = (int64_t)s->h_ctl->graph_passes[1];
+    s->stats.launches_traverse += gp0;
+    s->stats.launches_shadow += gp1;
+    s->stats.launches_total += gp0 + gp1 + (gp0 + gp1) / 2;
     s->stats.node_visits = (int64_t)s->h_ctl->node_visits;
     s->stats.tri_tests = (int64_t)s->h_ctl->tri_tests;
     s->stats.shadow_node_visits = (int64_t)s->h_ctl->shadow_node_visits;

@@ -1,0 +1,195 @@
+// graph_kernels.cu -- kernels of the graph form of the wavefront.
+//
+// The host-driven form sizes every traversal launch from queue counts it reads back, one
+// round trip per subdomain pass; the persistent form removes the round trips but runs every
+// step at the one occupancy its register budget allows.  The graph form keeps one kernel per
+// step, each at its own occupancy, and reads the counts on the device instead: every launch
+// has a fixed grid (SMs x resident blocks) that strides over subdomain-aligned 128-ray chunks
+// of the queues (traversal) or over the generation's rays (shading).  A generation is the
+// closest-hit passes, shading, the shadow passes; the passes run in conditional 'while' nodes
+// of the frame's CUDA graph whose condition kernel (k_loop_cond) reads the queue counts, so a
+// whole frame is captured once and replayed with no host round trip and no empty passes
+// beyond the second of a loop iteration (a ray crosses each slab at most once, Sec. 5
+// hand-off, which bounds the iterations).  The per-ray work is the same device code as the
+// other forms (render_device.cuh, bundle_device.cuh).
+#include "bundle_device.cuh"
+#include "chunk_sched.cuh"
+#include "graph_form.h"
+
+#include <mutex>
+#include <unordered_map>
+
+namespace sdd {
+
+namespace {
+
+// Closest-hit pass over the queues whose counts are counts_in.
+template <bool kStats>
+__global__ void __launch_bounds__(kChunk, 12) k_traverse_g(RenderParams p, const int* counts_in, QueuePair qp,
+                                                           RayBuf rb, float2* hits, Control* ctl) {
+  __shared__ int s_prefix[kMaxSubdomains + 1];
+  __shared__ int s_count[kMaxSubdomains];
+  const int n_sub = p.sc.n_sub;
+  const int total = load_prefix(counts_in, n_sub, qp.cap, s_prefix, s_count);
+  for (int c0 = blockIdx.x * kChunk; c0 < total; c0 += gridDim.x * kChunk) {
+    const int s = find_subdomain(s_prefix, n_sub, c0);  // the whole chunk's subdomain
+    const int i = c0 - s_prefix[s] + (int)threadIdx.x;
+    dev_traverse_warp<kStats>(p, s, i, i < s_count[s], nullptr, 0, qp, rb, hits, ctl);
+  }
+}
+
+// Shading of the generation's *n_in rays (children counted in *next_count).
+template <int kTM, bool kBund>
+__global__ void __launch_bounds__(kBlock) k_shade_g(RenderParams p, WaveDesc w, const int* n_in, RayBuf cur,
+                                                    const float2* __restrict__ hits, RayBuf next, int* next_count,
+                                                    uint32_t* q, int* q_count, int qcap, ShadowBuf sb, uint32_t* sq,
+                                                    int* sq_count, float* path_L, Control* ctl) {
+  // a count above the capacity was already reported by the append that overflowed
+  const int n = min(*(volatile const int*)n_in, qcap);
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const int r = base + (int)threadIdx.x;
+    if constexpr (kBund) {
+      dev_shade_bundle<kTM>(p, w, r, r < n, cur, hits, next, next_count, q, q_count, qcap, sb, &ctl->next_shadow, sq,
+                            sq_count, path_L, ctl);
+    } else {
+      dev_shade<kTM>(p, w, r, r < n, cur, hits, next, next_count, q, q_count, qcap, sb, &ctl->next_shadow, sq,
+                     sq_count, path_L, ctl);
+    }
+  }
+}
+
+// Shadow pass over the queues whose counts are counts_in (walk choice as in the other forms).
+template <bool kStats, int kTM, bool kBund>
+__global__ void __launch_bounds__(kChunk, kTM == 1 ? 1 : 8) k_shadow_g(RenderParams p, WaveDesc w,
+                                                                      const int* counts_in, QueuePair qp,
+                                                                      ShadowBuf sb, float* path_L, Control* ctl) {
+  __shared__ int s_prefix[kMaxSubdomains + 1];
+  __shared__ int s_count[kMaxSubdomains];
+  const int n_sub = p.sc.n_sub;
+  const int total = load_prefix(counts_in, n_sub, qp.cap, s_prefix, s_count);
+  for (int c0 = blockIdx.x * kChunk; c0 < total; c0 += gridDim.x * kChunk) {
+    const int s = find_subdomain(s_prefix, n_sub, c0);
+    const int i = c0 - s_prefix[s] + (int)threadIdx.x;
+    const bool act = i < s_count[s];
+    if constexpr (kBund) {
+      dev_shadow_bundle<kStats, kTM, kTM == 1>(p, w, s, i, act, nullptr, 0, qp, sb, path_L, ctl);
+    } else if constexpr (kTM == 1) {
+      dev_shadow_warp<kStats, kTM>(p, w, s, i, act, nullptr, 0, qp, sb, path_L, ctl);
+    } else {
+      dev_shadow<kStats, kTM>(p, w, s, i, act, nullptr, 0, qp, sb, path_L, ctl);
+    }
+  }
+}
+
+__global__ void k_set_int(int* dst, int v) { *dst = v; }
+
+// Condition of a pass loop (a conditional 'while' node whose body runs two passes): go on
+// while rays remain in the queues the second pass wrote, for at most max_iter iterations
+// (then the timeout bit).  kind 0 counts closest-hit passes, 1 shadow passes.
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, const int* counts, int n_sub, int max_iter, int kind,
+                            Control* ctl) {
+  int any = 0;
+  for (int s = 0; s < n_sub; ++s) any |= counts[s] > 0;
+  const int it = ++ctl->loop_iter;
+  ctl->graph_passes[kind] += 2;
+  if (any && it >= max_iter) atomicOr(&ctl->error, ERR_TIMEOUT);
+  cudaGraphSetConditional(h, (any && it < max_iter) ? 1u : 0u);
+}
+
+// Rays left in a queue after the last pass of a generation: raise the timeout bit.
+__global__ void k_check_drained(const int* counts, int n_sub, Control* ctl) {
+  const int s = threadIdx.x;
+  if (s < n_sub && counts[s] > 0) atomicOr(&ctl->error, ERR_TIMEOUT);
+}
+
+// Resident blocks x SMs of a kernel, queried once per kernel.
+int grid_of(const void* fn, int block) {
+  static std::mutex m;
+  static std::unordered_map<const void*, int> cache;
+  std::lock_guard<std::mutex> lk(m);
+  auto it = cache.find(fn);
+  if (it != cache.end()) return it->second;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, 0);
+  const int g = std::max(1, sms * per_sm);
+  cache[fn] = g;
+  return g;
+}
+
+// The kernel of each step for a render's parameters.
+const void* traverse_fn(const RenderParams& p) {
+  return p.stats >= 2 ? (const void*)k_traverse_g<true> : (const void*)k_traverse_g<false>;
+}
+
+template <int kTM>
+const void* shade_fn_t(bool b) {
+  return b ? (const void*)k_shade_g<kTM, true> : (const void*)k_shade_g<kTM, false>;
+}
+const void* shade_fn(const RenderParams& p) {
+  const bool b = p.bundle > 1;
+  switch (tile_mode(p)) {
+    case 1: return shade_fn_t<1>(b);
+    case 2: return shade_fn_t<2>(b);
+    default: return shade_fn_t<0>(b);
+  }
+}
+
+template <bool kStats, int kTM>
+const void* shadow_fn_t(bool b) {
+  return b ? (const void*)k_shadow_g<kStats, kTM, true> : (const void*)k_shadow_g<kStats, kTM, false>;
+}
+const void* shadow_fn(const RenderParams& p) {
+  const bool b = p.bundle > 1, st = p.stats >= 2;
+  switch (tile_mode(p)) {
+    case 1: return st ? shadow_fn_t<true, 1>(b) : shadow_fn_t<false, 1>(b);
+    case 2: return st ? shadow_fn_t<true, 2>(b) : shadow_fn_t<false, 2>(b);
+    default: return st ? shadow_fn_t<true, 0>(b) : shadow_fn_t<false, 0>(b);
+  }
+}
+
+cudaError_t launch_fn(const void* fn, int grid, int block, void** args, cudaStream_t st) {
+  return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, 0, st);
+}
+
+}  // namespace
+
+GraphGrids graph_grids(const RenderParams& p) {
+  return GraphGrids{grid_of(traverse_fn(p), kChunk), grid_of(shade_fn(p), kBlock), grid_of(shadow_fn(p), kChunk)};
+}
+
+cudaError_t launch_traverse_g(const RenderParams& p, const GraphGrids& g, const int* counts_in, QueuePair qp,
+                              RayBuf rb, float2* hits, Control* ctl, cudaStream_t st) {
+  void* args[] = {(void*)&p, (void*)&counts_in, (void*)&qp, (void*)&rb, (void*)&hits, (void*)&ctl};
+  return launch_fn(traverse_fn(p), g.traverse, kChunk, args, st);
+}
+
+cudaError_t launch_shade_g(const RenderParams& p, const GraphGrids& g, const WaveDesc& w, const int* n_in,
+                           RayBuf cur, const float2* hits, RayBuf next, int* next_count, uint32_t* q, int* q_count,
+                           int qcap, ShadowBuf sb, uint32_t* sq, int* sq_count, float* path_L, Control* ctl,
+                           cudaStream_t st) {
+  void* args[] = {(void*)&p,  (void*)&w,       (void*)&n_in, (void*)&cur, (void*)&hits,     (void*)&next,
+                  (void*)&next_count, (void*)&q, (void*)&q_count, (void*)&qcap, (void*)&sb, (void*)&sq,
+                  (void*)&sq_count, (void*)&path_L, (void*)&ctl};
+  return launch_fn(shade_fn(p), g.shade, kBlock, args, st);
+}
+
+cudaError_t launch_shadow_g(const RenderParams& p, const GraphGrids& g, const WaveDesc& w, const int* counts_in,
+                            QueuePair qp, ShadowBuf sb, float* path_L, Control* ctl, cudaStream_t st) {
+  void* args[] = {(void*)&p, (void*)&w, (void*)&counts_in, (void*)&qp, (void*)&sb, (void*)&path_L, (void*)&ctl};
+  return launch_fn(shadow_fn(p), g.shadow, kChunk, args, st);
+}
+
+void launch_set_int(int* dst, int v, cudaStream_t st) { k_set_int<<<1, 1, 0, st>>>(dst, v); }
+
+void launch_loop_cond(cudaGraphConditionalHandle h, const int* counts, int n_sub, int max_iter, int kind,
+                      Control* ctl, cudaStream_t st) {
+  k_loop_cond<<<1, 1, 0, st>>>(h, counts, n_sub, max_iter, kind, ctl);
+}
+
+void launch_check_drained(const int* counts, int n_sub, Control* ctl, cudaStream_t st) {
+  k_check_drained<<<1, kMaxSubdomains, 0, st>>>(counts, n_sub, ctl);
+}
+
+}  // namespace sdd

@@ -109,9 +109,12 @@ struct Control {
   int next_shadow;                      // shadow rays written this generation
   uint32_t error;
   int tile_hits;                        // tile hits queued for the network this generation
+  int gen_rays[2];                      // graph form: rays of the current / next generation
+  int loop_iter;                        // graph form: iterations of the running pass loop
   unsigned long long node_visits, tri_tests, shadow_node_visits, shadow_tri_tests;
   unsigned long long rays_closest, rays_shadow, crossings;
   unsigned long long tile_shaded;       // tile hits shaded by the network (profiling level >= 2)
+  unsigned long long graph_passes[2];   // graph form: closest-hit / shadow pass launches
 };
 
 enum RayFlags : uint32_t { FLAG_SUN_COUNTED = 1u };
