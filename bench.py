@@ -55,9 +55,14 @@ sys.path.insert(0, ROOT)
 METRIC = "Mspectral-samples/s at <=1% rel. image error vs FP64 oracle; surrogate vs plain"
 UNIT = "Mspectral-samples/s"
 WORKLOAD = "nave-200k {w}x{h} {spp}spp 81lambda depth12 RR S={s} (Monte Carlo, spectral bundles of {b}, {form})"
-TRAVERSE_SOURCES = ["paper_1912_05494_gb300/csrc/render_kernels.cu", "paper_1912_05494_gb300/csrc/render_device.cuh",
-                    "paper_1912_05494_gb300/csrc/device_math.cuh", "paper_1912_05494_gb300/csrc/sdd_internal.h"]
-NCU_SUMMARY = os.path.join(ROOT, "profiles", "traverse_nave_ncu.md")
+# per form: the sources of the dominant traversal kernel, and the committed ncu summary
+# whose DRAM counters are valid while those sources are unchanged
+_CSRC = "paper_1912_05494_gb300/csrc/"
+TRAVERSE_SOURCES = {0: [_CSRC + f for f in ("render_kernels.cu", "render_device.cuh", "device_math.cuh", "sdd_internal.h")],
+                    2: [_CSRC + f for f in ("graph_kernels.cu", "render_device.cuh", "device_math.cuh", "sdd_internal.h",
+                                            "chunk_sched.cuh")]}
+NCU_SUMMARY = {0: os.path.join(ROOT, "profiles", "traverse_nave_ncu.md"),
+               2: os.path.join(ROOT, "profiles", "traverse_graph_nave_ncu.md")}
 FORMS = {0: "host-driven", 1: "batched: persistent kernel + CUDA graph",
          2: "graph form: fixed-grid kernels reading device counts, CUDA graph"}
 TRAVERSE_KERNEL = {0: "k_traverse (closest hit)", 1: "k_persistent_wave (all steps of a wave)",
@@ -79,17 +84,17 @@ def source_hash(paths) -> str:
     return h.hexdigest()[:16]
 
 
-def read_traffic():
-    """DRAM bytes per traversed ray from the committed ncu summary, or None when the
-    kernel source changed since the counters were taken."""
-    if not os.path.exists(NCU_SUMMARY):
+def read_traffic(form):
+    """DRAM bytes per traversed ray from the committed ncu summary of the form's traversal
+    kernel, or None when there is none or its source changed since the counters were taken."""
+    if form not in NCU_SUMMARY or not os.path.exists(NCU_SUMMARY[form]):
         return None
     vals = {}
-    for line in open(NCU_SUMMARY):
+    for line in open(NCU_SUMMARY[form]):
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("kernel_source_hash") != source_hash(TRAVERSE_SOURCES):
+    if vals.get("kernel_source_hash") != source_hash(TRAVERSE_SOURCES[form]):
         return None
     try:
         return float(vals["traffic_bytes_per_ray"])
@@ -290,6 +295,8 @@ def run_gpu(args):
     cam = S.CameraData(**{**cam.__dict__, "width": args.width, "height": args.height})
     spec = S.RenderSpec(**{**spec.__dict__, "seed": spec.seed + 7919 * rank, "spp": args.spp, "bundle": args.bundle})
     h = sdd.SceneHandle(scene)
+    if args.no_graph:  # the graph form's kernels launched one by one (profiling the kernels)
+        sdd.sdd_set_tuning(h.h, {**sdd.sdd_get_tuning(h.h), "no_graph": 1})
     n_px = cam.width * cam.height
     out = torch.empty((n_px, spec.n_lambda), device="cuda", dtype=torch.float32)
     xyz = torch.empty((n_px, 3), device="cuda", dtype=torch.float32)
@@ -352,7 +359,7 @@ def run_gpu(args):
     peak, peak_kind = measured_peaks()
     peak, peak_kind = measured_peaks()
     avg_launch_ms = ms_trav / max(n_trav, 1)
-    per_ray = read_traffic()
+    per_ray = read_traffic(args.batched)
     traffic = per_ray * cnt["rays_closest"] / trav_launches if per_ray is not None else None
     bytes_per_launch = trav_bytes / trav_launches
     achieved = bytes_per_launch / (avg_launch_ms / 1e3) / 1e9 if avg_launch_ms > 0 else 0.0
@@ -608,6 +615,8 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batched", type=int, default=2, choices=[0, 1, 2],
                     help="0: host-driven; 1: persistent kernels + CUDA graph; 2: graph form")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="forms 1 and 2: launch the frame's kernels directly instead of replaying a CUDA graph")
     ap.add_argument("--bundle", type=int, default=14,
                     help="nave workload: wavelengths per spectral bundle (1 = every wavelength its own path)")
     ap.add_argument("--workload", choices=["nave", "large", "network"], default="nave")

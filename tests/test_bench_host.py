@@ -50,7 +50,8 @@ def test_traffic_is_null_when_kernel_changed(tmp_path, monkeypatch):
     import bench
     f = tmp_path / "s.md"
     f.write_text("- kernel_source_hash: 0000\n- traffic_bytes_per_ray: 123.0\n")
-    monkeypatch.setattr(bench, "NCU_SUMMARY", str(f))
-    assert bench.read_traffic() is None
-    f.write_text(f"- kernel_source_hash: {bench.source_hash(bench.TRAVERSE_SOURCES)}\n- traffic_bytes_per_ray: 123.0\n")
-    assert bench.read_traffic() == 123.0
+    monkeypatch.setattr(bench, "NCU_SUMMARY", {2: str(f)})
+    assert bench.read_traffic(2) is None
+    assert bench.read_traffic(1) is None  # the persistent form has no per-kernel summary
+    f.write_text(f"- kernel_source_hash: {bench.source_hash(bench.TRAVERSE_SOURCES[2])}\n- traffic_bytes_per_ray: 123.0\n")
+    assert bench.read_traffic(2) == 123.0
