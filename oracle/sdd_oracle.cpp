@@ -734,7 +734,7 @@ double trace_split(const RenderCtx& cx, V3 o, V3 d, double seg0, int vertex, int
 // Monte Carlo path (Sec. 3.2): one chain per (pixel, sample, wavelength) with the same
 // Philox draws the GPU uses.  Returns the path radiance; optionally its event hash.
 // Spectral bundling: with cx.bundle = B > 1 the wavelengths l = jB .. jB + B - 1 draw every
-// random number on the counter word j instead of l (one draw serves the B wavelengths, Sec. 5
+// random number on the counter word j instead of l (one draw serves the B wavelengths; Sec. 4
 // cuts the spectral array into groups).  Each wavelength still follows its own chain with its
 // own decisions; only the uniforms are shared, so each chain has the distribution it has with
 // B = 1 and the wavelengths of a bundle are correlated.

@@ -1,7 +1,7 @@
 // bundle_device.cuh -- spectral bundles: the wavefront path with several wavelengths per ray.
 //
-// Sec. 5 of the paper cuts the spectral array into groups that are traced together.  Here a
-// bundle is B consecutive wavelengths (B = RenderParams::bundle, 2..16) of one (pixel,
+// Sec. 4 of the paper cuts the 81-value spectral array into groups of n wavelengths as units
+// of work.  Here a bundle is B consecutive wavelengths (B = RenderParams::bundle, 2..16) of one (pixel,
 // sample).  Every random number of the bundle's chains is drawn on the bundle index j in
 // place of the wavelength index (the rule the oracle follows), so as long as their decisions
 // agree the B chains share every vertex and one traversal serves them all.  A ray carries the

@@ -103,7 +103,7 @@ def test_closest_hit_matches_oracle_brute_force(sdd, orc, n_sub):
     assert hit.mean() > 0.3
 
 
-# ----------------------------------------------------------------------------- config 1: slab
+# ----------------------------------------------------------------------------- deterministic slab (64x64, 16 wavelengths, depth 6)
 @pytest.mark.parametrize("size", [64, 16, 24])
 def test_slab_deterministic_matches_oracle(sdd, orc, size):
     """64x64 pinhole, 16 wavelengths, reflect+transmit splitting to depth 6: per-pixel
@@ -157,7 +157,7 @@ def test_render_to_host_equals_device_render(sdd):
     assert np.array_equal(hx.astype(np.float64), gxyz)
 
 
-# ----------------------------------------------------------------------------- config 2: nave (MC)
+# ----------------------------------------------------------------------------- the nave (Monte Carlo, 1024x768, 16 spp, 81 wavelengths)
 @pytest.fixture(scope="module")
 def nave():
     return S.nave_scene(seed=1)
