@@ -442,7 +442,7 @@ def run_large(args):
     p, y = pred.cpu().numpy(), hy.cpu().numpy()
     held = {"mae_T": float(np.abs(p[:, 0] - y[:, 0]).mean()), "mae_R": float(np.abs(p[:, 1] - y[:, 1]).mean()),
             "samples": int(hr.shape[0])}
-    net_kw = {"use_surrogate": 1, "surrogate": net, "batched": 1}
+    net_kw = {"use_surrogate": 1, "surrogate": net, "batched": 2}  # graph form
     # the network forms trace spectral bundles; the plain form every wavelength on its own
     spec_net = S.RenderSpec(**{**spec.__dict__, "bundle": args.bundle})
     tuned = None
@@ -494,7 +494,8 @@ def run_large(args):
     clocks.start()
     ms_net, launches_net, img_net, _ = timed(net_kw, args.steps, args.warmup, spec_net)
     ms_net_host, launches_net_host, _, ms_tile = timed({**net_kw, "batched": 0}, args.steps, args.warmup, spec_net)
-    ms_net1, _, img_net1, _ = timed(net_kw, args.steps, args.warmup)  # network + batched, no bundles
+    ms_net1, _, img_net1, _ = timed(net_kw, args.steps, args.warmup)  # network + graph form, no bundles
+    ms_net_p, launches_net_p, _, _ = timed({**net_kw, "batched": 1}, args.steps, args.warmup, spec_net)
     ms_plain, launches_plain, img_plain, _ = timed({"batched": 0}, args.steps, args.warmup)
     clk = clocks.stop()
     spec2 = S.RenderSpec(**{**spec.__dict__, "seed": spec.seed + 4099})
@@ -508,7 +509,7 @@ def run_large(args):
             "warmup": args.warmup, "ms_per_step": ms_net, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"large nave {scene.n_triangles} triangles, 96 windows x 400 heterogeneous tiles, "
-                                   f"{cam.width}x{cam.height} {spec.spp}spp 81lambda depth16 RR, network + batched, "
+                                   f"{cam.width}x{cam.height} {spec.spp}spp 81lambda depth16 RR, network + graph form, "
                                    f"spectral bundles of {args.bundle}",
                        "paths_per_step": frame_paths, "subdomains": scene.n_subdomains,
                        "l2": "flushed (512 MB write) before every frame; the FP64 film alone is 5.4 GB"},
@@ -516,8 +517,13 @@ def run_large(args):
                                      "form": "host-driven wavefront, brute-force ray through the tile per tile hit"},
                            "network_batched": {"value": value_net, "ms_per_step": ms_net,
                                                "gpu_launches": launches_net,
-                                               "form": "persistent kernels + CUDA graph, fused tile shading, "
+                                               "form": "graph form (fixed-grid kernels, conditional pass loops, one "
+                                                       "CUDA graph per frame), fused tile shading, "
                                                        f"spectral bundles of {args.bundle}"},
+                           "network_persistent": {"value": frame_paths / (ms_net_p / 1e3) / 1e6,
+                                                  "ms_per_step": ms_net_p, "gpu_launches": launches_net_p,
+                                                  "form": "persistent kernel segments + CUDA graph, fused tile "
+                                                          f"shading, spectral bundles of {args.bundle}"},
                            "network_batched_unbundled": {"value": frame_paths / (ms_net1 / 1e3) / 1e6,
                                                          "ms_per_step": ms_net1,
                                                          "image_error_block8": rel_err(block_avg(img_net1, cam), bp)},
