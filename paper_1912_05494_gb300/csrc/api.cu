@@ -454,9 +454,10 @@ sdd_status graph_passes(sdd_scene* s, const RenderParams& p, const GraphGrids& g
   uint32_t* const* qs = shadow ? b.sq : b.q;
   auto pass = [&](int a, cudaStream_t st) -> sdd_status {
     CK(cudaMemsetAsync(counts[1 - a], 0, sizeof(int) * kMaxSubdomains, st));
+    CK(cudaMemsetAsync(&c->work[a], 0, sizeof(int), st));
     QueuePair qp{qs[a], qs[1 - a], counts[1 - a], qcap};
-    if (shadow) CK(launch_shadow_g(p, gg, w, counts[a], qp, b.sb, b.path_L, c, st));
-    else CK(launch_traverse_g(p, gg, counts[a], qp, b.rb[cur], b.hits, c, st));
+    if (shadow) CK(launch_shadow_g(p, gg, w, counts[a], &c->work[a], qp, b.sb, b.path_L, c, st));
+    else CK(launch_traverse_g(p, gg, counts[a], &c->work[a], qp, b.rb[cur], b.hits, c, st));
     return SDD_OK;
   };
   const int kind = shadow ? TK_SHADOW : TK_TRAVERSE;

@@ -12,14 +12,15 @@ struct GraphGrids {
 };
 GraphGrids graph_grids(const RenderParams& p);
 
-cudaError_t launch_traverse_g(const RenderParams& p, const GraphGrids& g, const int* counts_in, QueuePair qp,
-                              RayBuf rb, float2* hits, Control* ctl, cudaStream_t st);
+// work: the pass's chunk counter, zero before the pass
+cudaError_t launch_traverse_g(const RenderParams& p, const GraphGrids& g, const int* counts_in, int* work,
+                              QueuePair qp, RayBuf rb, float2* hits, Control* ctl, cudaStream_t st);
 cudaError_t launch_shade_g(const RenderParams& p, const GraphGrids& g, const WaveDesc& w, const int* n_in,
                            RayBuf cur, const float2* hits, RayBuf next, int* next_count, uint32_t* q, int* q_count,
                            int qcap, ShadowBuf sb, uint32_t* sq, int* sq_count, float* path_L, Control* ctl,
                            cudaStream_t st);
 cudaError_t launch_shadow_g(const RenderParams& p, const GraphGrids& g, const WaveDesc& w, const int* counts_in,
-                            QueuePair qp, ShadowBuf sb, float* path_L, Control* ctl, cudaStream_t st);
+                            int* work, QueuePair qp, ShadowBuf sb, float* path_L, Control* ctl, cudaStream_t st);
 void launch_set_int(int* dst, int v, cudaStream_t st);
 void launch_loop_cond(cudaGraphConditionalHandle h, const int* counts, int n_sub, int max_iter, int kind,
                       Control* ctl, cudaStream_t st);

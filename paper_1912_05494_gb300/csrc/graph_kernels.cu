@@ -4,8 +4,9 @@
 // round trip per subdomain pass; the persistent form removes the round trips but runs every
 // step at the one occupancy its register budget allows.  The graph form keeps one kernel per
 // step, each at its own occupancy, and reads the counts on the device instead: every launch
-// has a fixed grid (SMs x resident blocks) that strides over subdomain-aligned 128-ray chunks
-// of the queues (traversal) or over the generation's rays (shading).  A generation is the
+// has a fixed grid (SMs x resident blocks) whose blocks take subdomain-aligned 128-ray chunks
+// of the queues from a work counter (traversal) or stride over the generation's rays
+// (shading).  A generation is the
 // closest-hit passes, shading, the shadow passes; the passes run in conditional 'while' nodes
 // of the frame's CUDA graph whose condition kernel (k_loop_cond) reads the queue counts, so a
 // whole frame is captured once and replayed with no host round trip and no empty passes
@@ -23,15 +24,26 @@ namespace sdd {
 
 namespace {
 
+// Next chunk of a pass for this block from the pass's work counter (zeroed before the pass):
+// blocks take chunks as they finish, so the pass's cost balances over the grid as when every
+// chunk is its own block.  Returns a value >= total when the pass is done.
+__device__ __forceinline__ int next_chunk(int* work) {
+  __shared__ int s_chunk;
+  __syncthreads();
+  if (threadIdx.x == 0) s_chunk = atomicAdd(work, kChunk);
+  __syncthreads();
+  return s_chunk;
+}
+
 // Closest-hit pass over the queues whose counts are counts_in.
 template <bool kStats>
-__global__ void __launch_bounds__(kChunk, 12) k_traverse_g(RenderParams p, const int* counts_in, QueuePair qp,
-                                                           RayBuf rb, float2* hits, Control* ctl) {
+__global__ void __launch_bounds__(kChunk, 12) k_traverse_g(RenderParams p, const int* counts_in, int* work,
+                                                           QueuePair qp, RayBuf rb, float2* hits, Control* ctl) {
   __shared__ int s_prefix[kMaxSubdomains + 1];
   __shared__ int s_count[kMaxSubdomains];
   const int n_sub = p.sc.n_sub;
   const int total = load_prefix(counts_in, n_sub, qp.cap, s_prefix, s_count);
-  for (int c0 = blockIdx.x * kChunk; c0 < total; c0 += gridDim.x * kChunk) {
+  for (int c0 = next_chunk(work); c0 < total; c0 = next_chunk(work)) {
     const int s = find_subdomain(s_prefix, n_sub, c0);  // the whole chunk's subdomain
     const int i = c0 - s_prefix[s] + (int)threadIdx.x;
     dev_traverse_warp<kStats>(p, s, i, i < s_count[s], nullptr, 0, qp, rb, hits, ctl);
@@ -61,13 +73,14 @@ __global__ void __launch_bounds__(kBlock) k_shade_g(RenderParams p, WaveDesc w, 
 // Shadow pass over the queues whose counts are counts_in (walk choice as in the other forms).
 template <bool kStats, int kTM, bool kBund>
 __global__ void __launch_bounds__(kChunk, kTM == 1 ? 1 : 8) k_shadow_g(RenderParams p, WaveDesc w,
-                                                                      const int* counts_in, QueuePair qp,
-                                                                      ShadowBuf sb, float* path_L, Control* ctl) {
+                                                                      const int* counts_in, int* work,
+                                                                      QueuePair qp, ShadowBuf sb, float* path_L,
+                                                                      Control* ctl) {
   __shared__ int s_prefix[kMaxSubdomains + 1];
   __shared__ int s_count[kMaxSubdomains];
   const int n_sub = p.sc.n_sub;
   const int total = load_prefix(counts_in, n_sub, qp.cap, s_prefix, s_count);
-  for (int c0 = blockIdx.x * kChunk; c0 < total; c0 += gridDim.x * kChunk) {
+  for (int c0 = next_chunk(work); c0 < total; c0 = next_chunk(work)) {
     const int s = find_subdomain(s_prefix, n_sub, c0);
     const int i = c0 - s_prefix[s] + (int)threadIdx.x;
     const bool act = i < s_count[s];
@@ -159,9 +172,9 @@ GraphGrids graph_grids(const RenderParams& p) {
   return GraphGrids{grid_of(traverse_fn(p), kChunk), grid_of(shade_fn(p), kBlock), grid_of(shadow_fn(p), kChunk)};
 }
 
-cudaError_t launch_traverse_g(const RenderParams& p, const GraphGrids& g, const int* counts_in, QueuePair qp,
-                              RayBuf rb, float2* hits, Control* ctl, cudaStream_t st) {
-  void* args[] = {(void*)&p, (void*)&counts_in, (void*)&qp, (void*)&rb, (void*)&hits, (void*)&ctl};
+cudaError_t launch_traverse_g(const RenderParams& p, const GraphGrids& g, const int* counts_in, int* work,
+                              QueuePair qp, RayBuf rb, float2* hits, Control* ctl, cudaStream_t st) {
+  void* args[] = {(void*)&p, (void*)&counts_in, (void*)&work, (void*)&qp, (void*)&rb, (void*)&hits, (void*)&ctl};
   return launch_fn(traverse_fn(p), g.traverse, kChunk, args, st);
 }
 
@@ -176,8 +189,9 @@ cudaError_t launch_shade_g(const RenderParams& p, const GraphGrids& g, const Wav
 }
 
 cudaError_t launch_shadow_g(const RenderParams& p, const GraphGrids& g, const WaveDesc& w, const int* counts_in,
-                            QueuePair qp, ShadowBuf sb, float* path_L, Control* ctl, cudaStream_t st) {
-  void* args[] = {(void*)&p, (void*)&w, (void*)&counts_in, (void*)&qp, (void*)&sb, (void*)&path_L, (void*)&ctl};
+                            int* work, QueuePair qp, ShadowBuf sb, float* path_L, Control* ctl, cudaStream_t st) {
+  void* args[] = {(void*)&p,  (void*)&w,      (void*)&counts_in, (void*)&work,
+                  (void*)&qp, (void*)&sb, (void*)&path_L,    (void*)&ctl};
   return launch_fn(shadow_fn(p), g.shadow, kChunk, args, st);
 }
 

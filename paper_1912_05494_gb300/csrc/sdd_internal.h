@@ -111,6 +111,7 @@ struct Control {
   int tile_hits;                        // tile hits queued for the network this generation
   int gen_rays[2];                      // graph form: rays of the current / next generation
   int loop_iter;                        // graph form: iterations of the running pass loop
+  int work[2];                          // graph form: chunk counters of a loop's two passes
   unsigned long long node_visits, tri_tests, shadow_node_visits, shadow_tri_tests;
   unsigned long long rays_closest, rays_shadow, crossings;
   unsigned long long tile_shaded;       // tile hits shaded by the network (profiling level >= 2)
