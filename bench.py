@@ -322,12 +322,14 @@ def run_gpu(args):
     # timed region: K frames, L2 flushed before each, per-launch CUDA events in the library
     flush = torch.empty(512 * 1024 * 1024 // 4, device="cuda", dtype=torch.float32)  # 512 MB > L2
     sdd.sdd_set_profiling(h.h, 1)
-    # the clock sampler starts before the last untimed frame: nvidia-smi's start-up briefly
-    # delays the next graph launch, which must not fall in the timed region
+    # the clock sampler and the first write of the flush buffer come before the last untimed
+    # frame: either delayed the first frame after it by ~0.25 s in the graph form
     clocks = ClockSampler(local)
     clocks.start()
+    flush.zero_()
     time.sleep(0.5)
     # the profiling level is part of a captured frame: one untimed frame captures it again
+    flush.zero_()
     sdd.sdd_render(h.h, cam, spec, out, xyz, **kw)
     if dist is not None:
         dist.barrier()
