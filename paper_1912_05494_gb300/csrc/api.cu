@@ -948,7 +948,6 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
     s->stats.rays_closest = (int64_t)s->h_ctl->rays_closest;
     s->stats.rays_shadow = (int64_t)s->h_ctl->rays_shadow;
     s->stats.crossings = (int64_t)s->h_ctl->crossings;
-  s->stats.tile_shaded = (int64_t)s->h_ctl->tile_shaded;
     s->stats.tile_shaded = (int64_t)s->h_ctl->tile_shaded;
     s->stats.bytes_ray_state = s->stats.rays_closest * 44 + s->stats.rays_shadow * 44;
     s->stats.ms_total = s->stats.ms_persistent;

@@ -39,7 +39,7 @@ using namespace sdd;
 namespace {
 
 using namespace sdd::net;
-constexpr int kTargets = kHeadTargets, kPred = kHeadPred;
+constexpr int kTargets = kHeadTargets;
 constexpr int kRows = 128;    // batch rows per block
 constexpr int kThreads = 256;  // 8 warps, 16 rows each
 
