@@ -295,3 +295,19 @@ class OracleScene:
         if rc != 0:
             raise ValueError("oracle rejected the render arguments")
         return film, path_L, path_h
+
+
+def bubble_scatter(d, rad, sin_i, u, n_re, k=0.0, r=50e-6):
+    """Sphere optics of one air bubble with the surface choices given: d, rad [n, 3], sin_i [n],
+    u [n, m] uniforms taken one per surface met.  Returns (exit direction [n, 3], surfaces met,
+    or -1 where the m uniforms ran out inside the bubble)."""
+    d = _c(d, np.float64).reshape(-1, 3)
+    n = d.shape[0]
+    rad = _c(rad, np.float64).reshape(n, 3)
+    sin_i = _c(np.broadcast_to(sin_i, (n,)), np.float64)
+    u = _c(u, np.float64).reshape(n, -1)
+    out = np.zeros((n, 3))
+    ev = np.zeros(n, np.int32)
+    lib().orc_bubble_scatter(n, _p(d), _p(rad), _p(sin_i), C.c_double(r), C.c_double(n_re), C.c_double(k),
+                             u.shape[1], _p(u), _p(out), _p(ev))
+    return out, ev

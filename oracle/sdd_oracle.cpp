@@ -341,6 +341,45 @@ double tile_back_hit(const TileGeom& g, V3 o, V3 d, double t_max, int max_cells,
   return -1.0;
 }
 
+// Exact optics of one air bubble in the glass (Sec. 1: air micro-bubbles; Fresnel and Snell
+// at each of its surfaces, the glass of index n + ik outside, air inside).  The ray with
+// direction *d meets a sphere of radius r at impact parameter b = sin_i * r, displaced from
+// the centre line toward the unit vector rad (normal to *d).  At every surface met,
+// choice() gives the uniform that picks reflection (u < R) or refraction; inside the air the
+// ray crosses the chord to the next surface point.  choice() returns a negative value when
+// the event cap is reached: the function then returns false (the ray is lost in the bubble).
+// On true, *d holds the direction with which the ray leaves the sphere into the glass.
+template <class Choice>
+bool bubble_scatter(V3* dp, V3 rad, double sin_i, double r, double n, double k, Choice&& choice) {
+  V3 d = *dp;
+  double cos_i0 = std::sqrt(std::max(0.0, 1.0 - sin_i * sin_i));
+  // the sphere in its own frame: q is the current point relative to the centre
+  V3 q = r * ((-cos_i0) * d + sin_i * rad);  // entry point (outward normal q / r)
+  bool inside = false;                          // inside the bubble (air)
+  for (;;) {
+    double u = choice();
+    if (u < 0.0) { *dp = d; return false; }
+    V3 nn = (1.0 / r) * q;
+    double ci = std::fabs(dot(d, nn));
+    V3 nf = dot(d, nn) < 0 ? nn : -1.0 * nn;  // facing the incoming ray
+    double m1 = inside ? 1.0 : n;
+    cd m2 = inside ? cd(n, k) : cd(1.0, 0.0);
+    double Rb = fresnel_R(ci, m1, m2);
+    double et = m1 / std::real(m2);
+    double cc = 1.0 - et * et * (1.0 - ci * ci);
+    if (u < Rb || cc <= 0.0) {
+      d = reflect(d, nf);
+    } else {
+      d = normalize(et * d + (et * ci - std::sqrt(cc)) * nf);
+      inside = !inside;
+    }
+    if (!inside) break;           // back in the glass, leaving the sphere
+    q = q + (-2.0 * dot(q, d)) * d;  // across the chord to the next point on the sphere
+  }
+  *dp = d;
+  return true;
+}
+
 struct TileRay {
   int side;     // 0 reflected (front), 1 transmitted (back), 2 absorbed (event cap)
   double w;     // throughput
@@ -421,34 +460,15 @@ TileRay tile_trace(const TileGeom& g, const TileParams& tp, double x0, double y0
         out.bubbles++;
         double r = std::sqrt(r_lo * r_lo + us.u[1] * (r_hi * r_hi - r_lo * r_lo));
         double sin_i = std::sqrt(us.u[2]);  // impact parameter / r, uniform over the disc
-        double cos_i0 = std::sqrt(std::max(0.0, 1.0 - sin_i * sin_i));
         V3 t1, t2;
         onb(d, &t1, &t2);
         double phi = 2.0 * PI * us.u[3];
         V3 rad = std::cos(phi) * t1 + std::sin(phi) * t2;
-        // the sphere in its own frame: q is the current point relative to the centre
-        V3 q = r * ((-cos_i0) * d + sin_i * rad);  // entry point (outward normal q / r)
-        bool inside = false;                          // inside the bubble (air)
-        for (;;) {
-          if (e >= max_events) { out.side = 2; out.w = w; out.events = e; return out; }
-          Draw ub = next_u();
-          V3 nn = (1.0 / r) * q;
-          double ci = std::fabs(dot(d, nn));
-          V3 nf = dot(d, nn) < 0 ? nn : -1.0 * nn;  // facing the incoming ray
-          double m1 = inside ? 1.0 : n;
-          cd m2 = inside ? cd(n, k) : cd(1.0, 0.0);
-          double Rb = fresnel_R(ci, m1, m2);
-          double et = m1 / std::real(m2);
-          double cc = 1.0 - et * et * (1.0 - ci * ci);
-          if (ub.u[0] < Rb || cc <= 0.0) {
-            d = reflect(d, nf);
-          } else {
-            d = normalize(et * d + (et * ci - std::sqrt(cc)) * nf);
-            inside = !inside;
-          }
-          if (!inside) break;           // back in the glass, leaving the sphere
-          q = q + (-2.0 * dot(q, d)) * d;  // across the chord to the next point on the sphere
-        }
+        auto choice = [&]() -> double {
+          if (e >= max_events) return -1.0;
+          return next_u().u[0];
+        };
+        if (!bubble_scatter(&d, rad, sin_i, r, n, k, choice)) { out.side = 2; out.w = w; out.events = e; return out; }
         // bubbles (<= 100 um) are point scatterers at the scale of the tile: the ray leaves
         // the encounter where it met it, with the direction the sphere optics gave
         continue;
@@ -1197,6 +1217,22 @@ void orc_tile_trace(const OrcTile* t, int G, double L, const double* h, int n, c
     dout[3 * i] = r.dir.x; dout[3 * i + 1] = r.dir.y; dout[3 * i + 2] = r.dir.z;
     bubbles[i] = r.bubbles;
     events[i] = r.events;
+  }
+}
+
+// The bubble optics alone, driven by given uniforms instead of Philox draws: ray i has
+// direction d[i], impact direction rad[i] and impact parameter sin_i[i] (b / r); its surface
+// interactions take u[i * n_u + j] in turn.  dout gets the exit direction and n_events the
+// number of surfaces met, or -1 when the n_u uniforms ran out inside the bubble.
+void orc_bubble_scatter(int n, const double* d, const double* rad, const double* sin_i, double r, double n_re,
+                        double k, int n_u, const double* u, double* dout, int32_t* n_events) {
+  for (int i = 0; i < n; ++i) {
+    V3 di{d[3 * i], d[3 * i + 1], d[3 * i + 2]};
+    int j = 0;
+    auto choice = [&]() -> double { return j < n_u ? u[(size_t)i * n_u + j++] : -1.0; };
+    bool ok = bubble_scatter(&di, {rad[3 * i], rad[3 * i + 1], rad[3 * i + 2]}, sin_i[i], r, n_re, k, choice);
+    dout[3 * i] = di.x; dout[3 * i + 1] = di.y; dout[3 * i + 2] = di.z;
+    n_events[i] = ok ? j : -1;
   }
 }
 
