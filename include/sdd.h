@@ -362,8 +362,15 @@ sdd_status sdd_surrogate_infer(sdd_surrogate* s, int n, const float* raw_dev, fl
  * allocate when a batch arrives.
  *   - Capacity: n * (48 + 8 * n_subdomains) bytes plus a small control block must fit in
  *     16 MiB (about 149,000 rays at 8 subdomains); larger n returns SDD_ERR_ARG.
- *   - The first call on a device looks up the array's device address for that device (with
- *     that device current); make that first call before any stream capture.
+ *   - Every call looks up the array's device address on the current device.  Under CUDA's
+ *     default lazy module loading the 16 MiB become device memory at the first lookup on a
+ *     device, not when the process starts: a caller that budgets its memory at start-up
+ *     makes one call with n = 0 then (it only does this set-up and returns).  That first
+ *     call on a device should come before any stream capture.
+ *   - The call synchronises the given stream before it returns (it reads the queue counts
+ *     back after every pass).
+ *   - Errors raised on the device come back as SDD_ERR_STACK (traversal stack or the walk's
+ *     step bound), SDD_ERR_QUEUE_OVERFLOW (queue capacity) or SDD_ERR_TIMEOUT (a loop cap).
  *   - Every GPU that uses the library keeps the 16 MiB until the process exits.
  *   - All calls share the array and it keeps the previous call's contents; the call clears
  *     what must start at zero.  Calls whose GPU work overlaps (other threads or streams)

@@ -16,7 +16,6 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <mutex>
 #include <string>
 
 #include "../../include/sdd.h"
@@ -34,13 +33,9 @@ using namespace sdd;
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;  // 16 MiB per device
-constexpr int kMaxDevices = 64;
 constexpr int kBlock = 128;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
-
-std::mutex g_setup_mutex;
-void* g_scratch_ptr[kMaxDevices] = {};
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -52,24 +47,30 @@ size_t scratch_bytes(size_t n, int n_sub) {
          2 * align256(4 * n * (size_t)n_sub);
 }
 
-// Device address of the static scratch on the current device, looked up once per device.
+// Device address of the static scratch on the current device.  The array is a host-side
+// stand-in in host code, so its device address is looked up, with the device current, on
+// every call: the first lookup on a device loads the library's module there (under CUDA's
+// default lazy loading this is when the 16 MiB are placed in device memory); later lookups
+// are cheap, and a lookup per call follows a context that was destroyed and created again
+// (cudaDeviceReset), where a cached address would go stale.
 sdd_status scratch_on_current_device(unsigned char** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return set_last_error(SDD_ERR_CUDA, cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return set_last_error(SDD_ERR_ARG, "device ordinal out of range");
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      return set_last_error(SDD_ERR_CUDA, (std::string("cudaGetSymbolAddress(scratch): ") +
-                                           cudaGetErrorString(e)).c_str());
-    }
-    g_scratch_ptr[dev] = p;
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    return set_last_error(SDD_ERR_CUDA, (std::string("cudaGetSymbolAddress(scratch): ") +
+                                         cudaGetErrorString(e)).c_str());
   }
-  *out = static_cast<unsigned char*>(g_scratch_ptr[dev]);
+  *out = static_cast<unsigned char*>(p);
   return SDD_OK;
+}
+
+// Status for the error bits the traversal kernels raise in the control block.
+sdd_status status_of_error_bits(uint32_t bits) {
+  if (bits & ERR_STACK_OVERFLOW)
+    return set_last_error(SDD_ERR_STACK, "BVH traversal stack overflow or walk step bound reached");
+  if (bits & (ERR_QUEUE_OVERFLOW | ERR_SHADOW_OVERFLOW))
+    return set_last_error(SDD_ERR_QUEUE_OVERFLOW, "ray queue capacity exceeded");
+  return set_last_error(SDD_ERR_TIMEOUT, "device loop hit its iteration cap");
 }
 
 }  // namespace
@@ -79,7 +80,10 @@ extern "C" sdd_status sdd_trace_closest_noalloc(sdd_scene* scene, int n, const f
                                                 void* cuda_stream) {
   if (!scene || n < 0 || (n > 0 && (!org_dev || !dir_dev || !t_out_dev || !prim_out_dev)))
     return set_last_error(SDD_ERR_ARG, "bad arguments");
-  if (n == 0) return SDD_OK;
+  if (n == 0) {  // set-up only: place the scratch on this device now
+    unsigned char* base = nullptr;
+    return scratch_on_current_device(&base);
+  }
   const DevScene* ds = scene_device_view(scene);
   const size_t need = scratch_bytes((size_t)n, ds->n_sub);
   if (need > kNoAllocScratchBytes) {
@@ -127,8 +131,7 @@ extern "C" sdd_status sdd_trace_closest_noalloc(sdd_scene* scene, int n, const f
     if ((e = cudaMemcpyAsync(&h, ctl, sizeof(Control), cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
         (e = cudaStreamSynchronize(stream)) != cudaSuccess)
       return set_last_error(SDD_ERR_CUDA, cudaGetErrorString(e));
-    if (h.error & ERR_STACK_OVERFLOW) return set_last_error(SDD_ERR_STACK, "BVH traversal stack overflow");
-    if (h.error) return set_last_error(SDD_ERR_QUEUE_OVERFLOW, "ray queue capacity exceeded");
+    if (h.error) return status_of_error_bits(h.error);
     Sched sch;
     sch.n_sub = ds->n_sub;
     int blocks = 0;

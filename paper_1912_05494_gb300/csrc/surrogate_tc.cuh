@@ -238,7 +238,11 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_infer_tc(SurrogateView v, c
   }
   if (failed) {
     if (tid == 0) atomicOr(pol.err(ctx), tc::kErrTimeout);
-    tc::bar_wait(bar_a, phase);  // the MMAs still in flight, bounded again
+    // The phase bit was flipped after the wait that gave up, so the phase still owed by the
+    // MMAs in flight is phase ^ 1 (try_wait.parity(p) succeeds at once for a parity p that
+    // is not the barrier's current phase).  Wait for it, bounded again, before the TMEM
+    // columns are freed; the results of this launch are already flagged invalid.
+    tc::bar_wait(bar_a, phase ^ 1u);
   }
   tc::fence_before();
   __syncthreads();

@@ -46,6 +46,18 @@ def nave_rays(seed, n):
     return o.astype(np.float32), d.astype(np.float32)
 
 
+def test_noalloc_setup_call_without_rays(sdd):
+    """A call with n = 0 only places the static scratch on the current device (what a caller
+    that budgets its memory at start-up does once); it succeeds and touches no output."""
+    sc = S.tiny_scene(7, n_triangles=64)
+    h = sdd.SceneHandle(sc)
+    e = torch.empty((0, 3), device="cuda")
+    t = torch.empty((0,), device="cuda")
+    p = torch.empty((0,), device="cuda", dtype=torch.int32)
+    sdd.sdd_trace_closest_noalloc(h.h, e, e, t, p)
+    torch.cuda.synchronize()
+
+
 @pytest.mark.parametrize("n_sub", [1, 5])
 def test_noalloc_matches_allocating_entry_point_tiny(sdd, n_sub):
     sc = S.tiny_scene(7, n_triangles=64)
