@@ -38,7 +38,7 @@ class OrcScene(C.Structure):
         ("sky", C.c_void_p), ("sky_mode", C.c_int),
         ("sun_dir", C.c_float * 3), ("sun_half_angle", C.c_float), ("sun", C.c_void_p),
         ("ray_eps", C.c_float), ("n_tiles", C.c_int), ("tiles", C.c_void_p), ("mat_tile", C.c_void_p),
-        ("tile_grid", C.c_int), ("tile_size", C.c_double),
+        ("tile_grid", C.c_int), ("tile_size", C.c_double), ("slab_polarisation", C.c_int),
     ]
 
 
@@ -106,12 +106,13 @@ def fresnel(cos_i, n1, n2_re, n2_im):
     return R.reshape(shp), Rs.reshape(shp), Rp.reshape(shp)
 
 
-def slab(cos_i, n, k, d_m, lambda_nm):
+def slab(cos_i, n, k, d_m, lambda_nm, pol=0):
+    """Thin-slab (R, T); pol = 1 runs the series for s and p separately and averages."""
     arrs = np.broadcast_arrays(*(np.asarray(x, np.float64) for x in (cos_i, n, k, d_m, lambda_nm)))
     args = [_c(x, np.float64).ravel() for x in arrs]
     m = args[0].size
     R, T = np.zeros(m), np.zeros(m)
-    lib().orc_slab(m, *(_p(a) for a in args), _p(R), _p(T))
+    lib().orc_slab(m, *(_p(a) for a in args), int(pol), _p(R), _p(T))
     return R.reshape(arrs[0].shape), T.reshape(arrs[0].shape)
 
 
@@ -245,6 +246,7 @@ class OracleScene:
         d.sun_half_angle = float(sd.sun_half_angle)
         d.sun = keep(sd.sun, np.float32) if sd.sun is not None else None
         d.ray_eps = float(sd.ray_eps)
+        d.slab_polarisation = int(getattr(sd, "slab_polarisation", 0))
         if getattr(sd, "tiles", None):
             arr = _tiles(sd.tiles)
             self._keep.append(arr)

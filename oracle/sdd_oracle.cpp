@@ -116,18 +116,36 @@ double beer_lambert(double k, double len_m, double lambda_nm) {
   return std::exp(-4.0 * PI * k * len_m / (lambda_nm * 1e-9));
 }
 
-// Thin slab of thickness d: incoherent sum over all internal reflections.  R is the
-// single-interface reflectance at the incidence angle, tau the one-way internal
-// transmittance along the refracted direction (real-index Snell).
-void slab_RT(double cos_i, double n, double k, double d_m, double lambda_nm, double* R_slab,
-             double* T_slab) {
-  double R = fresnel_R(cos_i, 1.0, cd(n, k));
-  double sin2_t = (1.0 - cos_i * cos_i) / (n * n);
-  double cos_t = std::sqrt(1.0 - sin2_t);
-  double tau = beer_lambert(k, d_m / cos_t, lambda_nm);
+// Thin slab of thickness d: incoherent sum over all internal reflections, for an interface
+// reflectance R and the one-way internal transmittance tau:
+//   R_slab = R + (1 - R)^2 R tau^2 / (1 - R^2 tau^2),  T_slab = (1 - R)^2 tau / (1 - R^2 tau^2).
+void slab_series(double R, double tau, double* R_slab, double* T_slab) {
   double denom = (1.0 - R * tau) * (1.0 + R * tau);  // 1 - R^2 tau^2
   *R_slab = R + (1.0 - R) * (1.0 - R) * R * tau * tau / denom;
   *T_slab = (1.0 - R) * (1.0 - R) * tau / denom;
+}
+
+// The slab at incidence cos_i (Sec. 2, Eq. 1 optical constants; tau along the refracted
+// direction, real-index Snell).  pol = 0: the series runs once on the unpolarised
+// interface reflectance (Rs + Rp) / 2; pol = 1: s and p light do not mix at the slab's
+// parallel faces, so the series runs for each polarisation on its own reflectance and the
+// two results are averaged (unpolarised light is half s, half p).
+void slab_RT(double cos_i, double n, double k, double d_m, double lambda_nm, double* R_slab,
+             double* T_slab, int pol = 0) {
+  double Rs, Rp;
+  double R = fresnel_R(cos_i, 1.0, cd(n, k), &Rs, &Rp);
+  double sin2_t = (1.0 - cos_i * cos_i) / (n * n);
+  double cos_t = std::sqrt(1.0 - sin2_t);
+  double tau = beer_lambert(k, d_m / cos_t, lambda_nm);
+  if (pol == 0) {
+    slab_series(R, tau, R_slab, T_slab);
+    return;
+  }
+  double Rss, Tss, Rsp, Tsp;
+  slab_series(Rs, tau, &Rss, &Tss);
+  slab_series(Rp, tau, &Rsp, &Tsp);
+  *R_slab = 0.5 * (Rss + Rsp);
+  *T_slab = 0.5 * (Tss + Tsp);
 }
 
 // ---------------------------------------------------------------- CMF fit
@@ -496,6 +514,7 @@ struct Scene {
   V3 sun_dir{0, 0, 1};
   double sun_h = 0.0;            // 1 - cos(sun half-angle)
   double eps = 1e-5;             // origin offset along the geometric normal (m)
+  int slab_pol = 0;              // thin-slab series: 0 unpolarised interface R, 1 per polarisation
   // heterogeneous tiles: per material the tile index (-1 for other kinds)
   std::vector<int> mat_tile;
   std::vector<TileParams> tiles;
@@ -597,7 +616,7 @@ void shadow_rec(const Scene& s, int ni, V3 o, V3 d, int lam, double lambda_nm, c
       if (m.kind == MAT_SLAB) {
         double cos_i = std::fabs(dot(d, s.nrm[t]));
         double Rs, Ts;
-        slab_RT(cos_i, m.n[lam], m.k[lam], m.thickness, lambda_nm, &Rs, &Ts);
+        slab_RT(cos_i, m.n[lam], m.k[lam], m.thickness, lambda_nm, &Rs, &Ts, s.slab_pol);
         T *= Ts;
       } else if (m.kind == MAT_TILE) {
         // one brute-force ray through the tile: it counts only if it leaves on the far side
@@ -731,7 +750,7 @@ double trace_split(const RenderCtx& cx, V3 o, V3 d, double seg0, int vertex, int
     }
     case MAT_SLAB: {
       double Rs, Ts;
-      slab_RT(cos_i, m.n[lam], m.k[lam], m.thickness, lambda, &Rs, &Ts);
+      slab_RT(cos_i, m.n[lam], m.k[lam], m.thickness, lambda, &Rs, &Ts, s.slab_pol);
       V3 dr = reflect(d, nf);
       return Rs * trace_split(cx, offset(s, p, ng, dr), dr, seg0_of(s, ng, dr), v, lam) +
              Ts * trace_split(cx, offset(s, p, ng, d), d, seg0_of(s, ng, d), v, lam);
@@ -804,7 +823,7 @@ double trace_mc(const RenderCtx& cx, uint32_t px, uint32_t sample, int lam, uint
       sun_counted = false;
     } else if (m.kind == MAT_SLAB) {
       double Rs, Ts;
-      slab_RT(cos_i, m.n[lam], m.k[lam], m.thickness, lambda, &Rs, &Ts);
+      slab_RT(cos_i, m.n[lam], m.k[lam], m.thickness, lambda, &Rs, &Ts, s.slab_pol);
       double P = Rs / (Rs + Ts);
       thr *= (Rs + Ts);
       if (u.u[0] < P) {
@@ -896,8 +915,8 @@ void orc_fresnel(int n, const double* cos_i, const double* n1, const double* n2_
 
 // Thin-slab reflectance and transmittance (air on both sides).
 void orc_slab(int n, const double* cos_i, const double* nre, const double* k, const double* d_m,
-              const double* lambda_nm, double* R_slab, double* T_slab) {
-  for (int i = 0; i < n; ++i) slab_RT(cos_i[i], nre[i], k[i], d_m[i], lambda_nm[i], R_slab + i, T_slab + i);
+              const double* lambda_nm, int pol, double* R_slab, double* T_slab) {
+  for (int i = 0; i < n; ++i) slab_RT(cos_i[i], nre[i], k[i], d_m[i], lambda_nm[i], R_slab + i, T_slab + i, pol);
 }
 
 double orc_beer_lambert(double k, double len_m, double lambda_nm) {
@@ -947,6 +966,7 @@ struct OrcScene {
   const int32_t* mat_tile;    // [M] tile index of HETERO_TILE materials, -1 otherwise (or NULL)
   int tile_grid;
   double tile_size;
+  int slab_polarisation;      // 0: thin-slab series on the unpolarised R; 1: per polarisation
 };
 
 struct OrcTile {
@@ -1013,6 +1033,7 @@ void* orc_scene_create(const OrcScene* d) {
   double ha = d->sun_half_angle;
   s.sun_h = (d->sun && ha > 0.0) ? 2.0 * std::sin(0.5 * ha) * std::sin(0.5 * ha) : 0.0;
   s.eps = d->ray_eps;
+  s.slab_pol = d->slab_polarisation;
   std::vector<int> idx(d->n_triangles);
   std::vector<V3> cen(d->n_triangles);
   for (int t = 0; t < d->n_triangles; ++t) {

@@ -55,6 +55,7 @@ class SceneData:
     mat_tile: np.ndarray | None = None  # int32 [M] tile index of HETERO_TILE materials, -1 otherwise
     tile_grid: int = 64
     tile_size: float = 0.1
+    slab_polarisation: int = 0    # thin slabs: 0 series on the unpolarised R, 1 per polarisation
 
     @property
     def n_triangles(self) -> int:

@@ -454,3 +454,68 @@ def test_philox_matches_independent_library_implementation(orc, tmp_path):
     ref = np.load(outp).reshape(n, 4)
     mine = np.vstack([orc.philox(ctr[i], keys[i]) for i in range(n)])
     assert np.array_equal(mine, ref)
+
+
+# ----------------------------------------------------------------------------- polarisation (Sec. 2, Eq. 1)
+def _pol_slab_by_bounce_sums(theta, n, k, d, lam):
+    """Per-polarisation slab: the bounce sum run on R_s and on R_p, then averaged."""
+    _, Rs, Rp = fresnel_real_form(theta, n, k)
+    cos_t = math.sqrt(1.0 - (math.sin(theta) / n) ** 2)
+    tau = math.exp(-4.0 * math.pi * k * d / cos_t / (lam * 1e-9))
+    (Rss, Tss), (Rsp, Tsp) = slab_by_bounce_sum(Rs, tau), slab_by_bounce_sum(Rp, tau)
+    return 0.5 * (Rss + Rsp), 0.5 * (Tss + Tsp)
+
+
+@pytest.mark.parametrize("n,k", [(1.52, 0.0), (1.53, 2e-6), (1.58, 4e-5)])
+def test_slab_per_polarisation_against_bounce_sums(orc, n, k):
+    d, lam = 3.5e-3, 520.0
+    thetas = np.radians([0.0, 20.0, 45.0, 56.7, 70.0, 85.0, 89.0])
+    R1, T1 = orc.slab(np.cos(thetas), n, k, d, lam, pol=1)
+    for i, th in enumerate(thetas):
+        r, t = _pol_slab_by_bounce_sums(th, n, k, d, lam)
+        assert abs(R1[i] - r) < 1e-12 and abs(T1[i] - t) < 1e-12, (th, R1[i], r, T1[i], t)
+    R0, T0 = orc.slab(np.cos(thetas), n, k, d, lam, pol=0)
+    assert np.all(np.abs(R1 - R0) <= 0.5 * np.abs(R1 + R0))  # the same order of magnitude
+    assert abs(R0[0] - R1[0]) < 1e-15 and abs(T0[0] - T1[0]) < 1e-15   # s = p at normal incidence
+    assert abs(T1[4] / T0[4] - 1.0) > 3e-3                             # and they differ obliquely
+
+
+def test_slab_per_polarisation_lossless_and_brewster(orc):
+    """k = 0: R + T = 1 for each polarisation, so for the average too.  At Brewster's angle
+    R_p = 0, so the p slab transmits everything and T = ((1 - Rs) / (1 + Rs) + 1) / 2 with
+    Rs = ((n^2 - 1) / (n^2 + 1))^2 (lossless slab: T = (1 - R) / (1 + R))."""
+    n = 1.52
+    c = np.linspace(1e-3, 1.0, 101)  # (exact grazing incidence, cos = 0, makes the series 0 / 0)
+    R, T = orc.slab(c, n, 0.0, 3e-3, 550.0, pol=1)
+    assert np.allclose(R + T, 1.0, atol=1e-14)
+    tb = math.atan(n)
+    Rs = ((n * n - 1) / (n * n + 1)) ** 2
+    _, Tb = orc.slab(math.cos(tb), n, 0.0, 3e-3, 550.0, pol=1)
+    assert abs(float(Tb) - 0.5 * ((1 - Rs) / (1 + Rs) + 1.0)) < 1e-14
+    _, Tb0 = orc.slab(math.cos(tb), n, 0.0, 3e-3, 550.0, pol=0)
+    assert float(Tb) > float(Tb0) + 1e-3
+
+
+@pytest.mark.parametrize("theta_deg", [30.0, 60.0, 80.0])
+def test_scene_slab_polarisation_flag(orc, theta_deg):
+    """A horizontal thin slab under an upper-hemisphere sky, seen obliquely from above: the
+    reflected ray sees the sky (1), the transmitted one the dark lower hemisphere (0), so the
+    deterministic pixel is R_slab(theta) -- per polarisation when the scene asks for it."""
+    n, k, d, lam = 1.55, 3e-6, 4e-3, 600.0
+    tris = quad((-5, -5, 0), (5, -5, 0), (5, 5, 0), (-5, 5, 0), 0)
+    th = math.radians(theta_deg)
+    cam = S.CameraData(pos=(0.0, -math.sin(th), math.cos(th)), look_at=(0.0, 0.0, 0.0), up=(0.0, 0.0, 1.0),
+                       vfov_deg=1.0, width=2, height=2, ortho=1, ortho_height=0.01)
+    spec = S.RenderSpec(lambda_nm=np.array([lam], np.float32), spp=1, seed=0, max_depth=4, mode=0)
+    f32 = lambda x: float(np.float32(x))  # noqa: E731
+    for pol in (0, 1):
+        sc = custom_scene(tris, [{"kind": S.MAT_SLAB, "n": n, "k": k, "d": d}], sky_mode=1, lam=lam)
+        sc.slab_polarisation = pol
+        film, _, _ = orc.OracleScene(sc).render(cam, spec)
+        if pol:
+            want, _ = _pol_slab_by_bounce_sums(th, f32(n), f32(k), f32(d), lam)
+        else:
+            R, _, _ = fresnel_real_form(th, f32(n), f32(k))
+            cos_t = math.sqrt(1.0 - (math.sin(th) / f32(n)) ** 2)
+            want, _ = slab_by_bounce_sum(R, math.exp(-4 * math.pi * f32(k) * f32(d) / cos_t / (lam * 1e-9)))
+        assert np.allclose(film, want, rtol=1e-6, atol=0), (pol, film.ravel(), want)  # float32 camera
