@@ -102,6 +102,10 @@ typedef struct {
   const sdd_tileset* tiles; /* tile set of the HETERO_TILE materials (tile_param_id indexes it), or
                                NULL; must outlive the scene.  A tile's front face is on the +n side
                                of its triangles' geometric normal, its frame the normal's Duff basis */
+  int slab_polarisation;    /* THIN_SLAB series (Sec. 2, Eq. 1): 0 = one incoherent series on the
+                               unpolarised interface reflectance (R_s + R_p) / 2; 1 = s and p light do
+                               not mix at the slab's parallel faces, so the series runs on R_s and on
+                               R_p separately and the results are averaged.  Other values: SDD_ERR_ARG */
 } sdd_scene_desc;
 
 typedef struct {
@@ -380,11 +384,12 @@ sdd_status sdd_trace_closest_noalloc(sdd_scene* scene, int n, const float* org_d
 
 /* Spectral material module on its own (for tests): for n queries with device arrays
  * cos_i, n, k, thickness_m, lambda_nm writes the single-interface reflectance R (air ->
- * n + ik), and the thin-slab reflectance / transmittance.  FP32, with the FP64 branch near
- * grazing incidence exactly as the renderer uses them. */
+ * n + ik), and the thin-slab reflectance / transmittance with the series of slab_polarisation
+ * (as in sdd_scene_desc).  FP32, with the FP64 branch near grazing incidence exactly as the
+ * renderer uses them. */
 sdd_status sdd_eval_optics(int n, const float* cos_i, const float* n_re, const float* k,
-                           const float* thickness_m, const float* lambda_nm, float* R_out,
-                           float* R_slab_out, float* T_slab_out, void* cuda_stream);
+                           const float* thickness_m, const float* lambda_nm, int slab_polarisation,
+                           float* R_out, float* R_slab_out, float* T_slab_out, void* cuda_stream);
 
 /* Philox4x32-10 as the renderer draws it: out[i] = philox(ctr[i], key) for device uint32
  * arrays ctr [n][4] and out [n][4]. */

@@ -97,6 +97,7 @@ struct sdd_scene {
   float sun_dir[3] = {0, 0, 1};
   float sun_half = 0.f;
   float eps = 1e-5f;
+  int slab_pol = 0;
   // heterogeneous tiles
   const sdd_tileset* tiles = nullptr;
   std::vector<int> mat_tile;           // tile index per material, -1 otherwise
@@ -599,7 +600,7 @@ sdd_status render_batched(sdd_scene* s, const RenderParams& p, const std::vector
   int grid = 0;
   GraphGrids gg{};
   if (form == 2) {
-    gg = graph_grids(p);  // occupancy queries stay outside the capture
+    gg = graph_grids(p, s->tuning.top_nodes);  // occupancy queries stay outside the capture
   } else {
     grid = persistent_grid(p.stats >= 2, tile_mode(p), p.bundle > 1);
     if (grid <= 0) return fail(SDD_ERR_CUDA, "persistent kernel does not fit on this device");
@@ -849,6 +850,7 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
   p.sp.sky = s->t_sky.p;
   p.sp.sun = s->t_sun.p;
   p.sp.sky_mode = s->sky_mode;
+  p.sp.slab_pol = s->slab_pol;
   {
     double sd[3] = {s->sun_dir[0], s->sun_dir[1], s->sun_dir[2]};
     double l = std::sqrt(sd[0] * sd[0] + sd[1] * sd[1] + sd[2] * sd[2]);
@@ -1154,6 +1156,11 @@ sdd_status sdd_scene_create(const sdd_scene_desc* d, sdd_scene** out) {
   if (axis < 0) axis = (hi[0] - lo[0] >= hi[1] - lo[1] && hi[0] - lo[0] >= hi[2] - lo[2]) ? 0
                        : (hi[1] - lo[1] >= hi[2] - lo[2] ? 1 : 2);
   s->eps = d->ray_epsilon_m > 0.f ? d->ray_epsilon_m : (float)std::max(1e-5, 2e-6 * amax);
+  if (d->slab_polarisation != 0 && d->slab_polarisation != 1) {
+    delete s;
+    return fail(SDD_ERR_ARG, "slab_polarisation must be 0 or 1");
+  }
+  s->slab_pol = d->slab_polarisation;
   BuildInput in;
   in.verts = d->vertices;
   in.idx = d->indices;
@@ -1352,12 +1359,13 @@ sdd_status sdd_trace_closest(sdd_scene* s, int n, const float* org, const float*
 }
 
 sdd_status sdd_eval_optics(int n, const float* cos_i, const float* n_re, const float* k, const float* d,
-                           const float* lam, float* R, float* Rs, float* Ts, void* stream) {
+                           const float* lam, int slab_polarisation, float* R, float* Rs, float* Ts, void* stream) {
   g_err.clear();
   if (n < 0 || (n > 0 && (!cos_i || !n_re || !k || !d || !lam || !R || !Rs || !Ts))) return fail(SDD_ERR_ARG, "bad arguments");
+  if (slab_polarisation != 0 && slab_polarisation != 1) return fail(SDD_ERR_ARG, "slab_polarisation must be 0 or 1");
   if (n == 0) return SDD_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  launch_eval_optics(n, cos_i, n_re, k, d, lam, R, Rs, Ts, st);
+  launch_eval_optics(n, cos_i, n_re, k, d, lam, slab_polarisation, R, Rs, Ts, st);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));
   return SDD_OK;

@@ -212,7 +212,7 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
           for (uint32_t m = mask; m; m &= m - 1) {
             int b = __ffs(m) - 1;
             float Rs, Ts;
-            slab_RT(cos_i, __ldg(mn + b), __ldg(mk + b), thick, __ldg(p.sp.lambda_nm + lam0 + b), &Rs, &Ts);
+            slab_RT(cos_i, __ldg(mn + b), __ldg(mk + b), thick, __ldg(p.sp.lambda_nm + lam0 + b), &Rs, &Ts, p.sp.slab_pol);
             float P = Rs / (Rs + Ts);
             wr[b] = wr[b] * (Rs + Ts);
             gm[u.x < P ? 0 : 1] |= 1u << b;
@@ -423,7 +423,7 @@ __device__ __forceinline__ void dev_shadow_bundle(const RenderParams& p, const W
         int b = __ffs(m) - 1;
         float Rs, Ts;
         slab_RT(cos_i, __ldg(p.sp.mat_n + m0 + b), __ldg(p.sp.mat_k + m0 + b), thick,
-                __ldg(p.sp.lambda_nm + lam0 + b), &Rs, &Ts);
+                __ldg(p.sp.lambda_nm + lam0 + b), &Rs, &Ts, p.sp.slab_pol);
         c[b] *= Ts;
       }
       return false;

@@ -68,9 +68,9 @@ __device__ __forceinline__ cf csqrt(cf z) {
   return {fabsf(z.im) / (2.f * fabsf(im)), im};
 }
 
-// Unpolarised Fresnel reflectance from a medium of real index n1 into one of complex index
-// n2 = (n2re, n2im): mean of |r_s|^2 and |r_p|^2, cos(theta_t) from the complex Snell law.
-__device__ __forceinline__ float fresnel_R(float cos_i, float n1, float n2re, float n2im) {
+// Fresnel reflectances |r_s|^2 and |r_p|^2 from a medium of real index n1 into one of
+// complex index n2 = (n2re, n2im) (Eq. 1), cos(theta_t) from the complex Snell law.
+__device__ __forceinline__ float2 fresnel_RsRp(float cos_i, float n1, float n2re, float n2im) {
   float sin2 = fmaxf(0.f, 1.f - cos_i * cos_i);
   cf n2 = {n2re, n2im};
   cf eta = cdiv_real(n1, n2);
@@ -82,11 +82,16 @@ __device__ __forceinline__ float fresnel_R(float cos_i, float n1, float n2re, fl
   cf n2ci = {n2re * cos_i, n2im * cos_i};
   cf n1ct = {n1 * cos_t.re, n1 * cos_t.im};
   float Rp = cnorm(csub(n2ci, n1ct)) / cnorm(cadd(n2ci, n1ct));
-  return 0.5f * (Rs + Rp);
+  return make_float2(Rs, Rp);
+}
+// Unpolarised reflectance: the mean of the two.
+__device__ __forceinline__ float fresnel_R(float cos_i, float n1, float n2re, float n2im) {
+  const float2 r = fresnel_RsRp(cos_i, n1, n2re, n2im);
+  return 0.5f * (r.x + r.y);
 }
 
 // The same in FP64 (near-grazing branch).
-__device__ __forceinline__ double fresnel_R_f64(double cos_i, double n1, double n2re, double n2im) {
+__device__ __forceinline__ double2 fresnel_RsRp_f64(double cos_i, double n1, double n2re, double n2im) {
   double sin2 = fmax(0.0, 1.0 - cos_i * cos_i);
   double den = n2re * n2re + n2im * n2im;
   double er = n1 * n2re / den, ei = -n1 * n2im / den;           // eta = n1 / n2
@@ -107,7 +112,7 @@ __device__ __forceinline__ double fresnel_R_f64(double cos_i, double n1, double 
   double Rs = ((a1 - ar) * (a1 - ar) + ai * ai) / ((a1 + ar) * (a1 + ar) + ai * ai);
   double br = n2re * cos_i, bi = n2im * cos_i, cr = n1 * ctr, ci = n1 * cti;
   double Rp = ((br - cr) * (br - cr) + (bi - ci) * (bi - ci)) / ((br + cr) * (br + cr) + (bi + ci) * (bi + ci));
-  return 0.5 * (Rs + Rp);
+  return make_double2(Rs, Rp);
 }
 
 constexpr float kFourPi = 12.566370614359172f;
@@ -115,28 +120,55 @@ constexpr float kGrazingCos = 0.0625f;  // below this cosine the slab series run
 
 // Thin slab (air / glass / air): incoherent sum over internal reflections.
 //   R_slab = R + (1-R)^2 R tau^2 / (1 - R^2 tau^2),  T_slab = (1-R)^2 tau / (1 - R^2 tau^2)
-// with tau = exp(-4 pi k d / (lambda cos theta_t)).
-__device__ __forceinline__ void slab_RT(float cos_i, float n, float k, float d, float lambda_nm,
-                                        float* Rs_out, float* Ts_out) {
-  if (cos_i < kGrazingCos) {
-    double ci = cos_i;
-    double R = fresnel_R_f64(ci, 1.0, n, k);
-    double sin2t = (1.0 - ci * ci) / ((double)n * n);
-    double cos_t = sqrt(1.0 - sin2t);
-    double tau = exp(-12.566370614359172 * (double)k * (double)d / ((double)lambda_nm * 1e-9 * cos_t));
-    double den = (1.0 - R * tau) * (1.0 + R * tau);
-    *Rs_out = (float)(R + (1.0 - R) * (1.0 - R) * R * tau * tau / den);
-    *Ts_out = (float)((1.0 - R) * (1.0 - R) * tau / den);
-    return;
-  }
-  float R = fresnel_R(cos_i, 1.f, n, k);
-  float sin2t = (1.f - cos_i * cos_i) / (n * n);
-  float cos_t = sqrtf(1.f - sin2t);
-  float tau = expf(-kFourPi * k * d / (lambda_nm * 1e-9f * cos_t));
+// with tau = exp(-4 pi k d / (lambda cos theta_t)).  pol = 0: one series on the unpolarised
+// interface reflectance (R_s + R_p) / 2; pol = 1: s and p light do not mix at the parallel
+// faces, so the series runs on R_s and on R_p and the two results are averaged.
+__device__ __forceinline__ void slab_series(float R, float tau, float* Rs_out, float* Ts_out) {
   float omr = 1.f - R, rt = R * tau;
   float den = (1.f - rt) * (1.f + rt);
   *Rs_out = R + omr * omr * R * tau * tau / den;
   *Ts_out = omr * omr * tau / den;
+}
+__device__ __forceinline__ void slab_series_f64(double R, double tau, double* Rs_out, double* Ts_out) {
+  double den = (1.0 - R * tau) * (1.0 + R * tau);
+  *Rs_out = R + (1.0 - R) * (1.0 - R) * R * tau * tau / den;
+  *Ts_out = (1.0 - R) * (1.0 - R) * tau / den;
+}
+__device__ __forceinline__ void slab_RT(float cos_i, float n, float k, float d, float lambda_nm,
+                                        float* Rs_out, float* Ts_out, int pol = 0) {
+  if (cos_i < kGrazingCos) {
+    double ci = cos_i;
+    const double2 rsp = fresnel_RsRp_f64(ci, 1.0, n, k);
+    double sin2t = (1.0 - ci * ci) / ((double)n * n);
+    double cos_t = sqrt(1.0 - sin2t);
+    double tau = exp(-12.566370614359172 * (double)k * (double)d / ((double)lambda_nm * 1e-9 * cos_t));
+    double Rsl, Tsl;
+    if (pol == 0) {
+      slab_series_f64(0.5 * (rsp.x + rsp.y), tau, &Rsl, &Tsl);
+    } else {
+      double R1, T1, R2, T2;
+      slab_series_f64(rsp.x, tau, &R1, &T1);
+      slab_series_f64(rsp.y, tau, &R2, &T2);
+      Rsl = 0.5 * (R1 + R2);
+      Tsl = 0.5 * (T1 + T2);
+    }
+    *Rs_out = (float)Rsl;
+    *Ts_out = (float)Tsl;
+    return;
+  }
+  const float2 rsp = fresnel_RsRp(cos_i, 1.f, n, k);
+  float sin2t = (1.f - cos_i * cos_i) / (n * n);
+  float cos_t = sqrtf(1.f - sin2t);
+  float tau = expf(-kFourPi * k * d / (lambda_nm * 1e-9f * cos_t));
+  if (pol == 0) {
+    slab_series(0.5f * (rsp.x + rsp.y), tau, Rs_out, Ts_out);
+    return;
+  }
+  float R1, T1, R2, T2;
+  slab_series(rsp.x, tau, &R1, &T1);
+  slab_series(rsp.y, tau, &R2, &T2);
+  *Rs_out = 0.5f * (R1 + R2);
+  *Ts_out = 0.5f * (T1 + T2);
 }
 
 // Beer-Lambert transmittance over `len` metres.

@@ -174,7 +174,8 @@ __device__ __forceinline__ bool shadow_surface(const RenderParams& p, const DevS
   if (kind == MAT_SLAB) {
     float cos_i = fabsf(dot3(d, f3(nm)));
     float Rs, Ts;
-    slab_RT(cos_i, __ldg(sp.mat_n + mi), __ldg(sp.mat_k + mi), __ldg(sp.mat_thick + mat), lambda_nm, &Rs, &Ts);
+    slab_RT(cos_i, __ldg(sp.mat_n + mi), __ldg(sp.mat_k + mi), __ldg(sp.mat_thick + mat), lambda_nm, &Rs, &Ts,
+            sp.slab_pol);
     *T *= Ts;
     return false;
   }
@@ -649,7 +650,7 @@ __device__ __forceinline__ void dev_shade(const RenderParams& p, const WaveDesc&
         } else if (kind == MAT_SLAB) {
           float Rs, Ts;
           slab_RT(cos_i, __ldg(p.sp.mat_n + mi), __ldg(p.sp.mat_k + mi), __ldg(p.sp.mat_thick + mat), lambda, &Rs,
-                  &Ts);
+                  &Ts, p.sp.slab_pol);
           float3 dr = reflect3(d, nf);
           uint32_t fl_r = flags & ~FLAG_SUN_COUNTED;
           if (!mc) {

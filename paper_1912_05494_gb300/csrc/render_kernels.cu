@@ -183,11 +183,11 @@ __global__ void k_hits_to_arrays(int n, const float2* hits, float* t_out, int32_
 }
 
 __global__ void k_eval_optics(int n, const float* cos_i, const float* n_re, const float* k, const float* d,
-                              const float* lam, float* R, float* Rs, float* Ts) {
+                              const float* lam, int pol, float* R, float* Rs, float* Ts) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float a, b;
-  slab_RT(cos_i[i], n_re[i], k[i], d[i], lam[i], &a, &b);
+  slab_RT(cos_i[i], n_re[i], k[i], d[i], lam[i], &a, &b, pol);
   R[i] = fresnel_R(cos_i[i], 1.f, n_re[i], k[i]);
   Rs[i] = a;
   Ts[i] = b;
@@ -304,8 +304,8 @@ void launch_hits_to_arrays(int n, const float2* hits, float* t_out, int32_t* pri
 }
 
 void launch_eval_optics(int n, const float* cos_i, const float* n_re, const float* k, const float* d,
-                        const float* lam, float* R, float* Rs, float* Ts, cudaStream_t st) {
-  k_eval_optics<<<blocks_for(n, 256), 256, 0, st>>>(n, cos_i, n_re, k, d, lam, R, Rs, Ts);
+                        const float* lam, int pol, float* R, float* Rs, float* Ts, cudaStream_t st) {
+  k_eval_optics<<<blocks_for(n, 256), 256, 0, st>>>(n, cos_i, n_re, k, d, lam, pol, R, Rs, Ts);
 }
 
 void launch_philox(int n, const uint32_t* ctr, uint64_t key, uint32_t* out, cudaStream_t st) {

@@ -49,7 +49,7 @@ void launch_rays_from_arrays(int n, const float* org, const float* dir, const De
                              int* q_count, int qcap, cudaStream_t st);
 void launch_hits_to_arrays(int n, const float2* hits, float* t_out, int32_t* prim_out, cudaStream_t st);
 void launch_eval_optics(int n, const float* cos_i, const float* n_re, const float* k, const float* d,
-                        const float* lam, float* R, float* Rs, float* Ts, cudaStream_t st);
+                        const float* lam, int pol, float* R, float* Rs, float* Ts, cudaStream_t st);
 void launch_philox(int n, const uint32_t* ctr, uint64_t key, uint32_t* out, cudaStream_t st);
 
 }  // namespace sdd

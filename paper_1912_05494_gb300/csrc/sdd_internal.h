@@ -73,6 +73,7 @@ struct DevSpectral {
   float3 sun_dir;
   float sun_h;               // 1 - cos(half angle); 0 = no sun
   float sun_omega;           // solid angle of the disc
+  int slab_pol;              // thin-slab series: 0 on the unpolarised R, 1 per polarisation
 };
 
 struct DevCamera {

@@ -46,7 +46,7 @@ class sdd_scene_desc(C.Structure):
                 ("indices", C.c_void_p), ("material_of_triangle", C.c_void_p),
                 ("n_materials", C.c_int), ("materials", C.c_void_p), ("illum", sdd_illuminant),
                 ("n_subdomains", C.c_int), ("split_axis", C.c_int), ("ray_epsilon_m", C.c_float),
-                ("tiles", C.c_void_p)]
+                ("tiles", C.c_void_p), ("slab_polarisation", C.c_int)]
 
 
 class sdd_camera(C.Structure):
@@ -121,7 +121,7 @@ def lib():
         L.sdd_scene_get_info.argtypes = [vp, C.POINTER(sdd_scene_info)]
         L.sdd_trace_closest.argtypes = [vp, i32, vp, vp, vp, vp, vp]
         L.sdd_trace_closest_noalloc.argtypes = [vp, i32, vp, vp, vp, vp, vp]
-        L.sdd_eval_optics.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.sdd_eval_optics.argtypes = [i32, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp]
         L.sdd_philox.argtypes = [i32, vp, C.c_uint64, vp, vp]
         L.sdd_tileset_create.argtypes = [C.POINTER(sdd_tileset_desc), C.POINTER(vp)]
         L.sdd_tileset_destroy.argtypes = [vp]
@@ -233,6 +233,7 @@ def sdd_scene_create(sd, n_subdomains=None, split_axis=None, ray_epsilon_m=None,
     d.split_axis = int(sd.split_axis if split_axis is None else split_axis)
     d.ray_epsilon_m = float(sd.ray_eps if ray_epsilon_m is None else ray_epsilon_m)
     d.tiles = tileset
+    d.slab_polarisation = int(getattr(sd, "slab_polarisation", 0))
     h = C.c_void_p()
     _check(lib().sdd_scene_create(C.byref(d), C.byref(h)))
     return h
@@ -344,10 +345,10 @@ def sdd_trace_closest_noalloc(h, org, dirs, t_out, prim_out, stream=None):
                                            _stream(stream)))
 
 
-def sdd_eval_optics(cos_i, n_re, k, d, lam, R, Rs, Ts, stream=None):
+def sdd_eval_optics(cos_i, n_re, k, d, lam, R, Rs, Ts, stream=None, slab_polarisation=0):
     n = int(cos_i.numel())
-    _check(lib().sdd_eval_optics(n, _ptr(cos_i), _ptr(n_re), _ptr(k), _ptr(d), _ptr(lam), _ptr(R), _ptr(Rs),
-                                 _ptr(Ts), _stream(stream)))
+    _check(lib().sdd_eval_optics(n, _ptr(cos_i), _ptr(n_re), _ptr(k), _ptr(d), _ptr(lam), int(slab_polarisation),
+                                 _ptr(R), _ptr(Rs), _ptr(Ts), _stream(stream)))
 
 
 def sdd_philox(ctr, key: int, out, stream=None):

@@ -60,3 +60,37 @@ def test_bad_scene_descriptions_are_rejected(lib):
     bad3.table_nm = sc.table_nm[::-1].copy()
     with pytest.raises(lib.SddError, match="ascending"):
         lib.sdd_scene_create(bad3)
+
+
+def declared_arity():
+    """Parameter count of every function include/sdd.h declares."""
+    text = open(os.path.join(ROOT, "include", "sdd.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(sdd_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", text):
+        params = m.group(2).strip()
+        out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_argument_counts_match_the_header(lib):
+    """Every ctypes declaration of the binding takes as many arguments as the C declaration."""
+    L = lib.lib()
+    arity = declared_arity()
+    assert len(arity) >= 30
+    checked = 0
+    for name, n in arity.items():
+        f = getattr(L, name)
+        if f.argtypes is not None:
+            assert len(f.argtypes) == n, (name, len(f.argtypes), n)
+            checked += 1
+    assert checked >= 25
+
+
+def test_bad_slab_polarisation_is_rejected(lib):
+    from paper_1912_05494_gb300 import scenes as S
+    sc, _, _ = S.slab_scene(0)
+    bad = S.SceneData(**{**sc.__dict__})
+    bad.slab_polarisation = 2
+    with pytest.raises(lib.SddError, match="slab_polarisation"):
+        lib.sdd_scene_create(bad)
