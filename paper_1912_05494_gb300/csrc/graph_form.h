@@ -9,8 +9,9 @@ namespace sdd {
 // query them before a stream capture begins.
 struct GraphGrids {
   int traverse, shade, shadow;
+  int top_nodes;  // BVH nodes per subdomain the traversal stages in shared memory (0: none)
 };
-GraphGrids graph_grids(const RenderParams& p);
+GraphGrids graph_grids(const RenderParams& p, int top_nodes);
 
 // work: the pass's chunk counter, zero before the pass
 cudaError_t launch_traverse_g(const RenderParams& p, const GraphGrids& g, const int* counts_in, int* work,

@@ -24,29 +24,48 @@ namespace sdd {
 
 namespace {
 
-// Next chunk of a pass for this block from the pass's work counter (zeroed before the pass):
-// blocks take chunks as they finish, so the pass's cost balances over the grid as when every
-// chunk is its own block.  Returns a value >= total when the pass is done.
-__device__ __forceinline__ int next_chunk(int* work) {
-  __shared__ int s_chunk;
-  __syncthreads();
-  if (threadIdx.x == 0) s_chunk = atomicAdd(work, kChunk);
-  __syncthreads();
-  return s_chunk;
+constexpr int kWarpChunk = 32;  // rays a warp takes from the pass's work counter at a time
+
+// Next 32-ray chunk of a pass for this warp from the pass's work counter (zeroed before the
+// pass): warps take chunks as they finish, each on its own (no block barrier, so a warp
+// never waits for the slowest warp of its block), and the pass's cost balances over the
+// grid.  The per-subdomain layout is padded to 128-ray chunks, so a 32-ray chunk never
+// straddles two subdomains and the warp enters the walk converged.  Returns a value >= total
+// when the pass is done.
+__device__ __forceinline__ int next_warp_chunk(int* work) {
+  int c = 0;
+  if ((threadIdx.x & 31) == 0) c = atomicAdd(work, kWarpChunk);
+  return __shfl_sync(0xFFFFFFFFu, c, 0);
 }
 
-// Closest-hit pass over the queues whose counts are counts_in.
+// Closest-hit pass over the queues whose counts are counts_in.  With top_nodes > 0 every
+// block first stages the top_nodes first (breadth-first: top-level) nodes of every
+// subdomain's BVH in shared memory (Sec. 5: the top of the hierarchy first).
 template <bool kStats>
 __global__ void __launch_bounds__(kChunk, 12) k_traverse_g(RenderParams p, const int* counts_in, int* work,
-                                                           QueuePair qp, RayBuf rb, float2* hits, Control* ctl) {
+                                                           int top_nodes, QueuePair qp, RayBuf rb, float2* hits,
+                                                           Control* ctl) {
   __shared__ int s_prefix[kMaxSubdomains + 1];
   __shared__ int s_count[kMaxSubdomains];
+  extern __shared__ Node s_top[];
   const int n_sub = p.sc.n_sub;
   const int total = load_prefix(counts_in, n_sub, qp.cap, s_prefix, s_count);
-  for (int c0 = next_chunk(work); c0 < total; c0 = next_chunk(work)) {
+  if (total == 0) return;
+  if (top_nodes > 0) {
+    for (int s = 0; s < n_sub; ++s) {
+      const int n = min(top_nodes, p.sc.n_nodes_sub[s]);
+      const float4* src = reinterpret_cast<const float4*>(p.sc.nodes + p.sc.root[s]);
+      float4* dst = reinterpret_cast<float4*>(s_top + (size_t)s * top_nodes);
+      for (int i = threadIdx.x; i < 4 * n; i += blockDim.x) dst[i] = __ldg(src + i);
+    }
+    __syncthreads();
+  }
+  const int lane = threadIdx.x & 31;
+  for (int c0 = next_warp_chunk(work); c0 < total; c0 = next_warp_chunk(work)) {
     const int s = find_subdomain(s_prefix, n_sub, c0);  // the whole chunk's subdomain
-    const int i = c0 - s_prefix[s] + (int)threadIdx.x;
-    dev_traverse_warp<kStats>(p, s, i, i < s_count[s], nullptr, 0, qp, rb, hits, ctl);
+    const int i = c0 - s_prefix[s] + lane;
+    const int n_staged = top_nodes > 0 ? min(top_nodes, p.sc.n_nodes_sub[s]) : 0;
+    dev_traverse_warp<kStats>(p, s, i, i < s_count[s], s_top + (size_t)s * top_nodes, n_staged, qp, rb, hits, ctl);
   }
 }
 
@@ -80,9 +99,10 @@ __global__ void __launch_bounds__(kChunk, kTM == 1 ? 1 : 8) k_shadow_g(RenderPar
   __shared__ int s_count[kMaxSubdomains];
   const int n_sub = p.sc.n_sub;
   const int total = load_prefix(counts_in, n_sub, qp.cap, s_prefix, s_count);
-  for (int c0 = next_chunk(work); c0 < total; c0 = next_chunk(work)) {
+  const int lane = threadIdx.x & 31;
+  for (int c0 = next_warp_chunk(work); c0 < total; c0 = next_warp_chunk(work)) {
     const int s = find_subdomain(s_prefix, n_sub, c0);
-    const int i = c0 - s_prefix[s] + (int)threadIdx.x;
+    const int i = c0 - s_prefix[s] + lane;
     const bool act = i < s_count[s];
     if constexpr (kBund) {
       dev_shadow_bundle<kStats, kTM, kTM == 1>(p, w, s, i, act, nullptr, 0, qp, sb, path_L, ctl);
@@ -115,20 +135,28 @@ __global__ void k_check_drained(const int* counts, int n_sub, Control* ctl) {
   if (s < n_sub && counts[s] > 0) atomicOr(&ctl->error, ERR_TIMEOUT);
 }
 
-// Resident blocks x SMs of a kernel, queried once per kernel.
-int grid_of(const void* fn, int block) {
+// Resident blocks x SMs of a kernel at a dynamic shared-memory size, queried once each.
+int grid_of(const void* fn, int block, size_t smem = 0) {
   static std::mutex m;
-  static std::unordered_map<const void*, int> cache;
+  static std::unordered_map<const void*, std::unordered_map<size_t, int>> cache;
   std::lock_guard<std::mutex> lk(m);
-  auto it = cache.find(fn);
-  if (it != cache.end()) return it->second;
+  auto& c = cache[fn];
+  auto it = c.find(smem);
+  if (it != c.end()) return it->second;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, block, smem);
   const int g = std::max(1, sms * per_sm);
-  cache[fn] = g;
+  c[smem] = g;
   return g;
+}
+
+// Shared memory of the staged top nodes: top_nodes per subdomain, within the 48 KB a block
+// may take without opting in (fewer nodes per subdomain when there are many subdomains).
+int staged_nodes(int n_sub, int top_nodes) {
+  const int cap = (48 * 1024) / (std::max(n_sub, 1) * (int)sizeof(Node));
+  return std::max(0, std::min(top_nodes, cap));
 }
 
 // The kernel of each step for a render's parameters.
@@ -168,14 +196,20 @@ cudaError_t launch_fn(const void* fn, int grid, int block, void** args, cudaStre
 
 }  // namespace
 
-GraphGrids graph_grids(const RenderParams& p) {
-  return GraphGrids{grid_of(traverse_fn(p), kChunk), grid_of(shade_fn(p), kBlock), grid_of(shadow_fn(p), kChunk)};
+GraphGrids graph_grids(const RenderParams& p, int top_nodes) {
+  const int tn = staged_nodes(p.sc.n_sub, top_nodes);
+  const size_t smem = (size_t)tn * p.sc.n_sub * sizeof(Node);
+  return GraphGrids{grid_of(traverse_fn(p), kChunk, smem), grid_of(shade_fn(p), kBlock),
+                    grid_of(shadow_fn(p), kChunk), tn};
 }
 
 cudaError_t launch_traverse_g(const RenderParams& p, const GraphGrids& g, const int* counts_in, int* work,
                               QueuePair qp, RayBuf rb, float2* hits, Control* ctl, cudaStream_t st) {
-  void* args[] = {(void*)&p, (void*)&counts_in, (void*)&work, (void*)&qp, (void*)&rb, (void*)&hits, (void*)&ctl};
-  return launch_fn(traverse_fn(p), g.traverse, kChunk, args, st);
+  int tn = g.top_nodes;
+  void* args[] = {(void*)&p, (void*)&counts_in, (void*)&work, (void*)&tn, (void*)&qp, (void*)&rb, (void*)&hits,
+                  (void*)&ctl};
+  const size_t smem = (size_t)tn * p.sc.n_sub * sizeof(Node);
+  return cudaLaunchKernel(traverse_fn(p), dim3(g.traverse), dim3(kChunk), args, smem, st);
 }
 
 cudaError_t launch_shade_g(const RenderParams& p, const GraphGrids& g, const WaveDesc& w, const int* n_in,
