@@ -1,5 +1,5 @@
-// surrogate_head.cuh -- the output head of the tile-BTDF network, shared by its training
-// loss (mlp.cu) and by the renderer that samples it (surrogate_render.cu).
+// surrogate_head.cuh -- the output head of the tile-BTDF network and its training loss,
+// shared by training (train_tc.cuh) and by the renderer that samples it (surrogate_render.cu).
 //
 // Of the network's 16 outputs z, eight are used:
 //   T = sigmoid(z0), R = sigmoid(z1)
@@ -53,6 +53,58 @@ __device__ __forceinline__ float lobe_mass_within(float w, float k1, float k2, f
   vmf_cdf(a, k1, &F1, &d);
   vmf_cdf(a, k2, &F2, &d);
   return w * F1 + (1.f - w) * F2;
+}
+
+// Training loss of one row and its gradient in the network outputs z (targets y: T, R, then
+// the tracer's deflection-bin fractions of each side): (T - y_T)^2 + (R - y_R)^2
+// + kLobeWeight [y_T KL(h_T | m_T) + y_R KL(h_R | m_R)], m a side's mixture mass per bin,
+// KL with kKlDelta added to both sides.  Returns the row's loss; g gets d loss / d z.
+__device__ __forceinline__ float head_loss_row(const float* z, const float* y, float* g) {
+  float l = 0.f;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) g[j] = 0.f;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {  // T, R
+    const float p = head_sigmoid(z[j]);
+    const float d = p - y[j];
+    l += d * d;
+    g[j] = 2.f * d * p * (1.f - p);
+  }
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const int jw = 2 + 3 * side;
+    const float wt = kLobeWeight * y[side];
+    const float w = head_sigmoid(z[jw]);
+    const float u1 = z[jw + 1] + kLkOffset1, u2 = z[jw + 2] + kLkOffset2;
+    const float k1 = expf(fminf(kLkMax, fmaxf(kLkMin, u1))), k2 = expf(fminf(kLkMax, fmaxf(kLkMin, u2)));
+    const float* h = y + 2 + side * kHeadBins;
+    float F1p = 0.f, F2p = 0.f, dF1p = 0.f, dF2p = 0.f;  // CDFs at the bin's lower edge
+    float gw = 0.f, gk1 = 0.f, gk2 = 0.f;
+    for (int b = 0; b < kHeadBins; ++b) {
+      float F1, F2, dF1, dF2;
+      if (b == kHeadBins - 1) {
+        F1 = F2 = 1.f;
+        dF1 = dF2 = 0.f;
+      } else {
+        const float a = head_bin_a(b + 1);
+        vmf_cdf(a, k1, &F1, &dF1);
+        vmf_cdf(a, k2, &F2, &dF2);
+      }
+      const float P1 = F1 - F1p, P2 = F2 - F2p;
+      const float m = w * P1 + (1.f - w) * P2;
+      const float hb = h[b];
+      l += wt * hb * (logf(hb + kKlDelta) - logf(m + kKlDelta));
+      const float gm = -wt * hb / (m + kKlDelta);
+      gw += gm * (P1 - P2);
+      gk1 += gm * w * (dF1 - dF1p);
+      gk2 += gm * (1.f - w) * (dF2 - dF2p);
+      F1p = F1; F2p = F2; dF1p = dF1; dF2p = dF2;
+    }
+    g[jw] = gw * w * (1.f - w);
+    g[jw + 1] = (u1 > kLkMin && u1 < kLkMax) ? gk1 * k1 : 0.f;
+    g[jw + 2] = (u2 > kLkMin && u2 < kLkMax) ? gk2 * k2 : 0.f;
+  }
+  return l;
 }
 
 }  // namespace sdd

@@ -1,6 +1,6 @@
-// surrogate_net.cuh -- the tile-BTDF network's shape, its BF16 warp-MMA building blocks (the
-// training kernels of mlp.cu), the feature map, and the policy interface of the fused
-// inference kernel (surrogate_tc.cuh).
+// surrogate_net.cuh -- the tile-BTDF network's shape, its activation and feature map, and the
+// policy interface of the fused inference kernel (surrogate_tc.cuh); the training kernels
+// are in train_tc.cuh.
 //
 // Network: Fourier features of the 7 normalised inputs (48 wide) -> 4 x 128 GELU -> 16, the
 // first 8 outputs mapped by the head of surrogate_head.cuh.  Parameters are one FP32 array,
@@ -29,59 +29,6 @@ __host__ __device__ constexpr int layer_offset(int l) {
   return o;
 }
 constexpr int kParams = layer_offset(kLayers);
-
-// ------------------------------------------------------------------ warp MMA helpers
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void ldmatrix_x4(uint32_t r[4], const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(smem_addr(p)));
-}
-__device__ __forceinline__ void ldmatrix_x2(uint32_t r[2], const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r[0]), "=r"(r[1]) : "r"(smem_addr(p)));
-}
-__device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], const uint32_t b[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-// acc[j] (j = n-tile of 8 columns) += A[16 rows of the warp][0..Kd) * Bt[cols][0..Kd)^T, with
-// A at sa (row stride lda elements) and Bt at sb (row stride ldb elements), both shared memory.
-// Accumulator layout (m16n8 fragment): acc[j][2h + e] is row (lane / 4) + 8 h, column
-// 8 j + 2 (lane % 4) + e.
-template <int Kd, int NT>
-__device__ __forceinline__ void warp_gemm(float (*acc)[4], const __nv_bfloat16* sa, int lda, const __nv_bfloat16* sb,
-                                          int ldb) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int kk = 0; kk < Kd; kk += 16) {
-    uint32_t a[4];
-    ldmatrix_x4(a, sa + (lane & 15) * lda + kk + (lane >> 4) * 8);
-#pragma unroll
-    for (int j = 0; j < NT; ++j) {
-      uint32_t b[2];
-      ldmatrix_x2(b, sb + (j * 8 + (lane & 7)) * ldb + kk + ((lane >> 3) & 1) * 8);
-      mma16816(acc[j], a, b);
-    }
-  }
-}
-
-// Copy a [rows][cols] BF16 tile (row-major, `cols` contiguous, cols % 8 == 0) into shared
-// memory with row stride ld; rows beyond `valid` are zero.
-__device__ __forceinline__ void load_tile(__nv_bfloat16* dst, int ld, const __nv_bfloat16* src, int src_ld, int rows,
-                                          int cols, int valid) {
-  const int vec = cols / 8;
-  for (int i = threadIdx.x; i < rows * vec; i += blockDim.x) {
-    int r = i / vec, c = (i - r * vec) * 8;
-    uint4 v = make_uint4(0, 0, 0, 0);
-    if (r < valid) v = *reinterpret_cast<const uint4*>(src + (size_t)r * src_ld + c);
-    *reinterpret_cast<uint4*>(dst + r * ld + c) = v;
-  }
-}
 
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float z) {
