@@ -197,13 +197,29 @@ sdd_status sdd_render_to_host(sdd_scene* scene, const sdd_camera* cam, const sdd
  *                   the wave size, 4x in deterministic mode, 2x with spectral bundles, and a
  *                   host-driven wave that needs more is rendered again as two halves).
  *                   Buffers keep their automatic size; with a bound set, a frame that needs
- *                   more returns SDD_ERR_QUEUE_OVERFLOW. */
+ *                   more returns SDD_ERR_QUEUE_OVERFLOW;
+ *   block_chunks:   graph form: how the fixed grid takes work from a pass's queues, bit 0 for
+ *                   the closest-hit passes, bit 1 for the shadow passes: 1 = each block takes
+ *                   128 rays at a time (its warps wait for each other), 0 = each warp takes 32
+ *                   (default 0 for both);
+ *   resident_subdomains: out-of-core subdomains (Sec. 5: sub-domains loaded according to the
+ *                   memory available, unloaded when few rays remain).  0 (default) or >=
+ *                   n_subdomains: every subdomain's BVH stays in device memory.  1 <= C <
+ *                   n_subdomains: the BVH moves to pinned host memory and at most C subdomains'
+ *                   nodes and triangle records occupy device memory at a time; before every
+ *                   traversal pass the C subdomains with the most queued rays are made resident
+ *                   (copied in, evicting those with the fewest), rays queued for the others wait.
+ *                   Images are bit-identical to the all-resident ones.  Host-driven form only:
+ *                   renders with batched != 0 and sdd_trace_closest_noalloc return SDD_ERR_STATE
+ *                   while it is on; sdd_trace_closest works.  Setting it synchronises the device. */
 typedef struct {
   int traverse_block;
   int top_nodes;
   int wave_paths;
   int no_graph;
   int queue_capacity;
+  int block_chunks;
+  int resident_subdomains;
 } sdd_tuning;
 sdd_status sdd_set_tuning(sdd_scene* scene, const sdd_tuning* tuning);
 sdd_status sdd_get_tuning(const sdd_scene* scene, sdd_tuning* out);
@@ -237,6 +253,8 @@ typedef struct {
   int64_t tile_shaded;     /* network form: tile hits shaded by the network (level >= 2) */
   int64_t wave_splits;     /* host-driven form: waves rendered again as two halves after their
                               rays outgrew the queues (spectral bundles that split often) */
+  int64_t subdomain_loads; /* out-of-core subdomains: subdomains copied into device slots */
+  int64_t bytes_streamed;  /* out-of-core subdomains: node and triangle bytes copied in */
 } sdd_stats;
 
 /* level 0: nothing; 1: CUDA-event timing of every launch; 2: also count BVH nodes and

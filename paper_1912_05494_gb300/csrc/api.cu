@@ -114,8 +114,23 @@ struct sdd_scene {
   DevArr<TriRec> tris;
   DevArr<float4> prim;
   DevScene dev{};
+  // out-of-core subdomains (sdd_tuning.resident_subdomains > 0): the BVH lives in pinned host
+  // memory and at most `cap` subdomains' nodes and triangle records occupy device slots
+  struct Streaming {
+    int cap = 0;
+    Node* h_nodes = nullptr;   // pinned host copy of every subdomain's nodes (absolute links)
+    TriRec* h_tris = nullptr;
+    int64_t n_nodes = 0, n_tris = 0;
+    std::vector<int> node0, nnodes, tri0, ntris;  // per subdomain ranges in the host arrays
+    int slot_nodes = 0, slot_tris = 0;            // capacity of one slot
+    DevArr<Node> d_nodes;      // cap slots
+    DevArr<TriRec> d_tris;
+    Node* stage_nodes = nullptr;  // pinned staging of the rebased copies, one area per slot
+    TriRec* stage_tris = nullptr;
+    std::vector<int> slot_of, sub_in_slot;  // subdomain -> slot, slot -> subdomain (-1: none)
+  } strm;
   int n_sub = 1, axis = 0, bvh_max_depth = 0;
-  int64_t n_refs = 0, n_nodes = 0;
+  int64_t n_refs = 0, n_nodes = 0, n_tri_recs = 0;
   // per-render spectral tables (cached for the last wavelength set)
   std::vector<float> cached_lambda;
   DevArr<float> t_lambda, t_thick, t_n, t_k, t_alb, t_sky, t_sun;
@@ -134,7 +149,7 @@ struct sdd_scene {
   DevArr<float> out_spec, out_xyz;
   Control* d_ctl = nullptr;
   Control* h_ctl = nullptr;
-  sdd_tuning tuning{128, 0, 0, 0};
+  sdd_tuning tuning{128, 0, 0, 0, 0, 0, 0};
   // batched form: persistent-wave bookkeeping, internal stream and the captured frame graph
   PersistCtl* d_pc = nullptr;
   cudaStream_t gstream = nullptr;
@@ -155,6 +170,12 @@ struct sdd_scene {
   ~sdd_scene() {
     DevArr<Node>* a[] = {&nodes};
     for (auto* x : a) x->release();
+    strm.d_nodes.release();
+    strm.d_tris.release();
+    cudaFreeHost(strm.h_nodes);
+    cudaFreeHost(strm.h_tris);
+    cudaFreeHost(strm.stage_nodes);
+    cudaFreeHost(strm.stage_tris);
     tris.release();
     prim.release();
     t_lambda.release(); t_thick.release(); t_n.release(); t_k.release(); t_alb.release();
@@ -223,6 +244,7 @@ struct sdd_scene {
 namespace sdd {
 // Used by the allocation-free entry point (noalloc.cu).
 const DevScene* scene_device_view(const sdd_scene* s) { return &s->dev; }
+bool scene_streaming(const sdd_scene* s) { return s->strm.cap > 0; }
 sdd_status set_last_error(sdd_status st, const char* msg) {
   g_err = msg;
   return st;
@@ -265,6 +287,107 @@ sdd_status device_error(uint32_t e) {
   return SDD_OK;
 }
 
+// ------------------------------------------------------------------ out-of-core subdomains
+// Sec. 5: sub-domains are loaded according to the memory available and unloaded when few
+// rays remain for them.  With streaming on (host-driven form), before every traversal pass the
+// (at most cap) subdomains with the most queued rays are made resident: a subdomain not in a
+// device slot takes the slot of a resident one that is left out (the one with the fewest
+// queued rays), its nodes and triangle records copied in from pinned host memory with their
+// links rebased to the slot.  Rays queued for subdomains left out wait, unchanged, for a
+// later pass.  The traversal code is the same; only where the nodes lie changes, so every
+// hit, path and image is the all-resident one bit for bit.
+
+// Copy subdomain `sub` into slot j (links rebased to the slot), enqueued on st.
+cudaError_t load_subdomain(sdd_scene* s, int sub, int j, cudaStream_t st) {
+  auto& m = s->strm;
+  Node* sn = m.stage_nodes + (size_t)j * m.slot_nodes;
+  TriRec* stri = m.stage_tris + (size_t)j * m.slot_tris;
+  const int n0 = m.node0[sub], nn = m.nnodes[sub], t0 = m.tri0[sub], nt = m.ntris[sub];
+  const int nbase = j * m.slot_nodes, tbase = j * m.slot_tris;
+  for (int i = 0; i < nn; ++i) {
+    Node nd = m.h_nodes[n0 + i];
+    int l0 = nd.d.x, l1 = nd.d.y;
+    if (nd.d.z > 0) l0 = l0 - t0 + tbase;        // leaf: triangle records
+    else if (l0 >= 0) l0 = l0 - n0 + nbase;      // inner child
+    if (nd.d.w > 0) l1 = l1 - t0 + tbase;
+    else if (l1 >= 0) l1 = l1 - n0 + nbase;
+    nd.d.x = l0;
+    nd.d.y = l1;
+    sn[i] = nd;
+  }
+  if (nt > 0) std::memcpy(stri, m.h_tris + t0, sizeof(TriRec) * (size_t)nt);
+  cudaError_t e = cudaMemcpyAsync(m.d_nodes.p + nbase, sn, sizeof(Node) * (size_t)nn, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && nt > 0)
+    e = cudaMemcpyAsync(m.d_tris.p + tbase, stri, sizeof(TriRec) * (size_t)nt, cudaMemcpyHostToDevice, st);
+  s->stats.bytes_streamed += (int64_t)(sizeof(Node) * (size_t)nn + sizeof(TriRec) * (size_t)nt);
+  s->stats.subdomain_loads++;
+  return e;
+}
+
+// Make the subdomains with the most queued rays resident (at most cap); runs[i] = the queued
+// count of a resident subdomain this pass traverses, 0 for the others.  sc gets the slots.
+sdd_status stream_in(sdd_scene* s, const int* counts, DevScene* sc, int* runs, cudaStream_t st) {
+  auto& m = s->strm;
+  std::vector<int> want;
+  for (int i = 0; i < s->n_sub; ++i)
+    if (counts[i] > 0) want.push_back(i);
+  std::sort(want.begin(), want.end(), [&](int a, int b) {
+    if (counts[a] != counts[b]) return counts[a] > counts[b];
+    const bool ra = m.slot_of[a] >= 0, rb = m.slot_of[b] >= 0;
+    if (ra != rb) return ra;  // on a tie keep what is resident
+    return a < b;
+  });
+  if ((int)want.size() > m.cap) want.resize(m.cap);
+  std::vector<char> keep(s->n_sub, 0);
+  for (int i : want) keep[i] = 1;
+  for (int i : want) {
+    if (m.slot_of[i] >= 0) continue;
+    int j = -1;
+    for (int k = 0; k < m.cap; ++k) {  // an empty slot, else the left-out occupant with the fewest rays
+      const int o = m.sub_in_slot[k];
+      if (o < 0) {
+        j = k;
+        break;
+      }
+      if (!keep[o] && (j < 0 || counts[o] < counts[m.sub_in_slot[j]])) j = k;
+    }
+    if (j < 0) return fail(SDD_ERR_STATE, "no subdomain slot to evict");
+    if (m.sub_in_slot[j] >= 0) m.slot_of[m.sub_in_slot[j]] = -1;
+    CK(load_subdomain(s, i, j, st));
+    m.slot_of[i] = j;
+    m.sub_in_slot[j] = i;
+  }
+  sc->nodes = m.d_nodes.p;
+  sc->tris = m.d_tris.p;
+  for (int i = 0; i < s->n_sub; ++i) {
+    runs[i] = keep[i] ? counts[i] : 0;
+    if (m.slot_of[i] >= 0) sc->root[i] = m.slot_of[i] * m.slot_nodes;
+  }
+  return SDD_OK;
+}
+
+// Rays of subdomains this pass leaves out move, unchanged, to the pass's output queues
+// (whose counts were just cleared); the traversal then appends behind them.
+sdd_status carry_queues(sdd_scene* s, const int* counts, const int* runs, uint32_t* qin, uint32_t* qout,
+                        int* out_count, int qcap, cudaStream_t st) {
+  for (int i = 0; i < s->n_sub; ++i) {
+    const int c = std::min(std::max(counts[i], 0), qcap);
+    if (c == 0 || runs[i] > 0) continue;
+    CK(cudaMemcpyAsync(qout + (size_t)i * qcap, qin + (size_t)i * qcap, sizeof(uint32_t) * (size_t)c,
+                       cudaMemcpyDeviceToDevice, st));
+    launch_set_int(out_count + i, c, st);
+  }
+  return SDD_OK;
+}
+
+// Pass bound of one generation's passes: without streaming a ray crosses each slab at most
+// once; with it a pass may leave subdomains out, each left-out queue waits at most
+// ceil(n_sub / cap) passes per pass it would otherwise have had.
+int pass_bound(const sdd_scene* s) {
+  const int n = s->n_sub;
+  return s->strm.cap > 0 ? (2 * n + 2) * ((n + s->strm.cap - 1) / s->strm.cap + 1) : 2 * kMaxSubdomains + 2;
+}
+
 Sched make_sched(int n_sub, const int* counts, int cap, int block, int* total_blocks, long long* total) {
   Sched sc;
   sc.n_sub = n_sub;
@@ -284,18 +407,28 @@ Sched make_sched(int n_sub, const int* counts, int cap, int block, int* total_bl
 
 // Closest-hit passes: the queues in q[a] (counts in ctl->q_count[a]) are traversed and
 // rays crossing an interface move to q[1-a], until every ray has a hit record.
-sdd_status run_closest_passes(sdd_scene* s, const RenderParams& p, RayBuf rb, int qcap, cudaStream_t st) {
+sdd_status run_closest_passes(sdd_scene* s, const RenderParams& p0, RayBuf rb, int qcap, cudaStream_t st) {
+  RenderParams p = p0;
   int a = 0;
-  for (int pass = 0; pass <= 2 * kMaxSubdomains + 2; ++pass) {
+  const int bound = pass_bound(s);
+  for (int pass = 0; pass <= bound; ++pass) {
     sdd_status r = read_ctl(s, st);
     if (r) return r;
     if (s->h_ctl->error) return device_error(s->h_ctl->error);
     int nb;
     long long total;
     const int blk = s->tuning.traverse_block;
-    Sched sch = make_sched(s->n_sub, s->h_ctl->q_count[a], qcap, blk, &nb, &total);
-    if (total == 0) return SDD_OK;
+    const int* counts = s->h_ctl->q_count[a];
+    int runs[kMaxSubdomains];
+    long long queued = 0;
+    for (int i = 0; i < s->n_sub; ++i) queued += std::max(counts[i], 0);
+    if (queued == 0) return SDD_OK;
+    if (s->strm.cap > 0 && (r = stream_in(s, counts, &p.sc, runs, st))) return r;
+    Sched sch = make_sched(s->n_sub, s->strm.cap > 0 ? runs : counts, qcap, blk, &nb, &total);
     CK(cudaMemsetAsync(s->d_ctl->q_count[1 - a], 0, sizeof(int) * kMaxSubdomains, st));
+    if (s->strm.cap > 0 &&
+        (r = carry_queues(s, counts, runs, s->q[a].p, s->q[1 - a].p, s->d_ctl->q_count[1 - a], qcap, st)))
+      return r;
     QueuePair qp{s->q[a].p, s->q[1 - a].p, s->d_ctl->q_count[1 - a], qcap};
     int ev = s->ev_begin(TK_TRAVERSE, st);
     launch_traverse(p, sch, nb, blk, s->tuning.top_nodes, qp, rb, s->hits.p, s->d_ctl, st);
@@ -307,19 +440,29 @@ sdd_status run_closest_passes(sdd_scene* s, const RenderParams& p, RayBuf rb, in
   return fail(SDD_ERR_TIMEOUT, "closest-hit passes did not drain the subdomain queues");
 }
 
-sdd_status run_shadow_passes(sdd_scene* s, const RenderParams& p, const WaveDesc& w, int qcap, cudaStream_t st) {
+sdd_status run_shadow_passes(sdd_scene* s, const RenderParams& p0, const WaveDesc& w, int qcap, cudaStream_t st) {
+  RenderParams p = p0;
   int a = 0;
   ShadowBuf sb{s->sb_o.p, s->sb_d.p, s->sb_info.p, qcap, s->sb_c.p};
-  for (int pass = 0; pass <= 2 * kMaxSubdomains + 2; ++pass) {
+  const int bound = pass_bound(s);
+  for (int pass = 0; pass <= bound; ++pass) {
     sdd_status r = read_ctl(s, st);
     if (r) return r;
     if (s->h_ctl->error) return device_error(s->h_ctl->error);
     int nb;
     long long total;
     const int blk = s->tuning.traverse_block;
-    Sched sch = make_sched(s->n_sub, s->h_ctl->sq_count[a], qcap, blk, &nb, &total);
-    if (total == 0) return SDD_OK;
+    const int* counts = s->h_ctl->sq_count[a];
+    int runs[kMaxSubdomains];
+    long long queued = 0;
+    for (int i = 0; i < s->n_sub; ++i) queued += std::max(counts[i], 0);
+    if (queued == 0) return SDD_OK;
+    if (s->strm.cap > 0 && (r = stream_in(s, counts, &p.sc, runs, st))) return r;
+    Sched sch = make_sched(s->n_sub, s->strm.cap > 0 ? runs : counts, qcap, blk, &nb, &total);
     CK(cudaMemsetAsync(s->d_ctl->sq_count[1 - a], 0, sizeof(int) * kMaxSubdomains, st));
+    if (s->strm.cap > 0 &&
+        (r = carry_queues(s, counts, runs, s->sq[a].p, s->sq[1 - a].p, s->d_ctl->sq_count[1 - a], qcap, st)))
+      return r;
     QueuePair qp{s->sq[a].p, s->sq[1 - a].p, s->d_ctl->sq_count[1 - a], qcap};
     int ev = s->ev_begin(TK_SHADOW, st);
     launch_shadow(p, w, sch, nb, blk, s->tuning.top_nodes, qp, sb, s->path_L.p, s->d_ctl, st);
@@ -600,7 +743,7 @@ sdd_status render_batched(sdd_scene* s, const RenderParams& p, const std::vector
   int grid = 0;
   GraphGrids gg{};
   if (form == 2) {
-    gg = graph_grids(p, s->tuning.top_nodes);  // occupancy queries stay outside the capture
+    gg = graph_grids(p, s->tuning.top_nodes, s->tuning.block_chunks);  // occupancy queries stay outside the capture
   } else {
     grid = persistent_grid(p.stats >= 2, tile_mode(p), p.bundle > 1);
     if (grid <= 0) return fail(SDD_ERR_CUDA, "persistent kernel does not fit on this device");
@@ -776,6 +919,8 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
   for (int i = 0; i < o->n_pixels; ++i)
     if (o->pixels[i] < 0 || o->pixels[i] >= img) return fail(SDD_ERR_ARG, "pixel index out of range");
   if (o->batched < 0 || o->batched > 2) return fail(SDD_ERR_ARG, "batched must be 0, 1 or 2");
+  if (o->batched != 0 && s->strm.cap > 0)
+    return fail(SDD_ERR_STATE, "out-of-core subdomains (resident_subdomains > 0) need the host-driven form (batched = 0)");
   if (o->bundle < 0 || o->bundle > kMaxBundle) return fail(SDD_ERR_ARG, "bundle must be in [0, 16]");
   const int B = o->bundle > 1 ? o->bundle : 1;
   if (B > 1 && o->mode != SDD_MODE_MONTE_CARLO) return fail(SDD_ERR_ARG, "spectral bundles need Monte Carlo mode");
@@ -1212,6 +1357,7 @@ sdd_status sdd_scene_create(const sdd_scene_desc* d, sdd_scene** out) {
   s->bvh_max_depth = bvh.max_depth;
   s->n_refs = bvh.n_refs;
   s->n_nodes = (int64_t)bvh.nodes.size();
+  s->n_tri_recs = (int64_t)bvh.tris.size();
   cudaError_t e;
   if ((e = s->nodes.ensure(bvh.nodes.size())) != cudaSuccess ||
       (e = s->tris.ensure(std::max<size_t>(1, bvh.tris.size()))) != cudaSuccess ||
@@ -1305,6 +1451,98 @@ sdd_status sdd_watchdog_selftest(int timeout_ms) {
   return SDD_OK;
 }
 
+namespace {
+void free_streaming(sdd_scene* s) {
+  auto& m = s->strm;
+  m.d_nodes.release();
+  m.d_tris.release();
+  cudaFreeHost(m.h_nodes);
+  cudaFreeHost(m.h_tris);
+  cudaFreeHost(m.stage_nodes);
+  cudaFreeHost(m.stage_tris);
+  m.h_nodes = nullptr;
+  m.h_tris = nullptr;
+  m.stage_nodes = nullptr;
+  m.stage_tris = nullptr;
+  m.cap = 0;
+}
+
+// Switch to at most `cap` resident subdomains (0 or >= n_sub: all resident).  Entering keeps
+// the BVH in pinned host memory, allocates cap slots and frees the all-resident device copy;
+// leaving uploads it again.
+sdd_status set_streaming(sdd_scene* s, int cap) {
+  auto& m = s->strm;
+  if (cap >= s->n_sub) cap = 0;
+  if (cap == m.cap) return SDD_OK;
+  CK(cudaDeviceSynchronize());  // no render in flight reads the BVH
+  if (m.cap > 0) {  // restore the all-resident device copy
+    CK(s->nodes.ensure((size_t)m.n_nodes));
+    CK(s->tris.ensure((size_t)std::max<int64_t>(1, m.n_tris)));
+    CK(cudaMemcpy(s->nodes.p, m.h_nodes, sizeof(Node) * (size_t)m.n_nodes, cudaMemcpyHostToDevice));
+    if (m.n_tris > 0) CK(cudaMemcpy(s->tris.p, m.h_tris, sizeof(TriRec) * (size_t)m.n_tris, cudaMemcpyHostToDevice));
+    s->dev.nodes = s->nodes.p;
+    s->dev.tris = s->tris.p;
+    for (int i = 0; i < s->n_sub; ++i) s->dev.root[i] = m.node0[i];
+    free_streaming(s);
+    s->graph_key.clear();
+  }
+  if (cap == 0) return SDD_OK;
+  m.n_nodes = s->n_nodes;
+  m.n_tris = (int64_t)s->n_tri_recs;
+  m.node0.assign(s->n_sub, 0);
+  m.nnodes.assign(s->n_sub, 0);
+  m.tri0.assign(s->n_sub, 0);
+  m.ntris.assign(s->n_sub, 0);
+  cudaError_t e = cudaMallocHost(&m.h_nodes, sizeof(Node) * (size_t)std::max<int64_t>(1, m.n_nodes));
+  if (e == cudaSuccess) e = cudaMallocHost(&m.h_tris, sizeof(TriRec) * (size_t)std::max<int64_t>(1, m.n_tris));
+  if (e == cudaSuccess) e = cudaMemcpy(m.h_nodes, s->nodes.p, sizeof(Node) * (size_t)m.n_nodes, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && m.n_tris > 0)
+    e = cudaMemcpy(m.h_tris, s->tris.p, sizeof(TriRec) * (size_t)m.n_tris, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    free_streaming(s);
+    return fail(e == cudaErrorMemoryAllocation ? SDD_ERR_OOM : SDD_ERR_CUDA, cudaGetErrorString(e));
+  }
+  // per subdomain: its nodes (one breadth-first block from its root) and the triangle
+  // records its leaves reference
+  int max_nodes = 1, max_tris = 1;
+  for (int i = 0; i < s->n_sub; ++i) {
+    const int n0 = s->dev.root[i], nn = s->dev.n_nodes_sub[i];
+    int t0 = INT32_MAX, t1 = 0;
+    for (int k = n0; k < n0 + nn; ++k) {
+      const int4 d = m.h_nodes[k].d;
+      if (d.z > 0) { t0 = std::min(t0, d.x); t1 = std::max(t1, d.x + d.z); }
+      if (d.w > 0) { t0 = std::min(t0, d.y); t1 = std::max(t1, d.y + d.w); }
+    }
+    if (t0 > t1) t0 = t1 = 0;
+    m.node0[i] = n0;
+    m.nnodes[i] = nn;
+    m.tri0[i] = t0;
+    m.ntris[i] = t1 - t0;
+    max_nodes = std::max(max_nodes, nn);
+    max_tris = std::max(max_tris, t1 - t0);
+  }
+  m.slot_nodes = max_nodes;
+  m.slot_tris = max_tris;
+  e = m.d_nodes.ensure((size_t)cap * max_nodes);
+  if (e == cudaSuccess) e = m.d_tris.ensure((size_t)cap * max_tris);
+  if (e == cudaSuccess) e = cudaMallocHost(&m.stage_nodes, sizeof(Node) * (size_t)cap * max_nodes);
+  if (e == cudaSuccess) e = cudaMallocHost(&m.stage_tris, sizeof(TriRec) * (size_t)cap * max_tris);
+  if (e != cudaSuccess) {
+    free_streaming(s);
+    return fail(e == cudaErrorMemoryAllocation ? SDD_ERR_OOM : SDD_ERR_CUDA, cudaGetErrorString(e));
+  }
+  m.slot_of.assign(s->n_sub, -1);
+  m.sub_in_slot.assign(cap, -1);
+  m.cap = cap;
+  s->nodes.release();  // the device now holds only the slots
+  s->tris.release();
+  s->dev.nodes = nullptr;
+  s->dev.tris = nullptr;
+  s->graph_key.clear();
+  return SDD_OK;
+}
+}  // namespace
+
 sdd_status sdd_set_tuning(sdd_scene* s, const sdd_tuning* t) {
   if (!s || !t) return fail(SDD_ERR_ARG, "NULL argument");
   if (t->traverse_block != 64 && t->traverse_block != 128 && t->traverse_block != 256)
@@ -1313,7 +1551,11 @@ sdd_status sdd_set_tuning(sdd_scene* s, const sdd_tuning* t) {
   if (t->wave_paths < 0) return fail(SDD_ERR_ARG, "wave_paths must be >= 0");
   if (t->no_graph != 0 && t->no_graph != 1) return fail(SDD_ERR_ARG, "no_graph must be 0 or 1");
   if (t->queue_capacity < 0) return fail(SDD_ERR_ARG, "queue_capacity must be >= 0");
+  if (t->block_chunks < 0 || t->block_chunks > 3) return fail(SDD_ERR_ARG, "block_chunks must be in [0, 3]");
+  if (t->resident_subdomains < 0) return fail(SDD_ERR_ARG, "resident_subdomains must be >= 0");
+  if (sdd_status r = set_streaming(s, t->resident_subdomains)) return r;
   s->tuning = *t;
+  s->tuning.resident_subdomains = s->strm.cap;
   return SDD_OK;
 }
 

@@ -9,9 +9,10 @@ namespace sdd {
 // query them before a stream capture begins.
 struct GraphGrids {
   int traverse, shade, shadow;
-  int top_nodes;  // BVH nodes per subdomain the traversal stages in shared memory (0: none)
+  int top_nodes;     // BVH nodes per subdomain the traversal stages in shared memory (0: none)
+  int block_chunks;  // bit 0 closest-hit, bit 1 shadow passes: 128-ray chunks per block (else 32 per warp)
 };
-GraphGrids graph_grids(const RenderParams& p, int top_nodes);
+GraphGrids graph_grids(const RenderParams& p, int top_nodes, int block_chunks);
 
 // work: the pass's chunk counter, zero before the pass
 cudaError_t launch_traverse_g(const RenderParams& p, const GraphGrids& g, const int* counts_in, int* work,

@@ -37,14 +37,23 @@ __device__ __forceinline__ int next_warp_chunk(int* work) {
   if ((threadIdx.x & 31) == 0) c = atomicAdd(work, kWarpChunk);
   return __shfl_sync(0xFFFFFFFFu, c, 0);
 }
+// The block-wide alternative: the block takes a 128-ray chunk (one per thread) at a time,
+// which keeps a block's warps on consecutive queue entries but makes them wait for each other.
+__device__ __forceinline__ int next_block_chunk(int* work) {
+  __shared__ int s_chunk;
+  __syncthreads();
+  if (threadIdx.x == 0) s_chunk = atomicAdd(work, kChunk);
+  __syncthreads();
+  return s_chunk;
+}
 
 // Closest-hit pass over the queues whose counts are counts_in.  With top_nodes > 0 every
 // block first stages the top_nodes first (breadth-first: top-level) nodes of every
 // subdomain's BVH in shared memory (Sec. 5: the top of the hierarchy first).
 template <bool kStats>
 __global__ void __launch_bounds__(kChunk, 12) k_traverse_g(RenderParams p, const int* counts_in, int* work,
-                                                           int top_nodes, QueuePair qp, RayBuf rb, float2* hits,
-                                                           Control* ctl) {
+                                                           int top_nodes, int block_chunks, QueuePair qp, RayBuf rb,
+                                                           float2* hits, Control* ctl) {
   __shared__ int s_prefix[kMaxSubdomains + 1];
   __shared__ int s_count[kMaxSubdomains];
   extern __shared__ Node s_top[];
@@ -60,8 +69,9 @@ __global__ void __launch_bounds__(kChunk, 12) k_traverse_g(RenderParams p, const
     }
     __syncthreads();
   }
-  const int lane = threadIdx.x & 31;
-  for (int c0 = next_warp_chunk(work); c0 < total; c0 = next_warp_chunk(work)) {
+  const int lane = block_chunks ? (int)threadIdx.x : ((int)threadIdx.x & 31);
+  for (int c0 = block_chunks ? next_block_chunk(work) : next_warp_chunk(work); c0 < total;
+       c0 = block_chunks ? next_block_chunk(work) : next_warp_chunk(work)) {
     const int s = find_subdomain(s_prefix, n_sub, c0);  // the whole chunk's subdomain
     const int i = c0 - s_prefix[s] + lane;
     const int n_staged = top_nodes > 0 ? min(top_nodes, p.sc.n_nodes_sub[s]) : 0;
@@ -93,14 +103,15 @@ __global__ void __launch_bounds__(kBlock) k_shade_g(RenderParams p, WaveDesc w, 
 template <bool kStats, int kTM, bool kBund>
 __global__ void __launch_bounds__(kChunk, kTM == 1 ? 1 : 8) k_shadow_g(RenderParams p, WaveDesc w,
                                                                       const int* counts_in, int* work,
-                                                                      QueuePair qp, ShadowBuf sb, float* path_L,
-                                                                      Control* ctl) {
+                                                                      int block_chunks, QueuePair qp, ShadowBuf sb,
+                                                                      float* path_L, Control* ctl) {
   __shared__ int s_prefix[kMaxSubdomains + 1];
   __shared__ int s_count[kMaxSubdomains];
   const int n_sub = p.sc.n_sub;
   const int total = load_prefix(counts_in, n_sub, qp.cap, s_prefix, s_count);
-  const int lane = threadIdx.x & 31;
-  for (int c0 = next_warp_chunk(work); c0 < total; c0 = next_warp_chunk(work)) {
+  const int lane = block_chunks ? (int)threadIdx.x : ((int)threadIdx.x & 31);
+  for (int c0 = block_chunks ? next_block_chunk(work) : next_warp_chunk(work); c0 < total;
+       c0 = block_chunks ? next_block_chunk(work) : next_warp_chunk(work)) {
     const int s = find_subdomain(s_prefix, n_sub, c0);
     const int i = c0 - s_prefix[s] + lane;
     const bool act = i < s_count[s];
@@ -196,18 +207,18 @@ cudaError_t launch_fn(const void* fn, int grid, int block, void** args, cudaStre
 
 }  // namespace
 
-GraphGrids graph_grids(const RenderParams& p, int top_nodes) {
+GraphGrids graph_grids(const RenderParams& p, int top_nodes, int block_chunks) {
   const int tn = staged_nodes(p.sc.n_sub, top_nodes);
   const size_t smem = (size_t)tn * p.sc.n_sub * sizeof(Node);
   return GraphGrids{grid_of(traverse_fn(p), kChunk, smem), grid_of(shade_fn(p), kBlock),
-                    grid_of(shadow_fn(p), kChunk), tn};
+                    grid_of(shadow_fn(p), kChunk), tn, block_chunks};
 }
 
 cudaError_t launch_traverse_g(const RenderParams& p, const GraphGrids& g, const int* counts_in, int* work,
                               QueuePair qp, RayBuf rb, float2* hits, Control* ctl, cudaStream_t st) {
-  int tn = g.top_nodes;
-  void* args[] = {(void*)&p, (void*)&counts_in, (void*)&work, (void*)&tn, (void*)&qp, (void*)&rb, (void*)&hits,
-                  (void*)&ctl};
+  int tn = g.top_nodes, bc = g.block_chunks & 1;
+  void* args[] = {(void*)&p, (void*)&counts_in, (void*)&work, (void*)&tn, (void*)&bc, (void*)&qp, (void*)&rb,
+                  (void*)&hits, (void*)&ctl};
   const size_t smem = (size_t)tn * p.sc.n_sub * sizeof(Node);
   return cudaLaunchKernel(traverse_fn(p), dim3(g.traverse), dim3(kChunk), args, smem, st);
 }
@@ -224,7 +235,8 @@ cudaError_t launch_shade_g(const RenderParams& p, const GraphGrids& g, const Wav
 
 cudaError_t launch_shadow_g(const RenderParams& p, const GraphGrids& g, const WaveDesc& w, const int* counts_in,
                             int* work, QueuePair qp, ShadowBuf sb, float* path_L, Control* ctl, cudaStream_t st) {
-  void* args[] = {(void*)&p,  (void*)&w,      (void*)&counts_in, (void*)&work,
+  int bc = (g.block_chunks >> 1) & 1;
+  void* args[] = {(void*)&p,  (void*)&w,  (void*)&counts_in, (void*)&work, (void*)&bc,
                   (void*)&qp, (void*)&sb, (void*)&path_L,    (void*)&ctl};
   return launch_fn(shadow_fn(p), g.shadow, kChunk, args, st);
 }

@@ -25,6 +25,7 @@
 namespace sdd {
 // Defined in api.cu: the device-side description of a scene and the thread-local error text.
 const DevScene* scene_device_view(const sdd_scene* s);
+bool scene_streaming(const sdd_scene* s);
 sdd_status set_last_error(sdd_status st, const char* msg);
 }  // namespace sdd
 
@@ -84,6 +85,8 @@ extern "C" sdd_status sdd_trace_closest_noalloc(sdd_scene* scene, int n, const f
     unsigned char* base = nullptr;
     return scratch_on_current_device(&base);
   }
+  if (scene_streaming(scene))
+    return set_last_error(SDD_ERR_STATE, "out-of-core subdomains are on (resident_subdomains > 0): the BVH is not resident");
   const DevScene* ds = scene_device_view(scene);
   const size_t need = scratch_bytes((size_t)n, ds->n_sub);
   if (need > kNoAllocScratchBytes) {

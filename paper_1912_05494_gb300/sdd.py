@@ -73,7 +73,7 @@ class sdd_stats(C.Structure):
                                           "shadow_tri_tests", "crossings", "paths", "waves", "bytes_ray_state")] + \
                [("ms_persistent", C.c_double), ("launches_persistent", C.c_int64), ("graph_replays", C.c_int64),
                 ("ms_tile", C.c_double), ("launches_tile", C.c_int64), ("tile_shaded", C.c_int64),
-                ("wave_splits", C.c_int64)]
+                ("wave_splits", C.c_int64), ("subdomain_loads", C.c_int64), ("bytes_streamed", C.c_int64)]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
@@ -91,7 +91,7 @@ class sdd_tileset_desc(C.Structure):
 
 class sdd_tuning(C.Structure):
     _fields_ = [("traverse_block", C.c_int), ("top_nodes", C.c_int), ("wave_paths", C.c_int), ("no_graph", C.c_int),
-                ("queue_capacity", C.c_int)]
+                ("queue_capacity", C.c_int), ("block_chunks", C.c_int), ("resident_subdomains", C.c_int)]
 
 
 class sdd_scene_info(C.Structure):
