@@ -35,17 +35,32 @@ __device__ __forceinline__ float gelu_grad(float z) {
   return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * 0.3989422804014327f * expf(-0.5f * z * z);
 }
 
+// The raw inputs q of one row normalised to [0, 1].
+__device__ __forceinline__ void normalise_row(const float q[kIn], float x[kIn]) {
+  x[0] = 0.5f * (q[0] + 1.f);
+  x[1] = q[1] * 0.15915494309189535f;
+  x[2] = (q[2] - 380.f) / 400.f;
+  x[3] = (q[3] - 2e-3f) / 3e-3f;
+  x[4] = q[4] / 2e10f;
+  x[5] = (q[5] - 1.45f) / 0.2f;
+  x[6] = (log10f(fmaxf(q[6], 1e-30f)) + 8.f) / 4.f;
+}
+// Fourier pair i of the normalised inputs x: sin and cos of 2 pi (B x)_i.
+__device__ __forceinline__ void fourier_pair(const float x[kIn], const float* __restrict__ Bm, int i, float* s,
+                                             float* c) {
+  float p = 0.f;
+  for (int j = 0; j < kIn; ++j) p += __ldg(Bm + i * kIn + j) * x[j];
+  sincospif(2.f * p, s, c);
+}
+
 // The 48 BF16 features of one row of raw inputs q: [sin(2 pi B x), cos(2 pi B x), x, 0 pad]
 // with x the inputs normalised to [0, 1].
 __device__ __forceinline__ void features_row(const float q[kIn], const float* __restrict__ Bm, __nv_bfloat16* f) {
-  const float x[kIn] = {0.5f * (q[0] + 1.f), q[1] * 0.15915494309189535f, (q[2] - 380.f) / 400.f,
-                        (q[3] - 2e-3f) / 3e-3f, q[4] / 2e10f, (q[5] - 1.45f) / 0.2f,
-                        (log10f(fmaxf(q[6], 1e-30f)) + 8.f) / 4.f};
+  float x[kIn];
+  normalise_row(q, x);
   for (int i = 0; i < kFourier; ++i) {
-    float p = 0.f;
-    for (int j = 0; j < kIn; ++j) p += __ldg(Bm + i * kIn + j) * x[j];
     float s, c;
-    sincospif(2.f * p, &s, &c);
+    fourier_pair(x, Bm, i, &s, &c);
     f[i] = __float2bfloat16(s);
     f[kFourier + i] = __float2bfloat16(c);
   }

@@ -99,6 +99,14 @@ __device__ __forceinline__ void copy16(unsigned char* dst, const unsigned char* 
     *reinterpret_cast<uint4*>(dst + i) = *reinterpret_cast<const uint4*>(src + i);
 }
 
+// Asynchronous 16-byte global -> shared copies (cp.async, completed by copy_async_wait).
+__device__ __forceinline__ void copy16_async(unsigned char* dst, const unsigned char* src, uint32_t bytes) {
+  for (uint32_t i = threadIdx.x * 16u; i < bytes; i += blockDim.x * 16u)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::sa(dst + i)), "l"(src + i) : "memory");
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void copy_async_wait() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 __device__ __forceinline__ void store_bf16(unsigned char* base, uint32_t off, float x) {
   *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16(x);
 }
@@ -157,17 +165,41 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int row0 = c * kRows, valid = min(kRows, n - row0);
     unsigned char* rc = rec + (size_t)c * kRecBytes;
     __syncthreads();  // the previous chunk's staging copy is done
-    if (tid < kRows) {  // features of row tid: layer 0's A operand and in_0^T
+    {  // features (the inference kernel's map): four threads per row, four Fourier pairs each;
+       // layer 0's A operand and in_0^T
+      const int r = tid & (kRows - 1), part = tid >> 7;
       float q[kIn] = {0.f, 0.f, 380.f, 2e-3f, 0.f, 1.45f, 1e-8f};
-      if (tid < valid)
-        for (int j = 0; j < kIn; ++j) q[j] = raw[(size_t)(row0 + tid) * kIn + j];
-      __align__(16) __nv_bfloat16 f[kFeat];
-      features_row(q, v.Bm, f);
+      if (r < valid)
+        for (int j = 0; j < kIn; ++j) q[j] = raw[(size_t)(row0 + r) * kIn + j];
+      float x[kIn];
+      normalise_row(q, x);
+      __align__(8) __nv_bfloat16 fs[4], fc[4];
 #pragma unroll
-      for (int j = 0; j < kFeat / 8; ++j)
-        *reinterpret_cast<uint4*>(sA + tc::chunk_off(tid, j, tc::sbo_of(kFeat))) = reinterpret_cast<const uint4*>(f)[j];
-#pragma unroll 8
-      for (int j = 0; j < kFeat; ++j) *reinterpret_cast<__nv_bfloat16*>(sT + tcanon(j, tid)) = f[j];
+      for (int i = 0; i < 4; ++i) {
+        float sn, cs;
+        fourier_pair(x, v.Bm, 4 * part + i, &sn, &cs);
+        fs[i] = __float2bfloat16(sn);
+        fc[i] = __float2bfloat16(cs);
+      }
+      const uint32_t s48 = tc::sbo_of(kFeat);
+      *reinterpret_cast<uint2*>(sA + tc::chunk_off(r, part / 2, s48) + (part & 1) * 8) =
+          *reinterpret_cast<const uint2*>(fs);
+      *reinterpret_cast<uint2*>(sA + tc::chunk_off(r, 2 + part / 2, s48) + (part & 1) * 8) =
+          *reinterpret_cast<const uint2*>(fc);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        *reinterpret_cast<__nv_bfloat16*>(sT + tcanon(4 * part + i, r)) = fs[i];
+        *reinterpret_cast<__nv_bfloat16*>(sT + tcanon(kFourier + 4 * part + i, r)) = fc[i];
+      }
+      if (part == 0) {  // the normalised inputs and the zero padding: features 32..47
+        __align__(16) __nv_bfloat16 f[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) f[j] = __float2bfloat16(j < kIn ? x[j] : 0.f);
+        *reinterpret_cast<uint4*>(sA + tc::chunk_off(r, 4, s48)) = reinterpret_cast<const uint4*>(f)[0];
+        *reinterpret_cast<uint4*>(sA + tc::chunk_off(r, 5, s48)) = reinterpret_cast<const uint4*>(f)[1];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) *reinterpret_cast<__nv_bfloat16*>(sT + tcanon(2 * kFourier + j, r)) = f[j];
+      }
     }
     tc::fence_async_smem();
     __syncthreads();
@@ -198,12 +230,14 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll 1
         for (int g = 0; g < 2; ++g) {
           const int col = cg * 32 + g * 16;
-          float z[16];
+          float z[16], bb[16];
           tc::ld16(t_row + (uint32_t)col, z);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) *reinterpret_cast<float4*>(bb + 4 * j) = __ldg(reinterpret_cast<const float4*>(bias + col) + j);
           uint32_t zb[8], a8[8];
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
-            const float z0 = z[2 * j] + __ldg(bias + col + 2 * j), z1 = z[2 * j + 1] + __ldg(bias + col + 2 * j + 1);
+            const float z0 = z[2 * j] + bb[2 * j], z1 = z[2 * j + 1] + bb[2 * j + 1];
             zb[j] = tc::pack2(z0, z1);
             const float g0 = gelu(z0), g1 = gelu(z1);
             a8[j] = tc::pack2(g0, g1);
@@ -371,6 +405,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc::commit(bar_a);
       }
+      // z_{l-1} of this thread's columns of the first half, loaded while the MMAs run
+      const unsigned char* zr = rc + rec_z(l > 0 ? l - 1 : 0);
+      auto z_of = [&](int h2) {
+        const int col = h2 * 64 + cg * 16;
+        return reinterpret_cast<const uint4*>(zr + (((uint32_t)(col / 16) * kRows + row) * 16u) * 2u);
+      };
+      uint4 zz[2] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0)};
+      if (l > 0) {
+        zz[0] = z_of(0)[0];
+        zz[1] = z_of(0)[1];
+      }
       if (!wait_mma()) {
         failed = true;
         break;
@@ -378,7 +423,6 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (l == 0) break;
       // gz_{l-1} = d in_l * GELU'(z_{l-1}), two halves of 64 columns; written over gz_l^T
       // (into the normal layout) and in_l^T (transposed), both consumed by dW_l
-      const unsigned char* zr = rc + rec_z(l - 1);
 #pragma unroll 1
       for (int h2 = 0; h2 < 2; ++h2) {
         if (h2 == 1) {
@@ -392,10 +436,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                       id, kk > 0 ? 1u : 0u);
             tc::commit(bar_a);
           }
+          zz[0] = z_of(1)[0];
+          zz[1] = z_of(1)[1];
           if (!wait_mma()) {
             failed = true;
             break;
           }
+          // both halves of d in_l are computed: in_{l-1}^T goes into the buffer gz_l used,
+          // asynchronously, while this half's epilogue runs
+          copy16_async(buf[bx], rc + rec_in_t(l - 1), l - 1 == 0 ? kInT0Bytes : kTileBytes);
         }
         tc::fence_after();
         // this warp: rows of its quadrant, columns cg * 16 .. + 15 of the 64-column half
@@ -404,8 +453,6 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int col = h2 * 64 + wc;       // column of d in_l
           float d[16];
           tc::ld16(tmem + t_lane + kColWork + (uint32_t)wc, d);
-          const uint4* zp = reinterpret_cast<const uint4*>(zr + (((uint32_t)(col / 16) * kRows + row) * 16u) * 2u);
-          uint4 zz[2] = {zp[0], zp[1]};
           const __nv_bfloat162* zh = reinterpret_cast<const __nv_bfloat162*>(zz);
           uint32_t g8[8];
 #pragma unroll
@@ -422,9 +469,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc::fence_before();
         __syncthreads();  // every thread's reads of the working columns are done
       }
+      copy_async_wait();  // in_{l-1}^T has landed (also on the way out of a failed wait)
       if (failed) break;
-      // in_{l-1}^T into the buffer gz_l used (both halves of d in_l are done)
-      copy16(buf[bx], rc + rec_in_t(l - 1), l - 1 == 0 ? kInT0Bytes : kTileBytes);
       tc::fence_async_smem();
       __syncthreads();
       add_bias_grad(l - 1, buf[bz]);
