@@ -18,6 +18,12 @@ Printed JSON line (rank 0):
   roofline   traversal kernel: algorithmic bytes (BVH nodes x 64 B + triangles x 48 B + ray
              state) / its CUDA-event time, against the measured HBM copy bandwidth
   cpu_baseline  the FP64 oracle on the host cores on a bounded pixel sample of the same frame
+  unbundled  the same frame with one wavelength per path
+  surrogate  (N = 1) the surrogate half of the metric on the large batched frame: the BTDF
+             network trained on the GPU, then 64 seeded 8 x 8-pixel blocks of the 3840 x 2160
+             frame at 4,096 spp in the plain form (brute-force tile rays) and the network form
+             (with and without bundles): block-mean image error against two plain renders,
+             their noise floor, and each form's throughput, with the sun off and on
 
 --workload large runs the large batched frame instead: the nave refined to ~1.07M triangles
 with 96 windows of 400 heterogeneous tiles (38,400 tiles), 3840 x 2160, 81 wavelengths,
@@ -283,6 +289,107 @@ def run_e2e(args, sdd, h, cam, spec, flush, n_px, frame_paths, world, dist, kw):
             "ms_per_step": e2e_ms}
 
 
+def surrogate_record():
+    """The surrogate half of the metric on the large batched frame (the ~1.07M-triangle nave,
+    96 windows of 400 heterogeneous tiles, 81 wavelengths, depth 16): the BTDF network is
+    trained on the GPU (tile-tracer data of the 512-tile set), then 64 seeded 8 x 8-pixel blocks
+    of the 3840 x 2160 frame (4,096 pixels; paths are keyed per pixel, so they are the frame's
+    own paths) are rendered at 4,096 spp by the plain form (host-driven, one wavelength per path,
+    one brute-force ray through the tile at every tile hit) with two seeds, and by the network
+    form (graph form, fused tile shading) with and without spectral bundles of 14.  Image error =
+    sum |a - b| / sum |b| of the wavelength-summed 8 x 8 block means against the mean of the two
+    brute-force renders; noise floor = the same between the two brute-force renders.  With the
+    sun off (sky light only) and with it on; throughput of each form from the same renders."""
+    import torch
+    from paper_1912_05494_gb300 import scenes as S
+    from paper_1912_05494_gb300 import sdd
+    from paper_1912_05494_gb300 import surrogate as SG
+
+    t0 = time.time()
+    scene, cam, spec = S.large_nave_scene(seed=5, n_subdomains=4)
+    tiles, tn, tk = S.tile_set(3, 512)
+    ts = sdd.TileSetHandle(tiles)
+    t_scene = time.time() - t0
+    t0 = time.time()
+    net, hist, (hr, hy) = SG.train_for_tileset(ts.h, tiles, tn, tk, n_samples=1 << 21, steps=20000, rays=256)
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    pred = torch.empty((hr.shape[0], 8), device="cuda")
+    net.infer(hr, pred)
+    p, y = pred.cpu().numpy(), hy.cpu().numpy()
+    nb, spp = 64, 4096
+    rng = np.random.default_rng(77)
+    sel = rng.choice((cam.width // 8) * (cam.height // 8), nb, replace=False)
+    bx, by = sel % (cam.width // 8), sel // (cam.width // 8)
+    pix = np.concatenate([((by[b] * 8 + np.arange(8))[:, None] * cam.width + bx[b] * 8 + np.arange(8)[None, :]).ravel()
+                          for b in range(nb)])
+    order = np.argsort(pix)
+    pix_sorted = pix[order].astype(np.int32)
+    inv = np.empty_like(order)
+    inv[order] = np.arange(order.size)
+    n = pix.size
+
+    def blocks(film):
+        return film[inv].sum(-1).reshape(nb, 64).mean(1)
+
+    def rel(a, b):
+        return float(np.abs(a - b).sum() / np.abs(b).sum())
+
+    stream = torch.cuda.current_stream()
+
+    def render(h, sp, **kw):
+        out = torch.empty((n, sp.n_lambda), device="cuda")
+        sdd.sdd_render(h.h, cam, sp, out, None, pixels=pix_sorted, **kw)  # untimed: the graph capture
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sdd.sdd_render(h.h, cam, sp, out, None, pixels=pix_sorted, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        return out.cpu().numpy().astype(np.float64), n * sp.spp * sp.n_lambda / (ms / 1e3) / 1e6
+
+    sp = S.RenderSpec(**{**spec.__dict__, "spp": spp})
+    sp_b = S.RenderSpec(**{**sp.__dict__, "bundle": 14})
+    net_kw = {"use_surrogate": 1, "surrogate": net, "batched": 2}
+    res = {}
+    for sun in (0, 1):
+        sc = S.SceneData(**scene.__dict__)
+        if not sun:
+            sc.sun = np.zeros_like(scene.sun)
+        h = sdd.SceneHandle(sc)
+        a, v_plain = render(h, sp, batched=0)
+        b, _ = render(h, S.RenderSpec(**{**sp.__dict__, "seed": sp.seed + 11}), batched=0)
+        nn14, v14 = render(h, sp_b, **net_kw)
+        nn1, v1 = render(h, sp, **net_kw)
+        h.close()
+        ref = blocks(0.5 * (a + b))
+        res["sun" if sun else "sky_only"] = {
+            "noise_floor_block8": rel(blocks(a), blocks(b)),
+            "image_error_block8_network_bundled": rel(blocks(nn14), ref),
+            "image_error_block8_network_unbundled": rel(blocks(nn1), ref),
+            "mean_ratio_network_bundled": float(blocks(nn14).mean() / ref.mean()),
+            "mean_ratio_network_unbundled": float(blocks(nn1).mean() / ref.mean()),
+            "value_plain": v_plain, "value_network_bundled": v14, "value_network_unbundled": v1,
+            "speedup_bundled": v14 / v_plain, "speedup_unbundled": v1 / v_plain}
+    net.close()
+    ts.close()
+    return {"workload": f"large nave {scene.n_triangles} triangles, 96 windows x 400 heterogeneous tiles, 81 lambda, "
+                        f"depth 16, RR; {nb} seeded 8x8-pixel blocks of the 3840x2160 frame ({n} pixels) at {spp} spp",
+            "unit": UNIT, "reference": "mean of two plain renders (seeds 5 and 16) at 4096 spp",
+            "forms": {"plain": "host-driven wavefront, one wavelength per path, one brute-force ray through the tile "
+                               "at every tile hit",
+                      "network": "graph form (fixed-grid kernels, conditional pass loops, one CUDA graph), fused "
+                                 "tcgen05 tile shading; bundled = spectral bundles of 14"},
+            "definition": "sum|a - b| / sum|b| over the wavelength-summed 8x8 block means; noise floor = the two plain "
+                          "renders against each other",
+            **res,
+            "network": {"train_steps": 20000, "train_samples": 1 << 21, "rays_per_sample": 256, "train_s": t_train,
+                        "loss_first": hist[0], "loss_last50": float(np.mean(hist[-50:])),
+                        "held_out_mae_T": float(np.abs(p[:, 0] - y[:, 0]).mean()),
+                        "held_out_mae_R": float(np.abs(p[:, 1] - y[:, 1]).mean())},
+            "setup_s": t_scene}
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_env()
@@ -302,6 +409,12 @@ def run_gpu(args):
     h = sdd.SceneHandle(scene)
     if args.no_graph:  # the graph form's kernels launched one by one (profiling the kernels)
         sdd.sdd_set_tuning(h.h, {**sdd.sdd_get_tuning(h.h), "no_graph": 1})
+    if args.top_nodes:  # top BVH nodes per subdomain staged in shared memory by the traversal
+        sdd.sdd_set_tuning(h.h, {**sdd.sdd_get_tuning(h.h), "top_nodes": args.top_nodes})
+    if args.resident:  # out-of-core subdomains: at most this many subdomain BVHs in device memory
+        sdd.sdd_set_tuning(h.h, {**sdd.sdd_get_tuning(h.h), "resident_subdomains": args.resident})
+    if args.block_chunks:  # graph form: 128-ray chunks per block (bit 0 closest hit, bit 1 shadow)
+        sdd.sdd_set_tuning(h.h, {**sdd.sdd_get_tuning(h.h), "block_chunks": args.block_chunks})
     n_px = cam.width * cam.height
     out = torch.empty((n_px, spec.n_lambda), device="cuda", dtype=torch.float32)
     xyz = torch.empty((n_px, 3), device="cuda", dtype=torch.float32)
@@ -399,6 +512,13 @@ def run_gpu(args):
                 "note": "algorithmic bytes = BVH nodes x 64 B + triangle records x 48 B + 44 B ray state per "
                         "subdomain visit; the ~35 MB BVH is L2-resident, so frac can exceed what DRAM moves"}
 
+    surrogate = None
+    if rank == 0 and world == 1 and not args.no_surrogate:
+        sclk = ClockSampler(local)
+        sclk.start()
+        surrogate = surrogate_record()
+        surrogate["clocks"] = sclk.stop()
+
     cpu = None
     parity = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -414,12 +534,15 @@ def run_gpu(args):
                            "form": FORMS[args.batched], "paths_per_step": frame_paths, "triangles": scene.n_triangles,
                            "subdomains": scene.n_subdomains, "l2": "flushed (512 MB write) before every frame",
                            "parallelism": f"replicas x{world}", "wave_paths": args.wave_paths or "auto",
-                           "spectral_bundle": args.bundle},
-                "e2e": e2e, "unbundled": unbundled,
+                           "spectral_bundle": args.bundle, "top_nodes_staged": args.top_nodes,
+                           "block_chunks": args.block_chunks, "resident_subdomains": args.resident},
+                "e2e": e2e, "unbundled": unbundled, "surrogate": surrogate,
                 "roofline": roofline, "cpu_baseline": cpu, "parity": parity, "clocks": clk,
                 "gpu_launches": launches,
                 "traversal_counts": {k: cnt[k] for k in ("rays_closest", "rays_shadow", "node_visits", "tri_tests",
                                                            "shadow_node_visits", "shadow_tri_tests", "crossings")},
+                "streaming": {"resident_subdomains": args.resident, "subdomain_loads_per_frame": st["subdomain_loads"],
+                              "bytes_streamed_per_frame": st["bytes_streamed"]} if args.resident else None,
                 "kernel_ms_per_step": {k: st[k] for k in ("ms_raygen", "ms_traverse", "ms_shade", "ms_shadow",
                                                           "ms_film")}}
         print(json.dumps(line), flush=True)
@@ -609,24 +732,27 @@ def run_network(args):
     e1.record(stream)
     torch.cuda.synchronize()
     ms_inf = e0.elapsed_time(e1) / args.steps
-    y = torch.rand((65536, 18), device="cuda")
-    xb = raw_d[:65536].contiguous()
-    for _ in range(args.warmup):
-        net.train_step(xb, y, lr=1e-3)
+    # training: whole sdd_surrogate_train runs (per step a 65,536-row minibatch gathered on the
+    # device, the fused forward + loss and backward tcgen05 kernels, then the CTA-ordered
+    # reduction fused with Adam), timed with CUDA events
+    n_tr = 1 << 20
+    y = torch.rand((n_tr, 18), device="cuda")
+    xb = raw_d[:n_tr].contiguous()
+    net.train(xb, y, steps=max(3, args.warmup), batch=65536, lr=1e-3, seed=1)
+    n_train = max(50, args.steps * 20)
+    e0.record(stream)
+    net.train(xb, y, steps=n_train, batch=65536, lr=1e-3, seed=2)
+    e1.record(stream)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    n_train = max(20, args.steps * 10)
-    for _ in range(n_train):
-        net.train_step(xb, y, lr=1e-3)
-    torch.cuda.synchronize()
-    ms_train = (time.perf_counter() - t0) * 1e3 / n_train
+    ms_train = e0.elapsed_time(e1) / n_train
     line = {"workload": "network", "rows_inference": n_inf,
             "inference": {"ms": ms_inf, "rows_per_s": n_inf / (ms_inf / 1e3),
                           "tflops": n_inf * flop_row / (ms_inf / 1e3) / 1e12,
                           "kernel": "k_infer_tc (tcgen05.mma kind::f16, TMEM accumulator)"},
             "training": {"batch": 65536, "ms_per_step": ms_train,
                          "tflops": 3 * 65536 * flop_row / (ms_train / 1e3) / 1e12,
-                         "kernels": "mma.sync m16n8k16 BF16 forward / backward + Adam (host-timed, includes the loss read-back)"},
+                         "kernels": "k_train_fwd + k_train_bwd (tcgen05.mma kind::f16, TMEM accumulators) + "
+                                    "k_reduce_adam, per step with the minibatch gather (CUDA events over whole runs)"},
             "flop_per_row": flop_row}
     print(json.dumps(line), flush=True)
     return 0
@@ -649,6 +775,14 @@ def main(argv=None):
     ap.add_argument("--subdomains", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-unbundled", action="store_true", help="skip the one-wavelength-per-path frames")
+    ap.add_argument("--no-surrogate", action="store_true",
+                    help="skip the large-frame network-versus-plain record (image error and throughput)")
+    ap.add_argument("--resident", type=int, default=0,
+                    help="host-driven form: at most this many subdomain BVHs in device memory (out-of-core streaming)")
+    ap.add_argument("--block-chunks", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="graph form: 128-ray chunks per block instead of 32 per warp (bit 0 closest hit, bit 1 shadow)")
+    ap.add_argument("--top-nodes", type=int, default=0,
+                    help="top BVH nodes per subdomain staged in shared memory by the traversal kernel")
     ap.add_argument("--batched", type=int, default=2, choices=[0, 1, 2],
                     help="0: host-driven; 1: persistent kernels + CUDA graph; 2: graph form")
     ap.add_argument("--no-graph", action="store_true",

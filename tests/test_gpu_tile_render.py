@@ -90,16 +90,17 @@ def trained(sdd):
     from paper_1912_05494_gb300 import surrogate as SG
     tiles, tn, tk = S.tile_set(2, 16)  # the room's tile set
     ts = sdd.TileSetHandle(tiles)
-    net, hist, held = SG.train_for_tileset(ts.h, tiles, tn, tk, n_samples=1 << 19, steps=1500, rays=128)
+    net, hist, held = SG.train_for_tileset(ts.h, tiles, tn, tk, n_samples=1 << 20, steps=8000, rays=256)
     return net, hist, held
 
 
 def test_network_gain_over_the_thin_slab(sdd, trained):
-    """Sky-lit room, 96 x 64, 128 spp: the network form stays within 3 % (block averages) of
-    brute force, where the thin-slab stand-in is off by more than four times as much."""
+    """Sky-lit room, 96 x 64: at 1024 spp (brute-force noise floor ~0.2 % on 8 x 8 block
+    averages) the network form stays within 1 % of brute force, where the thin-slab stand-in
+    is off by more than twenty times as much."""
     net, hist, _ = trained
     assert np.mean(hist[-50:]) < 0.2 * hist[0]
-    sc, cam, spec = S.tile_room_scene(width=96, height=64, spp=128)
+    sc, cam, spec = S.tile_room_scene(width=96, height=64, spp=1024)
     sc.sun = np.zeros_like(sc.sun)
     h = sdd.SceneHandle(sc)
     bf = render(sdd, h, cam, spec)
@@ -109,9 +110,10 @@ def test_network_gain_over_the_thin_slab(sdd, trained):
     noise = rel_err(blocks(bf2, cam), blocks(bf, cam))
     e_net = rel_err(blocks(net_img, cam), blocks(bf, cam))
     e_slab = rel_err(blocks(slab, cam), blocks(bf, cam))
-    assert noise < 0.01, noise
-    assert e_net < 0.03, (e_net, noise)
-    assert e_net < 0.25 * e_slab, (e_net, e_slab)
+    print(f"room, sky only, 1024 spp: network {e_net:.4f}, thin slab {e_slab:.4f}, noise floor {noise:.4f}")
+    assert noise < 0.004, noise
+    assert e_net < 0.01, (e_net, noise)
+    assert e_net < 0.05 * e_slab, (e_net, e_slab)
 
 
 def test_network_form_with_the_sun_is_within_the_noise_floor(sdd, trained):
@@ -186,16 +188,17 @@ def test_bundled_batched_form_is_bit_identical_with_tiles(sdd, trained, use_net)
 
 def test_bundled_network_form_matches_brute_force(sdd, trained):
     """Sky-lit room as in the gain test, with bundles of 9 in the network form against the
-    unbundled brute-force image: block averages within 3 %, like the unbundled network form.
+    unbundled brute-force image: block averages within 1 %, like the unbundled network form.
     The wavelengths of a bundle share their draws, so its noise is correlated across the
     spectrum and the wavelength-summed blocks are noisier at equal spp: the bundled render
-    takes 256 spp to the reference's 128."""
+    takes 2048 spp to the reference's 1024."""
     net, _, _ = trained
-    sc, cam, spec = S.tile_room_scene(width=96, height=64, spp=128)
+    sc, cam, spec = S.tile_room_scene(width=96, height=64, spp=1024)
     sc.sun = np.zeros_like(sc.sun)
     h = sdd.SceneHandle(sc)
     bf = render(sdd, h, cam, spec)
-    net_img = render(sdd, h, cam, S.RenderSpec(**{**spec.__dict__, "bundle": 9, "spp": 256}), use_surrogate=1,
+    net_img = render(sdd, h, cam, S.RenderSpec(**{**spec.__dict__, "bundle": 9, "spp": 2048}), use_surrogate=1,
                      surrogate=net, batched=1)
     e_net = rel_err(blocks(net_img, cam), blocks(bf, cam))
-    assert e_net < 0.03, e_net
+    print(f"room, sky only, bundles of 9: network {e_net:.4f}")
+    assert e_net < 0.01, e_net
