@@ -90,22 +90,26 @@ def source_hash(paths) -> str:
     return h.hexdigest()[:16]
 
 
-def read_traffic(form):
-    """DRAM bytes per traversed ray from the committed ncu summary of the form's traversal
-    kernel, or None when there is none or its source changed since the counters were taken."""
+def read_counters(form):
+    """Counters of the committed ncu summary of the form's traversal kernel (DRAM and L2 bytes
+    per traversed ray, L2-throughput and issue-slot fractions), or {} when there is none or its
+    source changed since the counters were taken."""
     if form not in NCU_SUMMARY or not os.path.exists(NCU_SUMMARY[form]):
-        return None
+        return {}
     vals = {}
     for line in open(NCU_SUMMARY[form]):
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip()
     if vals.get("kernel_source_hash") != source_hash(TRAVERSE_SOURCES[form]):
-        return None
-    try:
-        return float(vals["traffic_bytes_per_ray"])
-    except (KeyError, ValueError):
-        return None
+        return {}
+    out = {}
+    for k in ("traffic_bytes_per_ray", "l2_bytes_per_ray", "l2_frac", "issue_frac"):
+        try:
+            out[k] = float(vals[k])
+        except (KeyError, ValueError):
+            pass
+    return out
 
 
 def measured_peaks():
@@ -501,7 +505,8 @@ def run_gpu(args):
 
     peak, peak_kind = measured_peaks()
     avg_launch_ms = ms_trav / max(n_trav, 1)
-    per_ray = read_traffic(args.batched)
+    ctr = read_counters(args.batched)
+    per_ray = ctr.get("traffic_bytes_per_ray")
     traffic = per_ray * cnt["rays_closest"] / trav_launches if per_ray is not None else None
     bytes_per_launch = trav_bytes / trav_launches
     achieved = bytes_per_launch / (avg_launch_ms / 1e3) / 1e9 if avg_launch_ms > 0 else 0.0
@@ -509,8 +514,16 @@ def run_gpu(args):
                 "traffic": traffic if not persistent else None, "peak_kind": peak_kind,
                 "kernel": TRAVERSE_KERNEL[args.batched],
                 "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_ms,
+                "l2_traffic": (ctr["l2_bytes_per_ray"] * cnt["rays_closest"] / trav_launches
+                               if "l2_bytes_per_ray" in ctr and not persistent else None),
+                "l2_frac": ctr.get("l2_frac") if not persistent else None,
+                "issue_frac": ctr.get("issue_frac") if not persistent else None,
+                "counters_source": os.path.relpath(NCU_SUMMARY[args.batched], ROOT) if ctr else None,
                 "note": "algorithmic bytes = BVH nodes x 64 B + triangle records x 48 B + 44 B ray state per "
-                        "subdomain visit; the ~35 MB BVH is L2-resident, so frac can exceed what DRAM moves"}
+                        "subdomain visit; the ~35 MB BVH is L2-resident, so frac can exceed what DRAM moves. "
+                        "traffic / l2_traffic: DRAM / L2 bytes per launch scaled from the committed ncu capture; "
+                        "l2_frac = L2 throughput and issue_frac = issue slots active, as fractions of ncu's peaks, "
+                        "from the same capture: the walk is latency-bound at ~2/3 of its issue slots"}
 
     surrogate = None
     if rank == 0 and world == 1 and not args.no_surrogate:

@@ -289,12 +289,13 @@ sdd_status device_error(uint32_t e) {
 
 // ------------------------------------------------------------------ out-of-core subdomains
 // Sec. 5: sub-domains are loaded according to the memory available and unloaded when few
-// rays remain for them.  With streaming on (host-driven form), before every traversal pass the
-// (at most cap) subdomains with the most queued rays are made resident: a subdomain not in a
-// device slot takes the slot of a resident one that is left out (the one with the fewest
-// queued rays), its nodes and triangle records copied in from pinned host memory with their
-// links rebased to the slot.  Rays queued for subdomains left out wait, unchanged, for a
-// later pass.  The traversal code is the same; only where the nodes lie changes, so every
+// rays remain for them.  With streaming on (host-driven form), before every traversal pass a
+// resident subdomain stays in its device slot while its queue holds rays; slots whose
+// subdomain has none left (or that are empty) go to the waiting subdomains with the most
+// queued rays, whose nodes and triangle records are copied in from pinned host memory with
+// their links rebased to the slot.  Rays queued for subdomains that are not resident wait,
+// unchanged, for a later pass; rays cross each slab at most once, so resident queues drain
+// and every waiting queue is reached.  The traversal code is the same; only where the nodes lie changes, so every
 // hit, path and image is the all-resident one bit for bit.
 
 // Copy subdomain `sub` into slot j (links rebased to the slot), enqueued on st.
@@ -324,38 +325,31 @@ cudaError_t load_subdomain(sdd_scene* s, int sub, int j, cudaStream_t st) {
   return e;
 }
 
-// Make the subdomains with the most queued rays resident (at most cap); runs[i] = the queued
-// count of a resident subdomain this pass traverses, 0 for the others.  sc gets the slots.
+// Keep the resident subdomains that still have queued rays and give the other slots to the
+// waiting subdomains with the most queued rays; runs[i] = the queued count of a resident
+// subdomain this pass traverses, 0 for the others.  sc gets the slots.
 sdd_status stream_in(sdd_scene* s, const int* counts, DevScene* sc, int* runs, cudaStream_t st) {
   auto& m = s->strm;
-  std::vector<int> want;
-  for (int i = 0; i < s->n_sub; ++i)
-    if (counts[i] > 0) want.push_back(i);
-  std::sort(want.begin(), want.end(), [&](int a, int b) {
-    if (counts[a] != counts[b]) return counts[a] > counts[b];
-    const bool ra = m.slot_of[a] >= 0, rb = m.slot_of[b] >= 0;
-    if (ra != rb) return ra;  // on a tie keep what is resident
-    return a < b;
-  });
-  if ((int)want.size() > m.cap) want.resize(m.cap);
   std::vector<char> keep(s->n_sub, 0);
-  for (int i : want) keep[i] = 1;
-  for (int i : want) {
-    if (m.slot_of[i] >= 0) continue;
-    int j = -1;
-    for (int k = 0; k < m.cap; ++k) {  // an empty slot, else the left-out occupant with the fewest rays
-      const int o = m.sub_in_slot[k];
-      if (o < 0) {
-        j = k;
-        break;
-      }
-      if (!keep[o] && (j < 0 || counts[o] < counts[m.sub_in_slot[j]])) j = k;
-    }
-    if (j < 0) return fail(SDD_ERR_STATE, "no subdomain slot to evict");
-    if (m.sub_in_slot[j] >= 0) m.slot_of[m.sub_in_slot[j]] = -1;
+  std::vector<int> waiting;
+  for (int i = 0; i < s->n_sub; ++i) {
+    if (counts[i] <= 0) continue;
+    if (m.slot_of[i] >= 0) keep[i] = 1;
+    else waiting.push_back(i);
+  }
+  std::sort(waiting.begin(), waiting.end(), [&](int a, int b) {
+    return counts[a] != counts[b] ? counts[a] > counts[b] : a < b;
+  });
+  size_t next = 0;
+  for (int j = 0; j < m.cap && next < waiting.size(); ++j) {
+    const int o = m.sub_in_slot[j];
+    if (o >= 0 && keep[o]) continue;  // still has rays: stays
+    const int i = waiting[next++];
+    if (o >= 0) m.slot_of[o] = -1;    // nothing left for it: unloaded
     CK(load_subdomain(s, i, j, st));
     m.slot_of[i] = j;
     m.sub_in_slot[j] = i;
+    keep[i] = 1;
   }
   sc->nodes = m.d_nodes.p;
   sc->tris = m.d_tris.p;
@@ -380,12 +374,11 @@ sdd_status carry_queues(sdd_scene* s, const int* counts, const int* runs, uint32
   return SDD_OK;
 }
 
-// Pass bound of one generation's passes: without streaming a ray crosses each slab at most
-// once; with it a pass may leave subdomains out, each left-out queue waits at most
-// ceil(n_sub / cap) passes per pass it would otherwise have had.
+// Pass bound of one generation's passes (beyond it: SDD_ERR_TIMEOUT): without streaming a ray
+// crosses each slab at most once; with it waiting queues add passes, generously bounded.
 int pass_bound(const sdd_scene* s) {
   const int n = s->n_sub;
-  return s->strm.cap > 0 ? (2 * n + 2) * ((n + s->strm.cap - 1) / s->strm.cap + 1) : 2 * kMaxSubdomains + 2;
+  return s->strm.cap > 0 ? (2 * n + 2) * (n + 1) : 2 * kMaxSubdomains + 2;
 }
 
 Sched make_sched(int n_sub, const int* counts, int cap, int block, int* total_blocks, long long* total) {

@@ -45,13 +45,24 @@ def test_reduce_max_over_two_gloo_ranks():
     assert got == [(0, 15.0), (1, 15.0)]
 
 
-def test_traffic_is_null_when_kernel_changed(tmp_path, monkeypatch):
+def test_counters_are_null_when_kernel_changed(tmp_path, monkeypatch):
     sys.path.insert(0, ROOT)
     import bench
     f = tmp_path / "s.md"
-    f.write_text("- kernel_source_hash: 0000\n- traffic_bytes_per_ray: 123.0\n")
+    body = "- traffic_bytes_per_ray: 123.0\n- l2_bytes_per_ray: 700\n- l2_frac: 0.45\n- issue_frac: 0.66\n"
+    f.write_text("- kernel_source_hash: 0000\n" + body)
     monkeypatch.setattr(bench, "NCU_SUMMARY", {2: str(f)})
-    assert bench.read_traffic(2) is None
-    assert bench.read_traffic(1) is None  # the persistent form has no per-kernel summary
-    f.write_text(f"- kernel_source_hash: {bench.source_hash(bench.TRAVERSE_SOURCES[2])}\n- traffic_bytes_per_ray: 123.0\n")
-    assert bench.read_traffic(2) == 123.0
+    assert bench.read_counters(2) == {}
+    assert bench.read_counters(1) == {}  # the persistent form has no per-kernel summary
+    f.write_text(f"- kernel_source_hash: {bench.source_hash(bench.TRAVERSE_SOURCES[2])}\n" + body)
+    assert bench.read_counters(2) == {"traffic_bytes_per_ray": 123.0, "l2_bytes_per_ray": 700.0, "l2_frac": 0.45,
+                                      "issue_frac": 0.66}
+
+
+def test_committed_traversal_summary_matches_the_sources():
+    """The committed ncu summary of the benchmarked traversal kernel was taken on the current
+    sources (otherwise the bench reports its DRAM / L2 counters as null)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.read_counters(2)
+    assert set(c) == {"traffic_bytes_per_ray", "l2_bytes_per_ray", "l2_frac", "issue_frac"}
