@@ -55,7 +55,14 @@ class OrcOpts(C.Structure):
         ("n_lambda", C.c_int), ("lambda_nm", C.c_void_p), ("spp", C.c_int),
         ("seed", C.c_uint64), ("max_depth", C.c_int), ("mode", C.c_int),
         ("rr_start_depth", C.c_int), ("n_pixels", C.c_int), ("pixels", C.c_void_p),
-        ("n_threads", C.c_int), ("bundle", C.c_int),
+        ("n_threads", C.c_int), ("bundle", C.c_int), ("photons", C.c_void_p),
+    ]
+
+
+class OrcPhotonOpts(C.Structure):
+    _fields_ = [
+        ("n_per_lambda", C.c_int), ("seed", C.c_uint64), ("max_depth", C.c_int), ("center", C.c_float * 3),
+        ("radius", C.c_float), ("distance", C.c_float), ("gather_radius", C.c_float), ("n_threads", C.c_int),
     ]
 
 
@@ -75,6 +82,13 @@ def lib():
         _lib.orc_beer_lambert.argtypes = [C.c_double, C.c_double, C.c_double]
         _lib.orc_cone_dir.argtypes = [C.c_int, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]
         _lib.orc_hardware_threads.restype = C.c_int
+        _lib.orc_photons_trace.restype = C.c_void_p
+        _lib.orc_photons_trace.argtypes = [C.c_void_p, C.POINTER(OrcPhotonOpts), C.c_int, C.c_void_p]
+        _lib.orc_photons_destroy.argtypes = [C.c_void_p]
+        _lib.orc_photons_count.restype = C.c_int64
+        _lib.orc_photons_count.argtypes = [C.c_void_p, C.c_int]
+        _lib.orc_photons_get.argtypes = [C.c_void_p, C.c_int] + [C.c_void_p] * 5
+        _lib.orc_photons_gather.argtypes = [C.c_void_p, C.c_int] + [C.c_void_p] * 5
     return _lib
 
 
@@ -271,7 +285,13 @@ class OracleScene:
         lib().orc_closest(self.h, n, _p(org), _p(dirs), int(brute), _p(t), _p(prim))
         return t, prim
 
-    def render(self, cam, spec, pixels=None, n_threads=0, want_paths=False):
+    def photon_maps(self, lambda_nm, n_per_lambda, seed, center, radius, distance, gather_radius, max_depth=16,
+                    n_threads=0):
+        """Caustic and global photon maps of the sun (Sec. 3.2) for the given wavelengths."""
+        return PhotonMaps(self, lambda_nm, n_per_lambda, seed, center, radius, distance, gather_radius, max_depth,
+                          n_threads)
+
+    def render(self, cam, spec, pixels=None, n_threads=0, want_paths=False, photons=None):
         """Returns (film [n_px, L], path_L [n_px, spp, L] or None, hash or None)."""
         c = OrcCamera()
         for i in range(3):
@@ -289,6 +309,7 @@ class OracleScene:
         o.pixels = _p(px)
         o.n_threads = n_threads
         o.bundle = getattr(spec, "bundle", 1)
+        o.photons = photons.h if photons is not None else None
         npx = cam.width * cam.height if px is None else px.size
         film = np.zeros((npx, lam.size))
         path_L = np.zeros((npx, spec.spp, lam.size)) if want_paths else None
@@ -313,3 +334,49 @@ def bubble_scatter(d, rad, sin_i, u, n_re, k=0.0, r=50e-6):
     lib().orc_bubble_scatter(n, _p(d), _p(rad), _p(sin_i), C.c_double(r), C.c_double(n_re), C.c_double(k),
                              u.shape[1], _p(u), _p(out), _p(ev))
     return out, ev
+
+
+MAP_CAUSTIC, MAP_GLOBAL = 0, 1
+
+
+class PhotonMaps:
+    """Oracle photon maps (a handle of orc_photons_trace)."""
+
+    def __init__(self, osc, lambda_nm, n_per_lambda, seed, center, radius, distance, gather_radius, max_depth,
+                 n_threads):
+        self.lambda_nm = _c(lambda_nm, np.float32)
+        o = OrcPhotonOpts()
+        o.n_per_lambda, o.seed, o.max_depth = int(n_per_lambda), int(seed), int(max_depth)
+        for i in range(3):
+            o.center[i] = float(center[i])
+        o.radius, o.distance, o.gather_radius, o.n_threads = radius, distance, gather_radius, n_threads
+        self._osc = osc
+        self.h = lib().orc_photons_trace(osc.h, C.byref(o), self.lambda_nm.size, _p(self.lambda_nm))
+        if not self.h:
+            raise ValueError("oracle rejected the photon-map arguments")
+        self.radius = float(gather_radius)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().orc_photons_destroy(self.h)
+            self.h = None
+
+    def count(self, which):
+        return int(lib().orc_photons_count(self.h, which))
+
+    def photons(self, which):
+        """dict of pos [n, 3], nrm [n, 3], power [n], lam [n], id [n] of one map."""
+        n = self.count(which)
+        pos, nrm, pw = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros(n)
+        lam, pid = np.zeros(n, np.int32), np.zeros(n, np.uint32)
+        lib().orc_photons_get(self.h, which, _p(pos), _p(nrm), _p(pw), _p(lam), _p(pid))
+        return {"pos": pos, "nrm": nrm, "power": pw, "lam": lam, "id": pid}
+
+    def gather(self, x, nrm, lam):
+        """Irradiance estimates (caustic, global) at points x [n, 3] with normals nrm [n, 3]."""
+        x = _c(x, np.float64).reshape(-1, 3)
+        nrm = _c(np.broadcast_to(nrm, x.shape), np.float64)
+        lam = _c(np.broadcast_to(lam, (x.shape[0],)), np.int32)
+        ec, eg = np.zeros(x.shape[0]), np.zeros(x.shape[0])
+        lib().orc_photons_gather(self.h, x.shape[0], _p(x), _p(nrm), _p(lam), _p(ec), _p(eg))
+        return ec, eg

@@ -90,7 +90,8 @@ Draw draw(uint32_t pixel, uint32_t sample, uint32_t bounce, uint32_t stream, uin
   philox4x32_10(ctr, key, o);
   return Draw{{u01(o[0]), u01(o[1]), u01(o[2]), u01(o[3])}};
 }
-enum { STREAM_PATH = 0, STREAM_NEE = 1, STREAM_TILE = 2, STREAM_SHADOW_TILE = 3 };
+enum { STREAM_PATH = 0, STREAM_NEE = 1, STREAM_TILE = 2, STREAM_SHADOW_TILE = 3, STREAM_PHOTON = 4,
+       STREAM_PHOTON_TILE = 5 };
 
 // ---------------------------------------------------------------- optics
 // Unpolarised Fresnel reflectance at a plane interface, incident medium with real index
@@ -706,6 +707,130 @@ double seg0_of(const Scene& s, V3 n, V3 dir) {
   return s.eps / std::max(std::fabs(dot(n, dir)), 1e-6);
 }
 
+// ---------------------------------------------------------------- photon maps (Sec. 3.2)
+// Jensen's photon mapping as the paper describes it: a pre-rendering step shoots photons
+// from the light source and stores those that hit (diffuse) objects in two maps, one for
+// caustics and one for global illumination; the rendering step takes the direct and
+// specular contributions by ray tracing and the caustic and indirect diffuse ones from the
+// maps.  Here the light source is the sun (the sky's light is left to the camera paths).
+// Photon i of wavelength index l leaves a disc of radius R centred on C + D s (s the
+// direction toward the sun), perpendicular to s, at a point uniform over the disc, travelling
+// along -w with w uniform in the sun's cone about s; it carries the power
+//   Phi = L_sun(l) Omega (s . w) pi R^2 / N,   Omega = 2 pi (1 - cos half-angle),
+// so that the photons' summed power through any surface is, in expectation, the sun's flux.
+// Its path follows the Monte Carlo rules of the camera paths (Fresnel choice at solid glass,
+// R / (R + T) at thin slabs with the power times R + T, one brute-force ray through a tile)
+// and at a diffuse surface it is stored, then survives with probability albedo (power
+// unchanged) into a cosine-distributed direction.  Map of a stored photon:
+//   caustic  the photon met no diffuse surface yet, and some specular event changed its
+//            direction (solid glass, a reflection at a slab, a non-ballistic tile exit);
+//   global   the photon was reflected by a diffuse surface before;
+// a photon that reached its first diffuse surface only through straight slab transmission
+// (or ballistic tile exits) is direct light, which the renderer's sun NEE counts: not stored.
+enum { MAP_CAUSTIC = 0, MAP_GLOBAL = 1 };
+struct Photon {
+  V3 pos, nrm;   // hit point, geometric normal facing the arriving photon
+  double power;
+  int lam, map;
+  uint32_t id, seq;  // photon index, diffuse surfaces met before this one
+};
+struct PhotonEmitter {
+  V3 center;
+  double radius, distance;
+};
+
+void trace_photon(const Scene& s, const PhotonEmitter& em, uint32_t i, int l, double lambda_nm, uint64_t seed,
+                  int n_per_lambda, int max_depth, std::vector<Photon>& out) {
+  const V3 sdir = s.sun_dir;
+  Draw ue = draw(i, 0, 0, STREAM_PHOTON, 0, (uint32_t)l, seed);
+  V3 t1, t2;
+  onb(sdir, &t1, &t2);
+  const double rr = em.radius * std::sqrt(ue.u[0]), phi = 2.0 * PI * ue.u[1];
+  V3 o = em.center + em.distance * sdir + (rr * std::cos(phi)) * t1 + (rr * std::sin(phi)) * t2;
+  const V3 w = cone_dir(sdir, s.sun_h, ue.u[2], ue.u[3]);
+  V3 d = -1.0 * w;
+  const double omega = 2.0 * PI * s.sun_h;
+  double power = s.sun[l] * omega * dot(sdir, w) * PI * em.radius * em.radius / n_per_lambda;
+  bool spec = false, diff = false;
+  uint32_t seq = 0;
+  double seg0 = 0.0;
+  for (int v = 1; v <= max_depth; ++v) {
+    Hit h = closest(s, o, d);
+    if (h.prim < 0) return;
+    const Material& m = s.mats[s.mat[h.prim]];
+    V3 p = o + h.t * d;
+    V3 ng = s.nrm[h.prim];
+    double cos_n = dot(d, ng);
+    V3 nf = cos_n < 0.0 ? ng : -1.0 * ng;
+    double cos_i = std::fabs(cos_n);
+    Draw u = draw(i, 0, (uint32_t)v, STREAM_PHOTON, 0, (uint32_t)l, seed);
+    V3 nd;
+    if (m.kind == MAT_SOLID) {
+      bool inside = cos_n > 0.0;
+      if (inside) power *= beer_lambert(m.k[l], h.t + seg0, lambda_nm);
+      double n1 = inside ? m.n[l] : 1.0;
+      cd n2 = inside ? cd(1.0, 0.0) : cd(m.n[l], m.k[l]);
+      double R = fresnel_R(cos_i, n1, n2);
+      double eta = n1 / std::real(n2);
+      double c2 = 1.0 - eta * eta * (1.0 - cos_i * cos_i);
+      if (u.u[0] < R || c2 <= 0.0) nd = reflect(d, nf);
+      else nd = normalize(eta * d + (eta * cos_i - std::sqrt(c2)) * nf);
+      spec = true;
+    } else if (m.kind == MAT_SLAB) {
+      double Rs, Ts;
+      slab_RT(cos_i, m.n[l], m.k[l], m.thickness, lambda_nm, &Rs, &Ts, s.slab_pol);
+      power *= (Rs + Ts);
+      if (u.u[0] < Rs / (Rs + Ts)) {
+        nd = reflect(d, nf);
+        spec = true;
+      } else {
+        nd = d;
+      }
+    } else if (m.kind == MAT_TILE) {
+      int ti = s.mat_tile[s.mat[h.prim]];
+      double x, y;
+      V3 dl, tt1, tt2;
+      tile_frame(s, p, ng, d, &x, &y, &dl, &tt1, &tt2);
+      TileRay r = tile_trace(s.tile_geom[ti], s.tiles[ti], x, y, dl, m.n[l], m.k[l], lambda_nm, i, 0, (uint32_t)v,
+                             (uint32_t)l, seed, 64, STREAM_PHOTON_TILE);
+      if (r.side == 2) return;
+      power *= r.w;
+      nd = normalize(r.dir.x * tt1 + r.dir.y * tt2 + r.dir.z * ng);
+      if (!(r.side == 1 && dot(r.dir, dl) > kCos1Deg)) spec = true;
+    } else if (m.kind == MAT_DIFFUSE) {
+      if (spec || diff) out.push_back(Photon{p, nf, power, l, diff ? MAP_GLOBAL : MAP_CAUSTIC, i, seq});
+      if (u.u[3] >= m.albedo[l]) return;  // absorbed: survival with probability albedo
+      nd = cosine_dir(nf, u.u[1], u.u[2]);
+      diff = true;
+      ++seq;
+    } else {
+      return;
+    }
+    o = offset(s, p, ng, nd);
+    seg0 = seg0_of(s, ng, nd);
+    d = nd;
+  }
+}
+
+// Irradiance estimate of one map at x on a surface with normal n: the power of the map's
+// photons of wavelength l within distance r of x that arrived on the same side (n_p . n > 0),
+// over the disc area pi r^2.
+double photon_gather(const std::vector<Photon>& ph, int map, V3 x, V3 n, int l, double r) {
+  double sum = 0.0;
+  for (const Photon& p : ph) {
+    if (p.map != map || p.lam != l || dot(p.nrm, n) <= 0.0) continue;
+    V3 e = p.pos - x;
+    if (dot(e, e) < r * r) sum += p.power;
+  }
+  return sum / (PI * r * r);
+}
+
+struct PhotonMapD {
+  std::vector<Photon> ph;
+  std::vector<double> lambda_nm;
+  double radius;
+};
+
 struct RenderCtx {
   const Scene* s;
   const Camera* cam;
@@ -713,6 +838,8 @@ struct RenderCtx {
   int n_lambda, spp, max_depth, rr_start;
   uint64_t seed;
   int bundle;  // wavelengths per draw bundle (1: every wavelength draws on its own)
+  const PhotonMapD* pm = nullptr;  // photon maps: the first diffuse vertex takes the sun's caustic
+                                   // and indirect light from them
 };
 
 // Deterministic splitting (Sec. 3.1): the radiance carried back along one ray, spawning
@@ -787,10 +914,11 @@ double trace_mc(const RenderCtx& cx, uint32_t px, uint32_t sample, int lam, uint
   camera_ray(*cx.cam, (int)px, jit.u[0] - 0.5, jit.u[1] - 0.5, &o, &d);
   double thr = 1.0, L = 0.0, seg0 = 0.0;
   bool sun_counted = false;
+  bool photon_done = false;  // with photon maps: the sun's light was taken at a diffuse vertex
   for (int v = 1;; ++v) {
     Hit h = closest(s, o, d);
     if (h.prim < 0) {
-      L += thr * escape_radiance(s, d, lam, sun_counted);
+      L += thr * escape_radiance(s, d, lam, sun_counted || photon_done);
       ph.word(0xFFFFFFFFu); ph.byte(EV_ESCAPE);
       break;
     }
@@ -836,7 +964,13 @@ double trace_mc(const RenderCtx& cx, uint32_t px, uint32_t sample, int lam, uint
       }
     } else if (m.kind == MAT_DIFFUSE) {
       ph.byte(EV_DIFFUSE);
-      if (s.sun_h > 0.0) {
+      if (cx.pm && !photon_done) {  // the sun's caustic and indirect light from the maps
+        const double r = cx.pm->radius;
+        const double E = photon_gather(cx.pm->ph, MAP_CAUSTIC, p, nf, lam, r) +
+                         photon_gather(cx.pm->ph, MAP_GLOBAL, p, nf, lam, r);
+        L += thr * m.albedo[lam] / PI * E;
+      }
+      if (s.sun_h > 0.0 && !photon_done) {
         Draw un = draw(px, sample, (uint32_t)v, STREAM_NEE, 0, word, cx.seed);
         V3 wl = cone_dir(s.sun_dir, s.sun_h, un.u[0], un.u[1]);
         double cl = dot(nf, wl);
@@ -850,6 +984,7 @@ double trace_mc(const RenderCtx& cx, uint32_t px, uint32_t sample, int lam, uint
       thr *= m.albedo[lam];
       nd = cosine_dir(nf, u.u[1], u.u[2]);
       sun_counted = true;
+      if (cx.pm) photon_done = true;  // later vertices: sky light only
     } else if (m.kind == MAT_TILE) {
       // heterogeneous tile: one brute-force ray through the tile on the tile stream
       int ti = s.mat_tile[s.mat[h.prim]];
@@ -994,6 +1129,7 @@ struct OrcOpts {
   const int32_t* pixels;
   int n_threads;       // 0 = hardware concurrency
   int bundle;          // Monte Carlo: wavelengths sharing their draws (0 or 1: none)
+  const void* photons; // photon maps of orc_photons_trace for the same wavelengths, or NULL
 };
 
 struct OrcHandle {
@@ -1099,21 +1235,16 @@ void orc_closest(void* hp, int n, const double* org, const double* dir, int brut
 // Render the listed pixels.  film[pixel][lambda] is the mean over samples; path_L and
 // path_hash ([pixel][sample][lambda], optional) hold every path's radiance and event hash
 // (Monte Carlo only).  Returns 0, or -1 on bad arguments.
-int orc_render(void* hp, const OrcCamera* cam_in, const OrcOpts* op, double* film,
-               double* path_L, uint32_t* path_hash) {
-  OrcHandle* h = (OrcHandle*)hp;
+// Resample every material and light table to a list of wavelengths.
+void prepare_tables(OrcHandle* h, int n_lambda, const float* lambda_nm) {
   Scene& s = h->s;
-  if (op->n_lambda <= 0 || op->spp <= 0 || op->max_depth < 0) return -1;
-  if (op->mode == 0 && op->spp != 1) return -1;
-  if (op->bundle < 0 || op->bundle > 64 || (op->bundle > 1 && op->mode == 0)) return -1;
-  // Resample every table to the render wavelengths.
   s.mats.assign(h->mat_kind.size(), Material{});
   for (size_t m = 0; m < h->mat_kind.size(); ++m) {
     Material& mm = s.mats[m];
     mm.kind = h->mat_kind[m];
     mm.thickness = h->mat_thick[m];
-    for (int l = 0; l < op->n_lambda; ++l) {
-      double lam = op->lambda_nm[l];
+    for (int l = 0; l < n_lambda; ++l) {
+      double lam = lambda_nm[l];
       const size_t o = m * (size_t)h->n_table;
       mm.n.push_back(interp(h->table_nm.data(), h->mat_n.data() + o, h->n_table, lam));
       mm.k.push_back(interp(h->table_nm.data(), h->mat_k.data() + o, h->n_table, lam));
@@ -1121,11 +1252,107 @@ int orc_render(void* hp, const OrcCamera* cam_in, const OrcOpts* op, double* fil
     }
   }
   s.sky.clear(); s.sun.clear();
-  for (int l = 0; l < op->n_lambda; ++l) {
-    s.sky.push_back(interp(h->table_nm.data(), h->sky.data(), h->n_table, op->lambda_nm[l]));
-    s.sun.push_back(h->sun.empty() ? 0.0
-                                   : interp(h->table_nm.data(), h->sun.data(), h->n_table, op->lambda_nm[l]));
+  for (int l = 0; l < n_lambda; ++l) {
+    s.sky.push_back(interp(h->table_nm.data(), h->sky.data(), h->n_table, lambda_nm[l]));
+    s.sun.push_back(h->sun.empty() ? 0.0 : interp(h->table_nm.data(), h->sun.data(), h->n_table, lambda_nm[l]));
   }
+}
+
+struct OrcPhotonOpts {
+  int n_per_lambda;     // photons shot per wavelength
+  uint64_t seed;
+  int max_depth;        // surface interactions per photon
+  float center[3];      // emitter disc: centre C + distance * (direction to the sun), radius
+  float radius, distance;
+  float gather_radius;  // density-estimation radius (m)
+  int n_threads;        // 0 = hardware concurrency
+};
+
+// Photon maps (Sec. 3.2) for a list of wavelengths; returns a handle (orc_photons_destroy).
+void* orc_photons_trace(void* hp, const OrcPhotonOpts* po, int n_lambda, const float* lambda_nm) {
+  OrcHandle* h = (OrcHandle*)hp;
+  if (!po || n_lambda <= 0 || po->n_per_lambda <= 0 || po->radius <= 0.f || !(h->s.sun_h > 0.0)) return nullptr;
+  prepare_tables(h, n_lambda, lambda_nm);
+  PhotonEmitter em{{po->center[0], po->center[1], po->center[2]}, po->radius, po->distance};
+  const int total = po->n_per_lambda * n_lambda;
+  int nth = po->n_threads > 0 ? po->n_threads : (int)std::thread::hardware_concurrency();
+  if (nth < 1) nth = 1;
+  std::vector<std::vector<Photon>> part(nth);
+  std::atomic<int> next{0};
+  auto worker = [&](int t) {
+    for (;;) {
+      int j = next.fetch_add(1);
+      if (j >= total) break;
+      const int l = j / po->n_per_lambda;
+      trace_photon(h->s, em, (uint32_t)(j % po->n_per_lambda), l, lambda_nm[l], po->seed, po->n_per_lambda,
+                   po->max_depth, part[t]);
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nth; ++t) pool.emplace_back(worker, t);
+  for (auto& t : pool) t.join();
+  PhotonMapD* pm = new PhotonMapD;
+  for (auto& v : part) pm->ph.insert(pm->ph.end(), v.begin(), v.end());
+  std::sort(pm->ph.begin(), pm->ph.end(), [](const Photon& a, const Photon& b) {
+    if (a.lam != b.lam) return a.lam < b.lam;
+    if (a.id != b.id) return a.id < b.id;
+    return a.seq < b.seq;
+  });
+  pm->lambda_nm.assign(lambda_nm, lambda_nm + n_lambda);
+  pm->radius = po->gather_radius;
+  return pm;
+}
+
+void orc_photons_destroy(void* pm) { delete (PhotonMapD*)pm; }
+
+int64_t orc_photons_count(const void* pmv, int map) {
+  const PhotonMapD* pm = (const PhotonMapD*)pmv;
+  int64_t c = 0;
+  for (const Photon& p : pm->ph) c += p.map == map;
+  return c;
+}
+
+// The photons of one map in (wavelength, photon index, order along its path) order.
+void orc_photons_get(const void* pmv, int map, double* pos, double* nrm, double* power, int32_t* lam,
+                     uint32_t* id) {
+  const PhotonMapD* pm = (const PhotonMapD*)pmv;
+  size_t k = 0;
+  for (const Photon& p : pm->ph) {
+    if (p.map != map) continue;
+    pos[3 * k] = p.pos.x; pos[3 * k + 1] = p.pos.y; pos[3 * k + 2] = p.pos.z;
+    nrm[3 * k] = p.nrm.x; nrm[3 * k + 1] = p.nrm.y; nrm[3 * k + 2] = p.nrm.z;
+    power[k] = p.power;
+    lam[k] = p.lam;
+    id[k] = p.id;
+    ++k;
+  }
+}
+
+// Irradiance estimates of both maps at n query points (position, unit normal, wavelength index).
+void orc_photons_gather(const void* pmv, int n, const double* x, const double* nrm, const int32_t* lam,
+                        double* E_caustic, double* E_global) {
+  const PhotonMapD* pm = (const PhotonMapD*)pmv;
+  for (int i = 0; i < n; ++i) {
+    V3 p{x[3 * i], x[3 * i + 1], x[3 * i + 2]}, nn{nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2]};
+    E_caustic[i] = photon_gather(pm->ph, MAP_CAUSTIC, p, nn, lam[i], pm->radius);
+    E_global[i] = photon_gather(pm->ph, MAP_GLOBAL, p, nn, lam[i], pm->radius);
+  }
+}
+
+int orc_render(void* hp, const OrcCamera* cam_in, const OrcOpts* op, double* film,
+               double* path_L, uint32_t* path_hash) {
+  OrcHandle* h = (OrcHandle*)hp;
+  Scene& s = h->s;
+  if (op->n_lambda <= 0 || op->spp <= 0 || op->max_depth < 0) return -1;
+  if (op->mode == 0 && op->spp != 1) return -1;
+  if (op->bundle < 0 || op->bundle > 64 || (op->bundle > 1 && op->mode == 0)) return -1;
+  const PhotonMapD* pm = (const PhotonMapD*)op->photons;
+  if (pm) {  // the maps must be for the same wavelengths, and are for Monte Carlo paths
+    if (op->mode == 0 || (int)pm->lambda_nm.size() != op->n_lambda) return -1;
+    for (int l = 0; l < op->n_lambda; ++l)
+      if (pm->lambda_nm[l] != op->lambda_nm[l]) return -1;
+  }
+  prepare_tables(h, op->n_lambda, op->lambda_nm);
   Camera cam;
   V3 pos{cam_in->pos[0], cam_in->pos[1], cam_in->pos[2]};
   V3 at{cam_in->look_at[0], cam_in->look_at[1], cam_in->look_at[2]};
@@ -1142,7 +1369,7 @@ int orc_render(void* hp, const OrcCamera* cam_in, const OrcOpts* op, double* fil
   cam.height = cam_in->height;
   std::vector<double> lam_d(op->lambda_nm, op->lambda_nm + op->n_lambda);
   RenderCtx cx{&s, &cam, lam_d.data(), op->n_lambda, op->spp, op->max_depth, op->rr_start_depth, op->seed,
-               op->bundle > 1 ? op->bundle : 1};
+               op->bundle > 1 ? op->bundle : 1, pm};
 
   int npx = op->n_pixels > 0 ? op->n_pixels : cam.width * cam.height;
   int nth = op->n_threads > 0 ? op->n_threads : (int)std::thread::hardware_concurrency();
