@@ -38,6 +38,7 @@ extern "C" {
 typedef struct sdd_scene sdd_scene;         /* opaque, owned by the library */
 typedef struct sdd_tileset sdd_tileset;     /* heterogeneous glass tiles (see below) */
 typedef struct sdd_surrogate sdd_surrogate; /* tile-BTDF network (see below) */
+typedef struct sdd_photon_maps sdd_photon_maps; /* caustic and global photon maps (see below) */
 
 typedef enum {
   SDD_OK = 0,
@@ -161,6 +162,14 @@ typedef struct {
                               Each wavelength's chain keeps its distribution; the wavelengths of a
                               bundle become correlated.  Every form; at heterogeneous tiles each
                               member leaves on its own ray (brute force or network) */
+  const sdd_photon_maps* photon_maps; /* Sec. 3.2 (Jensen's photon mapping): NULL = none; else maps
+                              built for the same wavelength list (equal lambda_nm), used by Monte
+                              Carlo renders of the host-driven form (batched = 0) without bundles
+                              (bundle <= 1) or the network (use_surrogate = 0); other
+                              combinations return SDD_ERR_ARG.  At its first diffuse vertex a path
+                              adds albedo / pi x (E_caustic + E_global) of the maps at the hit point
+                              beside the sun NEE; later vertices take sky light only (no NEE, no sun
+                              disc on escape) */
 } sdd_render_opts;
 
 /* Build the scene: validates, partitions the geometry into n_subdomains slabs (Sec. 5:
@@ -373,6 +382,59 @@ sdd_status sdd_surrogate_get_weights(const sdd_surrogate* s, void* host_out, siz
 sdd_status sdd_surrogate_set_weights(sdd_surrogate* s, const void* host_in, size_t bytes);
 /* Predictions [n][8] (device) for n rows of raw inputs (any n; processed max_batch at a time). */
 sdd_status sdd_surrogate_infer(sdd_surrogate* s, int n, const float* raw_dev, float* out_dev, void* cuda_stream);
+
+/* ---------------------------------------------------------------- photon maps
+ * Sec. 3.2: Jensen's photon mapping as the global-illumination algorithm.  Photons leave a
+ * disc of radius R centred on C + D s (s toward the sun), perpendicular to s, from a point
+ * uniform over the disc, along -w with w uniform in the sun's cone, each with power
+ * L_sun(lambda) Omega (s . w) pi R^2 / N (N photons per wavelength), so that the photons'
+ * power through any plane is, in expectation, the sun's flux through the disc's shadow.  The
+ * disc must cover the region of interest as seen from the sun.  Photon i of wavelength index
+ * l draws on Philox (i, 0, bounce, photon stream, wavelength l); it is traced through the
+ * subdomain queues like the camera paths: at glass it follows the Monte Carlo rules of the
+ * camera paths (Fresnel choice at solid glass with Beer-Lambert inside, R / (R + T) at thin
+ * slabs with the power times R + T, one brute-force ray through a heterogeneous tile on the
+ * photon tile stream); at a diffuse surface it is stored, then survives with probability
+ * albedo (power unchanged) into a cosine-distributed direction.  Maps: caustic (0) -- a
+ * specular event changed the photon's direction (solid glass, a reflection at a slab, a
+ * non-ballistic tile exit) before any diffuse surface; global (1) -- the photon was
+ * reflected by a diffuse surface before.  A photon that reached its first diffuse surface
+ * only through straight slab transmission (or ballistic tile exits) is direct light, which
+ * the sun NEE counts, and is not stored.  Density estimate at x with normal n: the power of
+ * the map's photons of that wavelength within gather_radius r of x that arrived on the
+ * side of n, over pi r^2.  The photons of each map are sorted into a hashed uniform grid of
+ * cell edge 2 r. */
+typedef struct {
+  int n_lambda;             /* wavelengths (each traced on its own), 1..4096 */
+  const float* lambda_nm;   /* host [n_lambda], positive */
+  int n_per_lambda;         /* photons per wavelength, N >= 1; n_lambda * N <= 2^31 - 1 */
+  uint64_t seed;            /* Philox key */
+  int max_depth;            /* surface interactions per photon, 1..255 */
+  float center[3];          /* emitter disc: centre C + distance * s, radius R > 0 */
+  float radius_m;
+  float distance_m;
+  float gather_radius_m;    /* density-estimation radius r > 0 */
+} sdd_photon_opts;
+/* Trace the photons and build both maps (device memory owned by the handle; the maps keep
+ * no reference to the scene).  Requires a sun (SDD_ERR_STATE otherwise).  The stored-photon
+ * buffers start at n_lambda * N entries per map and grow by tracing again when that was too
+ * few; a map of more than 2^30 photons returns SDD_ERR_QUEUE_OVERFLOW. */
+sdd_status sdd_photon_maps_build(sdd_scene* scene, const sdd_photon_opts* opts, sdd_photon_maps** out,
+                                 void* cuda_stream);
+void sdd_photon_maps_destroy(sdd_photon_maps* maps);
+/* Stored photons per map. */
+sdd_status sdd_photon_maps_count(const sdd_photon_maps* maps, int64_t* n_caustic, int64_t* n_global);
+/* Copy the photons of map `map` (0 caustic, 1 global) to HOST arrays of count entries, in no
+ * particular order: position [n][3], normal facing the photon's arrival [n][3], power [n],
+ * wavelength index [n], photon index within its wavelength [n], diffuse surfaces met before
+ * this one [n].  Any pointer may be NULL. */
+sdd_status sdd_photon_maps_get(const sdd_photon_maps* maps, int map, float* pos, float* nrm, float* power,
+                               int32_t* lam, uint32_t* id, uint32_t* seq);
+/* Density estimates of both maps at n query points (device arrays): x [n][3], unit normal
+ * [n][3], wavelength index [n] (an index with no photons gives 0); writes device
+ * E_caustic [n] and E_global [n] (irradiance per nm in the illuminant's units). */
+sdd_status sdd_photon_gather(const sdd_photon_maps* maps, int n, const float* x_dev, const float* nrm_dev,
+                             const int32_t* lam_dev, float* e_caustic_dev, float* e_global_dev, void* cuda_stream);
 
 /* sdd_trace_closest without any allocation (the paper has no counterpart; this serves
  * callers).  Same arguments, results and queue passes as sdd_trace_closest, but its scratch

@@ -16,7 +16,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsdd.so")
 ROOT = os.path.dirname(HERE)
 
-CUDA_SOURCES = ["api.cu", "render_kernels.cu", "bundle_kernels.cu", "graph_kernels.cu", "noalloc.cu", "persistent.cu", "persistent_bundle.cu", "tile.cu", "mlp.cu", "surrogate_render.cu"]
+CUDA_SOURCES = ["api.cu", "render_kernels.cu", "photon.cu", "bundle_kernels.cu", "graph_kernels.cu", "noalloc.cu", "persistent.cu", "persistent_bundle.cu", "tile.cu", "mlp.cu", "surrogate_render.cu"]
 CXX_SOURCES = ["scene_build.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # The persistent kernel reads, within one launch, ray / hit / queue / path data that other

@@ -21,6 +21,7 @@
 #include "../../include/sdd.h"
 #include "graph_form.h"
 #include "persistent.cuh"
+#include "photon.cuh"
 #include "render_kernels.cuh"
 #include "scene_build.h"
 #include "surrogate_render.cuh"
@@ -238,6 +239,36 @@ struct sdd_scene {
     }
     ev_used.clear();
     ev_next = 0;
+  }
+};
+
+// Photon maps (Sec. 3.2): per map (0 caustic, 1 global) the stored photons as appended
+// (kept for sdd_photon_maps_get) and sorted into the buckets of the hashed grid.
+struct sdd_photon_maps {
+  std::vector<float> lambda;  // wavelengths the maps were built for
+  float radius = 0.f, inv_cell = 0.f;
+  uint32_t mask = 0;
+  int64_t count[2] = {0, 0};
+  DevArr<float4> raw_pos[2], raw_nrm[2], pos[2], nrm[2];
+  DevArr<uint2> raw_id[2];
+  DevArr<uint32_t> start[2];
+  ~sdd_photon_maps() {
+    for (int m = 0; m < 2; ++m) {
+      raw_pos[m].release(); raw_nrm[m].release(); pos[m].release(); nrm[m].release();
+      raw_id[m].release(); start[m].release();
+    }
+  }
+  PhotonMapDev view() const {
+    PhotonMapDev v{};
+    for (int m = 0; m < 2; ++m) {
+      v.pos_pw[m] = pos[m].p;
+      v.nrm_lam[m] = nrm[m].p;
+      v.start[m] = start[m].p;
+    }
+    v.mask = mask;
+    v.inv_cell = inv_cell;
+    v.radius = radius;
+    return v;
   }
 };
 
@@ -877,6 +908,36 @@ std::vector<WaveDesc> halve_waves(const std::vector<WaveDesc>& in) {
 
 // (pixel, sample, wavelength) chains of a wave: its cells times the samples, with bundles the
 // members of each cell's bundle (the last bundle of a pixel may be partial).
+// Parameters every launch over the scene shares: geometry, the spectral tables of the
+// current wavelength set (prepare_spectral) and illuminant, and the tile set.
+RenderParams scene_params(const sdd_scene* s, int L) {
+  RenderParams p{};
+  p.sc = s->dev;
+  p.sp.n_lambda = L;
+  p.sp.lambda_nm = s->t_lambda.p;
+  p.sp.mat_kind = s->t_kind.p;
+  p.sp.mat_thick = s->t_thick.p;
+  p.sp.mat_n = s->t_n.p;
+  p.sp.mat_k = s->t_k.p;
+  p.sp.mat_albedo = s->t_alb.p;
+  p.sp.sky = s->t_sky.p;
+  p.sp.sun = s->t_sun.p;
+  p.sp.sky_mode = s->sky_mode;
+  p.sp.slab_pol = s->slab_pol;
+  double sd[3] = {s->sun_dir[0], s->sun_dir[1], s->sun_dir[2]};
+  double l = std::sqrt(sd[0] * sd[0] + sd[1] * sd[1] + sd[2] * sd[2]);
+  p.sp.sun_dir = make_float3((float)(sd[0] / l), (float)(sd[1] / l), (float)(sd[2] / l));
+  bool has_sun = !s->il_sun.empty() && s->sun_half > 0.f;
+  double h = has_sun ? 2.0 * std::sin(0.5 * s->sun_half) * std::sin(0.5 * s->sun_half) : 0.0;
+  p.sp.sun_h = (float)h;
+  p.sp.sun_omega = (float)(2.0 * M_PI * h);
+  if (!s->tile_mats.empty()) {
+    p.tiles = *tileset_device_view(s->tiles);
+    p.mat_tile = s->t_mat_tile.p;
+  }
+  return p;
+}
+
 int64_t spectral_paths(const RenderParams& p, const WaveDesc& w) {
   if (p.bundle <= 1) return (int64_t)w.n_paths;
   const int64_t nb = p.n_bundles, c0 = w.c0, c1 = (int64_t)w.c0 + w.nc;
@@ -915,6 +976,14 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
   if (o->batched != 0 && s->strm.cap > 0)
     return fail(SDD_ERR_STATE, "out-of-core subdomains (resident_subdomains > 0) need the host-driven form (batched = 0)");
   if (o->bundle < 0 || o->bundle > kMaxBundle) return fail(SDD_ERR_ARG, "bundle must be in [0, 16]");
+  if (const sdd_photon_maps* pm = o->photon_maps) {
+    if (o->mode != SDD_MODE_MONTE_CARLO) return fail(SDD_ERR_ARG, "photon maps need Monte Carlo mode");
+    if (o->batched != 0) return fail(SDD_ERR_ARG, "photon maps need the host-driven form (batched = 0)");
+    if (o->bundle > 1) return fail(SDD_ERR_ARG, "photon maps need bundle <= 1");
+    if (o->use_surrogate) return fail(SDD_ERR_ARG, "photon maps need use_surrogate = 0");
+    if (pm->lambda != std::vector<float>(o->lambda_nm, o->lambda_nm + o->n_lambda))
+      return fail(SDD_ERR_ARG, "photon maps were built for another wavelength list");
+  }
   const int B = o->bundle > 1 ? o->bundle : 1;
   if (B > 1 && o->mode != SDD_MODE_MONTE_CARLO) return fail(SDD_ERR_ARG, "spectral bundles need Monte Carlo mode");
   const int L = o->n_lambda;
@@ -976,28 +1045,7 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
     CK(cudaMemcpyAsync(s->pixel_list.p, o->pixels, sizeof(int32_t) * o->n_pixels, cudaMemcpyHostToDevice, st));
   }
 
-  RenderParams p{};
-  p.sc = s->dev;
-  p.sp.n_lambda = L;
-  p.sp.lambda_nm = s->t_lambda.p;
-  p.sp.mat_kind = s->t_kind.p;
-  p.sp.mat_thick = s->t_thick.p;
-  p.sp.mat_n = s->t_n.p;
-  p.sp.mat_k = s->t_k.p;
-  p.sp.mat_albedo = s->t_alb.p;
-  p.sp.sky = s->t_sky.p;
-  p.sp.sun = s->t_sun.p;
-  p.sp.sky_mode = s->sky_mode;
-  p.sp.slab_pol = s->slab_pol;
-  {
-    double sd[3] = {s->sun_dir[0], s->sun_dir[1], s->sun_dir[2]};
-    double l = std::sqrt(sd[0] * sd[0] + sd[1] * sd[1] + sd[2] * sd[2]);
-    p.sp.sun_dir = make_float3((float)(sd[0] / l), (float)(sd[1] / l), (float)(sd[2] / l));
-    bool has_sun = !s->il_sun.empty() && s->sun_half > 0.f;
-    double h = has_sun ? 2.0 * std::sin(0.5 * s->sun_half) * std::sin(0.5 * s->sun_half) : 0.0;
-    p.sp.sun_h = (float)h;
-    p.sp.sun_omega = (float)(2.0 * M_PI * h);
-  }
+  RenderParams p = scene_params(s, L);
   p.cam = make_camera(cam);
   p.pixel_list = o->n_pixels > 0 ? s->pixel_list.p : nullptr;
   p.n_px = (int)n_px;
@@ -1011,10 +1059,10 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
   p.path_hash = want_hash ? s->path_hash.p : nullptr;
   p.bundle = B;
   p.n_bundles = n_bundles;
-  if (!s->tile_mats.empty()) {
-    p.tiles = *tileset_device_view(s->tiles);
-    p.mat_tile = s->t_mat_tile.p;
-    p.use_surrogate = o->use_surrogate ? 1 : 0;
+  if (!s->tile_mats.empty()) p.use_surrogate = o->use_surrogate ? 1 : 0;
+  if (o->photon_maps) {
+    p.use_photons = 1;
+    p.pm = o->photon_maps->view();
   }
   if (p.use_surrogate) {
     // one entry per tile hit, with bundles one per member (entries ray << 4 | member)
@@ -1186,6 +1234,131 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
   s->ev_collect();
   s->stats.ms_total = s->stats.ms_raygen + s->stats.ms_traverse + s->stats.ms_shade + s->stats.ms_shadow +
                       s->stats.ms_film + s->stats.ms_tile;
+  return SDD_OK;
+}
+
+// ------------------------------------------------------------------ photon maps (Sec. 3.2)
+constexpr int64_t kMaxMapPhotons = 1LL << 30;
+
+// Trace every photon and append the stored ones to the maps' buffers (capacity cap per map);
+// *need receives each map's count, or an estimate of it when the tracing stopped early
+// because a buffer was full.
+sdd_status photon_trace(sdd_scene* s, const RenderParams& p, PhotonEmit pe, int64_t total, int max_depth,
+                        sdd_photon_maps* m, int* d_count, int64_t cap, int64_t need[2], cudaStream_t st) {
+  // one ray per photon; waves small enough that a wave's stores cannot overflow the counters
+  const int W = (int)std::min<int64_t>({total, 1LL << 24, (1LL << 29) / std::max(max_depth, 1)});
+  sdd_status r = ensure_workspace(s, (size_t)W, 1, 1, false, 1);
+  if (r) return r;
+  PhotonStore ps{};
+  for (int k = 0; k < 2; ++k) {
+    ps.pos_pw[k] = m->raw_pos[k].p;
+    ps.nrm_lam[k] = m->raw_nrm[k].p;
+    ps.id_seq[k] = m->raw_id[k].p;
+  }
+  ps.count = d_count;
+  ps.cap = (int)cap;
+  CK(cudaMemsetAsync(d_count, 0, 2 * sizeof(int), st));
+  for (int64_t j0 = 0; j0 < total; j0 += W) {
+    const int n = (int)std::min<int64_t>(W, total - j0);
+    pe.j0 = (uint32_t)j0;
+    CK(cudaMemsetAsync(s->d_ctl, 0, sizeof(Control), st));
+    RayBuf rb0{s->rb_o[0].p, s->rb_d[0].p, s->rb_info[0].p, W, nullptr};
+    launch_photon_emit(p, pe, n, rb0, s->q[0].p, s->d_ctl->q_count[0], W, s->d_ctl, st);
+    CK(cudaGetLastError());
+    int cur = 0, n_rays = n;
+    for (int gen = 0; n_rays > 0; ++gen) {
+      if (gen > max_depth + 1) return fail(SDD_ERR_TIMEOUT, "photon generations exceeded max_depth + 1");
+      RayBuf rc{s->rb_o[cur].p, s->rb_d[cur].p, s->rb_info[cur].p, W, nullptr};
+      RayBuf rn{s->rb_o[1 - cur].p, s->rb_d[1 - cur].p, s->rb_info[1 - cur].p, W, nullptr};
+      r = run_closest_passes(s, p, rc, W, st);
+      if (r) return r;
+      CK(cudaMemsetAsync(s->d_ctl, 0, offsetof(Control, error), st));
+      launch_photon_shade(p, pe, n_rays, rc, s->hits.p, rn, &s->d_ctl->next_rays, s->q[0].p, s->d_ctl->q_count[0], W,
+                          ps, s->d_ctl, st);
+      CK(cudaGetLastError());
+      r = read_ctl(s, st);
+      if (r) return r;
+      if (s->h_ctl->error) return device_error(s->h_ctl->error);
+      n_rays = s->h_ctl->next_rays;
+      if (n_rays > W) return fail(SDD_ERR_QUEUE_OVERFLOW, "photon ray buffer exceeded");
+      cur = 1 - cur;
+    }
+    int c[2];
+    CK(cudaMemcpyAsync(c, d_count, sizeof(c), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const int64_t done = j0 + n;
+    for (int k = 0; k < 2; ++k) need[k] = c[k];
+    if (c[0] > cap || c[1] > cap) {  // stop: project the counts over all photons
+      for (int k = 0; k < 2; ++k)
+        need[k] = std::min<int64_t>(kMaxMapPhotons + 1, (int64_t)((double)c[k] * (double)total / (double)done * 1.1) + 1024);
+      return SDD_OK;
+    }
+  }
+  return SDD_OK;
+}
+
+sdd_status photon_build(sdd_scene* s, const sdd_photon_opts* o, sdd_photon_maps* m, cudaStream_t st) {
+  const int L = o->n_lambda;
+  sdd_status r = prepare_spectral(s, L, o->lambda_nm, st);
+  if (r) return r;
+  r = ensure_ctl(s);
+  if (r) return r;
+  RenderParams p = scene_params(s, L);
+  p.seed = o->seed;
+  p.max_depth = o->max_depth;
+  p.mode = SDD_MODE_MONTE_CARLO;
+  PhotonEmit pe{};
+  {
+    double sd[3] = {s->sun_dir[0], s->sun_dir[1], s->sun_dir[2]};
+    const double l = std::sqrt(sd[0] * sd[0] + sd[1] * sd[1] + sd[2] * sd[2]);
+    pe.origin = make_float3((float)(o->center[0] + o->distance_m * sd[0] / l),
+                            (float)(o->center[1] + o->distance_m * sd[1] / l),
+                            (float)(o->center[2] + o->distance_m * sd[2] / l));
+    const double h = 2.0 * std::sin(0.5 * s->sun_half) * std::sin(0.5 * s->sun_half);
+    const double R = o->radius_m;
+    pe.radius = o->radius_m;
+    pe.power_scale = (float)(2.0 * M_PI * h * M_PI * R * R / o->n_per_lambda);
+    pe.n_per_lambda = o->n_per_lambda;
+  }
+  const int64_t total = (int64_t)L * o->n_per_lambda;
+  DevArr<int> d_count;
+  CK(d_count.ensure(2));
+  int64_t cap = std::min<int64_t>(std::max<int64_t>(total, 1024), kMaxMapPhotons);
+  int64_t need[2] = {0, 0};
+  for (int attempt = 0;; ++attempt) {
+    for (int k = 0; k < 2; ++k) {
+      CK(m->raw_pos[k].ensure((size_t)cap));
+      CK(m->raw_nrm[k].ensure((size_t)cap));
+      CK(m->raw_id[k].ensure((size_t)cap));
+    }
+    r = photon_trace(s, p, pe, total, o->max_depth, m, d_count.p, cap, need, st);
+    if (r) return r;
+    if (need[0] <= cap && need[1] <= cap) break;
+    if (need[0] > kMaxMapPhotons || need[1] > kMaxMapPhotons || attempt >= 4)
+      return fail(SDD_ERR_QUEUE_OVERFLOW, "a photon map would hold more than 2^30 photons");
+    cap = std::min<int64_t>(std::max(need[0], need[1]), kMaxMapPhotons);
+  }
+  // hashed grids of cell edge 2 r, one table size for both maps
+  m->count[0] = need[0];
+  m->count[1] = need[1];
+  m->radius = o->gather_radius_m;
+  m->inv_cell = 1.f / (2.f * o->gather_radius_m);
+  int64_t T = 1024;
+  while (T < 2 * std::max(need[0], need[1]) && T < (1LL << 27)) T <<= 1;
+  m->mask = (uint32_t)(T - 1);
+  DevArr<uint32_t> scratch;
+  CK(scratch.ensure((size_t)(T + T / 1024)));
+  for (int k = 0; k < 2; ++k) {
+    CK(m->start[k].ensure((size_t)T + 1));
+    CK(m->pos[k].ensure((size_t)need[k]));
+    CK(m->nrm[k].ensure((size_t)need[k]));
+    CK(build_photon_grid((int)need[k], m->raw_pos[k].p, m->raw_nrm[k].p, m->inv_cell, m->mask, m->start[k].p,
+                         scratch.p, m->pos[k].p, m->nrm[k].p, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  scratch.release();
+  d_count.release();
+  m->lambda.assign(o->lambda_nm, o->lambda_nm + L);
   return SDD_OK;
 }
 
@@ -1601,6 +1774,79 @@ sdd_status sdd_eval_optics(int n, const float* cos_i, const float* n_re, const f
   if (n == 0) return SDD_OK;
   cudaStream_t st = (cudaStream_t)stream;
   launch_eval_optics(n, cos_i, n_re, k, d, lam, slab_polarisation, R, Rs, Ts, st);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  return SDD_OK;
+}
+
+sdd_status sdd_photon_maps_build(sdd_scene* s, const sdd_photon_opts* o, sdd_photon_maps** out, void* stream) {
+  g_err.clear();
+  if (!s || !o || !out) return fail(SDD_ERR_ARG, "NULL scene, options or output");
+  *out = nullptr;
+  if (o->n_lambda < 1 || o->n_lambda > 4096 || !o->lambda_nm) return fail(SDD_ERR_ARG, "n_lambda must be in [1, 4096]");
+  for (int i = 0; i < o->n_lambda; ++i)
+    if (!(o->lambda_nm[i] > 0.f) || !std::isfinite(o->lambda_nm[i])) return fail(SDD_ERR_ARG, "lambda_nm must be positive");
+  if (o->n_per_lambda < 1) return fail(SDD_ERR_ARG, "n_per_lambda must be >= 1");
+  if ((int64_t)o->n_lambda * o->n_per_lambda > 0x7FFFFFFFLL) return fail(SDD_ERR_ARG, "n_lambda x n_per_lambda exceeds 2^31 - 1");
+  if (o->max_depth < 1 || o->max_depth > 255) return fail(SDD_ERR_ARG, "max_depth must be in [1, 255]");
+  for (int i = 0; i < 3; ++i)
+    if (!std::isfinite(o->center[i])) return fail(SDD_ERR_ARG, "center must be finite");
+  if (!(o->radius_m > 0.f) || !std::isfinite(o->radius_m)) return fail(SDD_ERR_ARG, "radius_m must be > 0");
+  if (!(o->distance_m >= 0.f) || !std::isfinite(o->distance_m)) return fail(SDD_ERR_ARG, "distance_m must be >= 0");
+  if (!(o->gather_radius_m > 0.f) || !std::isfinite(o->gather_radius_m))
+    return fail(SDD_ERR_ARG, "gather_radius_m must be > 0");
+  if (s->il_sun.empty() || !(s->sun_half > 0.f)) return fail(SDD_ERR_STATE, "photon maps need a sun");
+  sdd_photon_maps* m = new (std::nothrow) sdd_photon_maps;
+  if (!m) return fail(SDD_ERR_OOM, "host allocation failed");
+  sdd_status r = photon_build(s, o, m, (cudaStream_t)stream);
+  if (r) {
+    delete m;
+    return r;
+  }
+  *out = m;
+  return SDD_OK;
+}
+
+void sdd_photon_maps_destroy(sdd_photon_maps* m) { delete m; }
+
+sdd_status sdd_photon_maps_count(const sdd_photon_maps* m, int64_t* n_caustic, int64_t* n_global) {
+  g_err.clear();
+  if (!m || !n_caustic || !n_global) return fail(SDD_ERR_ARG, "NULL argument");
+  *n_caustic = m->count[0];
+  *n_global = m->count[1];
+  return SDD_OK;
+}
+
+sdd_status sdd_photon_maps_get(const sdd_photon_maps* m, int map, float* pos, float* nrm, float* power, int32_t* lam,
+                               uint32_t* id, uint32_t* seq) {
+  g_err.clear();
+  if (!m) return fail(SDD_ERR_ARG, "NULL maps");
+  if (map != 0 && map != 1) return fail(SDD_ERR_ARG, "map must be 0 (caustic) or 1 (global)");
+  const size_t n = (size_t)m->count[map];
+  if (n == 0) return SDD_OK;
+  std::vector<float4> a(n), b(n);
+  std::vector<uint2> c(n);
+  CK(cudaMemcpy(a.data(), m->raw_pos[map].p, n * sizeof(float4), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(b.data(), m->raw_nrm[map].p, n * sizeof(float4), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(c.data(), m->raw_id[map].p, n * sizeof(uint2), cudaMemcpyDeviceToHost));
+  for (size_t i = 0; i < n; ++i) {
+    if (pos) { pos[3 * i] = a[i].x; pos[3 * i + 1] = a[i].y; pos[3 * i + 2] = a[i].z; }
+    if (nrm) { nrm[3 * i] = b[i].x; nrm[3 * i + 1] = b[i].y; nrm[3 * i + 2] = b[i].z; }
+    if (power) power[i] = a[i].w;
+    if (lam) { int v; std::memcpy(&v, &b[i].w, sizeof(int)); lam[i] = v; }
+    if (id) id[i] = c[i].x;
+    if (seq) seq[i] = c[i].y;
+  }
+  return SDD_OK;
+}
+
+sdd_status sdd_photon_gather(const sdd_photon_maps* m, int n, const float* x, const float* nrm, const int32_t* lam,
+                             float* ec, float* eg, void* stream) {
+  g_err.clear();
+  if (!m || n < 0 || (n > 0 && (!x || !nrm || !lam || !ec || !eg))) return fail(SDD_ERR_ARG, "bad arguments");
+  if (n == 0) return SDD_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  launch_photon_gather(m->view(), n, x, nrm, lam, ec, eg, st);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(st));
   return SDD_OK;

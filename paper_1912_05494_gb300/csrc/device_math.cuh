@@ -26,7 +26,14 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 // Uniform in [0,1) from the top 24 bits (exact in FP32).
 __device__ __forceinline__ float u01(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
 
-enum Stream : uint32_t { STREAM_PATH = 0, STREAM_NEE = 1, STREAM_TILE = 2, STREAM_SHADOW_TILE = 3 };
+enum Stream : uint32_t {
+  STREAM_PATH = 0,
+  STREAM_NEE = 1,
+  STREAM_TILE = 2,
+  STREAM_SHADOW_TILE = 3,
+  STREAM_PHOTON = 4,       // photon emission and interactions (Sec. 3.2)
+  STREAM_PHOTON_TILE = 5   // a photon's brute-force ray through a heterogeneous tile
+};
 
 // Four uniforms keyed by (pixel, sample, bounce | stream | group, lambda index).
 __device__ __forceinline__ float4 draw4(uint32_t pixel, uint32_t sample, uint32_t bounce,

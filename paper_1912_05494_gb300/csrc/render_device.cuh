@@ -19,6 +19,7 @@
 #include <math_constants.h>
 
 #include "device_math.cuh"
+#include "photon_device.cuh"
 #include "render_kernels.cuh"
 #include "tile_device.cuh"
 
@@ -568,7 +569,10 @@ __device__ __forceinline__ void dev_traverse_warp(const RenderParams& p, int s, 
 // Shade ray r of the current generation (every lane of the warp calls this): adds escape
 // and NEE radiance, appends the children to `next` (counter *next_count) and the subdomain
 // queues q, and the shadow ray to sb (counter *shadow_count) and the shadow queues sq.
-template <int kTM>
+// kPM: with photon maps (Sec. 3.2) the first diffuse vertex of a path adds albedo / pi times
+// the maps' caustic and indirect irradiance beside its sun NEE; after it the path carries
+// FLAG_PHOTON_DONE and takes sky light only (no NEE, no sun disc on escape).
+template <int kTM, bool kPM = false>
 __device__ __forceinline__ void dev_shade(const RenderParams& p, const WaveDesc& w, int r, bool active, RayBuf cur,
                                           const float2* __restrict__ hits, RayBuf next, int* next_count, uint32_t* q,
                                           int* q_count, int qcap, ShadowBuf sb, int* shadow_count, uint32_t* sq,
@@ -599,7 +603,7 @@ __device__ __forceinline__ void dev_shade(const RenderParams& p, const WaveDesc&
       // already carries the overflow error; nothing is read through the stale index
       atomicOr(&ctl->error, ERR_QUEUE_OVERFLOW);
     } else if (prim == kMissPrim) {
-      path_L[slot] += thr * escape_radiance(p.sp, d, lam, (flags & FLAG_SUN_COUNTED) != 0u);
+      path_L[slot] += thr * escape_radiance(p.sp, d, lam, (flags & (FLAG_SUN_COUNTED | FLAG_PHOTON_DONE)) != 0u);
       hsh = fnv_byte(fnv_word(hsh, 0xFFFFFFFFu), EV_ESCAPE);
     } else {
       hsh = fnv_word(hsh, prim);
@@ -674,7 +678,12 @@ __device__ __forceinline__ void dev_shade(const RenderParams& p, const WaveDesc&
         } else if (kind == MAT_DIFFUSE) {
           float alb = __ldg(p.sp.mat_albedo + mi);
           if (mc) hsh = fnv_byte(hsh, EV_DIFFUSE);
-          if (p.sp.sun_h > 0.f) {
+          const bool photon_done = kPM && (flags & FLAG_PHOTON_DONE) != 0u;
+          if (kPM && !photon_done) {
+            const float E = photon_irradiance(p.pm, 0, pt, nf, lam) + photon_irradiance(p.pm, 1, pt, nf, lam);
+            path_L[slot] += thr * alb * kInvPi * E;
+          }
+          if (p.sp.sun_h > 0.f && !photon_done) {
             float3 wl = p.sp.sun_dir;
             if (mc) {
               float4 un = draw4(id.pixel, id.sample, v, STREAM_NEE, 0, lam, p.seed);
@@ -694,7 +703,7 @@ __device__ __forceinline__ void dev_shade(const RenderParams& p, const WaveDesc&
             e0 = true;
             d0 = cosine_dir(nf, u.y, u.z);
             thr0 = thr * alb;
-            meta0 = base_meta | ((flags | FLAG_SUN_COUNTED) << 8);
+            meta0 = base_meta | ((flags | FLAG_SUN_COUNTED | (kPM ? FLAG_PHOTON_DONE : 0u)) << 8);
           }
         } else if (kTM == 1 && kind == MAT_TILE && mc) {
           // heterogeneous tile: one brute-force ray through it on the tile stream

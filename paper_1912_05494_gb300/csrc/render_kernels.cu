@@ -38,14 +38,14 @@ __global__ void __launch_bounds__(kB, 12 * 128 / kB) k_traverse(RenderParams p, 
   dev_traverse_warp<kStats>(p, s, i, i < sch.count[s], s_nodes, n_staged, qp, rb, hits, ctl);
 }
 
-template <int kTM>
+template <int kTM, bool kPM = false>
 __global__ void __launch_bounds__(kBlock) k_shade(RenderParams p, WaveDesc w, int n_rays, RayBuf cur,
                                                   const float2* __restrict__ hits, RayBuf next, uint32_t* q,
                                                   int* q_count, int qcap, ShadowBuf sb, uint32_t* sq, int* sq_count,
                                                   float* path_L, Control* ctl) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
-  dev_shade<kTM>(p, w, r, r < n_rays, cur, hits, next, &ctl->next_rays, q, q_count, qcap, sb, &ctl->next_shadow, sq,
-                 sq_count, path_L, ctl);
+  dev_shade<kTM, kPM>(p, w, r, r < n_rays, cur, hits, next, &ctl->next_rays, q, q_count, qcap, sb, &ctl->next_shadow,
+                      sq, sq_count, path_L, ctl);
 }
 
 template <bool kStats, int kTM>
@@ -233,6 +233,15 @@ void launch_shade(const RenderParams& p, const WaveDesc& w, int n_rays, RayBuf c
     return launch_shade_bundle(p, w, n_rays, cur, hits, next, q, q_count, qcap, sb, sq, sq_count, path_L, ctl, st);
   if (n_rays <= 0) return;
   const int tm = tile_mode(p);
+  if (p.use_photons) {  // photon maps: host-driven, one wavelength per path, brute-force tiles
+    if (tm == 1)
+      k_shade<1, true><<<blocks_for(n_rays, kBlock), kBlock, 0, st>>>(p, w, n_rays, cur, hits, next, q, q_count, qcap,
+                                                                      sb, sq, sq_count, path_L, ctl);
+    else
+      k_shade<0, true><<<blocks_for(n_rays, kBlock), kBlock, 0, st>>>(p, w, n_rays, cur, hits, next, q, q_count, qcap,
+                                                                      sb, sq, sq_count, path_L, ctl);
+    return;
+  }
   if (tm == 1)
     k_shade<1><<<blocks_for(n_rays, kBlock), kBlock, 0, st>>>(p, w, n_rays, cur, hits, next, q, q_count, qcap, sb, sq,
                                                               sq_count, path_L, ctl);

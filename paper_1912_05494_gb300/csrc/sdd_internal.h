@@ -119,7 +119,19 @@ struct Control {
   unsigned long long graph_passes[2];   // graph form: closest-hit / shadow pass launches
 };
 
-enum RayFlags : uint32_t { FLAG_SUN_COUNTED = 1u };
+// Ray flags: the sun's direct light was counted by a diffuse vertex's NEE; with photon maps,
+// the sun's light was taken from the maps at a diffuse vertex (later vertices: sky only).
+enum RayFlags : uint32_t { FLAG_SUN_COUNTED = 1u, FLAG_PHOTON_DONE = 2u };
+
+// Photon maps on the device (Sec. 3.2): per map (0 caustic, 1 global) the stored photons
+// sorted into the buckets of a hashed uniform grid of cell edge 2 r.
+struct PhotonMapDev {
+  const float4* pos_pw[2];        // position xyz, power
+  const float4* nrm_lam[2];       // normal facing the photon's arrival xyz, wavelength index (int bits)
+  const uint32_t* start[2];       // [table + 1] first photon of each bucket
+  uint32_t mask;                  // table size - 1 (a power of two)
+  float inv_cell, radius;        // 1 / cell edge (cell edge 2 r), gather radius
+};
 
 struct WaveDesc {
   uint32_t s0, ns;        // samples [s0, s0 + ns)
@@ -154,6 +166,10 @@ struct RenderParams {
   // chains agree; 1 = every wavelength is its own path
   int bundle;
   int n_bundles;               // ceil(L / bundle)
+  // photon maps: the first diffuse vertex of a path takes the sun's caustic and indirect light
+  // from them (host-driven form, one wavelength per path)
+  int use_photons;
+  PhotonMapDev pm;
 };
 
 // Heterogeneous-tile mode compiled into the shading and shadow kernels: 0 the scene has no

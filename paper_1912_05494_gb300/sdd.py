@@ -61,7 +61,13 @@ class sdd_render_opts(C.Structure):
                 ("rr_start_depth", C.c_int), ("use_surrogate", C.c_int), ("batched", C.c_int),
                 ("n_pixels", C.c_int), ("pixels", C.c_void_p), ("wave_paths", C.c_int),
                 ("path_radiance_out", C.c_void_p), ("path_hash_out", C.c_void_p), ("surrogate", C.c_void_p),
-                ("bundle", C.c_int)]
+                ("bundle", C.c_int), ("photon_maps", C.c_void_p)]
+
+
+class sdd_photon_opts(C.Structure):
+    _fields_ = [("n_lambda", C.c_int), ("lambda_nm", C.c_void_p), ("n_per_lambda", C.c_int), ("seed", C.c_uint64),
+                ("max_depth", C.c_int), ("center", C.c_float * 3), ("radius_m", C.c_float),
+                ("distance_m", C.c_float), ("gather_radius_m", C.c_float)]
 
 
 class sdd_stats(C.Structure):
@@ -143,6 +149,12 @@ def lib():
         L.sdd_surrogate_train.argtypes = [vp, i32, vp, vp, C.POINTER(sdd_train_opts), vp, vp]
         L.sdd_surrogate_get_weights.argtypes = [vp, vp, C.c_size_t]
         L.sdd_surrogate_set_weights.argtypes = [vp, vp, C.c_size_t]
+        L.sdd_photon_maps_build.argtypes = [vp, C.POINTER(sdd_photon_opts), C.POINTER(vp), vp]
+        L.sdd_photon_maps_destroy.argtypes = [vp]
+        L.sdd_photon_maps_destroy.restype = None
+        L.sdd_photon_maps_count.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+        L.sdd_photon_maps_get.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp]
+        L.sdd_photon_gather.argtypes = [vp, i32, vp, vp, vp, vp, vp, vp]
         L.sdd_last_error.restype = C.c_char_p
         L.sdd_version.restype = C.c_char_p
         for name in ("sdd_scene_create", "sdd_render", "sdd_render_to_host", "sdd_set_profiling", "sdd_get_stats",
@@ -151,7 +163,8 @@ def lib():
                      "sdd_tile_trace_rays", "sdd_tile_generate", "sdd_surrogate_create", "sdd_surrogate_get_params",
                      "sdd_surrogate_set_params", "sdd_surrogate_gradients", "sdd_surrogate_train_step",
                      "sdd_surrogate_infer", "sdd_watchdog_selftest", "sdd_surrogate_train",
-                     "sdd_surrogate_get_weights", "sdd_surrogate_set_weights"):
+                     "sdd_surrogate_get_weights", "sdd_surrogate_set_weights", "sdd_photon_maps_build",
+                     "sdd_photon_maps_count", "sdd_photon_maps_get", "sdd_photon_gather"):
             getattr(L, name).restype = C.c_int
         L.sdd_watchdog_selftest.argtypes = [C.c_int]
         _lib = L
@@ -263,7 +276,7 @@ def make_camera(cam) -> sdd_camera:
 
 
 def make_opts(spec, pixels=None, wave_paths=0, batched=0, path_radiance_out=None, path_hash_out=None,
-              use_surrogate=0, surrogate=None):
+              use_surrogate=0, surrogate=None, photon_maps=None):
     keep = []
     o = sdd_render_opts()
     lam = _c(spec.lambda_nm, np.float32)
@@ -287,6 +300,7 @@ def make_opts(spec, pixels=None, wave_paths=0, batched=0, path_radiance_out=None
     o.path_hash_out = _ptr(path_hash_out)
     o.surrogate = surrogate.h if surrogate is not None else None
     o.bundle = getattr(spec, "bundle", 1)
+    o.photon_maps = photon_maps.h if photon_maps is not None else None
     o._keep = keep
     return o
 
@@ -483,6 +497,63 @@ class Surrogate:
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
             lib().sdd_surrogate_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+MAP_CAUSTIC, MAP_GLOBAL = 0, 1
+
+
+class PhotonMaps:
+    """Caustic and global photon maps of a scene (Sec. 3.2), built on the device by
+    sdd_photon_maps_build; pass as ``photon_maps=`` to a render."""
+
+    def __init__(self, scene_h, lambda_nm, n_per_lambda, seed, center, radius, distance, gather_radius, max_depth=16,
+                 stream=None):
+        lam = _c(lambda_nm, np.float32)
+        o = sdd_photon_opts()
+        o.n_lambda = lam.size
+        o.lambda_nm = C.c_void_p(lam.ctypes.data)
+        o.n_per_lambda = int(n_per_lambda)
+        o.seed = int(seed)
+        o.max_depth = int(max_depth)
+        o.center[:] = [float(c) for c in center]
+        o.radius_m = float(radius)
+        o.distance_m = float(distance)
+        o.gather_radius_m = float(gather_radius)
+        self.h = C.c_void_p()
+        _check(lib().sdd_photon_maps_build(scene_h, C.byref(o), C.byref(self.h), _stream(stream)))
+
+    def count(self, m: int) -> int:
+        a, b = C.c_int64(), C.c_int64()
+        _check(lib().sdd_photon_maps_count(self.h, C.byref(a), C.byref(b)))
+        return int(a.value if m == MAP_CAUSTIC else b.value)
+
+    def photons(self, m: int) -> dict:
+        """The photons of map m as host arrays, in no particular order."""
+        n = self.count(m)
+        out = {"pos": np.zeros((n, 3), np.float32), "nrm": np.zeros((n, 3), np.float32),
+               "power": np.zeros(n, np.float32), "lam": np.zeros(n, np.int32), "id": np.zeros(n, np.uint32),
+               "seq": np.zeros(n, np.uint32)}
+        if n:
+            _check(lib().sdd_photon_maps_get(self.h, int(m), *(C.c_void_p(out[k].ctypes.data)
+                                                               for k in ("pos", "nrm", "power", "lam", "id", "seq"))))
+        return out
+
+    def gather(self, x, nrm, lam, e_caustic, e_global, stream=None):
+        """Density estimates at device points x [n, 3] with unit normals nrm [n, 3] and
+        wavelength indices lam [n] (int32) into device e_caustic [n], e_global [n]."""
+        _check(lib().sdd_photon_gather(self.h, int(lam.numel()), _ptr(x), _ptr(nrm), _ptr(lam), _ptr(e_caustic),
+                                       _ptr(e_global), _stream(stream)))
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().sdd_photon_maps_destroy(self.h)
         self.h = None
 
     def __del__(self):

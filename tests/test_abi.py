@@ -94,3 +94,46 @@ def test_bad_slab_polarisation_is_rejected(lib):
     bad.slab_polarisation = 2
     with pytest.raises(lib.SddError, match="slab_polarisation"):
         lib.sdd_scene_create(bad)
+
+
+def test_photon_map_entry_points_reject_null_arguments(lib):
+    L = lib.lib()
+    out = C.c_void_p()
+    assert L.sdd_photon_maps_build(None, None, C.byref(out), None) == -1
+    assert L.sdd_photon_gather(None, 1, None, None, None, None, None, None) == -1
+    a, b = C.c_int64(), C.c_int64()
+    assert L.sdd_photon_maps_count(None, C.byref(a), C.byref(b)) == -1
+    assert L.sdd_photon_maps_get(None, 0, None, None, None, None, None, None) == -1
+    L.sdd_photon_maps_destroy(None)
+
+
+def test_binding_structures_match_the_header_layout(lib, tmp_path):
+    """The ctypes structures have the size and field offsets that a C compiler gives the
+    header's structures (compiled here with gcc)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"sdd_render_opts": lib.sdd_render_opts, "sdd_photon_opts": lib.sdd_photon_opts,
+               "sdd_scene_desc": lib.sdd_scene_desc, "sdd_camera": lib.sdd_camera, "sdd_tuning": lib.sdd_tuning,
+               "sdd_stats": lib.sdd_stats, "sdd_tileset_desc": lib.sdd_tileset_desc,
+               "sdd_train_opts": lib.sdd_train_opts, "sdd_scene_info": lib.sdd_scene_info}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "sdd.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for f in cls._fields_:
+            lines.append(f'  printf("{name} {f[0]} %zu\\n", offsetof({name}, {f[0]}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        s, f, v = line.split()
+        got[(s, f)] = int(v)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == C.sizeof(cls), name
+        for f in cls._fields_:
+            assert got[(name, f[0])] == getattr(cls, f[0]).offset, (name, f[0])
