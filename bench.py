@@ -19,6 +19,8 @@ Printed JSON line (rank 0):
              state) / its CUDA-event time, against the measured HBM copy bandwidth
   cpu_baseline  the FP64 oracle on the host cores on a bounded pixel sample of the same frame
   unbundled  the same frame with one wavelength per path
+  photons    (N = 1) photon maps (Sec. 3.2) of the nave: build rate for 81 x 2^20 sun photons,
+             density-estimation rate, and the frame at 4 spp with and without the maps
   surrogate  (N = 1) the surrogate half of the metric on the large batched frame: the BTDF
              network trained on the GPU, then 64 seeded 8 x 8-pixel blocks of the 3840 x 2160
              frame at 4,096 spp in the plain form (brute-force tile rays) and the network form
@@ -394,6 +396,82 @@ def surrogate_record():
             "setup_s": t_scene}
 
 
+def photon_record(sdd, h, cam, spec, flush, n_per_lambda=1 << 20, gather_radius=0.25, render_spp=4):
+    """Photon maps (Sec. 3.2) on the nave: the sun's photons for all 81 wavelengths from a disc
+    that covers the sunward wall (centre (30, 0, 7) m + 60 m toward the sun, radius 31 m), traced
+    through the subdomain queues and sorted into the hashed grids (timed build); then the frame
+    at render_spp samples per pixel in the host-driven form, one wavelength per path, with the
+    maps (the first diffuse vertex of every path gathers both maps) and without them."""
+    import torch
+    stream = torch.cuda.current_stream()
+    lam = spec.lambda_nm
+    opts = dict(n_per_lambda=n_per_lambda, seed=2024, center=(30.0, 0.0, 7.0), radius=31.0, distance=60.0,
+                gather_radius=gather_radius, max_depth=spec.max_depth)
+
+    def build():
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pm = sdd.PhotonMaps(h.h, lam, stream=stream, **opts)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return pm, e0.elapsed_time(e1)
+
+    pm, _ = build()  # untimed: allocations
+    pm.close()
+    pm, ms_build = build()
+    n_ph = n_per_lambda * lam.size
+    # gather throughput: 2^22 points on the floor and the walls' inner faces, random wavelengths
+    rng = np.random.default_rng(5)
+    nq = 1 << 22
+    q = np.column_stack([rng.uniform(0, 60, nq), rng.uniform(0, 12, nq), np.zeros(nq)]).astype(np.float32)
+    qn = np.tile(np.array([0, 0, 1], np.float32), (nq, 1))
+    ql = rng.integers(0, lam.size, nq).astype(np.int32)
+    dq, dn, dl = (torch.from_numpy(a).cuda() for a in (q, qn, ql))
+    ec, eg = torch.empty(nq, device="cuda"), torch.empty(nq, device="cuda")
+    pm.gather(dq, dn, dl, ec, eg)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    pm.gather(dq, dn, dl, ec, eg)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_gather = e0.elapsed_time(e1)
+    e_mean = (float(ec.mean()), float(eg.mean()))
+    # renders with and without the maps
+    from paper_1912_05494_gb300 import scenes as S
+    sp = S.RenderSpec(**{**spec.__dict__, "spp": render_spp, "bundle": 1})
+    n_px = cam.width * cam.height
+    out = torch.empty((n_px, lam.size), device="cuda")
+    paths = n_px * render_spp * lam.size
+
+    def render(**kw):
+        sdd.sdd_render(h.h, cam, sp, out, None, batched=0, **kw)
+        torch.cuda.synchronize()
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sdd.sdd_render(h.h, cam, sp, out, None, batched=0, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), float(out.double().mean())
+
+    ms_with, mean_with = render(photon_maps=pm)
+    ms_without, mean_without = render()
+    rec = {"n_photons": n_ph, "n_per_lambda": n_per_lambda, "gather_radius_m": gather_radius,
+           "stored": {"caustic": pm.count(0), "global": pm.count(1)},
+           "build_ms": ms_build, "build_Mphotons_per_s": n_ph / (ms_build / 1e3) / 1e6,
+           "gather_queries": nq, "gather_ms": ms_gather, "gather_Mqueries_per_s": nq / (ms_gather / 1e3) / 1e6,
+           "gather_mean_E": {"caustic": e_mean[0], "global": e_mean[1]},
+           "render": {"spp": render_spp, "form": "host-driven, one wavelength per path", "unit": UNIT,
+                      "value_with_maps": paths / (ms_with / 1e3) / 1e6,
+                      "value_without_maps": paths / (ms_without / 1e3) / 1e6,
+                      "image_mean_with_maps": mean_with, "image_mean_without_maps": mean_without},
+           "emitter": {"center": opts["center"], "distance_m": opts["distance"], "radius_m": opts["radius"]}}
+    pm.close()
+    return rec
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_env()
@@ -525,6 +603,10 @@ def run_gpu(args):
                         "l2_frac = L2 throughput and issue_frac = issue slots active, as fractions of ncu's peaks, "
                         "from the same capture: the walk is latency-bound at ~2/3 of its issue slots"}
 
+    photons = None
+    if rank == 0 and world == 1 and not args.no_photons:
+        photons = photon_record(sdd, h, cam, spec, flush)
+
     surrogate = None
     if rank == 0 and world == 1 and not args.no_surrogate:
         sclk = ClockSampler(local)
@@ -549,7 +631,7 @@ def run_gpu(args):
                            "parallelism": f"replicas x{world}", "wave_paths": args.wave_paths or "auto",
                            "spectral_bundle": args.bundle, "top_nodes_staged": args.top_nodes,
                            "block_chunks": args.block_chunks, "resident_subdomains": args.resident},
-                "e2e": e2e, "unbundled": unbundled, "surrogate": surrogate,
+                "e2e": e2e, "unbundled": unbundled, "surrogate": surrogate, "photons": photons,
                 "roofline": roofline, "cpu_baseline": cpu, "parity": parity, "clocks": clk,
                 "gpu_launches": launches,
                 "traversal_counts": {k: cnt[k] for k in ("rays_closest", "rays_shadow", "node_visits", "tri_tests",
@@ -771,6 +853,26 @@ def run_network(args):
     return 0
 
 
+def run_photons(args):
+    """The photon-map record alone (profiling captures; smaller frames and photon counts
+    through --width/--height/--photons-per-lambda)."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__ as g
+    g.build()
+    from paper_1912_05494_gb300 import scenes as S
+    from paper_1912_05494_gb300 import sdd
+
+    scene, cam, spec = S.nave_scene(seed=1, n_subdomains=args.subdomains)
+    cam = S.CameraData(**{**cam.__dict__, "width": args.width, "height": args.height})
+    h = sdd.SceneHandle(scene)
+    flush = torch.empty(512 * 1024 * 1024 // 4, device="cuda", dtype=torch.float32)
+    rec = photon_record(sdd, h, cam, spec, flush, n_per_lambda=args.photons_per_lambda)
+    print(json.dumps({"workload": "photons", "scene": f"nave {scene.n_triangles} triangles, 81 lambda, "
+                                                      f"{cam.width}x{cam.height}", **rec}), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -788,6 +890,7 @@ def main(argv=None):
     ap.add_argument("--subdomains", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-unbundled", action="store_true", help="skip the one-wavelength-per-path frames")
+    ap.add_argument("--no-photons", action="store_true", help="skip the photon-map record")
     ap.add_argument("--no-surrogate", action="store_true",
                     help="skip the large-frame network-versus-plain record (image error and throughput)")
     ap.add_argument("--resident", type=int, default=0,
@@ -802,7 +905,8 @@ def main(argv=None):
                     help="forms 1 and 2: launch the frame's kernels directly instead of replaying a CUDA graph")
     ap.add_argument("--bundle", type=int, default=14,
                     help="nave workload: wavelengths per spectral bundle (1 = every wavelength its own path)")
-    ap.add_argument("--workload", choices=["nave", "large", "network"], default="nave")
+    ap.add_argument("--workload", choices=["nave", "large", "network", "photons"], default="nave")
+    ap.add_argument("--photons-per-lambda", type=int, default=1 << 20, help="photons workload: sun photons per wavelength")
     ap.add_argument("--net-rows", type=int, default=1 << 24, help="network workload: inference rows per step")
     ap.add_argument("--train-steps", type=int, default=20000, help="large workload: network training steps")
     ap.add_argument("--train-samples", type=int, default=1 << 21, help="large workload: tile-tracer samples")
@@ -820,6 +924,8 @@ def main(argv=None):
         return run_large(args)
     if args.workload == "network":
         return run_network(args)
+    if args.workload == "photons":
+        return run_photons(args)
     return run_gpu(args)
 
 

@@ -237,8 +237,9 @@ __global__ void k_photon_gather(PhotonMapDev pm, int n, const float* __restrict_
   if (i >= n) return;
   const float3 p = make_float3(x[3 * i], x[3 * i + 1], x[3 * i + 2]);
   const float3 nn = make_float3(nrm[3 * i], nrm[3 * i + 1], nrm[3 * i + 2]);
-  ec[i] = photon_irradiance(pm, 0, p, nn, lam[i]);
-  eg[i] = photon_irradiance(pm, 1, p, nn, lam[i]);
+  const float2 e = photon_irradiance(pm, p, nn, lam[i]);
+  ec[i] = e.x;
+  eg[i] = e.y;
 }
 
 int blocks(long long n, int b) { return (int)((n + b - 1) / b); }

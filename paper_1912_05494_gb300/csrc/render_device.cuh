@@ -680,8 +680,8 @@ __device__ __forceinline__ void dev_shade(const RenderParams& p, const WaveDesc&
           if (mc) hsh = fnv_byte(hsh, EV_DIFFUSE);
           const bool photon_done = kPM && (flags & FLAG_PHOTON_DONE) != 0u;
           if (kPM && !photon_done) {
-            const float E = photon_irradiance(p.pm, 0, pt, nf, lam) + photon_irradiance(p.pm, 1, pt, nf, lam);
-            path_L[slot] += thr * alb * kInvPi * E;
+            const float2 E = photon_irradiance(p.pm, pt, nf, lam);
+            path_L[slot] += thr * alb * kInvPi * (E.x + E.y);
           }
           if (p.sp.sun_h > 0.f && !photon_done) {
             float3 wl = p.sp.sun_dir;
