@@ -45,27 +45,13 @@ __device__ __forceinline__ void normalise_row(const float q[kIn], float x[kIn]) 
   x[5] = (q[5] - 1.45f) / 0.2f;
   x[6] = (log10f(fmaxf(q[6], 1e-30f)) + 8.f) / 4.f;
 }
-// Fourier pair i of the normalised inputs x: sin and cos of 2 pi (B x)_i.
+// Fourier pair i of the normalised inputs x: sin and cos of 2 pi (B x)_i.  A row's 48 features
+// are [sin(2 pi B x) (16), cos(2 pi B x) (16), x (7), zero padding (9)].
 __device__ __forceinline__ void fourier_pair(const float x[kIn], const float* __restrict__ Bm, int i, float* s,
                                              float* c) {
   float p = 0.f;
   for (int j = 0; j < kIn; ++j) p += __ldg(Bm + i * kIn + j) * x[j];
   sincospif(2.f * p, s, c);
-}
-
-// The 48 BF16 features of one row of raw inputs q: [sin(2 pi B x), cos(2 pi B x), x, 0 pad]
-// with x the inputs normalised to [0, 1].
-__device__ __forceinline__ void features_row(const float q[kIn], const float* __restrict__ Bm, __nv_bfloat16* f) {
-  float x[kIn];
-  normalise_row(q, x);
-  for (int i = 0; i < kFourier; ++i) {
-    float s, c;
-    fourier_pair(x, Bm, i, &s, &c);
-    f[i] = __float2bfloat16(s);
-    f[kFourier + i] = __float2bfloat16(c);
-  }
-  for (int j = 0; j < kIn; ++j) f[2 * kFourier + j] = __float2bfloat16(x[j]);
-  for (int j = 2 * kFourier + kIn; j < kFeat; ++j) f[j] = __float2bfloat16(0.f);
 }
 
 }  // namespace net

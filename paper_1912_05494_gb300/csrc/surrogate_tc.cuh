@@ -1,18 +1,21 @@
 // surrogate_tc.cuh -- fused inference of the tile-BTDF network on the 5th-generation tensor
 // cores (tcgen05 with a TMEM accumulator), used by the renderer and by sdd_surrogate_infer.
 //
-// One CTA of 256 threads per SM keeps every layer's BF16 weights in shared memory in the
+// One CTA of 512 threads per SM keeps every layer's BF16 weights in shared memory in the
 // canonical K-major layout without swizzle (8-row x 16-byte core matrices; element (r, k) of
 // an [R][K] operand at (r / 8) * SBO + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2 bytes,
 // SBO = K / 8 * 128) and loops over chunks of 128 rows.  Per chunk:
-//   1. threads 0..127 gather one row's raw inputs (policy) and write its 48 Fourier features
-//      as the A operand;
+//   1. threads 0..127 gather one row's raw inputs (policy) and stage them normalised; then
+//      all 512 threads write the 48 features as the A operand (four threads per row, four
+//      Fourier pairs each);
 //   2. per layer, one thread issues K / 16 tcgen05.mma (M = 128, N = 128 or 16, BF16 in,
 //      FP32 accumulate) into 128 TMEM columns and commits them to an mbarrier;
-//   3. every warp reads its quadrant of rows (warp % 4) and half of the columns (warp / 4)
-//      back with tcgen05.ld, adds the bias, applies GELU and writes the BF16 activations as
-//      the next layer's A operand (the output layer's 16 columns go through the head into a
-//      staging array for the policy's consumer).
+//   3. every warp reads its quadrant of rows (warp % 4) and a quarter of the columns
+//      (warp / 4) back with tcgen05.ld, adds the bias, applies GELU and writes the BF16
+//      activations as the next layer's A operand (the output layer's 16 columns go through
+//      the head into a staging array for the policy's consumer).  Sixteen warps per SM
+//      rather than eight: the epilogues (exact-erf GELU, packing) bound the kernel, not the
+//      tensor cores.
 // Every mbarrier wait is bounded by the global timer; on expiry the kernel raises the
 // policy's timeout error bit, waits (bounded) for the MMAs in flight, frees its TMEM and
 // returns.
@@ -23,7 +26,7 @@
 namespace sdd {
 namespace tc {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr int kRows = 128;
 constexpr uint32_t kTmemCols = 128;
 constexpr uint32_t kErrTimeout = 4u;  // the renderer's timeout error bit
@@ -40,7 +43,8 @@ __host__ __device__ constexpr uint32_t w_off(int l) {
 }
 constexpr uint32_t kAOff = w_off(net::kLayers);                    // 114,688
 constexpr uint32_t kZOff = kAOff + kRows * net::kHid * 2u;         // 147,456
-constexpr uint32_t kBarOff = kZOff + kRows * kInferZLd * 4u;       // 155,648
+constexpr uint32_t kXOff = kZOff + kRows * kInferZLd * 4u;         // 155,648: normalised inputs [128][8]
+constexpr uint32_t kBarOff = kXOff + kRows * 8 * 4u;               // 159,744
 constexpr size_t kSmem = kBarOff + 16;
 
 __device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -120,6 +124,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_infer_tc(SurrogateView v, c
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sA = smem + tc::kAOff;
   float* sz = reinterpret_cast<float*>(smem + tc::kZOff);
+  float* sx = reinterpret_cast<float*>(smem + tc::kXOff);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + tc::kBarOff);
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + tc::kBarOff + 8);
   __shared__ int s_fail;
@@ -155,7 +160,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_infer_tc(SurrogateView v, c
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = *s_tmem;
-  const int quad = warp & 3, half = warp >> 2;
+  const int quad = warp & 3, quarter = warp >> 2;
   const int row = quad * 32 + lane;  // this thread's row of the chunk in the epilogues
   const uint32_t t_row = tmem + ((uint32_t)(quad * 32) << 16);
   uint32_t phase = 0;
@@ -164,14 +169,38 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_infer_tc(SurrogateView v, c
   for (int row0 = blockIdx.x * tc::kRows; row0 < n && !failed; row0 += gridDim.x * tc::kRows) {
     const int valid = min(tc::kRows, n - row0);
     __syncthreads();  // the previous chunk's consumer is done with sz
-    if (tid < tc::kRows) {  // features of row tid as the layer-0 A operand (K = 48)
+    const uint32_t s48 = tc::sbo_of(kFeat);
+    if (tid < tc::kRows) {  // row tid's inputs, normalised; features 32..47 (x, zero padding)
       float q[kIn] = {0.f, 0.f, 380.f, 2e-3f, 0.f, 1.45f, 1e-8f};
       if (tid < valid) pol.load(ctx, row0 + tid, q);
-      __align__(16) __nv_bfloat16 f[kFeat];
-      features_row(q, v.Bm, f);
+      float x[kIn];
+      normalise_row(q, x);
+      __align__(16) __nv_bfloat16 f[16];
 #pragma unroll
-      for (int c = 0; c < kFeat / 8; ++c)
-        *reinterpret_cast<uint4*>(sA + tc::chunk_off(tid, c, tc::sbo_of(kFeat))) = reinterpret_cast<const uint4*>(f)[c];
+      for (int j = 0; j < 16; ++j) f[j] = __float2bfloat16(j < kIn ? x[j] : 0.f);
+      *reinterpret_cast<uint4*>(sA + tc::chunk_off(tid, 4, s48)) = reinterpret_cast<const uint4*>(f)[0];
+      *reinterpret_cast<uint4*>(sA + tc::chunk_off(tid, 5, s48)) = reinterpret_cast<const uint4*>(f)[1];
+#pragma unroll
+      for (int j = 0; j < kIn; ++j) sx[tid * 8 + j] = x[j];
+    }
+    __syncthreads();
+    {  // Fourier pairs 4 part .. 4 part + 3 of row r: sines at features 0..15, cosines 16..31
+      const int r = tid & (tc::kRows - 1), part = tid >> 7;
+      float x[kIn];
+#pragma unroll
+      for (int j = 0; j < kIn; ++j) x[j] = sx[r * 8 + j];
+      __align__(8) __nv_bfloat16 fs[4], fc[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        float sn, cs;
+        fourier_pair(x, v.Bm, 4 * part + i, &sn, &cs);
+        fs[i] = __float2bfloat16(sn);
+        fc[i] = __float2bfloat16(cs);
+      }
+      *reinterpret_cast<uint2*>(sA + tc::chunk_off(r, part / 2, s48) + (part & 1) * 8) =
+          *reinterpret_cast<const uint2*>(fs);
+      *reinterpret_cast<uint2*>(sA + tc::chunk_off(r, 2 + part / 2, s48) + (part & 1) * 8) =
+          *reinterpret_cast<const uint2*>(fc);
     }
     tc::fence_async_smem();
     __syncthreads();
@@ -198,8 +227,8 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_infer_tc(SurrogateView v, c
       if (l < kLayers - 1) {  // hidden layer: bias + GELU -> next A (K = 128)
         const float* bias = v.params + layer_offset(l) + K * N;
 #pragma unroll 1
-        for (int g = 0; g < 4; ++g) {
-          const int col = half * 64 + g * 16;
+        for (int g = 0; g < 2; ++g) {
+          const int col = quarter * 32 + g * 16;
           float z[16];
           tc::ld16(t_row + (uint32_t)col, z);
           uint32_t w8[8];
@@ -215,7 +244,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_infer_tc(SurrogateView v, c
         tc::fence_async_smem();
         __syncthreads();
       } else {  // output layer: the head of the first 8 outputs
-        if (half == 0) {
+        if (quarter == 0) {
           const float* bias = v.params + layer_offset(l) + K * N;
           float z[16];
           tc::ld16(t_row, z);
