@@ -87,6 +87,27 @@ __device__ __forceinline__ int emit_bundle_ray(bool want, const DevScene& sc, Ra
 // Child throughput of a member after the roulette it survived (q = min(0.95, t)).
 __device__ __forceinline__ float after_roulette(float t, bool roulette) { return roulette ? t / fminf(0.95f, t) : t; }
 
+// Writes the B member values val(0..B-1) of the record in slot pos (pos < 0: none) of dst
+// ([slots][B]).  Every lane of the warp calls this; the lanes with a slot hold consecutive
+// slots in lane order (warp_append), so their values go through the warp's staging area
+// (32 x kMaxBundle floats of shared memory) and the warp's block of dst is written with
+// coalesced stores instead of B strided partial-sector stores per lane.
+template <class F>
+__device__ __forceinline__ void store_members(float* dst, int pos, int B, float* stage, F val) {
+  const unsigned m = __ballot_sync(0xffffffffu, pos >= 0);
+  if (m == 0u) return;
+  const int first = __shfl_sync(0xffffffffu, pos, __ffs(m) - 1);
+  if (pos >= 0) {
+    const int rank = pos - first;
+    for (int b = 0; b < B; ++b) stage[rank * B + b] = val(b);
+  }
+  __syncwarp();
+  const int n = __popc(m) * B;
+  float* d = dst + (size_t)first * B;
+  for (int k = (int)(threadIdx.x & 31); k < n; k += 32) d[k] = stage[k];
+  __syncwarp();
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------------ raygen
@@ -118,9 +139,10 @@ __device__ __forceinline__ void dev_raygen_bundle(const RenderParams& p, const W
 // Shade bundle ray r of the current generation (every lane of the warp calls this).  The
 // per-member loop over the vertex's material (Eq. 1 with the complex index, the thin-slab
 // series, Beer-Lambert, the Lambertian albedo) decides each member's branch with the shared
-// uniforms; the members are then grouped into child rays as the header describes.  The
-// parent's throughput slots (cur.w) are reused to hold each member's throughput after the
-// vertex and before the roulette.
+// uniforms; the members are then grouped into child rays as the header describes.  Each
+// member's throughput after the vertex (before the roulette) is kept in shared memory, one
+// row of kMaxBundle floats per thread; the children's member values are written through a
+// per-warp staging area.  Blocks of at most kBlock threads.
 template <int kTM>
 __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const WaveDesc& w, int r, bool active,
                                                  RayBuf cur, const float2* __restrict__ hits, RayBuf next,
@@ -140,7 +162,10 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
   bool roulette = false;
   float uw = 0.f, cl_sh = 0.f, cos_i = 0.f, seg0 = 0.f;
   float3 pt = gd0, ng = gd0, d = gd0;
-  float* wr = cur.w + (size_t)(active ? r : 0) * B;
+  __shared__ float s_member_w[kBlock * kMaxBundle];
+  __shared__ float s_stage[kBlock * kMaxBundle];
+  float* wr = s_member_w + threadIdx.x * kMaxBundle;
+  float* stage = s_stage + (threadIdx.x & ~31u) * kMaxBundle;
   uint32_t* hp = nullptr;
   PathId id{};
   if (active) {
@@ -151,6 +176,7 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
     const uint32_t depth = inf.y & 0xFFu, mask = inf.y >> 16;
     flags = (inf.y >> 8) & 0xFFu;
     seg0 = O.w;
+    for (int b = 0; b < B; ++b) wr[b] = cur.w[(size_t)r * B + b];
     const float3 o = f3(O);
     d = f3(D);
     id = path_id_bundle(p, w, path);
@@ -215,7 +241,8 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
             slab_RT(cos_i, __ldg(mn + b), __ldg(mk + b), thick, __ldg(p.sp.lambda_nm + lam0 + b), &Rs, &Ts, p.sp.slab_pol);
             float P = Rs / (Rs + Ts);
             wr[b] = wr[b] * (Rs + Ts);
-            gm[u.x < P ? 0 : 1] |= 1u << b;
+            if (u.x < P) gm[0] |= 1u << b;  // (a computed index would put gm in local memory)
+            else gm[1] |= 1u << b;
           }
           hash_event(hp, gm[0], EV_REFLECT);
           hash_event(hp, gm[1], EV_TRANSMIT);
@@ -279,10 +306,8 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
     }
     const int pos = emit_bundle_ray(gm[g] != 0u, p.sc, next, next_count, q, q_count, qcap, og, sg, dg, path,
                                     v | (gf[g] << 8) | (gm[g] << 16), ctl);
-    if (pos >= 0) {
-      float* cw = next.w + (size_t)pos * B;
-      for (int b = 0; b < B; ++b) cw[b] = ((gm[g] >> b) & 1u) ? after_roulette(wr[b], roulette) : 0.f;
-    }
+    const uint32_t mg = gm[g];
+    store_members(next.w, pos, B, stage, [&](int b) { return ((mg >> b) & 1u) ? after_roulette(wr[b], roulette) : 0.f; });
   }
   // singles: each member on its own direction (transmission into or out of solid glass,
   // brute-force tiles)
@@ -339,10 +364,7 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
       }
       const int pos = emit_bundle_ray(want, p.sc, next, next_count, q, q_count, qcap, os, ss, ds, path,
                                       v | (fs << 8) | ((1u << b) << 16), ctl);
-      if (pos >= 0) {
-        float* cw = next.w + (size_t)pos * B;
-        for (int k = 0; k < B; ++k) cw[k] = k == b ? ts : 0.f;
-      }
+      store_members(next.w, pos, B, stage, [&](int k) { return k == b ? ts : 0.f; });
     }
   }
   // network form: one tile-queue entry (ray << 4 | member) per member at a tile hit
@@ -366,10 +388,10 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
     sb.o[pos] = make_float4(osh.x, osh.y, osh.z, 0.f);
     sb.d[pos] = make_float4(dsh.x, dsh.y, dsh.z, 0.f);
     sb.info[pos] = make_uint2(path, msh | (v << 16));
-    float* c = sb.c + (size_t)pos * B;
-    for (int b = 0; b < B; ++b)
-      c[b] = ((msh >> b) & 1u) ? wr[b] * kInvPi * cl_sh * __ldg(p.sp.sun + lam0 + b) * p.sp.sun_omega : 0.f;
   }
+  store_members(sb.c, ok ? pos : -1, B, stage, [&](int b) {
+    return ((msh >> b) & 1u) ? wr[b] * kInvPi * cl_sh * __ldg(p.sp.sun + lam0 + b) * p.sp.sun_omega : 0.f;
+  });
   int ss = ok ? subdomain_of(p.sc, osh) : 0;
   int qpos = warp_append(sq_count, ss, ok);
   if (ok) {

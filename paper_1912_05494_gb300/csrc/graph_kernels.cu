@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kChunk, 12) k_traverse_g(RenderParams p, const
 }
 
 // Shading of the generation's *n_in rays (children counted in *next_count).
-template <int kTM, bool kBund>
+template <int kTM>
 __global__ void __launch_bounds__(kBlock) k_shade_g(RenderParams p, WaveDesc w, const int* n_in, RayBuf cur,
                                                     const float2* __restrict__ hits, RayBuf next, int* next_count,
                                                     uint32_t* q, int* q_count, int qcap, ShadowBuf sb, uint32_t* sq,
@@ -89,13 +89,25 @@ __global__ void __launch_bounds__(kBlock) k_shade_g(RenderParams p, WaveDesc w, 
   const int n = min(*(volatile const int*)n_in, qcap);
   for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
     const int r = base + (int)threadIdx.x;
-    if constexpr (kBund) {
-      dev_shade_bundle<kTM>(p, w, r, r < n, cur, hits, next, next_count, q, q_count, qcap, sb, &ctl->next_shadow, sq,
-                            sq_count, path_L, ctl);
-    } else {
-      dev_shade<kTM>(p, w, r, r < n, cur, hits, next, next_count, q, q_count, qcap, sb, &ctl->next_shadow, sq,
-                     sq_count, path_L, ctl);
-    }
+    dev_shade<kTM>(p, w, r, r < n, cur, hits, next, next_count, q, q_count, qcap, sb, &ctl->next_shadow, sq, sq_count,
+                   path_L, ctl);
+  }
+}
+
+// The same for bundle rays.  Resident blocks per SM: a register cap that keeps more warps in
+// flight for the shading's memory latency (measured on the nave frame: no cap 63.2 ms, 4
+// blocks 52.6, 5 blocks 51.6, 6 blocks 49.5); brute-force tiles keep their registers.
+constexpr int kShadeBlocks = 6;
+template <int kTM>
+__global__ void __launch_bounds__(kBlock, kTM == 1 ? 1 : kShadeBlocks)
+    k_shade_bundle_g(RenderParams p, WaveDesc w, const int* n_in, RayBuf cur, const float2* __restrict__ hits,
+                     RayBuf next, int* next_count, uint32_t* q, int* q_count, int qcap, ShadowBuf sb, uint32_t* sq,
+                     int* sq_count, float* path_L, Control* ctl) {
+  const int n = min(*(volatile const int*)n_in, qcap);
+  for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+    const int r = base + (int)threadIdx.x;
+    dev_shade_bundle<kTM>(p, w, r, r < n, cur, hits, next, next_count, q, q_count, qcap, sb, &ctl->next_shadow, sq,
+                          sq_count, path_L, ctl);
   }
 }
 
@@ -177,7 +189,7 @@ const void* traverse_fn(const RenderParams& p) {
 
 template <int kTM>
 const void* shade_fn_t(bool b) {
-  return b ? (const void*)k_shade_g<kTM, true> : (const void*)k_shade_g<kTM, false>;
+  return b ? (const void*)k_shade_bundle_g<kTM> : (const void*)k_shade_g<kTM>;
 }
 const void* shade_fn(const RenderParams& p) {
   const bool b = p.bundle > 1;
