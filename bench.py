@@ -729,12 +729,25 @@ def run_large(args):
         ms = e0.elapsed_time(e1) / steps
         return ms, launches, out.cpu().numpy().astype(np.float64), ms_tile / steps
 
-    if args.forms != "both":  # one form only (profiling); no comparison
+    if args.forms != "both":  # one form only (profiling, out-of-core runs); no comparison
         kw = net_kw if args.forms == "net" else {"batched": 0}
+        if args.forms == "net":
+            kw = {**kw, "batched": args.batched}
+        streaming = None
+        info = sdd.sdd_scene_get_info(h.h)  # the all-resident scene
+        if args.resident:  # out-of-core subdomains: the host-driven form of the chosen form
+            sdd.sdd_set_tuning(h.h, {**sdd.sdd_get_tuning(h.h), "resident_subdomains": args.resident})
+            kw = {**kw, "batched": 0}
         ms, launches, _, _ = timed(kw, args.steps, args.warmup, spec_net if args.forms == "net" else spec)
+        if args.resident:
+            st = sdd.sdd_get_stats(h.h)
+            streaming = {"resident_subdomains": args.resident, "subdomains": scene.n_subdomains,
+                         "subdomain_loads_per_frame": st["subdomain_loads"],
+                         "bytes_streamed_per_frame": st["bytes_streamed"], "scene_device_bytes": info["device_bytes"]}
         print(json.dumps({"workload": "large", "form": args.forms, "frame": [cam.width, cam.height, spec.spp],
+                          "subdomains": scene.n_subdomains, "batched": kw.get("batched"),
                           "ms_per_step": ms, "value": frame_paths / (ms / 1e3) / 1e6, "unit": UNIT,
-                          "gpu_launches": launches}), flush=True)
+                          "gpu_launches": launches, "streaming": streaming}), flush=True)
         h.close()
         return 0
     clocks = ClockSampler(0)
