@@ -126,8 +126,6 @@ struct sdd_scene {
     int slot_nodes = 0, slot_tris = 0;            // capacity of one slot
     DevArr<Node> d_nodes;      // cap slots
     DevArr<TriRec> d_tris;
-    Node* stage_nodes = nullptr;  // pinned staging of the rebased copies, one area per slot
-    TriRec* stage_tris = nullptr;
     std::vector<int> slot_of, sub_in_slot;  // subdomain -> slot, slot -> subdomain (-1: none)
   } strm;
   int n_sub = 1, axis = 0, bvh_max_depth = 0;
@@ -175,8 +173,6 @@ struct sdd_scene {
     strm.d_tris.release();
     cudaFreeHost(strm.h_nodes);
     cudaFreeHost(strm.h_tris);
-    cudaFreeHost(strm.stage_nodes);
-    cudaFreeHost(strm.stage_tris);
     tris.release();
     prim.release();
     t_lambda.release(); t_thick.release(); t_n.release(); t_k.release(); t_alb.release();
@@ -323,34 +319,39 @@ sdd_status device_error(uint32_t e) {
 // rays remain for them.  With streaming on (host-driven form), before every traversal pass a
 // resident subdomain stays in its device slot while its queue holds rays; slots whose
 // subdomain has none left (or that are empty) go to the waiting subdomains with the most
-// queued rays, whose nodes and triangle records are copied in from pinned host memory with
-// their links rebased to the slot.  Rays queued for subdomains that are not resident wait,
-// unchanged, for a later pass; rays cross each slab at most once, so resident queues drain
-// and every waiting queue is reached.  The traversal code is the same; only where the nodes lie changes, so every
-// hit, path and image is the all-resident one bit for bit.
+// queued rays, whose nodes and triangle records are copied in from pinned host memory (one
+// asynchronous copy each) and whose links a small kernel then rebases to the slot.  Rays
+// queued for subdomains that are not resident wait, unchanged, for a later pass; rays cross
+// each slab at most once, so resident queues drain and every waiting queue is reached.  The
+// traversal code is the same; only where the nodes lie changes, so every hit, path and image
+// is the all-resident one bit for bit.
 
-// Copy subdomain `sub` into slot j (links rebased to the slot), enqueued on st.
+// Links of a subdomain's nodes copied into slot j: inner children from the subdomain's first
+// node n0 to the slot's nbase, leaf triangle ranges from its first record t0 to tbase.
+__global__ void k_rebase_nodes(Node* nodes, int nn, int n0, int nbase, int t0, int tbase) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nn) return;
+  int4 d = nodes[i].d;
+  if (d.z > 0) d.x = d.x - t0 + tbase;
+  else if (d.x >= 0) d.x = d.x - n0 + nbase;
+  if (d.w > 0) d.y = d.y - t0 + tbase;
+  else if (d.y >= 0) d.y = d.y - n0 + nbase;
+  nodes[i].d = d;
+}
+
+// Copy subdomain `sub` from pinned host memory into device slot j and rebase its links there.
 cudaError_t load_subdomain(sdd_scene* s, int sub, int j, cudaStream_t st) {
   auto& m = s->strm;
-  Node* sn = m.stage_nodes + (size_t)j * m.slot_nodes;
-  TriRec* stri = m.stage_tris + (size_t)j * m.slot_tris;
   const int n0 = m.node0[sub], nn = m.nnodes[sub], t0 = m.tri0[sub], nt = m.ntris[sub];
   const int nbase = j * m.slot_nodes, tbase = j * m.slot_tris;
-  for (int i = 0; i < nn; ++i) {
-    Node nd = m.h_nodes[n0 + i];
-    int l0 = nd.d.x, l1 = nd.d.y;
-    if (nd.d.z > 0) l0 = l0 - t0 + tbase;        // leaf: triangle records
-    else if (l0 >= 0) l0 = l0 - n0 + nbase;      // inner child
-    if (nd.d.w > 0) l1 = l1 - t0 + tbase;
-    else if (l1 >= 0) l1 = l1 - n0 + nbase;
-    nd.d.x = l0;
-    nd.d.y = l1;
-    sn[i] = nd;
-  }
-  if (nt > 0) std::memcpy(stri, m.h_tris + t0, sizeof(TriRec) * (size_t)nt);
-  cudaError_t e = cudaMemcpyAsync(m.d_nodes.p + nbase, sn, sizeof(Node) * (size_t)nn, cudaMemcpyHostToDevice, st);
+  cudaError_t e = cudaMemcpyAsync(m.d_nodes.p + nbase, m.h_nodes + n0, sizeof(Node) * (size_t)nn,
+                                  cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && nt > 0)
-    e = cudaMemcpyAsync(m.d_tris.p + tbase, stri, sizeof(TriRec) * (size_t)nt, cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(m.d_tris.p + tbase, m.h_tris + t0, sizeof(TriRec) * (size_t)nt, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && nn > 0) {
+    k_rebase_nodes<<<(nn + 255) / 256, 256, 0, st>>>(m.d_nodes.p + nbase, nn, n0, nbase, t0, tbase);
+    e = cudaGetLastError();
+  }
   s->stats.bytes_streamed += (int64_t)(sizeof(Node) * (size_t)nn + sizeof(TriRec) * (size_t)nt);
   s->stats.subdomain_loads++;
   return e;
@@ -1624,12 +1625,8 @@ void free_streaming(sdd_scene* s) {
   m.d_tris.release();
   cudaFreeHost(m.h_nodes);
   cudaFreeHost(m.h_tris);
-  cudaFreeHost(m.stage_nodes);
-  cudaFreeHost(m.stage_tris);
   m.h_nodes = nullptr;
   m.h_tris = nullptr;
-  m.stage_nodes = nullptr;
-  m.stage_tris = nullptr;
   m.cap = 0;
 }
 
@@ -1691,8 +1688,6 @@ sdd_status set_streaming(sdd_scene* s, int cap) {
   m.slot_tris = max_tris;
   e = m.d_nodes.ensure((size_t)cap * max_nodes);
   if (e == cudaSuccess) e = m.d_tris.ensure((size_t)cap * max_tris);
-  if (e == cudaSuccess) e = cudaMallocHost(&m.stage_nodes, sizeof(Node) * (size_t)cap * max_nodes);
-  if (e == cudaSuccess) e = cudaMallocHost(&m.stage_tris, sizeof(TriRec) * (size_t)cap * max_tris);
   if (e != cudaSuccess) {
     free_streaming(s);
     return fail(e == cudaErrorMemoryAllocation ? SDD_ERR_OOM : SDD_ERR_CUDA, cudaGetErrorString(e));
