@@ -164,12 +164,13 @@ typedef struct {
                               member leaves on its own ray (brute force or network) */
   const sdd_photon_maps* photon_maps; /* Sec. 3.2 (Jensen's photon mapping): NULL = none; else maps
                               built for the same wavelength list (equal lambda_nm), used by Monte
-                              Carlo renders of the host-driven form (batched = 0) without bundles
-                              (bundle <= 1) or the network (use_surrogate = 0); other
-                              combinations return SDD_ERR_ARG.  At its first diffuse vertex a path
-                              adds albedo / pi x (E_caustic + E_global) of the maps at the hit point
-                              beside the sun NEE; later vertices take sky light only (no NEE, no sun
-                              disc on escape) */
+                              Carlo renders of the host-driven or the graph form (batched = 0 or 2),
+                              with or without spectral bundles, without the network
+                              (use_surrogate = 0); other combinations return SDD_ERR_ARG.  At its
+                              first diffuse vertex a path adds albedo / pi x (E_caustic + E_global)
+                              of the maps at the hit point beside the sun NEE (each bundle member
+                              those of its wavelength); later vertices take sky light only (no NEE,
+                              no sun disc on escape) */
 } sdd_render_opts;
 
 /* Build the scene: validates, partitions the geometry into n_subdomains slabs (Sec. 5:

@@ -979,8 +979,7 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
   if (o->bundle < 0 || o->bundle > kMaxBundle) return fail(SDD_ERR_ARG, "bundle must be in [0, 16]");
   if (const sdd_photon_maps* pm = o->photon_maps) {
     if (o->mode != SDD_MODE_MONTE_CARLO) return fail(SDD_ERR_ARG, "photon maps need Monte Carlo mode");
-    if (o->batched != 0) return fail(SDD_ERR_ARG, "photon maps need the host-driven form (batched = 0)");
-    if (o->bundle > 1) return fail(SDD_ERR_ARG, "photon maps need bundle <= 1");
+    if (o->batched == 1) return fail(SDD_ERR_ARG, "photon maps need the host-driven or the graph form (batched = 0 or 2)");
     if (o->use_surrogate) return fail(SDD_ERR_ARG, "photon maps need use_surrogate = 0");
     if (pm->lambda != std::vector<float>(o->lambda_nm, o->lambda_nm + o->n_lambda))
       return fail(SDD_ERR_ARG, "photon maps were built for another wavelength list");

@@ -143,7 +143,10 @@ __device__ __forceinline__ void dev_raygen_bundle(const RenderParams& p, const W
 // member's throughput after the vertex (before the roulette) is kept in shared memory, one
 // row of kMaxBundle floats per thread; the children's member values are written through a
 // per-warp staging area.  Blocks of at most kBlock threads.
-template <int kTM>
+// kPM: photon maps (Sec. 3.2), as in dev_shade: the first diffuse vertex adds each member's
+// albedo / pi x (E_caustic + E_global) of its wavelength; the continuation carries
+// FLAG_PHOTON_DONE (sky light only: no NEE, no sun disc on escape).
+template <int kTM, bool kPM = false>
 __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const WaveDesc& w, int r, bool active,
                                                  RayBuf cur, const float2* __restrict__ hits, RayBuf next,
                                                  int* next_count, uint32_t* q, int* q_count, int qcap, ShadowBuf sb,
@@ -188,7 +191,7 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
     if (prim != kMissPrim && prim >= (uint32_t)p.sc.n_prims) {
       atomicOr(&ctl->error, ERR_QUEUE_OVERFLOW);  // stale hit record of a dropped ray
     } else if (prim == kMissPrim) {
-      const bool sun_counted = (flags & FLAG_SUN_COUNTED) != 0u;
+      const bool sun_counted = (flags & (FLAG_SUN_COUNTED | FLAG_PHOTON_DONE)) != 0u;
       for (uint32_t m = mask; m; m &= m - 1) {
         int b = __ffs(m) - 1;
         Lp[b] += wr[b] * escape_radiance(p.sp, d, (int)lam0 + b, sun_counted);
@@ -256,7 +259,15 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
             int b = __ffs(m) - 1;
             wr[b] = wr[b] * __ldg(ma + b);
           }
-          if (p.sp.sun_h > 0.f) {
+          const bool photon_done = kPM && (flags & FLAG_PHOTON_DONE) != 0u;
+          if (kPM && !photon_done) {
+            for (uint32_t m = mask; m; m &= m - 1) {
+              int b = __ffs(m) - 1;
+              const float2 E = photon_irradiance(p.pm, pt, nf, (int)lam0 + b);
+              Lp[b] += wr[b] * kInvPi * (E.x + E.y);
+            }
+          }
+          if (p.sp.sun_h > 0.f && !photon_done) {
             float4 un = draw4(id.pixel, id.sample, v, STREAM_NEE, 0, j, p.seed);
             float3 wl = cone_dir(p.sp.sun_dir, p.sp.sun_h, un.x, un.y);
             float cl = dot3(nf, wl);
@@ -268,7 +279,7 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
           }
           gm[0] = mask;
           gd0 = cosine_dir(nf, u.y, u.z);
-          gf[0] = flags | FLAG_SUN_COUNTED;
+          gf[0] = flags | FLAG_SUN_COUNTED | (kPM ? FLAG_PHOTON_DONE : 0u);
         } else if (kTM == 1 && kind == MAT_TILE) {
           singles = mask;  // each member traces its own ray through the tile
         } else if (kTM == 2 && kind == MAT_TILE) {

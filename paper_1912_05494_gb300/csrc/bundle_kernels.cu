@@ -13,14 +13,14 @@ __global__ void __launch_bounds__(kBlock) k_raygen_bundle(RenderParams p, WaveDe
 
 // Six resident blocks per SM as in the graph form's bundle shading (a register cap that keeps
 // more warps in flight for the shading's memory latency); brute-force tiles keep their registers.
-template <int kTM>
+template <int kTM, bool kPM = false>
 __global__ void __launch_bounds__(kBlock, kTM == 1 ? 1 : 6) k_shade_bundle(RenderParams p, WaveDesc w, int n_rays, RayBuf cur,
                                                          const float2* __restrict__ hits, RayBuf next, uint32_t* q,
                                                          int* q_count, int qcap, ShadowBuf sb, uint32_t* sq,
                                                          int* sq_count, float* path_L, Control* ctl) {
   int r = blockIdx.x * blockDim.x + threadIdx.x;
-  dev_shade_bundle<kTM>(p, w, r, r < n_rays, cur, hits, next, &ctl->next_rays, q, q_count, qcap, sb,
-                        &ctl->next_shadow, sq, sq_count, path_L, ctl);
+  dev_shade_bundle<kTM, kPM>(p, w, r, r < n_rays, cur, hits, next, &ctl->next_rays, q, q_count, qcap, sb,
+                             &ctl->next_shadow, sq, sq_count, path_L, ctl);
 }
 
 // Blocks grouped by subdomain as in the traversal kernel; the per-lane walk without
@@ -83,6 +83,15 @@ void launch_shade_bundle(const RenderParams& p, const WaveDesc& w, int n_rays, R
                          RayBuf next, uint32_t* q, int* q_count, int qcap, ShadowBuf sb, uint32_t* sq, int* sq_count,
                          float* path_L, Control* ctl, cudaStream_t st) {
   if (n_rays <= 0) return;
+  if (p.use_photons) {  // photon maps: brute-force tiles or none
+    if (tile_mode(p) == 1)
+      k_shade_bundle<1, true><<<blocks_for(n_rays, kBlock), kBlock, 0, st>>>(p, w, n_rays, cur, hits, next, q, q_count,
+                                                                             qcap, sb, sq, sq_count, path_L, ctl);
+    else
+      k_shade_bundle<0, true><<<blocks_for(n_rays, kBlock), kBlock, 0, st>>>(p, w, n_rays, cur, hits, next, q, q_count,
+                                                                             qcap, sb, sq, sq_count, path_L, ctl);
+    return;
+  }
   if (tile_mode(p) == 1)
     k_shade_bundle<1><<<blocks_for(n_rays, kBlock), kBlock, 0, st>>>(p, w, n_rays, cur, hits, next, q, q_count, qcap,
                                                                      sb, sq, sq_count, path_L, ctl);

@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kChunk, 12) k_traverse_g(RenderParams p, const
 }
 
 // Shading of the generation's *n_in rays (children counted in *next_count).
-template <int kTM>
+template <int kTM, bool kPM>
 __global__ void __launch_bounds__(kBlock) k_shade_g(RenderParams p, WaveDesc w, const int* n_in, RayBuf cur,
                                                     const float2* __restrict__ hits, RayBuf next, int* next_count,
                                                     uint32_t* q, int* q_count, int qcap, ShadowBuf sb, uint32_t* sq,
@@ -89,8 +89,8 @@ __global__ void __launch_bounds__(kBlock) k_shade_g(RenderParams p, WaveDesc w, 
   const int n = min(*(volatile const int*)n_in, qcap);
   for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
     const int r = base + (int)threadIdx.x;
-    dev_shade<kTM>(p, w, r, r < n, cur, hits, next, next_count, q, q_count, qcap, sb, &ctl->next_shadow, sq, sq_count,
-                   path_L, ctl);
+    dev_shade<kTM, kPM>(p, w, r, r < n, cur, hits, next, next_count, q, q_count, qcap, sb, &ctl->next_shadow, sq,
+                        sq_count, path_L, ctl);
   }
 }
 
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kBlock) k_shade_g(RenderParams p, WaveDesc w, 
 // flight for the shading's memory latency (measured on the nave frame: no cap 63.2 ms, 4
 // blocks 52.6, 5 blocks 51.6, 6 blocks 49.5); brute-force tiles keep their registers.
 constexpr int kShadeBlocks = 6;
-template <int kTM>
+template <int kTM, bool kPM>
 __global__ void __launch_bounds__(kBlock, kTM == 1 ? 1 : kShadeBlocks)
     k_shade_bundle_g(RenderParams p, WaveDesc w, const int* n_in, RayBuf cur, const float2* __restrict__ hits,
                      RayBuf next, int* next_count, uint32_t* q, int* q_count, int qcap, ShadowBuf sb, uint32_t* sq,
@@ -106,8 +106,8 @@ __global__ void __launch_bounds__(kBlock, kTM == 1 ? 1 : kShadeBlocks)
   const int n = min(*(volatile const int*)n_in, qcap);
   for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
     const int r = base + (int)threadIdx.x;
-    dev_shade_bundle<kTM>(p, w, r, r < n, cur, hits, next, next_count, q, q_count, qcap, sb, &ctl->next_shadow, sq,
-                          sq_count, path_L, ctl);
+    dev_shade_bundle<kTM, kPM>(p, w, r, r < n, cur, hits, next, next_count, q, q_count, qcap, sb, &ctl->next_shadow,
+                               sq, sq_count, path_L, ctl);
   }
 }
 
@@ -187,16 +187,18 @@ const void* traverse_fn(const RenderParams& p) {
   return p.stats >= 2 ? (const void*)k_traverse_g<true> : (const void*)k_traverse_g<false>;
 }
 
-template <int kTM>
+template <int kTM, bool kPM>
 const void* shade_fn_t(bool b) {
-  return b ? (const void*)k_shade_bundle_g<kTM> : (const void*)k_shade_g<kTM>;
+  return b ? (const void*)k_shade_bundle_g<kTM, kPM> : (const void*)k_shade_g<kTM, kPM>;
 }
 const void* shade_fn(const RenderParams& p) {
   const bool b = p.bundle > 1;
+  if (p.use_photons)  // photon maps: brute-force tiles or none
+    return tile_mode(p) == 1 ? shade_fn_t<1, true>(b) : shade_fn_t<0, true>(b);
   switch (tile_mode(p)) {
-    case 1: return shade_fn_t<1>(b);
-    case 2: return shade_fn_t<2>(b);
-    default: return shade_fn_t<0>(b);
+    case 1: return shade_fn_t<1, false>(b);
+    case 2: return shade_fn_t<2, false>(b);
+    default: return shade_fn_t<0, false>(b);
   }
 }
 

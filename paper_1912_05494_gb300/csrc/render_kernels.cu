@@ -233,7 +233,7 @@ void launch_shade(const RenderParams& p, const WaveDesc& w, int n_rays, RayBuf c
     return launch_shade_bundle(p, w, n_rays, cur, hits, next, q, q_count, qcap, sb, sq, sq_count, path_L, ctl, st);
   if (n_rays <= 0) return;
   const int tm = tile_mode(p);
-  if (p.use_photons) {  // photon maps: host-driven, one wavelength per path, brute-force tiles
+  if (p.use_photons) {  // photon maps: brute-force tiles or none
     if (tm == 1)
       k_shade<1, true><<<blocks_for(n_rays, kBlock), kBlock, 0, st>>>(p, w, n_rays, cur, hits, next, q, q_count, qcap,
                                                                       sb, sq, sq_count, path_L, ctl);

@@ -12,7 +12,8 @@ density estimates are checked against the definition (brute force over the same 
 and against the oracle's estimates over its own photons; renders that take the sun's
 caustic and indirect light from the maps are compared path by path as the other Monte Carlo
 parity tests are (0.1 % event-hash flips; image error 2e-3, the maps differing by the
-photons FP32 decisions moved).
+photons FP32 decisions moved), one wavelength per path and in spectral bundles; the graph
+form equals the host-driven form bit for bit.
 """
 import math
 
@@ -203,6 +204,27 @@ def test_render_with_photon_maps_matches_the_oracle(sdd, orc, court_maps):
     assert np.abs(plain - gpu).sum() > 1e-3 * np.abs(gpu).sum()  # the maps do change the image
 
 
+def test_render_with_photon_maps_in_bundles_and_the_graph_form(sdd, orc, court_maps):
+    """Spectral bundles (the three wavelengths share one ray while their decisions agree, the
+    oracle tracing each as its own chain on the bundle's draws): host-driven against the
+    oracle path by path, and the graph form equal to the host-driven form bit for bit."""
+    h, gm, om = court_maps
+    sc = court()
+    cam = S.CameraData(pos=(0.0, -5.0, 4.0), look_at=(0.0, 0.5, 0.0), up=(0, 0, 1), vfov_deg=60.0, width=24,
+                       height=16)
+    spec = S.RenderSpec(lambda_nm=LAMS, spp=8, seed=5, max_depth=8, mode=S.RENDER_MC, rr_start_depth=3, bundle=3)
+    gpu, gx, gp, gh = render_gpu(sdd, h, cam, spec, paths=True, photon_maps=gm, batched=0)
+    ref, rp, rh = orc.OracleScene(sc).render(cam, spec, want_paths=True, photons=om)
+    assert float(np.mean(gh != rh)) <= 1e-3, float(np.mean(gh != rh))
+    assert mean_rel_image_error(gpu, ref) <= 2e-3, mean_rel_image_error(gpu, ref)
+    g2, gx2, gp2, gh2 = render_gpu(sdd, h, cam, spec, paths=True, photon_maps=gm, batched=2)
+    assert np.array_equal(g2, gpu) and np.array_equal(gx2, gx) and np.array_equal(gp2, gp) and np.array_equal(gh2, gh)
+    one = S.RenderSpec(**{**spec.__dict__, "bundle": 1})
+    u0, _ = render_gpu(sdd, h, cam, one, photon_maps=gm, batched=0)
+    u2, _ = render_gpu(sdd, h, cam, one, photon_maps=gm, batched=2)
+    assert np.array_equal(u0, u2)
+
+
 def test_photon_buffers_grow_when_photons_are_stored_many_times(sdd, orc):
     """A closed white room (albedo 0.7) with the emitter disc inside it: a photon is stored
     about 2.3 times, past the first buffer size (one entry per photon), so the build traces
@@ -233,8 +255,8 @@ def test_invalid_photon_map_use_is_rejected(sdd, court_maps):
     h, gm, _ = court_maps
     cam = S.CameraData(pos=(0.0, -5.0, 4.0), look_at=(0.0, 0.5, 0.0), up=(0, 0, 1), vfov_deg=60.0, width=4, height=4)
     spec = S.RenderSpec(lambda_nm=LAMS, spp=1, seed=5, max_depth=8, mode=S.RENDER_MC, rr_start_depth=3)
-    with pytest.raises(sdd.SddError, match="host-driven"):
-        render_gpu(sdd, h, cam, spec, photon_maps=gm, batched=2)
+    with pytest.raises(sdd.SddError, match="batched = 0 or 2"):
+        render_gpu(sdd, h, cam, spec, photon_maps=gm, batched=1)
     other = S.RenderSpec(**{**spec.__dict__, "lambda_nm": LAMS + 1.0})
     with pytest.raises(sdd.SddError, match="wavelength"):
         render_gpu(sdd, h, cam, other, photon_maps=gm)
