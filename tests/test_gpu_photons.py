@@ -242,13 +242,34 @@ def test_photon_buffers_grow_when_photons_are_stored_many_times(sdd, orc):
     check_sets(gm, om, min_counts=(1000, 2 * n))
 
 
-def test_photon_maps_in_the_nave(sdd, orc, nave):
-    """The nave (184,864 triangles, 8 subdomains): sunlight through the thin-slab windows of
-    the sunward wall; 9 of the 81 wavelengths."""
+@pytest.fixture(scope="module")
+def nave_maps(sdd, orc, nave):
     sc, _, _ = nave
     lams = sc.table_nm[::10].astype(np.float32)
-    h, gm, om = both_maps(sdd, orc, sc, lams, 40000, 9, (30.0, 0.0, 7.0), 31.0, 60.0, 0.25)
+    return lams, both_maps(sdd, orc, sc, lams, 40000, 9, (30.0, 0.0, 7.0), 31.0, 60.0, 0.25)
+
+
+def test_photon_maps_in_the_nave(nave_maps):
+    """The nave (184,864 triangles, 8 subdomains): sunlight through the thin-slab windows of
+    the sunward wall; 9 of the 81 wavelengths."""
+    _, (h, gm, om) = nave_maps
     check_sets(gm, om, min_counts=(1, 1000), pos_tol=1e-3)  # coordinates up to ~100 m
+
+
+def test_render_with_photon_maps_in_the_nave(sdd, orc, nave, nave_maps):
+    """300 seeded pixels of the 1024 x 768 nave frame at 4 spp with its photon maps (9
+    wavelengths): the graph form with bundles of 9 and the host-driven form with one wavelength
+    per path, each against the oracle's render with its own maps, path by path."""
+    sc, cam, spec = nave
+    lams, (h, gm, om) = nave_maps
+    pixels = np.sort(np.random.default_rng(23).choice(cam.width * cam.height, 300, replace=False)).astype(np.int32)
+    for bundle, batched in ((9, 2), (1, 0)):
+        sp = S.RenderSpec(**{**spec.__dict__, "lambda_nm": lams, "spp": 4, "bundle": bundle})
+        gpu, _, gp, gh = render_gpu(sdd, h, cam, sp, pixels=pixels, paths=True, photon_maps=gm, batched=batched)
+        ref, rp, rh = orc.OracleScene(sc).render(cam, sp, pixels=pixels, want_paths=True, photons=om)
+        flips = float(np.mean(gh != rh))
+        assert flips <= 1e-3, (bundle, flips)
+        assert mean_rel_image_error(gpu, ref) <= 2e-3, (bundle, mean_rel_image_error(gpu, ref))
 
 
 def test_invalid_photon_map_use_is_rejected(sdd, court_maps):
