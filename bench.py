@@ -66,9 +66,11 @@ WORKLOAD = "nave-200k {w}x{h} {spp}spp 81lambda depth12 RR S={s} (Monte Carlo, s
 # per form: the sources of the dominant traversal kernel, and the committed ncu summary
 # whose DRAM counters are valid while those sources are unchanged
 _CSRC = "paper_1912_05494_gb300/csrc/"
-TRAVERSE_SOURCES = {0: [_CSRC + f for f in ("render_kernels.cu", "render_device.cuh", "device_math.cuh", "sdd_internal.h")],
+# the traversal kernel's sources and the BVH builder (the tree it walks sets its traffic)
+TRAVERSE_SOURCES = {0: [_CSRC + f for f in ("render_kernels.cu", "render_device.cuh", "device_math.cuh", "sdd_internal.h",
+                                            "scene_build.cpp")],
                     2: [_CSRC + f for f in ("graph_kernels.cu", "render_device.cuh", "device_math.cuh", "sdd_internal.h",
-                                            "chunk_sched.cuh")]}
+                                            "chunk_sched.cuh", "scene_build.cpp")]}
 NCU_SUMMARY = {0: os.path.join(ROOT, "profiles", "traverse_nave_ncu.md"),
                2: os.path.join(ROOT, "profiles", "traverse_graph_nave_ncu.md")}
 FORMS = {0: "host-driven", 1: "batched: persistent kernel + CUDA graph",
