@@ -109,7 +109,7 @@ def both_maps(sdd, orc, sc, lams, n, seed, center, radius, distance, r, max_dept
     return h, gm, om
 
 
-def check_sets(gm, om, min_counts=(1, 1), pos_tol=1e-4):
+def check_sets(gm, om, min_counts=(1, 1), pos_tol=1e-4, moved_max=2e-3):
     """pos_tol: 1e-4 m where the coordinates (emitter included) stay within ~20 m; FP32
     positions carry ~1e-7 of the coordinates' magnitude per operation, so a scene whose
     coordinates reach ~100 m takes ten times that."""
@@ -121,7 +121,7 @@ def check_sets(gm, om, min_counts=(1, 1), pos_tol=1e-4):
         # per-photon rank counts only the stores of that map, the GPU's seq counts diffuse
         # surfaces met: global photons are stored from the second surface on (seq >= 1)
         moved, dpos, dpw = compare_sets(gph, oph, global_offset=1 if m == GLOBAL else 0, moved_at=10 * pos_tol)
-        assert moved <= 2e-3, (m, moved)
+        assert moved <= moved_max, (m, moved)
         assert np.quantile(dpos, 0.999) < pos_tol, (m, np.quantile(dpos, 0.999))
         assert np.quantile(dpw, 0.999) < 1e-4, (m, np.quantile(dpw, 0.999))
 
@@ -270,6 +270,38 @@ def test_render_with_photon_maps_in_the_nave(sdd, orc, nave, nave_maps):
         flips = float(np.mean(gh != rh))
         assert flips <= 1e-3, (bundle, flips)
         assert mean_rel_image_error(gpu, ref) <= 2e-3, (bundle, mean_rel_image_error(gpu, ref))
+
+
+def test_photon_maps_through_heterogeneous_tiles(sdd, orc):
+    """Sunlight through the brute-force-traced window of heterogeneous tiles (height-field back
+    faces, air bubbles) of the tiled room: each photon meeting a tile takes one ray through it
+    on the photon tile stream.  Tile rays flip at FP32 rounding for ~0.2% of rays (the tile
+    parity tests), so up to 0.5% of the photons may end elsewhere, and a ray's dozens of
+    refractions and bubble scatterings in a tile carry FP32 rounding into its exit direction:
+    positions to 1 mm after the metres to the floor."""
+    sc, _, _ = S.tile_room_scene()
+    lams = sc.table_nm[::10].astype(np.float32)
+    h, gm, om = both_maps(sdd, orc, sc, lams, 20000, 13, (3.0, 0.0, 2.0), 0.8, 5.0, 0.1)
+    check_sets(gm, om, min_counts=(20000, 20000), pos_tol=1e-3, moved_max=5e-3)
+
+
+def test_photon_maps_with_out_of_core_subdomains(sdd, court_maps):
+    """With at most one of the court's four subdomain BVHs in device memory the photons are
+    the all-resident ones bit for bit (in another order: their slots follow the appends)."""
+    h, gm, _ = court_maps
+    sdd.sdd_set_tuning(h.h, {**sdd.sdd_get_tuning(h.h), "resident_subdomains": 1})
+    try:
+        loads = sdd.sdd_get_stats(h.h)["subdomain_loads"]
+        gs = sdd.PhotonMaps(h.h, LAMS, 200000, 17, (0.0, 0.0, 0.5), 5.0, 20.0, 0.1)
+        assert sdd.sdd_get_stats(h.h)["subdomain_loads"] > loads  # the subdomains were streamed in
+    finally:
+        sdd.sdd_set_tuning(h.h, {**sdd.sdd_get_tuning(h.h), "resident_subdomains": 0})
+    for m in (CAUSTIC, GLOBAL):
+        a, b = gm.photons(m), gs.photons(m)
+        ka = np.lexsort((a["seq"], a["id"], a["lam"]))
+        kb = np.lexsort((b["seq"], b["id"], b["lam"]))
+        for k in ("pos", "nrm", "power", "lam", "id", "seq"):
+            assert np.array_equal(a[k][ka], b[k][kb]), (m, k)
 
 
 def test_invalid_photon_map_use_is_rejected(sdd, court_maps):
