@@ -155,7 +155,7 @@ typedef struct {
                                      tracing at heterogeneous-tile hits; its weights are read at
                                      render time (a replayed frame uses the current weights) */
   int bundle;              /* Monte Carlo spectral bundles (Sec. 4: the spectral array cut into
-                              groups): 0 or 1 = every wavelength is its own path; B = 2..16 =
+                              groups): 0 or 1 = every wavelength is its own path; B = 2..64 =
                               wavelengths jB .. jB+B-1 draw every random number on counter word j
                               and share one ray while their decisions agree (one traversal for the
                               group); a member whose branch differs continues on its own ray.

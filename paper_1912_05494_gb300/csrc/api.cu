@@ -138,6 +138,7 @@ struct sdd_scene {
   // workspace
   DevArr<float4> rb_o[2], rb_d[2], sb_o, sb_d;
   DevArr<float> rb_w[2], sb_c;  // spectral bundles: per-member throughput / shadow contribution
+  DevArr<unsigned long long> rb_m[2], sb_m;  // spectral bundles: member masks of rays / shadow rays
   DevArr<uint2> rb_info[2], sb_info;
   DevArr<float2> hits;
   DevArr<uint32_t> q[2], sq[2];
@@ -181,8 +182,10 @@ struct sdd_scene {
     for (int i = 0; i < 2; ++i) {
       rb_o[i].release(); rb_d[i].release(); rb_info[i].release(); q[i].release(); sq[i].release();
       rb_w[i].release();
+      rb_m[i].release();
     }
     sb_c.release();
+    sb_m.release();
     sb_o.release(); sb_d.release(); sb_info.release(); hits.release(); path_L.release();
     path_hash.release(); film.release(); pixel_list.release(); out_spec.release(); out_xyz.release();
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
@@ -468,7 +471,7 @@ sdd_status run_closest_passes(sdd_scene* s, const RenderParams& p0, RayBuf rb, i
 sdd_status run_shadow_passes(sdd_scene* s, const RenderParams& p0, const WaveDesc& w, int qcap, cudaStream_t st) {
   RenderParams p = p0;
   int a = 0;
-  ShadowBuf sb{s->sb_o.p, s->sb_d.p, s->sb_info.p, qcap, s->sb_c.p};
+  ShadowBuf sb{s->sb_o.p, s->sb_d.p, s->sb_info.p, qcap, s->sb_c.p, s->sb_m.p};
   const int bound = pass_bound(s);
   for (int pass = 0; pass <= bound; ++pass) {
     sdd_status r = read_ctl(s, st);
@@ -591,6 +594,7 @@ sdd_status ensure_ctl(sdd_scene* s) {
 sdd_status ensure_workspace(sdd_scene* s, size_t cap, size_t paths, int n_slots, bool hash, int bundle) {
   for (int i = 0; i < 2; ++i) {
     if (bundle > 1) CK(s->rb_w[i].ensure(cap * (size_t)bundle));
+    if (bundle > 1) CK(s->rb_m[i].ensure(cap));
     CK(s->rb_o[i].ensure(cap));
     CK(s->rb_d[i].ensure(cap));
     CK(s->rb_info[i].ensure(cap));
@@ -598,6 +602,7 @@ sdd_status ensure_workspace(sdd_scene* s, size_t cap, size_t paths, int n_slots,
     CK(s->sq[i].ensure(cap * (size_t)s->n_sub));
   }
   if (bundle > 1) CK(s->sb_c.ensure(cap * (size_t)bundle));
+  if (bundle > 1) CK(s->sb_m.ensure(cap));
   CK(s->sb_o.ensure(cap));
   CK(s->sb_d.ensure(cap));
   CK(s->sb_info.ensure(cap));
@@ -770,17 +775,17 @@ sdd_status render_batched(sdd_scene* s, const RenderParams& p, const std::vector
   if (form == 2) {
     gg = graph_grids(p, s->tuning.top_nodes, s->tuning.block_chunks);  // occupancy queries stay outside the capture
   } else {
-    grid = persistent_grid(p.stats >= 2, tile_mode(p), p.bundle > 1);
+    grid = persistent_grid(p.stats >= 2, tile_mode(p), p.bundle);
     if (grid <= 0) return fail(SDD_ERR_CUDA, "persistent kernel does not fit on this device");
   }
   PersistBuffers b;
   for (int i = 0; i < 2; ++i) {
-    b.rb[i] = RayBuf{s->rb_o[i].p, s->rb_d[i].p, s->rb_info[i].p, qcap, s->rb_w[i].p};
+    b.rb[i] = RayBuf{s->rb_o[i].p, s->rb_d[i].p, s->rb_info[i].p, qcap, s->rb_w[i].p, s->rb_m[i].p};
     b.q[i] = s->q[i].p;
     b.sq[i] = s->sq[i].p;
   }
   b.hits = s->hits.p;
-  b.sb = ShadowBuf{s->sb_o.p, s->sb_d.p, s->sb_info.p, qcap, s->sb_c.p};
+  b.sb = ShadowBuf{s->sb_o.p, s->sb_d.p, s->sb_info.p, qcap, s->sb_c.p, s->sb_m.p};
   b.path_L = s->path_L.p;
   b.qcap = qcap;
   // graph key: everything the captured frame depends on
@@ -976,7 +981,7 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
   if (o->batched < 0 || o->batched > 2) return fail(SDD_ERR_ARG, "batched must be 0, 1 or 2");
   if (o->batched != 0 && s->strm.cap > 0)
     return fail(SDD_ERR_STATE, "out-of-core subdomains (resident_subdomains > 0) need the host-driven form (batched = 0)");
-  if (o->bundle < 0 || o->bundle > kMaxBundle) return fail(SDD_ERR_ARG, "bundle must be in [0, 16]");
+  if (o->bundle < 0 || o->bundle > kMaxBundle) return fail(SDD_ERR_ARG, "bundle must be in [0, 64]");
   if (const sdd_photon_maps* pm = o->photon_maps) {
     if (o->mode != SDD_MODE_MONTE_CARLO) return fail(SDD_ERR_ARG, "photon maps need Monte Carlo mode");
     if (o->batched == 1) return fail(SDD_ERR_ARG, "photon maps need the host-driven or the graph form (batched = 0 or 2)");
@@ -1065,9 +1070,9 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
     p.pm = o->photon_maps->view();
   }
   if (p.use_surrogate) {
-    // one entry per tile hit, with bundles one per member (entries ray << 4 | member)
+    // one entry per tile hit, with bundles one per member (entries ray << 6 | member)
     const size_t tcap = cap * (size_t)B;
-    if (B > 1 && cap > (1u << 28)) return fail(SDD_ERR_ARG, "wave too large for spectral bundles with the network");
+    if (B > 1 && cap > (1u << 26)) return fail(SDD_ERR_ARG, "wave too large for spectral bundles with the network");
     if (tcap > 0x7FFFFFFFu) return fail(SDD_ERR_ARG, "wave too large for the tile queue");
     CK(s->tile_queue.ensure(tcap));
     p.tile_queue = s->tile_queue.p;
@@ -1146,7 +1151,7 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
     CK(cudaMemsetAsync(s->d_ctl, 0, offsetof(Control, node_visits), st));
     CK(cudaMemsetAsync(s->path_L.p, 0, sizeof(float) * (size_t)w.n_paths * n_slots, st));
     int cur = 0;
-    RayBuf rb0{s->rb_o[0].p, s->rb_d[0].p, s->rb_info[0].p, qcap, s->rb_w[0].p};
+    RayBuf rb0{s->rb_o[0].p, s->rb_d[0].p, s->rb_info[0].p, qcap, s->rb_w[0].p, s->rb_m[0].p};
     int ev = s->ev_begin(TK_RAYGEN, st);
     launch_raygen(p, w, rb0, s->q[0].p, s->d_ctl->q_count[0], qcap, s->d_ctl, st);
     s->ev_end(ev, st);
@@ -1155,14 +1160,15 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
     int n_rays = (int)w.n_paths;
     for (int gen = 0; n_rays > 0; ++gen) {
       if (gen > o->max_depth + 1) return fail(SDD_ERR_TIMEOUT, "generation count exceeded max_depth + 1");
-      RayBuf rc{s->rb_o[cur].p, s->rb_d[cur].p, s->rb_info[cur].p, qcap, s->rb_w[cur].p};
-      RayBuf rn{s->rb_o[1 - cur].p, s->rb_d[1 - cur].p, s->rb_info[1 - cur].p, qcap, s->rb_w[1 - cur].p};
+      RayBuf rc{s->rb_o[cur].p, s->rb_d[cur].p, s->rb_info[cur].p, qcap, s->rb_w[cur].p, s->rb_m[cur].p};
+      RayBuf rn{s->rb_o[1 - cur].p, s->rb_d[1 - cur].p, s->rb_info[1 - cur].p, qcap, s->rb_w[1 - cur].p,
+                s->rb_m[1 - cur].p};
       r = run_closest_passes(s, p, rc, qcap, st);
       if (r) return r;
       // the closest passes left every count at zero; shade refills q[0] and sq[0]
       CK(cudaMemsetAsync(s->d_ctl, 0, offsetof(Control, error), st));
       CK(cudaMemsetAsync(&s->d_ctl->tile_hits, 0, sizeof(int), st));
-      ShadowBuf sb{s->sb_o.p, s->sb_d.p, s->sb_info.p, qcap, s->sb_c.p};
+      ShadowBuf sb{s->sb_o.p, s->sb_d.p, s->sb_info.p, qcap, s->sb_c.p, s->sb_m.p};
       ev = s->ev_begin(TK_SHADE, st);
       launch_shade(p, w, n_rays, rc, s->hits.p, rn, s->q[0].p, s->d_ctl->q_count[0], qcap, sb, s->sq[0].p,
                    s->d_ctl->sq_count[0], s->path_L.p, s->d_ctl, st);

@@ -1,12 +1,12 @@
 // bundle_device.cuh -- spectral bundles: the wavefront path with several wavelengths per ray.
 //
 // Sec. 4 of the paper cuts the 81-value spectral array into groups of n wavelengths as units
-// of work.  Here a bundle is B consecutive wavelengths (B = RenderParams::bundle, 2..16) of one (pixel,
+// of work.  Here a bundle is B consecutive wavelengths (B = RenderParams::bundle, 2..64) of one (pixel,
 // sample).  Every random number of the bundle's chains is drawn on the bundle index j in
 // place of the wavelength index (the rule the oracle follows), so as long as their decisions
 // agree the B chains share every vertex and one traversal serves them all.  A ray carries the
-// mask of the members that still follow it (the high 16 bits of its meta word) and one
-// throughput per member (RayBuf::w, [cap][B]).  At a vertex the members are split:
+// 64-bit mask of the members that still follow it (RayBuf::m) and one throughput per member
+// (RayBuf::w, [cap][B]).  At a vertex the members are split:
 //   thin-slab glass    reflected members and transmitted members (at most two rays);
 //   diffuse            one ray (the cosine direction does not depend on the wavelength) and
 //                      one shadow ray whose per-member contributions (ShadowBuf::c) the
@@ -40,24 +40,29 @@ __device__ __forceinline__ PathId path_id_bundle(const RenderParams& p, const Wa
   return r;
 }
 
+using Members = unsigned long long;
+
 // Members of bundle j: wavelengths j B .. min(j B + B, L) - 1.
-__device__ __forceinline__ uint32_t bundle_members(const RenderParams& p, uint32_t j) {
+__device__ __forceinline__ Members bundle_members(const RenderParams& p, uint32_t j) {
   int n = min(p.bundle, p.sp.n_lambda - (int)j * p.bundle);
-  return n >= 32 ? 0xFFFFFFFFu : ((1u << n) - 1u);
+  return n >= 64 ? ~0ull : ((1ull << n) - 1ull);
 }
 
+// Index of the lowest member in m (m != 0).
+__device__ __forceinline__ int first_member(Members m) { return __ffsll((long long)m) - 1; }
+
 // Hash updates of every member in `mask` (no-op without hashes).
-__device__ __forceinline__ void hash_word(uint32_t* hp, uint32_t mask, uint32_t w) {
+__device__ __forceinline__ void hash_word(uint32_t* hp, Members mask, uint32_t w) {
   if (!hp) return;
-  for (uint32_t m = mask; m; m &= m - 1) {
-    int b = __ffs(m) - 1;
+  for (Members m = mask; m; m &= m - 1) {
+    int b = first_member(m);
     hp[b] = fnv_word(hp[b], w);
   }
 }
-__device__ __forceinline__ void hash_event(uint32_t* hp, uint32_t mask, uint32_t ev) {
+__device__ __forceinline__ void hash_event(uint32_t* hp, Members mask, uint32_t ev) {
   if (!hp) return;
-  for (uint32_t m = mask; m; m &= m - 1) {
-    int b = __ffs(m) - 1;
+  for (Members m = mask; m; m &= m - 1) {
+    int b = first_member(m);
     hp[b] = fnv_byte(hp[b], ev);
   }
 }
@@ -66,7 +71,7 @@ __device__ __forceinline__ void hash_event(uint32_t* hp, uint32_t mask, uint32_t
 // returns its slot (-1 when not appended).  The caller writes its throughputs.
 __device__ __forceinline__ int emit_bundle_ray(bool want, const DevScene& sc, RayBuf nb, int* next_count, uint32_t* q,
                                                int* q_count, int qcap, float3 o, float seg0, float3 d, uint32_t path,
-                                               uint32_t meta, Control* ctl) {
+                                               uint32_t meta, Members members, Control* ctl) {
   int pos = warp_append(next_count, 0, want);
   bool ok = want && pos < nb.cap;
   if (want && !ok) atomicOr(&ctl->error, ERR_QUEUE_OVERFLOW);
@@ -74,6 +79,7 @@ __device__ __forceinline__ int emit_bundle_ray(bool want, const DevScene& sc, Ra
     nb.o[pos] = make_float4(o.x, o.y, o.z, seg0);
     nb.d[pos] = make_float4(d.x, d.y, d.z, 0.f);
     nb.info[pos] = make_uint2(path, meta);
+    nb.m[pos] = members;
   }
   int s = ok ? subdomain_of(sc, o) : 0;
   int qpos = warp_append(q_count, s, ok);
@@ -90,8 +96,8 @@ __device__ __forceinline__ float after_roulette(float t, bool roulette) { return
 // Writes the B member values val(0..B-1) of the record in slot pos (pos < 0: none) of dst
 // ([slots][B]).  Every lane of the warp calls this; the lanes with a slot hold consecutive
 // slots in lane order (warp_append), so their values go through the warp's staging area
-// (32 x kMaxBundle floats of shared memory) and the warp's block of dst is written with
-// coalesced stores instead of B strided partial-sector stores per lane.
+// (32 x B floats of shared memory) and the warp's block of dst is written with coalesced
+// stores instead of B strided partial-sector stores per lane.
 template <class F>
 __device__ __forceinline__ void store_members(float* dst, int pos, int B, float* stage, F val) {
   const unsigned m = __ballot_sync(0xffffffffu, pos >= 0);
@@ -122,7 +128,8 @@ __device__ __forceinline__ void dev_raygen_bundle(const RenderParams& p, const W
     primary_ray(p, id.pixel, u.x - 0.5f, u.y - 0.5f, &o, &d);
     rb.o[i] = make_float4(o.x, o.y, o.z, 0.f);
     rb.d[i] = make_float4(d.x, d.y, d.z, 0.f);
-    rb.info[i] = make_uint2(i, bundle_members(p, id.lam) << 16);  // depth 0, no flags
+    rb.info[i] = make_uint2(i, 0u);  // depth 0, no flags
+    rb.m[i] = bundle_members(p, id.lam);
     for (int b = 0; b < B; ++b) rb.w[(size_t)i * B + b] = 1.f;
     if (p.path_hash)
       for (int b = 0; b < B; ++b) p.path_hash[(size_t)i * B + b] = 0x811C9DC5u;
@@ -141,8 +148,9 @@ __device__ __forceinline__ void dev_raygen_bundle(const RenderParams& p, const W
 // series, Beer-Lambert, the Lambertian albedo) decides each member's branch with the shared
 // uniforms; the members are then grouped into child rays as the header describes.  Each
 // member's throughput after the vertex (before the roulette) is kept in shared memory, one
-// row of kMaxBundle floats per thread; the children's member values are written through a
-// per-warp staging area.  Blocks of at most kBlock threads.
+// row of B floats per thread; the children's member values are written through a per-warp
+// staging area of 32 x B floats.  The kernel's dynamic shared memory holds both:
+// bundle_shade_smem(B) bytes for blocks of kBlock threads.
 // kPM: photon maps (Sec. 3.2), as in dev_shade: the first diffuse vertex adds each member's
 // albedo / pi x (E_caustic + E_global) of its wavelength; the continuation carries
 // FLAG_PHOTON_DONE (sky light only: no NEE, no sun disc on escape).
@@ -157,7 +165,7 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
   // children: group 0 (members leaving in direction gd0), group 1 (thin-slab transmission:
   // members going straight on) and singles (each member on its own direction).  Origins and
   // the facing normal are recomputed where needed rather than kept live.
-  uint32_t gm[2] = {0u, 0u}, singles = 0u, msh = 0u, tile_m = 0u;
+  Members gm[2] = {0ull, 0ull}, singles = 0ull, msh = 0ull, tile_m = 0ull;
   uint32_t gf[2] = {0u, 0u};
   float3 gd0 = make_float3(0.f, 0.f, 0.f), dsh = gd0;
   uint32_t path = 0, v = 0, flags = 0, j = 0, lam0 = 0;
@@ -165,10 +173,9 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
   bool roulette = false;
   float uw = 0.f, cl_sh = 0.f, cos_i = 0.f, seg0 = 0.f;
   float3 pt = gd0, ng = gd0, d = gd0;
-  __shared__ float s_member_w[kBlock * kMaxBundle];
-  __shared__ float s_stage[kBlock * kMaxBundle];
-  float* wr = s_member_w + threadIdx.x * kMaxBundle;
-  float* stage = s_stage + (threadIdx.x & ~31u) * kMaxBundle;
+  extern __shared__ float s_bundle_rows[];
+  float* wr = s_bundle_rows + threadIdx.x * B;
+  float* stage = s_bundle_rows + (kBlock + (threadIdx.x & ~31u)) * B;
   uint32_t* hp = nullptr;
   PathId id{};
   if (active) {
@@ -176,7 +183,8 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
     uint2 inf = cur.info[r];
     float2 H = hits[r];
     path = inf.x;
-    const uint32_t depth = inf.y & 0xFFu, mask = inf.y >> 16;
+    const uint32_t depth = inf.y & 0xFFu;
+    const Members mask = cur.m[r];
     flags = (inf.y >> 8) & 0xFFu;
     seg0 = O.w;
     for (int b = 0; b < B; ++b) wr[b] = cur.w[(size_t)r * B + b];
@@ -192,8 +200,8 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
       atomicOr(&ctl->error, ERR_QUEUE_OVERFLOW);  // stale hit record of a dropped ray
     } else if (prim == kMissPrim) {
       const bool sun_counted = (flags & (FLAG_SUN_COUNTED | FLAG_PHOTON_DONE)) != 0u;
-      for (uint32_t m = mask; m; m &= m - 1) {
-        int b = __ffs(m) - 1;
+      for (Members m = mask; m; m &= m - 1) {
+        int b = first_member(m);
         Lp[b] += wr[b] * escape_radiance(p.sp, d, (int)lam0 + b, sun_counted);
       }
       hash_word(hp, mask, 0xFFFFFFFFu);
@@ -218,8 +226,8 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
         const float* mk = p.sp.mat_k + (size_t)mat * p.sp.n_lambda + lam0;
         if (kind == MAT_SOLID) {
           const bool inside = cos_n > 0.f;
-          for (uint32_t m = mask; m; m &= m - 1) {
-            int b = __ffs(m) - 1;
+          for (Members m = mask; m; m &= m - 1) {
+            int b = first_member(m);
             float nre = __ldg(mn + b), kk = __ldg(mk + b);
             float thr = wr[b];
             if (inside) thr *= beer_lambert(kk, H.x + seg0, __ldg(p.sp.lambda_nm + lam0 + b));
@@ -229,8 +237,8 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
             float eta = n1 / n2re;
             float c2 = 1.f - eta * eta * (1.f - cos_i * cos_i);
             wr[b] = thr;
-            if (u.x < R || c2 <= 0.f) gm[0] |= 1u << b;
-            else singles |= 1u << b;
+            if (u.x < R || c2 <= 0.f) gm[0] |= 1ull << b;
+            else singles |= 1ull << b;
           }
           hash_event(hp, gm[0], EV_REFLECT);
           hash_event(hp, singles, EV_TRANSMIT);
@@ -238,14 +246,14 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
           gf[0] = flags & ~FLAG_SUN_COUNTED;
         } else if (kind == MAT_SLAB) {
           const float thick = __ldg(p.sp.mat_thick + mat);
-          for (uint32_t m = mask; m; m &= m - 1) {
-            int b = __ffs(m) - 1;
+          for (Members m = mask; m; m &= m - 1) {
+            int b = first_member(m);
             float Rs, Ts;
             slab_RT(cos_i, __ldg(mn + b), __ldg(mk + b), thick, __ldg(p.sp.lambda_nm + lam0 + b), &Rs, &Ts, p.sp.slab_pol);
             float P = Rs / (Rs + Ts);
             wr[b] = wr[b] * (Rs + Ts);
-            if (u.x < P) gm[0] |= 1u << b;  // (a computed index would put gm in local memory)
-            else gm[1] |= 1u << b;
+            if (u.x < P) gm[0] |= 1ull << b;  // (a computed index would put gm in local memory)
+            else gm[1] |= 1ull << b;
           }
           hash_event(hp, gm[0], EV_REFLECT);
           hash_event(hp, gm[1], EV_TRANSMIT);
@@ -255,14 +263,14 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
         } else if (kind == MAT_DIFFUSE) {
           const float* ma = p.sp.mat_albedo + (size_t)mat * p.sp.n_lambda + lam0;
           hash_event(hp, mask, EV_DIFFUSE);
-          for (uint32_t m = mask; m; m &= m - 1) {
-            int b = __ffs(m) - 1;
+          for (Members m = mask; m; m &= m - 1) {
+            int b = first_member(m);
             wr[b] = wr[b] * __ldg(ma + b);
           }
           const bool photon_done = kPM && (flags & FLAG_PHOTON_DONE) != 0u;
           if (kPM && !photon_done) {
-            for (uint32_t m = mask; m; m &= m - 1) {
-              int b = __ffs(m) - 1;
+            for (Members m = mask; m; m &= m - 1) {
+              int b = first_member(m);
               const float2 E = photon_irradiance(p.pm, pt, nf, (int)lam0 + b);
               Lp[b] += wr[b] * kInvPi * (E.x + E.y);
             }
@@ -290,11 +298,11 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
         if ((int)v >= p.rr_start) {
           roulette = true;
           // tile members meet their roulette after their own trace (singles loop)
-          const uint32_t cand = gm[0] | gm[1] | (kind == MAT_SOLID ? singles : 0u);
-          for (uint32_t m = cand; m; m &= m - 1) {
-            int b = __ffs(m) - 1;
+          const Members cand = gm[0] | gm[1] | (kind == MAT_SOLID ? singles : 0ull);
+          for (Members m = cand; m; m &= m - 1) {
+            int b = first_member(m);
             if (uw >= fminf(0.95f, wr[b])) {
-              const uint32_t bit = 1u << b;
+              const Members bit = 1ull << b;
               gm[0] &= ~bit;
               gm[1] &= ~bit;
               if (kind == MAT_SOLID) singles &= ~bit;
@@ -315,18 +323,18 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
       og = offset_point(pt, ng, dg, eps);
       sg = seg0_of(ng, dg, eps);
     }
-    const int pos = emit_bundle_ray(gm[g] != 0u, p.sc, next, next_count, q, q_count, qcap, og, sg, dg, path,
-                                    v | (gf[g] << 8) | (gm[g] << 16), ctl);
-    const uint32_t mg = gm[g];
-    store_members(next.w, pos, B, stage, [&](int b) { return ((mg >> b) & 1u) ? after_roulette(wr[b], roulette) : 0.f; });
+    const int pos = emit_bundle_ray(gm[g] != 0ull, p.sc, next, next_count, q, q_count, qcap, og, sg, dg, path,
+                                    v | (gf[g] << 8), gm[g], ctl);
+    const Members mg = gm[g];
+    store_members(next.w, pos, B, stage, [&](int b) { return ((mg >> b) & 1ull) ? after_roulette(wr[b], roulette) : 0.f; });
   }
   // singles: each member on its own direction (transmission into or out of solid glass,
   // brute-force tiles)
-  if (__any_sync(0xffffffffu, singles != 0u)) {
+  if (__any_sync(0xffffffffu, singles != 0ull)) {
     const float* mn = p.sp.mat_n + (size_t)mat * p.sp.n_lambda + lam0;
     const float* mk = p.sp.mat_k + (size_t)mat * p.sp.n_lambda + lam0;
     for (int b = 0; b < B; ++b) {
-      bool want = (singles >> b) & 1u;
+      bool want = (singles >> b) & 1ull;
       float3 ds = d, os = d;
       float ts = 0.f, ss = 0.f;
       uint32_t fs = 0u;
@@ -347,7 +355,7 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
           tile_frame(p.tiles.L, pt, ng, d, &x, &y, &dl, &t1v, &t2v);
           TileOut tr = tile_trace(tile_of(p.tiles, __ldg(p.mat_tile + mat)), x, y, dl, __ldg(mn + b), __ldg(mk + b),
                                   lambda, id.pixel, id.sample, v, j, p.seed, kTileEvents, STREAM_TILE);
-          const uint32_t bit = 1u << b;
+          const Members bit = 1ull << b;
           if (tr.side == 2) {
             hash_event(hp, bit, EV_ABSORB);
             want = false;
@@ -373,24 +381,24 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
           ss = seg0_of(ng, ds, eps);
         }
       }
-      const int pos = emit_bundle_ray(want, p.sc, next, next_count, q, q_count, qcap, os, ss, ds, path,
-                                      v | (fs << 8) | ((1u << b) << 16), ctl);
+      const int pos = emit_bundle_ray(want, p.sc, next, next_count, q, q_count, qcap, os, ss, ds, path, v | (fs << 8),
+                                      1ull << b, ctl);
       store_members(next.w, pos, B, stage, [&](int k) { return k == b ? ts : 0.f; });
     }
   }
-  // network form: one tile-queue entry (ray << 4 | member) per member at a tile hit
-  if (kTM == 2 && __any_sync(0xffffffffu, tile_m != 0u)) {
+  // network form: one tile-queue entry (ray << 6 | member) per member at a tile hit
+  if (kTM == 2 && __any_sync(0xffffffffu, tile_m != 0ull)) {
     for (int b = 0; b < B; ++b) {
-      const bool want = (tile_m >> b) & 1u;
+      const bool want = (tile_m >> b) & 1ull;
       const int tpos = warp_append(p.tile_count, 0, want);
       if (want) {
-        if (tpos < p.tile_cap) p.tile_queue[tpos] = ((uint32_t)r << 4) | (uint32_t)b;
+        if (tpos < p.tile_cap) p.tile_queue[tpos] = ((uint32_t)r << 6) | (uint32_t)b;
         else atomicOr(&ctl->error, ERR_QUEUE_OVERFLOW);
       }
     }
   }
   // shadow ray toward the sun, one contribution per member
-  const bool esh = msh != 0u;
+  const bool esh = msh != 0ull;
   const float3 osh = esh ? offset_point(pt, ng, dsh, eps) : dsh;
   int pos = warp_append(shadow_count, 0, esh);
   bool ok = esh && pos < sb.cap;
@@ -398,10 +406,11 @@ __device__ __forceinline__ void dev_shade_bundle(const RenderParams& p, const Wa
   if (ok) {
     sb.o[pos] = make_float4(osh.x, osh.y, osh.z, 0.f);
     sb.d[pos] = make_float4(dsh.x, dsh.y, dsh.z, 0.f);
-    sb.info[pos] = make_uint2(path, msh | (v << 16));
+    sb.info[pos] = make_uint2(path, v << 16);
+    sb.m[pos] = msh;
   }
   store_members(sb.c, ok ? pos : -1, B, stage, [&](int b) {
-    return ((msh >> b) & 1u) ? wr[b] * kInvPi * cl_sh * __ldg(p.sp.sun + lam0 + b) * p.sp.sun_omega : 0.f;
+    return ((msh >> b) & 1ull) ? wr[b] * kInvPi * cl_sh * __ldg(p.sp.sun + lam0 + b) * p.sp.sun_omega : 0.f;
   });
   int ss = ok ? subdomain_of(p.sc, osh) : 0;
   int qpos = warp_append(sq_count, ss, ok);
@@ -440,7 +449,7 @@ __device__ __forceinline__ void dev_shadow_bundle(const RenderParams& p, const W
   const uint32_t lam0 = id.lam * (uint32_t)B;
   const uint32_t bounce = inf.y >> 16;
   const ShadowKey key{id.pixel, id.sample, bounce, p.seed, id.lam};
-  uint32_t live = inf.y & 0xFFFFu;
+  Members live = active ? sb.m[r] : 0ull;
   float* c = sb.c + (size_t)r * B;
   uint32_t* hp = (active && p.path_hash && p.mode == 1) ? p.path_hash + (size_t)inf.x * B : nullptr;
   const RayPre rp = ray_pre(o, d);
@@ -452,8 +461,8 @@ __device__ __forceinline__ void dev_shadow_bundle(const RenderParams& p, const W
     if (kind == MAT_SLAB) {
       const float cos_i = fabsf(dot3(d, f3(nm)));
       const float thick = __ldg(p.sp.mat_thick + mat);
-      for (uint32_t m = live; m; m &= m - 1) {
-        int b = __ffs(m) - 1;
+      for (Members m = live; m; m &= m - 1) {
+        int b = first_member(m);
         float Rs, Ts;
         slab_RT(cos_i, __ldg(p.sp.mat_n + m0 + b), __ldg(p.sp.mat_k + m0 + b), thick,
                 __ldg(p.sp.lambda_nm + lam0 + b), &Rs, &Ts, p.sp.slab_pol);
@@ -462,8 +471,8 @@ __device__ __forceinline__ void dev_shadow_bundle(const RenderParams& p, const W
       return false;
     }
     if (kTM == 2 && kind == MAT_TILE) {
-      for (uint32_t m = live; m; m &= m - 1) {
-        int b = __ffs(m) - 1;
+      for (Members m = live; m; m &= m - 1) {
+        int b = first_member(m);
         c[b] *= __ldg(p.tile_sun_T + m0 + b);
       }
       return false;
@@ -473,19 +482,19 @@ __device__ __forceinline__ void dev_shadow_bundle(const RenderParams& p, const W
       float3 dl, t1v, t2v;
       tile_frame(p.tiles.L, rp.o + t * d, f3(nm), d, &x, &y, &dl, &t1v, &t2v);
       const TileDev tile = tile_of(p.tiles, __ldg(p.mat_tile + mat));
-      for (uint32_t m = live; m; m &= m - 1) {
-        int b = __ffs(m) - 1;
+      for (Members m = live; m; m &= m - 1) {
+        int b = first_member(m);
         TileOut tr = tile_trace(tile, x, y, dl, __ldg(p.sp.mat_n + m0 + b), __ldg(p.sp.mat_k + m0 + b),
                                 __ldg(p.sp.lambda_nm + lam0 + b), key.pixel, key.sample, key.bounce, key.word,
                                 key.seed, kTileEvents, STREAM_SHADOW_TILE);
         if (tr.side == 1 && dot3(tr.dir, dl) > kCos1Deg) {
           c[b] *= tr.w;
         } else {
-          live &= ~(1u << b);
-          hash_event(hp, 1u << b, EV_SHADOW_BLOCKED);
+          live &= ~(1ull << b);
+          hash_event(hp, 1ull << b, EV_SHADOW_BLOCKED);
         }
       }
-      return live == 0u;
+      return live == 0ull;
     }
     return true;
   };
@@ -500,11 +509,11 @@ __device__ __forceinline__ void dev_shadow_bundle(const RenderParams& p, const W
     if (ovf) atomicOr(&ctl->error, ERR_STACK_OVERFLOW);
     cross = !blocked && next >= 0;
     if (cross) {
-      sb.info[r].y = live | (bounce << 16);
+      sb.m[r] = live;
     } else if (!blocked) {
       float* Lp = path_L + (size_t)inf.x * B;
-      for (uint32_t m = live; m; m &= m - 1) {
-        int b = __ffs(m) - 1;
+      for (Members m = live; m; m &= m - 1) {
+        int b = first_member(m);
         Lp[b] += c[b];
       }
       hash_event(hp, live, EV_SHADOW_OPEN);

@@ -11,10 +11,10 @@ __global__ void __launch_bounds__(kBlock) k_raygen_bundle(RenderParams p, WaveDe
   dev_raygen_bundle(p, w, i, i < w.n_paths, rb, q, q_count, qcap, ctl);
 }
 
-// Six resident blocks per SM as in the graph form's bundle shading (a register cap that keeps
+// Five resident blocks per SM as in the graph form's bundle shading (a register cap that keeps
 // more warps in flight for the shading's memory latency); brute-force tiles keep their registers.
 template <int kTM, bool kPM = false>
-__global__ void __launch_bounds__(kBlock, kTM == 1 ? 1 : 6) k_shade_bundle(RenderParams p, WaveDesc w, int n_rays, RayBuf cur,
+__global__ void __launch_bounds__(kBlock, kTM == 1 ? 1 : 5) k_shade_bundle(RenderParams p, WaveDesc w, int n_rays, RayBuf cur,
                                                          const float2* __restrict__ hits, RayBuf next, uint32_t* q,
                                                          int* q_count, int qcap, ShadowBuf sb, uint32_t* sq,
                                                          int* sq_count, float* path_L, Control* ctl) {
@@ -79,28 +79,34 @@ void launch_raygen_bundle(const RenderParams& p, const WaveDesc& w, RayBuf rb, u
   k_raygen_bundle<<<blocks_for(w.n_paths, kBlock), kBlock, 0, st>>>(p, w, rb, q, q_count, qcap, ctl);
 }
 
+template <int kTM, bool kPM>
+static void launch_shade_bundle_t(const RenderParams& p, const WaveDesc& w, int n_rays, RayBuf cur, const float2* hits,
+                                  RayBuf next, uint32_t* q, int* q_count, int qcap, ShadowBuf sb, uint32_t* sq,
+                                  int* sq_count, float* path_L, Control* ctl, cudaStream_t st) {
+  const size_t smem = bundle_shade_smem(p.bundle);
+  if (allow_dynamic_smem((const void*)k_shade_bundle<kTM, kPM>, smem) != cudaSuccess) return;  // reported at the
+                                                                                                 // next error check
+  k_shade_bundle<kTM, kPM><<<blocks_for(n_rays, kBlock), kBlock, smem, st>>>(p, w, n_rays, cur, hits, next, q, q_count,
+                                                                           qcap, sb, sq, sq_count, path_L, ctl);
+}
+
 void launch_shade_bundle(const RenderParams& p, const WaveDesc& w, int n_rays, RayBuf cur, const float2* hits,
                          RayBuf next, uint32_t* q, int* q_count, int qcap, ShadowBuf sb, uint32_t* sq, int* sq_count,
                          float* path_L, Control* ctl, cudaStream_t st) {
   if (n_rays <= 0) return;
   if (p.use_photons) {  // photon maps: brute-force tiles or none
     if (tile_mode(p) == 1)
-      k_shade_bundle<1, true><<<blocks_for(n_rays, kBlock), kBlock, 0, st>>>(p, w, n_rays, cur, hits, next, q, q_count,
-                                                                             qcap, sb, sq, sq_count, path_L, ctl);
+      launch_shade_bundle_t<1, true>(p, w, n_rays, cur, hits, next, q, q_count, qcap, sb, sq, sq_count, path_L, ctl, st);
     else
-      k_shade_bundle<0, true><<<blocks_for(n_rays, kBlock), kBlock, 0, st>>>(p, w, n_rays, cur, hits, next, q, q_count,
-                                                                             qcap, sb, sq, sq_count, path_L, ctl);
+      launch_shade_bundle_t<0, true>(p, w, n_rays, cur, hits, next, q, q_count, qcap, sb, sq, sq_count, path_L, ctl, st);
     return;
   }
   if (tile_mode(p) == 1)
-    k_shade_bundle<1><<<blocks_for(n_rays, kBlock), kBlock, 0, st>>>(p, w, n_rays, cur, hits, next, q, q_count, qcap,
-                                                                     sb, sq, sq_count, path_L, ctl);
+    launch_shade_bundle_t<1, false>(p, w, n_rays, cur, hits, next, q, q_count, qcap, sb, sq, sq_count, path_L, ctl, st);
   else if (tile_mode(p) == 2)
-    k_shade_bundle<2><<<blocks_for(n_rays, kBlock), kBlock, 0, st>>>(p, w, n_rays, cur, hits, next, q, q_count, qcap,
-                                                                     sb, sq, sq_count, path_L, ctl);
+    launch_shade_bundle_t<2, false>(p, w, n_rays, cur, hits, next, q, q_count, qcap, sb, sq, sq_count, path_L, ctl, st);
   else
-    k_shade_bundle<0><<<blocks_for(n_rays, kBlock), kBlock, 0, st>>>(p, w, n_rays, cur, hits, next, q, q_count, qcap,
-                                                                     sb, sq, sq_count, path_L, ctl);
+    launch_shade_bundle_t<0, false>(p, w, n_rays, cur, hits, next, q, q_count, qcap, sb, sq, sq_count, path_L, ctl, st);
 }
 
 template <int kB, int kTM>

@@ -95,9 +95,11 @@ __global__ void __launch_bounds__(kBlock) k_shade_g(RenderParams p, WaveDesc w, 
 }
 
 // The same for bundle rays.  Resident blocks per SM: a register cap that keeps more warps in
-// flight for the shading's memory latency (measured on the nave frame: no cap 63.2 ms, 4
-// blocks 52.6, 5 blocks 51.6, 6 blocks 49.5); brute-force tiles keep their registers.
-constexpr int kShadeBlocks = 6;
+// flight for the shading's memory latency (measured on the nave frame, shading per frame:
+// bundles of 14: no cap 63.2 ms, 4 blocks 52.6, 5 blocks 51.6, 6 blocks 49.5; bundles of 41,
+// whose 42 KB of member rows per block allow 5: 4 blocks 37.2, 5 blocks 37.0, 6 blocks (5
+// resident) 38.9); brute-force tiles keep their registers.
+constexpr int kShadeBlocks = 5;
 template <int kTM, bool kPM>
 __global__ void __launch_bounds__(kBlock, kTM == 1 ? 1 : kShadeBlocks)
     k_shade_bundle_g(RenderParams p, WaveDesc w, const int* n_in, RayBuf cur, const float2* __restrict__ hits,
@@ -224,7 +226,9 @@ cudaError_t launch_fn(const void* fn, int grid, int block, void** args, cudaStre
 GraphGrids graph_grids(const RenderParams& p, int top_nodes, int block_chunks) {
   const int tn = staged_nodes(p.sc.n_sub, top_nodes);
   const size_t smem = (size_t)tn * p.sc.n_sub * sizeof(Node);
-  return GraphGrids{grid_of(traverse_fn(p), kChunk, smem), grid_of(shade_fn(p), kBlock),
+  const size_t shade_smem = bundle_shade_smem(p.bundle);
+  allow_dynamic_smem(shade_fn(p), shade_smem);
+  return GraphGrids{grid_of(traverse_fn(p), kChunk, smem), grid_of(shade_fn(p), kBlock, shade_smem),
                     grid_of(shadow_fn(p), kChunk), tn, block_chunks};
 }
 
@@ -244,7 +248,7 @@ cudaError_t launch_shade_g(const RenderParams& p, const GraphGrids& g, const Wav
   void* args[] = {(void*)&p,  (void*)&w,       (void*)&n_in, (void*)&cur, (void*)&hits,     (void*)&next,
                   (void*)&next_count, (void*)&q, (void*)&q_count, (void*)&qcap, (void*)&sb, (void*)&sq,
                   (void*)&sq_count, (void*)&path_L, (void*)&ctl};
-  return launch_fn(shade_fn(p), g.shade, kBlock, args, st);
+  return cudaLaunchKernel(shade_fn(p), dim3(g.shade), dim3(kBlock), args, bundle_shade_smem(p.bundle), st);
 }
 
 cudaError_t launch_shadow_g(const RenderParams& p, const GraphGrids& g, const WaveDesc& w, const int* counts_in,

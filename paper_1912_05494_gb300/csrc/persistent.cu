@@ -27,14 +27,17 @@ cudaError_t barrier_selftest(PersistCtl* pc, Control* ctl, int timeout_ms) {
   return cudaGetLastError();
 }
 
-// Blocks of the cooperative launch: every SM times the blocks of the kernel that fit on one.
-int persistent_grid(bool stats, int tile_mode, bool bundle) {
-  const void* fn = persistent_kernel(stats, tile_mode, bundle);
+// Blocks of the cooperative launch: every SM times the blocks of the kernel that fit on one
+// (with spectral bundles of width `bundle`, their shading rows in dynamic shared memory).
+int persistent_grid(bool stats, int tile_mode, int bundle) {
+  const void* fn = persistent_kernel(stats, tile_mode, bundle > 1);
   if (!fn) return 0;
+  const size_t smem = bundle_shade_smem(bundle);
+  if (allow_dynamic_smem(fn, smem) != cudaSuccess) return 0;
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPB, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPB, smem);
   return sms * per_sm;
 }
 
@@ -43,7 +46,7 @@ cudaError_t launch_persistent_wave(const RenderParams& p, const WaveDesc& w, con
   void* args[] = {(void*)&p, (void*)&w, (void*)&b, (void*)&pc, (void*)&ctl, (void*)&seg};
   const void* fn = persistent_kernel(p.stats >= 2, tile_mode(p), p.bundle > 1);
   if (!fn) return cudaErrorInvalidValue;
-  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPB), args, 0, st);
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPB), args, bundle_shade_smem(p.bundle), st);
 }
 
 }  // namespace sdd

@@ -46,7 +46,7 @@ struct PersistCtl {
 
 // Blocks of the cooperative launch (SMs x resident blocks) for a scene's tile mode (0 none,
 // 1 brute force, 2 network), with or without spectral bundles.
-int persistent_grid(bool stats, int tile_mode, bool bundle);
+int persistent_grid(bool stats, int tile_mode, int bundle);
 // The spectral-bundle kernels (persistent_bundle.cu) per tile mode; nullptr otherwise.
 const void* persistent_bundle_kernel(bool stats, int tile_mode);
 // Runs k_barrier_selftest (four blocks, the last never arrives) on the legacy stream.

@@ -35,6 +35,7 @@ namespace sdd {
 namespace {
 
 constexpr int kPB = 128;  // threads per block
+static_assert(kPB == kShadeThreads, "bundle shading rows are sized for kShadeThreads threads");
 constexpr int kBundleBlocks = 8;  // resident blocks per SM of the spectral-bundle kernels (measured best of 4, 6, 8)
 constexpr unsigned long long kBarrierTimeoutNs = 5ull * 1000 * 1000 * 1000;
 

@@ -29,6 +29,7 @@ namespace {
 
 constexpr float kInvPi = 0.31830988618379067f;
 constexpr int kBlock = 128;
+static_assert(kBlock == kShadeThreads, "bundle shading rows are sized for kShadeThreads threads");
 
 enum Event : uint32_t {
   EV_REFLECT = 0, EV_TRANSMIT = 1, EV_DIFFUSE = 2, EV_ABSORB = 3, EV_RR_KILL = 4,

@@ -13,7 +13,7 @@
 namespace sdd {
 
 constexpr int kMaxSubdomains = 64;
-constexpr int kMaxBundle = 16;            // wavelengths per spectral bundle (member mask bits)
+constexpr int kMaxBundle = 64;            // wavelengths per spectral bundle (member mask bits)
 constexpr int kStackSize = 64;            // BVH traversal stack entries per ray
 constexpr uint32_t kMissPrim = 0xFFFFFFFFu;
 
@@ -82,24 +82,38 @@ struct DevCamera {
   int width, height, ortho;
 };
 
+// Threads per block of the shading kernels (host-driven, graph form and persistent).
+constexpr int kShadeThreads = 128;
+// Dynamic shared memory of a kernel that shades spectral-bundle rays: per thread a row of its
+// ray's B member throughputs and a staging row of B child values.
+inline size_t bundle_shade_smem(int bundle) {
+  return bundle > 1 ? 2u * (size_t)kShadeThreads * (size_t)bundle * sizeof(float) : 0u;
+}
+// Lets kernel fn take `bytes` of dynamic shared memory (above 48 KB a kernel must opt in).
+inline cudaError_t allow_dynamic_smem(const void* fn, size_t bytes) {
+  return bytes > 48u * 1024u ? cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes)
+                             : cudaSuccess;
+}
+
 // Ray state, structure of arrays with capacity `cap`.
 struct RayBuf {
   float4* o;      // origin xyz, w = seg0 (distance back to the previous surface plane)
   float4* d;      // direction xyz, w = throughput (unused with spectral bundles)
-  uint2* info;    // x = wave-local path id, y = depth(8) | flags(8) << 8 | code(16) << 16;
-                  // with spectral bundles the high 16 bits are the member mask instead
+  uint2* info;    // x = wave-local path id, y = depth(8) | flags(8) << 8 | code(16) << 16
+                  // (the code is unused with spectral bundles)
   int cap;
   float* w;       // spectral bundles: per-member throughput [cap][bundle], else unused
+  unsigned long long* m;  // spectral bundles: the members that follow the ray [cap], else unused
 };
 
 struct ShadowBuf {
   float4* o;      // origin xyz, w unused
   float4* d;      // direction xyz, w = contribution carried so far (unused with bundles)
   uint2* info;    // x = wave-local path id, y = contribution slot (deterministic mode, low 16
-                  // bits; with spectral bundles the live member mask) | bounce of the vertex
-                  // that cast it << 16
+                  // bits) | bounce of the vertex that cast it << 16
   int cap;
   float* c;       // spectral bundles: per-member contribution [cap][bundle], else unused
+  unsigned long long* m;  // spectral bundles: the members still carried [cap], else unused
 };
 
 // Device control block: queue counters and error word, read back by the host.

@@ -49,13 +49,13 @@ struct TileHit {
   int member;  // spectral bundles: the member of the ray's bundle (0 otherwise)
 };
 
-// The tile hit of tile-queue entry e: a ray slot, or with spectral bundles ray << 4 | member.
+// The tile hit of tile-queue entry e: a ray slot, or with spectral bundles ray << 6 | member.
 __device__ __forceinline__ TileHit tile_hit(const RenderParams& p, const WaveDesc& w, const RayBuf& cur,
                                             const float2* hits, uint32_t e) {
   TileHit h;
   const bool bund = p.bundle > 1;
-  const uint32_t r = bund ? e >> 4 : e;
-  h.member = bund ? (int)(e & 15u) : 0;
+  const uint32_t r = bund ? e >> 6 : e;
+  h.member = bund ? (int)(e & 63u) : 0;
   const float4 O = cur.o[r], D = cur.d[r];
   h.info = cur.info[r];
   const float2 H = hits[r];
@@ -156,7 +156,7 @@ struct TileShadePolicy {
         const uint32_t fl = (!refl && ballistic) ? flags : (flags & ~FLAG_SUN_COUNTED);
         e0 = true;
         d0 = normalize3(dir.x * h.t1 + dir.y * h.t2 + dir.z * h.ng);
-        meta0 = v | (fl << 8) | (bund ? (1u << member) << 16 : 0u);
+        meta0 = v | (fl << 8);
         if ((int)v >= p.rr_start) {
           const float qs = fminf(0.95f, thr);
           if (up.w >= qs) {
@@ -178,7 +178,7 @@ struct TileShadePolicy {
     }
     if (bund) {
       const int pos = emit_bundle_ray(e0, p.sc, c.next, c.next_count, c.q, c.q_count, qcap, o0, s00, d0, path, meta0,
-                                      ctl);
+                                      1ull << member, ctl);
       if (pos >= 0) {
         float* cw = c.next.w + (size_t)pos * p.bundle;
         for (int k = 0; k < p.bundle; ++k) cw[k] = k == member ? thr0 : 0.f;

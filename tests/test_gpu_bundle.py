@@ -4,7 +4,8 @@ With bundle B the wavelengths jB .. jB+B-1 of a (pixel, sample) draw every rando
 counter word j; the oracle still traces each wavelength's chain on its own, so every member
 of a GPU bundle is compared with the oracle's chain of that wavelength path by path, on the
 Monte Carlo bars of the unbundled path (relative image error <= 1e-3, branch flips <= 0.1 %
-of paths).  Cases cover full and partial last bundles (81 = 9 x 9 = 20 x 4 + 1 = 5 x 16 + 1),
+of paths).  Cases cover full and partial last bundles (81 = 9 x 9 = 20 x 4 + 1 = 5 x 16 + 1 =
+3 x 27 = 41 + 40 = 64 + 17),
 the split into reflected and transmitted members at thin slabs, the per-member rays of solid
 glass and brute-force tiles, the subdomain hand-off and the host-side argument checks.
 """
@@ -56,7 +57,7 @@ def nave():
     return S.nave_scene(seed=1)
 
 
-@pytest.mark.parametrize("bundle", [9, 4, 16, 2])
+@pytest.mark.parametrize("bundle", [9, 4, 16, 2, 27, 41, 64])
 def test_bundled_nave_matches_the_oracle(sdd, orc, nave, bundle):
     sc, cam, spec = nave
     cam = S.CameraData(**{**cam.__dict__, "width": 48, "height": 32})
@@ -125,12 +126,12 @@ def test_bundles_through_brute_force_tiles(sdd, orc):
     assert err <= 1e-3, err
 
 
-@pytest.mark.parametrize("n_sub", [8, 3])
-def test_batched_bundles_equal_host_driven(sdd, nave, n_sub):
+@pytest.mark.parametrize("n_sub,bundle", [(8, 14), (3, 14), (8, 41)])
+def test_batched_bundles_equal_host_driven(sdd, nave, n_sub, bundle):
     """The persistent form runs the same per-ray device code: the same image, bit for bit."""
     sc, cam, spec = nave
     cam = S.CameraData(**{**cam.__dict__, "width": 64, "height": 40})
-    spec = S.RenderSpec(**{**spec.__dict__, "spp": 3, "bundle": 14})
+    spec = S.RenderSpec(**{**spec.__dict__, "spp": 3, "bundle": bundle})
     h = sdd.SceneHandle(sc, n_subdomains=n_sub)
     a, pa, ha = render(sdd, h, cam, spec)
     b, pb, hb = render(sdd, h, cam, spec, batched=1)
@@ -159,7 +160,7 @@ def test_bundle_argument_checks(sdd, nave):
     h = sdd.SceneHandle(sc)
     out = torch.empty((64, spec.n_lambda), device="cuda")
     with pytest.raises(sdd.SddError, match="bundle"):
-        sdd.sdd_render(h.h, cam, S.RenderSpec(**{**spec.__dict__, "bundle": 17}), out)
+        sdd.sdd_render(h.h, cam, S.RenderSpec(**{**spec.__dict__, "bundle": 65}), out)
     dsc, dcam, dspec = S.slab_scene(0)
     with pytest.raises(sdd.SddError, match="bundle"):
         sdd.sdd_render(sdd.SceneHandle(dsc).h, dcam, S.RenderSpec(**{**dspec.__dict__, "bundle": 4}),

@@ -41,7 +41,7 @@ def same(a, b):
     return all(np.array_equal(x, y) for x, y in zip(a, b))
 
 
-@pytest.mark.parametrize("bundle,n_sub", [(1, 8), (14, 8), (9, 3), (1, 1)])
+@pytest.mark.parametrize("bundle,n_sub", [(1, 8), (14, 8), (9, 3), (1, 1), (41, 8), (64, 5)])
 def test_graph_form_equals_host_driven_on_the_nave(sdd, bundle, n_sub):
     sc, cam, spec = S.nave_scene(seed=1)
     cam = S.CameraData(**{**cam.__dict__, "width": 64, "height": 40})
@@ -85,7 +85,7 @@ def test_graph_form_with_several_waves_and_profiling(sdd):
     sdd.sdd_set_profiling(h.h, 0)
 
 
-@pytest.mark.parametrize("bundle", [1, 8])
+@pytest.mark.parametrize("bundle", [1, 8, 41])
 def test_graph_form_with_network_tiles(sdd, bundle):
     """Heterogeneous tiles shaded by the network (weights as initialised: the comparison is
     of the two forms, not of the network's quality)."""
