@@ -1009,6 +1009,9 @@ sdd_status render_impl(sdd_scene* s, const sdd_camera* cam, const sdd_render_opt
   long long wmax = o->wave_paths > 0 ? o->wave_paths
                                      : (s->tuning.wave_paths > 0 ? s->tuning.wave_paths : (B > 1 ? 1LL << 25 : 1LL << 26));
   wmax = std::min<long long>(wmax, 1LL << 28);
+  // the network form queues one entry per member of every tile hit: 2 x wave x B of them
+  if (o->use_surrogate && B > 1 && o->wave_paths <= 0 && s->tuning.wave_paths <= 0)
+    wmax = std::min<long long>(wmax, 0x7FFFFFFFLL / (2LL * B));
   std::vector<WaveDesc> waves;
   if (n_cells <= wmax) {
     uint32_t ns_per = (uint32_t)std::max<long long>(1, wmax / n_cells);
