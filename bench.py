@@ -297,15 +297,16 @@ def run_e2e(args, sdd, h, cam, spec, flush, n_px, frame_paths, world, dist, kw):
             "ms_per_step": e2e_ms}
 
 
-def surrogate_record(bundle=41):
+def surrogate_record(bundle=14):
     """The surrogate half of the metric on the large batched frame (the ~1.07M-triangle nave,
     96 windows of 400 heterogeneous tiles, 81 wavelengths, depth 16): the BTDF network is
     trained on the GPU (tile-tracer data of the 512-tile set), then 64 seeded 8 x 8-pixel blocks
     of the 3840 x 2160 frame (4,096 pixels; paths are keyed per pixel, so they are the frame's
     own paths) are rendered at 4,096 spp by the plain form (host-driven, one wavelength per path,
     one brute-force ray through the tile at every tile hit) with two seeds, and by the network
-    form (graph form, fused tile shading) with spectral bundles of `bundle` and of 14 and without
-    bundles.  Image error =
+    form (graph form, fused tile shading) with and without spectral bundles of `bundle` (14: at a
+    heterogeneous tile every member leaves on its own ray, so wider bundles only add rays on this
+    tiled frame).  Image error =
     sum |a - b| / sum |b| of the wavelength-summed 8 x 8 block means against the mean of the two
     brute-force renders; noise floor = the same between the two brute-force renders.  With the
     sun off (sky light only) and with it on; throughput of each form from the same renders."""
@@ -359,7 +360,6 @@ def surrogate_record(bundle=41):
 
     sp = S.RenderSpec(**{**spec.__dict__, "spp": spp})
     sp_b = S.RenderSpec(**{**sp.__dict__, "bundle": bundle})
-    sp_14 = S.RenderSpec(**{**sp.__dict__, "bundle": 14})
     net_kw = {"use_surrogate": 1, "surrogate": net, "batched": 2}
     res = {}
     for sun in (0, 1):
@@ -370,21 +370,17 @@ def surrogate_record(bundle=41):
         a, v_plain = render(h, sp, batched=0)
         b, _ = render(h, S.RenderSpec(**{**sp.__dict__, "seed": sp.seed + 11}), batched=0)
         nnb, vb = render(h, sp_b, **net_kw)
-        nn14, v14 = render(h, sp_14, **net_kw)
         nn1, v1 = render(h, sp, **net_kw)
         h.close()
         ref = blocks(0.5 * (a + b))
         res["sun" if sun else "sky_only"] = {
             "noise_floor_block8": rel(blocks(a), blocks(b)),
             "image_error_block8_network_bundled": rel(blocks(nnb), ref),
-            "image_error_block8_network_bundled_14": rel(blocks(nn14), ref),
             "image_error_block8_network_unbundled": rel(blocks(nn1), ref),
             "mean_ratio_network_bundled": float(blocks(nnb).mean() / ref.mean()),
-            "mean_ratio_network_bundled_14": float(blocks(nn14).mean() / ref.mean()),
             "mean_ratio_network_unbundled": float(blocks(nn1).mean() / ref.mean()),
-            "value_plain": v_plain, "value_network_bundled": vb, "value_network_bundled_14": v14,
-            "value_network_unbundled": v1,
-            "speedup_bundled": vb / v_plain, "speedup_bundled_14": v14 / v_plain, "speedup_unbundled": v1 / v_plain}
+            "value_plain": v_plain, "value_network_bundled": vb, "value_network_unbundled": v1,
+            "speedup_bundled": vb / v_plain, "speedup_unbundled": v1 / v_plain}
     net.close()
     ts.close()
     return {"workload": f"large nave {scene.n_triangles} triangles, 96 windows x 400 heterogeneous tiles, 81 lambda, "
@@ -393,7 +389,7 @@ def surrogate_record(bundle=41):
             "forms": {"plain": "host-driven wavefront, one wavelength per path, one brute-force ray through the tile "
                                "at every tile hit",
                       "network": "graph form (fixed-grid kernels, conditional pass loops, one CUDA graph), fused "
-                                 f"tcgen05 tile shading; bundled = spectral bundles of {bundle} (bundled_14: of 14)"},
+                                 f"tcgen05 tile shading; bundled = spectral bundles of {bundle}"},
             "definition": "sum|a - b| / sum|b| over the wavelength-summed 8x8 block means; noise floor = the two plain "
                           "renders against each other",
             **res,
@@ -619,7 +615,7 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_surrogate:
         sclk = ClockSampler(local)
         sclk.start()
-        surrogate = surrogate_record(args.bundle if args.bundle > 1 else 41)
+        surrogate = surrogate_record()
         surrogate["clocks"] = sclk.stop()
 
     cpu = None
@@ -925,7 +921,7 @@ def main(argv=None):
     ap.add_argument("--no-graph", action="store_true",
                     help="forms 1 and 2: launch the frame's kernels directly instead of replaying a CUDA graph")
     ap.add_argument("--bundle", type=int, default=41,
-                    help="nave workload: wavelengths per spectral bundle (1 = every wavelength its own path)")
+                    help="wavelengths per spectral bundle (1 = every wavelength its own path; the large workload defaults to 14)")
     ap.add_argument("--workload", choices=["nave", "large", "network", "photons"], default="nave")
     ap.add_argument("--photons-per-lambda", type=int, default=1 << 20, help="photons workload: sun photons per wavelength")
     ap.add_argument("--net-rows", type=int, default=1 << 24, help="network workload: inference rows per step")
@@ -936,8 +932,11 @@ def main(argv=None):
                     help="large workload: time both forms and compare (default), or one form alone")
     ap.add_argument("--large-frame", default="", help="large workload: WxH instead of 3840x2160 (profiling)")
     args = ap.parse_args(argv)
-    if args.workload == "large" and "--spp" not in (argv if argv is not None else sys.argv):
+    given = argv if argv is not None else sys.argv
+    if args.workload == "large" and "--spp" not in given:
         args.spp = 4
+    if args.workload == "large" and "--bundle" not in given:
+        args.bundle = 14  # tiled windows: every member leaves a heterogeneous tile on its own ray
     args.warmup = max(args.warmup, 3)  # timing rule: at least three untimed warm-up frames
     if args.impl == "reference":
         return run_reference(args)
