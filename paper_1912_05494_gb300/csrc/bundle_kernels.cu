@@ -11,10 +11,11 @@ __global__ void __launch_bounds__(kBlock) k_raygen_bundle(RenderParams p, WaveDe
   dev_raygen_bundle(p, w, i, i < w.n_paths, rb, q, q_count, qcap, ctl);
 }
 
-// Five resident blocks per SM as in the graph form's bundle shading (a register cap that keeps
-// more warps in flight for the shading's memory latency); brute-force tiles keep their registers.
+// Resident blocks per SM as in the graph form's bundle shading (a register cap that keeps more
+// warps in flight for the shading's memory latency: 5, 6 with the network's tile queue);
+// brute-force tiles keep their registers.
 template <int kTM, bool kPM = false>
-__global__ void __launch_bounds__(kBlock, kTM == 1 ? 1 : 5) k_shade_bundle(RenderParams p, WaveDesc w, int n_rays, RayBuf cur,
+__global__ void __launch_bounds__(kBlock, kTM == 1 ? 1 : (kTM == 2 ? 6 : 5)) k_shade_bundle(RenderParams p, WaveDesc w, int n_rays, RayBuf cur,
                                                          const float2* __restrict__ hits, RayBuf next, uint32_t* q,
                                                          int* q_count, int qcap, ShadowBuf sb, uint32_t* sq,
                                                          int* sq_count, float* path_L, Control* ctl) {

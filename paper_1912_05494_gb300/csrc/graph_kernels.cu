@@ -95,13 +95,15 @@ __global__ void __launch_bounds__(kBlock) k_shade_g(RenderParams p, WaveDesc w, 
 }
 
 // The same for bundle rays.  Resident blocks per SM: a register cap that keeps more warps in
-// flight for the shading's memory latency (measured on the nave frame, shading per frame:
+// flight for the shading's memory latency.  Measured on the nave frame (shading per frame):
 // bundles of 14: no cap 63.2 ms, 4 blocks 52.6, 5 blocks 51.6, 6 blocks 49.5; bundles of 41,
 // whose 42 KB of member rows per block allow 5: 4 blocks 37.2, 5 blocks 37.0, 6 blocks (5
-// resident) 38.9); brute-force tiles keep their registers.
-constexpr int kShadeBlocks = 5;
+// resident) 38.9.  With the network's tile queue (the large frame, bundles of 14) 6 blocks:
+// 338 ms per frame against 457 ms with 5.  Brute-force tiles keep their registers.
+template <int kTM>
+constexpr int shade_blocks() { return kTM == 1 ? 1 : (kTM == 2 ? 6 : 5); }
 template <int kTM, bool kPM>
-__global__ void __launch_bounds__(kBlock, kTM == 1 ? 1 : kShadeBlocks)
+__global__ void __launch_bounds__(kBlock, shade_blocks<kTM>())
     k_shade_bundle_g(RenderParams p, WaveDesc w, const int* n_in, RayBuf cur, const float2* __restrict__ hits,
                      RayBuf next, int* next_count, uint32_t* q, int* q_count, int qcap, ShadowBuf sb, uint32_t* sq,
                      int* sq_count, float* path_L, Control* ctl) {
