@@ -711,15 +711,20 @@ def run_large(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, device="cuda", dtype=torch.float32)
     frame_paths = n_px * spec.spp * spec.n_lambda
     stream = torch.cuda.current_stream()
+    replays = [0]  # timed frames of the last timed() call that replayed a captured graph
 
     def timed(kw, steps, warmup, spec=spec):
         sdd.sdd_set_profiling(h.h, 1)  # before the warm-up: captured frames include the timing events
+        # warm-up frames as the timed ones, flush included: the first write of the flush buffer
+        # delayed the graph-form frame after it by ~0.25 s
         for _ in range(warmup):
+            flush.zero_()
             sdd.sdd_render(h.h, cam, spec, out, xyz, **kw)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         launches = 0
         ms_tile = 0.0
+        replays[0] = 0
         e0.record(stream)
         for _ in range(steps):
             flush.zero_()
@@ -727,6 +732,7 @@ def run_large(args):
             st = sdd.sdd_get_stats(h.h)
             launches += st["launches_total"] + 1
             ms_tile += st["ms_tile"]
+            replays[0] += st["graph_replays"]
         e1.record(stream)
         torch.cuda.synchronize()
         sdd.sdd_set_profiling(h.h, 0)
@@ -751,12 +757,17 @@ def run_large(args):
         print(json.dumps({"workload": "large", "form": args.forms, "frame": [cam.width, cam.height, spec.spp],
                           "subdomains": scene.n_subdomains, "batched": kw.get("batched"),
                           "ms_per_step": ms, "value": frame_paths / (ms / 1e3) / 1e6, "unit": UNIT,
-                          "gpu_launches": launches, "streaming": streaming}), flush=True)
+                          "gpu_launches": launches, "graph_replays": replays[0], "streaming": streaming,
+                          "last_frame": {k: v for k, v in sdd.sdd_get_stats(h.h).items()
+                                         if k.startswith("ms_") or k in ("waves", "wave_splits", "tile_shaded",
+                                                                         "rays_closest", "rays_shadow")}}),
+              flush=True)
         h.close()
         return 0
     clocks = ClockSampler(0)
     clocks.start()
     ms_net, launches_net, img_net, _ = timed(net_kw, args.steps, args.warmup, spec_net)
+    replays_net = replays[0]
     ms_net_host, launches_net_host, _, ms_tile = timed({**net_kw, "batched": 0}, args.steps, args.warmup, spec_net)
     ms_net1, _, img_net1, _ = timed(net_kw, args.steps, args.warmup)  # network + graph form, no bundles
     ms_net_p, launches_net_p, _, _ = timed({**net_kw, "batched": 1}, args.steps, args.warmup, spec_net)
@@ -780,7 +791,7 @@ def run_large(args):
             "comparison": {"plain": {"value": value_plain, "ms_per_step": ms_plain, "gpu_launches": launches_plain,
                                      "form": "host-driven wavefront, brute-force ray through the tile per tile hit"},
                            "network_batched": {"value": value_net, "ms_per_step": ms_net,
-                                               "gpu_launches": launches_net,
+                                               "gpu_launches": launches_net, "graph_replays": replays_net,
                                                "form": "graph form (fixed-grid kernels, conditional pass loops, one "
                                                        "CUDA graph per frame), fused tile shading, "
                                                        f"spectral bundles of {args.bundle}"},
