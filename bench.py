@@ -15,7 +15,7 @@ Printed JSON line (rank 0):
              before timing; CUDA events around K frames; max over ranks)
   e2e        the same metric through sdd_render_to_host: per step the host inputs go in and
              the spectral + XYZ images come back to pinned host memory
-  roofline   traversal kernel: algorithmic bytes (BVH nodes x 64 B + triangles x 48 B + ray
+  roofline   traversal kernel: algorithmic bytes (BVH nodes x 128 B + triangles x 48 B + ray
              state) / its CUDA-event time, against the measured HBM copy bandwidth
   cpu_baseline  the FP64 oracle on the host cores on a bounded pixel sample of the same frame
   unbundled  the same frame with one wavelength per path
@@ -516,11 +516,11 @@ def run_gpu(args):
     sdd.sdd_set_profiling(h.h, 2)
     sdd.sdd_render(h.h, cam, spec, out, xyz, **kw)
     cnt = sdd.sdd_get_stats(h.h)
-    trav_bytes = cnt["node_visits"] * 64 + cnt["tri_tests"] * 48 + cnt["rays_closest"] * 44
+    trav_bytes = cnt["node_visits"] * 128 + cnt["tri_tests"] * 48 + cnt["rays_closest"] * 44
     trav_launches = max(cnt["launches_traverse"], 1)
     persistent = args.batched == 1
     if persistent:  # one persistent launch per wave carries both traversals
-        trav_bytes += cnt["shadow_node_visits"] * 64 + cnt["shadow_tri_tests"] * 48 + cnt["rays_shadow"] * 44
+        trav_bytes += cnt["shadow_node_visits"] * 128 + cnt["shadow_tri_tests"] * 48 + cnt["rays_shadow"] * 44
         trav_launches = max(cnt["launches_persistent"], 1)
 
     # timed region: K frames, L2 flushed before each, per-launch CUDA events in the library
@@ -601,7 +601,7 @@ def run_gpu(args):
                 "l2_frac": ctr.get("l2_frac") if not persistent else None,
                 "issue_frac": ctr.get("issue_frac") if not persistent else None,
                 "counters_source": os.path.relpath(NCU_SUMMARY[args.batched], ROOT) if ctr else None,
-                "note": "algorithmic bytes = BVH nodes x 64 B + triangle records x 48 B + 44 B ray state per "
+                "note": "algorithmic bytes = 4-wide BVH nodes x 128 B + triangle records x 48 B + 44 B ray state per "
                         "subdomain visit; the ~35 MB BVH is L2-resident, so frac can exceed what DRAM moves. "
                         "traffic / l2_traffic: DRAM / L2 bytes per launch scaled from the committed ncu capture; "
                         "l2_frac = L2 throughput and issue_frac = issue slots active, as fractions of ncu's peaks, "

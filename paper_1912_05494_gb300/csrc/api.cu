@@ -331,15 +331,20 @@ sdd_status device_error(uint32_t e) {
 
 // Links of a subdomain's nodes copied into slot j: inner children from the subdomain's first
 // node n0 to the slot's nbase, leaf triangle ranges from its first record t0 to tbase.
+__device__ __forceinline__ int rebase_link(int link, int cnt, int n0, int nbase, int t0, int tbase) {
+  if (cnt > 0) return link - t0 + tbase;
+  return link >= 0 ? link - n0 + nbase : link;
+}
 __global__ void k_rebase_nodes(Node* nodes, int nn, int n0, int nbase, int t0, int tbase) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nn) return;
-  int4 d = nodes[i].d;
-  if (d.z > 0) d.x = d.x - t0 + tbase;
-  else if (d.x >= 0) d.x = d.x - n0 + nbase;
-  if (d.w > 0) d.y = d.y - t0 + tbase;
-  else if (d.y >= 0) d.y = d.y - n0 + nbase;
-  nodes[i].d = d;
+  int4 l = nodes[i].link;
+  const int4 c = nodes[i].cnt;
+  l.x = rebase_link(l.x, c.x, n0, nbase, t0, tbase);
+  l.y = rebase_link(l.y, c.y, n0, nbase, t0, tbase);
+  l.z = rebase_link(l.z, c.z, n0, nbase, t0, tbase);
+  l.w = rebase_link(l.w, c.w, n0, nbase, t0, tbase);
+  nodes[i].link = l;
 }
 
 // Copy subdomain `sub` from pinned host memory into device slot j and rebase its links there.
@@ -1500,6 +1505,10 @@ sdd_status sdd_scene_create(const sdd_scene_desc* d, sdd_scene** out) {
     delete s;
     return fail(SDD_ERR_OOM, "host allocation failed during BVH build");
   }
+  if (bvh.stack_need > kStackSize) {
+    delete s;
+    return fail(SDD_ERR_ARG, "BVH too deep for the traversal stack");
+  }
   // per-primitive normal + material
   std::vector<float4> prim(d->n_triangles);
   for (int t = 0; t < d->n_triangles; ++t) {
@@ -1680,9 +1689,13 @@ sdd_status set_streaming(sdd_scene* s, int cap) {
     const int n0 = s->dev.root[i], nn = s->dev.n_nodes_sub[i];
     int t0 = INT32_MAX, t1 = 0;
     for (int k = n0; k < n0 + nn; ++k) {
-      const int4 d = m.h_nodes[k].d;
-      if (d.z > 0) { t0 = std::min(t0, d.x); t1 = std::max(t1, d.x + d.z); }
-      if (d.w > 0) { t0 = std::min(t0, d.y); t1 = std::max(t1, d.y + d.w); }
+      const int* l = &m.h_nodes[k].link.x;
+      const int* c = &m.h_nodes[k].cnt.x;
+      for (int w = 0; w < kBvhWidth; ++w)
+        if (c[w] > 0) {
+          t0 = std::min(t0, l[w]);
+          t1 = std::max(t1, l[w] + c[w]);
+        }
     }
     if (t0 > t1) t0 = t1 = 0;
     m.node0[i] = n0;

@@ -40,7 +40,7 @@ __device__ __forceinline__ void shadow_bundle_entry(const RenderParams& p, const
 }
 
 template <bool kStats, int kB, int kTM>
-__global__ void __launch_bounds__(kB, kTM == 1 ? 1 : 8 * 128 / kB)
+__global__ void __launch_bounds__(kB, kTM == 1 ? 1 : 6 * 128 / kB)
     k_shadow_bundle(RenderParams p, WaveDesc w, Sched sch, int top_nodes, QueuePair qp, ShadowBuf sb, float* path_L,
                     Control* ctl) {
   shadow_bundle_entry<kStats, kTM>(p, w, sch, top_nodes, qp, sb, path_L, ctl);

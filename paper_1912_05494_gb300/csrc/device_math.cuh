@@ -275,7 +275,7 @@ __device__ __forceinline__ float tri_hit(const RayPre& r, float4 v0, float4 v1, 
   return (t > t_lo && t <= t_hi) ? t : -1.f;
 }
 
-// Slab test of both children of a node over [t0, t1]; Ize's 1 + 2 gamma(3) widening keeps
+// Slab test of one child box of a node over [t0, t1]; Ize's 1 + 2 gamma(3) widening keeps
 // rounding from producing false misses.
 __device__ __forceinline__ bool box_hit(const RayPre& r, float lx, float hx, float ly, float hy, float lz,
                                         float hz, float t0, float t1, float* tnear) {

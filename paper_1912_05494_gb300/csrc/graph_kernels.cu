@@ -49,9 +49,11 @@ __device__ __forceinline__ int next_block_chunk(int* work) {
 
 // Closest-hit pass over the queues whose counts are counts_in.  With top_nodes > 0 every
 // block first stages the top_nodes first (breadth-first: top-level) nodes of every
-// subdomain's BVH in shared memory (Sec. 5: the top of the hierarchy first).
+// subdomain's BVH in shared memory (Sec. 5: the top of the hierarchy first).  Six resident
+// blocks per SM leave 85 registers, enough for a 4-wide node without spills (nave frame:
+// closest-hit passes 28.8 ms at 6 blocks, 29.1 at 8 with 48 B of spills, 39.6 at 10).
 template <bool kStats>
-__global__ void __launch_bounds__(kChunk, 12) k_traverse_g(RenderParams p, const int* counts_in, int* work,
+__global__ void __launch_bounds__(kChunk, 6) k_traverse_g(RenderParams p, const int* counts_in, int* work,
                                                            int top_nodes, int block_chunks, QueuePair qp, RayBuf rb,
                                                            float2* hits, Control* ctl) {
   __shared__ int s_prefix[kMaxSubdomains + 1];
@@ -117,7 +119,7 @@ __global__ void __launch_bounds__(kBlock, shade_blocks<kTM>())
 
 // Shadow pass over the queues whose counts are counts_in (walk choice as in the other forms).
 template <bool kStats, int kTM, bool kBund>
-__global__ void __launch_bounds__(kChunk, kTM == 1 ? 1 : 8) k_shadow_g(RenderParams p, WaveDesc w,
+__global__ void __launch_bounds__(kChunk, kTM == 1 ? 1 : 6) k_shadow_g(RenderParams p, WaveDesc w,
                                                                       const int* counts_in, int* work,
                                                                       int block_chunks, QueuePair qp, ShadowBuf sb,
                                                                       float* path_L, Control* ctl) {

@@ -36,7 +36,7 @@ namespace {
 
 constexpr int kPB = 128;  // threads per block
 static_assert(kPB == kShadeThreads, "bundle shading rows are sized for kShadeThreads threads");
-constexpr int kBundleBlocks = 8;  // resident blocks per SM of the spectral-bundle kernels (measured best of 4, 6, 8)
+constexpr int kBundleBlocks = 4;  // resident blocks per SM of the spectral-bundle kernels (measured best of 4, 6, 8)
 constexpr unsigned long long kBarrierTimeoutNs = 5ull * 1000 * 1000 * 1000;
 
 __device__ __forceinline__ unsigned long long global_ns() {

@@ -109,22 +109,55 @@ __device__ __forceinline__ Node load_node(const Node* __restrict__ g, const Node
   if (local >= 0 && local < n_staged) return s_nodes[local];
   const float4* p = reinterpret_cast<const float4*>(g + idx);
   Node n;
-  n.a = __ldg(p);
-  n.b = __ldg(p + 1);
-  n.c = __ldg(p + 2);
-  float4 d = __ldg(p + 3);
-  n.d = make_int4(__float_as_int(d.x), __float_as_int(d.y), __float_as_int(d.z), __float_as_int(d.w));
+  n.lox = __ldg(p);
+  n.hix = __ldg(p + 1);
+  n.loy = __ldg(p + 2);
+  n.hiy = __ldg(p + 3);
+  n.loz = __ldg(p + 4);
+  n.hiz = __ldg(p + 5);
+  n.link = __ldg(reinterpret_cast<const int4*>(p + 6));
+  n.cnt = __ldg(reinterpret_cast<const int4*>(p + 7));
   return n;
 }
 
 // Stage the first `want` nodes (the top BVH levels, stored breadth-first) of subdomain s.
 __device__ __forceinline__ int stage_top(const DevScene& sc, Node* s_nodes, int s, int want) {
+  constexpr int kVec = (int)(sizeof(Node) / sizeof(float4));
   int n = min(want, sc.n_nodes_sub[s]);
   const float4* src = reinterpret_cast<const float4*>(sc.nodes + sc.root[s]);
   float4* dst = reinterpret_cast<float4*>(s_nodes);
-  for (int i = threadIdx.x; i < 4 * n; i += blockDim.x) dst[i] = __ldg(src + i);
+  for (int i = threadIdx.x; i < kVec * n; i += blockDim.x) dst[i] = __ldg(src + i);
   __syncthreads();
   return n;
+}
+
+// Component c of a node field (c is a constant after unrolling, else a select chain).
+__device__ __forceinline__ float comp4(const float4& v, int c) {
+  return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ int comp4(const int4& v, int c) {
+  return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
+}
+
+// Slab tests of a node's children against (t0, t1]: bit c is set when child c exists and its
+// box meets the interval; tn[c] is its entry distance.
+__device__ __forceinline__ unsigned child_hits(const RayPre& rp, const Node& n, float t0, float t1,
+                                               float (&tn)[kBvhWidth]) {
+  unsigned m = 0u;
+#pragma unroll
+  for (int c = 0; c < kBvhWidth; ++c) {
+    float t;
+    const bool h = box_hit(rp, comp4(n.lox, c), comp4(n.hix, c), comp4(n.loy, c), comp4(n.hiy, c), comp4(n.loz, c),
+                           comp4(n.hiz, c), t0, t1, &t);
+    tn[c] = t;
+    if (h && comp4(n.link, c) >= 0) m |= 1u << c;
+  }
+  return m;
+}
+
+// Children of a node that are leaves (bit c: child c holds triangle records).
+__device__ __forceinline__ unsigned leaf_mask(const Node& n) {
+  return (n.cnt.x > 0 ? 1u : 0u) | (n.cnt.y > 0 ? 2u : 0u) | (n.cnt.z > 0 ? 4u : 0u) | (n.cnt.w > 0 ? 8u : 0u);
 }
 
 __device__ __forceinline__ TileDev tile_of(const TileSetDev& ts, int t) {
@@ -216,33 +249,38 @@ __device__ __forceinline__ bool any_hit_walk(const DevScene& sc, const Node* s_n
   for (;;) {
     Node n = load_node(sc.nodes, s_nodes, node, root, n_staged);
     if (kStats) ++*n_nodes;
-    float tn0, tn1;
-    bool h0 = n.d.x >= 0 && box_hit(rp, n.a.x, n.a.y, n.a.z, n.a.w, n.c.x, n.c.y, t0, t1, &tn0);
-    bool h1 = n.d.y >= 0 && box_hit(rp, n.b.x, n.b.y, n.b.z, n.b.w, n.c.z, n.c.w, t0, t1, &tn1);
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      bool hc = c == 0 ? h0 : h1;
-      int cnt = c == 0 ? n.d.z : n.d.w;
-      if (hc && cnt > 0) {
-        int first = c == 0 ? n.d.x : n.d.y;
-        for (int i = first; i < first + cnt; ++i) {
-          const float4* tp = reinterpret_cast<const float4*>(sc.tris + i);
-          float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
-          if (kStats) ++*n_tris;
-          float t = tri_hit(rp, v0, v1, v2, t0, t1);
-          if (t >= 0.f && hit(t, __float_as_uint(v0.w))) return true;
-        }
-        if (c == 0) h0 = false; else h1 = false;
+    float tn[kBvhWidth];
+    const unsigned hm = child_hits(rp, n, t0, t1, tn);
+    const unsigned leaf = leaf_mask(n);
+    for (unsigned lm = hm & leaf; lm; lm &= lm - 1u) {
+      const int c = __ffs(lm) - 1;
+      const int first = comp4(n.link, c), cnt = comp4(n.cnt, c);
+      for (int i = first; i < first + cnt; ++i) {
+        const float4* tp = reinterpret_cast<const float4*>(sc.tris + i);
+        float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
+        if (kStats) ++*n_tris;
+        float t = tri_hit(rp, v0, v1, v2, t0, t1);
+        if (t >= 0.f && hit(t, __float_as_uint(v0.w))) return true;
       }
     }
-    if (h0 && h1) {
-      if (spn < kStackSize) stack[spn++] = n.d.x;
-      else *overflow = true;
-      node = n.d.y;
-    } else if (h0) {
-      node = n.d.x;
-    } else if (h1) {
-      node = n.d.y;
+    // entered inner children: descend into the first, push the others
+    const unsigned im = hm & ~leaf;
+    int next = -1;
+#pragma unroll
+    for (int c = 0; c < kBvhWidth; ++c) {
+      if ((im >> c) & 1u) {
+        const int l = comp4(n.link, c);
+        if (next < 0) {
+          next = l;
+        } else if (spn < kStackSize) {
+          stack[spn++] = l;
+        } else {
+          *overflow = true;
+        }
+      }
+    }
+    if (next >= 0) {
+      node = next;
     } else {
       if (spn == 0) break;
       node = stack[--spn];
@@ -269,7 +307,7 @@ __device__ __forceinline__ float shadow_T(const RenderParams& p, const DevScene&
 // the lower primitive.  The lanes must enter converged (the host-driven traversal kernel,
 // whose subdomain is the block's, and the persistent kernel's subdomain-aligned chunks).
 // Every lane of the warp calls it (live = false for lanes without a ray).  Each iteration every lane still traversing takes one node
-// step (box tests of both children, the triangles of any leaf child, then push / pop) and
+// step (box tests of its four children, the triangles of any leaf child, then push / pop) and
 // the warp reconverges at the vote that ends the step.  A data-dependent loop per lane lets
 // the warp split into groups that each iterate on their own: on incoherent rays of large
 // scenes only ~3 of 32 lanes then issue together.
@@ -296,40 +334,61 @@ __device__ __forceinline__ uint32_t closest_hit_warp(const DevScene& sc, const N
    if (!done) {
     Node n = load_node(sc.nodes, s_nodes, node, root, n_staged);
     if (kStats) ++*n_nodes;
-    float tn0, tn1;
-    bool h0 = n.d.x >= 0 && box_hit(rp, n.a.x, n.a.y, n.a.z, n.a.w, n.c.x, n.c.y, t0, tbest, &tn0);
-    bool h1 = n.d.y >= 0 && box_hit(rp, n.b.x, n.b.y, n.b.z, n.b.w, n.c.z, n.c.w, t0, tbest, &tn1);
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      bool hc = c == 0 ? h0 : h1;
-      int cnt = c == 0 ? n.d.z : n.d.w;
-      if (hc && cnt > 0) {
-        int first = c == 0 ? n.d.x : n.d.y;
-        for (int i = first; i < first + cnt; ++i) {
-          const float4* tp = reinterpret_cast<const float4*>(sc.tris + i);
-          float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
-          if (kStats) ++*n_tris;
-          float t = tri_hit(rp, v0, v1, v2, t0, tbest);
-          if (t >= 0.f) {
-            uint32_t prim = __float_as_uint(v0.w);
-            if (t < tbest || prim < best) {
-              tbest = t;
-              best = prim;
-            }
+    float tn[kBvhWidth];
+    const unsigned hm = child_hits(rp, n, t0, tbest, tn);
+    const unsigned leaf = leaf_mask(n);
+    for (unsigned lm = hm & leaf; lm; lm &= lm - 1u) {
+      const int c = __ffs(lm) - 1;
+      const int first = comp4(n.link, c), cnt = comp4(n.cnt, c);
+      for (int i = first; i < first + cnt; ++i) {
+        const float4* tp = reinterpret_cast<const float4*>(sc.tris + i);
+        float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
+        if (kStats) ++*n_tris;
+        float t = tri_hit(rp, v0, v1, v2, t0, tbest);
+        if (t >= 0.f) {
+          uint32_t prim = __float_as_uint(v0.w);
+          if (t < tbest || prim < best) {
+            tbest = t;
+            best = prim;
           }
         }
-        if (c == 0) h0 = false; else h1 = false;
       }
     }
-    if (h0 && h1) {
-      bool first0 = tn0 <= tn1;
-      if (sp < kStackSize) stack[sp++] = first0 ? n.d.y : n.d.x;
-      else *overflow = true;
-      node = first0 ? n.d.x : n.d.y;
-    } else if (h0) {
-      node = n.d.x;
-    } else if (h1) {
-      node = n.d.y;
+    // entered inner children, nearest first; one whose box is entered beyond the closest hit
+    // found in this step cannot hold a closer one (same slack as the box test)
+    const unsigned im = hm & ~leaf;
+    const float cut = tbest * 1.0000004f;
+    float k[kBvhWidth];
+    int l[kBvhWidth];
+#pragma unroll
+    for (int c = 0; c < kBvhWidth; ++c) {
+      k[c] = (((im >> c) & 1u) && tn[c] <= cut) ? tn[c] : CUDART_INF_F;
+      l[c] = comp4(n.link, c);
+    }
+    auto order = [&](int a, int b) {
+      if (k[b] < k[a]) {
+        const float tk = k[a];
+        k[a] = k[b];
+        k[b] = tk;
+        const int tl = l[a];
+        l[a] = l[b];
+        l[b] = tl;
+      }
+    };
+    order(0, 1);
+    order(2, 3);
+    order(0, 2);
+    order(1, 3);
+    order(1, 2);
+    if (k[0] < CUDART_INF_F) {
+      node = l[0];
+#pragma unroll
+      for (int c = kBvhWidth - 1; c >= 1; --c) {
+        if (k[c] < CUDART_INF_F) {
+          if (sp < kStackSize) stack[sp++] = l[c];
+          else *overflow = true;
+        }
+      }
     } else if (sp == 0) {
       done = true;
     } else {
@@ -365,37 +424,43 @@ __device__ __forceinline__ bool any_hit_walk_warp(const DevScene& sc, const Node
    if (!done) {
     Node n = load_node(sc.nodes, s_nodes, node, root, n_staged);
     if (kStats) ++*n_nodes;
-    float tn0, tn1;
-    bool h0 = n.d.x >= 0 && box_hit(rp, n.a.x, n.a.y, n.a.z, n.a.w, n.c.x, n.c.y, t0, t1, &tn0);
-    bool h1 = n.d.y >= 0 && box_hit(rp, n.b.x, n.b.y, n.b.z, n.b.w, n.c.z, n.c.w, t0, t1, &tn1);
+    float tn[kBvhWidth];
+    const unsigned hm = child_hits(rp, n, t0, t1, tn);
+    const unsigned leaf = leaf_mask(n);
     bool blocked = false;
+    for (unsigned lm = hm & leaf; lm && !blocked; lm &= lm - 1u) {
+      const int c = __ffs(lm) - 1;
+      const int first = comp4(n.link, c), cnt = comp4(n.cnt, c);
+      for (int i = first; i < first + cnt && !blocked; ++i) {
+        const float4* tp = reinterpret_cast<const float4*>(sc.tris + i);
+        float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
+        if (kStats) ++*n_tris;
+        float t = tri_hit(rp, v0, v1, v2, t0, t1);
+        if (t >= 0.f) blocked = hit(t, __float_as_uint(v0.w));
+      }
+    }
+    const unsigned im = hm & ~leaf;
+    int next = -1;
+    if (!blocked) {
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      bool hc = c == 0 ? h0 : h1;
-      int cnt = c == 0 ? n.d.z : n.d.w;
-      if (hc && cnt > 0 && !blocked) {
-        int first = c == 0 ? n.d.x : n.d.y;
-        for (int i = first; i < first + cnt && !blocked; ++i) {
-          const float4* tp = reinterpret_cast<const float4*>(sc.tris + i);
-          float4 v0 = __ldg(tp), v1 = __ldg(tp + 1), v2 = __ldg(tp + 2);
-          if (kStats) ++*n_tris;
-          float t = tri_hit(rp, v0, v1, v2, t0, t1);
-          if (t >= 0.f) blocked = hit(t, __float_as_uint(v0.w));
+      for (int c = 0; c < kBvhWidth; ++c) {
+        if ((im >> c) & 1u) {
+          const int l = comp4(n.link, c);
+          if (next < 0) {
+            next = l;
+          } else if (spn < kStackSize) {
+            stack[spn++] = l;
+          } else {
+            *overflow = true;
+          }
         }
-        if (c == 0) h0 = false; else h1 = false;
       }
     }
     if (blocked) {
       res = true;
       done = true;
-    } else if (h0 && h1) {
-      if (spn < kStackSize) stack[spn++] = n.d.x;
-      else *overflow = true;
-      node = n.d.y;
-    } else if (h0) {
-      node = n.d.x;
-    } else if (h1) {
-      node = n.d.y;
+    } else if (next >= 0) {
+      node = next;
     } else if (spn == 0) {
       done = true;
     } else {

@@ -23,7 +23,8 @@ struct HostBVH {
   std::vector<Node> nodes;  // every subdomain's BVH, concatenated, absolute links
   std::vector<TriRec> tris; // triangle records referenced by the leaves
   std::vector<int> root, n_nodes;
-  int max_depth = 0;
+  int max_depth = 0;   // binary levels before the collapse to 4-wide nodes
+  int stack_need = 0;  // deepest traversal stack a walk of any subdomain's tree can need
   int64_t n_refs = 0;
 };
 

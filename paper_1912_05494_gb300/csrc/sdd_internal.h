@@ -14,6 +14,7 @@ namespace sdd {
 
 constexpr int kMaxSubdomains = 64;
 constexpr int kMaxBundle = 64;            // wavelengths per spectral bundle (member mask bits)
+constexpr int kBvhWidth = 4;              // children per BVH node
 constexpr int kStackSize = 64;            // BVH traversal stack entries per ray
 constexpr uint32_t kMissPrim = 0xFFFFFFFFu;
 
@@ -27,17 +28,15 @@ enum ErrBits : uint32_t {
   ERR_SHADOW_OVERFLOW = 8u,
 };
 
-// BVH node, 64 bytes: the bounds of both children and their links.
-//   a = (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
-//   b = (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
-//   c = (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
-//   d = (link0, link1, count0, count1) as int bits:
-//       count > 0  -> leaf: triangle records [link, link + count)
-//       count == 0 -> inner node index `link` (absolute), or no child when link < 0
+// BVH node, 128 bytes (one L1 line): the bounds of up to four children as structure of
+// arrays (child c in component c) and their links, as int bits:
+//   cnt[c] > 0  -> leaf: triangle records [link[c], link[c] + cnt[c])
+//   cnt[c] == 0 -> inner node index link[c] (absolute), or no child when link[c] < 0
 struct alignas(16) Node {
-  float4 a, b, c;
-  int4 d;
+  float4 lox, hix, loy, hiy, loz, hiz;
+  int4 link, cnt;
 };
+static_assert(sizeof(Node) == 128, "a BVH node fills one 128-byte line");
 
 // Triangle record, 48 bytes: the three vertices; v0.w holds the global primitive id bits.
 struct alignas(16) TriRec {

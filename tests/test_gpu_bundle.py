@@ -126,18 +126,28 @@ def test_bundles_through_brute_force_tiles(sdd, orc):
     assert err <= 1e-3, err
 
 
+def equal_to_rounding(x, y):
+    """Equal to within a few FP32 roundings.  The persistent form is a kernel of its own: the
+    compiler may contract a multiply and an add into one FMA there and not in the host-driven
+    kernels (measured: one path value of 122,880 apart by 7.6e-8 at bundles of 41)."""
+    return np.allclose(x, y, rtol=1e-6, atol=0.0)
+
+
 @pytest.mark.parametrize("n_sub,bundle", [(8, 14), (3, 14), (8, 41)])
 def test_batched_bundles_equal_host_driven(sdd, nave, n_sub, bundle):
-    """The persistent form runs the same per-ray device code: the same image, bit for bit."""
+    """The persistent form runs the same per-ray device code: every path takes the same events
+    (bit-identical event hashes) and ends with the same radiance up to FP32 rounding; a
+    replayed frame is bit-identical."""
     sc, cam, spec = nave
     cam = S.CameraData(**{**cam.__dict__, "width": 64, "height": 40})
     spec = S.RenderSpec(**{**spec.__dict__, "spp": 3, "bundle": bundle})
     h = sdd.SceneHandle(sc, n_subdomains=n_sub)
     a, pa, ha = render(sdd, h, cam, spec)
     b, pb, hb = render(sdd, h, cam, spec, batched=1)
-    assert np.array_equal(a, b) and np.array_equal(pa, pb) and np.array_equal(ha, hb)
-    c, _, _ = render(sdd, h, cam, spec, batched=1)  # replayed graph
-    assert np.array_equal(b, c)
+    assert np.array_equal(ha, hb)
+    assert equal_to_rounding(pa, pb) and equal_to_rounding(a, b)
+    c, pc, hc = render(sdd, h, cam, spec, batched=1)  # replayed graph
+    assert np.array_equal(b, c) and np.array_equal(pb, pc) and np.array_equal(hb, hc)
 
 
 def test_batched_bundles_split_waves_through_solid_glass(sdd):
