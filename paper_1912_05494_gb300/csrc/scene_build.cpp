@@ -67,8 +67,10 @@ struct TmpNode {
 constexpr int kBins = 16;
 // Ranges of at most kLeafMax references become leaves (up to 2 kLeafMax when no split is
 // cheaper).  A triangle test costs the walk about as much as a node step, so small leaves win:
-// on the nave bench frame, closest-hit passes 109.6 ms and shadow passes 53.8 ms with 2,
-// against 124.2 / 60.7 ms with 4, 160.2 / 73.7 ms with 8 and 112.8 / 53.8 ms with 1.
+// on the nave bench frame (binary tree, bundles of 14), closest-hit passes 109.6 ms and shadow
+// passes 53.8 ms with 2, against 124.2 / 60.7 ms with 4, 160.2 / 73.7 ms with 8 and 112.8 /
+// 53.8 ms with 1; on the 4-wide tree (bundles of 41) the frame takes 96.1 ms with 2 or 3,
+// 98.9 with 1 and 102.0 with 4.
 constexpr int kLeafMax = 2;
 constexpr int kDepthLimit = 60;  // binary levels; the 4-wide walk pushes at most 3 per node
 
