@@ -130,17 +130,60 @@ constexpr float kGrazingCos = 0.0625f;  // below this cosine the slab series run
 // with tau = exp(-4 pi k d / (lambda cos theta_t)).  pol = 0: one series on the unpolarised
 // interface reflectance (R_s + R_p) / 2; pol = 1: s and p light do not mix at the parallel
 // faces, so the series runs on R_s and on R_p and the two results are averaged.
-__device__ __forceinline__ void slab_series(float R, float tau, float* Rs_out, float* Ts_out) {
-  float omr = 1.f - R, rt = R * tau;
-  float den = (1.f - rt) * (1.f + rt);
-  *Rs_out = R + omr * omr * R * tau * tau / den;
-  *Ts_out = omr * omr * tau / den;
-}
 __device__ __forceinline__ void slab_series_f64(double R, double tau, double* Rs_out, double* Ts_out) {
   double den = (1.0 - R * tau) * (1.0 + R * tau);
   *Rs_out = R + (1.0 - R) * (1.0 - R) * R * tau * tau / den;
   *Ts_out = (1.0 - R) * (1.0 - R) * tau / den;
 }
+// The FP32 branch, with air outside the slab (n1 = 1): eta = 1 / (n + ik) by one reciprocal of
+// n^2 + k^2, the complex square root without the overflow guard of hypotf (|z| is of order
+// one here), and its divisions and exponential through __fdividef and __expf (within a few
+// ulp for these well-scaled operands; IEEE division took most of the slab's shading cost).
+// Every product and sum is an explicitly rounded intrinsic, so the compiler cannot contract
+// them differently in the kernels that inline this (the forms' per-path results stay
+// bit-identical).
+__device__ __forceinline__ void slab_RT_f32(float cos_i, float n, float k, float d, float lambda_nm,
+                                            float* Rs_out, float* Ts_out, int pol) {
+  const float sin2 = fmaxf(0.f, __fmaf_rn(-cos_i, cos_i, 1.f));
+  const float inv_nk = __fdividef(1.f, __fmaf_rn(n, n, __fmul_rn(k, k)));
+  const float er = __fmul_rn(n, inv_nk), ei = -__fmul_rn(k, inv_nk);  // eta = 1 / n2
+  const float e2r = __fmaf_rn(er, er, -__fmul_rn(ei, ei)), e2i = __fmul_rn(__fmul_rn(2.f, er), ei);
+  const float zr = __fmaf_rn(-e2r, sin2, 1.f), zi = -__fmul_rn(e2i, sin2);  // cos_t^2 = 1 - eta^2 sin^2
+  const float rz = sqrtf(__fmaf_rn(zr, zr, __fmul_rn(zi, zi)));
+  float ctr, cti;
+  if (zr >= 0.f) {
+    ctr = sqrtf(__fmul_rn(0.5f, __fadd_rn(rz, zr)));
+    cti = ctr > 0.f ? __fdividef(zi, __fmul_rn(2.f, ctr)) : 0.f;
+  } else {
+    cti = copysignf(sqrtf(__fmul_rn(0.5f, __fsub_rn(rz, zr))), zi);
+    ctr = __fdividef(fabsf(zi), __fmul_rn(2.f, fabsf(cti)));
+  }
+  const float ar = __fmaf_rn(n, ctr, -__fmul_rn(k, cti)), ai = __fmaf_rn(n, cti, __fmul_rn(k, ctr));  // n2 cos_t
+  auto ratio = [](float xr, float xi, float yr, float yi) {  // |x - y|^2 / |x + y|^2
+    const float mr = __fsub_rn(xr, yr), mi = __fsub_rn(xi, yi), pr = __fadd_rn(xr, yr), pi = __fadd_rn(xi, yi);
+    return __fdividef(__fmaf_rn(mr, mr, __fmul_rn(mi, mi)), __fmaf_rn(pr, pr, __fmul_rn(pi, pi)));
+  };
+  const float Rsi = ratio(cos_i, 0.f, ar, ai);
+  const float Rpi = ratio(__fmul_rn(n, cos_i), __fmul_rn(k, cos_i), ctr, cti);  // n2 cos_i against cos_t
+  const float cos_t = sqrtf(__fsub_rn(1.f, __fdividef(sin2, __fmul_rn(n, n))));
+  const float tau = __expf(-__fdividef(__fmul_rn(__fmul_rn(kFourPi, k), d), __fmul_rn(__fmul_rn(lambda_nm, 1e-9f), cos_t)));
+  auto series = [tau](float R, float* Rsl, float* Tsl) {
+    const float omr = __fsub_rn(1.f, R), rt = __fmul_rn(R, tau);
+    const float g = __fdividef(__fmul_rn(__fmul_rn(omr, omr), tau), __fmul_rn(__fsub_rn(1.f, rt), __fadd_rn(1.f, rt)));
+    *Rsl = __fmaf_rn(g, rt, R);
+    *Tsl = g;
+  };
+  if (pol == 0) {
+    series(__fmul_rn(0.5f, __fadd_rn(Rsi, Rpi)), Rs_out, Ts_out);
+    return;
+  }
+  float R1, T1, R2, T2;
+  series(Rsi, &R1, &T1);
+  series(Rpi, &R2, &T2);
+  *Rs_out = __fmul_rn(0.5f, __fadd_rn(R1, R2));
+  *Ts_out = __fmul_rn(0.5f, __fadd_rn(T1, T2));
+}
+
 __device__ __forceinline__ void slab_RT(float cos_i, float n, float k, float d, float lambda_nm,
                                         float* Rs_out, float* Ts_out, int pol = 0) {
   if (cos_i < kGrazingCos) {
@@ -163,19 +206,7 @@ __device__ __forceinline__ void slab_RT(float cos_i, float n, float k, float d, 
     *Ts_out = (float)Tsl;
     return;
   }
-  const float2 rsp = fresnel_RsRp(cos_i, 1.f, n, k);
-  float sin2t = (1.f - cos_i * cos_i) / (n * n);
-  float cos_t = sqrtf(1.f - sin2t);
-  float tau = expf(-kFourPi * k * d / (lambda_nm * 1e-9f * cos_t));
-  if (pol == 0) {
-    slab_series(0.5f * (rsp.x + rsp.y), tau, Rs_out, Ts_out);
-    return;
-  }
-  float R1, T1, R2, T2;
-  slab_series(rsp.x, tau, &R1, &T1);
-  slab_series(rsp.y, tau, &R2, &T2);
-  *Rs_out = 0.5f * (R1 + R2);
-  *Ts_out = 0.5f * (T1 + T2);
+  slab_RT_f32(cos_i, n, k, d, lambda_nm, Rs_out, Ts_out, pol);
 }
 
 // Beer-Lambert transmittance over `len` metres.
