@@ -306,17 +306,4 @@ __device__ __forceinline__ float tri_hit(const RayPre& r, float4 v0, float4 v1, 
   return (t > t_lo && t <= t_hi) ? t : -1.f;
 }
 
-// Slab test of one child box of a node over [t0, t1]; Ize's 1 + 2 gamma(3) widening keeps
-// rounding from producing false misses.
-__device__ __forceinline__ bool box_hit(const RayPre& r, float lx, float hx, float ly, float hy, float lz,
-                                        float hz, float t0, float t1, float* tnear) {
-  float tx0 = fmaf(lx, r.inv.x, -r.oinv.x), tx1 = fmaf(hx, r.inv.x, -r.oinv.x);
-  float ty0 = fmaf(ly, r.inv.y, -r.oinv.y), ty1 = fmaf(hy, r.inv.y, -r.oinv.y);
-  float tz0 = fmaf(lz, r.inv.z, -r.oinv.z), tz1 = fmaf(hz, r.inv.z, -r.oinv.z);
-  float tmin = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), t0));
-  float tmax = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), t1));
-  *tnear = tmin;
-  return tmin <= tmax * 1.0000004f;
-}
-
 }  // namespace sdd

@@ -49,11 +49,12 @@ __device__ __forceinline__ int next_block_chunk(int* work) {
 
 // Closest-hit pass over the queues whose counts are counts_in.  With top_nodes > 0 every
 // block first stages the top_nodes first (breadth-first: top-level) nodes of every
-// subdomain's BVH in shared memory (Sec. 5: the top of the hierarchy first).  Six resident
-// blocks per SM leave 85 registers, enough for a 4-wide node without spills (nave frame:
-// closest-hit passes 28.8 ms at 6 blocks, 29.1 at 8 with 48 B of spills, 39.6 at 10).
+// subdomain's BVH in shared memory (Sec. 5: the top of the hierarchy first).  Seven resident
+// blocks per SM (73 registers) hold a 4-wide node as the ray's octant sees it (nave frame:
+// closest-hit passes 28.0 ms at 7 blocks, 29.5 at 6; before the octant view, 28.8 at 6, 29.1
+// at 8 with 48 B of spills and 39.6 at 10).
 template <bool kStats>
-__global__ void __launch_bounds__(kChunk, 6) k_traverse_g(RenderParams p, const int* counts_in, int* work,
+__global__ void __launch_bounds__(kChunk, 7) k_traverse_g(RenderParams p, const int* counts_in, int* work,
                                                            int top_nodes, int block_chunks, QueuePair qp, RayBuf rb,
                                                            float2* hits, Control* ctl) {
   __shared__ int s_prefix[kMaxSubdomains + 1];

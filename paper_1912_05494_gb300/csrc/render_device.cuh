@@ -103,21 +103,49 @@ __device__ __forceinline__ void slab_interval(const DevScene& sc, int s, float3 
   }
 }
 
-__device__ __forceinline__ Node load_node(const Node* __restrict__ g, const Node* s_nodes, int idx, int root,
-                                          int n_staged) {
-  int local = idx - root;
-  if (local >= 0 && local < n_staged) return s_nodes[local];
+// A node as one ray sees it: per axis the child planes the ray enters through (near) and
+// leaves through (far), picked once per walk from the signs of its direction, so that a slab
+// test takes no min / max per axis (the values equal the min / max of the two plane
+// distances: t(plane) is monotonic in the plane, increasing for a positive component).
+struct NodeView {
+  float4 nx, fx, ny, fy, nz, fz;
+  int4 link, cnt;
+};
+// Node fields of the near planes for the ray's octant: 1 where the direction component is
+// negative (the near plane is then the upper bound).
+struct Octant {
+  int ox, oy, oz;
+};
+__device__ __forceinline__ Octant octant_of(const RayPre& rp) {
+  return Octant{rp.inv.x < 0.f ? 1 : 0, rp.inv.y < 0.f ? 1 : 0, rp.inv.z < 0.f ? 1 : 0};
+}
+
+__device__ __forceinline__ NodeView load_view(const Node* __restrict__ g, const Node* s_nodes, int idx, int root,
+                                              int n_staged, const Octant& o) {
+  const int local = idx - root;
+  NodeView v;
+  if (local >= 0 && local < n_staged) {
+    const float4* p = reinterpret_cast<const float4*>(s_nodes + local);
+    v.nx = p[o.ox];
+    v.fx = p[1 - o.ox];
+    v.ny = p[2 + o.oy];
+    v.fy = p[3 - o.oy];
+    v.nz = p[4 + o.oz];
+    v.fz = p[5 - o.oz];
+    v.link = reinterpret_cast<const int4*>(p)[6];
+    v.cnt = reinterpret_cast<const int4*>(p)[7];
+    return v;
+  }
   const float4* p = reinterpret_cast<const float4*>(g + idx);
-  Node n;
-  n.lox = __ldg(p);
-  n.hix = __ldg(p + 1);
-  n.loy = __ldg(p + 2);
-  n.hiy = __ldg(p + 3);
-  n.loz = __ldg(p + 4);
-  n.hiz = __ldg(p + 5);
-  n.link = __ldg(reinterpret_cast<const int4*>(p + 6));
-  n.cnt = __ldg(reinterpret_cast<const int4*>(p + 7));
-  return n;
+  v.nx = __ldg(p + o.ox);
+  v.fx = __ldg(p + 1 - o.ox);
+  v.ny = __ldg(p + 2 + o.oy);
+  v.fy = __ldg(p + 3 - o.oy);
+  v.nz = __ldg(p + 4 + o.oz);
+  v.fz = __ldg(p + 5 - o.oz);
+  v.link = __ldg(reinterpret_cast<const int4*>(p + 6));
+  v.cnt = __ldg(reinterpret_cast<const int4*>(p + 7));
+  return v;
 }
 
 // Stage the first `want` nodes (the top BVH levels, stored breadth-first) of subdomain s.
@@ -140,23 +168,26 @@ __device__ __forceinline__ int comp4(const int4& v, int c) {
 }
 
 // Slab tests of a node's children against (t0, t1]: bit c is set when child c exists and its
-// box meets the interval; tn[c] is its entry distance.
-__device__ __forceinline__ unsigned child_hits(const RayPre& rp, const Node& n, float t0, float t1,
+// box meets the interval; tn[c] is its entry distance.  The exit distance is widened by
+// Ize's 1 + 2 gamma(3) so that rounding cannot produce a false miss.
+__device__ __forceinline__ unsigned child_hits(const RayPre& rp, const NodeView& n, float t0, float t1,
                                                float (&tn)[kBvhWidth]) {
   unsigned m = 0u;
 #pragma unroll
   for (int c = 0; c < kBvhWidth; ++c) {
-    float t;
-    const bool h = box_hit(rp, comp4(n.lox, c), comp4(n.hix, c), comp4(n.loy, c), comp4(n.hiy, c), comp4(n.loz, c),
-                           comp4(n.hiz, c), t0, t1, &t);
-    tn[c] = t;
-    if (h && comp4(n.link, c) >= 0) m |= 1u << c;
+    const float tnx = fmaf(comp4(n.nx, c), rp.inv.x, -rp.oinv.x), tfx = fmaf(comp4(n.fx, c), rp.inv.x, -rp.oinv.x);
+    const float tny = fmaf(comp4(n.ny, c), rp.inv.y, -rp.oinv.y), tfy = fmaf(comp4(n.fy, c), rp.inv.y, -rp.oinv.y);
+    const float tnz = fmaf(comp4(n.nz, c), rp.inv.z, -rp.oinv.z), tfz = fmaf(comp4(n.fz, c), rp.inv.z, -rp.oinv.z);
+    const float tmin = fmaxf(fmaxf(tnx, tny), fmaxf(tnz, t0));
+    const float tmax = fminf(fminf(tfx, tfy), fminf(tfz, t1));
+    tn[c] = tmin;
+    if (tmin <= tmax * 1.0000004f && comp4(n.link, c) >= 0) m |= 1u << c;
   }
   return m;
 }
 
 // Children of a node that are leaves (bit c: child c holds triangle records).
-__device__ __forceinline__ unsigned leaf_mask(const Node& n) {
+__device__ __forceinline__ unsigned leaf_mask(const NodeView& n) {
   return (n.cnt.x > 0 ? 1u : 0u) | (n.cnt.y > 0 ? 2u : 0u) | (n.cnt.z > 0 ? 4u : 0u) | (n.cnt.w > 0 ? 8u : 0u);
 }
 
@@ -246,8 +277,9 @@ __device__ __forceinline__ bool any_hit_walk(const DevScene& sc, const Node* s_n
   int spn = 0;
   const int root = sc.root[s];
   int node = root;
+  const Octant oct = octant_of(rp);
   for (;;) {
-    Node n = load_node(sc.nodes, s_nodes, node, root, n_staged);
+    const NodeView n = load_view(sc.nodes, s_nodes, node, root, n_staged, oct);
     if (kStats) ++*n_nodes;
     float tn[kBvhWidth];
     const unsigned hm = child_hits(rp, n, t0, t1, tn);
@@ -319,6 +351,7 @@ __device__ __forceinline__ uint32_t closest_hit_warp(const DevScene& sc, const N
   int sp = 0;
   const int root = sc.root[s];
   int node = root;
+  const Octant oct = octant_of(rp);
   float tbest = t1;
   uint32_t best = kMissPrim;
   bool done = !live;
@@ -332,7 +365,7 @@ __device__ __forceinline__ uint32_t closest_hit_warp(const DevScene& sc, const N
     done = true;
    }
    if (!done) {
-    Node n = load_node(sc.nodes, s_nodes, node, root, n_staged);
+    const NodeView n = load_view(sc.nodes, s_nodes, node, root, n_staged, oct);
     if (kStats) ++*n_nodes;
     float tn[kBvhWidth];
     const unsigned hm = child_hits(rp, n, t0, tbest, tn);
@@ -412,6 +445,7 @@ __device__ __forceinline__ bool any_hit_walk_warp(const DevScene& sc, const Node
   int spn = 0;
   const int root = sc.root[s];
   int node = root;
+  const Octant oct = octant_of(rp);
   bool done = !live, res = false;
   int steps = 0;
   bool any = __any_sync(0xffffffffu, !done);
@@ -422,7 +456,7 @@ __device__ __forceinline__ bool any_hit_walk_warp(const DevScene& sc, const Node
     done = true;
    }
    if (!done) {
-    Node n = load_node(sc.nodes, s_nodes, node, root, n_staged);
+    const NodeView n = load_view(sc.nodes, s_nodes, node, root, n_staged, oct);
     if (kStats) ++*n_nodes;
     float tn[kBvhWidth];
     const unsigned hm = child_hits(rp, n, t0, t1, tn);

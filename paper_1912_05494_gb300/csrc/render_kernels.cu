@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(kBlock) k_raygen(RenderParams p, WaveDesc w, R
 // spills; 9 without the bound), 8 x 128 for shadow rays without brute-force tiles (64
 // registers; 6 without).
 template <bool kStats, int kB>
-__global__ void __launch_bounds__(kB, 6 * 128 / kB) k_traverse(RenderParams p, Sched sch, int top_nodes, QueuePair qp,
+__global__ void __launch_bounds__(kB, 7 * 128 / kB) k_traverse(RenderParams p, Sched sch, int top_nodes, QueuePair qp,
                                                      RayBuf rb, float2* hits, Control* ctl) {
   extern __shared__ Node s_nodes[];
   int b = blockIdx.x;
