@@ -59,16 +59,28 @@ __global__ void k_film_accum_bundle(RenderParams p, WaveDesc w, const float* __r
   const uint32_t px_i = cell / (uint32_t)p.n_bundles, j = cell - px_i * (uint32_t)p.n_bundles;
   const uint32_t lam = j * B + b;
   if (lam >= L) return;
-  double acc = film[(size_t)px_i * L + lam];
-  for (uint32_t ls = 0; ls < w.ns; ++ls) {
-    const size_t slot = (size_t)(ls * w.nc + lc) * B + b;
-    const float v = path_L[slot];
-    acc += (double)v;
-    const size_t out = ((size_t)px_i * p.spp + (w.s0 + ls)) * L + lam;
-    if (path_rad_out) path_rad_out[out] = v;
-    if (path_hash_out && p.path_hash) path_hash_out[out] = p.path_hash[slot];
+  // the wave's samples, in sample order, summed exactly as a double-float pair (GB300's FP64
+  // rate made one FP64 add per sample the kernel's limit), added once to the FP64 film;
+  // values are loaded kS at a time
+  constexpr uint32_t kS = 8;
+  const size_t stride = (size_t)w.nc * B;
+  const size_t slot0 = (size_t)lc * B + b;
+  float hi = 0.f, lo = 0.f;
+  for (uint32_t s0 = 0; s0 < w.ns; s0 += kS) {
+    const uint32_t m = min(kS, w.ns - s0);
+    float v[kS];
+#pragma unroll
+    for (uint32_t u = 0; u < kS; ++u) v[u] = u < m ? path_L[slot0 + (size_t)(s0 + u) * stride] : 0.f;
+#pragma unroll
+    for (uint32_t u = 0; u < kS; ++u) {
+      if (u >= m) break;
+      two_sum_add(hi, lo, v[u]);
+      const size_t out = ((size_t)px_i * p.spp + (w.s0 + s0 + u)) * L + lam;
+      if (path_rad_out) path_rad_out[out] = v[u];
+      if (path_hash_out && p.path_hash) path_hash_out[out] = p.path_hash[slot0 + (size_t)(s0 + u) * stride];
+    }
   }
-  film[(size_t)px_i * L + lam] = acc;
+  film[(size_t)px_i * L + lam] += (double)hi + (double)lo;
 }
 
 // ------------------------------------------------------------------------------ launchers

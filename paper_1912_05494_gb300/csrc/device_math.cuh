@@ -53,6 +53,19 @@ __device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a
 __device__ __forceinline__ float3 normalize3(float3 a) { return rsqrtf(dot3(a, a)) * a; }
 __device__ __forceinline__ float comp3(float3 a, int i) { return i == 0 ? a.x : (i == 1 ? a.y : a.z); }
 
+// ------------------------------------------------------------------ double-float sums
+// (hi, lo) += v without rounding error: Knuth's TwoSum (TAOCP vol. 2, 4.2.2) adds v to hi and
+// keeps the rounding error of that addition in lo (explicitly rounded operations, so the
+// compiler cannot reassociate them).  hi + lo then carries about 48 significant bits; a sum
+// of a few dozen FP32 values of one sign is exact to well below FP32 rounding.
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
+  const float s = __fadd_rn(hi, v);
+  const float bv = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(v, bv));
+  hi = s;
+  lo = __fadd_rn(lo, e);
+}
+
 // ------------------------------------------------------------------ complex FP32
 struct cf { float re, im; };
 __device__ __forceinline__ cf cmul(cf a, cf b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }

@@ -23,9 +23,8 @@ __global__ void __launch_bounds__(kBlock) k_raygen(RenderParams p, WaveDesc w, R
   dev_raygen(p, w, i, i < w.n_paths, rb, q, q_count, qcap, ctl);
 }
 
-// Resident blocks per SM measured best: 12 x 128 threads for traversal (40 registers, small
-// spills; 9 without the bound), 8 x 128 for shadow rays without brute-force tiles (64
-// registers; 6 without).
+// Resident blocks per SM: 7 x 128 threads for traversal (4-wide nodes seen by the ray's
+// octant, 72 registers), 6 x 128 for shadow rays without brute-force tiles (80 registers).
 template <bool kStats, int kB>
 __global__ void __launch_bounds__(kB, 7 * 128 / kB) k_traverse(RenderParams p, Sched sch, int top_nodes, QueuePair qp,
                                                      RayBuf rb, float2* hits, Control* ctl) {
@@ -93,6 +92,28 @@ __global__ void k_film_accum(RenderParams p, WaveDesc w, const float* __restrict
   uint32_t cell = w.c0 + lc;
   uint32_t L = (uint32_t)p.sp.n_lambda;
   uint32_t px_i = cell / L, lam = cell - px_i * L;
+  if (p.n_slots == 1) {
+    // one slot per path: the wave's samples, in sample order, summed exactly as a
+    // double-float pair and added once to the FP64 film (as k_film_accum_bundle)
+    constexpr uint32_t kS = 8;
+    float hi = 0.f, lo = 0.f;
+    for (uint32_t s0 = 0; s0 < w.ns; s0 += kS) {
+      const uint32_t m = min(kS, w.ns - s0);
+      float v[kS];
+#pragma unroll
+      for (uint32_t u = 0; u < kS; ++u) v[u] = u < m ? path_L[(size_t)(s0 + u) * w.nc + lc] : 0.f;
+#pragma unroll
+      for (uint32_t u = 0; u < kS; ++u) {
+        if (u >= m) break;
+        two_sum_add(hi, lo, v[u]);
+        const size_t out = ((size_t)px_i * p.spp + (w.s0 + s0 + u)) * L + lam;
+        if (path_rad_out) path_rad_out[out] = v[u];
+        if (path_hash_out && p.path_hash) path_hash_out[out] = p.path_hash[(size_t)(s0 + u) * w.nc + lc];
+      }
+    }
+    film[cell] += (double)hi + (double)lo;
+    return;
+  }
   double acc = film[cell];
   for (uint32_t ls = 0; ls < w.ns; ++ls) {
     uint32_t path = ls * w.nc + lc;
