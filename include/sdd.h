@@ -280,6 +280,37 @@ typedef struct {
 } sdd_scene_info;
 sdd_status sdd_scene_get_info(const sdd_scene* scene, sdd_scene_info* out);
 
+/* Host-side build of the subdomain split and of the per-subdomain BVHs that sdd_scene_create
+ * makes for the same desc (Sec. 5: the geometry is split once, every sub-domain keeps its own
+ * hierarchy), without a device: for inspecting and testing the structure the traversal
+ * kernels walk.  Only the geometry fields of desc are read (vertices, indices, n_subdomains,
+ * split_axis, ray_epsilon_m) and validated as sdd_scene_create validates them.
+ *
+ * Node, 128 bytes (int32 / float, child c in element c of each array):
+ *   float lo_x[4], hi_x[4], lo_y[4], hi_y[4], lo_z[4], hi_z[4]; int32 link[4], count[4];
+ *   count[c] > 0: leaf child, triangle records [link[c], link[c] + count[c]);
+ *   count[c] == 0 and link[c] >= 0: inner child, node link[c] (absolute index);
+ *   link[c] < 0: no child.  Every subdomain's nodes form one block in breadth-first order
+ *   from root[s].
+ * Triangle record, 48 bytes: float v0[3], uint32 primitive index, float v1[3], pad,
+ *   float v2[3], pad.
+ * Call with nodes and tris NULL to get the sizes in *info; then again with buffers of
+ * info->n_nodes nodes (nodes_cap >= that) and info->n_tri_records records.  root and
+ * n_nodes_sub (n_subdomains entries) and planes (n_subdomains + 1 entries, first -inf and
+ * last +inf) are filled when not NULL.  Caller-owned buffers; SDD_ERR_ARG on invalid
+ * geometry or a buffer that is too small, SDD_ERR_OOM when the host allocation fails. */
+typedef struct {
+  int n_subdomains, split_axis;
+  int bvh_max_depth;   /* levels of the binary SAH tree before its collapse to 4-wide nodes */
+  int stack_need;      /* deepest traversal stack a walk of any subdomain's tree can need;
+                          sdd_scene_create refuses a scene above 64 */
+  int64_t n_nodes, n_tri_records;
+  float slop;          /* a triangle is referenced by every slab its box overlaps widened by
+                          this much, its box clipped to the widened slab */
+} sdd_bvh_info;
+sdd_status sdd_bvh_build_host(const sdd_scene_desc* desc, sdd_bvh_info* info, void* nodes, int64_t nodes_cap,
+                              void* tris, int64_t tris_cap, int32_t* root, int32_t* n_nodes_sub, float* planes);
+
 /* Batched closest-hit query (used by tests and by tools): n rays with device origins
  * [n][3] and directions [n][3] (float), t in (0, inf).  Writes device t_out[n] (inf on a
  * miss) and prim_out[n] (-1 on a miss), going through the subdomain queues exactly as

@@ -1376,6 +1376,51 @@ sdd_status photon_build(sdd_scene* s, const sdd_photon_opts* o, sdd_photon_maps*
   return SDD_OK;
 }
 
+// The geometry checks of a scene description (vertices, indices, subdomain count, axis).
+sdd_status validate_geometry(const sdd_scene_desc* d) {
+  if (d->n_vertices < 3 || !d->vertices) return fail(SDD_ERR_ARG, "need >= 3 vertices");
+  if (d->n_triangles < 1 || !d->indices) return fail(SDD_ERR_ARG, "need >= 1 triangle");
+  if (d->n_triangles > (1 << 28)) return fail(SDD_ERR_ARG, "too many triangles");
+  if (d->n_subdomains < 1 || d->n_subdomains > kMaxSubdomains) return fail(SDD_ERR_ARG, "n_subdomains must be 1..64");
+  if (d->split_axis < -1 || d->split_axis > 2) return fail(SDD_ERR_ARG, "split_axis must be -1, 0, 1 or 2");
+  for (long long i = 0; i < 3LL * d->n_vertices; ++i)
+    if (!std::isfinite(d->vertices[i])) return fail(SDD_ERR_ARG, "non-finite vertex coordinate");
+  for (long long i = 0; i < 3LL * d->n_triangles; ++i)
+    if (d->indices[i] >= (uint32_t)d->n_vertices) return fail(SDD_ERR_ARG, "triangle index out of range");
+  return SDD_OK;
+}
+
+// The split of a validated description (Sec. 5): the scene box, the split axis (the longest
+// unless given), S slabs of equal length along it (the outer two open), the ray epsilon
+// (*eps) and the slop by which a triangle's slab overlap is widened.
+BuildInput split_input(const sdd_scene_desc* d, float* eps) {
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300}, amax = 0.0;
+  for (int i = 0; i < d->n_vertices; ++i)
+    for (int a = 0; a < 3; ++a) {
+      double x = d->vertices[3 * i + a];
+      lo[a] = std::min(lo[a], x);
+      hi[a] = std::max(hi[a], x);
+      amax = std::max(amax, std::fabs(x));
+    }
+  int axis = d->split_axis;
+  if (axis < 0) axis = (hi[0] - lo[0] >= hi[1] - lo[1] && hi[0] - lo[0] >= hi[2] - lo[2]) ? 0
+                       : (hi[1] - lo[1] >= hi[2] - lo[2] ? 1 : 2);
+  *eps = d->ray_epsilon_m > 0.f ? d->ray_epsilon_m : (float)std::max(1e-5, 2e-6 * amax);
+  BuildInput in;
+  in.verts = d->vertices;
+  in.idx = d->indices;
+  in.n_tris = d->n_triangles;
+  in.n_sub = d->n_subdomains;
+  in.axis = axis;
+  in.slop = (float)std::max<double>(*eps, 1e-6 * amax);
+  for (int i = 0; i <= in.n_sub; ++i) {
+    if (i == 0) in.planes[i] = -INFINITY;
+    else if (i == in.n_sub) in.planes[i] = INFINITY;
+    else in.planes[i] = (float)(lo[axis] + (hi[axis] - lo[axis]) * i / in.n_sub);
+  }
+  return in;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1387,16 +1432,9 @@ sdd_status sdd_scene_create(const sdd_scene_desc* d, sdd_scene** out) {
   g_err.clear();
   if (!d || !out) return fail(SDD_ERR_ARG, "NULL desc or out");
   *out = nullptr;
-  if (d->n_vertices < 3 || !d->vertices) return fail(SDD_ERR_ARG, "need >= 3 vertices");
-  if (d->n_triangles < 1 || !d->indices || !d->material_of_triangle) return fail(SDD_ERR_ARG, "need >= 1 triangle");
-  if (d->n_triangles > (1 << 28)) return fail(SDD_ERR_ARG, "too many triangles");
+  if (sdd_status r = validate_geometry(d)) return r;
+  if (!d->material_of_triangle) return fail(SDD_ERR_ARG, "need >= 1 triangle");
   if (d->n_materials < 1 || !d->materials) return fail(SDD_ERR_ARG, "need >= 1 material");
-  if (d->n_subdomains < 1 || d->n_subdomains > kMaxSubdomains) return fail(SDD_ERR_ARG, "n_subdomains must be 1..64");
-  if (d->split_axis < -1 || d->split_axis > 2) return fail(SDD_ERR_ARG, "split_axis must be -1, 0, 1 or 2");
-  for (long long i = 0; i < 3LL * d->n_vertices; ++i)
-    if (!std::isfinite(d->vertices[i])) return fail(SDD_ERR_ARG, "non-finite vertex coordinate");
-  for (long long i = 0; i < 3LL * d->n_triangles; ++i)
-    if (d->indices[i] >= (uint32_t)d->n_vertices) return fail(SDD_ERR_ARG, "triangle index out of range");
   for (int t = 0; t < d->n_triangles; ++t)
     if (d->material_of_triangle[t] >= d->n_materials) return fail(SDD_ERR_ARG, "material index out of range");
   sdd_scene* s = new (std::nothrow) sdd_scene;
@@ -1468,36 +1506,13 @@ sdd_status sdd_scene_create(const sdd_scene_desc* d, sdd_scene** out) {
   for (int i = 0; i < 3; ++i) s->sun_dir[i] = il.sun_dir[i];
   s->sun_half = il.sun_half_angle_rad;
 
-  // scene box, split axis, planes, epsilon
-  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300}, amax = 0.0;
-  for (int i = 0; i < d->n_vertices; ++i)
-    for (int a = 0; a < 3; ++a) {
-      double x = d->vertices[3 * i + a];
-      lo[a] = std::min(lo[a], x);
-      hi[a] = std::max(hi[a], x);
-      amax = std::max(amax, std::fabs(x));
-    }
-  int axis = d->split_axis;
-  if (axis < 0) axis = (hi[0] - lo[0] >= hi[1] - lo[1] && hi[0] - lo[0] >= hi[2] - lo[2]) ? 0
-                       : (hi[1] - lo[1] >= hi[2] - lo[2] ? 1 : 2);
-  s->eps = d->ray_epsilon_m > 0.f ? d->ray_epsilon_m : (float)std::max(1e-5, 2e-6 * amax);
   if (d->slab_polarisation != 0 && d->slab_polarisation != 1) {
     delete s;
     return fail(SDD_ERR_ARG, "slab_polarisation must be 0 or 1");
   }
   s->slab_pol = d->slab_polarisation;
-  BuildInput in;
-  in.verts = d->vertices;
-  in.idx = d->indices;
-  in.n_tris = d->n_triangles;
-  in.n_sub = d->n_subdomains;
-  in.axis = axis;
-  in.slop = (float)std::max<double>(s->eps, 1e-6 * amax);
-  for (int i = 0; i <= in.n_sub; ++i) {
-    if (i == 0) in.planes[i] = -INFINITY;
-    else if (i == in.n_sub) in.planes[i] = INFINITY;
-    else in.planes[i] = (float)(lo[axis] + (hi[axis] - lo[axis]) * i / in.n_sub);
-  }
+  const BuildInput in = split_input(d, &s->eps);
+  const int axis = in.axis;
   HostBVH bvh;
   try {
     build_scene_bvh(in, bvh);
@@ -1588,6 +1603,43 @@ sdd_status sdd_scene_get_info(const sdd_scene* s, sdd_scene_info* out) {
   out->n_nodes = s->n_nodes;
   out->device_bytes = (int64_t)(s->nodes.n * sizeof(Node) + s->tris.n * sizeof(TriRec) + s->prim.n * sizeof(float4));
   for (int i = 0; i <= s->n_sub; ++i) out->planes[i] = s->dev.planes[i];
+  return SDD_OK;
+}
+
+sdd_status sdd_bvh_build_host(const sdd_scene_desc* d, sdd_bvh_info* info, void* nodes, int64_t nodes_cap,
+                              void* tris, int64_t tris_cap, int32_t* root, int32_t* n_nodes_sub, float* planes) {
+  g_err.clear();
+  if (!d || !info) return fail(SDD_ERR_ARG, "NULL desc or info");
+  if (sdd_status r = validate_geometry(d)) return r;
+  float eps = 0.f;
+  const BuildInput in = split_input(d, &eps);
+  HostBVH bvh;
+  try {
+    build_scene_bvh(in, bvh);
+  } catch (const std::bad_alloc&) {
+    return fail(SDD_ERR_OOM, "host allocation failed during BVH build");
+  }
+  info->n_subdomains = in.n_sub;
+  info->split_axis = in.axis;
+  info->bvh_max_depth = bvh.max_depth;
+  info->stack_need = bvh.stack_need;
+  info->n_nodes = (int64_t)bvh.nodes.size();
+  info->n_tri_records = (int64_t)bvh.tris.size();
+  info->slop = in.slop;
+  if (nodes) {
+    if (nodes_cap < info->n_nodes) return fail(SDD_ERR_ARG, "nodes buffer too small");
+    std::memcpy(nodes, bvh.nodes.data(), sizeof(Node) * bvh.nodes.size());
+  }
+  if (tris) {
+    if (tris_cap < info->n_tri_records) return fail(SDD_ERR_ARG, "tris buffer too small");
+    std::memcpy(tris, bvh.tris.data(), sizeof(TriRec) * bvh.tris.size());
+  }
+  for (int k = 0; k < in.n_sub; ++k) {
+    if (root) root[k] = bvh.root[k];
+    if (n_nodes_sub) n_nodes_sub[k] = bvh.n_nodes[k];
+  }
+  if (planes)
+    for (int k = 0; k <= in.n_sub; ++k) planes[k] = in.planes[k];
   return SDD_OK;
 }
 

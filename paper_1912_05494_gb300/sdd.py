@@ -106,6 +106,12 @@ class sdd_scene_info(C.Structure):
                 ("device_bytes", C.c_int64), ("planes", C.c_float * 65)]
 
 
+class sdd_bvh_info(C.Structure):
+    _fields_ = [("n_subdomains", C.c_int), ("split_axis", C.c_int), ("bvh_max_depth", C.c_int),
+                ("stack_need", C.c_int), ("n_nodes", C.c_int64), ("n_tri_records", C.c_int64),
+                ("slop", C.c_float)]
+
+
 def lib():
     """Load libsdd.so; raises if it has not been built (no fallback path exists)."""
     global _lib
@@ -125,6 +131,8 @@ def lib():
         L.sdd_set_tuning.argtypes = [vp, C.POINTER(sdd_tuning)]
         L.sdd_get_tuning.argtypes = [vp, C.POINTER(sdd_tuning)]
         L.sdd_scene_get_info.argtypes = [vp, C.POINTER(sdd_scene_info)]
+        L.sdd_bvh_build_host.argtypes = [C.POINTER(sdd_scene_desc), C.POINTER(sdd_bvh_info), vp, C.c_int64, vp,
+                                         C.c_int64, vp, vp, vp]
         L.sdd_trace_closest.argtypes = [vp, i32, vp, vp, vp, vp, vp]
         L.sdd_trace_closest_noalloc.argtypes = [vp, i32, vp, vp, vp, vp, vp]
         L.sdd_eval_optics.argtypes = [i32, vp, vp, vp, vp, vp, i32, vp, vp, vp, vp]
@@ -198,9 +206,9 @@ def _c(a, dt):
 
 
 # ----------------------------------------------------------------------------- scene
-def sdd_scene_create(sd, n_subdomains=None, split_axis=None, ray_epsilon_m=None, tileset=None):
-    """Create a device scene from a ``scenes.SceneData``; returns the opaque handle.  Scenes
-    with heterogeneous tiles need ``tileset`` (an sdd_tileset handle built from sd.tiles)."""
+def _scene_desc(sd, n_subdomains=None, split_axis=None, ray_epsilon_m=None, tileset=None):
+    """The sdd_scene_desc of a ``scenes.SceneData`` and the arrays it points into (keep them
+    alive while the descriptor is in use)."""
     keep = []
 
     def P(a, dt):
@@ -247,9 +255,45 @@ def sdd_scene_create(sd, n_subdomains=None, split_axis=None, ray_epsilon_m=None,
     d.ray_epsilon_m = float(sd.ray_eps if ray_epsilon_m is None else ray_epsilon_m)
     d.tiles = tileset
     d.slab_polarisation = int(getattr(sd, "slab_polarisation", 0))
+    keep.append(mats)
+    return d, keep
+
+
+def sdd_scene_create(sd, n_subdomains=None, split_axis=None, ray_epsilon_m=None, tileset=None):
+    """Create a device scene from a ``scenes.SceneData``; returns the opaque handle.  Scenes
+    with heterogeneous tiles need ``tileset`` (an sdd_tileset handle built from sd.tiles)."""
+    d, keep = _scene_desc(sd, n_subdomains, split_axis, ray_epsilon_m, tileset)
     h = C.c_void_p()
     _check(lib().sdd_scene_create(C.byref(d), C.byref(h)))
     return h
+
+
+# Layout of the BVH node and triangle record sdd_bvh_build_host returns (child c in element c).
+BVH_NODE = np.dtype([("lo_x", "<f4", 4), ("hi_x", "<f4", 4), ("lo_y", "<f4", 4), ("hi_y", "<f4", 4),
+                     ("lo_z", "<f4", 4), ("hi_z", "<f4", 4), ("link", "<i4", 4), ("count", "<i4", 4)])
+BVH_TRI = np.dtype([("v0", "<f4", 3), ("prim", "<u4"), ("v1", "<f4", 3), ("pad1", "<u4"), ("v2", "<f4", 3),
+                    ("pad2", "<u4")])
+
+
+def sdd_bvh_build_host(sd, n_subdomains=None, split_axis=None, ray_epsilon_m=None) -> dict:
+    """The subdomain split and BVHs sdd_scene_create would build for ``sd``, built on the host
+    (no device): info fields, nodes (BVH_NODE), triangle records (BVH_TRI), per-subdomain root
+    and node count, and the planes."""
+    d, keep = _scene_desc(sd, n_subdomains, split_axis, ray_epsilon_m)
+    info = sdd_bvh_info()
+    L = lib()
+    _check(L.sdd_bvh_build_host(C.byref(d), C.byref(info), None, 0, None, 0, None, None, None))
+    n_sub = info.n_subdomains
+    nodes = np.zeros(info.n_nodes, BVH_NODE)
+    tris = np.zeros(info.n_tri_records, BVH_TRI)
+    root = np.zeros(n_sub, np.int32)
+    nn = np.zeros(n_sub, np.int32)
+    planes = np.zeros(n_sub + 1, np.float32)
+    _check(L.sdd_bvh_build_host(C.byref(d), C.byref(info), nodes.ctypes.data, nodes.size, tris.ctypes.data,
+                                tris.size, root.ctypes.data, nn.ctypes.data, planes.ctypes.data))
+    out = {f[0]: getattr(info, f[0]) for f in info._fields_}
+    out.update(nodes=nodes, tris=tris, root=root, n_nodes_sub=nn, planes=planes)
+    return out
 
 
 def sdd_scene_destroy(h):
