@@ -602,10 +602,10 @@ def run_gpu(args):
                 "issue_frac": ctr.get("issue_frac") if not persistent else None,
                 "counters_source": os.path.relpath(NCU_SUMMARY[args.batched], ROOT) if ctr else None,
                 "note": "algorithmic bytes = 4-wide BVH nodes x 128 B + triangle records x 48 B + 44 B ray state per "
-                        "subdomain visit; the ~35 MB BVH is L2-resident, so frac can exceed what DRAM moves. "
+                        "subdomain visit; the ~18 MB scene (nodes, triangle records, normals) is L2-resident, so frac can exceed what DRAM moves. "
                         "traffic / l2_traffic: DRAM / L2 bytes per launch scaled from the committed ncu capture; "
                         "l2_frac = L2 throughput and issue_frac = issue slots active, as fractions of ncu's peaks, "
-                        "from the same capture: the walk is latency-bound at ~2/3 of its issue slots"}
+                        "from the same capture: the walk is bound by instruction issue (~2/3 of the slots active), not by DRAM"}
 
     photons = None
     if rank == 0 and world == 1 and not args.no_photons:
