@@ -198,7 +198,8 @@ sdd_status sdd_render_to_host(sdd_scene* scene, const sdd_camera* cam, const sdd
 /* Launch-shape knobs of a scene (chosen by the autotuner; the defaults are safe):
  *   traverse_block: threads per block of the traversal kernels: 64, 128 (default) or 256;
  *   top_nodes:      BVH nodes per subdomain (the top levels, stored breadth-first) that each
- *                   traversal block stages in shared memory, 0..640 (0 = none, default);
+ *                   traversal block stages in shared memory, 0..384 (48 KB of 128-byte nodes;
+ *                   0 = none, default);
  *   wave_paths:     paths per wave when sdd_render_opts.wave_paths is 0 (0 = 2^26, or 2^25
  *                   bundle paths with spectral bundles);
  *   no_graph:       batched form only: 1 = launch the frame's kernels directly instead of

@@ -1781,7 +1781,10 @@ sdd_status sdd_set_tuning(sdd_scene* s, const sdd_tuning* t) {
   if (!s || !t) return fail(SDD_ERR_ARG, "NULL argument");
   if (t->traverse_block != 64 && t->traverse_block != 128 && t->traverse_block != 256)
     return fail(SDD_ERR_ARG, "traverse_block must be 64, 128 or 256");
-  if (t->top_nodes < 0 || t->top_nodes > 640) return fail(SDD_ERR_ARG, "top_nodes must be in [0, 640]");
+  // staged nodes take the 48 KB of shared memory a block may use without opting in
+  constexpr int kMaxStaged = (int)((48 * 1024) / sizeof(Node));
+  static_assert(kMaxStaged == 384, "the message below names the bound");
+  if (t->top_nodes < 0 || t->top_nodes > kMaxStaged) return fail(SDD_ERR_ARG, "top_nodes must be in [0, 384]");
   if (t->wave_paths < 0) return fail(SDD_ERR_ARG, "wave_paths must be >= 0");
   if (t->no_graph != 0 && t->no_graph != 1) return fail(SDD_ERR_ARG, "no_graph must be 0 or 1");
   if (t->queue_capacity < 0) return fail(SDD_ERR_ARG, "queue_capacity must be >= 0");
