@@ -17,6 +17,8 @@ import pytest
 
 from paper_1912_05494_gb300 import scenes as S
 
+ERR_ARG = -1  # SDD_ERR_ARG of include/sdd.h
+
 
 @pytest.fixture(scope="module")
 def sdd():
@@ -138,3 +140,22 @@ def test_invalid_geometry_is_refused(sdd):
     bad = S.SceneData(**{**sc.__dict__, "indices": np.full_like(sc.indices, 10 ** 6)})
     with pytest.raises(sdd.SddError):
         sdd.sdd_bvh_build_host(bad, n_subdomains=2)
+
+
+def test_too_small_buffers_are_refused(sdd):
+    """Buffers below the sizes the first call reports are refused with SDD_ERR_ARG."""
+    import ctypes as C
+    sc = S.tiny_scene(3, n_triangles=40)
+    d, keep = sdd._scene_desc(sc, n_subdomains=2)
+    info = sdd.sdd_bvh_info()
+    L = sdd.lib()
+    assert L.sdd_bvh_build_host(C.byref(d), C.byref(info), None, 0, None, 0, None, None, None) == 0
+    nodes = np.zeros(info.n_nodes, sdd.BVH_NODE)
+    tris = np.zeros(info.n_tri_records, sdd.BVH_TRI)
+    short = L.sdd_bvh_build_host(C.byref(d), C.byref(info), nodes.ctypes.data, nodes.size - 1, None, 0, None, None,
+                                 None)
+    assert short == ERR_ARG and b"nodes buffer too small" in L.sdd_last_error()
+    short = L.sdd_bvh_build_host(C.byref(d), C.byref(info), None, 0, tris.ctypes.data, tris.size - 1, None, None,
+                                 None)
+    assert short == ERR_ARG and b"tris buffer too small" in L.sdd_last_error()
+    assert L.sdd_bvh_build_host(C.byref(d), None, None, 0, None, 0, None, None, None) == ERR_ARG
